@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark of the boundary-integral hot path on one GPU (or N independent replicas).
+
+Workload (default): two perturbed unit drops of degree p = 32, centre gap 2.1 (surface gap
+0.1), lambda = 5, R = 2, Q = 0.5, uniform field E = z (the two-drop configuration), inputs
+seeded and synthetic. One step is one operator stage of a time step for a new geometry:
+  set_drops (geometry + singular self rows of every kernel),
+  electric GMRES solve to 1e-8 (Eq. galerkin_En),
+  Laplace single layer of the solution (potential of Eq. BIE01),
+  Stokes single layer of a traction density (right-hand side of Eq. main_eq),
+  Stokes GMRES solve to 1e-8 (double layer, Eq. main_eq).
+Metric: target-source kernel pairs per second = operator applications in the step x
+sum_i N_t(i) x sum_j N_s(j) / step time (self pairs counted as N_t N_s rotated pairs).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import inputs  # noqa: E402
+
+METRIC = "target-source kernel pairs/s, GMRES time-to-1e-8 per step: mixed/batched vs FP64"
+UNIT = "pairs/s"
+FP64_PEAK_TFLOPS = 1.25         # GB300 FP64 rate (vector and tensor), see the design doc
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def workload(p: int = 32):
+    cfg = inputs.config2(p=p, seed=0, gap=0.1)
+    rng = np.random.default_rng(1234)
+    f = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
+    return cfg, f
+
+
+def pairs_per_application(cfg) -> int:
+    nt = sum((d.p + 1) * (2 * d.p + 2) for d in cfg.drops)
+    q = [2 * d.p + 1 for d in cfg.drops]
+    ns = sum((qq + 1) * (2 * qq + 2) for qq in q)
+    return nt * ns
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, index: int = 0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+               "--format=csv,noheader,nounits", "-lms", "200"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- own arm
+
+def run_own(args):
+    import torch
+    import paper_1811_10270_gb300 as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    S.lib()
+
+    cfg, f = workload(args.p)
+    prec = S.FP32_COMP if args.precision == "fp32comp" else S.FP64
+    ctx = S.Context(precision=prec, R=cfg.R, gmres_tol=1e-8, gmres_restart=50)
+    ps = [d.p for d in cfg.drops]
+    lam = [d.lam for d in cfg.drops]
+    x_host = np.concatenate([d.xcoef.ravel() for d in cfg.drops])
+    f_host = np.concatenate([a.ravel() for a in f])
+    xc = torch.tensor(x_host, device=dev)
+    F = torch.tensor(f_host, device=dev)
+    nc = sum((p + 1) ** 2 for p in ps)
+    nt = sum((p + 1) * (2 * p + 2) for p in ps)
+    rhs_e = torch.empty(nc, device=dev, dtype=torch.float64)
+    En = torch.empty(nc, device=dev, dtype=torch.float64)
+    phi = torch.empty(nc, device=dev, dtype=torch.float64)
+    rhs_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    u = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    P = pairs_per_application(cfg)
+    E = cfg.E_u
+
+    def step(xdev, Fdev):
+        ctx.set_drops(ps, xdev, lam)
+        ctx.electric_rhs(E, rhs_e)
+        it_e, res_e = ctx.gmres_solve(S.SYS_ELECTRIC, rhs_e, En)
+        ctx.eval_electric(S.LAPLACE_SL, En, phi, S.OUT_COEF)
+        ctx.eval_stokes(Fdev, None, rhs_s, S.OUT_COEF)
+        it_s, res_s = ctx.gmres_solve(S.SYS_STOKES, rhs_s, u)
+        apps = (it_e + 1) + 1 + 1 + (it_s + 1)
+        return apps, it_e, it_s, res_e, res_s
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step(xc, F)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    launches0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    apps_total = 0
+    stats = []
+    for _ in range(args.steps):
+        r = step(xc, F)
+        apps_total += r[0]
+        stats.append(r)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count() - launches0
+    cls_ms = {}
+    cls_n = {}
+    names = {S.K_SELF_WEIGHTS: "self_weights", S.K_SELF_ANALYSIS: "self_analysis",
+             S.K_PAIRS: "pairs", S.K_SELF_GEMV: "self_gemv", S.K_SHT: "sht"}
+    for k, nm in names.items():
+        cls_ms[nm], cls_n[nm] = ctx.kernel_stats(k)
+    ctx.set_timing(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        a = torch.tensor([apps_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(a)
+        apps_total = int(a.item())
+    value = apps_total * P / (ms / 1e3)
+
+    # end to end: host inputs copied in, solutions copied out, every step
+    x_pin = torch.tensor(x_host).pin_memory()
+    F_pin = torch.tensor(f_host).pin_memory()
+    En_h = torch.empty(nc, dtype=torch.float64).pin_memory()
+    u_h = torch.empty(3 * nc, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    apps_e2e = 0
+    for _ in range(args.steps):
+        xd = x_pin.to(dev, non_blocking=True)
+        Fd = F_pin.to(dev, non_blocking=True)
+        r = step(xd, Fd)
+        apps_e2e += r[0]
+        En_h.copy_(En, non_blocking=True)
+        u_h.copy_(u, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    e2e_value = apps_e2e * P / (ms_e2e / 1e3)
+
+    # roofline of the dominant kernel class (measured above with CUDA events)
+    dom = max(cls_ms, key=lambda k: cls_ms[k])
+    roof = roofline(dom, cls_ms[dom], cls_n[dom], cfg, args.steps, args.precision, P, apps_total)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "fp32comp" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "two drops p=32 gap=0.1 (lambda=5, R=2, Q=0.5, E=z), one operator "
+                               "stage: geometry + singular rows + electric GMRES + potential + "
+                               "Stokes RHS + Stokes GMRES, tol 1e-8",
+                   "pair_sums": args.precision, "pairs_per_application": P,
+                   "applications_per_step": apps_total / max(1, args.steps) / max(1, world),
+                   "gmres_iters": {"electric": stats[-1][1], "stokes": stats[-1][2]},
+                   "gmres_final_resid": {"electric": stats[-1][3], "stokes": stats[-1][4]},
+                   "l2": "working set (singular rows 0.53 GB) exceeds the 129 MB L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "phase_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(x_host.nbytes + f_host.nbytes),
+                "d2h_bytes_per_step": int(8 * (nc + 3 * nc))},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.p, args.cpu_targets)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def roofline(dom, ms, n, cfg, steps, precision, P, apps):
+    p = cfg.drops[0].p
+    q = 2 * p + 1
+    nt = (p + 1) * (2 * p + 2)
+    ns = (q + 1) * (2 * q + 2)
+    if dom == "self_weights":
+        # per (target, rotated node): Fourier synthesis 9 fields x 2p terms x 2 FMA, Legendre
+        # 18 (p+1)(p+2)/2 FMA per (target, latitude) spread over 2q+2 nodes, ~70 flops weights
+        per_unit = 9 * 2 * p * 2 * 2 + 18 * (p + 1) * (p + 2) / 2 * 2 / (2 * q + 2) + 70
+        units = sum(nt * ns for _ in cfg.drops) * steps
+        flops = per_unit * units
+        ach = flops / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "k_self_weights (FP64)", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n),
+                "peak_source": "GB300 FP64 rate 1.25 TFLOP/s (derived, see DESIGN.md)",
+                "per_unit_flops": per_unit}
+    if dom == "self_analysis":
+        per_unit = (p + 1) * 2 * 2 + 2 * (p + 1) * (p + 2) / 2 * 2 / (2 * q + 2)
+        units = sum(nt * ns * 14 for _ in cfg.drops) * steps
+        ach = per_unit * units / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "k_analysis_fourier/legendre (FP64)", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n)}
+    if dom == "pairs":
+        per_pair = 20
+        pk = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+        cross = P - sum(((d.p + 1) * (2 * d.p + 2)) * ((2 * d.p + 2) * (4 * d.p + 4)) for d in cfg.drops)
+        ach = per_pair * cross * apps / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "k_pairs (FP32)", "achieved": ach, "peak": pk,
+                "unit": "TFLOP/s", "frac": ach / pk, "traffic": None, "launches": n,
+                "avg_launch_ms": ms / max(1, n)}
+    return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": None, "unit": "GB/s",
+            "frac": None, "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def cpu_baseline(p: int, targets_per_drop: int):
+    """The FP64 oracle timed on a bounded sample of the same workload: the electric double
+    layer (self rows + regular sums from the other drop) at a few targets per drop."""
+    from oracle import operators
+    cfg, _ = workload(p)
+    rng = np.random.default_rng(7)
+    sig = [inputs.random_density(d.p, rng)[0] for d in cfg.drops]
+    t0 = time.perf_counter()
+    sysm = operators.System([operators.DropGeom(d.xcoef, d.p, d.lam) for d in cfg.drops])
+    ns_tot = sum(d.xs.shape[1] for d in sysm.drops)
+    done = 0
+    for i, d in enumerate(sysm.drops):
+        sel = np.linspace(0, d.nt - 1, targets_per_drop).astype(int)
+        sysm.laplace_targets("ladl", sig, i, sel)
+        done += len(sel) * ns_tot
+    dt = time.perf_counter() - t0
+    cores = threads_used()
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "electric double layer at %d targets per drop of the p=%d two-drop "
+                      "workload (geometry set-up included), %.1f s" % (targets_per_drop, p, dt)}
+
+
+def threads_used():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(x.get("num_threads", 1)) for x in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_baseline(args.p, 2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.p, args.cpu_targets))
+    wall = time.perf_counter() - t0
+    v = float(np.mean([x["value"] for x in vals]))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "two drops p=%d gap=0.1, FP64 CPU oracle on a bounded sample" % args.p},
+           "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"],
+                            "value": v, "unit": UNIT},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--precision", default="fp32comp", choices=["fp32comp", "fp64"])
+    ap.add_argument("--p", type=int, default=32)
+    ap.add_argument("--cpu-targets", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_own(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * shbim.h -- C ABI of the GB300 boundary-integral operator library.
+ *
+ * Operators of Sorgentone, Tornberg & Vlahovska, "A 3D boundary integral method for the
+ * electrohydrodynamics of surfactant-covered drops": the Laplace layer operators of the
+ * leaky-dielectric problem (Eqs. BIE01, E_n, dl_op_laplace), the Stokes single and double
+ * layer (Eqs. main_eq, GandT, op_stokes) and their Galerkin projections (Eqs. BIM_galerkin,
+ * galerkin_En), discretised with spherical harmonics on Gaussian grids (Section 3), the
+ * regular rule (Eq. reg_quadrature) and the rotated-pole singular rule (Eq. mod_weights).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Coefficients: real orthonormal spherical harmonics, Condon-Shortley phase,
+ *   S_n0 = Pbar_n^0(cos t), S_nm = sqrt2 Pbar_n^m cos(m f), S_n,-m = sqrt2 Pbar_n^m sin(m f),
+ *   Pbar_n^m = sqrt((2n+1)/(4 pi) (n-m)!/(n+m)!) P_n^m   (Eqs. normalized_spharm, pneg).
+ *   A degree-p scalar field is (p+1)^2 doubles, entry n*n + n + m.
+ * Grids: a degree-q grid has q+1 Gauss-Legendre latitudes theta_j = acos(t_j) ordered by
+ *   increasing theta, and 2q+2 longitudes phi_k = pi k/(q+1) (Eq. spharm_ex); values are
+ *   stored [j][k] row-major, (q+1)(2q+2) doubles per field.
+ * Drops: drop i has degree p_i. Its targets are the nodes of its degree-p_i grid; its
+ *   quadrature sources are the nodes of its degree q_i = 2 p_i + 1 grid.
+ * Multi-drop vectors are concatenated drop-major. A scalar density has (p_i+1)^2 entries
+ *   for drop i; a vector density (Stokes) stores its three components component-major
+ *   inside each drop: [drop0: x-coefs, y-coefs, z-coefs][drop1: ...].
+ *   Target-grid outputs are concatenated the same way, (p_i+1)(2p_i+2) per component.
+ * Ownership: every pointer argument named *_dev is device memory owned by the caller and
+ *   must stay valid until the work queued on `stream` has finished. *_host arguments are
+ *   read before the call returns. The library owns the context, its tables, geometry and
+ *   workspaces (allocated with cudaMalloc in shbim_set_drops and freed in shbim_destroy).
+ * Streams: every call queues its work on `stream` (a cudaStream_t passed as void*; NULL
+ *   means the legacy default stream) and returns without synchronising, except where a
+ *   call says it reads results back to the host.
+ * Errors: every call returns 0 on success or a negative SHBIM_ERR_* code; the message of
+ *   the last failure is returned by shbim_last_error(ctx). No call aborts the process.
+ */
+#ifndef SHBIM_H
+#define SHBIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHBIM_OK 0
+#define SHBIM_ERR_ARG (-1)          /* invalid argument (sizes, null pointers, state) */
+#define SHBIM_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define SHBIM_ERR_NOMEM (-3)        /* device allocation failed */
+#define SHBIM_ERR_NOT_CONVERGED (-4)/* GMRES hit its iteration limit */
+#define SHBIM_ERR_NONFINITE (-6)    /* a NaN or Inf was detected in a reduction */
+
+#define SHBIM_CONTINUE 0            /* shbim_gmres_step: not converged yet */
+#define SHBIM_CONVERGED 1           /* shbim_gmres_step: relative residual <= tol */
+
+/* Arithmetic of the all-pairs sums (the singular self rows, the transforms and GMRES are
+ * always FP64). */
+#define SHBIM_PREC_FP64 0           /* FP64 sums */
+#define SHBIM_PREC_FP32_COMP 1      /* FP32 pair arithmetic, positions relative to the drop
+                                       centres, compensated (two-sum) accumulation */
+
+/* Kernels of the Laplace operator (shbim_eval_electric `which`). Both carry 1/(4 pi). */
+#define SHBIM_LAPLACE_DL 0          /* L[s](x0) = 1/(4pi) int s(x) (x0-x).n(x0) / r^3 dS  (Eq. E_n) */
+#define SHBIM_LAPLACE_SL 1          /* S_L[s](x0) = 1/(4pi) int s(x) / r dS */
+
+/* Output kinds. */
+#define SHBIM_OUT_GRID 0            /* values at every target (degree-p grid of each drop) */
+#define SHBIM_OUT_COEF 1            /* Galerkin coefficients: forward transform of the values */
+
+/* Transform directions and grids for shbim_sht. */
+#define SHBIM_SHT_INVERSE 0         /* coefficients -> grid values (Eq. spharm_ex) */
+#define SHBIM_SHT_FORWARD 1         /* grid values -> Galerkin inner products (., Y_nm) */
+#define SHBIM_GRID_BASE 0           /* degree-p grid (the targets) */
+#define SHBIM_GRID_UP 1             /* degree 2p+1 grid (the quadrature sources) */
+
+/* Linear systems for GMRES. */
+#define SHBIM_SYS_ELECTRIC 0        /* 1/2 s - (R-1)/(R+1) sum_j L_j[s] = b       (Eq. galerkin_En) */
+#define SHBIM_SYS_STOKES 1          /* (lam_i+1) u - sum_j (lam_j-1) D_j[u] = b   (Eq. main_eq)    */
+
+typedef struct shbim_ctx shbim_ctx;
+
+typedef struct shbim_opts {
+  int precision;        /* SHBIM_PREC_* for the all-pairs sums */
+  int gmres_restart;    /* Krylov dimension m before a restart (1..200); 0 -> 50 */
+  double gmres_tol;     /* relative residual ||b - A x|| / ||b|| to stop at; 0 -> 1e-8 */
+  int gmres_maxiter;    /* total Arnoldi steps allowed; 0 -> 1000 */
+  double R;             /* conductivity ratio of the electric system (Eq. EneEni) */
+} shbim_opts;
+
+/* Create a context. `opts` may be NULL (defaults: FP64, m = 50, tol 1e-8, R = 1).
+ * Returns SHBIM_ERR_ARG for out-of-range options. */
+int shbim_create(const shbim_opts* opts, shbim_ctx** out);
+
+/* Destroy a context and free its device memory (synchronises the device first). */
+int shbim_destroy(shbim_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none). Valid until the next call. */
+const char* shbim_last_error(shbim_ctx* ctx);
+
+/* Change the arithmetic of the all-pairs sums or the electric ratio R after creation. */
+int shbim_set_precision(shbim_ctx* ctx, int precision);
+int shbim_set_R(shbim_ctx* ctx, double R);
+
+/* Define the drops and build everything that depends only on their shapes:
+ * transform tables per distinct degree, target and source geometry (x, outward normal n,
+ * area element; Section 2 and Eq. reg_quadrature) and the singular self rows of every
+ * kernel (rotated-pole rule, Section 3.1).
+ *   n_drops      number of drops (>= 1)
+ *   p_host       degree of each drop, 1 <= p <= 64
+ *   lambda_host  viscosity ratio of each drop (Eq. main_eq); may be NULL (all 1)
+ *   xcoef_dev    position coefficients, per drop 3 (p+1)^2 doubles (x, y, z component-major)
+ * Allocates device memory (SHBIM_ERR_NOMEM on failure). Synchronises `stream` on entry,
+ * reads the degree-0 position coefficients back to the host (the drop centres) and
+ * synchronises again while building; the last kernels it queues on `stream` may still be
+ * running when it returns. Replaces any previous drop set of the context. */
+int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const double* lambda_host,
+                    const double* xcoef_dev, void* stream);
+
+/* Sizes of the current drop set: total scalar coefficients sum (p_i+1)^2, total targets
+ * sum (p_i+1)(2p_i+2) and total sources sum (q_i+1)(2q_i+2). */
+int shbim_sizes(shbim_ctx* ctx, int64_t* ncoef, int64_t* ntarget, int64_t* nsource);
+
+/* Geometry of the targets as built by shbim_set_drops: per target x, y, z, nx, ny, nz and
+ * the area element J relative to the unit sphere, each an array of ntarget doubles laid
+ * out [x..][y..][z..][nx..][ny..][nz..][J..] (7 * ntarget doubles in out_dev). */
+int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream);
+
+/* Right-hand side of the electric system (Eq. galerkin_En): Galerkin coefficients of
+ * R/(R+1) E_inf . n on every drop, for the far field E_inf(x) = E_u + E_q (x, -y, 0)
+ * (a uniform part E_u, a 3-vector read from the host, plus a linear field of strength E_q;
+ * the paper's uniform and quadrupole fields are both of this form up to orientation).
+ *   out_dev   ncoef coefficients */
+int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, double* out_dev,
+                       void* stream);
+
+/* Spherical-harmonic transform of n_fields fields of one drop's degree (Section 3).
+ *   drop         index of the drop whose degree p (and grid) is used
+ *   dir          SHBIM_SHT_INVERSE: in = n_fields x (p+1)^2 coefficients,
+ *                                  out = n_fields x grid values
+ *                SHBIM_SHT_FORWARD: in = n_fields x grid values, out = coefficients
+ *                (forward = Galerkin inner products by the regular rule on that grid)
+ *   grid         SHBIM_GRID_BASE (degree p) or SHBIM_GRID_UP (degree 2p+1) */
+int shbim_sht(shbim_ctx* ctx, int drop, int dir, int grid, int n_fields, const double* in_dev,
+              double* out_dev, void* stream);
+
+/* Laplace layer operator of the electric problem applied to a scalar density on all drops:
+ * for every target x0 on drop i, sum over drops j of the kernel `which` integrated over
+ * S_j -- the regular rule (Eq. reg_quadrature) on the degree-q source grid for j != i and
+ * the rotated-pole singular rule (Eq. mod_weights) for j == i.
+ *   dens_dev   sum_i (p_i+1)^2 coefficients
+ *   out_dev    SHBIM_OUT_GRID: ntarget values; SHBIM_OUT_COEF: ncoef Galerkin coefficients */
+int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, double* out_dev,
+                        int out_kind, void* stream);
+
+/* Stokes layer operators (Eqs. op_stokes, GandT) on all drops:
+ *   out = sum_j S_j[f_j] + sum_j (lam_j - 1) D_j[u_j]
+ * with the same regular / singular split as shbim_eval_electric.
+ *   f_dev, u_dev  vector densities, 3 sum_i (p_i+1)^2 coefficients each; either may be
+ *                 NULL (that term is omitted), not both
+ *   out_dev       SHBIM_OUT_GRID: 3 ntarget values; SHBIM_OUT_COEF: 3 ncoef coefficients */
+int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, double* out_dev,
+                      int out_kind, void* stream);
+
+/* GMRES on one of the Galerkin systems (the paper does not name its solver; this is
+ * restarted GMRES with classical Gram-Schmidt applied twice, in FP64).
+ * shbim_gmres_begin: set up the system `sys` with right-hand side rhs_dev (length n = ncoef
+ *   for SHBIM_SYS_ELECTRIC, 3 ncoef for SHBIM_SYS_STOKES) and initial guess x0_dev (NULL
+ *   means zero); computes the initial residual (reads one norm back to the host).
+ * shbim_gmres_step: one Arnoldi step (one operator application), restarting when the
+ *   Krylov space is full; reads the new column's norms back to the host and returns
+ *   SHBIM_CONTINUE, SHBIM_CONVERGED, or SHBIM_ERR_NOT_CONVERGED after gmres_maxiter steps.
+ *   *resid_host (may be NULL) receives the current relative residual estimate.
+ * shbim_gmres_finish: write the solution to x_dev (length n) and return the number of
+ *   Arnoldi steps taken in *iters_host (may be NULL).
+ * shbim_gmres_solve: begin + step until converged + finish; also reports the final true
+ *   relative residual ||b - A x|| / ||b|| in *resid_host. */
+int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
+                      void* stream);
+int shbim_gmres_step(shbim_ctx* ctx, double* resid_host, void* stream);
+int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* stream);
+int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
+                      double* x_dev, int* iters_host, double* resid_host, void* stream);
+
+/* Number of kernel launches the library has queued since the context was created. */
+int64_t shbim_launch_count(shbim_ctx* ctx);
+
+/* Kernel timing (measurement support, off by default). When on, the library brackets every
+ * launch of the timed kernel classes below with CUDA events on the launching stream.
+ * shbim_kernel_stats synchronises the device and returns the summed milliseconds and the
+ * number of launches of one class since timing was (re)enabled. */
+#define SHBIM_K_SELF_WEIGHTS 0      /* rotated-grid synthesis + kernel weights (singular rows) */
+#define SHBIM_K_SELF_ANALYSIS 1     /* analysis of the weights (singular rows) */
+#define SHBIM_K_PAIRS 2             /* all-pairs sums */
+#define SHBIM_K_SELF_GEMV 3         /* application of the singular rows */
+#define SHBIM_K_SHT 4               /* transforms of densities and outputs */
+#define SHBIM_K_COUNT 5
+int shbim_set_timing(shbim_ctx* ctx, int on);
+int shbim_kernel_stats(shbim_ctx* ctx, int kernel_class, double* ms_host, int64_t* launches_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHBIM_H */

@@ -39,15 +39,16 @@ class DropGeom:
         return self.x0.shape[1]
 
     def rows(self, kind: str, targets=None):
-        """Singular self rows for the given target indices (all when None)."""
-        if targets is None:
-            if kind not in self._rows:
-                self._rows[kind] = np.stack([
-                    quadrature.self_rows(self.xcoef, self.p, self.q, self.th[t], self.ph[t],
-                                         [kind])[kind] for t in range(self.nt)])
-            return self._rows[kind]
-        return np.stack([quadrature.self_rows(self.xcoef, self.p, self.q, self.th[t],
-                                              self.ph[t], [kind])[kind] for t in targets])
+        """Singular self rows of one kernel for the given target indices (all when None).
+        All four kernels are computed together per target and cached."""
+        tsel = range(self.nt) if targets is None else targets
+        missing = [t for t in tsel if (t, kind) not in self._rows]
+        for t in missing:
+            r = quadrature.self_rows(self.xcoef, self.p, self.q, self.th[t], self.ph[t],
+                                     ["lsl", "ladl", "sto_s", "sto_d"])
+            for k, v in r.items():
+                self._rows[(t, k)] = v
+        return np.stack([self._rows[(t, kind)] for t in tsel])
 
 
 class System:

@@ -1,0 +1,223 @@
+"""Python binding of the shbim C ABI (include/shbim.h): argument marshalling only.
+
+Every computation runs in the CUDA library libshbim.so built in-tree by build.py. There is no
+CPU fallback: if the library is missing or cannot be loaded, every call raises.
+Tensors passed in must be CUDA float64 tensors, contiguous, on the current device; the
+current torch stream is passed to the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libshbim.so")
+
+FP64 = 0
+FP32_COMP = 1
+LAPLACE_DL = 0
+LAPLACE_SL = 1
+OUT_GRID = 0
+OUT_COEF = 1
+SHT_INVERSE = 0
+SHT_FORWARD = 1
+GRID_BASE = 0
+GRID_UP = 1
+SYS_ELECTRIC = 0
+SYS_STOKES = 1
+CONTINUE = 0
+CONVERGED = 1
+
+EXPORTS = [
+    "shbim_create", "shbim_destroy", "shbim_last_error", "shbim_set_precision", "shbim_set_R",
+    "shbim_set_drops", "shbim_sizes", "shbim_target_geometry", "shbim_sht", "shbim_eval_electric",
+    "shbim_eval_stokes", "shbim_gmres_begin", "shbim_gmres_step", "shbim_gmres_finish",
+    "shbim_gmres_solve", "shbim_launch_count", "shbim_electric_rhs", "shbim_set_timing",
+    "shbim_kernel_stats",
+]
+K_SELF_WEIGHTS = 0
+K_SELF_ANALYSIS = 1
+K_PAIRS = 2
+K_SELF_GEMV = 3
+K_SHT = 4
+K_COUNT = 5
+
+
+class ShbimError(RuntimeError):
+    pass
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("gmres_maxiter", ctypes.c_int),
+                ("R", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libshbim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ShbimError("libshbim.so is not built (run paper_1811_10270_gb300.build.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "shbim_create": (i32, [P(Opts), P(vp)]),
+        "shbim_destroy": (i32, [vp]),
+        "shbim_last_error": (ctypes.c_char_p, [vp]),
+        "shbim_set_precision": (i32, [vp, i32]),
+        "shbim_set_R": (i32, [vp, dp]),
+        "shbim_set_drops": (i32, [vp, i32, P(ctypes.c_int32), P(dp), vp, vp]),
+        "shbim_sizes": (i32, [vp, P(i64), P(i64), P(i64)]),
+        "shbim_target_geometry": (i32, [vp, vp, vp]),
+        "shbim_sht": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
+        "shbim_eval_electric": (i32, [vp, i32, vp, vp, i32, vp]),
+        "shbim_eval_stokes": (i32, [vp, vp, vp, vp, i32, vp]),
+        "shbim_gmres_begin": (i32, [vp, i32, vp, vp, vp]),
+        "shbim_gmres_step": (i32, [vp, P(dp), vp]),
+        "shbim_gmres_finish": (i32, [vp, vp, P(i32), vp]),
+        "shbim_gmres_solve": (i32, [vp, i32, vp, vp, vp, P(i32), P(dp), vp]),
+        "shbim_launch_count": (i64, [vp]),
+        "shbim_electric_rhs": (i32, [vp, P(dp), dp, vp, vp]),
+        "shbim_set_timing": (i32, [vp, i32]),
+        "shbim_kernel_stats": (i32, [vp, i32, P(dp), P(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ShbimError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One shbim context (shbim_create / shbim_destroy)."""
+
+    def __init__(self, precision: int = FP64, gmres_restart: int = 50, gmres_tol: float = 1e-8,
+                 gmres_maxiter: int = 1000, R: float = 1.0):
+        L = lib()
+        self._L = L
+        o = Opts(precision, gmres_restart, gmres_tol, gmres_maxiter, R)
+        h = ctypes.c_void_p()
+        rc = L.shbim_create(ctypes.byref(o), ctypes.byref(h))
+        if rc != 0:
+            raise ShbimError("shbim_create failed (%d)" % rc)
+        self._h = h
+        self.p = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.shbim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc < 0:
+            msg = self._L.shbim_last_error(self._h).decode()
+            raise ShbimError("%s failed (%d): %s" % (what, rc, msg))
+        return rc
+
+    # ---------------------------------------------------------------- set-up
+    def set_precision(self, precision: int):
+        self._check(self._L.shbim_set_precision(self._h, precision), "shbim_set_precision")
+
+    def set_R(self, R: float):
+        self._check(self._L.shbim_set_R(self._h, float(R)), "shbim_set_R")
+
+    def set_drops(self, p_list, xcoef, lam_list=None):
+        n = len(p_list)
+        P = (ctypes.c_int32 * n)(*[int(p) for p in p_list])
+        lam = None if lam_list is None else (ctypes.c_double * n)(*[float(x) for x in lam_list])
+        self._check(self._L.shbim_set_drops(self._h, n, P, lam, _ptr(xcoef), _stream()),
+                    "shbim_set_drops")
+        self.p = [int(p) for p in p_list]
+
+    def sizes(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self._L.shbim_sizes(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                    "shbim_sizes")
+        return a.value, b.value, c.value
+
+    def target_geometry(self, out):
+        self._check(self._L.shbim_target_geometry(self._h, _ptr(out), _stream()),
+                    "shbim_target_geometry")
+
+    # ---------------------------------------------------------------- operators
+    def sht(self, drop: int, direction: int, grid: int, n_fields: int, inp, out):
+        self._check(self._L.shbim_sht(self._h, drop, direction, grid, n_fields, _ptr(inp), _ptr(out),
+                                      _stream()), "shbim_sht")
+
+    def eval_electric(self, which: int, dens, out, out_kind: int = OUT_COEF):
+        self._check(self._L.shbim_eval_electric(self._h, which, _ptr(dens), _ptr(out), out_kind,
+                                                _stream()), "shbim_eval_electric")
+
+    def eval_stokes(self, f, u, out, out_kind: int = OUT_COEF):
+        self._check(self._L.shbim_eval_stokes(self._h, _ptr(f), _ptr(u), _ptr(out), out_kind,
+                                              _stream()), "shbim_eval_stokes")
+
+    # ---------------------------------------------------------------- GMRES
+    def gmres_begin(self, sys: int, rhs, x0=None):
+        self._check(self._L.shbim_gmres_begin(self._h, sys, _ptr(rhs), _ptr(x0), _stream()),
+                    "shbim_gmres_begin")
+
+    def gmres_step(self):
+        r = ctypes.c_double()
+        rc = self._check(self._L.shbim_gmres_step(self._h, ctypes.byref(r), _stream()),
+                         "shbim_gmres_step")
+        return rc, r.value
+
+    def gmres_finish(self, x):
+        it = ctypes.c_int32()
+        self._check(self._L.shbim_gmres_finish(self._h, _ptr(x), ctypes.byref(it), _stream()),
+                    "shbim_gmres_finish")
+        return it.value
+
+    def gmres_solve(self, sys: int, rhs, x, x0=None):
+        it = ctypes.c_int32()
+        r = ctypes.c_double()
+        self._check(self._L.shbim_gmres_solve(self._h, sys, _ptr(rhs), _ptr(x0), _ptr(x),
+                                              ctypes.byref(it), ctypes.byref(r), _stream()),
+                    "shbim_gmres_solve")
+        return it.value, r.value
+
+    def electric_rhs(self, E_u, out, E_q: float = 0.0):
+        E = (ctypes.c_double * 3)(*[float(v) for v in E_u])
+        self._check(self._L.shbim_electric_rhs(self._h, E, float(E_q), _ptr(out), _stream()),
+                    "shbim_electric_rhs")
+
+    def set_timing(self, on: bool):
+        self._check(self._L.shbim_set_timing(self._h, 1 if on else 0), "shbim_set_timing")
+
+    def kernel_stats(self, cls: int):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._L.shbim_kernel_stats(self._h, cls, ctypes.byref(ms), ctypes.byref(n)),
+                    "shbim_kernel_stats")
+        return ms.value, n.value
+
+    def launch_count(self) -> int:
+        return int(self._L.shbim_launch_count(self._h))

@@ -1,0 +1,465 @@
+// C ABI entry points: context, drop set-up, transforms and operator evaluation.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <set>
+
+#include "internal.h"
+
+namespace shbim {
+
+int fail(shbim_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(shbim_ctx* ctx, cudaError_t e, const char* what) {
+  if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return SHBIM_ERR_CUDA;
+}
+
+int pairs_tile_targets();
+
+namespace {
+
+void free_drop_state(shbim_ctx* ctx) {
+  for (auto& d : ctx->drops) {
+    cudaFree(d.rows_lap);
+    cudaFree(d.rows_sto);
+  }
+  ctx->drops.clear();
+  cudaFree(ctx->geo.tgt);
+  cudaFree(ctx->geo.src);
+  cudaFree(ctx->geo.tgt32);
+  cudaFree(ctx->geo.src32);
+  cudaFree(ctx->geo.tgt_drop);
+  ctx->geo = Geometry{};
+  cudaFree(ctx->tiles_dev);
+  ctx->tiles_dev = nullptr;
+  cudaFree(ctx->drops_dev);
+  ctx->drops_dev = nullptr;
+  cudaFree(ctx->dens_up);
+  ctx->dens_up = nullptr;
+  cudaFree(ctx->dens_up32);
+  ctx->dens_up32 = nullptr;
+  cudaFree(ctx->part);
+  ctx->part = nullptr;
+  cudaFree(ctx->grid_out);
+  ctx->grid_out = nullptr;
+  ctx->tiles.clear();
+  ctx->n_drops = 0;
+  ctx->ncoef = ctx->ntarget = ctx->nsource = 0;
+}
+
+template <typename T>
+int dalloc(shbim_ctx* ctx, T** p, size_t n, const char* what) {
+  if (cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, SHBIM_ERR_NOMEM, std::string("cudaMalloc ") + what);
+  }
+  return SHBIM_OK;
+}
+
+bool valid_opts(const shbim_opts& o) {
+  return (o.precision == SHBIM_PREC_FP64 || o.precision == SHBIM_PREC_FP32_COMP) &&
+         o.gmres_restart >= 1 && o.gmres_restart <= 200 && o.gmres_tol > 0.0 && o.gmres_tol < 1.0 &&
+         o.gmres_maxiter >= 1 && std::isfinite(o.R) && o.R > 0.0;
+}
+
+}  // namespace
+}  // namespace shbim
+
+using namespace shbim;
+
+extern "C" {
+
+int shbim_create(const shbim_opts* opts, shbim_ctx** out) {
+  if (!out) return SHBIM_ERR_ARG;
+  *out = nullptr;
+  shbim_opts o{};
+  o.precision = SHBIM_PREC_FP64;
+  o.gmres_restart = 50;
+  o.gmres_tol = 1e-8;
+  o.gmres_maxiter = 1000;
+  o.R = 1.0;
+  if (opts) {
+    o = *opts;
+    if (o.gmres_restart == 0) o.gmres_restart = 50;
+    if (o.gmres_tol == 0.0) o.gmres_tol = 1e-8;
+    if (o.gmres_maxiter == 0) o.gmres_maxiter = 1000;
+  }
+  if (!valid_opts(o)) return SHBIM_ERR_ARG;
+  shbim_ctx* ctx = new shbim_ctx();
+  ctx->opts = o;
+  *out = ctx;
+  return SHBIM_OK;
+}
+
+int shbim_destroy(shbim_ctx* ctx) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  cudaDeviceSynchronize();
+  free_drop_state(ctx);
+  for (auto& kv : ctx->tables) free_degree_tables(kv.second);
+  cudaFree(ctx->sht_scratch);
+  cudaFree(ctx->rot_coef);
+  cudaFree(ctx->wbuf);
+  cudaFree(ctx->vbuf);
+  cudaFree(ctx->gm.V);
+  cudaFree(ctx->gm.w);
+  cudaFree(ctx->gm.x);
+  cudaFree(ctx->gm.b);
+  cudaFree(ctx->gm.h);
+  cudaFree(ctx->gm.Av);
+  cudaFree(ctx->gm.diag);
+  cudaFree(ctx->gm.y);
+  if (ctx->gm.h_host) cudaFreeHost(ctx->gm.h_host);
+  delete ctx;
+  return SHBIM_OK;
+}
+
+const char* shbim_last_error(shbim_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int shbim_set_precision(shbim_ctx* ctx, int precision) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_FP32_COMP)
+    return fail(ctx, SHBIM_ERR_ARG, "precision must be SHBIM_PREC_FP64 or SHBIM_PREC_FP32_COMP");
+  ctx->opts.precision = precision;
+  return SHBIM_OK;
+}
+
+int shbim_set_R(shbim_ctx* ctx, double R) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (!(R > 0.0) || !std::isfinite(R)) return fail(ctx, SHBIM_ERR_ARG, "R must be positive");
+  ctx->opts.R = R;
+  return SHBIM_OK;
+}
+
+int64_t shbim_launch_count(shbim_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int shbim_sizes(shbim_ctx* ctx, int64_t* nc, int64_t* nt, int64_t* ns) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (nc) *nc = ctx->ncoef;
+  if (nt) *nt = ctx->ntarget;
+  if (ns) *ns = ctx->nsource;
+  return SHBIM_OK;
+}
+
+int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const double* lambda_host,
+                    const double* xcoef_dev, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (n_drops < 1 || !p_host || !xcoef_dev) return fail(ctx, SHBIM_ERR_ARG, "need n_drops >= 1, p and x");
+  for (int i = 0; i < n_drops; ++i) {
+    if (p_host[i] < 1 || p_host[i] > 64) return fail(ctx, SHBIM_ERR_ARG, "degree p must be in [1, 64]");
+    if (lambda_host && (!std::isfinite(lambda_host[i]) || lambda_host[i] <= 0.0))
+      return fail(ctx, SHBIM_ERR_ARG, "viscosity ratios must be positive");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  free_drop_state(ctx);
+  int rc;
+  // tables per distinct degree (kept across calls)
+  for (int i = 0; i < n_drops; ++i) {
+    const int p = p_host[i];
+    if (!ctx->tables.count(p)) {
+      DegreeTables* T = nullptr;
+      if ((rc = build_degree_tables(ctx, p, &T))) return rc;
+      ctx->tables[p] = T;
+    }
+  }
+  // layout
+  ctx->drops.resize(n_drops);
+  int64_t co = 0, to = 0, so = 0;
+  for (int i = 0; i < n_drops; ++i) {
+    Drop& d = ctx->drops[i];
+    d.p = p_host[i];
+    d.q = 2 * d.p + 1;
+    d.nc = ncoef(d.p);
+    d.nt = npts(d.p);
+    d.ns = npts(d.q);
+    d.coef_off = co;
+    d.tgt_off = to;
+    d.src_off = so;
+    d.lam = lambda_host ? lambda_host[i] : 1.0;
+    d.tab = ctx->tables[d.p];
+    co += d.nc;
+    to += d.nt;
+    so += d.ns;
+  }
+  ctx->n_drops = n_drops;
+  ctx->ncoef = co;
+  ctx->ntarget = to;
+  ctx->nsource = so;
+  // centres: the mean position over the parameter sphere, x_00 / sqrt(4 pi)
+  for (auto& d : ctx->drops) {
+    double c00[3];
+    for (int c = 0; c < 3; ++c)
+      SHBIM_CUDA(ctx, cudaMemcpy(&c00[c], xcoef_dev + 3 * d.coef_off + (int64_t)c * d.nc,
+                                 sizeof(double), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < 3; ++c) d.centre[c] = c00[c] / std::sqrt(4.0 * kPi);
+  }
+  // geometry and workspaces
+  if ((rc = dalloc(ctx, &ctx->geo.tgt, 7 * (size_t)to, "targets")) ||
+      (rc = dalloc(ctx, &ctx->geo.src, 7 * (size_t)so, "sources")) ||
+      (rc = dalloc(ctx, &ctx->geo.tgt32, 7 * (size_t)to, "targets32")) ||
+      (rc = dalloc(ctx, &ctx->geo.src32, 7 * (size_t)so, "sources32")) ||
+      (rc = dalloc(ctx, &ctx->geo.tgt_drop, (size_t)to, "target drop ids")) ||
+      (rc = dalloc(ctx, &ctx->dens_up, 6 * (size_t)so, "source strengths")) ||
+      (rc = dalloc(ctx, &ctx->dens_up32, 6 * (size_t)so, "source strengths32")) ||
+      (rc = dalloc(ctx, &ctx->grid_out, 3 * (size_t)to, "target values")))
+    return rc;
+  for (auto& d : ctx->drops) {
+    if ((rc = dalloc(ctx, &d.rows_lap, (size_t)d.nt * kNumLap * d.nc, "laplace rows")) ||
+        (rc = dalloc(ctx, &d.rows_sto, (size_t)d.nt * kNumSto * d.nc, "stokes rows")))
+      return rc;
+  }
+  {
+    std::vector<int> tdrop(to);
+    for (int i = 0; i < n_drops; ++i)
+      std::fill(tdrop.begin() + ctx->drops[i].tgt_off,
+                tdrop.begin() + ctx->drops[i].tgt_off + ctx->drops[i].nt, i);
+    SHBIM_CUDA(ctx, cudaMemcpy(ctx->geo.tgt_drop, tdrop.data(), to * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<DropDev> dd(n_drops);
+    for (int i = 0; i < n_drops; ++i) {
+      const Drop& d = ctx->drops[i];
+      dd[i] = DropDev{d.p, d.q, d.nt, d.ns, d.nc, d.coef_off, d.tgt_off, d.src_off, d.lam,
+                      d.centre[0], d.centre[1], d.centre[2], d.rows_lap, d.rows_sto};
+    }
+    if ((rc = dalloc(ctx, &ctx->drops_dev, n_drops, "drop table"))) return rc;
+    SHBIM_CUDA(ctx, cudaMemcpy(ctx->drops_dev, dd.data(), n_drops * sizeof(DropDev), cudaMemcpyHostToDevice));
+  }
+  // all-pairs tiling: tiles never cross a drop; sources split so that the grid fills the GPU
+  {
+    const int TT = pairs_tile_targets();
+    int64_t min_other = so;
+    for (int i = 0; i < n_drops; ++i) {
+      const Drop& d = ctx->drops[i];
+      for (int t0 = 0; t0 < d.nt; t0 += TT)
+        ctx->tiles.push_back(PairTile{i, (int)(d.tgt_off + t0), std::min(TT, d.nt - t0)});
+      min_other = std::min<int64_t>(min_other, so - d.ns);
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (int64_t)nsm * 8;
+    int64_t splits = (want + (int64_t)ctx->tiles.size() - 1) / (int64_t)ctx->tiles.size();
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, min_other / 512));
+    ctx->pair_splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, 256));
+    if ((rc = dalloc(ctx, &ctx->tiles_dev, ctx->tiles.size(), "tiles"))) return rc;
+    SHBIM_CUDA(ctx, cudaMemcpy(ctx->tiles_dev, ctx->tiles.data(), ctx->tiles.size() * sizeof(PairTile),
+                               cudaMemcpyHostToDevice));
+    if ((rc = dalloc(ctx, &ctx->part, (size_t)ctx->pair_splits * 3 * to, "pair partials"))) return rc;
+  }
+  if ((rc = build_geometry(ctx, xcoef_dev, s))) return rc;
+  if ((rc = build_singular_rows(ctx, xcoef_dev, s))) return rc;
+  return SHBIM_OK;
+}
+
+int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream) {
+  if (!ctx || !out_dev) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(out_dev, ctx->geo.tgt, 7 * ctx->ntarget * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return SHBIM_OK;
+}
+
+int shbim_sht(shbim_ctx* ctx, int drop, int dir, int grid, int n_fields, const double* in_dev,
+              double* out_dev, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (drop < 0 || drop >= ctx->n_drops) return fail(ctx, SHBIM_ERR_ARG, "drop index out of range");
+  if (n_fields < 0 || !in_dev || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "bad fields or pointers");
+  if (grid != SHBIM_GRID_BASE && grid != SHBIM_GRID_UP) return fail(ctx, SHBIM_ERR_ARG, "bad grid");
+  const Drop& d = ctx->drops[drop];
+  const GridTables& g = grid == SHBIM_GRID_BASE ? d.tab->base : d.tab->up;
+  const int64_t n = npts(g.q);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dir == SHBIM_SHT_INVERSE)
+    return sht_synth(ctx, g, n_fields, in_dev, d.nc, 1, out_dev, n, 0, nullptr, nullptr, s);
+  if (dir == SHBIM_SHT_FORWARD) return sht_analysis(ctx, g, n_fields, in_dev, n, true, out_dev, d.nc, s);
+  return fail(ctx, SHBIM_ERR_ARG, "bad direction");
+}
+
+int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, double* out_dev, int out_kind,
+                        void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (which != SHBIM_LAPLACE_DL && which != SHBIM_LAPLACE_SL) return fail(ctx, SHBIM_ERR_ARG, "bad kernel");
+  if (out_kind != SHBIM_OUT_GRID && out_kind != SHBIM_OUT_COEF) return fail(ctx, SHBIM_ERR_ARG, "bad out kind");
+  if (!dens_dev || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  int rc;
+  if (ctx->n_drops > 1) {
+    TimeScope ts(ctx, SHBIM_K_SHT, s);
+    for (auto& d : ctx->drops) {
+      rc = sht_synth_scaled(ctx, d.tab->up, 1, dens_dev + d.coef_off, d.nc, ctx->dens_up + d.src_off, 0,
+                            ctx->geo.src + 6 * ctx->nsource + d.src_off, 1.0,
+                            f32 ? ctx->dens_up32 + d.src_off : nullptr, s);
+      if (rc) return rc;
+    }
+  }
+  double* vals = out_kind == SHBIM_OUT_GRID ? out_dev : ctx->grid_out;
+  {
+    TimeScope ts(ctx, SHBIM_K_SELF_GEMV, s);
+    if ((rc = apply_self_laplace(ctx, which, dens_dev, vals, s))) return rc;
+  }
+  {
+    TimeScope ts(ctx, SHBIM_K_PAIRS, s);
+    if ((rc = pairs_laplace(ctx, which, vals, s))) return rc;
+  }
+  if (out_kind == SHBIM_OUT_COEF) {
+    TimeScope ts(ctx, SHBIM_K_SHT, s);
+    for (auto& d : ctx->drops) {
+      rc = sht_analysis(ctx, d.tab->base, 1, vals + d.tgt_off, d.nt, true, out_dev + d.coef_off, d.nc, s);
+      if (rc) return rc;
+    }
+  }
+  return SHBIM_OK;
+}
+
+int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, double* out_dev,
+                      int out_kind, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (!f_dev && !u_dev) return fail(ctx, SHBIM_ERR_ARG, "need f or u");
+  if (out_kind != SHBIM_OUT_GRID && out_kind != SHBIM_OUT_COEF) return fail(ctx, SHBIM_ERR_ARG, "bad out kind");
+  if (!out_dev) return fail(ctx, SHBIM_ERR_ARG, "null output");
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const int64_t NS = ctx->nsource;
+  int rc;
+  if (ctx->n_drops > 1) {
+    TimeScope ts(ctx, SHBIM_K_SHT, s);
+    for (auto& d : ctx->drops) {
+      const double* w = ctx->geo.src + 6 * NS + d.src_off;
+      if (f_dev) {
+        rc = sht_synth_scaled(ctx, d.tab->up, 3, f_dev + 3 * d.coef_off, d.nc, ctx->dens_up + d.src_off, NS,
+                              w, 1.0, f32 ? ctx->dens_up32 + d.src_off : nullptr, s);
+        if (rc) return rc;
+      }
+      if (u_dev) {
+        rc = sht_synth_scaled(ctx, d.tab->up, 3, u_dev + 3 * d.coef_off, d.nc,
+                              ctx->dens_up + 3 * NS + d.src_off, NS, w, -6.0 * (d.lam - 1.0),
+                              f32 ? ctx->dens_up32 + 3 * NS + d.src_off : nullptr, s);
+        if (rc) return rc;
+      }
+    }
+  }
+  double* vals = out_kind == SHBIM_OUT_GRID ? out_dev : ctx->grid_out;
+  {
+    TimeScope ts(ctx, SHBIM_K_SELF_GEMV, s);
+    if ((rc = apply_self_stokes(ctx, f_dev, u_dev, vals, s))) return rc;
+  }
+  {
+    TimeScope ts(ctx, SHBIM_K_PAIRS, s);
+    if ((rc = pairs_stokes(ctx, f_dev != nullptr, u_dev != nullptr, vals, s))) return rc;
+  }
+  if (out_kind == SHBIM_OUT_COEF) {
+    TimeScope ts(ctx, SHBIM_K_SHT, s);
+    for (auto& d : ctx->drops) {
+      rc = sht_analysis(ctx, d.tab->base, 3, vals + 3 * d.tgt_off, d.nt, true, out_dev + 3 * d.coef_off,
+                        d.nc, s);
+      if (rc) return rc;
+    }
+  }
+  return SHBIM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- timing and right-hand side
+
+namespace shbim {
+
+TimeScope::TimeScope(shbim_ctx* c, int k, cudaStream_t st) : ctx(c), cls(k), s(st) {
+  if (!ctx->timing) return;
+  cudaEvent_t a;
+  if (ctx->event_pool.empty()) {
+    cudaEventCreate(&a);
+  } else {
+    a = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+  }
+  cudaEventRecord(a, s);
+  b = a;
+}
+
+TimeScope::~TimeScope() {
+  if (!ctx->timing || !b) return;
+  cudaEvent_t e;
+  if (ctx->event_pool.empty()) {
+    cudaEventCreate(&e);
+  } else {
+    e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+  }
+  cudaEventRecord(e, s);
+  ctx->timed.push_back(shbim_ctx::TimedRange{cls, b, e});
+}
+
+namespace {
+__global__ void k_field_normal(const double* __restrict__ tgt, int64_t ntarget, double ex, double ey,
+                               double ez, double eq, double scale, double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntarget) return;
+  const double x = tgt[t], y = tgt[ntarget + t];
+  const double nx = tgt[3 * ntarget + t], ny = tgt[4 * ntarget + t], nz = tgt[5 * ntarget + t];
+  out[t] = scale * ((ex + eq * x) * nx + (ey - eq * y) * ny + ez * nz);
+}
+}  // namespace
+
+}  // namespace shbim
+
+extern "C" {
+
+int shbim_set_timing(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  SHBIM_CUDA(ctx, cudaDeviceSynchronize());
+  for (auto& r : ctx->timed) {
+    ctx->event_pool.push_back(r.a);
+    ctx->event_pool.push_back(r.b);
+  }
+  ctx->timed.clear();
+  for (int k = 0; k < SHBIM_K_COUNT; ++k) {
+    ctx->class_ms[k] = 0.0;
+    ctx->class_launches[k] = 0;
+  }
+  ctx->timing = on != 0;
+  return SHBIM_OK;
+}
+
+int shbim_kernel_stats(shbim_ctx* ctx, int cls, double* ms, int64_t* launches) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (cls < 0 || cls >= SHBIM_K_COUNT) return fail(ctx, SHBIM_ERR_ARG, "bad kernel class");
+  SHBIM_CUDA(ctx, cudaDeviceSynchronize());
+  for (auto& r : ctx->timed) {
+    float t = 0.f;
+    SHBIM_CUDA(ctx, cudaEventElapsedTime(&t, r.a, r.b));
+    ctx->class_ms[r.cls] += t;
+    ctx->class_launches[r.cls] += 1;
+    ctx->event_pool.push_back(r.a);
+    ctx->event_pool.push_back(r.b);
+  }
+  ctx->timed.clear();
+  if (ms) *ms = ctx->class_ms[cls];
+  if (launches) *launches = ctx->class_launches[cls];
+  return SHBIM_OK;
+}
+
+int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, double* out_dev, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (!E_u_host || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double R = ctx->opts.R;
+  k_field_normal<<<(unsigned)((ctx->ntarget + 255) / 256), 256, 0, s>>>(
+      ctx->geo.tgt, ctx->ntarget, E_u_host[0], E_u_host[1], E_u_host[2], E_q, R / (R + 1.0), ctx->grid_out);
+  SHBIM_CHECK_LAUNCH(ctx, "k_field_normal");
+  for (auto& d : ctx->drops) {
+    int rc = sht_analysis(ctx, d.tab->base, 1, ctx->grid_out + d.tgt_off, d.nt, true, out_dev + d.coef_off,
+                          d.nc, s);
+    if (rc) return rc;
+  }
+  return SHBIM_OK;
+}
+
+}  // extern "C"

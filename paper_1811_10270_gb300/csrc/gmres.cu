@@ -1,0 +1,350 @@
+// Restarted GMRES on the Galerkin systems, FP64 on the device.
+//
+// The paper solves the Galerkin systems of Eqs. BIM_galerkin and galerkin_En without naming
+// a solver; this is restarted GMRES(m) (Saad & Schultz) with classical Gram-Schmidt applied
+// twice per Arnoldi step (every projection is one kernel, so a step costs a fixed number of
+// launches), Givens rotations for the small least-squares problem on the host, and one
+// device-to-host read of the new Hessenberg column per step.
+//   electric: A s = 1/2 s - (R-1)/(R+1) L[s]           (Eq. galerkin_En)
+//   Stokes:   A u = (lam_i + 1) u - sum_j (lam_j-1) D_j[u]   (Eq. main_eq, Galerkin form)
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace shbim {
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// h[i] = V_i . w for i < nvec (one block per vector, fixed summation order)
+__global__ void k_dots(const double* __restrict__ V, int64_t n, const double* __restrict__ w,
+                       double* __restrict__ h) {
+  const double* v = V + (int64_t)blockIdx.x * n;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(v[e], w[e], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) h[blockIdx.x] = acc;
+}
+
+// w -= sum_i h[i] V_i ; hacc[i] += h[i]
+__global__ void k_orth_update(double* __restrict__ w, const double* __restrict__ V, int64_t n, int nvec,
+                              const double* __restrict__ h, double* __restrict__ hacc, int first) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) {
+    for (int i = 0; i < nvec; ++i) hacc[i] = first ? h[i] : hacc[i] + h[i];
+  }
+  if (e >= n) return;
+  double acc = w[e];
+  for (int i = 0; i < nvec; ++i) acc = fma(-h[i], V[(int64_t)i * n + e], acc);
+  w[e] = acc;
+}
+
+__global__ void k_normalize(const double* __restrict__ w, const double* __restrict__ nrm2,
+                            double* __restrict__ out, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double s = nrm2[0] > 0.0 ? 1.0 / sqrt(nrm2[0]) : 0.0;
+  out[e] = w[e] * s;
+}
+
+__global__ void k_system(const double* __restrict__ diag, double off, const double* __restrict__ x,
+                         const double* __restrict__ Ax, double* __restrict__ y, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  y[e] = fma(diag[e], x[e], off * Ax[e]);
+}
+
+__global__ void k_sub(const double* __restrict__ b, const double* __restrict__ a, double* __restrict__ r,
+                      int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  r[e] = b[e] - a[e];
+}
+
+__global__ void k_xupdate(double* __restrict__ x, const double* __restrict__ V, const double* __restrict__ y,
+                          int k, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double acc = x[e];
+  for (int i = 0; i < k; ++i) acc = fma(y[i], V[(int64_t)i * n + e], acc);
+  x[e] = acc;
+}
+
+__global__ void k_fill_diag(double* __restrict__ diag, const DropDev* __restrict__ drops, int n_drops,
+                            int sys, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  if (sys == SHBIM_SYS_ELECTRIC) {
+    diag[e] = 0.5;
+    return;
+  }
+  int i = 0;
+  while (i + 1 < n_drops && 3 * drops[i + 1].coef_off <= e) ++i;
+  diag[e] = drops[i].lam + 1.0;
+}
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
+  auto& G = ctx->gm;
+  int rc = G.sys == SHBIM_SYS_ELECTRIC
+               ? shbim_eval_electric(ctx, SHBIM_LAPLACE_DL, v, G.Av, SHBIM_OUT_COEF, s)
+               : shbim_eval_stokes(ctx, nullptr, v, G.Av, SHBIM_OUT_COEF, s);
+  if (rc) return rc;
+  k_system<<<nb(G.n), 256, 0, s>>>(G.diag, G.offdiag, v, G.Av, out, G.n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_system");
+  return SHBIM_OK;
+}
+
+double* hacc_ptr(shbim_ctx* ctx) { return ctx->gm.h + (ctx->gm.m + 2); }
+
+// ||src||^2 into hacc[slot] and src/||src|| into dst; returns the norm read back on the host
+int normalize_into(shbim_ctx* ctx, const double* src, double* dst, int slot, double* norm, cudaStream_t s) {
+  auto& G = ctx->gm;
+  double* hacc = hacc_ptr(ctx);
+  k_dots<<<1, 256, 0, s>>>(src, G.n, src, hacc + slot);
+  SHBIM_CHECK_LAUNCH(ctx, "k_dots");
+  k_normalize<<<nb(G.n), 256, 0, s>>>(src, hacc + slot, dst, G.n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_normalize");
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(G.h_host, hacc + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  *norm = std::sqrt(std::max(0.0, G.h_host[0]));
+  if (!std::isfinite(*norm)) return fail(ctx, SHBIM_ERR_NONFINITE, "non-finite norm in GMRES");
+  return SHBIM_OK;
+}
+
+// start a cycle from the current x: V0 = (b - A x)/beta
+int start_cycle(shbim_ctx* ctx, bool x_is_zero, cudaStream_t s) {
+  auto& G = ctx->gm;
+  int rc;
+  if (x_is_zero) {
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(G.w, G.b, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    if ((rc = system_matvec(ctx, G.x, G.w, s))) return rc;
+    k_sub<<<nb(G.n), 256, 0, s>>>(G.b, G.w, G.w, G.n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_sub");
+  }
+  double beta = 0.0;
+  if ((rc = normalize_into(ctx, G.w, G.V, 0, &beta, s))) return rc;
+  std::fill(G.g.begin(), G.g.end(), 0.0);
+  G.g[0] = beta;
+  G.k = 0;
+  G.resid = G.bnorm > 0.0 ? beta / G.bnorm : 0.0;
+  return SHBIM_OK;
+}
+
+// y = R^{-1} g for the rotated Hessenberg matrix of the current cycle, x += V y
+int update_x(shbim_ctx* ctx, cudaStream_t s) {
+  auto& G = ctx->gm;
+  const int k = G.k;
+  if (k == 0) return SHBIM_OK;
+  const int ld = G.m + 1;
+  std::vector<double> y(k);
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = G.g[i];
+    for (int c = i + 1; c < k; ++c) acc -= G.H[(size_t)c * ld + i] * y[c];
+    y[i] = acc / G.H[(size_t)i * ld + i];
+  }
+  std::copy(y.begin(), y.end(), G.h_host);
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(G.y, G.h_host, k * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_xupdate<<<nb(G.n), 256, 0, s>>>(G.x, G.V, G.y, k, G.n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_xupdate");
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));  // h_host is reused by the next read-back
+  G.k = 0;
+  return SHBIM_OK;
+}
+
+}  // namespace
+
+}  // namespace shbim
+
+using namespace shbim;
+
+extern "C" {
+
+int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (sys != SHBIM_SYS_ELECTRIC && sys != SHBIM_SYS_STOKES) return fail(ctx, SHBIM_ERR_ARG, "bad system");
+  if (!rhs_dev) return fail(ctx, SHBIM_ERR_ARG, "null right-hand side");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto& G = ctx->gm;
+  const int64_t n = sys == SHBIM_SYS_ELECTRIC ? ctx->ncoef : 3 * ctx->ncoef;
+  const int m = ctx->opts.gmres_restart;
+  if (n * (m + 1) > G.cap || m != G.m || !G.V) {
+    SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+    cudaFree(G.V); cudaFree(G.w); cudaFree(G.x); cudaFree(G.b); cudaFree(G.h); cudaFree(G.Av);
+    cudaFree(G.diag); cudaFree(G.y);
+    if (G.h_host) cudaFreeHost(G.h_host);
+    G.V = G.w = G.x = G.b = G.h = G.Av = G.diag = G.y = G.h_host = nullptr;
+    const int64_t ncap = std::max<int64_t>(n, 3 * ctx->ncoef);
+    if (cudaMalloc(&G.V, (size_t)ncap * (m + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.w, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.x, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.b, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.Av, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.diag, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.y, (m + 2) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.h, 2 * (m + 2) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&G.h_host, 2 * (m + 2) * sizeof(double)) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "GMRES workspace allocation failed");
+    G.cap = ncap * (m + 1);
+    G.m = m;
+  }
+  G.sys = sys;
+  G.n = n;
+  G.H.assign((size_t)(m + 1) * m, 0.0);
+  G.cs.assign(m, 0.0);
+  G.sn.assign(m, 0.0);
+  G.g.assign(m + 1, 0.0);
+  G.total = 0;
+  G.k = 0;
+  const double R = ctx->opts.R;
+  G.offdiag = sys == SHBIM_SYS_ELECTRIC ? -(R - 1.0) / (R + 1.0) : -1.0;
+  k_fill_diag<<<nb(n), 256, 0, s>>>(G.diag, ctx->drops_dev, ctx->n_drops, sys, n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_fill_diag");
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(G.b, rhs_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (x0_dev) {
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(G.x, x0_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    SHBIM_CUDA(ctx, cudaMemsetAsync(G.x, 0, n * sizeof(double), s));
+  }
+  // ||b||
+  double* hacc = hacc_ptr(ctx);
+  k_dots<<<1, 256, 0, s>>>(G.b, n, G.b, hacc);
+  SHBIM_CHECK_LAUNCH(ctx, "k_dots");
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(G.h_host, hacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  G.bnorm = std::sqrt(std::max(0.0, G.h_host[0]));
+  if (!std::isfinite(G.bnorm)) return fail(ctx, SHBIM_ERR_NONFINITE, "non-finite right-hand side");
+  if (G.bnorm == 0.0) {
+    SHBIM_CUDA(ctx, cudaMemsetAsync(G.x, 0, n * sizeof(double), s));
+    G.resid = 0.0;
+    return SHBIM_OK;
+  }
+  return start_cycle(ctx, x0_dev == nullptr, s);
+}
+
+int shbim_gmres_step(shbim_ctx* ctx, double* resid_host, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  auto& G = ctx->gm;
+  if (G.sys < 0) return fail(ctx, SHBIM_ERR_ARG, "shbim_gmres_begin was not called");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (resid_host) *resid_host = G.resid;
+  if (G.resid <= ctx->opts.gmres_tol) return SHBIM_CONVERGED;
+  if (G.total >= ctx->opts.gmres_maxiter)
+    return fail(ctx, SHBIM_ERR_NOT_CONVERGED, "GMRES reached its iteration limit");
+  int rc;
+  const int k = G.k;
+  const int64_t n = G.n;
+  double* vk = G.V + (int64_t)k * n;
+  if ((rc = system_matvec(ctx, vk, G.w, s))) return rc;
+  double* htmp = G.h;
+  double* hacc = hacc_ptr(ctx);
+  for (int pass = 0; pass < 2; ++pass) {
+    k_dots<<<k + 1, 256, 0, s>>>(G.V, n, G.w, htmp);
+    SHBIM_CHECK_LAUNCH(ctx, "k_dots");
+    k_orth_update<<<nb(n), 256, 0, s>>>(G.w, G.V, n, k + 1, htmp, hacc, pass == 0);
+    SHBIM_CHECK_LAUNCH(ctx, "k_orth_update");
+  }
+  k_dots<<<1, 256, 0, s>>>(G.w, n, G.w, hacc + k + 1);
+  SHBIM_CHECK_LAUNCH(ctx, "k_dots");
+  k_normalize<<<nb(n), 256, 0, s>>>(G.w, hacc + k + 1, G.V + (int64_t)(k + 1) * n, n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_normalize");
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(G.h_host, hacc, (k + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  const int ld = G.m + 1;
+  double* Hc = &G.H[(size_t)k * ld];
+  for (int i = 0; i <= k; ++i) Hc[i] = G.h_host[i];
+  Hc[k + 1] = std::sqrt(std::max(0.0, G.h_host[k + 1]));
+  for (int i = 0; i <= k + 1; ++i)
+    if (!std::isfinite(Hc[i])) return fail(ctx, SHBIM_ERR_NONFINITE, "non-finite Arnoldi column");
+  for (int i = 0; i < k; ++i) {
+    const double a = Hc[i], b = Hc[i + 1];
+    Hc[i] = G.cs[i] * a + G.sn[i] * b;
+    Hc[i + 1] = -G.sn[i] * a + G.cs[i] * b;
+  }
+  const double den = std::hypot(Hc[k], Hc[k + 1]);
+  G.cs[k] = den > 0.0 ? Hc[k] / den : 1.0;
+  G.sn[k] = den > 0.0 ? Hc[k + 1] / den : 0.0;
+  Hc[k] = den;
+  Hc[k + 1] = 0.0;
+  G.g[k + 1] = -G.sn[k] * G.g[k];
+  G.g[k] = G.cs[k] * G.g[k];
+  G.k = k + 1;
+  G.total++;
+  G.resid = std::fabs(G.g[k + 1]) / G.bnorm;
+  if (resid_host) *resid_host = G.resid;
+  if (G.resid <= ctx->opts.gmres_tol) return SHBIM_CONVERGED;
+  if (G.k == G.m) {
+    // restart from the true residual of the updated iterate
+    if ((rc = update_x(ctx, s))) return rc;
+    if ((rc = start_cycle(ctx, false, s))) return rc;
+    if (resid_host) *resid_host = G.resid;
+    if (G.resid <= ctx->opts.gmres_tol) return SHBIM_CONVERGED;
+  }
+  if (G.total >= ctx->opts.gmres_maxiter)
+    return fail(ctx, SHBIM_ERR_NOT_CONVERGED, "GMRES reached its iteration limit");
+  return SHBIM_CONTINUE;
+}
+
+int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* stream) {
+  if (!ctx || !x_dev) return SHBIM_ERR_ARG;
+  auto& G = ctx->gm;
+  if (G.sys < 0) return fail(ctx, SHBIM_ERR_ARG, "shbim_gmres_begin was not called");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = update_x(ctx, s);
+  if (rc) return rc;
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(x_dev, G.x, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (iters_host) *iters_host = G.total;
+  return SHBIM_OK;
+}
+
+int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev, double* x_dev,
+                      int* iters_host, double* resid_host, void* stream) {
+  int rc = shbim_gmres_begin(ctx, sys, rhs_dev, x0_dev, stream);
+  if (rc) return rc;
+  for (;;) {
+    rc = shbim_gmres_step(ctx, nullptr, stream);
+    if (rc == SHBIM_CONVERGED) break;
+    if (rc != SHBIM_CONTINUE) return rc;
+  }
+  if ((rc = shbim_gmres_finish(ctx, x_dev, iters_host, stream))) return rc;
+  if (resid_host) {
+    auto& G = ctx->gm;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (G.bnorm == 0.0) {
+      *resid_host = 0.0;
+      return SHBIM_OK;
+    }
+    if ((rc = system_matvec(ctx, G.x, G.w, s))) return rc;
+    k_sub<<<nb(G.n), 256, 0, s>>>(G.b, G.w, G.w, G.n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_sub");
+    double* hacc = hacc_ptr(ctx);
+    k_dots<<<1, 256, 0, s>>>(G.w, G.n, G.w, hacc);
+    SHBIM_CHECK_LAUNCH(ctx, "k_dots");
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(G.h_host, hacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+    *resid_host = std::sqrt(std::max(0.0, G.h_host[0])) / G.bnorm;
+  }
+  return SHBIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// Internal declarations of the shbim library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "shbim.h"
+
+namespace shbim {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kInv4Pi = 0.07957747154594766788;   // 1/(4 pi)
+constexpr double kSqrt2 = 1.41421356237309504880;
+
+inline int ncoef(int p) { return (p + 1) * (p + 1); }
+inline int ntri(int p) { return (p + 1) * (p + 2) / 2; }
+inline int nlat(int q) { return q + 1; }
+inline int nlon(int q) { return 2 * q + 2; }
+inline int npts(int q) { return (q + 1) * (2 * q + 2); }
+
+// Number of Laplace / Stokes weight components in the singular self rows.
+constexpr int kNumLap = 2;        // 0: double layer (target normal), 1: single layer
+constexpr int kNumSto = 12;       // 0..5 Stokeslet xx,xy,xz,yy,yz,zz ; 6..11 stresslet (same order)
+
+// Transform tables of one (p, grid degree q) pair, device memory.
+struct GridTables {
+  int p = 0, q = 0;
+  double* alf = nullptr;     // [q+1][3][ntri(p)] m-major: Pbar, dPbar/dtheta, m Pbar / sin
+  double* omega = nullptr;   // [q+1] regular weight (pi/(q+1)) w_j^G
+  double* mu = nullptr;      // [q+1] modified weight omega_j 2 sin(theta_j/2) sum_{n<=q} P_n(t_j)
+  double* trig = nullptr;    // [2][2q+2] cos, sin of 2 pi k / (2q+2)
+  double* theta = nullptr;   // [q+1]
+};
+
+struct DegreeTables {
+  int p = 0;
+  GridTables base;           // q = p
+  GridTables up;             // q = 2p+1
+  double* dq = nullptr;      // rotation matrix blocks of Rx(pi/2), sum_n (2n+1)^2 doubles
+  std::vector<int> dq_off;   // host copy of block offsets (n -> offset)
+  int* dq_off_dev = nullptr;
+};
+
+struct Drop {
+  int p = 0, q = 0;
+  int64_t coef_off = 0;      // into scalar coefficient vectors
+  int64_t tgt_off = 0;       // into target arrays
+  int64_t src_off = 0;       // into source arrays
+  int nt = 0, ns = 0, nc = 0;
+  double lam = 1.0;
+  double centre[3] = {0, 0, 0};
+  DegreeTables* tab = nullptr;
+  double* rows_lap = nullptr;   // [nt][kNumLap][nc]
+  double* rows_sto = nullptr;   // [nt][kNumSto][nc]
+};
+
+// Per-drop description read by the kernels.
+struct DropDev {
+  int p, q, nt, ns, nc;
+  int64_t coef_off, tgt_off, src_off;
+  double lam;
+  double cx, cy, cz;
+  const double* rows_lap;
+  const double* rows_sto;
+};
+
+// Target tile of the all-pairs kernels: targets [t0, t0+nt) of one drop.
+struct PairTile {
+  int drop;
+  int t0;      // global target index
+  int nt;
+};
+
+struct Geometry {
+  // targets (FP64, SoA): x y z nx ny nz J, each [ntarget]
+  double* tgt = nullptr;
+  // sources (FP64, SoA): x y z nx ny nz w(=omega J), each [nsource]
+  double* src = nullptr;
+  // FP32 copies relative to the drop centre: targets (hi) and sources
+  float* tgt32 = nullptr;   // x y z nx ny nz  relative position + normal, each [ntarget]
+  float* src32 = nullptr;   // x y z nx ny nz w, each [nsource]
+  int* tgt_drop = nullptr;  // [ntarget]
+  double* centres = nullptr;// [n_drops][3]
+  int64_t* src_start = nullptr;  // [n_drops+1]
+};
+
+}  // namespace shbim
+
+struct shbim_ctx {
+  shbim_opts opts{};
+  std::string err;
+  int n_drops = 0;
+  int64_t ncoef = 0, ntarget = 0, nsource = 0;
+  std::vector<shbim::Drop> drops;
+  std::map<int, shbim::DegreeTables*> tables;
+  shbim::Geometry geo;
+  std::vector<shbim::PairTile> tiles;
+  shbim::PairTile* tiles_dev = nullptr;
+  shbim::DropDev* drops_dev = nullptr;
+  int pair_splits = 1;
+  // workspaces
+  double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
+  float* dens_up32 = nullptr;     // [3][nsource] source strengths (FP32)
+  double* part = nullptr;         // [pair_splits][3][ntarget] partial sums
+  double* grid_out = nullptr;     // [3][ntarget] operator values before projection
+  double* sht_scratch = nullptr;  // Fourier stage of forward transforms
+  size_t sht_scratch_elems = 0;
+  // singular-row build workspace
+  double* rot_coef = nullptr;
+  double* wbuf = nullptr;
+  double* vbuf = nullptr;
+  size_t rot_elems = 0, wbuf_elems = 0, vbuf_elems = 0;
+  // GMRES
+  struct Gmres {
+    int sys = -1;
+    int64_t n = 0;
+    int m = 50;
+    double* V = nullptr;        // [m+1][n]
+    double* w = nullptr;        // [n]
+    double* x = nullptr;        // [n]
+    double* b = nullptr;        // [n]
+    double* h = nullptr;        // [2][m+2] device dots
+    double* h_host = nullptr;   // pinned
+    double* Av = nullptr;       // [n] operator output
+    double* diag = nullptr;     // [n] identity part of the system
+    double* y = nullptr;        // [m] least-squares solution uploaded for x updates
+    double offdiag = 0.0;       // factor of the layer operator in the system
+    std::vector<double> H;      // (m+1) x m, column-major k*(m+1)+i
+    std::vector<double> cs, sn, g;
+    int k = 0;                  // Arnoldi steps in the current cycle
+    int total = 0;
+    double bnorm = 0.0;
+    double resid = 1.0;
+    int64_t cap = 0;
+  } gm;
+  int64_t launches = 0;
+  // optional per-class kernel timing
+  bool timing = false;
+  struct TimedRange {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<TimedRange> timed;
+  std::vector<cudaEvent_t> event_pool;
+  double class_ms[SHBIM_K_COUNT] = {0};
+  int64_t class_launches[SHBIM_K_COUNT] = {0};
+};
+
+namespace shbim {
+
+// ---- error helpers
+int fail(shbim_ctx* ctx, int code, const std::string& msg);
+int cuda_fail(shbim_ctx* ctx, cudaError_t e, const char* what);
+#define SHBIM_CHECK_LAUNCH(ctx, what)                                 \
+  do {                                                                \
+    (ctx)->launches++;                                                \
+    cudaError_t e_ = cudaGetLastError();                              \
+    if (e_ != cudaSuccess) return ::shbim::cuda_fail((ctx), e_, what);\
+  } while (0)
+#define SHBIM_CUDA(ctx, call)                                         \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return ::shbim::cuda_fail((ctx), e_, #call);\
+  } while (0)
+
+// ---- timing: bracket a launch of class `cls` on stream s (no-op unless timing is on)
+struct TimeScope {
+  shbim_ctx* ctx;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t b = nullptr;
+  TimeScope(shbim_ctx* c, int k, cudaStream_t st);
+  ~TimeScope();
+};
+
+// ---- tables (tables.cu)
+int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out);
+void free_degree_tables(DegreeTables* t);
+
+// ---- transforms (sht.cu)
+// Synthesis: for n_items coefficient vectors of degree p, values on grid g for the
+// requested kinds (bit 0 value, bit 1 d/dtheta, bit 2 (1/sin) d/dphi).
+// out[item * item_stride + kind_slot * kind_stride + node]; kinds are packed in order.
+// If scale != nullptr, each node value is multiplied by scale[node] (values only).
+// If out32 != nullptr the result is also written as float to out32 at the same index.
+int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
+              int64_t coef_stride, int kinds, double* out, int64_t item_stride,
+              int64_t kind_stride, const double* scale, float* out32, cudaStream_t s);
+int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
+                     int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
+                     double alpha, float* out32, cudaStream_t s);
+// Analysis: coef[item] = sum_nodes w(node) vals[item][node] S_nm(node) with w = omega_j when
+// weighted, else 1. Uses ctx->sht_scratch (grown as needed).
+int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double* vals,
+                 int64_t val_stride, bool weighted, double* coef, int64_t coef_stride,
+                 cudaStream_t s);
+
+// ---- geometry / singular rows (singular.cu)
+int build_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
+int build_singular_rows(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
+// out[t] (+)= self rows . density for every target (scalar Laplace kind or Stokes tensors).
+int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
+int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out,
+                      cudaStream_t s);
+
+// ---- all-pairs sums (pairs.cu)
+int pairs_laplace(shbim_ctx* ctx, int which, double* out_accum, cudaStream_t s);
+int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out_accum, cudaStream_t s);
+
+
+}  // namespace shbim

@@ -1,0 +1,337 @@
+// Tiled all-pairs sums of the regular rule (Eq. reg_quadrature) between different drops:
+// Laplace single layer and target-normal double layer (Eqs. E_n, dl_op_laplace), Stokeslet and
+// stresslet (Eqs. GandT, op_stokes). Same-drop pairs are excluded: those targets get the
+// singular self rows instead.
+//
+// Work decomposition: a CTA owns a tile of targets of one drop (128 threads x TPT targets,
+// register-blocked) and one split of the other drops' sources; sources are staged through
+// shared memory in tiles of 256 and read as warp-wide broadcasts. Each split writes its own
+// partial sums; a second kernel adds the splits in a fixed order (deterministic).
+//
+// FP32 path: sources are stored relative to their drop centre in FP32; for every (target,
+// source drop) the target offset x0 - c_j is formed in FP64 and kept as an unevaluated FP32
+// sum hi + lo, so xh = (hi - xs) + lo carries an error of order eps * r rather than
+// eps * |x0 - c_j| (drops 0.1 apart stay accurate). Each source tile is summed in FP32 and
+// added to a (hi, lo) accumulator with the two-sum of Knuth (compensated accumulation).
+#include <algorithm>
+
+#include "internal.h"
+
+namespace shbim {
+
+namespace {
+
+constexpr int kTile = 256;
+constexpr int kThreads = 128;
+constexpr int kTPT = 2;
+
+enum Kind { LDL = 0, LSL = 1, STO = 2 };
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float a) {
+  const float s = hi + a;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (a - bp);
+  hi = s;
+  lo += e;
+}
+
+// virtual source index v in [0, nsource - ns_i) skips drop i's own sources
+struct SrcRange {
+  int64_t a, b;
+};
+
+__device__ __forceinline__ SrcRange drop_range(const DropDev& Di, const DropDev& Dj, int i, int j,
+                                               int64_t v0, int64_t v1) {
+  const int64_t shift = (j > i) ? Di.ns : 0;
+  const int64_t vs = Dj.src_off - shift;
+  const int64_t ve = vs + Dj.ns;
+  SrcRange r;
+  r.a = max(v0, vs) + shift;
+  r.b = min(v1, ve) + shift;
+  return r;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads)
+k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
+          const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ src32,
+          int64_t nsource, const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
+          double* __restrict__ part) {
+  constexpr int NC = (KIND == STO) ? 3 : 1;
+  __shared__ float4 sh0[kTile];
+  __shared__ float4 sh1[KIND == STO ? kTile : 1];
+  __shared__ float4 sh2[KIND == STO ? kTile : 1];
+  const PairTile tile = tiles[blockIdx.x];
+  const int i = tile.drop;
+  const DropDev Di = drops[i];
+  const int64_t other = nsource - Di.ns;
+  const int64_t chunk = (other + nsplit - 1) / nsplit;
+  const int64_t v0 = (int64_t)blockIdx.y * chunk;
+  const int64_t v1 = min(other, v0 + chunk);
+
+  int64_t tg[kTPT];
+  bool ok[kTPT];
+  double X0[kTPT][3];
+  float N0[kTPT][3];
+#pragma unroll
+  for (int k = 0; k < kTPT; ++k) {
+    tg[k] = tile.t0 + threadIdx.x + k * kThreads;
+    ok[k] = tg[k] < (int64_t)tile.t0 + tile.nt;
+    const int64_t t = ok[k] ? tg[k] : tile.t0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      X0[k][c] = tgt[c * ntarget + t];
+      N0[k][c] = (float)tgt[(3 + c) * ntarget + t];
+    }
+  }
+  float hi[kTPT][NC], lo[kTPT][NC];
+#pragma unroll
+  for (int k = 0; k < kTPT; ++k)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) hi[k][c] = lo[k][c] = 0.f;
+
+  for (int j = 0; j < n_drops; ++j) {
+    if (j == i) continue;
+    const DropDev Dj = drops[j];
+    const SrcRange rg = drop_range(Di, Dj, i, j, v0, v1);
+    if (rg.a >= rg.b) continue;
+    float th[kTPT][3], tl[kTPT][3];
+    const double cj[3] = {Dj.cx, Dj.cy, Dj.cz};
+#pragma unroll
+    for (int k = 0; k < kTPT; ++k)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double d = X0[k][c] - cj[c];
+        const float h = (float)d;
+        th[k][c] = h;
+        tl[k][c] = (float)(d - (double)h);
+      }
+    for (int64_t base = rg.a; base < rg.b; base += kTile) {
+      const int cnt = (int)min((int64_t)kTile, rg.b - base);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += kThreads) {
+        const int64_t sI = base + e;
+        const float x = src32[sI], y = src32[nsource + sI], z = src32[2 * nsource + sI];
+        if (KIND != STO) {
+          sh0[e] = make_float4(x, y, z, dens32[sI]);
+        } else {
+          const float fx = has_f ? dens32[sI] : 0.f;
+          const float fy = has_f ? dens32[nsource + sI] : 0.f;
+          const float fz = has_f ? dens32[2 * nsource + sI] : 0.f;
+          const float ux = has_u ? dens32[3 * nsource + sI] : 0.f;
+          const float uy = has_u ? dens32[4 * nsource + sI] : 0.f;
+          const float uz = has_u ? dens32[5 * nsource + sI] : 0.f;
+          sh0[e] = make_float4(x, y, z, fx);
+          sh1[e] = make_float4(fy, fz, ux, uy);
+          sh2[e] = make_float4(uz, src32[3 * nsource + sI], src32[4 * nsource + sI],
+                               src32[5 * nsource + sI]);
+        }
+      }
+      __syncthreads();
+      float acc[kTPT][NC];
+#pragma unroll
+      for (int k = 0; k < kTPT; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[k][c] = 0.f;
+#pragma unroll 4
+      for (int e = 0; e < cnt; ++e) {
+        const float4 A = sh0[e];
+        if (KIND != STO) {
+#pragma unroll
+          for (int k = 0; k < kTPT; ++k) {
+            const float dx = (th[k][0] - A.x) + tl[k][0];
+            const float dy = (th[k][1] - A.y) + tl[k][1];
+            const float dz = (th[k][2] - A.z) + tl[k][2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrtf(r2);
+            if (KIND == LSL) {
+              acc[k][0] = fmaf(A.w, ri, acc[k][0]);
+            } else {
+              const float ri3 = ri * ri * ri;
+              const float dn = fmaf(dx, N0[k][0], fmaf(dy, N0[k][1], dz * N0[k][2]));
+              acc[k][0] = fmaf(A.w * ri3, dn, acc[k][0]);
+            }
+          }
+        } else {
+          const float4 B = sh1[e];
+          const float4 C = sh2[e];
+#pragma unroll
+          for (int k = 0; k < kTPT; ++k) {
+            const float dx = (th[k][0] - A.x) + tl[k][0];
+            const float dy = (th[k][1] - A.y) + tl[k][1];
+            const float dz = (th[k][2] - A.z) + tl[k][2];
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ri = rsqrtf(r2);
+            const float ri2 = ri * ri;
+            const float ri3 = ri2 * ri;
+            const float hf = fmaf(dx, A.w, fmaf(dy, B.x, dz * B.y));
+            const float hu = fmaf(dx, B.z, fmaf(dy, B.w, dz * C.x));
+            const float hn = fmaf(dx, C.y, fmaf(dy, C.z, dz * C.w));
+            const float t = ri3 * fmaf(hu * hn, ri2, hf);
+            acc[k][0] = fmaf(A.w, ri, fmaf(dx, t, acc[k][0]));
+            acc[k][1] = fmaf(B.x, ri, fmaf(dy, t, acc[k][1]));
+            acc[k][2] = fmaf(B.y, ri, fmaf(dz, t, acc[k][2]));
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kTPT; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) two_sum_acc(hi[k][c], lo[k][c], acc[k][c]);
+    }
+  }
+  double* P = part + (int64_t)blockIdx.y * NC * ntarget;
+#pragma unroll
+  for (int k = 0; k < kTPT; ++k) {
+    if (!ok[k]) continue;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double v = 0.07957747154594766788 * ((double)hi[k][c] + (double)lo[k][c]);
+      const int64_t o = (NC == 1) ? tg[k] : 3 * Di.tgt_off + (int64_t)c * Di.nt + (tg[k] - Di.tgt_off);
+      P[o] = v;
+    }
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads)
+k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
+          const double* __restrict__ tgt, int64_t ntarget, const double* __restrict__ src,
+          int64_t nsource, const double* __restrict__ dens, int nsplit, int has_f, int has_u,
+          double* __restrict__ part) {
+  constexpr int NC = (KIND == STO) ? 3 : 1;
+  constexpr int NF = (KIND == STO) ? 12 : 4;
+  __shared__ double sh[NF][kTile];
+  const PairTile tile = tiles[blockIdx.x];
+  const int i = tile.drop;
+  const DropDev Di = drops[i];
+  const int64_t other = nsource - Di.ns;
+  const int64_t chunk = (other + nsplit - 1) / nsplit;
+  const int64_t v0 = (int64_t)blockIdx.y * chunk;
+  const int64_t v1 = min(other, v0 + chunk);
+  int64_t tg[kTPT];
+  bool ok[kTPT];
+  double X0[kTPT][3], N0[kTPT][3], acc[kTPT][NC];
+#pragma unroll
+  for (int k = 0; k < kTPT; ++k) {
+    tg[k] = tile.t0 + threadIdx.x + k * kThreads;
+    ok[k] = tg[k] < (int64_t)tile.t0 + tile.nt;
+    const int64_t t = ok[k] ? tg[k] : tile.t0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      X0[k][c] = tgt[c * ntarget + t];
+      N0[k][c] = tgt[(3 + c) * ntarget + t];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[k][c] = 0.0;
+  }
+  for (int j = 0; j < n_drops; ++j) {
+    if (j == i) continue;
+    const DropDev Dj = drops[j];
+    const SrcRange rg = drop_range(Di, Dj, i, j, v0, v1);
+    if (rg.a >= rg.b) continue;
+    for (int64_t base = rg.a; base < rg.b; base += kTile) {
+      const int cnt = (int)min((int64_t)kTile, rg.b - base);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += kThreads) {
+        const int64_t sI = base + e;
+        sh[0][e] = src[sI];
+        sh[1][e] = src[nsource + sI];
+        sh[2][e] = src[2 * nsource + sI];
+        if (KIND != STO) {
+          sh[3][e] = dens[sI];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            sh[3 + c][e] = has_f ? dens[c * nsource + sI] : 0.0;
+            sh[6 + c][e] = has_u ? dens[(3 + c) * nsource + sI] : 0.0;
+            sh[9 + c][e] = src[(3 + c) * nsource + sI];
+          }
+        }
+      }
+      __syncthreads();
+      for (int e = 0; e < cnt; ++e) {
+        const double sx = sh[0][e], sy = sh[1][e], sz = sh[2][e];
+#pragma unroll
+        for (int k = 0; k < kTPT; ++k) {
+          const double dx = X0[k][0] - sx, dy = X0[k][1] - sy, dz = X0[k][2] - sz;
+          const double r2 = dx * dx + dy * dy + dz * dz;
+          const double ri = rsqrt(r2);
+          if (KIND == LSL) {
+            acc[k][0] = fma(sh[3][e], ri, acc[k][0]);
+          } else if (KIND == LDL) {
+            const double dn = dx * N0[k][0] + dy * N0[k][1] + dz * N0[k][2];
+            acc[k][0] = fma(sh[3][e] * ri * ri * ri, dn, acc[k][0]);
+          } else {
+            const double ri2 = ri * ri, ri3 = ri2 * ri;
+            const double fx = sh[3][e], fy = sh[4][e], fz = sh[5][e];
+            const double hf = dx * fx + dy * fy + dz * fz;
+            const double hu = dx * sh[6][e] + dy * sh[7][e] + dz * sh[8][e];
+            const double hn = dx * sh[9][e] + dy * sh[10][e] + dz * sh[11][e];
+            const double t = ri3 * (hf + hu * hn * ri2);
+            acc[k][0] += fx * ri + dx * t;
+            acc[k][1] += fy * ri + dy * t;
+            acc[k][2] += fz * ri + dz * t;
+          }
+        }
+      }
+    }
+  }
+  double* P = part + (int64_t)blockIdx.y * NC * ntarget;
+#pragma unroll
+  for (int k = 0; k < kTPT; ++k) {
+    if (!ok[k]) continue;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int64_t o = (NC == 1) ? tg[k] : 3 * Di.tgt_off + (int64_t)c * Di.nt + (tg[k] - Di.tgt_off);
+      P[o] = 0.07957747154594766788 * acc[k][c];
+    }
+  }
+}
+
+__global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int64_t n,
+                               double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * n + e];
+  out[e] += s;
+}
+
+template <int KIND>
+int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s) {
+  constexpr int NC = (KIND == STO) ? 3 : 1;
+  if (ctx->n_drops < 2 || ctx->tiles.empty()) return SHBIM_OK;
+  dim3 grid((unsigned)ctx->tiles.size(), ctx->pair_splits);
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
+    k_pairs32<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops,
+                                              ctx->geo.tgt, ctx->ntarget, ctx->geo.src32,
+                                              ctx->nsource, ctx->dens_up32, ctx->pair_splits,
+                                              has_f, has_u, ctx->part);
+  } else {
+    k_pairs64<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops,
+                                              ctx->geo.tgt, ctx->ntarget, ctx->geo.src,
+                                              ctx->nsource, ctx->dens_up, ctx->pair_splits, has_f,
+                                              has_u, ctx->part);
+  }
+  SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
+  const int64_t n = NC * ctx->ntarget;
+  k_reduce_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->part, ctx->pair_splits, n, out);
+  SHBIM_CHECK_LAUNCH(ctx, "k_reduce_parts");
+  return SHBIM_OK;
+}
+
+}  // namespace
+
+int pairs_laplace(shbim_ctx* ctx, int which, double* out, cudaStream_t s) {
+  return which == SHBIM_LAPLACE_SL ? launch_pairs<LSL>(ctx, false, false, out, s)
+                                   : launch_pairs<LDL>(ctx, false, false, out, s);
+}
+
+int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s) {
+  return launch_pairs<STO>(ctx, has_f, has_u, out, s);
+}
+
+int pairs_tile_targets() { return kThreads * kTPT; }
+
+}  // namespace shbim

@@ -1,0 +1,215 @@
+// Spherical-harmonic transforms on Gaussian grids (Section 3, Eq. spharm_ex), FP64.
+//
+// Synthesis splits into a Legendre stage (per latitude j and order m: sum over degree n of
+// coefficient x table) and a Fourier stage (per longitude: sum over m of cos / sin terms),
+// both inside one CTA per (item, latitude). Analysis is the adjoint: a Fourier stage per
+// (item, latitude) writing 2(p+1) partial sums to scratch, then a Legendre stage per
+// (item, coefficient) summing over latitudes in a fixed order (deterministic).
+#include "internal.h"
+
+namespace shbim {
+
+__device__ __forceinline__ int tri_off_d(int p, int m) { return m * (p + 1) - m * (m - 1) / 2; }
+
+// kinds bitmask -> table index of the slot-th set bit
+__device__ __forceinline__ int kind_of_slot(int kinds, int slot) {
+  int k = 0;
+  for (int b = 0; b < 3; ++b) {
+    if (kinds & (1 << b)) {
+      if (k == slot) return b;
+      ++k;
+    }
+  }
+  return 0;
+}
+
+__global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, int p, int q,
+                        const double* __restrict__ alf, const double* __restrict__ trig, int kinds,
+                        double* __restrict__ out, int64_t item_stride, int64_t kind_stride,
+                        const double* __restrict__ scale, double alpha, float* __restrict__ out32) {
+  extern __shared__ double sm[];
+  const int item = blockIdx.x;
+  const int j = blockIdx.y;
+  const int nk = __popc(kinds);
+  const int N = 2 * q + 2;
+  const int P1 = p + 1;
+  double* A = sm;                    // [nk][2][P1]
+  double* tc = A + nk * 2 * P1;      // [N]
+  double* ts = tc + N;               // [N]
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tc[i] = trig[i];
+    ts[i] = trig[N + i];
+  }
+  const double* c = coef + (int64_t)item * coef_stride;
+  const int nt = (p + 1) * (p + 2) / 2;
+  const double* T = alf + (int64_t)j * 3 * nt;
+  const int ntask = nk * 2 * P1;
+  for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
+    const int slot = task / (2 * P1);
+    const int r = task - slot * 2 * P1;
+    const int m = r >> 1;
+    const int cs = r & 1;
+    double acc = 0.0;
+    if (!(cs == 1 && m == 0)) {
+      const double* col = T + kind_of_slot(kinds, slot) * nt + tri_off_d(p, m);
+      const int sgn = cs ? -m : m;
+      for (int n = m; n <= p; ++n) acc = fma(__ldg(c + n * n + n + sgn), col[n - m], acc);
+    }
+    A[(slot * 2 + cs) * P1 + m] = acc;
+  }
+  __syncthreads();
+  const double s2 = 1.41421356237309504880;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const int64_t node = (int64_t)j * N + k;
+    for (int slot = 0; slot < nk; ++slot) {
+      const int kind = kind_of_slot(kinds, slot);
+      const double* Ac = A + (slot * 2) * P1;
+      const double* As = Ac + P1;
+      double v = 0.0;
+      int id = 0;
+      if (kind != 2) {
+        for (int m = 1; m <= p; ++m) {
+          id += k;
+          if (id >= N) id -= N;
+          v = fma(Ac[m], tc[id], v);
+          v = fma(As[m], ts[id], v);
+        }
+        v = Ac[0] + s2 * v;
+      } else {
+        for (int m = 1; m <= p; ++m) {
+          id += k;
+          if (id >= N) id -= N;
+          v = fma(-Ac[m], ts[id], v);
+          v = fma(As[m], tc[id], v);
+        }
+        v = s2 * v;
+      }
+      if (kind == 0 && scale) v *= scale[node] * alpha;
+      const int64_t o = (int64_t)item * item_stride + (int64_t)slot * kind_stride + node;
+      out[o] = v;
+      if (out32) out32[o] = (float)v;
+    }
+  }
+}
+
+int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
+              int64_t coef_stride, int kinds, double* out, int64_t item_stride,
+              int64_t kind_stride, const double* scale, float* out32, cudaStream_t s) {
+  if (n_items <= 0) return SHBIM_OK;
+  const int nk = __builtin_popcount(kinds);
+  const size_t smem = (size_t)(nk * 2 * (g.p + 1) + 2 * (2 * g.q + 2)) * sizeof(double);
+  dim3 grid(n_items, g.q + 1);
+  k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, kinds, out,
+                                  item_stride, kind_stride, scale, 1.0, out32);
+  SHBIM_CHECK_LAUNCH(ctx, "k_synth");
+  return SHBIM_OK;
+}
+
+// Synthesis with a scalar factor on the scaled values (used for (lam_j - 1) strengths).
+int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
+                     int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
+                     double alpha, float* out32, cudaStream_t s) {
+  if (n_items <= 0) return SHBIM_OK;
+  const size_t smem = (size_t)(2 * (g.p + 1) + 2 * (2 * g.q + 2)) * sizeof(double);
+  dim3 grid(n_items, g.q + 1);
+  k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, 1, out, item_stride,
+                                  0, scale, alpha, out32);
+  SHBIM_CHECK_LAUNCH(ctx, "k_synth");
+  return SHBIM_OK;
+}
+
+// Fourier stage of the analysis: F[item][j][cs][m] = (omega_j) sum_k v[j][k] (cos|sin)(m phi_k)
+__global__ void k_analysis_fourier(const double* __restrict__ vals, int64_t val_stride, int p, int q,
+                                   const double* __restrict__ trig, const double* __restrict__ omega,
+                                   int weighted, double* __restrict__ F) {
+  extern __shared__ double sm[];
+  const int item = blockIdx.x;
+  const int j = blockIdx.y;
+  const int N = 2 * q + 2;
+  const int P1 = p + 1;
+  double* row = sm;
+  double* tc = row + N;
+  double* ts = tc + N;
+  const double* v = vals + (int64_t)item * val_stride + (int64_t)j * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    row[i] = v[i];
+    tc[i] = trig[i];
+    ts[i] = trig[N + i];
+  }
+  __syncthreads();
+  const double w = weighted ? omega[j] : 1.0;
+  double* out = F + ((int64_t)item * (q + 1) + j) * 2 * P1;
+  for (int task = threadIdx.x; task < 2 * P1; task += blockDim.x) {
+    const int cs = task / P1;
+    const int m = task - cs * P1;
+    const double* tb = cs ? ts : tc;
+    double acc = 0.0;
+    int id = 0;
+    for (int k = 0; k < N; ++k) {
+      acc = fma(row[k], tb[id], acc);
+      id += m;
+      if (id >= N) id -= N;
+    }
+    out[task] = w * acc;
+  }
+}
+
+// Legendre stage: coef[item][n^2+n+-m] = s_m sum_j F[item][j][cs][m] Pbar_n^m(t_j)
+__global__ void k_analysis_legendre(const double* __restrict__ F, int p, int q,
+                                    const double* __restrict__ alf, double* __restrict__ coef,
+                                    int64_t coef_stride) {
+  const int item = blockIdx.x;
+  const int nt = (p + 1) * (p + 2) / 2;
+  const int o = blockIdx.y * blockDim.x + threadIdx.x;
+  if (o >= nt) return;
+  int m = 0;
+  while (m < p && tri_off_d(p, m + 1) <= o) ++m;
+  const int n = m + (o - tri_off_d(p, m));
+  const int P1 = p + 1;
+  const double* Fi = F + (int64_t)item * (q + 1) * 2 * P1;
+  double ac = 0.0, as = 0.0;
+  for (int j = 0; j <= q; ++j) {
+    const double a = alf[(int64_t)j * 3 * nt + o];
+    ac = fma(Fi[(int64_t)j * 2 * P1 + m], a, ac);
+    as = fma(Fi[(int64_t)j * 2 * P1 + P1 + m], a, as);
+  }
+  double* c = coef + (int64_t)item * coef_stride;
+  if (m == 0) {
+    c[n * n + n] = ac;
+  } else {
+    const double s2 = 1.41421356237309504880;
+    c[n * n + n + m] = s2 * ac;
+    c[n * n + n - m] = s2 * as;
+  }
+}
+
+int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double* vals,
+                 int64_t val_stride, bool weighted, double* coef, int64_t coef_stride,
+                 cudaStream_t s) {
+  if (n_items <= 0) return SHBIM_OK;
+  const size_t need = (size_t)n_items * (g.q + 1) * 2 * (g.p + 1);
+  if (need > ctx->sht_scratch_elems) {
+    // growing scratch: wait for queued users of the old buffer before freeing it
+    if (ctx->sht_scratch) {
+      SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+      cudaFree(ctx->sht_scratch);
+      ctx->sht_scratch = nullptr;
+    }
+    if (cudaMalloc(&ctx->sht_scratch, need * sizeof(double)) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc transform scratch");
+    ctx->sht_scratch_elems = need;
+  }
+  const int N = 2 * g.q + 2;
+  dim3 g1(n_items, g.q + 1);
+  k_analysis_fourier<<<g1, 64, 3 * N * sizeof(double), s>>>(vals, val_stride, g.p, g.q, g.trig,
+                                                            g.omega, weighted ? 1 : 0,
+                                                            ctx->sht_scratch);
+  SHBIM_CHECK_LAUNCH(ctx, "k_analysis_fourier");
+  const int nt = ntri(g.p);
+  dim3 g2(n_items, (nt + 127) / 128);
+  k_analysis_legendre<<<g2, 128, 0, s>>>(ctx->sht_scratch, g.p, g.q, g.alf, coef, coef_stride);
+  SHBIM_CHECK_LAUNCH(ctx, "k_analysis_legendre");
+  return SHBIM_OK;
+}
+
+}  // namespace shbim

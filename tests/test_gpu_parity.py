@@ -1,0 +1,324 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative L2 and relative max, each quantity): 1e-10 for the FP64 path, 1e-5 for
+the FP32 compensated all-pairs path.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import geometry, gmres, operators, sh
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    l2 = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+    mx = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+    return max(l2, mx)
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_10270_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_1811_10270_gb300 import build
+        build.build()
+    pkg.lib()
+    return pkg
+
+
+DEV = "cuda"
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
+
+
+def make(S, drops, precision, R=2.0):
+    ctx = S.Context(precision=precision, R=R, gmres_tol=1e-12)
+    xc = T(np.concatenate([d.xcoef.ravel() for d in drops]))
+    ctx.set_drops([d.p for d in drops], xc, [d.lam for d in drops])
+    return ctx
+
+
+def oracle_system(drops):
+    return operators.System([operators.DropGeom(d.xcoef, d.p, d.lam) for d in drops])
+
+
+def split_grid(vec, drops, ncomp):
+    out, o = [], 0
+    for d in drops:
+        k = ncomp * sh.npts(d.p) if hasattr(sh, "npts") else ncomp * (d.p + 1) * (2 * d.p + 2)
+        out.append(vec[o:o + k].reshape(ncomp, -1) if ncomp > 1 else vec[o:o + k])
+        o += k
+    return out
+
+
+# --------------------------------------------------------------------------- transforms
+
+@pytest.mark.parametrize("p", [1, 5, 16])
+def test_sht_matches_oracle(S, p):
+    d = inputs.config1(p).drops[0]
+    ctx = make(S, [d], S.FP64)
+    rng = np.random.default_rng(p)
+    c = rng.standard_normal((3, sh.ncoef(p)))
+    for grid, q in ((S.GRID_BASE, p), (S.GRID_UP, 2 * p + 1)):
+        n = (q + 1) * (2 * q + 2)
+        out = torch.empty(3 * n, device=DEV, dtype=torch.float64)
+        ctx.sht(0, S.SHT_INVERSE, grid, 3, T(c), out)
+        assert rel_err(out.cpu().numpy().reshape(3, n), sh.sht_inverse(c, p, q)) < 1e-12
+        g = rng.standard_normal((3, n))
+        cf = torch.empty(3 * sh.ncoef(p), device=DEV, dtype=torch.float64)
+        ctx.sht(0, S.SHT_FORWARD, grid, 3, T(g), cf)
+        assert rel_err(cf.cpu().numpy().reshape(3, -1), sh.sht_forward(g, p, q)) < 1e-12
+    ctx.close()
+
+
+def test_target_geometry_matches_oracle(S):
+    p = 9
+    xc = inputs.perturbed_coef(p, np.random.default_rng(11), 1.1, (0.3, -0.2, 0.5))
+    d = inputs.Drop(p, xc, np.zeros(sh.ncoef(p)), 1.0, np.zeros(3), 1.0)
+    ctx = make(S, [d], S.FP64)
+    nt = (p + 1) * (2 * p + 2)
+    g = torch.empty(7 * nt, device=DEV, dtype=torch.float64)
+    ctx.target_geometry(g)
+    g = g.cpu().numpy().reshape(7, nt)
+    x, n, J = geometry.surface_on_grid(xc, p, p)
+    assert rel_err(g[0:3], x) < 1e-12
+    assert rel_err(g[3:6], n) < 1e-12
+    assert rel_err(g[6], J) < 1e-12
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("p", [1, 16, 64])
+def test_single_layer_eigenrelation_unit_sphere(S, p):
+    """(1/4pi) int Y_lm / r = Y_lm/(2l+1) on the unit sphere; the target-normal double layer
+    is half of it there. p = 64 is the largest degree the library accepts."""
+    d = inputs.config1(p).drops[0]
+    ctx = make(S, [d], S.FP64)
+    rng = np.random.default_rng(3)
+    sig = inputs.random_density(p, rng)[0]
+    scale = np.array([1.0 / (2 * n + 1) for n in range(p + 1) for _ in range(2 * n + 1)])
+    nt = (p + 1) * (2 * p + 2)
+    out = torch.empty(nt, device=DEV, dtype=torch.float64)
+    ctx.eval_electric(S.LAPLACE_SL, T(sig), out, S.OUT_GRID)
+    expect = sh.sht_inverse(sig * scale, p, p) if p <= 32 else None
+    got = out.cpu().numpy()
+    coef = torch.empty(sh.ncoef(p), device=DEV, dtype=torch.float64)
+    ctx.eval_electric(S.LAPLACE_SL, T(sig), coef, S.OUT_COEF)
+    assert rel_err(coef.cpu().numpy(), sig * scale) < TOL64
+    if expect is not None:
+        assert rel_err(got, expect) < TOL64
+    ctx.eval_electric(S.LAPLACE_DL, T(sig), coef, S.OUT_COEF)
+    assert rel_err(coef.cpu().numpy(), 0.5 * sig * scale) < TOL64
+    ctx.close()
+
+
+def test_stokes_identities_unit_sphere(S):
+    """S[c] = (4/3) c, D[c] = c (as (lam-1) D with lam = 2) and S[n] = 0 on the unit sphere."""
+    p = 12
+    d = inputs.config1(p).drops[0]
+    d.lam = 2.0
+    ctx = make(S, [d], S.FP64)
+    nc = sh.ncoef(p)
+    c = np.zeros((3, nc))
+    c[:, 0] = np.array([0.3, -0.7, 1.1]) * math.sqrt(4 * math.pi)
+    out = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
+    ctx.eval_stokes(T(c), None, out)
+    assert rel_err(out.cpu().numpy(), 4.0 / 3.0 * c.ravel()) < TOL64
+    ctx.eval_stokes(None, T(c), out)
+    assert rel_err(out.cpu().numpy(), c.ravel()) < TOL64
+    ctx.eval_stokes(T(inputs.sphere_coef(p)), None, out)
+    assert np.abs(out.cpu().numpy()).max() < 1e-12
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- full parity
+
+def _two_drop_cfg(p, seed=0, gap=0.3):
+    cfg = inputs.config2(p=p, seed=seed, gap=gap)
+    cfg.drops[1].lam = 0.5
+    return cfg
+
+
+@pytest.fixture(scope="module")
+def two_drops_p12():
+    """Two perturbed drops at p = 12: 338 targets per drop = two pair tiles with a ragged tail."""
+    cfg = _two_drop_cfg(12)
+    return cfg, oracle_system(cfg.drops)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+def test_laplace_two_drops_matches_oracle(S, two_drops_p12, precision, tol):
+    cfg, sysm = two_drops_p12
+    ctx = make(S, cfg.drops, precision, cfg.R)
+    rng = np.random.default_rng(5)
+    sig = [inputs.random_density(d.p, rng)[0] for d in cfg.drops]
+    nc_tot = sum(sh.ncoef(d.p) for d in cfg.drops)
+    nt_tot = sum((d.p + 1) * (2 * d.p + 2) for d in cfg.drops)
+    for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
+        out = torch.empty(nt_tot, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(which, T(np.concatenate(sig)), out, S.OUT_GRID)
+        assert rel_err(out.cpu().numpy(), np.concatenate(sysm.laplace_grid(kind, sig))) < tol
+        co = torch.empty(nc_tot, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(which, T(np.concatenate(sig)), co, S.OUT_COEF)
+        assert rel_err(co.cpu().numpy(), np.concatenate(sysm.laplace_coef(kind, sig))) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+def test_stokes_two_drops_matches_oracle(S, two_drops_p12, precision, tol):
+    cfg, sysm = two_drops_p12
+    ctx = make(S, cfg.drops, precision, cfg.R)
+    rng = np.random.default_rng(6)
+    f = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
+    u = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
+    F = T(np.concatenate([a.ravel() for a in f]))
+    U = T(np.concatenate([a.ravel() for a in u]))
+    nt_tot = sum((d.p + 1) * (2 * d.p + 2) for d in cfg.drops)
+    nc_tot = sum(sh.ncoef(d.p) for d in cfg.drops)
+    for ff, uu, fo, uo in ((F, U, f, u), (F, None, f, None), (None, U, None, u)):
+        out = torch.empty(3 * nt_tot, device=DEV, dtype=torch.float64)
+        ctx.eval_stokes(ff, uu, out, S.OUT_GRID)
+        ref = np.concatenate([a.ravel() for a in sysm.stokes_grid(fo, uo)])
+        assert rel_err(out.cpu().numpy(), ref) < tol
+        co = torch.empty(3 * nc_tot, device=DEV, dtype=torch.float64)
+        ctx.eval_stokes(ff, uu, co, S.OUT_COEF)
+        ref = np.concatenate([a.ravel() for a in sysm.stokes_coef(fo, uo)])
+        assert rel_err(co.cpu().numpy(), ref) < tol
+    ctx.close()
+
+
+def test_three_drops_uneven_degrees_match_oracle(S):
+    rng = np.random.default_rng(9)
+    drops = []
+    for p, ctr, lam in ((4, (0, 0, 0), 3.0), (7, (2.6, 0.1, 0.2), 1.0), (5, (-0.3, 2.5, -0.4), 0.7)):
+        drops.append(inputs.Drop(p, inputs.perturbed_coef(p, rng, 1.0, ctr), np.zeros(sh.ncoef(p)),
+                                 lam, np.asarray(ctr, float), 1.0))
+    sysm = oracle_system(drops)
+    sig = [inputs.random_density(d.p, rng)[0] for d in drops]
+    u = [inputs.random_density(d.p, rng, 3) for d in drops]
+    nc_tot = sum(sh.ncoef(d.p) for d in drops)
+    for precision, tol in ((S.FP64, TOL64), (S.FP32_COMP, TOL32)):
+        ctx = make(S, drops, precision)
+        co = torch.empty(nc_tot, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), co, S.OUT_COEF)
+        assert rel_err(co.cpu().numpy(), np.concatenate(sysm.laplace_coef("ladl", sig))) < tol
+        co3 = torch.empty(3 * nc_tot, device=DEV, dtype=torch.float64)
+        ctx.eval_stokes(T(np.concatenate([a.ravel() for a in u])), T(np.concatenate([a.ravel() for a in u])),
+                        co3, S.OUT_COEF)
+        ref = np.concatenate([a.ravel() for a in sysm.stokes_coef(u, u)])
+        assert rel_err(co3.cpu().numpy(), ref) < tol
+        ctx.close()
+
+
+def test_full_size_two_drops_sampled_targets(S):
+    """Two p = 32 drops 0.1 apart (the two-drop workload) in the bench's launch
+    configuration: target values at sampled targets (first, last, tile edges, closest to the
+    gap) against the oracle evaluated one target at a time."""
+    cfg = inputs.config2(p=32, seed=0, gap=0.1)
+    sysm = oracle_system(cfg.drops)
+    rng = np.random.default_rng(12)
+    sig = [inputs.random_density(d.p, rng)[0] for d in cfg.drops]
+    f = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
+    nt = (32 + 1) * 66
+    picks = [0, 255, 256, 511, 2047, 2048, nt - 1]
+    for i, dg in enumerate(sysm.drops):
+        gap_t = int(np.argmin(np.abs(dg.x0[2] - 0.0)))
+        sel = sorted(set(picks + [gap_t]))
+        for precision, tol in ((0, TOL64), (1, TOL32)):
+            ctx = make(S, cfg.drops, precision, cfg.R)
+            out = torch.empty(2 * nt, device=DEV, dtype=torch.float64)
+            ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), out, S.OUT_GRID)
+            got = out.cpu().numpy()[i * nt:(i + 1) * nt][sel]
+            ref = sysm.laplace_targets("ladl", sig, i, sel)
+            assert rel_err(got, ref) < tol
+            out3 = torch.empty(6 * nt, device=DEV, dtype=torch.float64)
+            ctx.eval_stokes(T(np.concatenate([a.ravel() for a in f])), T(np.concatenate([a.ravel() for a in f])),
+                            out3, S.OUT_GRID)
+            got = out3.cpu().numpy()[3 * i * nt:3 * (i + 1) * nt].reshape(3, nt)[:, sel]
+            ref = sysm.stokes_targets(f, f, i, sel)
+            assert rel_err(got, ref) < tol
+            ctx.close()
+
+
+# --------------------------------------------------------------------------- GMRES
+
+def test_gmres_electric_unit_sphere_closed_form(S):
+    """Eq. E_n on the unit sphere in a uniform field: E_n = 3R/(R+2) E.n (config: p = 16,
+    R = 0.1, E = z)."""
+    cfg = inputs.config1(16)
+    ctx = make(S, cfg.drops, S.FP64, cfg.R)
+    sysm = oracle_system(cfg.drops)
+    b = T(sysm.electric_rhs(cfg.R, cfg.E_u))
+    x = torch.empty_like(b)
+    it, res = ctx.gmres_solve(S.SYS_ELECTRIC, b, x)
+    assert res < 1e-11
+    En = sh.sht_inverse(x.cpu().numpy(), 16, 16)
+    expect = 3 * cfg.R / (cfg.R + 2) * sysm.drops[0].n0[2]
+    assert np.abs(En - expect).max() < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("system", ["electric", "stokes"])
+def test_gmres_two_drops_matches_oracle_solution(S, system):
+    cfg = _two_drop_cfg(6, seed=2, gap=0.4)
+    sysm = oracle_system(cfg.drops)
+    ctx = make(S, cfg.drops, S.FP64, cfg.R)
+    rng = np.random.default_rng(4)
+    if system == "electric":
+        b = sysm.electric_rhs(cfg.R, cfg.E_u)
+        ref, _ = gmres.gmres(lambda v: sysm.electric_matvec(cfg.R, v), b, tol=1e-13)
+        sid = S.SYS_ELECTRIC
+    else:
+        b = np.concatenate([inputs.random_density(d.p, rng, 3).ravel() for d in cfg.drops])
+        ref, _ = gmres.gmres(sysm.stokes_matvec, b, tol=1e-13)
+        sid = S.SYS_STOKES
+    x = torch.empty(b.size, device=DEV, dtype=torch.float64)
+    it, res = ctx.gmres_solve(sid, T(b), x)
+    assert res < 1e-11
+    assert rel_err(x.cpu().numpy(), ref) < 1e-9
+    ctx.close()
+
+
+def test_gmres_restart_and_warm_start(S):
+    """A small Krylov space forces restarts; a warm start at the solution converges at once."""
+    cfg = _two_drop_cfg(5, seed=3, gap=0.4)
+    sysm = oracle_system(cfg.drops)
+    ctx = S.Context(precision=S.FP64, R=cfg.R, gmres_tol=1e-12, gmres_restart=3)
+    ctx.set_drops([d.p for d in cfg.drops], T(np.concatenate([d.xcoef.ravel() for d in cfg.drops])),
+                  [d.lam for d in cfg.drops])
+    b = sysm.electric_rhs(cfg.R, cfg.E_u)
+    x = torch.empty(b.size, device=DEV, dtype=torch.float64)
+    it, res = ctx.gmres_solve(S.SYS_ELECTRIC, T(b), x)
+    assert res < 1e-11 and it > 3
+    it2, res2 = ctx.gmres_solve(S.SYS_ELECTRIC, T(b), torch.empty_like(x), x0=x)
+    assert it2 <= 1 and res2 < 1e-11
+    ctx.close()
+
+
+def test_errors_are_reported_not_raised_by_the_library(S):
+    ctx = S.Context()
+    with pytest.raises(S.ShbimError, match="no drops"):
+        ctx.eval_electric(S.LAPLACE_DL, T(np.zeros(4)), T(np.zeros(4)))
+    cfg = inputs.config1(3)
+    ctx.set_drops([3], T(cfg.drops[0].xcoef.ravel()))
+    with pytest.raises(S.ShbimError, match="bad kernel"):
+        ctx.eval_electric(7, T(np.zeros(16)), T(np.zeros(16)))
+    with pytest.raises(S.ShbimError, match="drop index"):
+        ctx.sht(2, S.SHT_INVERSE, S.GRID_BASE, 1, T(np.zeros(16)), T(np.zeros(32)))
+    ctx.close()
