@@ -36,6 +36,9 @@ import inputs  # noqa: E402
 METRIC = "target-source kernel pairs/s, GMRES time-to-1e-8 per step: mixed/batched vs FP64"
 UNIT = "pairs/s"
 FP64_PEAK_TFLOPS = 1.25         # GB300 FP64 rate (vector and tensor), see the design doc
+# DRAM bytes per launch from one ncu capture of the same kernel and workload (profiles/);
+# None once the kernel has changed since the capture.
+TRAFFIC = {"self_weights": 8154624 + 211138560}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -141,14 +144,25 @@ def run_own(args):
     P = pairs_per_application(cfg)
     E = cfg.E_u
 
+    mixed = args.precision == "fp32comp"
+
+    def solve(sysid, rhs, x):
+        """Time-to-1e-8 solve; returns (operator applications, iterations, FP64 residual)."""
+        if mixed:
+            inner, outer, res = ctx.gmres_solve_refined(sysid, rhs, x, inner_tol=1e-5, max_outer=10)
+            # inner Arnoldi steps + one FP64 residual per outer step (the first residual is b)
+            return inner + outer, inner, res
+        it, res = ctx.gmres_solve(sysid, rhs, x)
+        return it + 1, it, res
+
     def step(xdev, Fdev):
         ctx.set_drops(ps, xdev, lam)
         ctx.electric_rhs(E, rhs_e)
-        it_e, res_e = ctx.gmres_solve(S.SYS_ELECTRIC, rhs_e, En)
+        a_e, it_e, res_e = solve(S.SYS_ELECTRIC, rhs_e, En)
         ctx.eval_electric(S.LAPLACE_SL, En, phi, S.OUT_COEF)
         ctx.eval_stokes(Fdev, None, rhs_s, S.OUT_COEF)
-        it_s, res_s = ctx.gmres_solve(S.SYS_STOKES, rhs_s, u)
-        apps = (it_e + 1) + 1 + 1 + (it_s + 1)
+        a_s, it_s, res_s = solve(S.SYS_STOKES, rhs_s, u)
+        apps = a_e + 1 + 1 + a_s
         return apps, it_e, it_s, res_e, res_s
 
     stream = torch.cuda.current_stream()
@@ -216,6 +230,9 @@ def run_own(args):
     ms_e2e = e2.elapsed_time(e3)
     e2e_value = apps_e2e * P / (ms_e2e / 1e3)
 
+    # time to a 1e-8 FP64 residual for both solves: mixed (refined) vs plain FP64 GMRES
+    tts = time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u)
+
     # roofline of the dominant kernel class (measured above with CUDA events)
     dom = max(cls_ms, key=lambda k: cls_ms[k])
     roof = roofline(dom, cls_ms[dom], cls_n[dom], cfg, args.steps, args.precision, P, apps_total)
@@ -236,6 +253,7 @@ def run_own(args):
                    "l2": "working set (singular rows 0.53 GB) exceeds the 129 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "phase_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
+        "time_to_1e-8": tts,
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": launches,
@@ -252,30 +270,67 @@ def run_own(args):
         torch.distributed.destroy_process_group()
 
 
+def time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u, reps=3):
+    """Electric + Stokes solves to an FP64 relative residual of 1e-8 on the current geometry:
+    mixed precision (FP32 compensated inner GMRES + FP64 refinement) vs plain FP64 GMRES."""
+    out = {}
+    for name in ("fp64", "mixed"):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if name == "fp64":
+                ctx.set_precision(S.FP64)
+                ie, re_ = ctx.gmres_solve(S.SYS_ELECTRIC, rhs_e, En)
+                is_, rs = ctx.gmres_solve(S.SYS_STOKES, rhs_s, u)
+                info = {"iters": [ie, is_], "resid": [re_, rs]}
+            else:
+                ie, oe, re_ = ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs_e, En, inner_tol=1e-5)
+                is_, os_, rs = ctx.gmres_solve_refined(S.SYS_STOKES, rhs_s, u, inner_tol=1e-5)
+                info = {"inner_iters": [ie, is_], "outer": [oe, os_], "resid": [re_, rs]}
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            if best is None or ms < best[0]:
+                best = (ms, info)
+        out[name] = {"ms": best[0], **best[1]}
+    ctx.set_precision(S.FP32_COMP)
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    return out
+
+
 def roofline(dom, ms, n, cfg, steps, precision, P, apps):
     p = cfg.drops[0].p
     q = 2 * p + 1
     nt = (p + 1) * (2 * p + 2)
     ns = (q + 1) * (2 * q + 2)
     if dom == "self_weights":
-        # per (target, rotated node): Fourier synthesis 9 fields x 2p terms x 2 FMA, Legendre
-        # 18 (p+1)(p+2)/2 FMA per (target, latitude) spread over 2q+2 nodes, ~70 flops weights
-        per_unit = 9 * 2 * p * 2 * 2 + 18 * (p + 1) * (p + 2) / 2 * 2 / (2 * q + 2) + 70
+        # per (target, rotated node), as implemented: Legendre sums 18 (p+1)(p+2)/2 FMA per
+        # (target, latitude); four-fold Fourier synthesis 9 (N/4+1) 2p FMA per (target,
+        # latitude); ~70 flops of pointwise geometry and kernel weights. FMA = 2 flops.
+        N = 2 * q + 2
+        per_unit = 2 * (18 * (p + 1) * (p + 2) / 2 + 9 * (N // 4 + 1) * 2 * p) / N + 70
         units = sum(nt * ns for _ in cfg.drops) * steps
         flops = per_unit * units
         ach = flops / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "k_self_weights (FP64)", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n),
-                "peak_source": "GB300 FP64 rate 1.25 TFLOP/s (derived, see DESIGN.md)",
-                "per_unit_flops": per_unit}
+                "traffic": TRAFFIC.get("self_weights"), "launches": n, "avg_launch_ms": ms / max(1, n),
+                "peak_source": "GB300 FP64 rate 1.25 TFLOP/s (nominal, derived in DESIGN.md)",
+                "per_unit_flops": per_unit, "unit_of_work": "(target, rotated source node)"}
     if dom == "self_analysis":
-        per_unit = (p + 1) * 2 * 2 + 2 * (p + 1) * (p + 2) / 2 * 2 / (2 * q + 2)
+        # per (target, component, node): four-fold Fourier 2(p+1)(N/4-1) FMA + N adds per row
+        # of N nodes, Legendre 2 ntri FMA per (item, latitude) spread over N nodes
+        N = 2 * q + 2
+        per_unit = (2 * (2 * (p + 1) * (N // 4 - 1)) + N + 2 * 2 * (p + 1) * (p + 2) / 2) / N
         units = sum(nt * ns * 14 for _ in cfg.drops) * steps
         ach = per_unit * units / (ms / 1e3) / 1e12
-        return {"bound": "alu", "kernel": "k_analysis_fourier/legendre (FP64)", "achieved": ach,
+        return {"bound": "alu", "kernel": "k_analysis_fourier4/legendre (FP64)", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n)}
+                "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n),
+                "per_unit_flops": per_unit, "unit_of_work": "(target, component, rotated node)"}
     if dom == "pairs":
         per_pair = 20
         pk = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12

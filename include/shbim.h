@@ -180,6 +180,16 @@ int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* str
 int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                       double* x_dev, int* iters_host, double* resid_host, void* stream);
 
+/* Mixed-precision solve by iterative refinement: every outer step forms the residual
+ * r = b - A x with FP64 all-pairs sums, solves A d = r by GMRES with FP32 compensated sums to
+ * the relative tolerance inner_tol (e.g. 1e-5), and updates x += d, until the FP64 relative
+ * residual reaches gmres_tol or max_outer steps were taken (SHBIM_ERR_NOT_CONVERGED).
+ * The context's precision setting is restored on return. Reports the total inner Arnoldi
+ * steps, the outer steps and the final FP64 relative residual (each pointer may be NULL). */
+int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
+                              double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
+                              int* outer_iters_host, double* resid_host, void* stream);
+
 /* Number of kernel launches the library has queued since the context was created. */
 int64_t shbim_launch_count(shbim_ctx* ctx);
 

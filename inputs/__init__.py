@@ -94,7 +94,8 @@ def config1(p: int = 16) -> Config:
     """Single unit sphere, lambda=1, R=0.1, Q=1, E=(0,0,1), Gamma = 1 + 0.1 Y_2^0."""
     g = np.zeros(ncoef(p))
     g[0] = SQRT_4PI
-    g[idx(2, 0)] = 0.1
+    if p >= 2:
+        g[idx(2, 0)] = 0.1
     d = Drop(p=p, xcoef=sphere_coef(p), gamma_coef=g, lam=1.0,
              centre=np.zeros(3), radius=1.0)
     return Config("single unit sphere p=%d" % p, [d], R=0.1, Q=1.0,

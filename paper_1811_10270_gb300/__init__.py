@@ -33,7 +33,7 @@ EXPORTS = [
     "shbim_set_drops", "shbim_sizes", "shbim_target_geometry", "shbim_sht", "shbim_eval_electric",
     "shbim_eval_stokes", "shbim_gmres_begin", "shbim_gmres_step", "shbim_gmres_finish",
     "shbim_gmres_solve", "shbim_launch_count", "shbim_electric_rhs", "shbim_set_timing",
-    "shbim_kernel_stats",
+    "shbim_kernel_stats", "shbim_gmres_solve_refined",
 ]
 K_SELF_WEIGHTS = 0
 K_SELF_ANALYSIS = 1
@@ -86,6 +86,7 @@ def lib():
         "shbim_electric_rhs": (i32, [vp, P(dp), dp, vp, vp]),
         "shbim_set_timing": (i32, [vp, i32]),
         "shbim_kernel_stats": (i32, [vp, i32, P(dp), P(i64)]),
+        "shbim_gmres_solve_refined": (i32, [vp, i32, vp, vp, vp, dp, i32, P(i32), P(i32), P(dp), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -218,6 +219,18 @@ class Context:
         self._check(self._L.shbim_kernel_stats(self._h, cls, ctypes.byref(ms), ctypes.byref(n)),
                     "shbim_kernel_stats")
         return ms.value, n.value
+
+    def gmres_solve_refined(self, sys: int, rhs, x, x0=None, inner_tol: float = 1e-5,
+                            max_outer: int = 10):
+        inner = ctypes.c_int32()
+        outer = ctypes.c_int32()
+        r = ctypes.c_double()
+        self._check(self._L.shbim_gmres_solve_refined(self._h, sys, _ptr(rhs), _ptr(x0), _ptr(x),
+                                                      float(inner_tol), int(max_outer),
+                                                      ctypes.byref(inner), ctypes.byref(outer),
+                                                      ctypes.byref(r), _stream()),
+                    "shbim_gmres_solve_refined")
+        return inner.value, outer.value, r.value
 
     def launch_count(self) -> int:
         return int(self._L.shbim_launch_count(self._h))

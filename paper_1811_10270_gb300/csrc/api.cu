@@ -112,6 +112,9 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->gm.Av);
   cudaFree(ctx->gm.diag);
   cudaFree(ctx->gm.y);
+  cudaFree(ctx->gm.xr);
+  cudaFree(ctx->gm.rr);
+  cudaFree(ctx->gm.dr);
   if (ctx->gm.h_host) cudaFreeHost(ctx->gm.h_host);
   delete ctx;
   return SHBIM_OK;
@@ -242,7 +245,7 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = (int64_t)nsm * 8;
     int64_t splits = (want + (int64_t)ctx->tiles.size() - 1) / (int64_t)ctx->tiles.size();
-    splits = std::min<int64_t>(splits, std::max<int64_t>(1, min_other / 512));
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, min_other / 128));
     ctx->pair_splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, 256));
     if ((rc = dalloc(ctx, &ctx->tiles_dev, ctx->tiles.size(), "tiles"))) return rc;
     SHBIM_CUDA(ctx, cudaMemcpy(ctx->tiles_dev, ctx->tiles.data(), ctx->tiles.size() * sizeof(PairTile),

@@ -348,3 +348,101 @@ int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
 }
 
 }  // extern "C"
+
+namespace shbim {
+namespace {
+__global__ void k_add(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) x[e] += d[e];
+}
+}  // namespace
+}  // namespace shbim
+
+extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
+                                         double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
+                                         int* outer_iters_host, double* resid_host, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (sys != SHBIM_SYS_ELECTRIC && sys != SHBIM_SYS_STOKES) return fail(ctx, SHBIM_ERR_ARG, "bad system");
+  if (!rhs_dev || !x_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  if (!(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
+    return fail(ctx, SHBIM_ERR_ARG, "need 0 < inner_tol < 1 and max_outer >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = sys == SHBIM_SYS_ELECTRIC ? ctx->ncoef : 3 * ctx->ncoef;
+  auto& G = ctx->gm;
+  // outer buffers (sized for the larger system)
+  if (!G.xr) {
+    const int64_t cap = 3 * ctx->ncoef;
+    if (cudaMalloc(&G.xr, cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.rr, cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.dr, cap * sizeof(double)) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "refinement buffers");
+  }
+  const int saved_prec = ctx->opts.precision;
+  const double saved_tol = ctx->opts.gmres_tol;
+  const double tol = saved_tol;
+  int inner_total = 0, outer = 0, rc = SHBIM_OK;
+  double rel = 1.0;
+  if (x0_dev) {
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(G.xr, x0_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else {
+    SHBIM_CUDA(ctx, cudaMemsetAsync(G.xr, 0, n * sizeof(double), s));
+  }
+  // ||b||, through the GMRES set-up of the system (FP64 residual)
+  double bnorm = 0.0;
+  for (;;) {
+    // FP64 residual r = b - A x
+    ctx->opts.precision = SHBIM_PREC_FP64;
+    rc = shbim_gmres_begin(ctx, sys, rhs_dev, nullptr, stream);  // sets diag/offdiag, b, ||b||
+    if (rc) break;
+    bnorm = G.bnorm;
+    if (bnorm == 0.0) {
+      rel = 0.0;
+      SHBIM_CUDA(ctx, cudaMemsetAsync(G.xr, 0, n * sizeof(double), s));
+      break;
+    }
+    if (outer == 0 && !x0_dev) {
+      // x = 0: the residual is b itself, no operator application needed
+      SHBIM_CUDA(ctx, cudaMemcpyAsync(G.rr, rhs_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+      rc = system_matvec(ctx, G.xr, G.w, s);
+      if (rc) break;
+      k_sub<<<nb(n), 256, 0, s>>>(rhs_dev, G.w, G.rr, n);
+      SHBIM_CHECK_LAUNCH(ctx, "k_sub");
+    }
+    double* hacc = hacc_ptr(ctx);
+    k_dots<<<1, 256, 0, s>>>(G.rr, n, G.rr, hacc);
+    SHBIM_CHECK_LAUNCH(ctx, "k_dots");
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(G.h_host, hacc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+    rel = std::sqrt(std::max(0.0, G.h_host[0])) / bnorm;
+    if (!std::isfinite(rel)) {
+      rc = fail(ctx, SHBIM_ERR_NONFINITE, "non-finite residual in refinement");
+      break;
+    }
+    if (rel <= tol) break;
+    if (outer >= max_outer) {
+      rc = fail(ctx, SHBIM_ERR_NOT_CONVERGED, "refinement reached max_outer");
+      break;
+    }
+    // inner solve A d = r with FP32 sums
+    ctx->opts.precision = SHBIM_PREC_FP32_COMP;
+    ctx->opts.gmres_tol = inner_tol;
+    int it = 0;
+    rc = shbim_gmres_solve(ctx, sys, G.rr, nullptr, G.dr, &it, nullptr, stream);
+    ctx->opts.gmres_tol = saved_tol;
+    if (rc) break;
+    inner_total += it;
+    k_add<<<nb(n), 256, 0, s>>>(G.xr, G.dr, n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_add");
+    ++outer;
+  }
+  ctx->opts.precision = saved_prec;
+  ctx->opts.gmres_tol = saved_tol;
+  if (rc) return rc;
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(x_dev, G.xr, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (inner_iters_host) *inner_iters_host = inner_total;
+  if (outer_iters_host) *outer_iters_host = outer;
+  if (resid_host) *resid_host = rel;
+  return SHBIM_OK;
+}

@@ -129,6 +129,9 @@ struct shbim_ctx {
     double* diag = nullptr;     // [n] identity part of the system
     double* y = nullptr;        // [m] least-squares solution uploaded for x updates
     double offdiag = 0.0;       // factor of the layer operator in the system
+    double* xr = nullptr;       // [n] refinement: outer iterate
+    double* rr = nullptr;       // [n] refinement: outer residual
+    double* dr = nullptr;       // [n] refinement: correction
     std::vector<double> H;      // (m+1) x m, column-major k*(m+1)+i
     std::vector<double> cs, sn, g;
     int k = 0;                  // Arnoldi steps in the current cycle

@@ -23,6 +23,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "fourier.cuh"
 
 namespace shbim {
 
@@ -96,15 +97,20 @@ __device__ __forceinline__ int isqrt_d(int o) {
   return n;
 }
 
-// v <- Dz(alpha) v in the real basis: S(Rz(alpha) y) = Dz(alpha) S(y).
-__device__ void dz_apply(double* v, int p, double alpha) {
+// cos(m alpha), sin(m alpha) for m = 0..p into shared memory (one sincos per order)
+__device__ void trig_table(double* cz, double* sz, int p, double alpha) {
+  for (int m = threadIdx.x; m <= p; m += blockDim.x) sincos(m * alpha, &sz[m], &cz[m]);
+}
+
+// v <- Dz(alpha) v in the real basis: S(Rz(alpha) y) = Dz(alpha) S(y); sgn = -1 applies
+// Dz(-alpha) from the same table.
+__device__ void dz_apply(double* v, int p, const double* cz, const double* sz, double sgn) {
   const int nc = (p + 1) * (p + 1);
   for (int o = threadIdx.x; o < nc; o += blockDim.x) {
     const int n = isqrt_d(o);
     const int m = o - n * n - n;
     if (m <= 0) continue;
-    double sa, ca;
-    sincos(m * alpha, &sa, &ca);
+    const double ca = cz[m], sa = sgn * sz[m];
     const double a = v[o];
     const double b = v[o - 2 * m];
     v[o] = ca * a - sa * b;
@@ -141,18 +147,24 @@ __global__ void k_rotate_fwd(const double* __restrict__ xc, int nc, int p, int t
   extern __shared__ double sm[];
   double* b0 = sm;
   double* b1 = sm + nc;
+  double* ct = b1 + nc;
+  double* st = ct + (p + 1);
+  double* cp = st + (p + 1);
+  double* sp = cp + (p + 1);
   const int tl = t_begin + blockIdx.x;
   const int f = blockIdx.y;
   const int nlon = 2 * p + 2;
   const double th = theta_base[tl / nlon];
   const double ph = 3.14159265358979323846 * (tl % nlon) / (p + 1);
+  trig_table(ct, st, p, th);
+  trig_table(cp, sp, p, ph);
   for (int o = threadIdx.x; o < nc; o += blockDim.x) b0[o] = xc[(int64_t)f * nc + o];
   __syncthreads();
-  dz_apply(b0, p, -ph);
+  dz_apply(b0, p, cp, sp, -1.0);
   __syncthreads();
   dq_apply(b0, b1, p, dq, dq_off, false);
   __syncthreads();
-  dz_apply(b1, p, -th);
+  dz_apply(b1, p, ct, st, -1.0);
   __syncthreads();
   dq_apply(b1, out + ((int64_t)blockIdx.x * 3 + f) * nc, p, dq, dq_off, true);
 }
@@ -165,19 +177,25 @@ __global__ void k_rotate_adj(const double* __restrict__ vbuf, int nc, int p, int
   extern __shared__ double sm[];
   double* b0 = sm;
   double* b1 = sm + nc;
+  double* ct = b1 + nc;
+  double* st = ct + (p + 1);
+  double* cp = st + (p + 1);
+  double* sp = cp + (p + 1);
   const int tl = t_begin + blockIdx.x;
   const int c = blockIdx.y;
   const int nlon = 2 * p + 2;
   const double th = theta_base[tl / nlon];
   const double ph = 3.14159265358979323846 * (tl % nlon) / (p + 1);
+  trig_table(ct, st, p, th);
+  trig_table(cp, sp, p, ph);
   const double* v = vbuf + ((int64_t)blockIdx.x * ncomp + c) * nc;
   dq_apply(v, b1, p, dq, dq_off, false);
   __syncthreads();
-  dz_apply(b1, p, th);
+  dz_apply(b1, p, ct, st, 1.0);
   __syncthreads();
   dq_apply(b1, b0, p, dq, dq_off, true);
   __syncthreads();
-  dz_apply(b0, p, ph);
+  dz_apply(b0, p, cp, sp, 1.0);
   __syncthreads();
   double* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
                             : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
@@ -204,6 +222,7 @@ __global__ void k_self_weights(const double* __restrict__ rot, int p, int q,
   double* A = sm;             // [3 f][3 kind][2][P1]
   double* tc = A + 18 * P1;
   double* ts = tc + N;
+  double* V = ts + N;         // [9][N] rotated x, x_theta, x_phi/sin on this latitude
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     tc[i] = trig[i];
     ts[i] = trig[N + i];
@@ -226,49 +245,34 @@ __global__ void k_self_weights(const double* __restrict__ rot, int p, int q,
     A[(fk * 2 + cs) * P1 + m] = acc;
   }
   __syncthreads();
+  // Fourier synthesis, four longitudes per task (N = 4(p+1) on the upsampled grid)
+  const int Q4 = N >> 2;
+  for (int task = threadIdx.x; task < 9 * (Q4 + 1); task += blockDim.x) {
+    const int fk = task / (Q4 + 1);
+    const int k = task - fk * (Q4 + 1);
+    const double* Ac = A + (fk * 2) * P1;
+    const double* As = Ac + P1;
+    if (fk % 3 != 2)
+      synth4(Ac, As, Ac[0], 1.0, p, k, N, tc, ts, V + fk * N);
+    else
+      synth4(As, Ac, 0.0, -1.0, p, k, N, tc, ts, V + fk * N);
+  }
+  __syncthreads();
   const int64_t tg = tgt0 + t;
   const double x0 = tgt[tg], y0 = tgt[ntarget + tg], z0 = tgt[2 * ntarget + tg];
   const double n0x = tgt[3 * ntarget + tg], n0y = tgt[4 * ntarget + tg], n0z = tgt[5 * ntarget + tg];
   const double w0 = mu[j] * 0.07957747154594766788;
-  const double s2 = 1.41421356237309504880;
   const int64_t Ns = (int64_t)(q + 1) * N;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    double val[9];
-#pragma unroll
-    for (int fk = 0; fk < 9; ++fk) {
-      const double* Ac = A + (fk * 2) * P1;
-      const double* As = Ac + P1;
-      const int kind = fk % 3;
-      double v = 0.0;
-      int id = 0;
-      if (kind != 2) {
-        for (int m = 1; m <= p; ++m) {
-          id += k;
-          if (id >= N) id -= N;
-          v = fma(Ac[m], tc[id], v);
-          v = fma(As[m], ts[id], v);
-        }
-        v = Ac[0] + s2 * v;
-      } else {
-        for (int m = 1; m <= p; ++m) {
-          id += k;
-          if (id >= N) id -= N;
-          v = fma(-Ac[m], ts[id], v);
-          v = fma(As[m], tc[id], v);
-        }
-        v = s2 * v;
-      }
-      val[fk] = v;
-    }
-    // val[f*3 + kind]: f = x,y,z ; kind = value, d/dtheta, (1/sin) d/dphi
-    const double xt0 = val[1], xt1 = val[4], xt2 = val[7];
-    const double xp0 = val[2], xp1 = val[5], xp2 = val[8];
+    // V[f*3 + kind]: f = x,y,z ; kind = value, d/dtheta, (1/sin) d/dphi
+    const double xt0 = V[1 * N + k], xt1 = V[4 * N + k], xt2 = V[7 * N + k];
+    const double xp0 = V[2 * N + k], xp1 = V[5 * N + k], xp2 = V[8 * N + k];
     const double c0 = xt1 * xp2 - xt2 * xp1;
     const double c1 = xt2 * xp0 - xt0 * xp2;
     const double c2 = xt0 * xp1 - xt1 * xp0;
     const double J = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
     const double nx = c0 / J, ny = c1 / J, nz = c2 / J;
-    const double hx = x0 - val[0], hy = y0 - val[3], hz = z0 - val[6];
+    const double hx = x0 - V[k], hy = y0 - V[3 * N + k], hz = z0 - V[6 * N + k];
     const double r2 = hx * hx + hy * hy + hz * hz;
     const double ri = 1.0 / sqrt(r2);
     const double ri2 = ri * ri;
@@ -324,15 +328,15 @@ int build_singular_rows(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
         (rc = ensure(ctx, &ctx->vbuf, &ctx->vbuf_elems, (size_t)CT * ncomp * nc, "row buffer")))
       return rc;
     const double* xc = xcoef + 3 * d.coef_off;
-    const int rot_smem = 2 * nc * (int)sizeof(double);
+    const int rot_smem = (2 * nc + 4 * (d.p + 1)) * (int)sizeof(double);
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
     for (int t0 = 0; t0 < d.nt; t0 += CT) {
       const int ct = std::min(CT, d.nt - t0);
-      k_rotate_fwd<<<dim3(ct, 3), 128, 2 * nc * sizeof(double), s>>>(
+      k_rotate_fwd<<<dim3(ct, 3), 128, rot_smem, s>>>(
           xc, nc, d.p, t0, d.tab->base.theta, d.tab->dq, d.tab->dq_off_dev, ctx->rot_coef);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_fwd");
-      const size_t smem = (size_t)(18 * (d.p + 1) + 2 * (2 * d.q + 2)) * sizeof(double);
+      const size_t smem = (size_t)(18 * (d.p + 1) + 11 * (2 * d.q + 2)) * sizeof(double);
       {
         TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
         k_self_weights<<<dim3(ct, d.q + 1), 128, smem, s>>>(ctx->rot_coef, d.p, d.q, up.alf, up.trig,
@@ -345,7 +349,7 @@ int build_singular_rows(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
         rc = sht_analysis(ctx, up, ct * ncomp, ctx->wbuf, Ns, false, ctx->vbuf, nc, s);
         if (rc) return rc;
       }
-      k_rotate_adj<<<dim3(ct, ncomp), 128, 2 * nc * sizeof(double), s>>>(
+      k_rotate_adj<<<dim3(ct, ncomp), 128, rot_smem, s>>>(
           ctx->vbuf, nc, d.p, t0, ncomp, d.tab->base.theta, d.tab->dq, d.tab->dq_off_dev,
           d.rows_lap, d.rows_sto);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_adj");

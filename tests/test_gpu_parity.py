@@ -322,3 +322,28 @@ def test_errors_are_reported_not_raised_by_the_library(S):
     with pytest.raises(S.ShbimError, match="drop index"):
         ctx.sht(2, S.SHT_INVERSE, S.GRID_BASE, 1, T(np.zeros(16)), T(np.zeros(32)))
     ctx.close()
+
+
+@pytest.mark.parametrize("system", ["electric", "stokes"])
+def test_refined_mixed_precision_solve_reaches_fp64_residual(S, system):
+    """Iterative refinement: FP32 compensated inner GMRES, FP64 outer residual; the result
+    satisfies the FP64 system to 1e-10 and equals the FP64 GMRES solution."""
+    cfg = _two_drop_cfg(8, seed=5, gap=0.2)
+    sysm = oracle_system(cfg.drops)
+    rng = np.random.default_rng(8)
+    if system == "electric":
+        b = sysm.electric_rhs(cfg.R, cfg.E_u)
+        ref, _ = gmres.gmres(lambda v: sysm.electric_matvec(cfg.R, v), b, tol=1e-13)
+        sid = S.SYS_ELECTRIC
+    else:
+        b = np.concatenate([inputs.random_density(d.p, rng, 3).ravel() for d in cfg.drops])
+        ref, _ = gmres.gmres(sysm.stokes_matvec, b, tol=1e-13)
+        sid = S.SYS_STOKES
+    ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-10)
+    ctx.set_drops([d.p for d in cfg.drops], T(np.concatenate([d.xcoef.ravel() for d in cfg.drops])),
+                  [d.lam for d in cfg.drops])
+    x = torch.empty(b.size, device=DEV, dtype=torch.float64)
+    inner, outer, res = ctx.gmres_solve_refined(sid, T(b), x, inner_tol=1e-5, max_outer=8)
+    assert res <= 1e-10 and 1 <= outer <= 4, (inner, outer, res)
+    assert rel_err(x.cpu().numpy(), ref) < 1e-9
+    ctx.close()
