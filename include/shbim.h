@@ -190,6 +190,29 @@ int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, co
                               double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
                               int* outer_iters_host, double* resid_host, void* stream);
 
+/* Allocation-free Laplace pair sum, for callers that must not allocate device memory at call
+ * time -- for example code running while a CUDA stream is being captured into a graph, or a
+ * host application that reserves all of its device memory up front. The paper has no
+ * counterpart: this is a service variant of the FP64 all-pairs kernel.
+ * Computes, for every target t, out[t] = 1/(4 pi) sum_s K(x_t, x_s) s_s over ALL sources (no
+ * pair is excluded), with K = (x_t - x_s).n_t / r^3 for SHBIM_LAPLACE_DL and 1/r for
+ * SHBIM_LAPLACE_SL, in FP64.
+ *   tgt_dev   6 * n_tgt doubles: [x..][y..][z..][nx..][ny..][nz..] (normals unused for SL)
+ *   src_dev   4 * n_src doubles: [x..][y..][z..][s..] with s the source strength
+ *             (density times quadrature weight)
+ *   out_dev   n_tgt doubles
+ * Needs no context and calls no allocator: its partial sums live in one fixed array of
+ * 2^21 doubles (16 MiB) in device memory, which every GPU that loads the library holds
+ * until the process exits. Hence n_tgt must not exceed 2^21 (2097152); larger sizes return
+ * SHBIM_ERR_ARG, as do a bad `which` or null pointers. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it per device; make that
+ * first call before any stream capture. All calls share the array: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race on it and must
+ * be serialised by the caller. Nothing in the array needs to start at zero (every slot read
+ * is written by the same call). Returns 0, SHBIM_ERR_ARG or SHBIM_ERR_CUDA. */
+int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int64_t n_tgt, const double* src_dev,
+                                int64_t n_src, double* out_dev, void* stream);
+
 /* Number of kernel launches the library has queued since the context was created. */
 int64_t shbim_launch_count(shbim_ctx* ctx);
 

@@ -33,8 +33,9 @@ EXPORTS = [
     "shbim_set_drops", "shbim_sizes", "shbim_target_geometry", "shbim_sht", "shbim_eval_electric",
     "shbim_eval_stokes", "shbim_gmres_begin", "shbim_gmres_step", "shbim_gmres_finish",
     "shbim_gmres_solve", "shbim_launch_count", "shbim_electric_rhs", "shbim_set_timing",
-    "shbim_kernel_stats", "shbim_gmres_solve_refined",
+    "shbim_kernel_stats", "shbim_gmres_solve_refined", "shbim_pairs_laplace_noalloc",
 ]
+NOALLOC_MAX_TARGETS = 1 << 21
 K_SELF_WEIGHTS = 0
 K_SELF_ANALYSIS = 1
 K_PAIRS = 2
@@ -87,6 +88,7 @@ def lib():
         "shbim_set_timing": (i32, [vp, i32]),
         "shbim_kernel_stats": (i32, [vp, i32, P(dp), P(i64)]),
         "shbim_gmres_solve_refined": (i32, [vp, i32, vp, vp, vp, dp, i32, P(i32), P(i32), P(dp), vp]),
+        "shbim_pairs_laplace_noalloc": (i32, [i32, vp, i64, vp, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -108,6 +110,17 @@ def _ptr(t):
 def _stream():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def pairs_laplace_noalloc(which: int, tgt, src, out, n_tgt=None, n_src=None) -> int:
+    """shbim_pairs_laplace_noalloc: FP64 Laplace pair sum of src (4 x n_src: x, y, z, strength)
+    at tgt (6 x n_tgt: x, y, z, nx, ny, nz) into out, without any device allocation. Returns the
+    library's status code (0 on success)."""
+    L = lib()
+    nt = out.numel() if n_tgt is None else int(n_tgt)
+    ns = src.numel() // 4 if n_src is None else int(n_src)
+    return int(L.shbim_pairs_laplace_noalloc(int(which), _ptr(tgt), nt, _ptr(src), ns, _ptr(out),
+                                             _stream()))
 
 
 class Context:
