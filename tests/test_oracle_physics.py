@@ -1,0 +1,107 @@
+"""Pins of the oracle's force, surfactant and time-step code (Section 2, Algorithm 1)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import sph_harm_y
+
+import inputs
+from oracle import physics as P, sh
+
+
+def test_second_derivative_basis_matches_library():
+    rng = np.random.default_rng(0)
+    th = rng.uniform(0.2, 2.9, 25)
+    ph = rng.uniform(0.0, 6.2, 25)
+    B = P.basis2(6, th, ph)
+    for n in range(7):
+        for m in range(0, n + 1):
+            Y, dY, d2Y = sph_harm_y(n, m, th, ph, diff_n=2)
+            f = 1.0 if m == 0 else math.sqrt(2.0)
+            refs = [Y, dY[:, 0], dY[:, 1], d2Y[:, 0, 0], d2Y[:, 0, 1], d2Y[:, 1, 1]]
+            for k, ref in enumerate(refs):
+                np.testing.assert_allclose(B[k][sh.idx(n, m)], f * ref.real, atol=1e-12)
+                if m > 0:
+                    np.testing.assert_allclose(B[k][sh.idx(n, -m)], f * ref.imag, atol=1e-12)
+
+
+def test_surface_calculus_identities():
+    """Sphere of radius a: H = 1/a, J = a^2. Any closed surface: int 2 H n dS = 0,
+    div_S x = 2, grad_S (c.x) = c - (c.n) n."""
+    sg = P.SurfaceGrid(inputs.sphere_coef(5, 1.7, (0.3, 0.0, 0.0)), 5, 11)
+    np.testing.assert_allclose(sg.H, 1 / 1.7, atol=1e-14)
+    np.testing.assert_allclose(sg.J, 1.7 ** 2, atol=1e-13)
+    xc = inputs.perturbed_coef(6, np.random.default_rng(1), 1.0, (0, 0, 0), lmax=3)
+    sg = P.SurfaceGrid(xc, 6, 13)
+    assert np.abs((sg.omega * sg.J * 2 * sg.H * sg.n).sum(axis=1)).max() < 1e-10
+    np.testing.assert_allclose(sg.div(xc), 2.0, atol=1e-13)
+    c = np.array([0.3, -1.0, 2.0])
+    g = sg.grad(c @ xc)
+    np.testing.assert_allclose(g, c[:, None] - (c[:, None] * sg.n).sum(0) * sg.n, atol=1e-13)
+
+
+def test_langmuir_and_traction_formulas():
+    g, dg = P.langmuir(np.array([1.0, 0.5]), 0.2, 0.5)
+    assert abs(g[0] - 1.0) < 1e-15                  # normalised: gamma(1) = 1
+    h = 1e-6
+    g2, _ = P.langmuir(np.array([0.5 + h, 0.5 - h]), 0.2, 0.5)
+    assert abs((g2[0] - g2[1]) / (2 * h) - dg[1]) < 1e-8
+    n = np.array([[0.0], [0.0], [1.0]])
+    Et = np.array([[0.3], [0.0], [0.0]])
+    fE = P.electric_traction(np.array([2.0]), Et, n, R=2.0, Q=0.5)
+    # Eq. el_force term by term
+    exp_n = 0.5 * ((1 - 0.5 / 4) * 4.0 - (1 - 0.5) * 0.09)
+    np.testing.assert_allclose(fE[:, 0], [(1 - 0.25) * 2.0 * 0.3, 0.0, exp_n], atol=1e-15)
+
+
+@pytest.mark.parametrize("R,Q", [(0.1, 1.0), (2.0, 0.5)])
+def test_initial_deformation_rate_of_a_sphere(R, Q):
+    """For a spherical drop the Stokes flow of the first instant is exact linear theory:
+    dD/dt = D_T / tau_D with D_T the first-order deformation of Eq. DS2clean (Ca_E term) and
+    tau_D = Ca_E (19 lam+16)(2 lam+3) / (40 (lam+1)) (Section 4.1). This fixes E_n, E_t, the
+    traction of Eq. el_force, the Stokes operators and the sign of the single layer of
+    Eq. main_eq at once (R = 0.1, Q = 1 flattens the drop; R = 2, Q = 0.5 elongates it)."""
+    p = 8
+    prm = P.Params(R=R, Q=Q, Ca_E=0.1, beta=0.0)
+    g0 = np.zeros(sh.ncoef(p))
+    g0[0] = math.sqrt(4 * math.pi)
+    u, _ = P.rates([inputs.sphere_coef(p)], [g0], [p], [1.0], prm)
+    uv = sh.sht_inverse(u[0], p, p)
+    th, ph = sh.grid_points(p)
+    n = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    ur = (uv * n).sum(0)
+    A = np.stack([np.ones_like(th), 0.5 * (3 * np.cos(th) ** 2 - 1)]).T
+    coef, *_ = np.linalg.lstsq(A, ur, rcond=None)
+    np.testing.assert_allclose(A @ coef, ur, atol=1e-12)     # a pure P_2 normal velocity
+    dD = 0.75 * coef[1]                                     # (u_r(pole) - u_r(equator)) / 2
+    lam = 1.0
+    DT = 9 * (2 + 3 * R + 2 * R * R - 7 * Q) / (32 * (2 + R) ** 2)
+    tau = (19 * lam + 16) * (2 * lam + 3) / (40 * (lam + 1))
+    assert abs(dD - DT / tau) < 1e-11
+
+
+def test_sphere_without_field_is_at_rest():
+    p = 6
+    prm = P.Params(E_u=(0.0, 0.0, 0.0), beta=0.2)
+    g0 = np.zeros(sh.ncoef(p))
+    g0[0] = math.sqrt(4 * math.pi)
+    u, gE = P.rates([inputs.sphere_coef(p)], [g0], [p], [1.0], prm)
+    assert np.abs(u[0]).max() < 1e-12 and np.abs(gE[0]).max() < 1e-12
+
+
+def test_step_conserves_surfactant_and_converges_second_order():
+    """One midpoint step on a perturbed surfactant-covered drop: the surfactant mass changes
+    by far less than the step moves the interface, and the explicit-Euler error estimate
+    shrinks like dt^2."""
+    p = 6
+    rng = np.random.default_rng(3)
+    x = inputs.perturbed_coef(p, rng, 1.0, (0, 0, 0), lmax=3)
+    g = inputs.gamma_random(p, rng)
+    prm = P.Params(R=2.0, Q=0.5, Ca_E=0.1)
+    m0 = P.surfactant_mass(x, g, p)
+    errs = []
+    for dt in (0.02, 0.01):
+        xn, gn, err, _ = P.step([x], [g], [p], [1.0], dt, prm)
+        errs.append(err)
+        assert abs(P.surfactant_mass(xn[0], gn[0], p) - m0) / m0 < 1e-4 * dt
+    assert 3.0 < errs[0] / errs[1] < 5.0
