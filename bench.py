@@ -3,12 +3,11 @@
 
 Workload (default): two perturbed unit drops of degree p = 32, centre gap 2.1 (surface gap
 0.1), lambda = 5, R = 2, Q = 0.5, uniform field E = z (the two-drop configuration), inputs
-seeded and synthetic. One step is one operator stage of a time step for a new geometry:
-  set_drops (geometry + singular self rows of every kernel),
-  electric GMRES solve to 1e-8 (Eq. galerkin_En),
-  Laplace single layer of the solution (potential of Eq. BIE01),
-  Stokes single layer of a traction density (right-hand side of Eq. main_eq),
-  Stokes GMRES solve to 1e-8 (double layer, Eq. main_eq).
+seeded and synthetic. One step is one midpoint time step of Algorithm 1 (shbim_step), whose two stages each
+build the geometry and singular self rows, solve the electric system (Eq. galerkin_En),
+evaluate the charge potential, the electric and interfacial forces (Eqs. el_force,
+interfacial_force, langmuir), solve the Stokes system (Eq. main_eq) and form the surfactant
+rate; GMRES stops at an FP64 relative residual of 1e-8 (mixed precision by refinement).
 Metric: target-source kernel pairs per second = operator applications in the step x
 sum_i N_t(i) x sum_j N_s(j) / step time (self pairs counted as N_t N_s rotated pairs).
 
@@ -131,43 +130,32 @@ def run_own(args):
     ps = [d.p for d in cfg.drops]
     lam = [d.lam for d in cfg.drops]
     x_host = np.concatenate([d.xcoef.ravel() for d in cfg.drops])
+    g_host = np.concatenate([d.gamma_coef for d in cfg.drops])
     f_host = np.concatenate([a.ravel() for a in f])
     xc = torch.tensor(x_host, device=dev)
+    gc = torch.tensor(g_host, device=dev)
     F = torch.tensor(f_host, device=dev)
     nc = sum((p + 1) ** 2 for p in ps)
-    nt = sum((p + 1) * (2 * p + 2) for p in ps)
-    rhs_e = torch.empty(nc, device=dev, dtype=torch.float64)
-    En = torch.empty(nc, device=dev, dtype=torch.float64)
-    phi = torch.empty(nc, device=dev, dtype=torch.float64)
-    rhs_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
-    u = torch.empty(3 * nc, device=dev, dtype=torch.float64)
     P = pairs_per_application(cfg)
     E = cfg.E_u
+    ph = S.phys(R=cfg.R, Q=cfg.Q, Ca_E=cfg.Ca_E, beta=0.2, x_s=0.5, E_u=tuple(E), inner_tol=1e-5)
+    ctx.set_drops(ps, xc, lam)
+    x_out = torch.empty_like(xc)
+    g_out = torch.empty_like(gc)
+    rhs_e = torch.empty(nc, device=dev, dtype=torch.float64)
+    rhs_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    En = torch.empty(nc, device=dev, dtype=torch.float64)
+    u = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    dt = args.dt
 
-    mixed = args.precision == "fp32comp"
-
-    def solve(sysid, rhs, x):
-        """Time-to-1e-8 solve; returns (operator applications, iterations, FP64 residual)."""
-        if mixed:
-            inner, outer, res = ctx.gmres_solve_refined(sysid, rhs, x, inner_tol=1e-5, max_outer=10)
-            # inner Arnoldi steps + one FP64 residual per outer step (the first residual is b)
-            return inner + outer, inner, res
-        it, res = ctx.gmres_solve(sysid, rhs, x)
-        return it + 1, it, res
-
-    def step(xdev, Fdev):
-        ctx.set_drops(ps, xdev, lam)
-        ctx.electric_rhs(E, rhs_e)
-        a_e, it_e, res_e = solve(S.SYS_ELECTRIC, rhs_e, En)
-        ctx.eval_electric(S.LAPLACE_SL, En, phi, S.OUT_COEF)
-        ctx.eval_stokes(Fdev, None, rhs_s, S.OUT_COEF)
-        a_s, it_s, res_s = solve(S.SYS_STOKES, rhs_s, u)
-        apps = a_e + 1 + 1 + a_s
-        return apps, it_e, it_s, res_e, res_s
+    def step(xdev, gdev):
+        a0 = ctx.operator_applications()
+        err, its = ctx.step(ph, xdev, gdev, dt, x_out, g_out)
+        return ctx.operator_applications() - a0, err, its
 
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
-        step(xc, F)
+        step(xc, gc)
     torch.cuda.synchronize()
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
@@ -182,7 +170,7 @@ def run_own(args):
     apps_total = 0
     stats = []
     for _ in range(args.steps):
-        r = step(xc, F)
+        r = step(xc, gc)
         apps_total += r[0]
         stats.append(r)
     e1.record(stream)
@@ -208,11 +196,11 @@ def run_own(args):
         apps_total = int(a.item())
     value = apps_total * P / (ms / 1e3)
 
-    # end to end: host inputs copied in, solutions copied out, every step
+    # end to end: the state is copied in from pinned host memory and the new state read back
     x_pin = torch.tensor(x_host).pin_memory()
-    F_pin = torch.tensor(f_host).pin_memory()
-    En_h = torch.empty(nc, dtype=torch.float64).pin_memory()
-    u_h = torch.empty(3 * nc, dtype=torch.float64).pin_memory()
+    g_pin = torch.tensor(g_host).pin_memory()
+    x_h = torch.empty(3 * nc, dtype=torch.float64).pin_memory()
+    g_h = torch.empty(nc, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
@@ -220,15 +208,19 @@ def run_own(args):
     apps_e2e = 0
     for _ in range(args.steps):
         xd = x_pin.to(dev, non_blocking=True)
-        Fd = F_pin.to(dev, non_blocking=True)
-        r = step(xd, Fd)
+        gd = g_pin.to(dev, non_blocking=True)
+        r = step(xd, gd)
         apps_e2e += r[0]
-        En_h.copy_(En, non_blocking=True)
-        u_h.copy_(u, non_blocking=True)
+        x_h.copy_(x_out, non_blocking=True)
+        g_h.copy_(g_out, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
     e2e_value = apps_e2e * P / (ms_e2e / 1e3)
+
+    # the operator solves on the half-step geometry: right-hand sides for the comparison
+    ctx.electric_rhs(E, rhs_e)
+    ctx.eval_stokes(F, None, rhs_s, S.OUT_COEF)
 
     # time to a 1e-8 FP64 residual for both solves: mixed (refined) vs plain FP64 GMRES
     tts = time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u)
@@ -243,13 +235,13 @@ def run_own(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "fp32comp" else "f64",
         "data": "synthetic",
-        "config": {"workload": "two drops p=32 gap=0.1 (lambda=5, R=2, Q=0.5, E=z), one operator "
-                               "stage: geometry + singular rows + electric GMRES + potential + "
-                               "Stokes RHS + Stokes GMRES, tol 1e-8",
-                   "pair_sums": args.precision, "pairs_per_application": P,
+        "config": {"workload": "two drops p=32 gap=0.1 (lambda=5, R=2, Q=0.5, Ca_E=0.1, Langmuir "
+                               "beta=0.2 x_s=0.5, E=z): one midpoint time step (Algorithm 1) = 2 x "
+                               "(geometry + singular rows + electric solve + potential + forces + "
+                               "Stokes solve + surfactant rate), GMRES to an FP64 residual of 1e-8",
+                   "dt": args.dt, "pair_sums": args.precision, "pairs_per_application": P,
                    "applications_per_step": apps_total / max(1, args.steps) / max(1, world),
-                   "gmres_iters": {"electric": stats[-1][1], "stokes": stats[-1][2]},
-                   "gmres_final_resid": {"electric": stats[-1][3], "stokes": stats[-1][4]},
+                   "gmres_iters_per_step": stats[-1][2], "step_error_estimate": stats[-1][1],
                    "l2": "working set (singular rows 0.53 GB) exceeds the 129 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "phase_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
@@ -258,8 +250,8 @@ def run_own(args):
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": int(x_host.nbytes + f_host.nbytes),
-                "d2h_bytes_per_step": int(8 * (nc + 3 * nc))},
+                "h2d_bytes_per_step": int(x_host.nbytes + g_host.nbytes),
+                "d2h_bytes_per_step": int(x_host.nbytes + g_host.nbytes)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.p, args.cpu_targets)
@@ -312,7 +304,7 @@ def roofline(dom, ms, n, cfg, steps, precision, P, apps):
         # latitude); ~70 flops of pointwise geometry and kernel weights. FMA = 2 flops.
         N = 2 * q + 2
         per_unit = 2 * (18 * (p + 1) * (p + 2) / 2 + 9 * (N // 4 + 1) * 2 * p) / N + 70
-        units = sum(nt * ns for _ in cfg.drops) * steps
+        units = sum(nt * ns for _ in cfg.drops) * steps * 2   # two geometries per step
         flops = per_unit * units
         ach = flops / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "k_self_weights (FP64)", "achieved": ach,
@@ -325,7 +317,7 @@ def roofline(dom, ms, n, cfg, steps, precision, P, apps):
         # of N nodes, Legendre 2 ntri FMA per (item, latitude) spread over N nodes
         N = 2 * q + 2
         per_unit = (2 * (2 * (p + 1) * (N // 4 - 1)) + N + 2 * 2 * (p + 1) * (p + 2) / 2) / N
-        units = sum(nt * ns * 14 for _ in cfg.drops) * steps
+        units = sum(nt * ns * 14 for _ in cfg.drops) * steps * 2
         ach = per_unit * units / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "k_analysis_fourier4/legendre (FP64)", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
@@ -409,6 +401,7 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--precision", default="fp32comp", choices=["fp32comp", "fp64"])
     ap.add_argument("--p", type=int, default=32)
+    ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--cpu-targets", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -180,6 +180,47 @@ int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* str
 int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                       double* x_dev, int* iters_host, double* resid_host, void* stream);
 
+/* Physical parameters of the drop problem (Section 2).
+ * E_n is solved with R; the traction uses Q and R (Eq. el_force, eps = 1); the capillary
+ * force is scaled by 1/Ca_E (Eq. main_eq); the tension follows the Langmuir law normalised so
+ * that gamma(1) = 1, gamma = (1 + beta ln(1 - x_s Gamma)) / (1 + beta ln(1 - x_s))
+ * (Eq. langmuir; beta = 0 is a clean drop). The far field is E_u + E_q (x, -y, 0).
+ * inner_tol is the FP32 inner tolerance of the refined solves used when the context's
+ * precision is SHBIM_PREC_FP32_COMP (otherwise plain FP64 GMRES). */
+typedef struct shbim_phys {
+  double R, Q, Ca_E;
+  double beta, x_s;
+  double E_u[3];
+  double E_q;
+  double inner_tol;
+} shbim_phys;
+
+/* Velocity and surfactant rate for the current drop shapes (steps i-vi of Section 2):
+ * solves for E_n, forms E_t = -grad_S(phi_inf + S_L[(1-1/R) E_n]), the electric and
+ * interfacial forces on each drop's degree 2p+1 grid (products de-aliased by projection to
+ * degree p), solves the Stokes system with right-hand side -sum_j S_j[f/Ca_E - f^E] and forms
+ * the surfactant rate -Gamma div_S u of nodes that move with u (Eq. surfactant0, material
+ * form, no diffusion).
+ *   gamma_dev  ncoef coefficients of Gamma
+ *   u_dev      3 ncoef velocity coefficients (out);  gE_dev  ncoef rate coefficients (out)
+ *   iters_host GMRES iterations of the electric and Stokes solves (2 ints, may be NULL)
+ * Synchronises `stream` (GMRES reads residuals back). */
+int shbim_rates(shbim_ctx* ctx, const shbim_phys* phys, const double* gamma_dev, double* u_dev,
+                double* gE_dev, int* iters_host, void* stream);
+
+/* One time step of Algorithm 1 (midpoint rule for x, explicit stage for Gamma):
+ * rates at (x, Gamma), half step, rates at the half step, full step
+ *   x_out = x + dt u(t+dt/2),  Gamma_out = Gamma + dt g_E(t+dt/2),
+ * and the error estimate err = dt max(|u(t+dt/2) - u(t)|, |g_E(t+dt/2) - g_E(t)|) (grid max
+ * norms on the degree-p grids), i.e. the distance to the explicit Euler step. The drop layout
+ * must have been set with shbim_set_drops; x_dev (3 ncoef) replaces the shapes. Outputs must
+ * not alias the inputs, so the caller can reject the step (adaptive dt: accept if err < tol,
+ * then dt <- dt (0.9 tol / err)^(1/2)). iters_host: 4 GMRES counts (may be NULL).
+ * After the call the context holds the geometry of the half step. */
+int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, const double* gamma_dev,
+               double dt, double* x_out_dev, double* gamma_out_dev, double* err_host, int* iters_host,
+               void* stream);
+
 /* Mixed-precision solve by iterative refinement: every outer step forms the residual
  * r = b - A x with FP64 all-pairs sums, solves A d = r by GMRES with FP32 compensated sums to
  * the relative tolerance inner_tol (e.g. 1e-5), and updates x += d, until the FP64 relative
@@ -215,6 +256,10 @@ int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int64_t n_tgt,
 
 /* Number of kernel launches the library has queued since the context was created. */
 int64_t shbim_launch_count(shbim_ctx* ctx);
+
+/* Number of layer-operator applications (calls of the electric or Stokes operator, including
+ * those made inside GMRES and the time step) since the context was created. */
+int64_t shbim_operator_applications(shbim_ctx* ctx);
 
 /* Kernel timing (measurement support, off by default). When on, the library brackets every
  * launch of the timed kernel classes below with CUDA events on the launching stream.

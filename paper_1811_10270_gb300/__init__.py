@@ -34,6 +34,7 @@ EXPORTS = [
     "shbim_eval_stokes", "shbim_gmres_begin", "shbim_gmres_step", "shbim_gmres_finish",
     "shbim_gmres_solve", "shbim_launch_count", "shbim_electric_rhs", "shbim_set_timing",
     "shbim_kernel_stats", "shbim_gmres_solve_refined", "shbim_pairs_laplace_noalloc",
+    "shbim_rates", "shbim_step", "shbim_operator_applications",
 ]
 NOALLOC_MAX_TARGETS = 1 << 21
 K_SELF_WEIGHTS = 0
@@ -52,6 +53,18 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("gmres_restart", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_maxiter", ctypes.c_int),
                 ("R", ctypes.c_double)]
+
+
+class Phys(ctypes.Structure):
+    """shbim_phys: R, Q, Ca_E, Langmuir beta and x_s, far field E_u + E_q (x, -y, 0), and the
+    inner tolerance of the mixed-precision solves."""
+    _fields_ = [("R", ctypes.c_double), ("Q", ctypes.c_double), ("Ca_E", ctypes.c_double),
+                ("beta", ctypes.c_double), ("x_s", ctypes.c_double), ("E_u", ctypes.c_double * 3),
+                ("E_q", ctypes.c_double), ("inner_tol", ctypes.c_double)]
+
+
+def phys(R=2.0, Q=0.5, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.0, 1.0), E_q=0.0, inner_tol=1e-5):
+    return Phys(R, Q, Ca_E, beta, x_s, (ctypes.c_double * 3)(*E_u), E_q, inner_tol)
 
 
 _lib = None
@@ -89,6 +102,9 @@ def lib():
         "shbim_kernel_stats": (i32, [vp, i32, P(dp), P(i64)]),
         "shbim_gmres_solve_refined": (i32, [vp, i32, vp, vp, vp, dp, i32, P(i32), P(i32), P(dp), vp]),
         "shbim_pairs_laplace_noalloc": (i32, [i32, vp, i64, vp, i64, vp, vp]),
+        "shbim_rates": (i32, [vp, P(Phys), vp, vp, vp, P(i32), vp]),
+        "shbim_step": (i32, [vp, P(Phys), vp, vp, dp, vp, vp, P(dp), P(i32), vp]),
+        "shbim_operator_applications": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -244,6 +260,23 @@ class Context:
                                                       ctypes.byref(r), _stream()),
                     "shbim_gmres_solve_refined")
         return inner.value, outer.value, r.value
+
+    def rates(self, ph, gamma, u, gE):
+        it = (ctypes.c_int32 * 2)()
+        self._check(self._L.shbim_rates(self._h, ctypes.byref(ph), _ptr(gamma), _ptr(u), _ptr(gE), it,
+                                        _stream()), "shbim_rates")
+        return list(it)
+
+    def step(self, ph, x, gamma, dt, x_out, gamma_out):
+        err = ctypes.c_double()
+        it = (ctypes.c_int32 * 4)()
+        self._check(self._L.shbim_step(self._h, ctypes.byref(ph), _ptr(x), _ptr(gamma), float(dt),
+                                       _ptr(x_out), _ptr(gamma_out), ctypes.byref(err), it, _stream()),
+                    "shbim_step")
+        return err.value, list(it)
+
+    def operator_applications(self) -> int:
+        return int(self._L.shbim_operator_applications(self._h))
 
     def launch_count(self) -> int:
         return int(self._L.shbim_launch_count(self._h))

@@ -20,6 +20,30 @@ int cuda_fail(shbim_ctx* ctx, cudaError_t e, const char* what) {
 
 int pairs_tile_targets();
 
+// Shape-dependent state for the current layout: drop centres (x_00 / sqrt(4 pi), the mean
+// position over the parameter sphere), the device drop table, geometry and singular rows.
+int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  for (auto& d : ctx->drops) {
+    double c00[3];
+    for (int c = 0; c < 3; ++c)
+      SHBIM_CUDA(ctx, cudaMemcpy(&c00[c], xcoef_dev + 3 * d.coef_off + (int64_t)c * d.nc, sizeof(double),
+                                 cudaMemcpyDeviceToHost));
+    for (int c = 0; c < 3; ++c) d.centre[c] = c00[c] / std::sqrt(4.0 * kPi);
+  }
+  std::vector<DropDev> dd(ctx->n_drops);
+  for (int i = 0; i < ctx->n_drops; ++i) {
+    const Drop& d = ctx->drops[i];
+    dd[i] = DropDev{d.p, d.q, d.nt, d.ns, d.nc, d.coef_off, d.tgt_off, d.src_off, d.lam,
+                    d.centre[0], d.centre[1], d.centre[2], d.rows_lap, d.rows_sto};
+  }
+  SHBIM_CUDA(ctx, cudaMemcpy(ctx->drops_dev, dd.data(), dd.size() * sizeof(DropDev), cudaMemcpyHostToDevice));
+  int rc;
+  if ((rc = build_geometry(ctx, xcoef_dev, s))) return rc;
+  if ((rc = build_singular_rows(ctx, xcoef_dev, s))) return rc;
+  return SHBIM_OK;
+}
+
 namespace {
 
 void free_drop_state(shbim_ctx* ctx) {
@@ -46,6 +70,8 @@ void free_drop_state(shbim_ctx* ctx) {
   ctx->part = nullptr;
   cudaFree(ctx->grid_out);
   ctx->grid_out = nullptr;
+  cudaFree(ctx->xup);
+  ctx->xup = nullptr;
   ctx->tiles.clear();
   ctx->n_drops = 0;
   ctx->ncoef = ctx->ntarget = ctx->nsource = 0;
@@ -112,6 +138,9 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->gm.Av);
   cudaFree(ctx->gm.diag);
   cudaFree(ctx->gm.y);
+  cudaFree(ctx->phys.buf);
+  cudaFree(ctx->phys.grid);
+  cudaFree(ctx->phys.state);
   cudaFree(ctx->gm.xr);
   cudaFree(ctx->gm.rr);
   cudaFree(ctx->gm.dr);
@@ -139,6 +168,8 @@ int shbim_set_R(shbim_ctx* ctx, double R) {
 
 int64_t shbim_launch_count(shbim_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+int64_t shbim_operator_applications(shbim_ctx* ctx) { return ctx ? ctx->applications : -1; }
+
 int shbim_sizes(shbim_ctx* ctx, int64_t* nc, int64_t* nt, int64_t* ns) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (nc) *nc = ctx->ncoef;
@@ -158,6 +189,13 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
   }
   cudaStream_t s = (cudaStream_t)stream;
   SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  bool same = ctx->n_drops == n_drops;
+  for (int i = 0; same && i < n_drops; ++i) same = ctx->drops[i].p == p_host[i];
+  if (same) {
+    // same layout: keep every allocation, refresh the shape-dependent state only
+    for (int i = 0; i < n_drops; ++i) ctx->drops[i].lam = lambda_host ? lambda_host[i] : 1.0;
+    return rebuild_geometry(ctx, xcoef_dev, s);
+  }
   free_drop_state(ctx);
   int rc;
   // tables per distinct degree (kept across calls)
@@ -192,14 +230,6 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
   ctx->ncoef = co;
   ctx->ntarget = to;
   ctx->nsource = so;
-  // centres: the mean position over the parameter sphere, x_00 / sqrt(4 pi)
-  for (auto& d : ctx->drops) {
-    double c00[3];
-    for (int c = 0; c < 3; ++c)
-      SHBIM_CUDA(ctx, cudaMemcpy(&c00[c], xcoef_dev + 3 * d.coef_off + (int64_t)c * d.nc,
-                                 sizeof(double), cudaMemcpyDeviceToHost));
-    for (int c = 0; c < 3; ++c) d.centre[c] = c00[c] / std::sqrt(4.0 * kPi);
-  }
   // geometry and workspaces
   if ((rc = dalloc(ctx, &ctx->geo.tgt, 7 * (size_t)to, "targets")) ||
       (rc = dalloc(ctx, &ctx->geo.src, 7 * (size_t)so, "sources")) ||
@@ -208,7 +238,8 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
       (rc = dalloc(ctx, &ctx->geo.tgt_drop, (size_t)to, "target drop ids")) ||
       (rc = dalloc(ctx, &ctx->dens_up, 6 * (size_t)so, "source strengths")) ||
       (rc = dalloc(ctx, &ctx->dens_up32, 6 * (size_t)so, "source strengths32")) ||
-      (rc = dalloc(ctx, &ctx->grid_out, 3 * (size_t)to, "target values")))
+      (rc = dalloc(ctx, &ctx->grid_out, 3 * (size_t)to, "target values")) ||
+      (rc = dalloc(ctx, &ctx->xup, 3 * (size_t)kNumTab * so, "position derivatives")))
     return rc;
   for (auto& d : ctx->drops) {
     if ((rc = dalloc(ctx, &d.rows_lap, (size_t)d.nt * kNumLap * d.nc, "laplace rows")) ||
@@ -221,14 +252,7 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
       std::fill(tdrop.begin() + ctx->drops[i].tgt_off,
                 tdrop.begin() + ctx->drops[i].tgt_off + ctx->drops[i].nt, i);
     SHBIM_CUDA(ctx, cudaMemcpy(ctx->geo.tgt_drop, tdrop.data(), to * sizeof(int), cudaMemcpyHostToDevice));
-    std::vector<DropDev> dd(n_drops);
-    for (int i = 0; i < n_drops; ++i) {
-      const Drop& d = ctx->drops[i];
-      dd[i] = DropDev{d.p, d.q, d.nt, d.ns, d.nc, d.coef_off, d.tgt_off, d.src_off, d.lam,
-                      d.centre[0], d.centre[1], d.centre[2], d.rows_lap, d.rows_sto};
-    }
     if ((rc = dalloc(ctx, &ctx->drops_dev, n_drops, "drop table"))) return rc;
-    SHBIM_CUDA(ctx, cudaMemcpy(ctx->drops_dev, dd.data(), n_drops * sizeof(DropDev), cudaMemcpyHostToDevice));
   }
   // all-pairs tiling: tiles never cross a drop; sources split so that the grid fills the GPU
   {
@@ -252,9 +276,7 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
                                cudaMemcpyHostToDevice));
     if ((rc = dalloc(ctx, &ctx->part, (size_t)ctx->pair_splits * 3 * to, "pair partials"))) return rc;
   }
-  if ((rc = build_geometry(ctx, xcoef_dev, s))) return rc;
-  if ((rc = build_singular_rows(ctx, xcoef_dev, s))) return rc;
-  return SHBIM_OK;
+  return rebuild_geometry(ctx, xcoef_dev, s);
 }
 
 int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream) {
@@ -291,6 +313,7 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   cudaStream_t s = (cudaStream_t)stream;
   const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
   int rc;
+  ctx->applications++;
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {
@@ -330,6 +353,7 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
   const int64_t NS = ctx->nsource;
   int rc;
+  ctx->applications++;
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {

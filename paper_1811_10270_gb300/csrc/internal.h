@@ -26,10 +26,19 @@ inline int npts(int q) { return (q + 1) * (2 * q + 2); }
 constexpr int kNumLap = 2;        // 0: double layer (target normal), 1: single layer
 constexpr int kNumSto = 12;       // 0..5 Stokeslet xx,xy,xz,yy,yz,zz ; 6..11 stresslet (same order)
 
+// Legendre tables per latitude (kinds of the synthesis). "phi-type" tables multiply the
+// sin/cos-swapped Fourier sum (a phi derivative); the others the plain one.
+constexpr int kNumTab = 7;
+//   0 Pbar            1 dPbar/dtheta        2 m Pbar / sin (phi-type)
+//   3 d2Pbar/dtheta2  4 m dPbar/dtheta (phi-type)   5 -m^2 Pbar   6 m Pbar (phi-type)
+// so that kinds 0,1,2 give f, f_theta, f_phi / sin and kinds 0,1,6,3,4,5 give f, f_theta,
+// f_phi, f_theta_theta, f_theta_phi, f_phi_phi.
+constexpr int kPhiTypeMask = (1 << 2) | (1 << 4) | (1 << 6);
+
 // Transform tables of one (p, grid degree q) pair, device memory.
 struct GridTables {
   int p = 0, q = 0;
-  double* alf = nullptr;     // [q+1][3][ntri(p)] m-major: Pbar, dPbar/dtheta, m Pbar / sin
+  double* alf = nullptr;     // [q+1][kNumTab][ntri(p)] m-major (see kNumTab)
   double* omega = nullptr;   // [q+1] regular weight (pi/(q+1)) w_j^G
   double* mu = nullptr;      // [q+1] modified weight omega_j 2 sin(theta_j/2) sum_{n<=q} P_n(t_j)
   double* trig = nullptr;    // [2][2q+2] cos, sin of 2 pi k / (2q+2)
@@ -107,6 +116,7 @@ struct shbim_ctx {
   float* dens_up32 = nullptr;     // [3][nsource] source strengths (FP32)
   double* part = nullptr;         // [pair_splits][3][ntarget] partial sums
   double* grid_out = nullptr;     // [3][ntarget] operator values before projection
+  double* xup = nullptr;          // per drop [3][kNumTab][ns]: position and derivatives on the up grid
   double* sht_scratch = nullptr;  // Fourier stage of forward transforms
   size_t sht_scratch_elems = 0;
   // singular-row build workspace
@@ -140,7 +150,17 @@ struct shbim_ctx {
     double resid = 1.0;
     int64_t cap = 0;
   } gm;
+  // physics workspaces (forces, rates, step state)
+  struct Phys {
+    double* buf = nullptr;
+    size_t cap = 0;
+    double* grid = nullptr;
+    size_t grid_cap = 0;
+    double* state = nullptr;
+    size_t state_cap = 0;
+  } phys;
   int64_t launches = 0;
+  int64_t applications = 0;
   // optional per-class kernel timing
   bool timing = false;
   struct TimedRange {
@@ -209,6 +229,9 @@ int build_singular_rows(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s)
 int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
 int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out,
                       cudaStream_t s);
+
+// ---- shape-dependent state for an unchanged layout (api.cu)
+int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 
 // ---- all-pairs sums (pairs.cu)
 int pairs_laplace(shbim_ctx* ctx, int which, double* out_accum, cudaStream_t s);

@@ -1,0 +1,340 @@
+// Forces, surfactant rate and the midpoint time step (Section 2 steps i-viii, Algorithm 1).
+//
+// rates(): for the current drop shapes and a surfactant distribution Gamma,
+//   (i)   solve the electric system for E_n (Eq. galerkin_En);
+//   (ii)  phi_q = S_L[q] with the charge q = (1 - 1/R) E_n (jump of E_n, Eq. EneEni);
+//   (iii) on each drop's upsampled grid: E_t = -grad_S(phi_inf + phi_q) (Eq. E_t),
+//   (iv)  electric traction f^E (Eq. el_force, eps = 1),
+//   (v)   Langmuir tension normalised to gamma(1) = 1 (Eq. langmuir) and the interfacial force
+//         f = 2 gamma H n - grad_S gamma (Eq. interfacial_force), H = 1/2 div_S n;
+//   then projects f/Ca_E - f^E to degree p (de-aliasing: products formed on the 2p+1 grid),
+//   (vi)  solves the Stokes system with right-hand side -sum_j S_j[f/Ca_E - f^E] (Eq. main_eq),
+//   and forms the surfactant rate -Gamma div_S u for nodes moving with u (Eq. surfactant0 in
+//   material form, no diffusion), projected to degree p.
+// step(): midpoint rule for x with the explicit IMEX stage for Gamma (Algorithm 1):
+//   half step with the rates at t, full step with the rates at t + dt/2; the error estimate is
+//   dt times the grid max-norm of the difference between the two rates (the distance between
+//   the midpoint and the explicit Euler step).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace shbim {
+
+int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
+                     int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
+                     double alpha, float* out32, cudaStream_t s);
+
+namespace {
+
+struct PhysDev {
+  double R, Q, Ca_E, beta, x_s, eu0, eu1, eu2, eq, lnorm;
+};
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+// position derivatives of node i on the upsampled grid (xup layout [c][kind][ns])
+struct Frame {
+  double x[3], xt[3], xp[3], n[3];
+  double E, F, G, det, H;
+};
+
+__device__ __forceinline__ Frame frame_at(const double* __restrict__ xup, int64_t ns, int64_t i) {
+  Frame f;
+  double xtt[3], xtp[3], xpp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double* b = xup + (int64_t)c * kNumTab * ns;
+    f.x[c] = b[i];
+    f.xt[c] = b[ns + i];
+    xtt[c] = b[3 * ns + i];
+    xtp[c] = b[4 * ns + i];
+    xpp[c] = b[5 * ns + i];
+    f.xp[c] = b[6 * ns + i];
+  }
+  const double c0 = f.xt[1] * f.xp[2] - f.xt[2] * f.xp[1];
+  const double c1 = f.xt[2] * f.xp[0] - f.xt[0] * f.xp[2];
+  const double c2 = f.xt[0] * f.xp[1] - f.xt[1] * f.xp[0];
+  const double W = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+  f.n[0] = c0 / W;
+  f.n[1] = c1 / W;
+  f.n[2] = c2 / W;
+  f.E = f.xt[0] * f.xt[0] + f.xt[1] * f.xt[1] + f.xt[2] * f.xt[2];
+  f.F = f.xt[0] * f.xp[0] + f.xt[1] * f.xp[1] + f.xt[2] * f.xp[2];
+  f.G = f.xp[0] * f.xp[0] + f.xp[1] * f.xp[1] + f.xp[2] * f.xp[2];
+  f.det = f.E * f.G - f.F * f.F;
+  const double L = xtt[0] * f.n[0] + xtt[1] * f.n[1] + xtt[2] * f.n[2];
+  const double M = xtp[0] * f.n[0] + xtp[1] * f.n[1] + xtp[2] * f.n[2];
+  const double N = xpp[0] * f.n[0] + xpp[1] * f.n[1] + xpp[2] * f.n[2];
+  f.H = -(f.E * N - 2.0 * f.F * M + f.G * L) / (2.0 * f.det);
+  return f;
+}
+
+// surface gradient of a scalar from its theta / phi derivatives
+__device__ __forceinline__ void surf_grad(const Frame& f, double dt_, double dp, double* g) {
+  const double a = (f.G * dt_ - f.F * dp) / f.det;
+  const double b = (f.E * dp - f.F * dt_) / f.det;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) g[c] = a * f.xt[c] + b * f.xp[c];
+}
+
+// fields [6][ns]: E_n, phi_theta, phi_phi, Gamma, Gamma_theta, Gamma_phi -> out [3][ns]
+__global__ void k_traction(const double* __restrict__ xup, int64_t ns, const double* __restrict__ fl,
+                           int64_t fstride, PhysDev P, double* __restrict__ out, int64_t ostride) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  const Frame f = frame_at(xup, ns, i);
+  const double En = fl[i], pt = fl[fstride + i], pp = fl[2 * fstride + i];
+  const double Gm = fl[3 * fstride + i], Gt = fl[4 * fstride + i], Gp = fl[5 * fstride + i];
+  double gphi[3], gG[3];
+  surf_grad(f, pt, pp, gphi);
+  surf_grad(f, Gt, Gp, gG);
+  const double Ei[3] = {P.eu0 + P.eq * f.x[0], P.eu1 - P.eq * f.x[1], P.eu2};
+  const double Ein = Ei[0] * f.n[0] + Ei[1] * f.n[1] + Ei[2] * f.n[2];
+  double Et[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) Et[c] = Ei[c] - Ein * f.n[c] - gphi[c];
+  const double Et2 = Et[0] * Et[0] + Et[1] * Et[1] + Et[2] * Et[2];
+  const double fn = 0.5 * ((1.0 - P.Q / (P.R * P.R)) * En * En - (1.0 - P.Q) * Et2);
+  const double ft = (1.0 - P.Q / P.R) * En;
+  const double gam = (1.0 + P.beta * log(1.0 - P.x_s * Gm)) / P.lnorm;
+  const double dgam = (-P.beta * P.x_s / (1.0 - P.x_s * Gm)) / P.lnorm;
+  const double inv_ca = 1.0 / P.Ca_E;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double fI = 2.0 * gam * f.H * f.n[c] - dgam * gG[c];
+    const double fE = fn * f.n[c] + ft * Et[c];
+    out[c * ostride + i] = fI * inv_ca - fE;
+  }
+}
+
+// uf [3 comps][2 kinds: theta, phi][ustride], Gamma value -> -Gamma div_S u
+__global__ void k_surf_rate(const double* __restrict__ xup, int64_t ns, const double* __restrict__ uf,
+                            int64_t ustride, const double* __restrict__ Gm, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  const Frame f = frame_at(xup, ns, i);
+  double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double ut = uf[(2 * k) * ustride + i], up = uf[(2 * k + 1) * ustride + i];
+    a += ut * f.xt[k];
+    b += ut * f.xp[k];
+    c += up * f.xt[k];
+    d += up * f.xp[k];
+  }
+  const double div = (f.G * a - f.F * (b + c) + f.E * d) / f.det;
+  out[i] = -Gm[i] * div;
+}
+
+__global__ void k_lincomb(double* __restrict__ y, const double* __restrict__ a, double alpha,
+                          const double* __restrict__ b, double beta, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = alpha * a[e] + beta * b[e];
+}
+
+// max over nodes of the Euclidean norm of ncomp fields [ncomp][stride] -> atomic max (bits)
+__global__ void k_maxnorm(const double* __restrict__ v, int64_t n, int ncomp, int64_t stride,
+                          unsigned long long* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (i < n) {
+    for (int c = 0; c < ncomp; ++c) s += v[c * stride + i] * v[c * stride + i];
+    s = sqrt(s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0 && s > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+int ensure_buf(shbim_ctx* ctx, double** p, size_t* cap, size_t need) {
+  if (need <= *cap) return SHBIM_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need * sizeof(double)) != cudaSuccess)
+    return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc physics workspace");
+  *cap = need;
+  return SHBIM_OK;
+}
+
+int solve(shbim_ctx* ctx, int sys, const double* rhs, double* x, double inner_tol, int* iters,
+          cudaStream_t s) {
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
+    int inner = 0, outer = 0;
+    int rc = shbim_gmres_solve_refined(ctx, sys, rhs, nullptr, x, inner_tol, 20, &inner, &outer, nullptr, s);
+    if (iters) *iters = inner;
+    return rc;
+  }
+  return shbim_gmres_solve(ctx, sys, rhs, nullptr, x, iters, nullptr, s);
+}
+
+}  // namespace
+
+int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, double* gE, int* it_e,
+          int* it_s, cudaStream_t s) {
+  const int64_t n = ctx->ncoef, NS = ctx->nsource;
+  auto& W = ctx->phys;
+  int rc;
+  const size_t need = (size_t)(4 * n + 6 * n) + (size_t)(6 + 3 + 6 + 1) * NS;
+  if ((rc = ensure_buf(ctx, &W.buf, &W.cap, need))) return rc;
+  double* rhs_e = W.buf;
+  double* En = rhs_e + n;
+  double* q = En + n;
+  double* phi = q + n;
+  double* tco = phi + n;       // 3n
+  double* rhs_s = tco + 3 * n;  // 3n
+  double* fl = rhs_s + 3 * n;   // 6 NS
+  double* tv = fl + 6 * NS;     // 3 NS
+  double* uf = tv + 3 * NS;     // 6 NS
+  double* gv = uf + 6 * NS;     // NS
+  const double R = ph.R;
+  ctx->opts.R = R;
+  // (i) E_n
+  if ((rc = shbim_electric_rhs(ctx, ph.E_u, ph.E_q, rhs_e, s))) return rc;
+  if ((rc = solve(ctx, SHBIM_SYS_ELECTRIC, rhs_e, En, ph.inner_tol, it_e, s))) return rc;
+  // (ii) phi_q = S_L[(1 - 1/R) E_n]
+  k_lincomb<<<nb(n), 256, 0, s>>>(q, En, 1.0 - 1.0 / R, En, 0.0, n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  // one-shot applications (not iterated by GMRES) always use FP64 sums: in mixed precision only
+  // the operator inside the inner GMRES runs in FP32
+  const int saved_prec = ctx->opts.precision;
+  ctx->opts.precision = SHBIM_PREC_FP64;
+  rc = shbim_eval_electric(ctx, SHBIM_LAPLACE_SL, q, phi, SHBIM_OUT_COEF, s);
+  ctx->opts.precision = saved_prec;
+  if (rc) return rc;
+  // (iii)-(v) traction on every drop's upsampled grid, projected to degree p
+  PhysDev P{ph.R, ph.Q, ph.Ca_E, ph.beta, ph.x_s, ph.E_u[0], ph.E_u[1], ph.E_u[2], ph.E_q,
+            1.0 + ph.beta * std::log(1.0 - ph.x_s)};
+  for (auto& d : ctx->drops) {
+    const GridTables& g = d.tab->up;
+    const int64_t o = d.src_off;
+    if ((rc = sht_synth(ctx, g, 1, En + d.coef_off, d.nc, 1 << 0, fl + o, 0, NS, nullptr, nullptr, s)) ||
+        (rc = sht_synth(ctx, g, 1, phi + d.coef_off, d.nc, (1 << 1) | (1 << 6), fl + NS + o, 0, NS, nullptr,
+                        nullptr, s)) ||
+        (rc = sht_synth(ctx, g, 1, gamma + d.coef_off, d.nc, (1 << 0) | (1 << 1) | (1 << 6), fl + 3 * NS + o, 0,
+                        NS, nullptr, nullptr, s)))
+      return rc;
+    k_traction<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, fl + o, NS, P, tv + o, NS);
+    SHBIM_CHECK_LAUNCH(ctx, "k_traction");
+    if ((rc = sht_analysis(ctx, g, 3, tv + o, NS, true, tco + 3 * d.coef_off, d.nc, s))) return rc;
+  }
+  // (vi) Stokes: (lam_i+1) u - sum (lam_j-1) D_j[u] = -sum_j S_j[f/Ca_E - f^E]
+  ctx->opts.precision = SHBIM_PREC_FP64;
+  rc = shbim_eval_stokes(ctx, tco, nullptr, rhs_s, SHBIM_OUT_COEF, s);
+  ctx->opts.precision = saved_prec;
+  if (rc) return rc;
+  k_lincomb<<<nb(3 * n), 256, 0, s>>>(rhs_s, rhs_s, -1.0, rhs_s, 0.0, 3 * n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  if ((rc = solve(ctx, SHBIM_SYS_STOKES, rhs_s, u, ph.inner_tol, it_s, s))) return rc;
+  // surfactant rate -Gamma div_S u, projected to degree p
+  for (auto& d : ctx->drops) {
+    const GridTables& g = d.tab->up;
+    const int64_t o = d.src_off;
+    if ((rc = sht_synth(ctx, g, 3, u + 3 * d.coef_off, d.nc, (1 << 1) | (1 << 6), uf + o, 2 * NS, NS, nullptr,
+                        nullptr, s)))
+      return rc;
+    k_surf_rate<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, uf + o, NS, fl + 3 * NS + o, gv + o);
+    SHBIM_CHECK_LAUNCH(ctx, "k_surf_rate");
+    if ((rc = sht_analysis(ctx, g, 1, gv + o, NS, true, gE + d.coef_off, d.nc, s))) return rc;
+  }
+  return SHBIM_OK;
+}
+
+int rebuild_geometry(shbim_ctx* ctx, const double* xcoef, cudaStream_t s);
+
+int grid_maxnorm(shbim_ctx* ctx, const double* coef, int ncomp, double* out_host, cudaStream_t s) {
+  auto& W = ctx->phys;
+  int rc;
+  const size_t need = (size_t)3 * ctx->ntarget + 1;
+  if ((rc = ensure_buf(ctx, &W.grid, &W.grid_cap, need))) return rc;
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(W.grid + 3 * ctx->ntarget);
+  SHBIM_CUDA(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+  for (auto& d : ctx->drops) {
+    const int64_t cstride = (int64_t)ncomp == 3 ? 3 * d.coef_off : d.coef_off;
+    if ((rc = sht_synth(ctx, d.tab->base, ncomp, coef + cstride, d.nc, 1, W.grid, d.nt, 0, nullptr, nullptr, s)))
+      return rc;
+    k_maxnorm<<<nb(d.nt), 256, 0, s>>>(W.grid, d.nt, ncomp, d.nt, mx);
+    SHBIM_CHECK_LAUNCH(ctx, "k_maxnorm");
+  }
+  unsigned long long h = 0;
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(&h, mx, sizeof(h), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  double v;
+  std::memcpy(&v, &h, sizeof(v));
+  *out_host = v;
+  return SHBIM_OK;
+}
+
+}  // namespace shbim
+
+using namespace shbim;
+
+extern "C" {
+
+int shbim_rates(shbim_ctx* ctx, const shbim_phys* ph, const double* gamma_dev, double* u_dev, double* gE_dev,
+                int* iters_host, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (!ph || !gamma_dev || !u_dev || !gE_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  if (!(ph->R > 0.0) || !(ph->Ca_E > 0.0) || ph->beta < 0.0 || !(ph->x_s >= 0.0 && ph->x_s < 1.0) ||
+      !(ph->inner_tol > 0.0 && ph->inner_tol < 1.0))
+    return fail(ctx, SHBIM_ERR_ARG, "bad physical parameters");
+  int ie = 0, is = 0;
+  int rc = rates(ctx, *ph, gamma_dev, u_dev, gE_dev, &ie, &is, (cudaStream_t)stream);
+  if (iters_host) {
+    iters_host[0] = ie;
+    iters_host[1] = is;
+  }
+  return rc;
+}
+
+int shbim_step(shbim_ctx* ctx, const shbim_phys* ph, const double* x_dev, const double* gamma_dev, double dt,
+               double* x_out_dev, double* gamma_out_dev, double* err_host, int* iters_host, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (!ph || !x_dev || !gamma_dev || !x_out_dev || !gamma_out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SHBIM_ERR_ARG, "dt must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = ctx->ncoef;
+  auto& W = ctx->phys;
+  int rc;
+  if ((rc = ensure_buf(ctx, &W.state, &W.state_cap, (size_t)12 * n))) return rc;
+  double* u0 = W.state;
+  double* g0 = u0 + 3 * n;
+  double* u1 = g0 + n;
+  double* g1 = u1 + 3 * n;
+  double* xh = g1 + n;  // 3n
+  // the half-step surfactant shares the last n entries with nothing else
+  double* gh = W.state + 11 * n;
+  int its[4] = {0, 0, 0, 0};
+  if ((rc = rebuild_geometry(ctx, x_dev, s))) return rc;
+  if ((rc = rates(ctx, *ph, gamma_dev, u0, g0, &its[0], &its[1], s))) return rc;
+  k_lincomb<<<nb(3 * n), 256, 0, s>>>(xh, x_dev, 1.0, u0, 0.5 * dt, 3 * n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  k_lincomb<<<nb(n), 256, 0, s>>>(gh, gamma_dev, 1.0, g0, 0.5 * dt, n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  if ((rc = rebuild_geometry(ctx, xh, s))) return rc;
+  if ((rc = rates(ctx, *ph, gh, u1, g1, &its[2], &its[3], s))) return rc;
+  k_lincomb<<<nb(3 * n), 256, 0, s>>>(x_out_dev, x_dev, 1.0, u1, dt, 3 * n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  k_lincomb<<<nb(n), 256, 0, s>>>(gamma_out_dev, gamma_dev, 1.0, g1, dt, n);
+  SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  if (err_host) {
+    // err = dt * max(max |u1 - u0|, max |g1 - g0|) on the degree-p grids
+    k_lincomb<<<nb(3 * n), 256, 0, s>>>(u0, u1, 1.0, u0, -1.0, 3 * n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+    k_lincomb<<<nb(n), 256, 0, s>>>(g0, g1, 1.0, g0, -1.0, n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+    double eu = 0.0, eg = 0.0;
+    if ((rc = grid_maxnorm(ctx, u0, 3, &eu, s)) || (rc = grid_maxnorm(ctx, g0, 1, &eg, s))) return rc;
+    *err_host = dt * std::max(eu, eg);
+  }
+  if (iters_host)
+    for (int k = 0; k < 4; ++k) iters_host[k] = its[k];
+  return SHBIM_OK;
+}
+
+}  // extern "C"

@@ -17,7 +17,7 @@ __device__ __forceinline__ int tri_off_d(int p, int m) { return m * (p + 1) - m 
 // kinds bitmask -> table index of the slot-th set bit
 __device__ __forceinline__ int kind_of_slot(int kinds, int slot) {
   int k = 0;
-  for (int b = 0; b < 3; ++b) {
+  for (int b = 0; b < kNumTab; ++b) {
     if (kinds & (1 << b)) {
       if (k == slot) return b;
       ++k;
@@ -45,7 +45,7 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
   }
   const double* c = coef + (int64_t)item * coef_stride;
   const int nt = (p + 1) * (p + 2) / 2;
-  const double* T = alf + (int64_t)j * 3 * nt;
+  const double* T = alf + (int64_t)j * kNumTab * nt;
   const int ntask = nk * 2 * P1;
   for (int task = threadIdx.x; task < ntask; task += blockDim.x) {
     const int slot = task / (2 * P1);
@@ -71,7 +71,7 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
       const int kind = kind_of_slot(kinds, slot);
       const double* Ac = A + (slot * 2) * P1;
       const double* As = Ac + P1;
-      if (kind != 2)
+      if (!((kPhiTypeMask >> kind) & 1))
         synth4(Ac, As, Ac[0], 1.0, p, k, N, tc, ts, V + slot * N);
       else
         synth4(As, Ac, 0.0, -1.0, p, k, N, tc, ts, V + slot * N);
@@ -98,7 +98,7 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
       const double* As = Ac + P1;
       double v = 0.0;
       int id = 0;
-      if (kind != 2) {
+      if (!((kPhiTypeMask >> kind) & 1)) {
         for (int m = 1; m <= p; ++m) {
           id += k;
           if (id >= N) id -= N;
@@ -275,7 +275,7 @@ __global__ void k_analysis_legendre(const double* __restrict__ F, int p, int q,
   const double* Fi = F + (int64_t)item * (q + 1) * 2 * P1;
   double ac = 0.0, as = 0.0;
   for (int j = 0; j <= q; ++j) {
-    const double a = alf[(int64_t)j * 3 * nt + o];
+    const double a = alf[(int64_t)j * kNumTab * nt + o];
     ac = fma(Fi[(int64_t)j * 2 * P1 + m], a, ac);
     as = fma(Fi[(int64_t)j * 2 * P1 + P1 + m], a, as);
   }

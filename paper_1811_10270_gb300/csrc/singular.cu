@@ -27,17 +27,19 @@
 
 namespace shbim {
 
-__global__ void k_geometry(const double* __restrict__ tmp, int n, int N, const double* __restrict__ omega,
-                           int weighted, double* __restrict__ out, int64_t ld, int64_t off,
-                           float* __restrict__ out32, double cx, double cy, double cz) {
+// tmp[c * nkind * n + slot * n + i]: slots 0, 1, 2 = x, x_theta, x_phi / sin
+__global__ void k_geometry(const double* __restrict__ tmp, int n, int nkind, int N,
+                           const double* __restrict__ omega, int weighted, double* __restrict__ out,
+                           int64_t ld, int64_t off, float* __restrict__ out32, double cx, double cy,
+                           double cz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double X[3], Xt[3], Xp[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    X[c] = tmp[(int64_t)(c * 3 + 0) * n + i];
-    Xt[c] = tmp[(int64_t)(c * 3 + 1) * n + i];
-    Xp[c] = tmp[(int64_t)(c * 3 + 2) * n + i];
+    X[c] = tmp[(int64_t)(c * nkind + 0) * n + i];
+    Xt[c] = tmp[(int64_t)(c * nkind + 1) * n + i];
+    Xp[c] = tmp[(int64_t)(c * nkind + 2) * n + i];
   }
   const double c0 = Xt[1] * Xp[2] - Xt[2] * Xp[1];
   const double c1 = Xt[2] * Xp[0] - Xt[0] * Xp[2];
@@ -58,7 +60,7 @@ __global__ void k_geometry(const double* __restrict__ tmp, int n, int N, const d
 int build_geometry(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
   // scratch for the 9 synthesised fields of the largest grid
   int64_t maxn = 0;
-  for (auto& d : ctx->drops) maxn = std::max<int64_t>(maxn, d.ns);
+  for (auto& d : ctx->drops) maxn = std::max<int64_t>(maxn, d.nt);
   double* tmp = nullptr;
   if (cudaMalloc(&tmp, (size_t)9 * maxn * sizeof(double)) != cudaSuccess)
     return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc geometry scratch");
@@ -68,14 +70,17 @@ int build_geometry(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
     for (int pass = 0; pass < 2 && rc == SHBIM_OK; ++pass) {
       const GridTables& g = pass == 0 ? d.tab->base : d.tab->up;
       const int n = npts(g.q);
-      rc = sht_synth(ctx, g, 3, xc, d.nc, 7, tmp, 3 * (int64_t)n, n, nullptr, nullptr, s);
+      // targets: x, x_theta, x_phi/sin into scratch; sources: all derivative kinds kept in xup
+      const int nkind = pass == 0 ? 3 : kNumTab;
+      double* buf = pass == 0 ? tmp : ctx->xup + 3 * kNumTab * d.src_off;
+      rc = sht_synth(ctx, g, 3, xc, d.nc, (1 << nkind) - 1, buf, (int64_t)nkind * n, n, nullptr, nullptr, s);
       if (rc) break;
       double* out = pass == 0 ? ctx->geo.tgt : ctx->geo.src;
       float* out32 = pass == 0 ? ctx->geo.tgt32 : ctx->geo.src32;
       const int64_t ld = pass == 0 ? ctx->ntarget : ctx->nsource;
       const int64_t off = pass == 0 ? d.tgt_off : d.src_off;
-      k_geometry<<<(n + 127) / 128, 128, 0, s>>>(tmp, n, 2 * g.q + 2, g.omega, pass == 1 ? 1 : 0, out,
-                                                 ld, off, out32, d.centre[0], d.centre[1],
+      k_geometry<<<(n + 127) / 128, 128, 0, s>>>(buf, n, nkind, 2 * g.q + 2, g.omega, pass == 1 ? 1 : 0,
+                                                 out, ld, off, out32, d.centre[0], d.centre[1],
                                                  d.centre[2]);
       ctx->launches++;
       cudaError_t e = cudaGetLastError();
@@ -227,7 +232,7 @@ __global__ void k_self_weights(const double* __restrict__ rot, int p, int q,
     tc[i] = trig[i];
     ts[i] = trig[N + i];
   }
-  const double* T = alf + (int64_t)j * 3 * nt;
+  const double* T = alf + (int64_t)j * kNumTab * nt;
   const double* cf = rot + (int64_t)t * 3 * nc;
   for (int task = threadIdx.x; task < 18 * P1; task += blockDim.x) {
     const int fk = task / (2 * P1);      // f * 3 + kind

@@ -3,9 +3,10 @@
 // * Gauss-Legendre nodes and weights (Newton on P_N) for the latitudes of the Gaussian grid
 //   (Section 3, Eq. spharm_ex).
 // * Normalised associated Legendre functions with the Condon-Shortley phase
-//   (Eqs. normalized_spharm, pneg) and the two derivative tables the transforms need,
-//   d/dtheta Pbar_n^m = (n t Pbar_n^m - sqrt((2n+1)/(2n-1) (n^2-m^2)) Pbar_{n-1}^m) / sin
-//   and m Pbar_n^m / sin, tabulated at the grid latitudes (never at a pole).
+//   (Eqs. normalized_spharm, pneg) and the derivative tables the transforms need,
+//   d/dtheta Pbar_n^m = (n t Pbar_n^m - sqrt((2n+1)/(2n-1) (n^2-m^2)) Pbar_{n-1}^m) / sin,
+//   the second derivative from the associated Legendre equation, and the m / m^2 factors of
+//   the phi derivatives, tabulated at the grid latitudes (never at a pole).
 // * Regular weights omega_j = (pi/(q+1)) w_j^G (Eq. reg_quadrature with the 2q+2 point
 //   trapezoid spacing) and modified weights mu_j = omega_j 2 sin(theta_j/2) sum_{n<=q} P_n(t_j)
 //   (Eq. mod_weights on the degree-q grid).
@@ -87,7 +88,7 @@ int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g) {
   std::vector<double> t, wg;
   gauss_legendre(q + 1, t, wg);
   const int nt = ntri(p);
-  std::vector<double> alf((size_t)(q + 1) * 3 * nt);
+  std::vector<double> alf((size_t)(q + 1) * kNumTab * nt);
   std::vector<double> om(q + 1), mu(q + 1), th(q + 1);
   std::vector<double> P(nt);
   for (int j = 0; j <= q; ++j) {
@@ -95,16 +96,22 @@ int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g) {
     double sj = std::sqrt((1.0 - tj) * (1.0 + tj));
     th[j] = std::acos(tj);
     alf_values(p, tj, sj, P.data());
-    double* A = &alf[(size_t)j * 3 * nt];
+    double* A = &alf[(size_t)j * kNumTab * nt];
     for (int m = 0; m <= p; ++m) {
       for (int n = m; n <= p; ++n) {
         int o = tri_off(p, m) + (n - m);
         double v = P[o];
         double prev = (n - 1 >= m) ? P[o - 1] : 0.0;
         double c = std::sqrt((2.0 * n + 1.0) / (2.0 * n - 1.0) * ((double)n * n - (double)m * m));
+        const double d1 = (n * tj * v - (n > 0 ? c * prev : 0.0)) / sj;
         A[o] = v;
-        A[nt + o] = (n * tj * v - (n > 0 ? c * prev : 0.0)) / sj;
+        A[nt + o] = d1;
         A[2 * nt + o] = m * v / sj;
+        // associated Legendre equation in theta: P'' = -cot P' - (n(n+1) - m^2/sin^2) P
+        A[3 * nt + o] = -(tj / sj) * d1 - (n * (n + 1.0) - (double)m * m / (sj * sj)) * v;
+        A[4 * nt + o] = m * d1;
+        A[5 * nt + o] = -(double)m * m * v;
+        A[6 * nt + o] = m * v;
       }
     }
     om[j] = kPi / (q + 1) * wg[j];

@@ -1,0 +1,138 @@
+"""Parity of the forces, rates and time step (Section 2, Algorithm 1) with the FP64 oracle."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import physics as P, sh
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return max(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300),
+               np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_10270_gb300 as pkg
+    if not os.path.exists(pkg.LIB_PATH):
+        from paper_1811_10270_gb300 import build
+        build.build()
+    pkg.lib()
+    return pkg
+
+
+def T(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def two_drops(p=6, seed=2, gap=0.4):
+    cfg = inputs.config2(p=p, seed=seed, gap=gap)
+    cfg.drops[1].lam = 0.5
+    return cfg
+
+
+def setup(S, cfg, precision, tol=1e-13):
+    ctx = S.Context(precision=precision, R=cfg.R, gmres_tol=tol)
+    x = T(np.concatenate([d.xcoef.ravel() for d in cfg.drops]))
+    ctx.set_drops([d.p for d in cfg.drops], x, [d.lam for d in cfg.drops])
+    g = T(np.concatenate([d.gamma_coef for d in cfg.drops]))
+    return ctx, x, g
+
+
+def test_initial_deformation_rate_of_a_sphere_on_gpu(S):
+    """dD/dt = D_T / tau_D for a clean spherical drop (see the oracle pin), through shbim_rates."""
+    p, R, Q = 10, 0.1, 1.0
+    cfg = inputs.config1(p)
+    ctx, x, g = setup(S, cfg, S.FP64)
+    u = torch.empty(3 * sh.ncoef(p), device="cuda", dtype=torch.float64)
+    gE = torch.empty(sh.ncoef(p), device="cuda", dtype=torch.float64)
+    ctx.rates(S.phys(R=R, Q=Q, beta=0.0), g, u, gE)
+    uv = sh.sht_inverse(u.cpu().numpy().reshape(3, -1), p, p)
+    th, ph = sh.grid_points(p)
+    n = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    ur = (uv * n).sum(0)
+    A = np.stack([np.ones_like(th), 0.5 * (3 * np.cos(th) ** 2 - 1)]).T
+    coef, *_ = np.linalg.lstsq(A, ur, rcond=None)
+    DT = 9 * (2 + 3 * R + 2 * R * R - 7 * Q) / (32 * (2 + R) ** 2)
+    tau = 35 * 5 / 80.0
+    assert abs(0.75 * coef[1] - DT / tau) < 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+def test_rates_match_oracle(S, precision, tol):
+    cfg = two_drops()
+    ps = [d.p for d in cfg.drops]
+    lams = [d.lam for d in cfg.drops]
+    prm = P.Params(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.2, 0.0, 1.0), gmres_tol=1e-13)
+    u_ref, g_ref = P.rates([d.xcoef for d in cfg.drops], [d.gamma_coef for d in cfg.drops], ps, lams, prm)
+    ctx, x, g = setup(S, cfg, precision)
+    nc = sum(sh.ncoef(p) for p in ps)
+    u = torch.empty(3 * nc, device="cuda", dtype=torch.float64)
+    gE = torch.empty(nc, device="cuda", dtype=torch.float64)
+    ctx.rates(S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.2, 0.0, 1.0), inner_tol=1e-6),
+              g, u, gE)
+    assert rel_err(u.cpu().numpy(), np.concatenate([a.ravel() for a in u_ref])) < tol
+    assert rel_err(gE.cpu().numpy(), np.concatenate(g_ref)) < tol
+    ctx.close()
+
+
+def test_step_matches_oracle(S):
+    cfg = two_drops(p=5, seed=4, gap=0.5)
+    ps = [d.p for d in cfg.drops]
+    lams = [d.lam for d in cfg.drops]
+    prm = P.Params(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.0, 1.0), gmres_tol=1e-13)
+    dt = 0.02
+    xn, gn, err, _ = P.step([d.xcoef for d in cfg.drops], [d.gamma_coef for d in cfg.drops], ps, lams, dt, prm)
+    ctx, x, g = setup(S, cfg, S.FP64)
+    xo = torch.empty_like(x)
+    go = torch.empty_like(g)
+    e, its = ctx.step(S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5), x, g, dt, xo, go)
+    assert rel_err(xo.cpu().numpy(), np.concatenate([a.ravel() for a in xn])) < TOL64
+    assert rel_err(go.cpu().numpy(), np.concatenate(gn)) < TOL64
+    assert abs(e - err) < 1e-9 * err
+    assert min(its) > 0
+    ctx.close()
+
+
+def test_adaptive_steps_conserve_surfactant(S):
+    """A few accepted steps with the paper's controller (accept if err < tol,
+    dt <- dt (0.9 tol/err)^(1/2)): surfactant mass drifts by far less than the tolerance."""
+    cfg = two_drops(p=6, seed=5, gap=0.4)
+    ps = [d.p for d in cfg.drops]
+    ctx, x, g = setup(S, cfg, S.FP32_COMP, tol=1e-10)
+    ph = S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5)
+    m0 = sum(P.surfactant_mass(d.xcoef, d.gamma_coef, d.p) for d in cfg.drops)
+    tol, dt, accepted = 1e-4, 0.01, 0
+    for _ in range(12):
+        xo, go = torch.empty_like(x), torch.empty_like(g)
+        err, _ = ctx.step(ph, x, g, dt, xo, go)
+        if err < tol:
+            x, g = xo, go
+            accepted += 1
+        dt = dt * math.sqrt(0.9 * tol / err)
+        if accepted >= 4:
+            break
+    assert accepted >= 4
+    xs = x.cpu().numpy()
+    gs = g.cpu().numpy()
+    off, m1 = 0, 0.0
+    for p in ps:
+        nc = sh.ncoef(p)
+        m1 += P.surfactant_mass(xs[3 * off:3 * off + 3 * nc].reshape(3, nc), gs[off:off + nc], p)
+        off += nc
+    assert abs(m1 - m0) / m0 < 1e-5
+    ctx.close()
