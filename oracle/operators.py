@@ -52,8 +52,18 @@ class DropGeom:
 
 
 class System:
-    def __init__(self, drops):
+    def __init__(self, drops, near: bool = False):
+        """near=True applies the nearly-singular correction of oracle.nearsing (drop j's
+        contribution at targets near S_j from the upsampled rule)."""
         self.drops = drops
+        self.near = near
+        self._pairs = None
+
+    def near_pairs(self):
+        from . import nearsing
+        if self._pairs is None:
+            self._pairs = nearsing.near_pairs(self)
+        return self._pairs
 
     # ---------------------------------------------------------------- Laplace
     def laplace_targets(self, kind: str, sigma, i: int, targets=None):
@@ -73,6 +83,9 @@ class System:
         return out
 
     def laplace_grid(self, kind: str, sigma):
+        if self.near:
+            from . import nearsing
+            return nearsing.corrected_laplace_grid(self, kind, sigma, self.near_pairs())
         return [self.laplace_targets(kind, sigma, i) for i in range(len(self.drops))]
 
     def laplace_coef(self, kind: str, sigma):
@@ -105,6 +118,9 @@ class System:
         return out
 
     def stokes_grid(self, f, u):
+        if self.near:
+            from . import nearsing
+            return nearsing.corrected_stokes_grid(self, f, u, self.near_pairs())
         return [self.stokes_targets(f, u, i) for i in range(len(self.drops))]
 
     def stokes_coef(self, f, u):

@@ -136,11 +136,12 @@ def far_field(x, prm: Params):
     return Eu + prm.E_q * np.stack([x[0], -x[1], np.zeros_like(x[2])])
 
 
-def rates(xcoefs, gcoefs, ps, lams, prm: Params, info=None):
+def rates(xcoefs, gcoefs, ps, lams, prm: Params, info=None, near: bool = True):
     """Velocity and surfactant-rate coefficients of every drop for one geometry
-    (steps i-vi of Section 2 and the explicit rate g_E of Algorithm 1)."""
+    (steps i-vi of Section 2 and the explicit rate g_E of Algorithm 1); near=True applies the
+    nearly-singular correction of oracle.nearsing to every layer operator."""
     drops = [operators.DropGeom(xc, p, lam) for xc, p, lam in zip(xcoefs, ps, lams)]
-    sysm = operators.System(drops)
+    sysm = operators.System(drops, near=near)
     R = prm.R
     # (i) E_n: 1/2 E_n - (R-1)/(R+1) L[E_n] = R/(R+1) E_inf . n
     b = sysm.pack([sh.sht_forward(R / (R + 1.0) * (far_field(d.x0, prm) * d.n0).sum(axis=0), d.p, d.p)
@@ -185,13 +186,13 @@ def grid_max_diff(acoefs, bcoefs, ps, ncomp):
     return m
 
 
-def step(xcoefs, gcoefs, ps, lams, dt: float, prm: Params):
+def step(xcoefs, gcoefs, ps, lams, dt: float, prm: Params, near: bool = True):
     """One midpoint step (Algorithm 1, Pe = infinity). Returns new x, Gamma and the error
     estimate err = max(err_drop, err_surfactant) against explicit Euler."""
-    u0, g0 = rates(xcoefs, gcoefs, ps, lams, prm)
+    u0, g0 = rates(xcoefs, gcoefs, ps, lams, prm, near=near)
     xh = [x + 0.5 * dt * u for x, u in zip(xcoefs, u0)]
     gh = [g + 0.5 * dt * r for g, r in zip(gcoefs, g0)]
-    u1, g1 = rates(xh, gh, ps, lams, prm)
+    u1, g1 = rates(xh, gh, ps, lams, prm, near=near)
     xn = [x + dt * u for x, u in zip(xcoefs, u1)]
     gn = [g + dt * r for g, r in zip(gcoefs, g1)]
     xe = [x + dt * u for x, u in zip(xcoefs, u0)]
