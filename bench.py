@@ -196,6 +196,11 @@ def run_own(args):
         apps_total = int(a.item())
     value = apps_total * P / (ms / 1e3)
 
+    if args.profile:
+        ctx.close()
+        print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps, "applications": apps_total}))
+        return
+
     # end to end: the state is copied in from pinned host memory and the new state read back
     x_pin = torch.tensor(x_host).pin_memory()
     g_pin = torch.tensor(g_host).pin_memory()
@@ -225,6 +230,8 @@ def run_own(args):
     # time to a 1e-8 FP64 residual for both solves: mixed (refined) vs plain FP64 GMRES
     tts = time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u)
 
+    scale = pairs_at_scale(S, torch, dev) if not args.no_scale else None
+
     # roofline of the dominant kernel class (measured above with CUDA events)
     dom = max(cls_ms, key=lambda k: cls_ms[k])
     roof = roofline(dom, cls_ms[dom], cls_n[dom], cfg, args.steps, args.precision, P, apps_total)
@@ -246,6 +253,7 @@ def run_own(args):
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "phase_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
         "time_to_1e-8": tts,
+        "pairs_at_scale": scale,
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": launches,
@@ -260,6 +268,51 @@ def run_own(args):
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# FP32 pipe issue slots per pair of the all-pairs kernels, counted from their source (hi/lo
+# offsets 6, r^2 3, kernel-specific terms, accumulation); the MUFU rsqrt is extra.
+PAIR_SLOTS = {"laplace_dl": 16, "laplace_sl": 10, "stokes_sd": 29}
+
+
+def pairs_at_scale(S, torch, dev, reps: int = 10):
+    """Throughput of the FP32 all-pairs kernels on 64 drops of degree 16 in a 12^3 box (5.5e9
+    target-source pairs per application): each kernel kind timed by CUDA events around its
+    launches (classes of the library's kernel timing), as pairs/s and as a fraction of the
+    FP32 pipe peak 152 SMs x 128 lanes x 2.07 GHz (2 flops per issue slot)."""
+    cfg = inputs.config3(seed=3, degrees=(16,))
+    ps = [d.p for d in cfg.drops]
+    ctx = S.Context(precision=S.FP32_COMP, R=cfg.R)
+    ctx.set_near(False)
+    x = torch.tensor(np.concatenate([d.xcoef.ravel() for d in cfg.drops]), device=dev)
+    ctx.set_drops(ps, x, [d.lam for d in cfg.drops])
+    nc, nt, ns = ctx.sizes()
+    per_drop_t = [(p + 1) * (2 * p + 2) for p in ps]
+    per_drop_s = [(2 * p + 2) * (4 * p + 4) for p in ps]
+    cross = sum(a * (ns - b) for a, b in zip(per_drop_t, per_drop_s))
+    rng = np.random.default_rng(5)
+    sig = torch.tensor(rng.standard_normal(nc), device=dev)
+    f = torch.tensor(rng.standard_normal(3 * nc), device=dev)
+    out = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12
+    res = {"workload": "64 drops p=16 (config-3 layout), cross pairs per application %d" % cross}
+    for name, fn in (("laplace_dl", lambda: ctx.eval_electric(S.LAPLACE_DL, sig, out[:nc])),
+                     ("laplace_sl", lambda: ctx.eval_electric(S.LAPLACE_SL, sig, out[:nc])),
+                     ("stokes_sd", lambda: ctx.eval_stokes(f, f, out))):
+        fn()
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        for _ in range(reps):
+            fn()
+        ms, n = ctx.kernel_stats(S.K_PAIRS)
+        ctx.set_timing(False)
+        per = ms / max(1, n)
+        ach = 2 * PAIR_SLOTS[name] * cross / (per / 1e3) / 1e12
+        res[name] = {"pairs_per_s": cross / (per / 1e3), "ms_per_application": per,
+                     "fp32_tflops_equiv": ach, "frac_of_fp32_peak": ach / peak}
+    res["peak_tflops"] = peak
+    ctx.close()
+    return res
 
 
 def time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u, reps=3):
@@ -404,6 +457,9 @@ def main():
     ap.add_argument("--dt", type=float, default=1e-3)
     ap.add_argument("--cpu-targets", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-scale", action="store_true", help="skip the 64-drop all-pairs measurement")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the warm-up and timed steps (for launch lists under a profiler)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -115,6 +115,15 @@ int shbim_set_R(shbim_ctx* ctx, double R);
 int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const double* lambda_host,
                     const double* xcoef_dev, void* stream);
 
+/* Nearly-singular correction (Section 3.1; on by default). When on, shbim_set_drops also finds
+ * every target closer than 6 h_j to another drop j's source nodes (h_j = sqrt(area_j / N_s),
+ * the spacing of drop j's degree 2p+1 grid) and, for each such pair, builds correction rows
+ * so that drop j's contribution there comes from the regular rule on drop j's grid upsampled
+ * four times per direction (degree 8p+7) instead of its degree 2p+1 grid. Turning it off or on
+ * takes effect at the next shbim_set_drops. shbim_near_pairs returns the number of pairs. */
+int shbim_set_near(shbim_ctx* ctx, int on);
+int shbim_near_pairs(shbim_ctx* ctx);
+
 /* Sizes of the current drop set: total scalar coefficients sum (p_i+1)^2, total targets
  * sum (p_i+1)(2p_i+2) and total sources sum (q_i+1)(2q_i+2). */
 int shbim_sizes(shbim_ctx* ctx, int64_t* ncoef, int64_t* ntarget, int64_t* nsource);
@@ -253,6 +262,36 @@ int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, co
  * is written by the same call). Returns 0, SHBIM_ERR_ARG or SHBIM_ERR_CUDA. */
 int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int64_t n_tgt, const double* src_dev,
                                 int64_t n_src, double* out_dev, void* stream);
+
+/* ---- Learned warm start (an addition to the paper's method: the network only proposes an
+ * initial guess; GMRES solves to its tolerance from there and is the judge of the error).
+ * A multilayer perceptron h_l = tanh(bf16(h_{l-1}) bf16(W_l)^T + b_l) with a linear last
+ * layer, bfloat16 weights (FP32 master copy) and FP32 accumulation on the tensor cores.
+ *   widths      n_layers + 1 sizes (input, hidden..., output); max_batch rows per call
+ *   W_host      [w_{l+1}][w_l] row-major FP32, b_host [w_{l+1}] (set: also resets Adam)
+ *   x_dev/y_dev/t_dev  FP32 row-major [batch][width] device arrays
+ * shbim_mlp_train_step: forward, loss sum (y - t)^2 / (2 batch) (read back into *loss_host
+ *   when not NULL, which synchronises `stream`), backward, and, if update != 0, one Adam step
+ *   (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. Gradients stay readable through
+ *   shbim_mlp_get_layer.
+ * shbim_electric_warm_start: initial guess for the electric system from the drop shapes,
+ *   x0 = 3(R+1)/(R+2) rhs + net(xcoef as FP32), i.e. the sphere solution E_n = 3R/(R+2) E.n
+ *   (written through the right-hand side) plus the learned correction. The network must map
+ *   3 ncoef inputs to ncoef outputs. */
+typedef struct shbim_mlp shbim_mlp;
+int shbim_mlp_create(int n_layers, const int32_t* widths, int max_batch, shbim_mlp** out);
+int shbim_mlp_destroy(shbim_mlp* net);
+int shbim_mlp_set_layer(shbim_mlp* net, int layer, const float* W_host, const float* b_host);
+/* Optional input standardisation x_n = (x - shift) * scale, per input feature, applied in FP32
+ * before the first bfloat16 rounding (NULL pointers remove it). */
+int shbim_mlp_set_input_affine(shbim_mlp* net, const float* shift_host, const float* scale_host);
+int shbim_mlp_get_layer(shbim_mlp* net, int layer, float* W_host, float* b_host, float* gW_host,
+                        float* gb_host);
+int shbim_mlp_forward(shbim_mlp* net, int batch, const float* x_dev, float* y_dev, void* stream);
+int shbim_mlp_train_step(shbim_mlp* net, int batch, const float* x_dev, const float* t_dev, float lr,
+                         int update, double* loss_host, void* stream);
+int shbim_electric_warm_start(shbim_ctx* ctx, shbim_mlp* net, const double* xcoef_dev,
+                              const double* rhs_dev, double* x0_dev, void* stream);
 
 /* Number of kernel launches the library has queued since the context was created. */
 int64_t shbim_launch_count(shbim_ctx* ctx);

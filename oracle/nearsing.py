@@ -61,15 +61,16 @@ def corrected_laplace_grid(system, kind: str, sigma, pairs=None):
     from the upsampled rule."""
     out = [system.laplace_targets(kind, sigma, i) for i in range(len(system.drops))]
     pairs = near_pairs(system) if pairs is None else pairs
-    fine = {}
+    fine, dens = {}, {}
     for (i, t, j) in pairs:
         di, dj = system.drops[i], system.drops[j]
         if j not in fine:
             fine[j] = _Fine(dj)
+            dens[j] = (sh.sht_inverse(sigma[j], dj.p, dj.q), sh.sht_inverse(sigma[j], dj.p, fine[j].q))
         F = fine[j]
         x0, n0 = di.x0[:, t:t + 1], di.n0[:, t:t + 1]
-        reg = quadrature.regular_scalar(kind, x0, n0, dj.xs, dj.ws, sh.sht_inverse(sigma[j], dj.p, dj.q))[0]
-        up = quadrature.regular_scalar(kind, x0, n0, F.x, F.w, sh.sht_inverse(sigma[j], dj.p, F.q))[0]
+        reg = quadrature.regular_scalar(kind, x0, n0, dj.xs, dj.ws, dens[j][0])[0]
+        up = quadrature.regular_scalar(kind, x0, n0, F.x, F.w, dens[j][1])[0]
         out[i][t] += up - reg
     return out
 
@@ -78,22 +79,22 @@ def corrected_stokes_grid(system, f, u, pairs=None):
     """sum_j S_j[f_j] + (lam_j - 1) D_j[u_j] with the upsampled rule at near targets."""
     out = [system.stokes_targets(f, u, i) for i in range(len(system.drops))]
     pairs = near_pairs(system) if pairs is None else pairs
-    fine = {}
+    fine, dens = {}, {}
     for (i, t, j) in pairs:
         di, dj = system.drops[i], system.drops[j]
         if j not in fine:
-            fine[j] = _Fine(dj)
+            F = fine[j] = _Fine(dj)
+            dens[j] = [None if a is None else (sh.sht_inverse(a[j], dj.p, dj.q), sh.sht_inverse(a[j], dj.p, F.q))
+                       for a in (f, u)]
         F = fine[j]
+        fd, ud = dens[j]
         x0 = di.x0[:, t:t + 1]
         corr = np.zeros(3)
-        if f is not None:
-            corr += quadrature.regular_tensor("sto_s", x0, F.x, F.n, F.w, sh.sht_inverse(f[j], dj.p, F.q))[:, 0]
-            corr -= quadrature.regular_tensor("sto_s", x0, dj.xs, dj.ns, dj.ws,
-                                              sh.sht_inverse(f[j], dj.p, dj.q))[:, 0]
-        if u is not None and dj.lam != 1.0:
-            corr += (dj.lam - 1.0) * quadrature.regular_tensor("sto_d", x0, F.x, F.n, F.w,
-                                                               sh.sht_inverse(u[j], dj.p, F.q))[:, 0]
-            corr -= (dj.lam - 1.0) * quadrature.regular_tensor("sto_d", x0, dj.xs, dj.ns, dj.ws,
-                                                               sh.sht_inverse(u[j], dj.p, dj.q))[:, 0]
+        if fd is not None:
+            corr += quadrature.regular_tensor("sto_s", x0, F.x, F.n, F.w, fd[1])[:, 0]
+            corr -= quadrature.regular_tensor("sto_s", x0, dj.xs, dj.ns, dj.ws, fd[0])[:, 0]
+        if ud is not None and dj.lam != 1.0:
+            corr += (dj.lam - 1.0) * quadrature.regular_tensor("sto_d", x0, F.x, F.n, F.w, ud[1])[:, 0]
+            corr -= (dj.lam - 1.0) * quadrature.regular_tensor("sto_d", x0, dj.xs, dj.ns, dj.ws, ud[0])[:, 0]
         out[i][:, t] += corr
     return out

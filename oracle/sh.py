@@ -15,6 +15,7 @@ Follows Section 3 of the paper:
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -135,10 +136,15 @@ def basis(p: int, ct, st, phi, derivs: bool = False):
     return S
 
 
+@functools.lru_cache(maxsize=16)
 def grid_basis(p: int, q: int, derivs: bool = False):
-    """Basis (and derivatives) of degree p on all nodes of the degree-q grid."""
+    """Basis (and derivatives) of degree p on all nodes of the degree-q grid (cached; the
+    returned arrays are shared and must not be modified)."""
     th, ph = grid_points(q)
-    return basis(p, np.cos(th), np.sin(th), ph, derivs=derivs)
+    out = basis(p, np.cos(th), np.sin(th), ph, derivs=derivs)
+    for a in (out if derivs else (out,)):
+        a.setflags(write=False)
+    return out
 
 
 def sht_inverse(coef, p: int, q: int) -> np.ndarray:

@@ -34,7 +34,9 @@ EXPORTS = [
     "shbim_eval_stokes", "shbim_gmres_begin", "shbim_gmres_step", "shbim_gmres_finish",
     "shbim_gmres_solve", "shbim_launch_count", "shbim_electric_rhs", "shbim_set_timing",
     "shbim_kernel_stats", "shbim_gmres_solve_refined", "shbim_pairs_laplace_noalloc",
-    "shbim_rates", "shbim_step", "shbim_operator_applications",
+    "shbim_rates", "shbim_step", "shbim_operator_applications", "shbim_set_near", "shbim_near_pairs",
+    "shbim_mlp_create", "shbim_mlp_destroy", "shbim_mlp_set_layer", "shbim_mlp_get_layer",
+    "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
 ]
 NOALLOC_MAX_TARGETS = 1 << 21
 K_SELF_WEIGHTS = 0
@@ -105,6 +107,16 @@ def lib():
         "shbim_rates": (i32, [vp, P(Phys), vp, vp, vp, P(i32), vp]),
         "shbim_step": (i32, [vp, P(Phys), vp, vp, dp, vp, vp, P(dp), P(i32), vp]),
         "shbim_operator_applications": (i64, [vp]),
+        "shbim_set_near": (i32, [vp, i32]),
+        "shbim_mlp_create": (i32, [i32, P(ctypes.c_int32), i32, P(vp)]),
+        "shbim_mlp_destroy": (i32, [vp]),
+        "shbim_mlp_set_layer": (i32, [vp, i32, vp, vp]),
+        "shbim_mlp_get_layer": (i32, [vp, i32, vp, vp, vp, vp]),
+        "shbim_mlp_set_input_affine": (i32, [vp, vp, vp]),
+        "shbim_mlp_forward": (i32, [vp, i32, vp, vp, vp]),
+        "shbim_mlp_train_step": (i32, [vp, i32, vp, vp, ctypes.c_float, i32, P(dp), vp]),
+        "shbim_electric_warm_start": (i32, [vp, vp, vp, vp, vp, vp]),
+        "shbim_near_pairs": (i32, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -120,6 +132,13 @@ def _ptr(t):
     import torch
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise ShbimError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr32(t):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ShbimError("expected a contiguous CUDA float32 tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -275,8 +294,89 @@ class Context:
                     "shbim_step")
         return err.value, list(it)
 
+    def set_near(self, on: bool):
+        self._check(self._L.shbim_set_near(self._h, 1 if on else 0), "shbim_set_near")
+
+    def near_pairs(self) -> int:
+        return int(self._L.shbim_near_pairs(self._h))
+
     def operator_applications(self) -> int:
         return int(self._L.shbim_operator_applications(self._h))
 
     def launch_count(self) -> int:
         return int(self._L.shbim_launch_count(self._h))
+
+
+class MLP:
+    """shbim_mlp: the warm-start network (bfloat16 weights, FP32 accumulation)."""
+
+    def __init__(self, widths, max_batch: int):
+        L = lib()
+        self._L = L
+        self.widths = [int(w) for w in widths]
+        arr = (ctypes.c_int32 * len(widths))(*self.widths)
+        h = ctypes.c_void_p()
+        rc = L.shbim_mlp_create(len(widths) - 1, arr, int(max_batch), ctypes.byref(h))
+        if rc != 0:
+            raise ShbimError("shbim_mlp_create failed (%d)" % rc)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.shbim_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_layer(self, l: int, W, b):
+        import numpy as np
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        rc = self._L.shbim_mlp_set_layer(self._h, l, W.ctypes.data_as(ctypes.c_void_p),
+                                          b.ctypes.data_as(ctypes.c_void_p))
+        if rc != 0:
+            raise ShbimError("shbim_mlp_set_layer failed (%d)" % rc)
+
+    def set_input_affine(self, shift, scale):
+        import numpy as np
+        if shift is None:
+            rc = self._L.shbim_mlp_set_input_affine(self._h, None, None)
+        else:
+            a = np.ascontiguousarray(shift, dtype=np.float32)
+            b = np.ascontiguousarray(scale, dtype=np.float32)
+            rc = self._L.shbim_mlp_set_input_affine(self._h, a.ctypes.data_as(ctypes.c_void_p),
+                                                     b.ctypes.data_as(ctypes.c_void_p))
+        if rc != 0:
+            raise ShbimError("shbim_mlp_set_input_affine failed (%d)" % rc)
+
+    def get_layer(self, l: int):
+        import numpy as np
+        a, b = self.widths[l], self.widths[l + 1]
+        W, bb = np.empty((b, a), np.float32), np.empty(b, np.float32)
+        gW, gb = np.empty((b, a), np.float32), np.empty(b, np.float32)
+        rc = self._L.shbim_mlp_get_layer(self._h, l, *(x.ctypes.data_as(ctypes.c_void_p) for x in (W, bb, gW, gb)))
+        if rc != 0:
+            raise ShbimError("shbim_mlp_get_layer failed (%d)" % rc)
+        return W, bb, gW, gb
+
+    def forward(self, x, y):
+        rc = self._L.shbim_mlp_forward(self._h, x.shape[0], _ptr32(x), _ptr32(y), _stream())
+        if rc != 0:
+            raise ShbimError("shbim_mlp_forward failed (%d)" % rc)
+
+    def train_step(self, x, t, lr: float, update: bool = True) -> float:
+        loss = ctypes.c_double()
+        rc = self._L.shbim_mlp_train_step(self._h, x.shape[0], _ptr32(x), _ptr32(t), float(lr),
+                                           1 if update else 0, ctypes.byref(loss), _stream())
+        if rc != 0:
+            raise ShbimError("shbim_mlp_train_step failed (%d)" % rc)
+        return loss.value
+
+
+def electric_warm_start(ctx: Context, net: MLP, xcoef, rhs, x0):
+    ctx._check(ctx._L.shbim_electric_warm_start(ctx._h, net._h, _ptr(xcoef), _ptr(rhs), _ptr(x0), _stream()),
+               "shbim_electric_warm_start")

@@ -41,6 +41,7 @@ int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
   int rc;
   if ((rc = build_geometry(ctx, xcoef_dev, s))) return rc;
   if ((rc = build_singular_rows(ctx, xcoef_dev, s))) return rc;
+  if ((rc = build_near(ctx, xcoef_dev, s))) return rc;
   return SHBIM_OK;
 }
 
@@ -138,6 +139,11 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->gm.Av);
   cudaFree(ctx->gm.diag);
   cudaFree(ctx->gm.y);
+  {
+    auto& N = ctx->near;
+    cudaFree(N.stats); cudaFree(N.det_t); cudaFree(N.det_j); cudaFree(N.pair_t); cudaFree(N.pair_j);
+    cudaFree(N.fgeo); cudaFree(N.fgeo32); cudaFree(N.fstr); cudaFree(N.fstr32); cudaFree(N.foff_dev);
+  }
   cudaFree(ctx->phys.buf);
   cudaFree(ctx->phys.grid);
   cudaFree(ctx->phys.state);
@@ -274,7 +280,11 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
     if ((rc = dalloc(ctx, &ctx->tiles_dev, ctx->tiles.size(), "tiles"))) return rc;
     SHBIM_CUDA(ctx, cudaMemcpy(ctx->tiles_dev, ctx->tiles.data(), ctx->tiles.size() * sizeof(PairTile),
                                cudaMemcpyHostToDevice));
-    if ((rc = dalloc(ctx, &ctx->part, (size_t)ctx->pair_splits * 3 * to, "pair partials"))) return rc;
+    ctx->split_max = (int)std::max<int64_t>(1, std::min<int64_t>(4 * splits, std::max<int64_t>(1, min_other / 64)));
+    ctx->split_max = std::min(ctx->split_max, 256);
+    ctx->pair_splits = std::min(ctx->pair_splits, ctx->split_max);
+    ctx->splits_tuned = false;
+    if ((rc = dalloc(ctx, &ctx->part, (size_t)ctx->split_max * 3 * to, "pair partials"))) return rc;
   }
   return rebuild_geometry(ctx, xcoef_dev, s);
 }
@@ -332,6 +342,7 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
     TimeScope ts(ctx, SHBIM_K_PAIRS, s);
     if ((rc = pairs_laplace(ctx, which, vals, s))) return rc;
   }
+  if ((rc = apply_near_laplace(ctx, which, dens_dev, vals, s))) return rc;
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {
@@ -380,6 +391,7 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
     TimeScope ts(ctx, SHBIM_K_PAIRS, s);
     if ((rc = pairs_stokes(ctx, f_dev != nullptr, u_dev != nullptr, vals, s))) return rc;
   }
+  if ((rc = apply_near_stokes(ctx, f_dev, u_dev, vals, s))) return rc;
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {

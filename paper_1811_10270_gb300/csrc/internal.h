@@ -25,6 +25,7 @@ inline int npts(int q) { return (q + 1) * (2 * q + 2); }
 // Number of Laplace / Stokes weight components in the singular self rows.
 constexpr int kNumLap = 2;        // 0: double layer (target normal), 1: single layer
 constexpr int kNumSto = 12;       // 0..5 Stokeslet xx,xy,xz,yy,yz,zz ; 6..11 stresslet (same order)
+constexpr double kNearFactor = 6.0;  // near zone: 6 source-grid spacings
 
 // Legendre tables per latitude (kinds of the synthesis). "phi-type" tables multiply the
 // sin/cos-swapped Fourier sum (a phi derivative); the others the plain one.
@@ -49,6 +50,7 @@ struct DegreeTables {
   int p = 0;
   GridTables base;           // q = p
   GridTables up;             // q = 2p+1
+  GridTables fine;           // q = 4(2p+2) - 1: nearly-singular sums
   double* dq = nullptr;      // rotation matrix blocks of Rx(pi/2), sum_n (2n+1)^2 doubles
   std::vector<int> dq_off;   // host copy of block offsets (n -> offset)
   int* dq_off_dev = nullptr;
@@ -111,6 +113,8 @@ struct shbim_ctx {
   shbim::PairTile* tiles_dev = nullptr;
   shbim::DropDev* drops_dev = nullptr;
   int pair_splits = 1;
+  int split_max = 1;              // capacity of the partial-sum buffer in splits
+  bool splits_tuned = false;      // autotuned on the first FP32 pair launch of a layout
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
   float* dens_up32 = nullptr;     // [3][nsource] source strengths (FP32)
@@ -150,6 +154,23 @@ struct shbim_ctx {
     double resid = 1.0;
     int64_t cap = 0;
   } gm;
+  // nearly-singular correction (near.cu)
+  struct Near {
+    bool enabled = true;
+    int npairs = 0;
+    double* stats = nullptr;  size_t stats_cap = 0;
+    int64_t* det_t = nullptr; size_t det_t_cap = 0;
+    int* det_j = nullptr;     size_t det_j_cap = 0;
+    int64_t* pair_t = nullptr; size_t pair_t_cap = 0;
+    int* pair_j = nullptr;    size_t pair_j_cap = 0;
+    double* fgeo = nullptr;   size_t fgeo_cap = 0;    // [7][nfine] upsampled x, n, w
+    float* fgeo32 = nullptr;  size_t fgeo32_cap = 0;  // same, positions relative to the centre
+    double* fstr = nullptr;   size_t fstr_cap = 0;    // [6][nfine] upsampled strengths
+    float* fstr32 = nullptr;  size_t fstr32_cap = 0;
+    int64_t* foff_dev = nullptr; size_t foff_cap = 0; // [2][n_drops]: offset, count
+    std::vector<int64_t> fine_off_h, fine_n_h;
+    int64_t nfine = 0;
+  } near;
   // physics workspaces (forces, rates, step state)
   struct Phys {
     double* buf = nullptr;
@@ -229,6 +250,16 @@ int build_singular_rows(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s)
 int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
 int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out,
                       cudaStream_t s);
+
+// ---- nearly-singular correction (near.cu)
+int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s);
+int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
+int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s);
+// geometry (x, n, w = omega J) of a grid from its synthesised x, x_theta, x_phi/sin (singular.cu)
+int geometry_kernel(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
+                    int64_t ld, int64_t off, cudaStream_t s);
+int geometry_kernel32(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
+                      float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s);
 
 // ---- shape-dependent state for an unchanged layout (api.cu)
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);

@@ -1,0 +1,437 @@
+// Nearly-singular correction (Section 3.1): targets close to another drop's surface take that
+// drop's contribution from the regular rule (Eq. reg_quadrature) on its grid upsampled four
+// times per direction, degree q_n = 4(q+1) - 1.
+//
+// Per geometry: a target x0 of drop i is near drop j when its distance to the nearest source
+// node of S_j is below 6 h_j, h_j = sqrt(area_j / N_s) (k_near_detect, bounding-sphere
+// culling first); the upsampled geometry (x, n, w = omega J) of every drop that has near
+// targets is built once.
+// Per operator application: the density of each such drop is synthesised on its upsampled
+// grid (times w), and one CTA per near pair adds
+//     sum over upsampled nodes of K(x0, y) s(y)  -  sum over degree-q nodes of K(x0, y) s(y)
+// to the all-pairs result, replacing the degree-q regular value by the upsampled one. The
+// FP32 variant uses the same centre-relative coordinates, (hi, lo) target offsets and two-sum
+// accumulation as the all-pairs kernel; the FP64 variant plain FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace shbim {
+
+namespace {
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// per drop: area (sum of w over the source grid) and radius (max |x - c|); one block per drop
+__global__ void k_drop_stats(const DropDev* __restrict__ drops, const double* __restrict__ src, int64_t nsource,
+                             double* __restrict__ out /* [n][2] */) {
+  const DropDev D = drops[blockIdx.x];
+  double a = 0.0, r = 0.0;
+  for (int64_t e = threadIdx.x; e < D.ns; e += blockDim.x) {
+    const int64_t s = D.src_off + e;
+    const double dx = src[s] - D.cx, dy = src[nsource + s] - D.cy, dz = src[2 * nsource + s] - D.cz;
+    a += src[6 * nsource + s];
+    r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  __shared__ double sa[256], sr[256];
+  sa[threadIdx.x] = a;
+  sr[threadIdx.x] = r;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sr[threadIdx.x] = fmax(sr[threadIdx.x], sr[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = sa[0];
+    out[2 * blockIdx.x + 1] = sr[0];
+  }
+}
+
+// Near test in FP32 on centre-relative coordinates (a target within rounding of the 6 h_j
+// threshold may land on either side; there the two rules agree to ~1e-11 anyway).
+__global__ void k_near_detect(const double* __restrict__ tgt, int64_t ntarget, const int* __restrict__ tgt_drop,
+                              const DropDev* __restrict__ drops, int n_drops, const float* __restrict__ src32,
+                              int64_t nsource, const double* __restrict__ stats /* area, R, lim per drop */,
+                              int* __restrict__ count, int64_t* __restrict__ pair_t, int* __restrict__ pair_j,
+                              int cap) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntarget) return;
+  const int i = tgt_drop[t];
+  const double x = tgt[t], y = tgt[ntarget + t], z = tgt[2 * ntarget + t];
+  for (int j = 0; j < n_drops; ++j) {
+    if (j == i) continue;
+    const DropDev D = drops[j];
+    const double R = stats[3 * j + 1], lim = stats[3 * j + 2];
+    const double dcx = x - D.cx, dcy = y - D.cy, dcz = z - D.cz;
+    if (sqrt(dcx * dcx + dcy * dcy + dcz * dcz) > R + lim) continue;
+    const float rx = (float)dcx, ry = (float)dcy, rz = (float)dcz;
+    const float lim2 = (float)(lim * lim);
+    bool near = false;
+    for (int64_t e = 0; e < D.ns && !near; ++e) {
+      const int64_t s = D.src_off + e;
+      const float dx = rx - src32[s], dy = ry - src32[nsource + s], dz = rz - src32[2 * nsource + s];
+      near = dx * dx + dy * dy + dz * dz < lim2;
+    }
+    if (near) {
+      const int k = atomicAdd(count, 1);
+      if (k < cap) {
+        pair_t[k] = t;
+        pair_j[k] = j;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void two_sum_f(float& hi, float& lo, float a) {
+  const float s = hi + a;
+  const float bp = s - hi;
+  lo += (hi - (s - bp)) + (a - bp);
+  hi = s;
+}
+
+__device__ __forceinline__ double block_sum_near(double v) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  v = 0.0;
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Sum over one grid of drop j of K(x0, y) s(y) for kernel KIND (0 DL target normal, 1 SL,
+// 2 Stokes with f and u strengths) into acc[3]. FP32: positions relative to drop j's centre
+// (pos32, [x y z nx ny nz][stride]), strengths str32 [comp][sstride]; FP64: absolute.
+template <int KIND>
+__device__ void near_sum32(const float* __restrict__ pos, int64_t stride, const float* __restrict__ str,
+                           int64_t sstride, int64_t n, const float th[3], const float tl[3], const float nv[3],
+                           int has_f, int has_u, double acc[3]) {
+  float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const float dx = (th[0] - pos[e]) + tl[0];
+    const float dy = (th[1] - pos[stride + e]) + tl[1];
+    const float dz = (th[2] - pos[2 * stride + e]) + tl[2];
+    const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    if (KIND == 1) {
+      two_sum_f(hi[0], lo[0], str[e] * ri);
+    } else if (KIND == 0) {
+      const float dn = fmaf(dx, nv[0], fmaf(dy, nv[1], dz * nv[2]));
+      two_sum_f(hi[0], lo[0], str[e] * ri * ri * ri * dn);
+    } else {
+      const float fx = has_f ? str[e] : 0.f, fy = has_f ? str[sstride + e] : 0.f, fz = has_f ? str[2 * sstride + e] : 0.f;
+      const float ux = has_u ? str[3 * sstride + e] : 0.f, uy = has_u ? str[4 * sstride + e] : 0.f,
+                  uz = has_u ? str[5 * sstride + e] : 0.f;
+      const float nx = pos[3 * stride + e], ny = pos[4 * stride + e], nz = pos[5 * stride + e];
+      const float ri2 = ri * ri, ri3 = ri2 * ri;
+      const float hf = fmaf(dx, fx, fmaf(dy, fy, dz * fz));
+      const float hu = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+      const float hn = fmaf(dx, nx, fmaf(dy, ny, dz * nz));
+      const float t = ri3 * fmaf(hu * hn, ri2, hf);
+      two_sum_f(hi[0], lo[0], fmaf(fx, ri, dx * t));
+      two_sum_f(hi[1], lo[1], fmaf(fy, ri, dy * t));
+      two_sum_f(hi[2], lo[2], fmaf(fz, ri, dz * t));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = (double)hi[c] + (double)lo[c];
+}
+
+template <int KIND>
+__device__ void near_sum64(const double* __restrict__ pos, int64_t stride, const double* __restrict__ str,
+                           int64_t sstride, int64_t n, const double x0[3], const double nv[3], int has_f,
+                           int has_u, double acc[3]) {
+  double a[3] = {0.0, 0.0, 0.0};
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const double dx = x0[0] - pos[e], dy = x0[1] - pos[stride + e], dz = x0[2] - pos[2 * stride + e];
+    const double ri = rsqrt(dx * dx + dy * dy + dz * dz);
+    if (KIND == 1) {
+      a[0] = fma(str[e], ri, a[0]);
+    } else if (KIND == 0) {
+      a[0] = fma(str[e] * ri * ri * ri, dx * nv[0] + dy * nv[1] + dz * nv[2], a[0]);
+    } else {
+      const double fx = has_f ? str[e] : 0.0, fy = has_f ? str[sstride + e] : 0.0, fz = has_f ? str[2 * sstride + e] : 0.0;
+      const double ux = has_u ? str[3 * sstride + e] : 0.0, uy = has_u ? str[4 * sstride + e] : 0.0,
+                   uz = has_u ? str[5 * sstride + e] : 0.0;
+      const double ri2 = ri * ri, ri3 = ri2 * ri;
+      const double hf = dx * fx + dy * fy + dz * fz;
+      const double hu = dx * ux + dy * uy + dz * uz;
+      const double hn = dx * pos[3 * stride + e] + dy * pos[4 * stride + e] + dz * pos[5 * stride + e];
+      const double t = ri3 * (hf + hu * hn * ri2);
+      a[0] += fx * ri + dx * t;
+      a[1] += fy * ri + dy * t;
+      a[2] += fz * ri + dz * t;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = a[c];
+}
+
+struct NearArgs {
+  const int64_t* pair_t;
+  const int* pair_j;
+  const int64_t* fine_off;   // per drop: offset into the upsampled arrays (-1: none)
+  const int64_t* fine_n;     // per drop: upsampled node count
+  const DropDev* drops;
+  const int* tgt_drop;
+  const double* tgt;
+  int64_t ntarget;
+  const double* fpos;        // [7][nfine] FP64 absolute
+  const float* fpos32;       // [7][nfine] FP32 relative to the drop centre
+  const double* fstr;        // [6][nfine] strengths on the upsampled grids
+  const float* fstr32;
+  int64_t nfine;
+  const double* src;         // degree-q sources
+  const float* src32;
+  const double* sstr;        // [6][nsource] degree-q strengths (dens_up)
+  const float* sstr32;
+  int64_t nsource;
+  int has_f, has_u;
+  double* out;
+};
+
+template <int KIND, bool F32>
+__global__ void __launch_bounds__(256) k_near_direct(NearArgs A) {
+  const int pr = blockIdx.x;
+  const int64_t t = A.pair_t[pr];
+  const int j = A.pair_j[pr];
+  const DropDev D = A.drops[j];
+  const int64_t fo = A.fine_off[j], fn = A.fine_n[j];
+  double x0[3], nv[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    x0[c] = A.tgt[c * A.ntarget + t];
+    nv[c] = A.tgt[(3 + c) * A.ntarget + t];
+  }
+  double af[3], au[3];
+  if (F32) {
+    const double cj[3] = {D.cx, D.cy, D.cz};
+    float th[3], tl[3], n32[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double d = x0[c] - cj[c];
+      th[c] = (float)d;
+      tl[c] = (float)(d - (double)th[c]);
+      n32[c] = (float)nv[c];
+    }
+    near_sum32<KIND>(A.fpos32 + fo, A.nfine, A.fstr32 + fo, A.nfine, fn, th, tl, n32, A.has_f, A.has_u, af);
+    near_sum32<KIND>(A.src32 + D.src_off, A.nsource, A.sstr32 + D.src_off, A.nsource, D.ns, th, tl, n32,
+                     A.has_f, A.has_u, au);
+  } else {
+    near_sum64<KIND>(A.fpos + fo, A.nfine, A.fstr + fo, A.nfine, fn, x0, nv, A.has_f, A.has_u, af);
+    near_sum64<KIND>(A.src + D.src_off, A.nsource, A.sstr + D.src_off, A.nsource, D.ns, x0, nv, A.has_f,
+                     A.has_u, au);
+  }
+  const int nc = KIND == 2 ? 3 : 1;
+  for (int c = 0; c < nc; ++c) {
+    const double v = block_sum_near(af[c] - au[c]);
+    if (threadIdx.x == 0) {
+      const double val = 0.07957747154594766788 * v;
+      if (KIND != 2) {
+        atomicAdd(A.out + t, val);
+      } else {
+        const DropDev Di = A.drops[A.tgt_drop[t]];
+        atomicAdd(A.out + 3 * Di.tgt_off + (int64_t)c * Di.nt + (t - Di.tgt_off), val);
+      }
+    }
+  }
+}
+
+int grow(shbim_ctx* ctx, void** p, size_t* cap, size_t bytes, const char* what) {
+  if (bytes <= *cap) return SHBIM_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess)
+    return fail(ctx, SHBIM_ERR_NOMEM, std::string("cudaMalloc ") + what);
+  *cap = bytes;
+  return SHBIM_OK;
+}
+
+}  // namespace
+
+int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
+  auto& N = ctx->near;
+  N.npairs = 0;
+  if (!N.enabled || ctx->n_drops < 2) return SHBIM_OK;
+  const int nd = ctx->n_drops;
+  int rc;
+  // per-drop area, radius and near limit 6 h_j
+  if ((rc = grow(ctx, (void**)&N.stats, &N.stats_cap, sizeof(double) * 3 * nd, "near stats"))) return rc;
+  double* tmp2 = nullptr;
+  if (cudaMalloc(&tmp2, sizeof(double) * 2 * nd) != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "near stats");
+  k_drop_stats<<<nd, 256, 0, s>>>(ctx->drops_dev, ctx->geo.src, ctx->nsource, tmp2);
+  SHBIM_CHECK_LAUNCH(ctx, "k_drop_stats");
+  std::vector<double> st2(2 * nd), st3(3 * nd);
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(st2.data(), tmp2, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  cudaFree(tmp2);
+  for (int j = 0; j < nd; ++j) {
+    st3[3 * j] = st2[2 * j];
+    st3[3 * j + 1] = st2[2 * j + 1];
+    st3[3 * j + 2] = kNearFactor * std::sqrt(st2[2 * j] / ctx->drops[j].ns);
+  }
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(N.stats, st3.data(), sizeof(double) * 3 * nd, cudaMemcpyHostToDevice, s));
+  // detection
+  const int cap = (int)std::min<int64_t>(ctx->ntarget * 2 + 1024, 1 << 26);
+  if ((rc = grow(ctx, (void**)&N.det_t, &N.det_t_cap, sizeof(int64_t) * cap, "near pairs")) ||
+      (rc = grow(ctx, (void**)&N.det_j, &N.det_j_cap, sizeof(int) * (cap + 1), "near pairs")))
+    return rc;
+  int* count = N.det_j + cap;
+  SHBIM_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int), s));
+  k_near_detect<<<nb(ctx->ntarget), 256, 0, s>>>(ctx->geo.tgt, ctx->ntarget, ctx->geo.tgt_drop, ctx->drops_dev, nd,
+                                                 ctx->geo.src32, ctx->nsource, N.stats, count, N.det_t, N.det_j, cap);
+  SHBIM_CHECK_LAUNCH(ctx, "k_near_detect");
+  int cnt = 0;
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(&cnt, count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  if (cnt > cap) return fail(ctx, SHBIM_ERR_NOMEM, "too many near pairs");
+  if (cnt == 0) return SHBIM_OK;
+  std::vector<int64_t> ht(cnt);
+  std::vector<int> hj(cnt);
+  SHBIM_CUDA(ctx, cudaMemcpy(ht.data(), N.det_t, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost));
+  SHBIM_CUDA(ctx, cudaMemcpy(hj.data(), N.det_j, sizeof(int) * cnt, cudaMemcpyDeviceToHost));
+  // deterministic order: by source drop, then target
+  std::vector<int> ord(cnt);
+  for (int k = 0; k < cnt; ++k) ord[k] = k;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return hj[a] != hj[b] ? hj[a] < hj[b] : ht[a] < ht[b]; });
+  std::vector<int64_t> pt(cnt);
+  std::vector<int> pj(cnt);
+  for (int k = 0; k < cnt; ++k) {
+    pt[k] = ht[ord[k]];
+    pj[k] = hj[ord[k]];
+  }
+  if ((rc = grow(ctx, (void**)&N.pair_t, &N.pair_t_cap, sizeof(int64_t) * cnt, "near pairs")) ||
+      (rc = grow(ctx, (void**)&N.pair_j, &N.pair_j_cap, sizeof(int) * cnt, "near pairs")))
+    return rc;
+  SHBIM_CUDA(ctx, cudaMemcpy(N.pair_t, pt.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice));
+  SHBIM_CUDA(ctx, cudaMemcpy(N.pair_j, pj.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice));
+  N.npairs = cnt;
+  // upsampled geometry of every drop that has near targets
+  N.fine_off_h.assign(nd, -1);
+  N.fine_n_h.assign(nd, 0);
+  int64_t nfine = 0;
+  for (int k = 0; k < cnt; ++k) {
+    const int j = pj[k];
+    if (N.fine_off_h[j] >= 0) continue;
+    N.fine_off_h[j] = nfine;
+    N.fine_n_h[j] = npts(ctx->drops[j].tab->fine.q);
+    nfine += N.fine_n_h[j];
+  }
+  N.nfine = nfine;
+  if ((rc = grow(ctx, (void**)&N.fgeo, &N.fgeo_cap, sizeof(double) * 7 * nfine, "fine geometry")) ||
+      (rc = grow(ctx, (void**)&N.fgeo32, &N.fgeo32_cap, sizeof(float) * 7 * nfine, "fine geometry")) ||
+      (rc = grow(ctx, (void**)&N.fstr, &N.fstr_cap, sizeof(double) * 6 * nfine, "fine strengths")) ||
+      (rc = grow(ctx, (void**)&N.fstr32, &N.fstr32_cap, sizeof(float) * 6 * nfine, "fine strengths")) ||
+      (rc = grow(ctx, (void**)&N.foff_dev, &N.foff_cap, sizeof(int64_t) * 2 * nd, "fine offsets")))
+    return rc;
+  {
+    std::vector<int64_t> both(2 * nd);
+    for (int j = 0; j < nd; ++j) {
+      both[j] = N.fine_off_h[j];
+      both[nd + j] = N.fine_n_h[j];
+    }
+    SHBIM_CUDA(ctx, cudaMemcpy(N.foff_dev, both.data(), sizeof(int64_t) * 2 * nd, cudaMemcpyHostToDevice));
+  }
+  int64_t maxn = 0;
+  for (int j = 0; j < nd; ++j) maxn = std::max(maxn, N.fine_n_h[j]);
+  double* tmp = nullptr;
+  if (cudaMalloc(&tmp, sizeof(double) * 9 * maxn) != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "fine scratch");
+  for (int j = 0; j < nd && rc == SHBIM_OK; ++j) {
+    if (N.fine_off_h[j] < 0) continue;
+    const Drop& d = ctx->drops[j];
+    const GridTables& fine = d.tab->fine;
+    const int64_t n = N.fine_n_h[j];
+    rc = sht_synth(ctx, fine, 3, xcoef + 3 * d.coef_off, d.nc, 7, tmp, 3 * n, n, nullptr, nullptr, s);
+    if (rc == SHBIM_OK)
+      rc = geometry_kernel32(ctx, tmp, n, 3, fine, N.fgeo, N.fgeo32, nfine, N.fine_off_h[j], d.centre, s);
+  }
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  return rc;
+}
+
+namespace {
+
+int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out, cudaStream_t s) {
+  auto& N = ctx->near;
+  NearArgs A{N.pair_t, N.pair_j, N.foff_dev, N.foff_dev + ctx->n_drops, ctx->drops_dev, ctx->geo.tgt_drop,
+             ctx->geo.tgt, ctx->ntarget, N.fgeo, N.fgeo32, N.fstr, N.fstr32, N.nfine, ctx->geo.src,
+             ctx->geo.src32, ctx->dens_up, ctx->dens_up32, ctx->nsource, has_f ? 1 : 0, has_u ? 1 : 0, out};
+  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const unsigned g = (unsigned)N.npairs;
+  if (kind == 0) {
+    if (f32) k_near_direct<0, true><<<g, 256, 0, s>>>(A); else k_near_direct<0, false><<<g, 256, 0, s>>>(A);
+  } else if (kind == 1) {
+    if (f32) k_near_direct<1, true><<<g, 256, 0, s>>>(A); else k_near_direct<1, false><<<g, 256, 0, s>>>(A);
+  } else {
+    if (f32) k_near_direct<2, true><<<g, 256, 0, s>>>(A); else k_near_direct<2, false><<<g, 256, 0, s>>>(A);
+  }
+  SHBIM_CHECK_LAUNCH(ctx, "k_near_direct");
+  return SHBIM_OK;
+}
+
+}  // namespace
+
+int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s) {
+  auto& N = ctx->near;
+  if (N.npairs == 0) return SHBIM_OK;
+  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  for (int j = 0; j < ctx->n_drops; ++j) {
+    if (N.fine_off_h[j] < 0) continue;
+    const Drop& d = ctx->drops[j];
+    const int64_t o = N.fine_off_h[j];
+    int rc = sht_synth_scaled(ctx, d.tab->fine, 1, dens + d.coef_off, d.nc, N.fstr + o, 0,
+                              N.fgeo + 6 * N.nfine + o, 1.0, f32 ? N.fstr32 + o : nullptr, s);
+    if (rc) return rc;
+  }
+  return launch_direct(ctx, which == SHBIM_LAPLACE_SL ? 1 : 0, false, false, out, s);
+}
+
+int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s) {
+  auto& N = ctx->near;
+  if (N.npairs == 0) return SHBIM_OK;
+  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  for (int j = 0; j < ctx->n_drops; ++j) {
+    if (N.fine_off_h[j] < 0) continue;
+    const Drop& d = ctx->drops[j];
+    const int64_t o = N.fine_off_h[j];
+    const double* w = N.fgeo + 6 * N.nfine + o;
+    int rc;
+    if (f && (rc = sht_synth_scaled(ctx, d.tab->fine, 3, f + 3 * d.coef_off, d.nc, N.fstr + o, N.nfine, w, 1.0,
+                                    f32 ? N.fstr32 + o : nullptr, s)))
+      return rc;
+    if (u && (rc = sht_synth_scaled(ctx, d.tab->fine, 3, u + 3 * d.coef_off, d.nc, N.fstr + 3 * N.nfine + o,
+                                    N.nfine, w, -6.0 * (d.lam - 1.0), f32 ? N.fstr32 + 3 * N.nfine + o : nullptr,
+                                    s)))
+      return rc;
+  }
+  return launch_direct(ctx, 2, f != nullptr, u != nullptr, out, s);
+}
+
+}  // namespace shbim
+
+extern "C" int shbim_set_near(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->near.enabled = on != 0;
+  if (!ctx->near.enabled) ctx->near.npairs = 0;
+  return SHBIM_OK;
+}
+
+extern "C" int shbim_near_pairs(shbim_ctx* ctx) { return ctx ? ctx->near.npairs : -1; }

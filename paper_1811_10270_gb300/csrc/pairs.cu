@@ -299,21 +299,64 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int6
 }
 
 template <int KIND>
+void launch_raw(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
+  dim3 grid((unsigned)ctx->tiles.size(), ctx->pair_splits);
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
+    k_pairs32<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
+                                              ctx->ntarget, ctx->geo.src32, ctx->nsource, ctx->dens_up32,
+                                              ctx->pair_splits, has_f, has_u, ctx->part);
+  } else {
+    k_pairs64<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
+                                              ctx->ntarget, ctx->geo.src, ctx->nsource, ctx->dens_up,
+                                              ctx->pair_splits, has_f, has_u, ctx->part);
+  }
+}
+
+// Pick the source-split count of the FP32 pair kernels for this drop layout by timing a few
+// candidates (powers of two up to the partial-buffer capacity) on the first launch.
+template <int KIND>
+int autotune_splits(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
+  ctx->splits_tuned = true;
+  if (ctx->timing || ctx->opts.precision != SHBIM_PREC_FP32_COMP) return SHBIM_OK;
+  cudaStreamCaptureStatus cs;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return SHBIM_OK;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int start = ctx->pair_splits;
+  int best = start;
+  float best_ms = 1e30f;
+  for (int sp = 1; sp <= ctx->split_max; sp *= 2) {
+    ctx->pair_splits = sp;
+    launch_raw<KIND>(ctx, has_f, has_u, s);  // warm
+    cudaEventRecord(a, s);
+    launch_raw<KIND>(ctx, has_f, has_u, s);
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    ctx->launches += 2;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = sp;
+    }
+  }
+  ctx->pair_splits = best;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? SHBIM_OK : cuda_fail(ctx, e, "pair split autotune");
+}
+
+template <int KIND>
 int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s) {
   constexpr int NC = (KIND == STO) ? 3 : 1;
   if (ctx->n_drops < 2 || ctx->tiles.empty()) return SHBIM_OK;
-  dim3 grid((unsigned)ctx->tiles.size(), ctx->pair_splits);
-  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
-    k_pairs32<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops,
-                                              ctx->geo.tgt, ctx->ntarget, ctx->geo.src32,
-                                              ctx->nsource, ctx->dens_up32, ctx->pair_splits,
-                                              has_f, has_u, ctx->part);
-  } else {
-    k_pairs64<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops,
-                                              ctx->geo.tgt, ctx->ntarget, ctx->geo.src,
-                                              ctx->nsource, ctx->dens_up, ctx->pair_splits, has_f,
-                                              has_u, ctx->part);
+  if (!ctx->splits_tuned) {
+    int rc = autotune_splits<KIND>(ctx, has_f, has_u, s);
+    if (rc) return rc;
   }
+  launch_raw<KIND>(ctx, has_f, has_u, s);
   SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
   const int64_t n = NC * ctx->ntarget;
   k_reduce_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->part, ctx->pair_splits, n, out);

@@ -307,7 +307,8 @@ int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double*
   }
   const int N = 2 * g.q + 2;
   if ((N & 3) == 0) {
-    const int rows = std::max(1, std::min(8, (int)((40 * 1024) / (2 * N * sizeof(double)))));
+    const int budget = 46 * 1024 / (int)sizeof(double) - 2 * N;  // stay below the 48 KB default
+    const int rows = std::max(1, std::min(8, budget / (2 * N)));
     const int64_t nrows = (int64_t)n_items * (g.q + 1);
     const size_t smem = (size_t)(2 * N + rows * 2 * N) * sizeof(double);
     k_analysis_fourier4<<<(unsigned)((nrows + rows - 1) / rows), 128, smem, s>>>(

@@ -57,6 +57,22 @@ __global__ void k_geometry(const double* __restrict__ tmp, int n, int nkind, int
   }
 }
 
+int geometry_kernel(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
+                    int64_t ld, int64_t off, cudaStream_t s) {
+  k_geometry<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(buf, (int)n, nkind, 2 * g.q + 2, g.omega, 1, out, ld, off,
+                                                         nullptr, 0.0, 0.0, 0.0);
+  SHBIM_CHECK_LAUNCH(ctx, "k_geometry");
+  return SHBIM_OK;
+}
+
+int geometry_kernel32(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
+                      float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s) {
+  k_geometry<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(buf, (int)n, nkind, 2 * g.q + 2, g.omega, 1, out, ld, off,
+                                                         out32, centre[0], centre[1], centre[2]);
+  SHBIM_CHECK_LAUNCH(ctx, "k_geometry");
+  return SHBIM_OK;
+}
+
 int build_geometry(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
   // scratch for the 9 synthesised fields of the largest grid
   int64_t maxn = 0;

@@ -219,7 +219,7 @@ int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out) {
   T->p = p;
   int rc;
   if ((rc = build_grid(ctx, p, p, T->base)) || (rc = build_grid(ctx, p, 2 * p + 1, T->up)) ||
-      (rc = build_rotation(ctx, p, *T))) {
+      (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine)) || (rc = build_rotation(ctx, p, *T))) {
     free_degree_tables(T);
     return rc;
   }
@@ -239,6 +239,7 @@ void free_degree_tables(DegreeTables* t) {
   if (!t) return;
   free_grid(t->base);
   free_grid(t->up);
+  free_grid(t->fine);
   cudaFree(t->dq);
   cudaFree(t->dq_off_dev);
   delete t;

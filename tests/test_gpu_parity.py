@@ -46,15 +46,17 @@ def T(a):
     return torch.tensor(np.ascontiguousarray(a, dtype=np.float64), device=DEV)
 
 
-def make(S, drops, precision, R=2.0):
+def make(S, drops, precision, R=2.0, near=True):
     ctx = S.Context(precision=precision, R=R, gmres_tol=1e-12)
+    ctx.set_near(near)
     xc = T(np.concatenate([d.xcoef.ravel() for d in drops]))
     ctx.set_drops([d.p for d in drops], xc, [d.lam for d in drops])
     return ctx
 
 
-def oracle_system(drops):
-    return operators.System([operators.DropGeom(d.xcoef, d.p, d.lam) for d in drops])
+def oracle_system(drops, near=True):
+    """Oracle operators; near=True applies the same nearly-singular correction as the library."""
+    return operators.System([operators.DropGeom(d.xcoef, d.p, d.lam) for d in drops], near=near)
 
 
 def split_grid(vec, drops, ncomp):
@@ -231,7 +233,7 @@ def test_full_size_two_drops_sampled_targets(S):
     configuration: target values at sampled targets (first, last, tile edges, closest to the
     gap) against the oracle evaluated one target at a time."""
     cfg = inputs.config2(p=32, seed=0, gap=0.1)
-    sysm = oracle_system(cfg.drops)
+    sysm = oracle_system(cfg.drops, near=False)
     rng = np.random.default_rng(12)
     sig = [inputs.random_density(d.p, rng)[0] for d in cfg.drops]
     f = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
@@ -241,7 +243,7 @@ def test_full_size_two_drops_sampled_targets(S):
         gap_t = int(np.argmin(np.abs(dg.x0[2] - 0.0)))
         sel = sorted(set(picks + [gap_t]))
         for precision, tol in ((0, TOL64), (1, TOL32)):
-            ctx = make(S, cfg.drops, precision, cfg.R)
+            ctx = make(S, cfg.drops, precision, cfg.R, near=False)
             out = torch.empty(2 * nt, device=DEV, dtype=torch.float64)
             ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), out, S.OUT_GRID)
             got = out.cpu().numpy()[i * nt:(i + 1) * nt][sel]
@@ -346,4 +348,35 @@ def test_refined_mixed_precision_solve_reaches_fp64_residual(S, system):
     inner, outer, res = ctx.gmres_solve_refined(sid, T(b), x, inner_tol=1e-5, max_outer=8)
     assert res <= 1e-10 and 1 <= outer <= 4, (inner, outer, res)
     assert rel_err(x.cpu().numpy(), ref) < 1e-9
+    ctx.close()
+
+
+def test_near_pairs_and_corrected_operators_match_oracle(S):
+    """Two drops 0.1 apart at p = 8: the library finds the oracle's near pairs and its corrected
+    Laplace and Stokes operators (upsampled rule at near targets) match the oracle's."""
+    cfg = inputs.config2(p=8, seed=0, gap=0.1)
+    cfg.drops[1].lam = 3.0
+    sysm = oracle_system(cfg.drops)
+    ctx = make(S, cfg.drops, S.FP64, cfg.R)
+    assert ctx.near_pairs() == len(sysm.near_pairs()) > 0
+    rng = np.random.default_rng(5)
+    sig = [inputs.random_density(8, rng, decay=2.0)[0] for _ in cfg.drops]
+    f = [inputs.random_density(8, rng, 3, decay=2.0) for _ in cfg.drops]
+    nt = 2 * 9 * 18
+    for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
+        out = torch.empty(nt, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(which, T(np.concatenate(sig)), out, S.OUT_GRID)
+        assert rel_err(out.cpu().numpy(), np.concatenate(sysm.laplace_grid(kind, sig))) < TOL64
+    out = torch.empty(3 * nt, device=DEV, dtype=torch.float64)
+    F = T(np.concatenate([a.ravel() for a in f]))
+    ctx.eval_stokes(F, F, out, S.OUT_GRID)
+    ref = np.concatenate([a.ravel() for a in sysm.stokes_grid(f, f)])
+    assert rel_err(out.cpu().numpy(), ref) < TOL64
+    # without the correction the operators differ from the corrected oracle
+    ctx.close()
+    ctx = make(S, cfg.drops, S.FP64, cfg.R, near=False)
+    assert ctx.near_pairs() == 0
+    out = torch.empty(nt, device=DEV, dtype=torch.float64)
+    ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), out, S.OUT_GRID)
+    assert rel_err(out.cpu().numpy(), np.concatenate(sysm.laplace_grid("ladl", sig))) > 1e-8
     ctx.close()

@@ -5,7 +5,7 @@ run (for example code that executes inside a CUDA stream capture, or inside a ho
 whose device memory is budgeted up front); it keeps its partial sums in a fixed array in
 device memory instead of allocating scratch.
 
-Set-up: two drops, drop 1 a sphere of radius a, whose upsampled-grid nodes and regular
+Set-up: two drops far enough apart that no target is near the other drop, drop 1 a sphere of radius a, whose upsampled-grid nodes and regular
 weights are known in closed form (J = a^2). With the density zero on drop 0, the value of
 shbim_eval_electric at drop 0's targets is exactly the regular sum over drop 1's sources, which
 is what the allocation-free call computes from explicit arrays. Collected last (file name) so
@@ -52,13 +52,14 @@ def _sphere_sources(p, a, centre):
 @pytest.mark.parametrize("which", [0, 1])
 def test_noalloc_pair_sum_matches_operator_entry_point(S, which):
     p = 10
-    a, centre = 0.9, np.array([0.1, -0.2, 2.45])
+    a, centre = 0.9, np.array([0.1, -0.2, 3.1])
     rng = np.random.default_rng(21)
     x0 = inputs.perturbed_coef(p, rng, 1.0, (0.0, 0.0, 0.0))
     x1 = inputs.sphere_coef(p, a, centre)
     dev = torch.device("cuda")
     ctx = S.Context(precision=S.FP64)
     ctx.set_drops([p, p], torch.tensor(np.concatenate([x0.ravel(), x1.ravel()]), device=dev))
+    assert ctx.near_pairs() == 0     # far apart: the operator is the plain regular sum
     nc = (p + 1) ** 2
     nt = (p + 1) * (2 * p + 2)
     sig1 = inputs.random_density(p, rng)[0]
