@@ -1,0 +1,399 @@
+// Learned GMRES warm start: a multilayer perceptron with bfloat16 weights and FP32
+// accumulation, trained and evaluated by the kernels in this file (the paper has no learned
+// component; the network only supplies an initial guess that GMRES then judges).
+//
+// Layers: h_l = tanh(bf16(h_{l-1}) bf16(W_l)^T + b_l), the last one linear; loss
+// sum (y - t)^2 / (2 B); backward with the bfloat16 rounding treated as identity; Adam on FP32
+// master weights, whose bfloat16 copy feeds the forward products.
+//
+// All products go through one tensor-core GEMM: C(m, n) = sum_k A(m, k) B(k, n) with A and B
+// read through arbitrary strides (so W, W^T, dZ^T need no transposed copies), staged to shared
+// memory as bfloat16 and multiplied by mma.sync m16n8k16 (bf16 x bf16 -> f32). A 64 x 64 CTA tile
+// is computed by four warps, each 32 x 32 = 2 x 4 MMA tiles, over K steps of 32.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+struct shbim_mlp {
+  int L = 0;
+  std::vector<int> w;          // widths, L+1
+  int max_batch = 0;
+  std::vector<float*> W, b, gW, gb, mW, vW, mb, vb;
+  std::vector<__nv_bfloat16*> Wh;
+  std::vector<float*> H;       // activations [max_batch][w_l], l = 0..L
+  float* xin = nullptr;        // [max_batch][w_0] standardised input when an input affine is set
+  float* shift = nullptr;      // [w_0] input affine x_n = (x - shift) * scale, applied in FP32
+  float* scale = nullptr;
+  bool affine = false;
+  float* dA = nullptr;         // [max_batch][max width]
+  float* dB = nullptr;
+  double* loss = nullptr;
+  int t = 0;                   // Adam step
+};
+
+namespace shbim {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(128)
+k_gemm_bf16(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
+            int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t scm, int64_t scn,
+            const float* __restrict__ bias, int act) {
+  __shared__ __nv_bfloat16 As[BM][BK + PAD];
+  __shared__ __nv_bfloat16 Bs[BN][BK + PAD];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int gid = lane >> 2, tig = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BM * BK; e += 128) {
+      const int mm = e / BK, kk = e - mm * BK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      const float v = (gm < M && gk < K) ? (float)A[(int64_t)gm * sam + (int64_t)gk * sak] : 0.f;
+      As[mm][kk] = __float2bfloat16_rn(v);
+    }
+    for (int e = threadIdx.x; e < BN * BK; e += 128) {
+      const int nn = e / BK, kk = e - nn * BK;
+      const int gn = n0 + nn, gk = k0 + kk;
+      const float v = (gn < N && gk < K) ? (float)B[(int64_t)gk * sbk + (int64_t)gn * sbn] : 0.f;
+      Bs[nn][kk] = __float2bfloat16_rn(v);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + gid;
+        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
+        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
+        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 8 + tig * 2]);
+        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 8 + tig * 2]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + j * 8 + gid;
+        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2]);
+        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 8 + tig * 2]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gm = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
+        const int gn = n0 + wn + j * 8 + tig * 2 + (r & 1);
+        if (gm < M && gn < N) {
+          float v = acc[i][j][r] + (bias ? bias[gn] : 0.f);
+          if (act) v = tanhf(v);
+          C[(int64_t)gm * scm + (int64_t)gn * scn] = v;
+        }
+      }
+}
+
+template <typename TA, typename TB>
+int gemm(shbim_mlp*, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
+         int64_t sbn, float* C, int64_t scm, int64_t scn, const float* bias, int act, cudaStream_t s) {
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  k_gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, scn, bias, act);
+  return cudaGetLastError() == cudaSuccess ? SHBIM_OK : SHBIM_ERR_CUDA;
+}
+
+__global__ void k_out_grad(const float* __restrict__ y, const float* __restrict__ t, int64_t n, float inv_b,
+                           float* __restrict__ d, double* __restrict__ loss) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (e < n) {
+    const float r = y[e] - t[e];
+    d[e] = r * inv_b;
+    l = 0.5 * (double)r * (double)r * inv_b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
+}
+
+__global__ void k_tanh_grad(float* __restrict__ d, const float* __restrict__ h, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) d[e] *= 1.f - h[e] * h[e];
+}
+
+// gb[n] = sum_b d[b][n]  (fixed order)
+__global__ void k_colsum(const float* __restrict__ d, int B, int N, float* __restrict__ gb) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) s += d[(int64_t)b * N + n];
+  gb[n] = s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, float lr, float c1, float c2, __nv_bfloat16* __restrict__ ph) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float gg = g[e];
+  const float mm = 0.9f * m[e] + 0.1f * gg;
+  const float vv = 0.999f * v[e] + 0.001f * gg * gg;
+  m[e] = mm;
+  v[e] = vv;
+  const float q = p[e] - lr * (mm / c1) / (sqrtf(vv / c2) + 1e-8f);
+  p[e] = q;
+  if (ph) ph[e] = __float2bfloat16_rn(q);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = __float2bfloat16_rn(a[e]);
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = (float)a[e];
+}
+
+__global__ void k_warm(const float* __restrict__ y, const double* __restrict__ rhs, double c, double* __restrict__ x0,
+                       int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) x0[e] = c * rhs[e] + (double)y[e];
+}
+
+inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+__global__ void k_affine(const float* __restrict__ x, const float* __restrict__ shift, const float* __restrict__ scale,
+                         int64_t n, int w, float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) {
+    const int c = (int)(e % w);
+    out[e] = (x[e] - shift[c]) * scale[c];
+  }
+}
+
+// network input after the optional FP32 affine
+const float* input_of(shbim_mlp* net, int B, const float* x, cudaStream_t s) {
+  if (!net->affine) return x;
+  const int64_t n = (int64_t)B * net->w[0];
+  k_affine<<<nb(n), 256, 0, s>>>(x, net->shift, net->scale, n, net->w[0], net->xin);
+  return net->xin;
+}
+
+int forward(shbim_mlp* net, int B, const float* x, cudaStream_t s) {
+  const float* in = x;
+  for (int l = 0; l < net->L; ++l) {
+    const int K = net->w[l], N = net->w[l + 1];
+    int rc = gemm<float, __nv_bfloat16>(net, B, N, K, in, K, 1, net->Wh[l], 1, K, net->H[l + 1], N, 1, net->b[l],
+                                        l < net->L - 1 ? 1 : 0, s);
+    if (rc) return rc;
+    in = net->H[l + 1];
+  }
+  return SHBIM_OK;
+}
+
+}  // namespace
+}  // namespace shbim
+
+using namespace shbim;
+
+extern "C" {
+
+int shbim_mlp_create(int n_layers, const int32_t* widths, int max_batch, shbim_mlp** out) {
+  if (!out || n_layers < 1 || n_layers > 16 || !widths || max_batch < 1) return SHBIM_ERR_ARG;
+  for (int l = 0; l <= n_layers; ++l)
+    if (widths[l] < 1 || widths[l] > (1 << 20)) return SHBIM_ERR_ARG;
+  shbim_mlp* n = new shbim_mlp();
+  n->L = n_layers;
+  n->w.assign(widths, widths + n_layers + 1);
+  n->max_batch = max_batch;
+  bool ok = true;
+  auto alloc = [&](float** p, size_t cnt) {
+    if (cudaMalloc(p, std::max<size_t>(cnt, 1) * sizeof(float)) != cudaSuccess) ok = false;
+    else cudaMemset(*p, 0, cnt * sizeof(float));
+  };
+  int wmax = 0;
+  for (int l = 0; l <= n_layers; ++l) wmax = std::max(wmax, widths[l]);
+  n->W.resize(n_layers); n->b.resize(n_layers); n->gW.resize(n_layers); n->gb.resize(n_layers);
+  n->mW.resize(n_layers); n->vW.resize(n_layers); n->mb.resize(n_layers); n->vb.resize(n_layers);
+  n->Wh.resize(n_layers);
+  n->H.resize(n_layers + 1);
+  for (int l = 0; l < n_layers && ok; ++l) {
+    const size_t nw = (size_t)widths[l] * widths[l + 1];
+    alloc(&n->W[l], nw); alloc(&n->gW[l], nw); alloc(&n->mW[l], nw); alloc(&n->vW[l], nw);
+    alloc(&n->b[l], widths[l + 1]); alloc(&n->gb[l], widths[l + 1]);
+    alloc(&n->mb[l], widths[l + 1]); alloc(&n->vb[l], widths[l + 1]);
+    if (cudaMalloc(&n->Wh[l], nw * sizeof(__nv_bfloat16)) != cudaSuccess) ok = false;
+    else cudaMemset(n->Wh[l], 0, nw * sizeof(__nv_bfloat16));
+  }
+  for (int l = 0; l <= n_layers && ok; ++l) alloc(&n->H[l], (size_t)max_batch * widths[l]);
+  if (ok) alloc(&n->xin, (size_t)max_batch * widths[0]);
+  if (ok) alloc(&n->shift, widths[0]);
+  if (ok) alloc(&n->scale, widths[0]);
+  if (ok) alloc(&n->dA, (size_t)max_batch * wmax);
+  if (ok) alloc(&n->dB, (size_t)max_batch * wmax);
+  if (ok && cudaMalloc(&n->loss, sizeof(double)) != cudaSuccess) ok = false;
+  if (!ok) {
+    *out = n;
+    return SHBIM_ERR_NOMEM;
+  }
+  *out = n;
+  return SHBIM_OK;
+}
+
+int shbim_mlp_destroy(shbim_mlp* n) {
+  if (!n) return SHBIM_ERR_ARG;
+  cudaDeviceSynchronize();
+  for (int l = 0; l < n->L; ++l) {
+    cudaFree(n->W[l]); cudaFree(n->gW[l]); cudaFree(n->mW[l]); cudaFree(n->vW[l]);
+    cudaFree(n->b[l]); cudaFree(n->gb[l]); cudaFree(n->mb[l]); cudaFree(n->vb[l]); cudaFree(n->Wh[l]);
+  }
+  for (auto* h : n->H) cudaFree(h);
+  cudaFree(n->xin);
+  cudaFree(n->shift);
+  cudaFree(n->scale);
+  cudaFree(n->dA);
+  cudaFree(n->dB);
+  cudaFree(n->loss);
+  delete n;
+  return SHBIM_OK;
+}
+
+int shbim_mlp_set_layer(shbim_mlp* n, int l, const float* W_host, const float* b_host) {
+  if (!n || l < 0 || l >= n->L || !W_host || !b_host) return SHBIM_ERR_ARG;
+  const size_t nw = (size_t)n->w[l] * n->w[l + 1];
+  if (cudaMemcpy(n->W[l], W_host, nw * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(n->b[l], b_host, n->w[l + 1] * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return SHBIM_ERR_CUDA;
+  k_to_bf16<<<nb(nw), 256>>>(n->W[l], n->Wh[l], nw);
+  cudaMemset(n->mW[l], 0, nw * sizeof(float));
+  cudaMemset(n->vW[l], 0, nw * sizeof(float));
+  cudaMemset(n->mb[l], 0, n->w[l + 1] * sizeof(float));
+  cudaMemset(n->vb[l], 0, n->w[l + 1] * sizeof(float));
+  n->t = 0;
+  return cudaDeviceSynchronize() == cudaSuccess ? SHBIM_OK : SHBIM_ERR_CUDA;
+}
+
+int shbim_mlp_set_input_affine(shbim_mlp* n, const float* shift_host, const float* scale_host) {
+  if (!n) return SHBIM_ERR_ARG;
+  if (!shift_host || !scale_host) {
+    n->affine = false;
+    return SHBIM_OK;
+  }
+  if (cudaMemcpy(n->shift, shift_host, n->w[0] * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(n->scale, scale_host, n->w[0] * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+    return SHBIM_ERR_CUDA;
+  n->affine = true;
+  return SHBIM_OK;
+}
+
+int shbim_mlp_get_layer(shbim_mlp* n, int l, float* W_host, float* b_host, float* gW_host, float* gb_host) {
+  if (!n || l < 0 || l >= n->L) return SHBIM_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SHBIM_ERR_CUDA;
+  const size_t nw = (size_t)n->w[l] * n->w[l + 1];
+  const size_t nbias = n->w[l + 1];
+  if ((W_host && cudaMemcpy(W_host, n->W[l], nw * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (b_host && cudaMemcpy(b_host, n->b[l], nbias * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (gW_host && cudaMemcpy(gW_host, n->gW[l], nw * 4, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (gb_host && cudaMemcpy(gb_host, n->gb[l], nbias * 4, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return SHBIM_ERR_CUDA;
+  return SHBIM_OK;
+}
+
+int shbim_mlp_forward(shbim_mlp* n, int batch, const float* x_dev, float* y_dev, void* stream) {
+  if (!n || batch < 1 || batch > n->max_batch || !x_dev || !y_dev) return SHBIM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = forward(n, batch, input_of(n, batch, x_dev, s), s);
+  if (rc) return rc;
+  const size_t ny = (size_t)batch * n->w[n->L];
+  return cudaMemcpyAsync(y_dev, n->H[n->L], ny * sizeof(float), cudaMemcpyDeviceToDevice, s) == cudaSuccess
+             ? SHBIM_OK : SHBIM_ERR_CUDA;
+}
+
+int shbim_mlp_train_step(shbim_mlp* n, int batch, const float* x_dev, const float* t_dev, float lr, int update,
+                         double* loss_host, void* stream) {
+  if (!n || batch < 1 || batch > n->max_batch || !x_dev || !t_dev) return SHBIM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const float* x_in = input_of(n, batch, x_dev, s);
+  int rc = forward(n, batch, x_in, s);
+  if (rc) return rc;
+  const int L = n->L;
+  const int64_t ny = (int64_t)batch * n->w[L];
+  cudaMemsetAsync(n->loss, 0, sizeof(double), s);
+  k_out_grad<<<nb(ny), 256, 0, s>>>(n->H[L], t_dev, ny, 1.0f / batch, n->dA, n->loss);
+  float* d = n->dA;
+  float* dn = n->dB;
+  for (int l = L - 1; l >= 0; --l) {
+    const int K = n->w[l], N = n->w[l + 1];
+    if (l < L - 1) k_tanh_grad<<<nb((int64_t)batch * N), 256, 0, s>>>(d, n->H[l + 1], (int64_t)batch * N);
+    const float* in = l == 0 ? x_in : n->H[l];
+    // gW[N x K] = d^T [N x B] . in [B x K]
+    if ((rc = gemm<float, float>(n, N, K, batch, d, 1, N, in, K, 1, n->gW[l], K, 1, nullptr, 0, s))) return rc;
+    k_colsum<<<(N + 255) / 256, 256, 0, s>>>(d, batch, N, n->gb[l]);
+    if (l > 0) {
+      // dn [B x K] = d [B x N] . W [N x K]
+      if ((rc = gemm<float, __nv_bfloat16>(n, batch, K, N, d, N, 1, n->Wh[l], K, 1, dn, K, 1, nullptr, 0, s)))
+        return rc;
+      std::swap(d, dn);
+    }
+  }
+  if (update) {
+    n->t += 1;
+    const float c1 = 1.f - std::pow(0.9f, (float)n->t), c2 = 1.f - std::pow(0.999f, (float)n->t);
+    for (int l = 0; l < L; ++l) {
+      const int64_t nw = (int64_t)n->w[l] * n->w[l + 1];
+      k_adam<<<nb(nw), 256, 0, s>>>(n->W[l], n->gW[l], n->mW[l], n->vW[l], nw, lr, c1, c2, n->Wh[l]);
+      k_adam<<<nb(n->w[l + 1]), 256, 0, s>>>(n->b[l], n->gb[l], n->mb[l], n->vb[l], n->w[l + 1], lr, c1, c2, nullptr);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return SHBIM_ERR_CUDA;
+  if (loss_host) {
+    if (cudaMemcpyAsync(loss_host, n->loss, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return SHBIM_ERR_CUDA;
+  }
+  return SHBIM_OK;
+}
+
+int shbim_electric_warm_start(shbim_ctx* ctx, shbim_mlp* n, const double* xcoef_dev, const double* rhs_dev,
+                              double* x0_dev, void* stream) {
+  if (!ctx || !n || !xcoef_dev || !rhs_dev || !x0_dev) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (n->w[0] != 3 * ctx->ncoef || n->w[n->L] != ctx->ncoef)
+    return fail(ctx, SHBIM_ERR_ARG, "network widths do not match 3 ncoef inputs and ncoef outputs");
+  cudaStream_t s = (cudaStream_t)stream;
+  float* feat = n->dA;  // [1][3 ncoef] as the network input
+  k_to_f32<<<nb(3 * ctx->ncoef), 256, 0, s>>>(xcoef_dev, feat, 3 * ctx->ncoef);
+  SHBIM_CHECK_LAUNCH(ctx, "k_to_f32");
+  int rc = forward(n, 1, input_of(n, 1, feat, s), s);
+  if (rc) return cuda_fail(ctx, cudaGetLastError(), "mlp forward");
+  const double R = ctx->opts.R;
+  // spherical baseline E_n = 3R/(R+2) E.n, i.e. 3(R+1)/(R+2) times the right-hand side
+  k_warm<<<nb(ctx->ncoef), 256, 0, s>>>(n->H[n->L], rhs_dev, 3.0 * (R + 1.0) / (R + 2.0), x0_dev, ctx->ncoef);
+  SHBIM_CHECK_LAUNCH(ctx, "k_warm");
+  return SHBIM_OK;
+}
+
+}  // extern "C"
