@@ -231,6 +231,7 @@ def run_own(args):
     tts = time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u)
 
     scale = pairs_at_scale(S, torch, dev) if not args.no_scale else None
+    learned = learned_warm_start(S, torch, dev) if not args.no_learned else None
 
     # roofline of the dominant kernel class (measured above with CUDA events)
     dom = max(cls_ms, key=lambda k: cls_ms[k])
@@ -254,6 +255,7 @@ def run_own(args):
         "phase_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
         "time_to_1e-8": tts,
         "pairs_at_scale": scale,
+        "learned_warm_start": learned,
         "roofline": roof,
         "clocks": clk,
         "gpu_launches": launches,
@@ -313,6 +315,65 @@ def pairs_at_scale(S, torch, dev, reps: int = 10):
     res["peak_tflops"] = peak
     ctx.close()
     return res
+
+
+def learned_warm_start(S, torch, dev, p: int = 8, n_train: int = 600, n_test: int = 16):
+    """The learned warm start at reduced scale (p = 8 two-drop inputs; the network and its
+    training run in the library's kernels): on held-out seeds, the electric solve to an FP64
+    residual of 1e-8 from zero, from the sphere solution and from sphere + network --
+    iterations, initial residual and time (CUDA events)."""
+    from paper_1811_10270_gb300 import warmstart
+    t0 = time.perf_counter()
+    X, Y, _ = warmstart.generate(range(1, n_train + 1), p)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, hist = warmstart.train(X, Y, hidden=(512, 512, 512), epochs=150, batch=32, lr=1e-3)
+    t_train = time.perf_counter() - t0
+    names = ("zero", "sphere", "learned")
+    it = {k: [] for k in names}
+    r0 = {k: [] for k in names}
+    ms = {k: 0.0 for k in names}
+    stream = torch.cuda.current_stream()
+    for sd in range(100000, 100000 + n_test):
+        cfg = inputs.config2(p=p, seed=sd, gap=0.1)
+        ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8)
+        x = torch.tensor(np.concatenate([d.xcoef.ravel() for d in cfg.drops]), device=dev)
+        ctx.set_drops([p, p], x, [d.lam for d in cfg.drops])
+        nc = x.numel() // 3
+        rhs = torch.empty(nc, device=dev, dtype=torch.float64)
+        ctx.electric_rhs(cfg.E_u, rhs)
+        sol = torch.empty_like(rhs)
+        ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs, sol)       # warm the graphs of this geometry
+        for k in names:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            x0 = None
+            if k == "sphere":
+                x0 = 3.0 * (cfg.R + 1) / (cfg.R + 2) * rhs
+            elif k == "learned":
+                x0 = torch.empty_like(rhs)
+                S.electric_warm_start(ctx, net, x, rhs, x0)
+            inner, outer, res = ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs, sol, x0=x0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms[k] += a.elapsed_time(b)
+            it[k].append(inner)
+            if x0 is None:
+                r0[k].append(1.0)
+            else:
+                Lx = torch.empty_like(rhs)
+                ctx.eval_electric(S.LAPLACE_DL, x0, Lx, S.OUT_COEF)
+                r = rhs - (0.5 * x0 - (cfg.R - 1) / (cfg.R + 1) * Lx)
+                r0[k].append(float(torch.linalg.norm(r) / torch.linalg.norm(rhs)))
+        ctx.close()
+    net.close()
+    return {"scale": "p=%d two-drop inputs, %d training solves, %d held out (north-star scale p=32 x 20000 "
+                     "not run)" % (p, n_train, n_test),
+            "train_s": t_train, "generate_s": t_gen, "final_loss_ratio": hist[-1] / hist[0],
+            "mean_inner_iters": {k: float(np.mean(v)) for k, v in it.items()},
+            "mean_initial_resid": {k: float(np.mean(v)) for k, v in r0.items()},
+            "mean_ms_to_1e-8": {k: v / n_test for k, v in ms.items()}}
 
 
 def time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u, reps=3):
@@ -458,6 +519,7 @@ def main():
     ap.add_argument("--cpu-targets", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the 64-drop all-pairs measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for launch lists under a profiler)")
     args = ap.parse_args()

@@ -296,6 +296,13 @@ int shbim_electric_warm_start(shbim_ctx* ctx, shbim_mlp* net, const double* xcoe
 /* Number of kernel launches the library has queued since the context was created. */
 int64_t shbim_launch_count(shbim_ctx* ctx);
 
+/* CUDA graphs for the operator applications inside GMRES (on by default): for each geometry,
+ * system and precision the second application is captured on a stream owned by the library
+ * and later ones replay it on the caller's stream, with the Krylov vector copied through fixed
+ * staging buffers. Kernel timing (shbim_set_timing) disables the replay while it is on. If a
+ * capture fails, the context falls back to direct launches. */
+int shbim_set_graphs(shbim_ctx* ctx, int on);
+
 /* Number of layer-operator applications (calls of the electric or Stokes operator, including
  * those made inside GMRES and the time step) since the context was created. */
 int64_t shbim_operator_applications(shbim_ctx* ctx);

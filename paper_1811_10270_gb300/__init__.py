@@ -37,6 +37,7 @@ EXPORTS = [
     "shbim_rates", "shbim_step", "shbim_operator_applications", "shbim_set_near", "shbim_near_pairs",
     "shbim_mlp_create", "shbim_mlp_destroy", "shbim_mlp_set_layer", "shbim_mlp_get_layer",
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
+    "shbim_set_graphs",
 ]
 NOALLOC_MAX_TARGETS = 1 << 21
 K_SELF_WEIGHTS = 0
@@ -108,6 +109,7 @@ def lib():
         "shbim_step": (i32, [vp, P(Phys), vp, vp, dp, vp, vp, P(dp), P(i32), vp]),
         "shbim_operator_applications": (i64, [vp]),
         "shbim_set_near": (i32, [vp, i32]),
+        "shbim_set_graphs": (i32, [vp, i32]),
         "shbim_mlp_create": (i32, [i32, P(ctypes.c_int32), i32, P(vp)]),
         "shbim_mlp_destroy": (i32, [vp]),
         "shbim_mlp_set_layer": (i32, [vp, i32, vp, vp]),
@@ -293,6 +295,9 @@ class Context:
                                        _ptr(x_out), _ptr(gamma_out), ctypes.byref(err), it, _stream()),
                     "shbim_step")
         return err.value, list(it)
+
+    def set_graphs(self, on: bool):
+        self._check(self._L.shbim_set_graphs(self._h, 1 if on else 0), "shbim_set_graphs")
 
     def set_near(self, on: bool):
         self._check(self._L.shbim_set_near(self._h, 1 if on else 0), "shbim_set_near")

@@ -24,6 +24,7 @@ int pairs_tile_targets();
 // position over the parameter sphere), the device drop table, geometry and singular rows.
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
   SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->geom_version++;  // invalidates captured operator graphs
   for (auto& d : ctx->drops) {
     double c00[3];
     for (int c = 0; c < 3; ++c)
@@ -144,6 +145,12 @@ int shbim_destroy(shbim_ctx* ctx) {
     cudaFree(N.stats); cudaFree(N.det_t); cudaFree(N.det_j); cudaFree(N.pair_t); cudaFree(N.pair_j);
     cudaFree(N.fgeo); cudaFree(N.fgeo32); cudaFree(N.fstr); cudaFree(N.fstr32); cudaFree(N.foff_dev);
   }
+  for (auto& g : ctx->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    cudaFree(g.in);
+    cudaFree(g.out);
+  }
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   cudaFree(ctx->phys.buf);
   cudaFree(ctx->phys.grid);
   cudaFree(ctx->phys.state);
@@ -168,6 +175,7 @@ int shbim_set_precision(shbim_ctx* ctx, int precision) {
 int shbim_set_R(shbim_ctx* ctx, double R) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (!(R > 0.0) || !std::isfinite(R)) return fail(ctx, SHBIM_ERR_ARG, "R must be positive");
+  if (R != ctx->opts.R) ctx->geom_version++;  // the electric system's factor is captured in graphs
   ctx->opts.R = R;
   return SHBIM_OK;
 }
@@ -175,6 +183,12 @@ int shbim_set_R(shbim_ctx* ctx, double R) {
 int64_t shbim_launch_count(shbim_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 int64_t shbim_operator_applications(shbim_ctx* ctx) { return ctx ? ctx->applications : -1; }
+
+int shbim_set_graphs(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->graphs_on = on != 0;
+  return SHBIM_OK;
+}
 
 int shbim_sizes(shbim_ctx* ctx, int64_t* nc, int64_t* nt, int64_t* ns) {
   if (!ctx) return SHBIM_ERR_ARG;

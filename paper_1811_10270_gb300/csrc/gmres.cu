@@ -102,7 +102,7 @@ __global__ void k_fill_diag(double* __restrict__ diag, const DropDev* __restrict
 
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
+int matvec_eager(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
   auto& G = ctx->gm;
   int rc = G.sys == SHBIM_SYS_ELECTRIC
                ? shbim_eval_electric(ctx, SHBIM_LAPLACE_DL, v, G.Av, SHBIM_OUT_COEF, s)
@@ -110,6 +110,67 @@ int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) 
   if (rc) return rc;
   k_system<<<nb(G.n), 256, 0, s>>>(G.diag, G.offdiag, v, G.Av, out, G.n);
   SHBIM_CHECK_LAUNCH(ctx, "k_system");
+  return SHBIM_OK;
+}
+
+// Operator application of the current system. With graphs on, the second application for a
+// given geometry, system and precision is captured on the library's stream (input and output
+// through fixed staging buffers) and later ones replay the graph on the caller's stream.
+int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
+  auto& G = ctx->gm;
+  if (!ctx->graphs_on || ctx->timing) return matvec_eager(ctx, v, out, s);
+  auto& GR = ctx->graphs[G.sys * 2 + (ctx->opts.precision == SHBIM_PREC_FP32_COMP ? 1 : 0)];
+  if (GR.version != ctx->geom_version || GR.n != G.n) {
+    if (GR.exec) cudaGraphExecDestroy(GR.exec);
+    GR.exec = nullptr;
+    GR.warm = false;
+    GR.version = ctx->geom_version;
+    if (GR.n < G.n) {
+      cudaFree(GR.in);
+      cudaFree(GR.out);
+      GR.in = GR.out = nullptr;
+      if (cudaMalloc(&GR.in, G.n * sizeof(double)) != cudaSuccess ||
+          cudaMalloc(&GR.out, G.n * sizeof(double)) != cudaSuccess)
+        return fail(ctx, SHBIM_ERR_NOMEM, "graph staging buffers");
+    }
+    GR.n = G.n;
+  }
+  if (!GR.exec) {
+    if (!GR.warm) {  // first application: eager, sizes every workspace
+      GR.warm = true;
+      return matvec_eager(ctx, v, out, s);
+    }
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return matvec_eager(ctx, v, out, s);
+    SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+    cudaGraph_t graph = nullptr;
+    const int64_t l0 = ctx->launches, a0 = ctx->applications;
+    SHBIM_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = matvec_eager(ctx, GR.in, GR.out, ctx->cap_stream);
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    GR.kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    ctx->applications = a0;
+    if (rc || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      ctx->graphs_on = false;  // fall back to eager launches for this context
+      return matvec_eager(ctx, v, out, s);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&GR.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      GR.exec = nullptr;
+      cudaGetLastError();
+      ctx->graphs_on = false;
+      return matvec_eager(ctx, v, out, s);
+    }
+  }
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(GR.in, v, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  SHBIM_CUDA(ctx, cudaGraphLaunch(GR.exec, s));
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(out, GR.out, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ctx->launches += GR.kernels;
+  ctx->applications += 1;
   return SHBIM_OK;
 }
 
@@ -207,6 +268,7 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
       return fail(ctx, SHBIM_ERR_NOMEM, "GMRES workspace allocation failed");
     G.cap = ncap * (m + 1);
     G.m = m;
+    ctx->geom_version++;  // captured operator graphs referenced the old workspaces
   }
   G.sys = sys;
   G.n = n;

@@ -182,6 +182,20 @@ struct shbim_ctx {
   } phys;
   int64_t launches = 0;
   int64_t applications = 0;
+  // CUDA graphs of the GMRES operator application, per (system, precision), re-captured per
+  // geometry on a library-owned stream and replayed on the caller's stream
+  bool graphs_on = true;
+  int64_t geom_version = 0;
+  cudaStream_t cap_stream = nullptr;
+  struct MatvecGraph {
+    cudaGraphExec_t exec = nullptr;
+    double* in = nullptr;
+    double* out = nullptr;
+    int64_t n = 0;
+    int64_t version = -1;
+    int64_t kernels = 0;   // kernel nodes per replay
+    bool warm = false;
+  } graphs[4];
   // optional per-class kernel timing
   bool timing = false;
   struct TimedRange {

@@ -21,9 +21,12 @@ namespace shbim {
 
 namespace {
 
+#ifndef SHBIM_PAIR_TPT
+#define SHBIM_PAIR_TPT 2
+#endif
 constexpr int kTile = 256;
 constexpr int kThreads = 128;
-constexpr int kTPT = 2;
+constexpr int kTPT = SHBIM_PAIR_TPT;   // targets per thread (register blocking)
 
 enum Kind { LDL = 0, LSL = 1, STO = 2 };
 

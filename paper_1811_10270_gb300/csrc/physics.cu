@@ -191,6 +191,7 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   double* uf = tv + 3 * NS;     // 6 NS
   double* gv = uf + 6 * NS;     // NS
   const double R = ph.R;
+  if (R != ctx->opts.R) ctx->geom_version++;
   ctx->opts.R = R;
   // (i) E_n
   if ((rc = shbim_electric_rhs(ctx, ph.E_u, ph.E_q, rhs_e, s))) return rc;

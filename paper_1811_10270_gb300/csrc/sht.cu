@@ -304,6 +304,7 @@ int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double*
     if (cudaMalloc(&ctx->sht_scratch, need * sizeof(double)) != cudaSuccess)
       return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc transform scratch");
     ctx->sht_scratch_elems = need;
+    ctx->geom_version++;  // captured operator graphs referenced the old scratch
   }
   const int N = 2 * g.q + 2;
   if ((N & 3) == 0) {

@@ -380,3 +380,35 @@ def test_near_pairs_and_corrected_operators_match_oracle(S):
     ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), out, S.OUT_GRID)
     assert rel_err(out.cpu().numpy(), np.concatenate(sysm.laplace_grid("ladl", sig))) > 1e-8
     ctx.close()
+
+
+def test_graph_replay_matches_direct_launches(S):
+    """GMRES with its operator applications replayed from CUDA graphs gives the solutions of
+    direct launches, in both precisions, and across a change of geometry."""
+    cfg = _two_drop_cfg(8, seed=6, gap=0.2)
+    rng = np.random.default_rng(9)
+    b_s = T(np.concatenate([inputs.random_density(8, rng, 3).ravel() for _ in cfg.drops]))
+    out = {}
+    for graphs in (False, True):
+        for precision in (S.FP64, S.FP32_COMP):
+            ctx = S.Context(precision=precision, R=cfg.R, gmres_tol=1e-10)
+            ctx.set_graphs(graphs)
+            sols = []
+            for shift in (0.0, 0.05):
+                xc = np.concatenate([d.xcoef.ravel() for d in cfg.drops])
+                xc[0] += shift          # moves drop 0 in x: a new geometry, graphs re-captured
+                ctx.set_drops([d.p for d in cfg.drops], T(xc), [d.lam for d in cfg.drops])
+                nc = b_s.numel() // 3
+                rhs = torch.empty(nc, device=DEV, dtype=torch.float64)
+                ctx.electric_rhs(cfg.E_u, rhs)
+                xe = torch.empty_like(rhs)
+                ie, _ = ctx.gmres_solve(S.SYS_ELECTRIC, rhs, xe)
+                xs = torch.empty_like(b_s)
+                is_, _ = ctx.gmres_solve(S.SYS_STOKES, b_s, xs)
+                sols.append((ie, is_, xe.cpu().numpy(), xs.cpu().numpy()))
+            out[(graphs, precision)] = sols
+            ctx.close()
+    for precision in (S.FP64, S.FP32_COMP):
+        for a, b in zip(out[(False, precision)], out[(True, precision)]):
+            assert a[0] == b[0] and a[1] == b[1]
+            assert rel_err(b[2], a[2]) < 1e-10 and rel_err(b[3], a[3]) < 1e-10
