@@ -62,6 +62,7 @@ class SurfaceGrid:
         self.theta, self.phi = th, ph
         B = basis2(p, th, ph)
         self.B = B
+        self._xcoef = np.asarray(xcoef)
         x, xt, xp, xtt, xtp, xpp = (np.asarray(xcoef) @ b for b in B)
         c = np.cross(xt.T, xp.T).T
         W = np.sqrt((c * c).sum(axis=0))
@@ -104,6 +105,25 @@ class SurfaceGrid:
         """Galerkin projection onto degree p by the regular rule of this grid."""
         return (np.asarray(vals) * self.omega) @ self.B[0].T
 
+    def laplace_beltrami(self, coef):
+        """Surface Laplacian of a scalar degree-p expansion in the (theta, phi) chart:
+        Delta_S f = g^{ab} (f_ab - Gamma^c_ab f_c), Gamma^c_ab = g^{cd} x_d . x_ab."""
+        c = np.asarray(coef)
+        ft, fp, ftt, ftp, fpp = (c @ self.B[k] for k in (1, 2, 3, 4, 5))
+        xc = self._xcoef
+        xtt, xtp, xpp = (xc @ self.B[k] for k in (3, 4, 5))
+        E, F, G, det = self.E, self.F, self.G, self.det
+        gtt, gtp, gpp = G / det, -F / det, E / det          # inverse metric
+        def christ(xab):
+            a = (self.xt * xab).sum(0)
+            b = (self.xp * xab).sum(0)
+            return gtt * a + gtp * b, gtp * a + gpp * b      # Gamma^theta_ab, Gamma^phi_ab
+        Ttt, Ptt = christ(xtt)
+        Ttp, Ptp = christ(xtp)
+        Tpp, Ppp = christ(xpp)
+        return (gtt * (ftt - Ttt * ft - Ptt * fp) + 2.0 * gtp * (ftp - Ttp * ft - Ptp * fp)
+                + gpp * (fpp - Tpp * ft - Ppp * fp))
+
 
 @dataclass
 class Params:
@@ -115,6 +135,7 @@ class Params:
     E_u: tuple = (0.0, 0.0, 1.0)
     E_q: float = 0.0            # linear field E_q (x, -y, 0) added to the uniform one
     gmres_tol: float = 1e-12
+    Pe: float = math.inf        # surfactant Peclet number (infinity: no diffusion)
 
 
 def langmuir(G, beta: float, x_s: float):
@@ -186,13 +207,34 @@ def grid_max_diff(acoefs, bcoefs, ps, ncomp):
     return m
 
 
+def diffusion_solve(xcoef, p: int, rhs, c: float, tol: float = 1e-13):
+    """Solve (I - c Delta_S) G = rhs in Galerkin form on the surface xcoef (degree 2p+1 grid),
+    by GMRES right-preconditioned with the sphere eigenvalues: M^{-1} = diag(1/(1 + c n(n+1)/a^2)),
+    a^2 = area / (4 pi). Returns the coefficients of G."""
+    sg = SurfaceGrid(xcoef, p, 2 * p + 1)
+    a2 = float((sg.omega * sg.J).sum()) / (4 * math.pi)
+    nn = np.array([n for n in range(p + 1) for _ in range(2 * n + 1)], dtype=np.float64)
+    minv = 1.0 / (1.0 + c * nn * (nn + 1) / a2)
+    A = lambda y: minv * y - c * sg.project(sg.laplace_beltrami(minv * y))
+    y, info = gmres.gmres(A, np.asarray(rhs), tol=tol)
+    return minv * y
+
+
 def step(xcoefs, gcoefs, ps, lams, dt: float, prm: Params, near: bool = True):
-    """One midpoint step (Algorithm 1, Pe = infinity). Returns new x, Gamma and the error
-    estimate err = max(err_drop, err_surfactant) against explicit Euler."""
+    """One midpoint step (Algorithm 1). Returns new x, Gamma and the error estimate
+    err = max(err_drop, err_surfactant) against explicit Euler. With a finite Peclet number the
+    surfactant follows the IMEX scheme of Algorithm 1: the half step is implicit in the
+    diffusion on the half-step surface, (I - dt/(2 Pe) Delta_S) G_half = G + dt/2 g_E, and the full
+    step adds dt (g_E + Delta_S G_half / Pe) evaluated at the half step."""
     u0, g0 = rates(xcoefs, gcoefs, ps, lams, prm, near=near)
     xh = [x + 0.5 * dt * u for x, u in zip(xcoefs, u0)]
     gh = [g + 0.5 * dt * r for g, r in zip(gcoefs, g0)]
+    if math.isfinite(prm.Pe):
+        gh = [diffusion_solve(x, p, g, 0.5 * dt / prm.Pe) for x, p, g in zip(xh, ps, gh)]
     u1, g1 = rates(xh, gh, ps, lams, prm, near=near)
+    if math.isfinite(prm.Pe):
+        g1 = [r + SurfaceGrid(x, p, 2 * p + 1).project(
+            SurfaceGrid(x, p, 2 * p + 1).laplace_beltrami(g)) / prm.Pe for r, x, p, g in zip(g1, xh, ps, gh)]
     xn = [x + dt * u for x, u in zip(xcoefs, u1)]
     gn = [g + dt * r for g, r in zip(gcoefs, g1)]
     xe = [x + dt * u for x, u in zip(xcoefs, u0)]

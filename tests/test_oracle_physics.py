@@ -105,3 +105,34 @@ def test_step_conserves_surfactant_and_converges_second_order():
         errs.append(err)
         assert abs(P.surfactant_mass(xn[0], gn[0], p) - m0) / m0 < 1e-4 * dt
     assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_laplace_beltrami_identities():
+    """Sphere of radius a: Delta_S Y_nm = -n(n+1)/a^2 Y_nm; any closed surface:
+    int Delta_S f dS = 0 and Delta_S x = -2 H n (position as a function on the surface)."""
+    p = 6
+    nn = np.array([n for n in range(p + 1) for _ in range(2 * n + 1)], dtype=float)
+    c = inputs.random_density(p, np.random.default_rng(1))[0]
+    for a in (1.0, 1.7):
+        sg = P.SurfaceGrid(inputs.sphere_coef(p, a, (0.2, 0.0, 0.0)), p, 13)
+        np.testing.assert_allclose(sg.project(sg.laplace_beltrami(c)), -nn * (nn + 1) / a ** 2 * c, atol=1e-12)
+    xc = inputs.perturbed_coef(p, np.random.default_rng(2), 1.0, (0, 0, 0), lmax=3)
+    sg = P.SurfaceGrid(xc, p, 13)
+    assert abs((sg.omega * sg.J * sg.laplace_beltrami(c)).sum()) < 1e-8
+    for k in range(3):
+        np.testing.assert_allclose(sg.laplace_beltrami(xc[k]), -2 * sg.H * sg.n[k], atol=1e-13)
+
+
+def test_imex_step_is_exact_for_pure_diffusion_on_a_sphere():
+    """No field, clean tension (beta = 0): a sphere stays at rest and Gamma only diffuses. The
+    IMEX step of Algorithm 1 then multiplies mode n by (1 - k/2)/(1 + k/2), k = dt n(n+1)/Pe."""
+    p = 5
+    g0 = 0.05 * inputs.random_density(p, np.random.default_rng(6))[0]
+    g0[0] = math.sqrt(4 * math.pi)
+    prm = P.Params(E_u=(0.0, 0.0, 0.0), beta=0.0, Pe=2.0)
+    dt = 0.1
+    xn, gn, err, _ = P.step([inputs.sphere_coef(p)], [g0], [p], [1.0], dt, prm)
+    nn = np.array([n for n in range(p + 1) for _ in range(2 * n + 1)], dtype=float)
+    k = dt * nn * (nn + 1) / prm.Pe
+    np.testing.assert_allclose(gn[0], g0 * (1 - k / 2) / (1 + k / 2), atol=1e-12)
+    np.testing.assert_allclose(xn[0], inputs.sphere_coef(p), atol=1e-12)
