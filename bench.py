@@ -123,6 +123,12 @@ def run_own(args):
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     S.lib()
+    if args.only == "pairs_at_scale":
+        print(json.dumps({"pairs_at_scale": pairs_at_scale(S, torch, dev)}))
+        return
+    if args.only in ("config3", "config5"):
+        print(json.dumps({args.only: batched_leg(S, torch, dev, args.only)}))
+        return
 
     cfg, f = workload(args.p)
     prec = S.FP32_COMP if args.precision == "fp32comp" else S.FP64
@@ -376,6 +382,89 @@ def learned_warm_start(S, torch, dev, p: int = 8, n_train: int = 600, n_test: in
             "mean_ms_to_1e-8": {k: v / n_test for k, v in ms.items()}}
 
 
+def batched_leg(S, torch, dev, name):
+    """The many-drop workloads on one GPU, each measured once with CUDA events:
+    config3 = 64 drops of degree 16/24/32/48 (uniform field), config5 = 16 drops of degree 64 in
+    the quadrupole field (x, -y, 0). Reports the geometry build (shapes, singular rows, near
+    pairs), one application of each layer operator in FP32 (compensated) and FP64 with the
+    algorithmic pair count sum_i N_t(i) * sum_j N_s(j), and the electric and Stokes solves to an
+    FP64 residual of 1e-8 from zero, mixed precision vs plain FP64; config5 also times one
+    mixed-precision IMEX step at Pe = 10 (Algorithm 1)."""
+    cfg = inputs.config3(seed=3) if name == "config3" else inputs.config5(seed=5)
+    ps = [d.p for d in cfg.drops]
+    lam = [d.lam for d in cfg.drops]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=1):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = None
+        for _ in range(reps):
+            r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps, r
+
+    ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8, gmres_restart=50)
+    x = torch.tensor(np.concatenate([d.xcoef.ravel() for d in cfg.drops]), device=dev)
+    g = torch.tensor(np.concatenate([d.gamma_coef for d in cfg.drops]), device=dev)
+    build_ms, _ = timed(lambda: ctx.set_drops(ps, x, lam))
+    nc, nt, ns = ctx.sizes()
+    pairs = nt * ns
+    rng = np.random.default_rng(1234)
+    sig = torch.tensor(rng.standard_normal(nc), device=dev)
+    f = torch.tensor(rng.standard_normal(3 * nc) / 4.0, device=dev)
+    out = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    res = {"workload": cfg.name, "drops": len(ps), "degrees": sorted(set(ps)), "ncoef": nc,
+           "targets": nt, "sources": ns, "pairs_per_application": pairs, "near_pairs": ctx.near_pairs(),
+           "geometry_build_ms": build_ms}
+    kinds = (("laplace_dl", lambda: ctx.eval_electric(S.LAPLACE_DL, sig, out[:nc])),
+             ("laplace_sl", lambda: ctx.eval_electric(S.LAPLACE_SL, sig, out[:nc])),
+             ("stokes_sd", lambda: ctx.eval_stokes(f, f, out)))
+    for pname, prec, reps in (("fp32comp", S.FP32_COMP, 3), ("fp64", S.FP64, 1)):
+        ctx.set_precision(prec)
+        res[pname] = {}
+        for kname, fn in kinds:
+            fn()                                    # first launch of a kind tunes its shape
+            ms, _ = timed(fn, reps)
+            res[pname][kname] = {"ms_per_application": ms, "pairs_per_s": pairs / (ms / 1e3)}
+    res["pair_shapes"] = [ctx.pair_shape(k)[:2] for k in range(3)]
+    # right-hand sides: the field term of the electric system; S[f] for Stokes
+    rhs_e = torch.empty(nc, device=dev, dtype=torch.float64)
+    ctx.electric_rhs(cfg.E_u, rhs_e, E_q=cfg.E_quad)
+    ctx.set_precision(S.FP64)
+    rhs_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    ctx.eval_stokes(f, None, rhs_s)
+    sol_e = torch.empty(nc, device=dev, dtype=torch.float64)
+    sol_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+    tts = {}
+    ms, (ie, oe, re_) = timed(lambda: ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs_e, sol_e, inner_tol=1e-5))
+    tts["electric_mixed"] = {"ms": ms, "inner_iters": ie, "outer": oe, "resid": re_}
+    ms, (is_, os_, rs) = timed(lambda: ctx.gmres_solve_refined(S.SYS_STOKES, rhs_s, sol_s, inner_tol=1e-5))
+    tts["stokes_mixed"] = {"ms": ms, "inner_iters": is_, "outer": os_, "resid": rs}
+    ctx.set_precision(S.FP64)
+    ms, (ie, re_) = timed(lambda: ctx.gmres_solve(S.SYS_ELECTRIC, rhs_e, sol_e))
+    tts["electric_fp64"] = {"ms": ms, "iters": ie, "resid": re_}
+    ms, (is_, rs) = timed(lambda: ctx.gmres_solve(S.SYS_STOKES, rhs_s, sol_s))
+    tts["stokes_fp64"] = {"ms": ms, "iters": is_, "resid": rs}
+    tts["speedup_mixed_vs_fp64"] = ((tts["electric_fp64"]["ms"] + tts["stokes_fp64"]["ms"])
+                                    / (tts["electric_mixed"]["ms"] + tts["stokes_mixed"]["ms"]))
+    res["time_to_1e-8"] = tts
+    if name == "config5":
+        ctx.set_precision(S.FP32_COMP)
+        ph = S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=tuple(cfg.E_u), E_q=cfg.E_quad,
+                    inner_tol=1e-5, Pe=10.0)
+        xo, go = torch.empty_like(x), torch.empty_like(g)
+        a0 = ctx.operator_applications()
+        ms, (err, its) = timed(lambda: ctx.step(ph, x, g, 1e-3, xo, go))
+        res["imex_step_pe10"] = {"ms": ms, "dt": 1e-3, "err_estimate": err, "gmres_iters": its,
+                                 "operator_applications": ctx.operator_applications() - a0}
+    ctx.close()
+    return res
+
+
 def time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u, reps=3):
     """Electric + Stokes solves to an FP64 relative residual of 1e-8 on the current geometry:
     mixed precision (FP32 compensated inner GMRES + FP64 refinement) vs plain FP64 GMRES."""
@@ -520,6 +609,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the 64-drop all-pairs measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--only", choices=["pairs_at_scale", "config3", "config5"],
+                    help="run one measurement leg alone and print its JSON (for profiling)")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for launch lists under a profiler)")
     args = ap.parse_args()

@@ -75,6 +75,10 @@ extern "C" {
 /* Linear systems for GMRES. */
 #define SHBIM_SYS_ELECTRIC 0        /* 1/2 s - (R-1)/(R+1) sum_j L_j[s] = b       (Eq. galerkin_En) */
 #define SHBIM_SYS_STOKES 1          /* (lam_i+1) u - sum_j (lam_j-1) D_j[u] = b   (Eq. main_eq)    */
+#define SHBIM_SYS_DIFFUSION 2       /* (I - c Delta_S) G = b on every drop (implicit surfactant
+                                       diffusion, Algorithm 1), c set by shbim_set_diffusion;
+                                       right-preconditioned by the sphere eigenvalues
+                                       1 + c n(n+1)/a_i^2, a_i^2 = area_i / (4 pi) */
 
 typedef struct shbim_ctx shbim_ctx;
 
@@ -172,8 +176,9 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
 /* GMRES on one of the Galerkin systems (the paper does not name its solver; this is
  * restarted GMRES with classical Gram-Schmidt applied twice, in FP64).
  * shbim_gmres_begin: set up the system `sys` with right-hand side rhs_dev (length n = ncoef
- *   for SHBIM_SYS_ELECTRIC, 3 ncoef for SHBIM_SYS_STOKES) and initial guess x0_dev (NULL
- *   means zero); computes the initial residual (reads one norm back to the host).
+ *   for SHBIM_SYS_ELECTRIC and SHBIM_SYS_DIFFUSION, 3 ncoef for SHBIM_SYS_STOKES) and initial
+ *   guess x0_dev (NULL means zero); computes the initial residual (reads one norm back to the
+ *   host). The diffusion system iterates on y = M x internally; x0_dev and x_dev are x.
  * shbim_gmres_step: one Arnoldi step (one operator application), restarting when the
  *   Krylov space is full; reads the new column's norms back to the host and returns
  *   SHBIM_CONTINUE, SHBIM_CONVERGED, or SHBIM_ERR_NOT_CONVERGED after gmres_maxiter steps.
@@ -202,6 +207,7 @@ typedef struct shbim_phys {
   double E_u[3];
   double E_q;
   double inner_tol;
+  double Pe;            /* surfactant Peclet number; 0 or infinity: no diffusion */
 } shbim_phys;
 
 /* Velocity and surfactant rate for the current drop shapes (steps i-vi of Section 2):
@@ -209,7 +215,7 @@ typedef struct shbim_phys {
  * interfacial forces on each drop's degree 2p+1 grid (products de-aliased by projection to
  * degree p), solves the Stokes system with right-hand side -sum_j S_j[f/Ca_E - f^E] and forms
  * the surfactant rate -Gamma div_S u of nodes that move with u (Eq. surfactant0, material
- * form, no diffusion).
+ * form, no diffusion; Pe is not used here).
  *   gamma_dev  ncoef coefficients of Gamma
  *   u_dev      3 ncoef velocity coefficients (out);  gE_dev  ncoef rate coefficients (out)
  *   iters_host GMRES iterations of the electric and Stokes solves (2 ints, may be NULL)
@@ -217,7 +223,17 @@ typedef struct shbim_phys {
 int shbim_rates(shbim_ctx* ctx, const shbim_phys* phys, const double* gamma_dev, double* u_dev,
                 double* gE_dev, int* iters_host, void* stream);
 
-/* One time step of Algorithm 1 (midpoint rule for x, explicit stage for Gamma):
+/* Surface Laplacian Delta_S (Laplace-Beltrami operator, the diffusion term of Eq. surfactant0)
+ * of a scalar on every drop of the current shapes, in Galerkin form:
+ * Delta_S f = g^{ab} (f_ab - Gamma^c_ab f_c) in the (theta, phi) chart, formed on each drop's
+ * degree 2p+1 grid and projected to degree p by the regular rule.
+ *   coef_dev, out_dev  ncoef coefficients each (device, caller-owned, must not alias) */
+int shbim_laplace_beltrami(shbim_ctx* ctx, const double* coef_dev, double* out_dev, void* stream);
+/* Coefficient c >= 0 of the diffusion system SHBIM_SYS_DIFFUSION, (I - c Delta_S) G = b
+ * (SHBIM_ERR_ARG for negative or non-finite c). shbim_step sets it to dt / (2 Pe). */
+int shbim_set_diffusion(shbim_ctx* ctx, double c);
+
+/* One time step of Algorithm 1 (midpoint rule for x, IMEX stages for Gamma):
  * rates at (x, Gamma), half step, rates at the half step, full step
  *   x_out = x + dt u(t+dt/2),  Gamma_out = Gamma + dt g_E(t+dt/2),
  * and the error estimate err = dt max(|u(t+dt/2) - u(t)|, |g_E(t+dt/2) - g_E(t)|) (grid max
@@ -225,6 +241,9 @@ int shbim_rates(shbim_ctx* ctx, const shbim_phys* phys, const double* gamma_dev,
  * must have been set with shbim_set_drops; x_dev (3 ncoef) replaces the shapes. Outputs must
  * not alias the inputs, so the caller can reject the step (adaptive dt: accept if err < tol,
  * then dt <- dt (0.9 tol / err)^(1/2)). iters_host: 4 GMRES counts (may be NULL).
+ * With 0 < Pe < infinity the surfactant follows the IMEX scheme of Algorithm 1: the half step
+ * solves (I - dt/(2 Pe) Delta_S) Gamma_half = Gamma + dt/2 g_E(t) on the half-step surface and
+ * the full step uses g_E(t+dt/2) + Delta_S Gamma_half / Pe.
  * After the call the context holds the geometry of the half step. */
 int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, const double* gamma_dev,
                double dt, double* x_out_dev, double* gamma_out_dev, double* err_host, int* iters_host,
@@ -234,7 +253,8 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, cons
  * r = b - A x with FP64 all-pairs sums, solves A d = r by GMRES with FP32 compensated sums to
  * the relative tolerance inner_tol (e.g. 1e-5), and updates x += d, until the FP64 relative
  * residual reaches gmres_tol or max_outer steps were taken (SHBIM_ERR_NOT_CONVERGED).
- * The context's precision setting is restored on return. Reports the total inner Arnoldi
+ * Only the electric and Stokes systems (the diffusion system has no all-pairs sums;
+ * SHBIM_ERR_ARG). The context's precision setting is restored on return. Reports the total inner Arnoldi
  * steps, the outer steps and the final FP64 relative residual (each pointer may be NULL). */
 int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                               double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
@@ -302,6 +322,23 @@ int64_t shbim_launch_count(shbim_ctx* ctx);
  * staging buffers. Kernel timing (shbim_set_timing) disables the replay while it is on. If a
  * capture fails, the context falls back to direct launches. */
 int shbim_set_graphs(shbim_ctx* ctx, int on);
+
+/* Launch-shape autotuning of the FP32 all-pairs kernels (on by default): on the first launch of
+ * each kernel kind for a drop layout, every register blocking (1, 2 or 4 targets per thread)
+ * with source-split counts around the layout's default is timed and the fastest kept. The shape
+ * changes the FP32 summation order, so two contexts may differ at rounding level; with the
+ * autotuner off every layout uses 1 target per thread and the default split count, which makes
+ * FP32 results reproducible across contexts. Takes effect immediately. */
+int shbim_set_autotune(shbim_ctx* ctx, int on);
+
+/* Launch shape of the FP32 all-pairs kernel of one kind (0 Laplace DL, 1 Laplace SL, 2 Stokes)
+ * for the current layout. shbim_pair_shape writes targets per thread and the split count (either
+ * pointer may be NULL) and returns 1 once the shape is fixed (tuned or set), 0 before, or an
+ * error code. shbim_set_pair_shape fixes it (tpt in {1, 2, 4}, 1 <= splits <= the layout's
+ * capacity, SHBIM_ERR_ARG otherwise) until the next shbim_set_drops with a new layout; it lets
+ * a caller reuse a shape tuned earlier. */
+int shbim_pair_shape(shbim_ctx* ctx, int kind, int* tpt_host, int* splits_host);
+int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits);
 
 /* Number of layer-operator applications (calls of the electric or Stokes operator, including
  * those made inside GMRES and the time step) since the context was created. */

@@ -116,6 +116,21 @@ def config2(p: int = 32, seed: int = 0, gap: float = 0.1) -> Config:
                   E_u=np.array([0.0, 0.0, 1.0]), meta={"seed": seed})
 
 
+def _place(rng: np.random.Generator, radii, box: float, gap: float):
+    """Centres uniform in the box (each sphere inside it), rejection-sampled so that nominal
+    spheres are at least `gap` apart."""
+    centres = []
+    for i in range(len(radii)):
+        for _ in range(100000):
+            c = rng.uniform(-box / 2 + radii[i], box / 2 - radii[i], size=3)
+            if all(np.linalg.norm(c - centres[j]) >= radii[i] + radii[j] + gap for j in range(len(centres))):
+                centres.append(c)
+                break
+        else:
+            raise RuntimeError("could not place drop %d" % i)
+    return centres
+
+
 def config3(seed: int = 3, n_drops: int = 64, box: float = 12.0, min_gap: float = 0.2,
             degrees=(16, 24, 32, 48), slack: float = 0.2) -> Config:
     """Many drops of uneven degree in a cubic box; centres by rejection sampling so that the
@@ -123,17 +138,7 @@ def config3(seed: int = 3, n_drops: int = 64, box: float = 12.0, min_gap: float 
     rng = np.random.default_rng(seed)
     ps = rng.choice(np.array(degrees), size=n_drops)
     radii = rng.uniform(0.8, 1.2, size=n_drops)
-    centres = []
-    for i in range(n_drops):
-        for _ in range(100000):
-            c = rng.uniform(-box / 2 + radii[i], box / 2 - radii[i], size=3)
-            ok = all(np.linalg.norm(c - centres[j]) >= radii[i] + radii[j] + min_gap + slack
-                     for j in range(len(centres)))
-            if ok:
-                centres.append(c)
-                break
-        else:
-            raise RuntimeError("could not place drop %d" % i)
+    centres = _place(rng, radii, box, min_gap + slack)
     drops = []
     for i in range(n_drops):
         p = int(ps[i])
@@ -142,6 +147,20 @@ def config3(seed: int = 3, n_drops: int = 64, box: float = 12.0, min_gap: float 
                           centre=np.asarray(centres[i]), radius=float(radii[i])))
     return Config("batched %d drops p in %s seed=%d" % (n_drops, list(degrees), seed), drops,
                   R=2.0, Q=0.5, E_u=np.array([0.0, 0.0, 1.0]), meta={"seed": seed})
+
+
+def config5(seed: int = 5, n_drops: int = 16, p: int = 64, box: float = 8.0, min_gap: float = 0.2,
+            slack: float = 0.2) -> Config:
+    """16 unit drops of degree 64 (perturbed as above) in an 8^3 box, nominal gaps >= min_gap +
+    slack, lambda = 1, R = 4.5, Q = 5, quadrupole field E = (x, -y, 0), surfactant as above
+    (the Peclet number 10 is a time-step parameter, not part of the inputs)."""
+    rng = np.random.default_rng(seed)
+    radii = np.ones(n_drops)
+    centres = _place(rng, radii, box, min_gap + slack)
+    drops = [Drop(p=p, xcoef=perturbed_coef(p, rng, 1.0, centres[i]), gamma_coef=gamma_random(p, rng),
+                  lam=1.0, centre=np.asarray(centres[i]), radius=1.0) for i in range(n_drops)]
+    return Config("%d drops p=%d quadrupole field seed=%d" % (n_drops, p, seed), drops, R=4.5, Q=5.0,
+                  E_u=np.array([0.0, 0.0, 0.0]), E_quad=1.0, meta={"seed": seed})
 
 
 def random_density(p: int, rng: np.random.Generator, ncomp: int = 1, decay: float = 1.0) -> np.ndarray:

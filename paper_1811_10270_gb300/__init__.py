@@ -8,6 +8,7 @@ current torch stream is passed to the library.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -25,6 +26,7 @@ GRID_BASE = 0
 GRID_UP = 1
 SYS_ELECTRIC = 0
 SYS_STOKES = 1
+SYS_DIFFUSION = 2
 CONTINUE = 0
 CONVERGED = 1
 
@@ -37,7 +39,8 @@ EXPORTS = [
     "shbim_rates", "shbim_step", "shbim_operator_applications", "shbim_set_near", "shbim_near_pairs",
     "shbim_mlp_create", "shbim_mlp_destroy", "shbim_mlp_set_layer", "shbim_mlp_get_layer",
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
-    "shbim_set_graphs",
+    "shbim_set_graphs", "shbim_laplace_beltrami", "shbim_set_diffusion",
+    "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape",
 ]
 NOALLOC_MAX_TARGETS = 1 << 21
 K_SELF_WEIGHTS = 0
@@ -59,15 +62,17 @@ class Opts(ctypes.Structure):
 
 
 class Phys(ctypes.Structure):
-    """shbim_phys: R, Q, Ca_E, Langmuir beta and x_s, far field E_u + E_q (x, -y, 0), and the
-    inner tolerance of the mixed-precision solves."""
+    """shbim_phys: R, Q, Ca_E, Langmuir beta and x_s, far field E_u + E_q (x, -y, 0), the
+    inner tolerance of the mixed-precision solves and the surfactant Peclet number (0 or
+    infinity: no diffusion)."""
     _fields_ = [("R", ctypes.c_double), ("Q", ctypes.c_double), ("Ca_E", ctypes.c_double),
                 ("beta", ctypes.c_double), ("x_s", ctypes.c_double), ("E_u", ctypes.c_double * 3),
-                ("E_q", ctypes.c_double), ("inner_tol", ctypes.c_double)]
+                ("E_q", ctypes.c_double), ("inner_tol", ctypes.c_double), ("Pe", ctypes.c_double)]
 
 
-def phys(R=2.0, Q=0.5, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.0, 1.0), E_q=0.0, inner_tol=1e-5):
-    return Phys(R, Q, Ca_E, beta, x_s, (ctypes.c_double * 3)(*E_u), E_q, inner_tol)
+def phys(R=2.0, Q=0.5, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.0, 1.0), E_q=0.0, inner_tol=1e-5,
+         Pe=math.inf):
+    return Phys(R, Q, Ca_E, beta, x_s, (ctypes.c_double * 3)(*E_u), E_q, inner_tol, Pe)
 
 
 _lib = None
@@ -110,6 +115,11 @@ def lib():
         "shbim_operator_applications": (i64, [vp]),
         "shbim_set_near": (i32, [vp, i32]),
         "shbim_set_graphs": (i32, [vp, i32]),
+        "shbim_set_autotune": (i32, [vp, i32]),
+        "shbim_pair_shape": (i32, [vp, i32, P(i32), P(i32)]),
+        "shbim_set_pair_shape": (i32, [vp, i32, i32, i32]),
+        "shbim_laplace_beltrami": (i32, [vp, vp, vp, vp]),
+        "shbim_set_diffusion": (i32, [vp, dp]),
         "shbim_mlp_create": (i32, [i32, P(ctypes.c_int32), i32, P(vp)]),
         "shbim_mlp_destroy": (i32, [vp]),
         "shbim_mlp_set_layer": (i32, [vp, i32, vp, vp]),
@@ -295,6 +305,29 @@ class Context:
                                        _ptr(x_out), _ptr(gamma_out), ctypes.byref(err), it, _stream()),
                     "shbim_step")
         return err.value, list(it)
+
+    def laplace_beltrami(self, coef, out):
+        self._check(self._L.shbim_laplace_beltrami(self._h, _ptr(coef), _ptr(out), _stream()),
+                    "shbim_laplace_beltrami")
+
+    def set_diffusion(self, c: float):
+        self._check(self._L.shbim_set_diffusion(self._h, float(c)), "shbim_set_diffusion")
+
+    def set_autotune(self, on: bool):
+        self._check(self._L.shbim_set_autotune(self._h, 1 if on else 0), "shbim_set_autotune")
+
+    def pair_shape(self, kind: int):
+        """(targets per thread, source splits, fixed) of the FP32 pair kernel `kind`."""
+        t = ctypes.c_int32()
+        sp = ctypes.c_int32()
+        rc = self._L.shbim_pair_shape(self._h, int(kind), ctypes.byref(t), ctypes.byref(sp))
+        if rc < 0:
+            self._check(rc, "shbim_pair_shape")
+        return t.value, sp.value, rc == 1
+
+    def set_pair_shape(self, kind: int, tpt: int, splits: int):
+        self._check(self._L.shbim_set_pair_shape(self._h, int(kind), int(tpt), int(splits)),
+                    "shbim_set_pair_shape")
 
     def set_graphs(self, on: bool):
         self._check(self._L.shbim_set_graphs(self._h, 1 if on else 0), "shbim_set_graphs")

@@ -139,6 +139,7 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->gm.h);
   cudaFree(ctx->gm.Av);
   cudaFree(ctx->gm.diag);
+  cudaFree(ctx->gm.tmp);
   cudaFree(ctx->gm.y);
   {
     auto& N = ctx->near;
@@ -154,6 +155,7 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->phys.buf);
   cudaFree(ctx->phys.grid);
   cudaFree(ctx->phys.state);
+  cudaFree(ctx->phys.lb);
   cudaFree(ctx->gm.xr);
   cudaFree(ctx->gm.rr);
   cudaFree(ctx->gm.dr);
@@ -183,6 +185,33 @@ int shbim_set_R(shbim_ctx* ctx, double R) {
 int64_t shbim_launch_count(shbim_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 int64_t shbim_operator_applications(shbim_ctx* ctx) { return ctx ? ctx->applications : -1; }
+
+int shbim_set_autotune(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->autotune = on != 0;
+  for (auto& c : ctx->pair_cfg) c = shbim_ctx::PairCfg{1, ctx->pair_splits, !ctx->autotune};
+  ctx->geom_version++;  // captured graphs hold the old launch shapes
+  return SHBIM_OK;
+}
+
+int shbim_pair_shape(shbim_ctx* ctx, int kind, int* tpt_host, int* splits_host) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  if (tpt_host) *tpt_host = ctx->pair_cfg[kind].tpt;
+  if (splits_host) *splits_host = ctx->pair_cfg[kind].splits;
+  return ctx->pair_cfg[kind].tuned ? 1 : 0;
+}
+
+int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  if (tpt != 1 && tpt != 2 && tpt != 4) return fail(ctx, SHBIM_ERR_ARG, "targets per thread must be 1, 2 or 4");
+  if (splits < 1 || splits > ctx->split_max) return fail(ctx, SHBIM_ERR_ARG, "split count out of range");
+  ctx->pair_cfg[kind] = shbim_ctx::PairCfg{tpt, splits, true};
+  ctx->geom_version++;
+  return SHBIM_OK;
+}
 
 int shbim_set_graphs(shbim_ctx* ctx, int on) {
   if (!ctx) return SHBIM_ERR_ARG;
@@ -287,8 +316,10 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // about 8 CTAs per SM at 2 targets per thread (2 CTAs per tile)
     const int64_t want = (int64_t)nsm * 8;
-    int64_t splits = (want + (int64_t)ctx->tiles.size() - 1) / (int64_t)ctx->tiles.size();
+    const int64_t ctas = 2 * (int64_t)ctx->tiles.size();
+    int64_t splits = (want + ctas - 1) / ctas;
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, min_other / 128));
     ctx->pair_splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, 256));
     if ((rc = dalloc(ctx, &ctx->tiles_dev, ctx->tiles.size(), "tiles"))) return rc;
@@ -297,7 +328,7 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
     ctx->split_max = (int)std::max<int64_t>(1, std::min<int64_t>(4 * splits, std::max<int64_t>(1, min_other / 64)));
     ctx->split_max = std::min(ctx->split_max, 256);
     ctx->pair_splits = std::min(ctx->pair_splits, ctx->split_max);
-    ctx->splits_tuned = false;
+    for (auto& c : ctx->pair_cfg) c = shbim_ctx::PairCfg{1, ctx->pair_splits, !ctx->autotune};
     if ((rc = dalloc(ctx, &ctx->part, (size_t)ctx->split_max * 3 * to, "pair partials"))) return rc;
   }
   return rebuild_geometry(ctx, xcoef_dev, s);

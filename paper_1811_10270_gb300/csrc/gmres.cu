@@ -7,6 +7,10 @@
 // device-to-host read of the new Hessenberg column per step.
 //   electric: A s = 1/2 s - (R-1)/(R+1) L[s]           (Eq. galerkin_En)
 //   Stokes:   A u = (lam_i + 1) u - sum_j (lam_j-1) D_j[u]   (Eq. main_eq, Galerkin form)
+//   diffusion: (I - c Delta_S) G = b on every drop (implicit surfactant diffusion of Algorithm 1),
+//             solved right-preconditioned, A y = M^{-1} y - c P[Delta_S M^{-1} y], G = M^{-1} y, with
+//             M^{-1} = diag(1/(1 + c n(n+1)/a_i^2)), a_i^2 = area_i/(4 pi): the exact inverse on a
+//             sphere of radius a_i, where Delta_S Y_nm = -n(n+1)/a^2 Y_nm.
 #include <algorithm>
 #include <cmath>
 
@@ -100,10 +104,55 @@ __global__ void k_fill_diag(double* __restrict__ diag, const DropDev* __restrict
   diag[e] = drops[i].lam + 1.0;
 }
 
+// Diffusion preconditioner: one block per drop sums the area (weights omega J of the source
+// grid) and writes 1/(1 + c n(n+1)/a^2) for the drop's coefficients (index n*n + n + m).
+__global__ void k_fill_minv(double* __restrict__ minv, const DropDev* __restrict__ drops,
+                            const double* __restrict__ src, int64_t nsource, double c) {
+  const DropDev D = drops[blockIdx.x];
+  double a = 0.0;
+  for (int64_t e = threadIdx.x; e < D.ns; e += blockDim.x) a += src[6 * nsource + D.src_off + e];
+  a = block_sum(a);
+  __shared__ double area;
+  if (threadIdx.x == 0) area = a;
+  __syncthreads();
+  const double a2 = area / (4.0 * 3.14159265358979323846);
+  for (int k = threadIdx.x; k < D.nc; k += blockDim.x) {
+    int n = (int)sqrt((double)k);
+    while (n * n > k) --n;
+    while ((n + 1) * (n + 1) <= k) ++n;
+    minv[D.coef_off + k] = 1.0 / (1.0 + c * n * (n + 1.0) / a2);
+  }
+}
+
+__global__ void k_mul(double* __restrict__ y, const double* __restrict__ a, const double* __restrict__ b,
+                      int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = a[e] * b[e];
+}
+
+__global__ void k_div(double* __restrict__ y, const double* __restrict__ a, const double* __restrict__ b,
+                      int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = a[e] / b[e];
+}
+
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+inline int64_t system_size(const shbim_ctx* ctx, int sys) {
+  return sys == SHBIM_SYS_STOKES ? 3 * ctx->ncoef : ctx->ncoef;
+}
 
 int matvec_eager(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
   auto& G = ctx->gm;
+  if (G.sys == SHBIM_SYS_DIFFUSION) {
+    k_mul<<<nb(G.n), 256, 0, s>>>(G.tmp, G.diag, v, G.n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_mul");
+    int rc = laplace_beltrami(ctx, G.tmp, G.Av, s);
+    if (rc) return rc;
+    k_system<<<nb(G.n), 256, 0, s>>>(G.diag, G.offdiag, v, G.Av, out, G.n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_system");
+    return SHBIM_OK;  // not a layer-operator application
+  }
   int rc = G.sys == SHBIM_SYS_ELECTRIC
                ? shbim_eval_electric(ctx, SHBIM_LAPLACE_DL, v, G.Av, SHBIM_OUT_COEF, s)
                : shbim_eval_stokes(ctx, nullptr, v, G.Av, SHBIM_OUT_COEF, s);
@@ -170,7 +219,7 @@ int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) 
   SHBIM_CUDA(ctx, cudaGraphLaunch(GR.exec, s));
   SHBIM_CUDA(ctx, cudaMemcpyAsync(out, GR.out, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   ctx->launches += GR.kernels;
-  ctx->applications += 1;
+  if (G.sys != SHBIM_SYS_DIFFUSION) ctx->applications += 1;
   return SHBIM_OK;
 }
 
@@ -243,18 +292,19 @@ extern "C" {
 int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev, void* stream) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
-  if (sys != SHBIM_SYS_ELECTRIC && sys != SHBIM_SYS_STOKES) return fail(ctx, SHBIM_ERR_ARG, "bad system");
+  if (sys != SHBIM_SYS_ELECTRIC && sys != SHBIM_SYS_STOKES && sys != SHBIM_SYS_DIFFUSION)
+    return fail(ctx, SHBIM_ERR_ARG, "bad system");
   if (!rhs_dev) return fail(ctx, SHBIM_ERR_ARG, "null right-hand side");
   cudaStream_t s = (cudaStream_t)stream;
   auto& G = ctx->gm;
-  const int64_t n = sys == SHBIM_SYS_ELECTRIC ? ctx->ncoef : 3 * ctx->ncoef;
+  const int64_t n = system_size(ctx, sys);
   const int m = ctx->opts.gmres_restart;
   if (n * (m + 1) > G.cap || m != G.m || !G.V) {
     SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
     cudaFree(G.V); cudaFree(G.w); cudaFree(G.x); cudaFree(G.b); cudaFree(G.h); cudaFree(G.Av);
-    cudaFree(G.diag); cudaFree(G.y);
+    cudaFree(G.diag); cudaFree(G.tmp); cudaFree(G.y);
     if (G.h_host) cudaFreeHost(G.h_host);
-    G.V = G.w = G.x = G.b = G.h = G.Av = G.diag = G.y = G.h_host = nullptr;
+    G.V = G.w = G.x = G.b = G.h = G.Av = G.diag = G.tmp = G.y = G.h_host = nullptr;
     const int64_t ncap = std::max<int64_t>(n, 3 * ctx->ncoef);
     if (cudaMalloc(&G.V, (size_t)ncap * (m + 1) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.w, ncap * sizeof(double)) != cudaSuccess ||
@@ -262,6 +312,7 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
         cudaMalloc(&G.b, ncap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.Av, ncap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.diag, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.tmp, ncap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.y, (m + 2) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.h, 2 * (m + 2) * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&G.h_host, 2 * (m + 2) * sizeof(double)) != cudaSuccess)
@@ -279,11 +330,20 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
   G.total = 0;
   G.k = 0;
   const double R = ctx->opts.R;
-  G.offdiag = sys == SHBIM_SYS_ELECTRIC ? -(R - 1.0) / (R + 1.0) : -1.0;
-  k_fill_diag<<<nb(n), 256, 0, s>>>(G.diag, ctx->drops_dev, ctx->n_drops, sys, n);
-  SHBIM_CHECK_LAUNCH(ctx, "k_fill_diag");
+  if (sys == SHBIM_SYS_DIFFUSION) {
+    G.offdiag = -ctx->diff_c;
+    k_fill_minv<<<ctx->n_drops, 256, 0, s>>>(G.diag, ctx->drops_dev, ctx->geo.src, ctx->nsource, ctx->diff_c);
+    SHBIM_CHECK_LAUNCH(ctx, "k_fill_minv");
+  } else {
+    G.offdiag = sys == SHBIM_SYS_ELECTRIC ? -(R - 1.0) / (R + 1.0) : -1.0;
+    k_fill_diag<<<nb(n), 256, 0, s>>>(G.diag, ctx->drops_dev, ctx->n_drops, sys, n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_fill_diag");
+  }
   SHBIM_CUDA(ctx, cudaMemcpyAsync(G.b, rhs_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  if (x0_dev) {
+  if (x0_dev && sys == SHBIM_SYS_DIFFUSION) {  // the iterate is y = M x
+    k_div<<<nb(n), 256, 0, s>>>(G.x, x0_dev, G.diag, n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_div");
+  } else if (x0_dev) {
     SHBIM_CUDA(ctx, cudaMemcpyAsync(G.x, x0_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
     SHBIM_CUDA(ctx, cudaMemsetAsync(G.x, 0, n * sizeof(double), s));
@@ -374,7 +434,12 @@ int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* str
   cudaStream_t s = (cudaStream_t)stream;
   int rc = update_x(ctx, s);
   if (rc) return rc;
-  SHBIM_CUDA(ctx, cudaMemcpyAsync(x_dev, G.x, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (G.sys == SHBIM_SYS_DIFFUSION) {
+    k_mul<<<nb(G.n), 256, 0, s>>>(x_dev, G.diag, G.x, G.n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_mul");
+  } else {
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(x_dev, G.x, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   if (iters_host) *iters_host = G.total;
   return SHBIM_OK;
 }
@@ -409,6 +474,14 @@ int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
   return SHBIM_OK;
 }
 
+int shbim_set_diffusion(shbim_ctx* ctx, double c) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (!(c >= 0.0) || !std::isfinite(c)) return fail(ctx, SHBIM_ERR_ARG, "diffusion coefficient must be >= 0");
+  if (c != ctx->diff_c) ctx->geom_version++;  // the factor is a parameter of captured graphs
+  ctx->diff_c = c;
+  return SHBIM_OK;
+}
+
 }  // extern "C"
 
 namespace shbim {
@@ -430,7 +503,7 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
   if (!(inner_tol > 0.0 && inner_tol < 1.0) || max_outer < 1)
     return fail(ctx, SHBIM_ERR_ARG, "need 0 < inner_tol < 1 and max_outer >= 1");
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t n = sys == SHBIM_SYS_ELECTRIC ? ctx->ncoef : 3 * ctx->ncoef;
+  const int64_t n = system_size(ctx, sys);
   auto& G = ctx->gm;
   // outer buffers (sized for the larger system)
   if (!G.xr) {

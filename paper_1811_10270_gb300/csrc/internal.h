@@ -112,9 +112,16 @@ struct shbim_ctx {
   std::vector<shbim::PairTile> tiles;
   shbim::PairTile* tiles_dev = nullptr;
   shbim::DropDev* drops_dev = nullptr;
-  int pair_splits = 1;
+  int pair_splits = 1;            // default source-split count of the layout
   int split_max = 1;              // capacity of the partial-sum buffer in splits
-  bool splits_tuned = false;      // autotuned on the first FP32 pair launch of a layout
+  // shape of the FP32 all-pairs launches per kernel kind (Laplace DL, Laplace SL, Stokes):
+  // targets per thread and source splits, autotuned on the first launch of a layout
+  struct PairCfg {
+    int tpt = 1;
+    int splits = 1;
+    bool tuned = false;
+  } pair_cfg[3];
+  bool autotune = true;           // off: every layout keeps the default launch shape
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
   float* dens_up32 = nullptr;     // [3][nsource] source strengths (FP32)
@@ -140,12 +147,13 @@ struct shbim_ctx {
     double* h = nullptr;        // [2][m+2] device dots
     double* h_host = nullptr;   // pinned
     double* Av = nullptr;       // [n] operator output
-    double* diag = nullptr;     // [n] identity part of the system
+    double* diag = nullptr;     // [n] identity part of the system (diffusion: M^{-1})
     double* y = nullptr;        // [m] least-squares solution uploaded for x updates
     double offdiag = 0.0;       // factor of the layer operator in the system
     double* xr = nullptr;       // [n] refinement: outer iterate
     double* rr = nullptr;       // [n] refinement: outer residual
     double* dr = nullptr;       // [n] refinement: correction
+    double* tmp = nullptr;      // [n] diffusion system: preconditioned vector M^{-1} v
     std::vector<double> H;      // (m+1) x m, column-major k*(m+1)+i
     std::vector<double> cs, sn, g;
     int k = 0;                  // Arnoldi steps in the current cycle
@@ -179,6 +187,8 @@ struct shbim_ctx {
     size_t grid_cap = 0;
     double* state = nullptr;
     size_t state_cap = 0;
+    double* lb = nullptr;       // surface Laplacian workspace [6][nsource]
+    size_t lb_cap = 0;
   } phys;
   int64_t launches = 0;
   int64_t applications = 0;
@@ -195,7 +205,8 @@ struct shbim_ctx {
     int64_t version = -1;
     int64_t kernels = 0;   // kernel nodes per replay
     bool warm = false;
-  } graphs[4];
+  } graphs[6];
+  double diff_c = 0.0;            // coefficient of the diffusion system
   // optional per-class kernel timing
   bool timing = false;
   struct TimedRange {
@@ -274,6 +285,9 @@ int geometry_kernel(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, con
                     int64_t ld, int64_t off, cudaStream_t s);
 int geometry_kernel32(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
                       float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s);
+
+// ---- surface Laplacian (physics.cu)
+int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream_t s);
 
 // ---- shape-dependent state for an unchanged layout (api.cu)
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);

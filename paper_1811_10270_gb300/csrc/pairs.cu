@@ -3,10 +3,12 @@
 // stresslet (Eqs. GandT, op_stokes). Same-drop pairs are excluded: those targets get the
 // singular self rows instead.
 //
-// Work decomposition: a CTA owns a tile of targets of one drop (128 threads x TPT targets,
-// register-blocked) and one split of the other drops' sources; sources are staged through
-// shared memory in tiles of 256 and read as warp-wide broadcasts. Each split writes its own
-// partial sums; a second kernel adds the splits in a fixed order (deterministic).
+// Work decomposition: the target list is cut into tiles of 512 targets of one drop; a CTA owns
+// 128 threads x TPT targets of a tile (register blocking, TPT = 1, 2 or 4, so a tile takes 4/TPT
+// CTAs) and one split of the other drops' sources; sources are staged through shared memory in
+// tiles of 256 and read as warp-wide broadcasts. Each split writes its own partial sums; a second
+// kernel adds the splits in a fixed order (deterministic). TPT and the split count are chosen per
+// kernel kind and drop layout by timing the candidates on the first FP32 launch (autotune).
 //
 // FP32 path: sources are stored relative to their drop centre in FP32; for every (target,
 // source drop) the target offset x0 - c_j is formed in FP64 and kept as an unevaluated FP32
@@ -21,12 +23,10 @@ namespace shbim {
 
 namespace {
 
-#ifndef SHBIM_PAIR_TPT
-#define SHBIM_PAIR_TPT 2
-#endif
 constexpr int kTile = 256;
 constexpr int kThreads = 128;
-constexpr int kTPT = SHBIM_PAIR_TPT;   // targets per thread (register blocking)
+constexpr int kMaxTPT = 4;                         // largest register blocking
+constexpr int kTileTargets = kThreads * kMaxTPT;   // targets per tile of the tile list
 
 enum Kind { LDL = 0, LSL = 1, STO = 2 };
 
@@ -54,7 +54,20 @@ __device__ __forceinline__ SrcRange drop_range(const DropDev& Di, const DropDev&
   return r;
 }
 
-template <int KIND>
+// blockIdx.x = tile * (kMaxTPT / TPT) + sub-tile; returns false for a sub-tile past the tile's
+// last target (the whole CTA then exits before any barrier)
+template <int TPT>
+__device__ __forceinline__ bool sub_tile(const PairTile* __restrict__ tiles, PairTile& t) {
+  constexpr int SUB = kMaxTPT / TPT;
+  const PairTile tile = tiles[blockIdx.x / SUB];
+  const int off = (int)(blockIdx.x % SUB) * kThreads * TPT;
+  t.drop = tile.drop;
+  t.t0 = tile.t0 + off;
+  t.nt = tile.nt - off;
+  return t.nt > 0;
+}
+
+template <int KIND, int kTPT>
 __global__ void __launch_bounds__(kThreads)
 k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
           const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ src32,
@@ -64,7 +77,8 @@ k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
   __shared__ float4 sh0[kTile];
   __shared__ float4 sh1[KIND == STO ? kTile : 1];
   __shared__ float4 sh2[KIND == STO ? kTile : 1];
-  const PairTile tile = tiles[blockIdx.x];
+  PairTile tile;
+  if (!sub_tile<kTPT>(tiles, tile)) return;
   const int i = tile.drop;
   const DropDev Di = drops[i];
   const int64_t other = nsource - Di.ns;
@@ -196,7 +210,7 @@ k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
   }
 }
 
-template <int KIND>
+template <int KIND, int kTPT>
 __global__ void __launch_bounds__(kThreads)
 k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
           const double* __restrict__ tgt, int64_t ntarget, const double* __restrict__ src,
@@ -205,7 +219,8 @@ k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
   constexpr int NC = (KIND == STO) ? 3 : 1;
   constexpr int NF = (KIND == STO) ? 12 : 4;
   __shared__ double sh[NF][kTile];
-  const PairTile tile = tiles[blockIdx.x];
+  PairTile tile;
+  if (!sub_tile<kTPT>(tiles, tile)) return;
   const int i = tile.drop;
   const DropDev Di = drops[i];
   const int64_t other = nsource - Di.ns;
@@ -301,68 +316,90 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int6
   out[e] += s;
 }
 
-template <int KIND>
-void launch_raw(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
-  dim3 grid((unsigned)ctx->tiles.size(), ctx->pair_splits);
+template <int KIND, int TPT>
+void launch_shape(shbim_ctx* ctx, bool has_f, bool has_u, int splits, cudaStream_t s) {
+  dim3 grid((unsigned)(ctx->tiles.size() * (kMaxTPT / TPT)), splits);
   if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
-    k_pairs32<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
-                                              ctx->ntarget, ctx->geo.src32, ctx->nsource, ctx->dens_up32,
-                                              ctx->pair_splits, has_f, has_u, ctx->part);
+    k_pairs32<KIND, TPT><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
+                                                   ctx->ntarget, ctx->geo.src32, ctx->nsource, ctx->dens_up32,
+                                                   splits, has_f, has_u, ctx->part);
   } else {
-    k_pairs64<KIND><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
-                                              ctx->ntarget, ctx->geo.src, ctx->nsource, ctx->dens_up,
-                                              ctx->pair_splits, has_f, has_u, ctx->part);
+    k_pairs64<KIND, TPT><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
+                                                   ctx->ntarget, ctx->geo.src, ctx->nsource, ctx->dens_up,
+                                                   splits, has_f, has_u, ctx->part);
   }
 }
 
-// Pick the source-split count of the FP32 pair kernels for this drop layout by timing a few
-// candidates (powers of two up to the partial-buffer capacity) on the first launch.
 template <int KIND>
-int autotune_splits(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
-  ctx->splits_tuned = true;
+void launch_raw(shbim_ctx* ctx, bool has_f, bool has_u, int tpt, int splits, cudaStream_t s) {
+  if (tpt == 4) launch_shape<KIND, 4>(ctx, has_f, has_u, splits, s);
+  else if (tpt == 2) launch_shape<KIND, 2>(ctx, has_f, has_u, splits, s);
+  else launch_shape<KIND, 1>(ctx, has_f, has_u, splits, s);
+}
+
+// Choose the register blocking (targets per thread) and the source-split count of one FP32
+// kernel kind for this drop layout: every TPT in {1, 2, 4} with split counts in powers of two
+// around the layout's default (times 1/4 ... 4, at most the partial-buffer capacity) is launched
+// twice and the second launch timed with CUDA events; the fastest is kept.
+template <int KIND>
+int autotune(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
+  auto& C = ctx->pair_cfg[KIND];
+  C.tuned = true;
   if (ctx->timing || ctx->opts.precision != SHBIM_PREC_FP32_COMP) return SHBIM_OK;
   cudaStreamCaptureStatus cs;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return SHBIM_OK;
   cudaEvent_t a, b;
-  cudaEventCreate(&a);
-  cudaEventCreate(&b);
-  const int start = ctx->pair_splits;
-  int best = start;
+  if (cudaEventCreate(&a) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "autotune event");
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cuda_fail(ctx, cudaGetLastError(), "autotune event");
+  }
+  const int lo = std::max(1, ctx->pair_splits / 4), hi = std::min(ctx->split_max, 4 * ctx->pair_splits);
+  int best_t = C.tpt, best_s = C.splits;
   float best_ms = 1e30f;
-  for (int sp = 1; sp <= ctx->split_max; sp *= 2) {
-    ctx->pair_splits = sp;
-    launch_raw<KIND>(ctx, has_f, has_u, s);  // warm
-    cudaEventRecord(a, s);
-    launch_raw<KIND>(ctx, has_f, has_u, s);
-    cudaEventRecord(b, s);
-    cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    ctx->launches += 2;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = sp;
+  int sp0 = 1;
+  while (2 * sp0 <= lo) sp0 *= 2;
+  for (int tpt = 1; tpt <= kMaxTPT; tpt *= 2) {
+    for (int sp = sp0; sp <= hi; sp *= 2) {
+      launch_raw<KIND>(ctx, has_f, has_u, tpt, sp, s);  // warm
+      cudaEventRecord(a, s);
+      launch_raw<KIND>(ctx, has_f, has_u, tpt, sp, s);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      ctx->launches += 2;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_t = tpt;
+        best_s = sp;
+      }
     }
   }
-  ctx->pair_splits = best;
+  C.tpt = best_t;
+  C.splits = best_s;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? SHBIM_OK : cuda_fail(ctx, e, "pair split autotune");
+  return e == cudaSuccess ? SHBIM_OK : cuda_fail(ctx, e, "pair kernel autotune");
 }
 
 template <int KIND>
 int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s) {
   constexpr int NC = (KIND == STO) ? 3 : 1;
   if (ctx->n_drops < 2 || ctx->tiles.empty()) return SHBIM_OK;
-  if (!ctx->splits_tuned) {
-    int rc = autotune_splits<KIND>(ctx, has_f, has_u, s);
+  auto& C = ctx->pair_cfg[KIND];
+  if (!C.tuned) {
+    int rc = autotune<KIND>(ctx, has_f, has_u, s);
     if (rc) return rc;
   }
-  launch_raw<KIND>(ctx, has_f, has_u, s);
+  // the FP64 kernels keep the layout's default shape (the FP64 pipe bounds them)
+  const bool fp32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const int tpt = fp32 ? C.tpt : 2, splits = fp32 ? C.splits : ctx->pair_splits;
+  launch_raw<KIND>(ctx, has_f, has_u, tpt, splits, s);
   SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
   const int64_t n = NC * ctx->ntarget;
-  k_reduce_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->part, ctx->pair_splits, n, out);
+  k_reduce_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->part, splits, n, out);
   SHBIM_CHECK_LAUNCH(ctx, "k_reduce_parts");
   return SHBIM_OK;
 }
@@ -378,6 +415,6 @@ int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
   return launch_pairs<STO>(ctx, has_f, has_u, out, s);
 }
 
-int pairs_tile_targets() { return kThreads * kTPT; }
+int pairs_tile_targets() { return kTileTargets; }
 
 }  // namespace shbim

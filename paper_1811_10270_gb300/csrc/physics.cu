@@ -11,10 +11,15 @@
 //   (vi)  solves the Stokes system with right-hand side -sum_j S_j[f/Ca_E - f^E] (Eq. main_eq),
 //   and forms the surfactant rate -Gamma div_S u for nodes moving with u (Eq. surfactant0 in
 //   material form, no diffusion), projected to degree p.
-// step(): midpoint rule for x with the explicit IMEX stage for Gamma (Algorithm 1):
+// step(): midpoint rule for x with the IMEX stages for Gamma (Algorithm 1):
 //   half step with the rates at t, full step with the rates at t + dt/2; the error estimate is
 //   dt times the grid max-norm of the difference between the two rates (the distance between
-//   the midpoint and the explicit Euler step).
+//   the midpoint and the explicit Euler step). With a finite Peclet number the half step is
+//   implicit in the surfactant diffusion on the half-step surface,
+//   (I - dt/(2 Pe) Delta_S) Gamma_half = Gamma + dt/2 g_E(t), and the full-step rate adds
+//   Delta_S Gamma_half / Pe.
+// laplace_beltrami(): Delta_S f = g^{ab} (f_ab - Gamma^c_ab f_c) in the (theta, phi) chart with
+//   Gamma^c_ab = g^{cd} x_d . x_ab, formed on the degree 2p+1 grid and projected to degree p.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -127,6 +132,38 @@ __global__ void k_surf_rate(const double* __restrict__ xup, int64_t ns, const do
   }
   const double div = (f.G * a - f.F * (b + c) + f.E * d) / f.det;
   out[i] = -Gm[i] * div;
+}
+
+// fd [5][fstride]: f_theta, f_theta_theta, f_theta_phi, f_phi_phi, f_phi -> Delta_S f.
+// g^{ab} Gamma^c_ab f_c is formed through X = g^{ab} x_ab: g^{ab} Gamma^c_ab = g^{cd} x_d . X.
+__global__ void k_laplace_beltrami(const double* __restrict__ xup, int64_t ns, const double* __restrict__ fd,
+                                   int64_t fstride, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns) return;
+  double xt[3], xp[3], xtt[3], xtp[3], xpp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double* b = xup + (int64_t)c * kNumTab * ns;
+    xt[c] = b[ns + i];
+    xtt[c] = b[3 * ns + i];
+    xtp[c] = b[4 * ns + i];
+    xpp[c] = b[5 * ns + i];
+    xp[c] = b[6 * ns + i];
+  }
+  const double E = xt[0] * xt[0] + xt[1] * xt[1] + xt[2] * xt[2];
+  const double F = xt[0] * xp[0] + xt[1] * xp[1] + xt[2] * xp[2];
+  const double G = xp[0] * xp[0] + xp[1] * xp[1] + xp[2] * xp[2];
+  const double det = E * G - F * F;
+  const double gtt = G / det, gtp = -F / det, gpp = E / det;
+  double X[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) X[c] = gtt * xtt[c] + 2.0 * gtp * xtp[c] + gpp * xpp[c];
+  const double a = xt[0] * X[0] + xt[1] * X[1] + xt[2] * X[2];
+  const double b = xp[0] * X[0] + xp[1] * X[1] + xp[2] * X[2];
+  const double ct = gtt * a + gtp * b, cp = gtp * a + gpp * b;
+  const double ft = fd[i], ftt = fd[fstride + i], ftp = fd[2 * fstride + i], fpp = fd[3 * fstride + i],
+               fp = fd[4 * fstride + i];
+  out[i] = gtt * ftt + 2.0 * gtp * ftp + gpp * fpp - ct * ft - cp * fp;
 }
 
 __global__ void k_lincomb(double* __restrict__ y, const double* __restrict__ a, double alpha,
@@ -244,6 +281,30 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   return SHBIM_OK;
 }
 
+int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream_t s) {
+  const int64_t NS = ctx->nsource;
+  auto& W = ctx->phys;
+  if (W.lb_cap < (size_t)6 * NS) {
+    // only at the first use for a layout: captured operator graphs hold this workspace
+    int rc = ensure_buf(ctx, &W.lb, &W.lb_cap, (size_t)6 * NS);
+    if (rc) return rc;
+    ctx->geom_version++;
+  }
+  double* fd = W.lb;
+  double* lv = fd + 5 * NS;
+  const int kinds = (1 << 1) | (1 << 3) | (1 << 4) | (1 << 5) | (1 << 6);
+  int rc;
+  for (auto& d : ctx->drops) {
+    const GridTables& g = d.tab->up;
+    const int64_t o = d.src_off;
+    if ((rc = sht_synth(ctx, g, 1, coef + d.coef_off, d.nc, kinds, fd + o, 0, NS, nullptr, nullptr, s))) return rc;
+    k_laplace_beltrami<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, fd + o, NS, lv + o);
+    SHBIM_CHECK_LAUNCH(ctx, "k_laplace_beltrami");
+    if ((rc = sht_analysis(ctx, g, 1, lv + o, NS, true, out + d.coef_off, d.nc, s))) return rc;
+  }
+  return SHBIM_OK;
+}
+
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef, cudaStream_t s);
 
 int grid_maxnorm(shbim_ctx* ctx, const double* coef, int ncomp, double* out_host, cudaStream_t s) {
@@ -281,7 +342,7 @@ int shbim_rates(shbim_ctx* ctx, const shbim_phys* ph, const double* gamma_dev, d
   if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
   if (!ph || !gamma_dev || !u_dev || !gE_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
   if (!(ph->R > 0.0) || !(ph->Ca_E > 0.0) || ph->beta < 0.0 || !(ph->x_s >= 0.0 && ph->x_s < 1.0) ||
-      !(ph->inner_tol > 0.0 && ph->inner_tol < 1.0))
+      !(ph->inner_tol > 0.0 && ph->inner_tol < 1.0) || !(ph->Pe >= 0.0))
     return fail(ctx, SHBIM_ERR_ARG, "bad physical parameters");
   int ie = 0, is = 0;
   int rc = rates(ctx, *ph, gamma_dev, u_dev, gE_dev, &ie, &is, (cudaStream_t)stream);
@@ -298,11 +359,13 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* ph, const double* x_dev, const 
   if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
   if (!ph || !x_dev || !gamma_dev || !x_out_dev || !gamma_out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ctx, SHBIM_ERR_ARG, "dt must be positive");
+  if (!(ph->Pe >= 0.0)) return fail(ctx, SHBIM_ERR_ARG, "Pe must be >= 0 (0 or infinity: no diffusion)");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = ctx->ncoef;
   auto& W = ctx->phys;
   int rc;
-  if ((rc = ensure_buf(ctx, &W.state, &W.state_cap, (size_t)12 * n))) return rc;
+  const bool diffuse = ph->Pe > 0.0 && std::isfinite(ph->Pe);
+  if ((rc = ensure_buf(ctx, &W.state, &W.state_cap, (size_t)13 * n))) return rc;
   double* u0 = W.state;
   double* g0 = u0 + 3 * n;
   double* u1 = g0 + n;
@@ -318,7 +381,18 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* ph, const double* x_dev, const 
   k_lincomb<<<nb(n), 256, 0, s>>>(gh, gamma_dev, 1.0, g0, 0.5 * dt, n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
   if ((rc = rebuild_geometry(ctx, xh, s))) return rc;
+  if (diffuse) {
+    // implicit half step of the diffusion on the half-step surface (FP64 in every mode)
+    if ((rc = shbim_set_diffusion(ctx, 0.5 * dt / ph->Pe))) return rc;
+    if ((rc = shbim_gmres_solve(ctx, SHBIM_SYS_DIFFUSION, gh, nullptr, gh, nullptr, nullptr, s))) return rc;
+  }
   if ((rc = rates(ctx, *ph, gh, u1, g1, &its[2], &its[3], s))) return rc;
+  if (diffuse) {
+    double* lg = W.state + 12 * n;
+    if ((rc = laplace_beltrami(ctx, gh, lg, s))) return rc;
+    k_lincomb<<<nb(n), 256, 0, s>>>(g1, g1, 1.0, lg, 1.0 / ph->Pe, n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
+  }
   k_lincomb<<<nb(3 * n), 256, 0, s>>>(x_out_dev, x_dev, 1.0, u1, dt, 3 * n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
   k_lincomb<<<nb(n), 256, 0, s>>>(gamma_out_dev, gamma_dev, 1.0, g1, dt, n);
@@ -336,6 +410,13 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* ph, const double* x_dev, const 
   if (iters_host)
     for (int k = 0; k < 4; ++k) iters_host[k] = its[k];
   return SHBIM_OK;
+}
+
+int shbim_laplace_beltrami(shbim_ctx* ctx, const double* coef_dev, double* out_dev, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (!coef_dev || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  return laplace_beltrami(ctx, coef_dev, out_dev, (cudaStream_t)stream);
 }
 
 }  // extern "C"

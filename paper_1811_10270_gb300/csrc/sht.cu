@@ -123,12 +123,21 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
   }
 }
 
+// Dynamic shared memory above the 48 KB default needs the kernel's opt-in (up to 227 KB per CTA).
+int synth_smem_ok(shbim_ctx* ctx, size_t smem) {
+  if (smem <= 48 * 1024) return SHBIM_OK;
+  if (smem > 227 * 1024) return fail(ctx, SHBIM_ERR_ARG, "synthesis grid too large for shared memory");
+  SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return SHBIM_OK;
+}
+
 int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
               int64_t coef_stride, int kinds, double* out, int64_t item_stride,
               int64_t kind_stride, const double* scale, float* out32, cudaStream_t s) {
   if (n_items <= 0) return SHBIM_OK;
   const int nk = __builtin_popcount(kinds);
   const size_t smem = (size_t)(nk * 2 * (g.p + 1) + (2 + nk) * (2 * g.q + 2)) * sizeof(double);
+  if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, kinds, out,
                                   item_stride, kind_stride, scale, 1.0, out32);
@@ -142,6 +151,7 @@ int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const dou
                      double alpha, float* out32, cudaStream_t s) {
   if (n_items <= 0) return SHBIM_OK;
   const size_t smem = (size_t)(2 * (g.p + 1) + 3 * (2 * g.q + 2)) * sizeof(double);
+  if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, 1, out, item_stride,
                                   0, scale, alpha, out32);

@@ -228,6 +228,55 @@ def test_three_drops_uneven_degrees_match_oracle(S):
         ctx.close()
 
 
+def test_every_pair_launch_shape_matches_oracle(S):
+    """Each register blocking (1, 2, 4 targets per thread) with one and several source splits:
+    drops of 200, 98 and 50 targets leave ragged and empty sub-tiles in every shape."""
+    rng = np.random.default_rng(21)
+    drops = []
+    for p, ctr, lam in ((9, (0, 0, 0), 2.0), (6, (2.4, 0.3, -0.2), 0.5), (4, (-0.4, -2.3, 0.5), 4.0)):
+        drops.append(inputs.Drop(p, inputs.perturbed_coef(p, rng, 1.0, ctr), np.zeros(sh.ncoef(p)),
+                                 lam, np.asarray(ctr, float), 1.0))
+    sysm = oracle_system(drops, near=False)
+    sig = [inputs.random_density(d.p, rng)[0] for d in drops]
+    u = [inputs.random_density(d.p, rng, 3) for d in drops]
+    f = [inputs.random_density(d.p, rng, 3) for d in drops]
+    ref = {0: np.concatenate(sysm.laplace_coef("ladl", sig)), 1: np.concatenate(sysm.laplace_coef("lsl", sig)),
+           2: np.concatenate([a.ravel() for a in sysm.stokes_coef(f, u)])}
+    nc = sum(sh.ncoef(d.p) for d in drops)
+    ctx = make(S, drops, S.FP32_COMP, near=False)
+    sig_d = T(np.concatenate(sig))
+    f_d = T(np.concatenate([a.ravel() for a in f]))
+    u_d = T(np.concatenate([a.ravel() for a in u]))
+    _, default_splits, fixed = ctx.pair_shape(2)
+    assert not fixed                      # nothing launched yet: the shape is not chosen
+    for tpt in (1, 2, 4):
+        for splits in sorted({1, max(1, default_splits)}):
+            for kind in (0, 1, 2):
+                ctx.set_pair_shape(kind, tpt, splits)
+                assert ctx.pair_shape(kind) == (tpt, splits, True)
+            out = torch.empty(nc, device=DEV, dtype=torch.float64)
+            ctx.eval_electric(S.LAPLACE_DL, sig_d, out, S.OUT_COEF)
+            assert rel_err(out.cpu().numpy(), ref[0]) < TOL32, (tpt, splits)
+            ctx.eval_electric(S.LAPLACE_SL, sig_d, out, S.OUT_COEF)
+            assert rel_err(out.cpu().numpy(), ref[1]) < TOL32, (tpt, splits)
+            out3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
+            ctx.eval_stokes(f_d, u_d, out3, S.OUT_COEF)
+            assert rel_err(out3.cpu().numpy(), ref[2]) < TOL32, (tpt, splits)
+    with pytest.raises(S.ShbimError):
+        ctx.set_pair_shape(0, 3, 1)
+    with pytest.raises(S.ShbimError):
+        ctx.set_pair_shape(0, 1, 0)
+    ctx.close()
+    # the autotuner settles on one of the shapes and keeps the results within tolerance
+    ctx = make(S, drops, S.FP32_COMP, near=False)
+    out3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
+    ctx.eval_stokes(f_d, u_d, out3, S.OUT_COEF)
+    tpt, splits, fixed = ctx.pair_shape(2)
+    assert fixed and tpt in (1, 2, 4) and splits >= 1
+    assert rel_err(out3.cpu().numpy(), ref[2]) < TOL32
+    ctx.close()
+
+
 def test_full_size_two_drops_sampled_targets(S):
     """Two p = 32 drops 0.1 apart (the two-drop workload) in the bench's launch
     configuration: target values at sampled targets (first, last, tile edges, closest to the
@@ -393,6 +442,7 @@ def test_graph_replay_matches_direct_launches(S):
         for precision in (S.FP64, S.FP32_COMP):
             ctx = S.Context(precision=precision, R=cfg.R, gmres_tol=1e-10)
             ctx.set_graphs(graphs)
+            ctx.set_autotune(False)     # the same FP32 summation order in both contexts
             sols = []
             for shift in (0.0, 0.05):
                 xc = np.concatenate([d.xcoef.ravel() for d in cfg.drops])
