@@ -126,6 +126,9 @@ def run_own(args):
     if args.only == "pairs_at_scale":
         print(json.dumps({"pairs_at_scale": pairs_at_scale(S, torch, dev)}))
         return
+    if args.only == "peaks":
+        print(json.dumps({"pipe_peaks_measured": pipe_peaks(S)}))
+        return
     if args.only in ("config3", "config5"):
         print(json.dumps({args.only: batched_leg(S, torch, dev, args.only)}))
         return
@@ -242,6 +245,9 @@ def run_own(args):
     # roofline of the dominant kernel class (measured above with CUDA events)
     dom = max(cls_ms, key=lambda k: cls_ms[k])
     roof = roofline(dom, cls_ms[dom], cls_n[dom], cfg, args.steps, args.precision, P, apps_total)
+    peaks = pipe_peaks(S)
+    if roof.get("bound") == "alu" and "FP64" in roof.get("kernel", ""):
+        roof["frac_of_measured_dfma"] = roof["achieved"] / peaks["dfma"]["value"]
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -263,6 +269,7 @@ def run_own(args):
         "pairs_at_scale": scale,
         "learned_warm_start": learned,
         "roofline": roof,
+        "pipe_peaks_measured": peaks,
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT,
@@ -380,6 +387,21 @@ def learned_warm_start(S, torch, dev, p: int = 8, n_train: int = 600, n_test: in
             "mean_inner_iters": {k: float(np.mean(v)) for k, v in it.items()},
             "mean_initial_resid": {k: float(np.mean(v)) for k, v in r0.items()},
             "mean_ms_to_1e-8": {k: v / n_test for k, v in ms.items()}}
+
+
+# outer iterations per probe: about 50 ms each on a GB300
+PROBE_ITERS = {"ffma": 200000, "dfma": 3000, "rsqrt": 25000, "hmma_bf16": 300000, "dmma_f64": 3000}
+
+
+def pipe_peaks(S):
+    """Measured issue-bound rates of the pipes the kernels use (shbim_probe_peak)."""
+    kinds = {"ffma": S.PROBE_FFMA, "dfma": S.PROBE_DFMA, "rsqrt": S.PROBE_RSQRT,
+             "hmma_bf16": S.PROBE_HMMA_BF16, "dmma_f64": S.PROBE_DMMA_F64}
+    out = {}
+    for name, k in kinds.items():
+        r, ms = S.probe_peak(k, PROBE_ITERS[name])
+        out[name] = {"value": r / 1e12, "unit": "Tops/s" if name == "rsqrt" else "TFLOP/s", "ms": ms}
+    return out
 
 
 def batched_leg(S, torch, dev, name):
@@ -609,7 +631,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-scale", action="store_true", help="skip the 64-drop all-pairs measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
-    ap.add_argument("--only", choices=["pairs_at_scale", "config3", "config5"],
+    ap.add_argument("--only", choices=["pairs_at_scale", "config3", "config5", "peaks"],
                     help="run one measurement leg alone and print its JSON (for profiling)")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for launch lists under a profiler)")

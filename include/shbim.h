@@ -331,6 +331,20 @@ int shbim_set_graphs(shbim_ctx* ctx, int on);
  * FP32 results reproducible across contexts. Takes effect immediately. */
 int shbim_set_autotune(shbim_ctx* ctx, int on);
 
+/* Pipe throughput probes (a measurement utility for roofline denominators; the paper has no
+ * counterpart). Launches 4 CTAs of 256 threads per SM on the current device, each thread running
+ * 8 independent dependency chains of one instruction for `iters` outer iterations, once to warm
+ * up and once timed with CUDA events on `stream`; synchronises the stream. Writes the achieved
+ * rate to *ops_per_s_host (flop/s for the FMA and MMA kinds, reciprocal square roots per second
+ * for SHBIM_PROBE_RSQRT) and the timed duration to *ms_host (may be NULL). Allocates and frees a
+ * small device buffer. SHBIM_ERR_ARG for a bad kind or iters < 1. */
+#define SHBIM_PROBE_FFMA 0       /* FP32 fma */
+#define SHBIM_PROBE_DFMA 1       /* FP64 fma */
+#define SHBIM_PROBE_RSQRT 2      /* MUFU reciprocal square root, FP32 */
+#define SHBIM_PROBE_HMMA_BF16 3  /* mma.sync m16n8k16 bf16 x bf16 -> f32 */
+#define SHBIM_PROBE_DMMA_F64 4   /* mma.sync m8n8k4 f64 */
+int shbim_probe_peak(int kind, int64_t iters, double* ops_per_s_host, double* ms_host, void* stream);
+
 /* Launch shape of the FP32 all-pairs kernel of one kind (0 Laplace DL, 1 Laplace SL, 2 Stokes)
  * for the current layout. shbim_pair_shape writes targets per thread and the split count (either
  * pointer may be NULL) and returns 1 once the shape is fixed (tuned or set), 0 before, or an

@@ -40,8 +40,13 @@ EXPORTS = [
     "shbim_mlp_create", "shbim_mlp_destroy", "shbim_mlp_set_layer", "shbim_mlp_get_layer",
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
     "shbim_set_graphs", "shbim_laplace_beltrami", "shbim_set_diffusion",
-    "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape",
+    "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
 ]
+PROBE_FFMA = 0
+PROBE_DFMA = 1
+PROBE_RSQRT = 2
+PROBE_HMMA_BF16 = 3
+PROBE_DMMA_F64 = 4
 NOALLOC_MAX_TARGETS = 1 << 21
 K_SELF_WEIGHTS = 0
 K_SELF_ANALYSIS = 1
@@ -117,6 +122,7 @@ def lib():
         "shbim_set_graphs": (i32, [vp, i32]),
         "shbim_set_autotune": (i32, [vp, i32]),
         "shbim_pair_shape": (i32, [vp, i32, P(i32), P(i32)]),
+        "shbim_probe_peak": (i32, [i32, i64, P(dp), P(dp), vp]),
         "shbim_set_pair_shape": (i32, [vp, i32, i32, i32]),
         "shbim_laplace_beltrami": (i32, [vp, vp, vp, vp]),
         "shbim_set_diffusion": (i32, [vp, dp]),
@@ -343,6 +349,17 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self._L.shbim_launch_count(self._h))
+
+
+def probe_peak(kind: int, iters: int = 20000):
+    """Measured throughput of one SM pipe (shbim_probe_peak): (ops per second, ms)."""
+    L = lib()
+    r = ctypes.c_double()
+    ms = ctypes.c_double()
+    rc = L.shbim_probe_peak(int(kind), int(iters), ctypes.byref(r), ctypes.byref(ms), _stream())
+    if rc != 0:
+        raise ShbimError("shbim_probe_peak failed (%d)" % rc)
+    return r.value, ms.value
 
 
 class MLP:
