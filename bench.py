@@ -248,12 +248,14 @@ def run_own(args):
     peaks = pipe_peaks(S)
     if roof.get("bound") == "alu" and "FP64" in roof.get("kernel", ""):
         roof["frac_of_measured_dfma"] = roof["achieved"] / peaks["dfma"]["value"]
+    if roof.get("unit") == "Tinst/s":
+        roof["frac_of_measured_ffma_issue"] = roof["achieved"] / (peaks["ffma"]["value"] / 2)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "fp32comp" else "f64",
+        "dtype": "f32+df32+f64" if args.precision == "fp32comp" else "f64",
         "data": "synthetic",
         "config": {"workload": "two drops p=32 gap=0.1 (lambda=5, R=2, Q=0.5, Ca_E=0.1, Langmuir "
                                "beta=0.2 x_s=0.5, E=z): one midpoint time step (Algorithm 1) = 2 x "
@@ -381,8 +383,8 @@ def learned_warm_start(S, torch, dev, p: int = 8, n_train: int = 600, n_test: in
                 r0[k].append(float(torch.linalg.norm(r) / torch.linalg.norm(rhs)))
         ctx.close()
     net.close()
-    return {"scale": "p=%d two-drop inputs, %d training solves, %d held out (north-star scale p=32 x 20000 "
-                     "not run)" % (p, n_train, n_test),
+    return {"scale": "p=%d two-drop inputs, %d training solves, %d held out (the 20 000-solve p = 32 "
+                     "training set is not run)" % (p, n_train, n_test),
             "train_s": t_train, "generate_s": t_gen, "final_loss_ratio": hist[-1] / hist[0],
             "mean_inner_iters": {k: float(np.mean(v)) for k, v in it.items()},
             "mean_initial_resid": {k: float(np.mean(v)) for k, v in r0.items()},
@@ -445,7 +447,7 @@ def batched_leg(S, torch, dev, name):
     kinds = (("laplace_dl", lambda: ctx.eval_electric(S.LAPLACE_DL, sig, out[:nc])),
              ("laplace_sl", lambda: ctx.eval_electric(S.LAPLACE_SL, sig, out[:nc])),
              ("stokes_sd", lambda: ctx.eval_stokes(f, f, out)))
-    for pname, prec, reps in (("fp32comp", S.FP32_COMP, 3), ("fp64", S.FP64, 1)):
+    for pname, prec, reps in (("fp32comp", S.FP32_COMP, 3), ("df64", S.DF64, 1), ("fp64", S.FP64, 1)):
         ctx.set_precision(prec)
         res[pname] = {}
         for kname, fn in kinds:
@@ -456,12 +458,13 @@ def batched_leg(S, torch, dev, name):
     # right-hand sides: the field term of the electric system; S[f] for Stokes
     rhs_e = torch.empty(nc, device=dev, dtype=torch.float64)
     ctx.electric_rhs(cfg.E_u, rhs_e, E_q=cfg.E_quad)
-    ctx.set_precision(S.FP64)
+    ctx.set_precision(S.DF64)
     rhs_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
     ctx.eval_stokes(f, None, rhs_s)
     sol_e = torch.empty(nc, device=dev, dtype=torch.float64)
     sol_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
     tts = {}
+    ctx.set_precision(S.FP32_COMP)
     ms, (ie, oe, re_) = timed(lambda: ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs_e, sol_e, inner_tol=1e-5))
     tts["electric_mixed"] = {"ms": ms, "inner_iters": ie, "outer": oe, "resid": re_}
     ms, (is_, os_, rs) = timed(lambda: ctx.gmres_solve_refined(S.SYS_STOKES, rhs_s, sol_s, inner_tol=1e-5))
@@ -471,6 +474,11 @@ def batched_leg(S, torch, dev, name):
     tts["electric_fp64"] = {"ms": ms, "iters": ie, "resid": re_}
     ms, (is_, rs) = timed(lambda: ctx.gmres_solve(S.SYS_STOKES, rhs_s, sol_s))
     tts["stokes_fp64"] = {"ms": ms, "iters": is_, "resid": rs}
+    ctx.set_precision(S.DF64)
+    ms, (ie, re_) = timed(lambda: ctx.gmres_solve(S.SYS_ELECTRIC, rhs_e, sol_e))
+    tts["electric_df64"] = {"ms": ms, "iters": ie, "resid": re_}
+    ms, (is_, rs) = timed(lambda: ctx.gmres_solve(S.SYS_STOKES, rhs_s, sol_s))
+    tts["stokes_df64"] = {"ms": ms, "iters": is_, "resid": rs}
     tts["speedup_mixed_vs_fp64"] = ((tts["electric_fp64"]["ms"] + tts["stokes_fp64"]["ms"])
                                     / (tts["electric_mixed"]["ms"] + tts["stokes_mixed"]["ms"]))
     res["time_to_1e-8"] = tts
@@ -488,22 +496,24 @@ def batched_leg(S, torch, dev, name):
 
 
 def time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u, reps=3):
-    """Electric + Stokes solves to an FP64 relative residual of 1e-8 on the current geometry:
-    mixed precision (FP32 compensated inner GMRES + FP64 refinement) vs plain FP64 GMRES."""
+    """Electric + Stokes solves to a relative residual of 1e-8 on the current geometry: plain
+    GMRES with native FP64 sums, plain GMRES with double-float sums (FP64-class accuracy on the
+    FP32 pipe), and mixed precision (FP32 compensated inner GMRES, double-float refinement)."""
     out = {}
-    for name in ("fp64", "mixed"):
+    for name in ("fp64", "df64", "mixed"):
         best = None
         for _ in range(reps):
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            if name == "fp64":
-                ctx.set_precision(S.FP64)
+            if name in ("fp64", "df64"):
+                ctx.set_precision(S.FP64 if name == "fp64" else S.DF64)
                 ie, re_ = ctx.gmres_solve(S.SYS_ELECTRIC, rhs_e, En)
                 is_, rs = ctx.gmres_solve(S.SYS_STOKES, rhs_s, u)
                 info = {"iters": [ie, is_], "resid": [re_, rs]}
             else:
+                ctx.set_precision(S.FP32_COMP)
                 ie, oe, re_ = ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs_e, En, inner_tol=1e-5)
                 is_, os_, rs = ctx.gmres_solve_refined(S.SYS_STOKES, rhs_s, u, inner_tol=1e-5)
                 info = {"inner_iters": [ie, is_], "outer": [oe, os_], "resid": [re_, rs]}
@@ -515,35 +525,67 @@ def time_to_solution(ctx, S, torch, stream, rhs_e, rhs_s, En, u, reps=3):
         out[name] = {"ms": best[0], **best[1]}
     ctx.set_precision(S.FP32_COMP)
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    out["speedup_df64_vs_fp64"] = out["fp64"]["ms"] / out["df64"]["ms"]
     return out
 
 
-def roofline(dom, ms, n, cfg, steps, precision, P, apps):
+# FP32 instruction slots of the double-float operations of csrc/dfloat.cuh, counted from the source:
+# multiply-accumulate into a running sum 12, product 7, sum / difference 11, 3-term dot product 31,
+# reciprocal square root 28 (one MUFU seed + Newton step), square 7.
+DF_MAC, DF_MUL, DF_ADD, DF_DOT3, DF_RSQRT, DF_SQR = 12, 7, 11, 31, 28, 7
+# per rotated node: tangents' cross product, J and n, offset and 1/r, the 14 weights
+DF_WEIGHTS_PER_NODE = (6 * DF_MUL + 3 * DF_ADD + DF_DOT3 + DF_RSQRT + DF_MUL + 3 * DF_MUL + 3 * DF_ADD
+                       + DF_DOT3 + DF_RSQRT + DF_SQR + 3 * DF_MUL + DF_DOT3 + 6 + 3 * DF_MUL + 2 * DF_MUL
+                       + DF_DOT3 + 2 * DF_MUL + 3 * DF_MUL + 6 * DF_MUL + 3 * DF_ADD + 3 * DF_MUL + 6 * DF_MUL)
+FP32_ISSUE_TINST = SM_COUNT * FP32_LANES_PER_SM * 2.07e9 / 1e12   # FP32 lane instructions / s
+
+
+def roofline(dom, ms, n, cfg, steps, precision, P, apps, rows_df=True):
     p = cfg.drops[0].p
     q = 2 * p + 1
     nt = (p + 1) * (2 * p + 2)
     ns = (q + 1) * (2 * q + 2)
+    N = 2 * q + 2
+    Q4 = N // 4
+    ntri = (p + 1) * (p + 2) // 2
+    # FP64 flops per (target, rotated node) of the weights stage: Legendre sums 18 (p+1)(p+2)/2
+    # FMA per (target, latitude); four-fold Fourier synthesis 9 (N/4+1) 2p FMA per (target,
+    # latitude); ~70 flops of pointwise geometry and kernel weights. FMA = 2 flops.
+    fp64_per_unit = 2 * (18 * ntri + 9 * (Q4 + 1) * 2 * p) / N + 70
+    units_w = sum(nt * ns for _ in cfg.drops) * steps * 2   # two geometries per step
+    if dom == "self_weights" and rows_df:
+        per_unit = (18 * ntri * DF_MAC + 9 * (Q4 + 1) * (2 * p * DF_MAC + 4 * 3 + 4 * DF_ADD
+                                                            + 4 * (DF_MUL + 2 * DF_ADD))) / N \
+            + DF_WEIGHTS_PER_NODE
+        ach = per_unit * units_w / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "k_self_weights_df (double-float on the FP32 pipe)",
+                "achieved": ach, "peak": FP32_ISSUE_TINST, "unit": "Tinst/s", "frac": ach / FP32_ISSUE_TINST,
+                "traffic": TRAFFIC.get("self_weights_df"), "launches": n, "avg_launch_ms": ms / max(1, n),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (derived; measured FFMA issue in "
+                               "pipe_peaks_measured)",
+                "per_unit_fp32_instructions": per_unit, "unit_of_work": "(target, rotated source node)",
+                "fp64_equivalent_tflops": fp64_per_unit * units_w / (ms / 1e3) / 1e12,
+                "fp64_equivalent_note": "the FP64 build's flops at this kernel's speed; FP64 peak 1.25"}
     if dom == "self_weights":
-        # per (target, rotated node), as implemented: Legendre sums 18 (p+1)(p+2)/2 FMA per
-        # (target, latitude); four-fold Fourier synthesis 9 (N/4+1) 2p FMA per (target,
-        # latitude); ~70 flops of pointwise geometry and kernel weights. FMA = 2 flops.
-        N = 2 * q + 2
-        per_unit = 2 * (18 * (p + 1) * (p + 2) / 2 + 9 * (N // 4 + 1) * 2 * p) / N + 70
-        units = sum(nt * ns for _ in cfg.drops) * steps * 2   # two geometries per step
-        flops = per_unit * units
-        ach = flops / (ms / 1e3) / 1e12
+        ach = fp64_per_unit * units_w / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "k_self_weights (FP64)", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": TRAFFIC.get("self_weights"), "launches": n, "avg_launch_ms": ms / max(1, n),
                 "peak_source": "GB300 FP64 rate 1.25 TFLOP/s (nominal, derived in DESIGN.md)",
-                "per_unit_flops": per_unit, "unit_of_work": "(target, rotated source node)"}
+                "per_unit_flops": fp64_per_unit, "unit_of_work": "(target, rotated source node)"}
+    units_a = sum(nt * ns * 14 for _ in cfg.drops) * steps * 2
+    if dom == "self_analysis" and rows_df:
+        # per (target, component, node): folds 4 adds per Q4 nodes, 2(p+1)(Q4-1) MACs per row of N
+        # nodes, Legendre 2 ntri (q+1) MACs per item over Ns nodes
+        per_unit = (4 * Q4 * DF_ADD + 2 * (p + 1) * (Q4 - 1) * DF_MAC) / N + 2 * ntri * (q + 1) * DF_MAC / ns
+        ach = per_unit * units_a / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "k_analysis_f4_df/leg_df (double-float on the FP32 pipe)",
+                "achieved": ach, "peak": FP32_ISSUE_TINST, "unit": "Tinst/s", "frac": ach / FP32_ISSUE_TINST,
+                "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n),
+                "per_unit_fp32_instructions": per_unit, "unit_of_work": "(target, component, rotated node)"}
     if dom == "self_analysis":
-        # per (target, component, node): four-fold Fourier 2(p+1)(N/4-1) FMA + N adds per row
-        # of N nodes, Legendre 2 ntri FMA per (item, latitude) spread over N nodes
-        N = 2 * q + 2
-        per_unit = (2 * (2 * (p + 1) * (N // 4 - 1)) + N + 2 * 2 * (p + 1) * (p + 2) / 2) / N
-        units = sum(nt * ns * 14 for _ in cfg.drops) * steps * 2
-        ach = per_unit * units / (ms / 1e3) / 1e12
+        per_unit = (2 * (2 * (p + 1) * (Q4 - 1)) + N + 2 * 2 * ntri) / N
+        ach = per_unit * units_a / (ms / 1e3) / 1e12
         return {"bound": "alu", "kernel": "k_analysis_fourier4/legendre (FP64)", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": None, "launches": n, "avg_launch_ms": ms / max(1, n),

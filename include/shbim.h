@@ -57,6 +57,9 @@ extern "C" {
 #define SHBIM_PREC_FP64 0           /* FP64 sums */
 #define SHBIM_PREC_FP32_COMP 1      /* FP32 pair arithmetic, positions relative to the drop
                                        centres, compensated (two-sum) accumulation */
+#define SHBIM_PREC_DF64 2           /* FP64-class sums in double-float arithmetic on the FP32 pipe:
+                                       every quantity is an FP32 pair (value, low part), ~2^-44
+                                       relative per operation (Dekker; Knuth two-sum) */
 
 /* Kernels of the Laplace operator (shbim_eval_electric `which`). Both carry 1/(4 pi). */
 #define SHBIM_LAPLACE_DL 0          /* L[s](x0) = 1/(4pi) int s(x) (x0-x).n(x0) / r^3 dS  (Eq. E_n) */
@@ -253,9 +256,16 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, cons
  * r = b - A x with FP64 all-pairs sums, solves A d = r by GMRES with FP32 compensated sums to
  * the relative tolerance inner_tol (e.g. 1e-5), and updates x += d, until the FP64 relative
  * residual reaches gmres_tol or max_outer steps were taken (SHBIM_ERR_NOT_CONVERGED).
+ * The outer residuals use the context's outer precision (shbim_set_outer_precision).
  * Only the electric and Stokes systems (the diffusion system has no all-pairs sums;
  * SHBIM_ERR_ARG). The context's precision setting is restored on return. Reports the total inner Arnoldi
  * steps, the outer steps and the final FP64 relative residual (each pointer may be NULL). */
+/* FP64-class arithmetic used where mixed precision needs it: the residuals of
+ * shbim_gmres_solve_refined and the one-shot applications of shbim_rates / shbim_step in
+ * SHBIM_PREC_FP32_COMP mode. SHBIM_PREC_DF64 (default: double-float on the FP32 pipe) or
+ * SHBIM_PREC_FP64 (native); SHBIM_ERR_ARG otherwise. */
+int shbim_set_outer_precision(shbim_ctx* ctx, int precision);
+
 int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                               double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
                               int* outer_iters_host, double* resid_host, void* stream);
@@ -330,6 +340,11 @@ int shbim_set_graphs(shbim_ctx* ctx, int on);
  * autotuner off every layout uses 1 target per thread and the default split count, which makes
  * FP32 results reproducible across contexts. Takes effect immediately. */
 int shbim_set_autotune(shbim_ctx* ctx, int on);
+
+/* Arithmetic of the singular-row build (Section 3.1; once per geometry, at the next
+ * shbim_set_drops): SHBIM_PREC_DF64 (default: double-float on the FP32 pipe, FP64-class rows) or
+ * SHBIM_PREC_FP64 (native). SHBIM_ERR_ARG otherwise. */
+int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
 
 /* Pipe throughput probes (a measurement utility for roofline denominators; the paper has no
  * counterpart). Launches 4 CTAs of 256 threads per SM on the current device, each thread running

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libshbim.so")
 
 FP64 = 0
 FP32_COMP = 1
+DF64 = 2
 LAPLACE_DL = 0
 LAPLACE_SL = 1
 OUT_GRID = 0
@@ -41,6 +42,7 @@ EXPORTS = [
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
     "shbim_set_graphs", "shbim_laplace_beltrami", "shbim_set_diffusion",
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
+    "shbim_set_outer_precision", "shbim_set_rows_precision",
 ]
 PROBE_FFMA = 0
 PROBE_DFMA = 1
@@ -121,6 +123,8 @@ def lib():
         "shbim_set_near": (i32, [vp, i32]),
         "shbim_set_graphs": (i32, [vp, i32]),
         "shbim_set_autotune": (i32, [vp, i32]),
+        "shbim_set_outer_precision": (i32, [vp, i32]),
+        "shbim_set_rows_precision": (i32, [vp, i32]),
         "shbim_pair_shape": (i32, [vp, i32, P(i32), P(i32)]),
         "shbim_probe_peak": (i32, [i32, i64, P(dp), P(dp), vp]),
         "shbim_set_pair_shape": (i32, [vp, i32, i32, i32]),
@@ -318,6 +322,12 @@ class Context:
 
     def set_diffusion(self, c: float):
         self._check(self._L.shbim_set_diffusion(self._h, float(c)), "shbim_set_diffusion")
+
+    def set_outer_precision(self, precision: int):
+        self._check(self._L.shbim_set_outer_precision(self._h, int(precision)), "shbim_set_outer_precision")
+
+    def set_rows_precision(self, precision: int):
+        self._check(self._L.shbim_set_rows_precision(self._h, int(precision)), "shbim_set_rows_precision")
 
     def set_autotune(self, on: bool):
         self._check(self._L.shbim_set_autotune(self._h, 1 if on else 0), "shbim_set_autotune")

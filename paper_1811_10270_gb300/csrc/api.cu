@@ -41,7 +41,9 @@ int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
   SHBIM_CUDA(ctx, cudaMemcpy(ctx->drops_dev, dd.data(), dd.size() * sizeof(DropDev), cudaMemcpyHostToDevice));
   int rc;
   if ((rc = build_geometry(ctx, xcoef_dev, s))) return rc;
-  if ((rc = build_singular_rows(ctx, xcoef_dev, s))) return rc;
+  if ((rc = ctx->rows_prec == SHBIM_PREC_DF64 ? build_singular_rows_df(ctx, s, xcoef_dev)
+                                              : build_singular_rows(ctx, xcoef_dev, s)))
+    return rc;
   if ((rc = build_near(ctx, xcoef_dev, s))) return rc;
   return SHBIM_OK;
 }
@@ -58,6 +60,7 @@ void free_drop_state(shbim_ctx* ctx) {
   cudaFree(ctx->geo.src);
   cudaFree(ctx->geo.tgt32);
   cudaFree(ctx->geo.src32);
+  cudaFree(ctx->geo.src32lo);
   cudaFree(ctx->geo.tgt_drop);
   ctx->geo = Geometry{};
   cudaFree(ctx->tiles_dev);
@@ -68,6 +71,8 @@ void free_drop_state(shbim_ctx* ctx) {
   ctx->dens_up = nullptr;
   cudaFree(ctx->dens_up32);
   ctx->dens_up32 = nullptr;
+  cudaFree(ctx->dens_up32lo);
+  ctx->dens_up32lo = nullptr;
   cudaFree(ctx->part);
   ctx->part = nullptr;
   cudaFree(ctx->grid_out);
@@ -89,7 +94,8 @@ int dalloc(shbim_ctx* ctx, T** p, size_t n, const char* what) {
 }
 
 bool valid_opts(const shbim_opts& o) {
-  return (o.precision == SHBIM_PREC_FP64 || o.precision == SHBIM_PREC_FP32_COMP) &&
+  return (o.precision == SHBIM_PREC_FP64 || o.precision == SHBIM_PREC_FP32_COMP ||
+          o.precision == SHBIM_PREC_DF64) &&
          o.gmres_restart >= 1 && o.gmres_restart <= 200 && o.gmres_tol > 0.0 && o.gmres_tol < 1.0 &&
          o.gmres_maxiter >= 1 && std::isfinite(o.R) && o.R > 0.0;
 }
@@ -145,6 +151,7 @@ int shbim_destroy(shbim_ctx* ctx) {
     auto& N = ctx->near;
     cudaFree(N.stats); cudaFree(N.det_t); cudaFree(N.det_j); cudaFree(N.pair_t); cudaFree(N.pair_j);
     cudaFree(N.fgeo); cudaFree(N.fgeo32); cudaFree(N.fstr); cudaFree(N.fstr32); cudaFree(N.foff_dev);
+    cudaFree(N.fgeo32lo); cudaFree(N.fstr32lo);
   }
   for (auto& g : ctx->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -168,8 +175,8 @@ const char* shbim_last_error(shbim_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 int shbim_set_precision(shbim_ctx* ctx, int precision) {
   if (!ctx) return SHBIM_ERR_ARG;
-  if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_FP32_COMP)
-    return fail(ctx, SHBIM_ERR_ARG, "precision must be SHBIM_PREC_FP64 or SHBIM_PREC_FP32_COMP");
+  if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_FP32_COMP && precision != SHBIM_PREC_DF64)
+    return fail(ctx, SHBIM_ERR_ARG, "precision must be SHBIM_PREC_FP64, SHBIM_PREC_FP32_COMP or SHBIM_PREC_DF64");
   ctx->opts.precision = precision;
   return SHBIM_OK;
 }
@@ -185,6 +192,14 @@ int shbim_set_R(shbim_ctx* ctx, double R) {
 int64_t shbim_launch_count(shbim_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
 int64_t shbim_operator_applications(shbim_ctx* ctx) { return ctx ? ctx->applications : -1; }
+
+int shbim_set_rows_precision(shbim_ctx* ctx, int precision) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_DF64)
+    return fail(ctx, SHBIM_ERR_ARG, "row precision must be SHBIM_PREC_FP64 or SHBIM_PREC_DF64");
+  ctx->rows_prec = precision;
+  return SHBIM_OK;
+}
 
 int shbim_set_autotune(shbim_ctx* ctx, int on) {
   if (!ctx) return SHBIM_ERR_ARG;
@@ -284,9 +299,11 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
       (rc = dalloc(ctx, &ctx->geo.src, 7 * (size_t)so, "sources")) ||
       (rc = dalloc(ctx, &ctx->geo.tgt32, 7 * (size_t)to, "targets32")) ||
       (rc = dalloc(ctx, &ctx->geo.src32, 7 * (size_t)so, "sources32")) ||
+      (rc = dalloc(ctx, &ctx->geo.src32lo, 7 * (size_t)so, "sources32 low parts")) ||
       (rc = dalloc(ctx, &ctx->geo.tgt_drop, (size_t)to, "target drop ids")) ||
       (rc = dalloc(ctx, &ctx->dens_up, 6 * (size_t)so, "source strengths")) ||
       (rc = dalloc(ctx, &ctx->dens_up32, 6 * (size_t)so, "source strengths32")) ||
+      (rc = dalloc(ctx, &ctx->dens_up32lo, 6 * (size_t)so, "source strengths32 low parts")) ||
       (rc = dalloc(ctx, &ctx->grid_out, 3 * (size_t)to, "target values")) ||
       (rc = dalloc(ctx, &ctx->xup, 3 * (size_t)kNumTab * so, "position derivatives")))
     return rc;
@@ -366,7 +383,8 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   if (out_kind != SHBIM_OUT_GRID && out_kind != SHBIM_OUT_COEF) return fail(ctx, SHBIM_ERR_ARG, "bad out kind");
   if (!dens_dev || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
   cudaStream_t s = (cudaStream_t)stream;
-  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;   // FP32 copies (FP32 and double-float sums)
+  const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
   int rc;
   ctx->applications++;
   if (ctx->n_drops > 1) {
@@ -374,7 +392,8 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
     for (auto& d : ctx->drops) {
       rc = sht_synth_scaled(ctx, d.tab->up, 1, dens_dev + d.coef_off, d.nc, ctx->dens_up + d.src_off, 0,
                             ctx->geo.src + 6 * ctx->nsource + d.src_off, 1.0,
-                            f32 ? ctx->dens_up32 + d.src_off : nullptr, s);
+                            f32 ? ctx->dens_up32 + d.src_off : nullptr, s,
+                            lo ? ctx->dens_up32lo + d.src_off : nullptr);
       if (rc) return rc;
     }
   }
@@ -406,7 +425,8 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   if (out_kind != SHBIM_OUT_GRID && out_kind != SHBIM_OUT_COEF) return fail(ctx, SHBIM_ERR_ARG, "bad out kind");
   if (!out_dev) return fail(ctx, SHBIM_ERR_ARG, "null output");
   cudaStream_t s = (cudaStream_t)stream;
-  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
+  const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
   const int64_t NS = ctx->nsource;
   int rc;
   ctx->applications++;
@@ -416,13 +436,15 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
       const double* w = ctx->geo.src + 6 * NS + d.src_off;
       if (f_dev) {
         rc = sht_synth_scaled(ctx, d.tab->up, 3, f_dev + 3 * d.coef_off, d.nc, ctx->dens_up + d.src_off, NS,
-                              w, 1.0, f32 ? ctx->dens_up32 + d.src_off : nullptr, s);
+                              w, 1.0, f32 ? ctx->dens_up32 + d.src_off : nullptr, s,
+                              lo ? ctx->dens_up32lo + d.src_off : nullptr);
         if (rc) return rc;
       }
       if (u_dev) {
         rc = sht_synth_scaled(ctx, d.tab->up, 3, u_dev + 3 * d.coef_off, d.nc,
                               ctx->dens_up + 3 * NS + d.src_off, NS, w, -6.0 * (d.lam - 1.0),
-                              f32 ? ctx->dens_up32 + 3 * NS + d.src_off : nullptr, s);
+                              f32 ? ctx->dens_up32 + 3 * NS + d.src_off : nullptr, s,
+                              lo ? ctx->dens_up32lo + 3 * NS + d.src_off : nullptr);
         if (rc) return rc;
       }
     }

@@ -168,7 +168,7 @@ int matvec_eager(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
 int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
   auto& G = ctx->gm;
   if (!ctx->graphs_on || ctx->timing) return matvec_eager(ctx, v, out, s);
-  auto& GR = ctx->graphs[G.sys * 2 + (ctx->opts.precision == SHBIM_PREC_FP32_COMP ? 1 : 0)];
+  auto& GR = ctx->graphs[G.sys * 3 + ctx->opts.precision];
   if (GR.version != ctx->geom_version || GR.n != G.n) {
     if (GR.exec) cudaGraphExecDestroy(GR.exec);
     GR.exec = nullptr;
@@ -474,6 +474,14 @@ int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
   return SHBIM_OK;
 }
 
+int shbim_set_outer_precision(shbim_ctx* ctx, int precision) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_DF64)
+    return fail(ctx, SHBIM_ERR_ARG, "outer precision must be SHBIM_PREC_FP64 or SHBIM_PREC_DF64");
+  ctx->outer_prec = precision;
+  return SHBIM_OK;
+}
+
 int shbim_set_diffusion(shbim_ctx* ctx, double c) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (!(c >= 0.0) || !std::isfinite(c)) return fail(ctx, SHBIM_ERR_ARG, "diffusion coefficient must be >= 0");
@@ -526,8 +534,8 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
   // ||b||, through the GMRES set-up of the system (FP64 residual)
   double bnorm = 0.0;
   for (;;) {
-    // FP64 residual r = b - A x
-    ctx->opts.precision = SHBIM_PREC_FP64;
+    // FP64-class residual r = b - A x (FP64 or double-float sums)
+    ctx->opts.precision = ctx->outer_prec;
     rc = shbim_gmres_begin(ctx, sys, rhs_dev, nullptr, stream);  // sets diag/offdiag, b, ||b||
     if (rc) break;
     bnorm = G.bnorm;

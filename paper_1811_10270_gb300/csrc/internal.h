@@ -54,6 +54,12 @@ struct DegreeTables {
   double* dq = nullptr;      // rotation matrix blocks of Rx(pi/2), sum_n (2n+1)^2 doubles
   std::vector<int> dq_off;   // host copy of block offsets (n -> offset)
   int* dq_off_dev = nullptr;
+  // double-float copies (hi, lo) for the double-float singular-row build (singular_df.cu)
+  float2* up_alf_df = nullptr;   // [2p+2 latitudes][3][ntri(p)]: Pbar, dPbar/dtheta, m Pbar/sin
+  float2* up_trig_df = nullptr;  // [2][4p+4]: cos, sin of 2 pi k / (4p+4)
+  float2* dq_df = nullptr;       // as dq
+  float2* cs_theta_df = nullptr; // [p+1 base latitudes][2][p+1]: cos(m theta_j), sin(m theta_j)
+  float2* cs_phi_df = nullptr;   // [2p+2 base longitudes][2][p+1]: cos(m phi_k), sin(m phi_k)
 };
 
 struct Drop {
@@ -94,6 +100,7 @@ struct Geometry {
   // FP32 copies relative to the drop centre: targets (hi) and sources
   float* tgt32 = nullptr;   // x y z nx ny nz  relative position + normal, each [ntarget]
   float* src32 = nullptr;   // x y z nx ny nz w, each [nsource]
+  float* src32lo = nullptr; // low parts: value - (double)src32, same layout (double-float sums)
   int* tgt_drop = nullptr;  // [ntarget]
   double* centres = nullptr;// [n_drops][3]
   int64_t* src_start = nullptr;  // [n_drops+1]
@@ -122,9 +129,12 @@ struct shbim_ctx {
     bool tuned = false;
   } pair_cfg[3];
   bool autotune = true;           // off: every layout keeps the default launch shape
+  int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
+  int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
-  float* dens_up32 = nullptr;     // [3][nsource] source strengths (FP32)
+  float* dens_up32 = nullptr;     // [6][nsource] source strengths (FP32)
+  float* dens_up32lo = nullptr;   // [6][nsource] low parts of the strengths (double-float sums)
   double* part = nullptr;         // [pair_splits][3][ntarget] partial sums
   double* grid_out = nullptr;     // [3][ntarget] operator values before projection
   double* xup = nullptr;          // per drop [3][kNumTab][ns]: position and derivatives on the up grid
@@ -175,6 +185,8 @@ struct shbim_ctx {
     float* fgeo32 = nullptr;  size_t fgeo32_cap = 0;  // same, positions relative to the centre
     double* fstr = nullptr;   size_t fstr_cap = 0;    // [6][nfine] upsampled strengths
     float* fstr32 = nullptr;  size_t fstr32_cap = 0;
+    float* fgeo32lo = nullptr;  size_t fgeo32lo_cap = 0;  // low parts (double-float sums)
+    float* fstr32lo = nullptr;  size_t fstr32lo_cap = 0;
     int64_t* foff_dev = nullptr; size_t foff_cap = 0; // [2][n_drops]: offset, count
     std::vector<int64_t> fine_off_h, fine_n_h;
     int64_t nfine = 0;
@@ -205,7 +217,7 @@ struct shbim_ctx {
     int64_t version = -1;
     int64_t kernels = 0;   // kernel nodes per replay
     bool warm = false;
-  } graphs[6];
+  } graphs[9];                    // [system][precision]
   double diff_c = 0.0;            // coefficient of the diffusion system
   // optional per-class kernel timing
   bool timing = false;
@@ -259,9 +271,10 @@ void free_degree_tables(DegreeTables* t);
 int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
               int64_t coef_stride, int kinds, double* out, int64_t item_stride,
               int64_t kind_stride, const double* scale, float* out32, cudaStream_t s);
+// out32lo (optional) receives value - (double)out32 as float (the low part of a double-float copy)
 int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
                      int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
-                     double alpha, float* out32, cudaStream_t s);
+                     double alpha, float* out32, cudaStream_t s, float* out32lo = nullptr);
 // Analysis: coef[item] = sum_nodes w(node) vals[item][node] S_nm(node) with w = omega_j when
 // weighted, else 1. Uses ctx->sht_scratch (grown as needed).
 int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double* vals,
@@ -271,6 +284,8 @@ int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double*
 // ---- geometry / singular rows (singular.cu)
 int build_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 int build_singular_rows(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
+// the same rows computed in double-float arithmetic on the FP32 pipe (singular_df.cu)
+int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef_dev);
 // out[t] (+)= self rows . density for every target (scalar Laplace kind or Stokes tensors).
 int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
 int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out,
@@ -284,7 +299,8 @@ int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* 
 int geometry_kernel(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
                     int64_t ld, int64_t off, cudaStream_t s);
 int geometry_kernel32(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
-                      float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s);
+                      float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s,
+                      float* out32lo = nullptr);
 
 // ---- surface Laplacian (physics.cu)
 int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream_t s);

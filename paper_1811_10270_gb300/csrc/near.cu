@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace shbim {
@@ -183,6 +184,51 @@ __device__ void near_sum64(const double* __restrict__ pos, int64_t stride, const
   for (int c = 0; c < 3; ++c) acc[c] = a[c];
 }
 
+// Double-float version (FP64-class accuracy on the FP32 pipe): positions, normals and strengths
+// are (FP32 copy, low part) pairs relative to drop j's centre; T is the target offset.
+template <int KIND>
+__device__ void near_sum_df(const float* __restrict__ pos, const float* __restrict__ poslo, int64_t stride,
+                            const float* __restrict__ str, const float* __restrict__ strlo, int64_t sstride,
+                            int64_t n, const dfl::df T[3], const dfl::df nv[3], int has_f, int has_u,
+                            double acc[3]) {
+  using dfl::df;
+  dfl::acc A[3];
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+    const df dx = dfl::diff(T[0], df{pos[e], poslo[e]});
+    const df dy = dfl::diff(T[1], df{pos[stride + e], poslo[stride + e]});
+    const df dz = dfl::diff(T[2], df{pos[2 * stride + e], poslo[2 * stride + e]});
+    const df ri = dfl::rsqrt(dfl::dot3(dx, dy, dz, dx, dy, dz));
+    if (KIND == 1) {
+      A[0].add_prod(df{str[e], strlo[e]}, ri);
+    } else if (KIND == 0) {
+      const df dn = dfl::dot3(dx, dy, dz, nv[0], nv[1], nv[2]);
+      A[0].add_prod(dfl::mul(df{str[e], strlo[e]}, dfl::mul(dfl::sqr(ri), ri)), dn);
+    } else {
+      df f[3], u[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        f[c] = has_f ? df{str[c * sstride + e], strlo[c * sstride + e]} : df{0.f, 0.f};
+        u[c] = has_u ? df{str[(3 + c) * sstride + e], strlo[(3 + c) * sstride + e]} : df{0.f, 0.f};
+      }
+      const df nx{pos[3 * stride + e], poslo[3 * stride + e]}, ny{pos[4 * stride + e], poslo[4 * stride + e]},
+          nz{pos[5 * stride + e], poslo[5 * stride + e]};
+      const df hf = dfl::dot3(dx, dy, dz, f[0], f[1], f[2]);
+      const df hu = dfl::dot3(dx, dy, dz, u[0], u[1], u[2]);
+      const df hn = dfl::dot3(dx, dy, dz, nx, ny, nz);
+      const df ri2 = dfl::sqr(ri);
+      const df tt = dfl::mul(dfl::mul(ri2, ri), dfl::add(hf, dfl::mul(dfl::mul(hu, hn), ri2)));
+      const df d[3] = {dx, dy, dz};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        A[c].add_prod(f[c], ri);
+        A[c].add_prod(d[c], tt);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = dfl::to_double(A[c].value());
+}
+
 struct NearArgs {
   const int64_t* pair_t;
   const int* pair_j;
@@ -202,12 +248,18 @@ struct NearArgs {
   const double* sstr;        // [6][nsource] degree-q strengths (dens_up)
   const float* sstr32;
   int64_t nsource;
+  const float* fpos32lo;     // low parts for the double-float sums
+  const float* fstr32lo;
+  const float* src32lo;
+  const float* sstr32lo;
   int has_f, has_u;
   double* out;
 };
 
-template <int KIND, bool F32>
+// MODE 0: FP64, 1: FP32 compensated, 2: double-float
+template <int KIND, int MODE>
 __global__ void __launch_bounds__(256) k_near_direct(NearArgs A) {
+  constexpr bool F32 = MODE == 1;
   const int pr = blockIdx.x;
   const int64_t t = A.pair_t[pr];
   const int j = A.pair_j[pr];
@@ -233,6 +285,17 @@ __global__ void __launch_bounds__(256) k_near_direct(NearArgs A) {
     near_sum32<KIND>(A.fpos32 + fo, A.nfine, A.fstr32 + fo, A.nfine, fn, th, tl, n32, A.has_f, A.has_u, af);
     near_sum32<KIND>(A.src32 + D.src_off, A.nsource, A.sstr32 + D.src_off, A.nsource, D.ns, th, tl, n32,
                      A.has_f, A.has_u, au);
+  } else if (MODE == 2) {
+    dfl::df T[3], nd[3];
+    T[0] = dfl::from_double(x0[0] - D.cx);
+    T[1] = dfl::from_double(x0[1] - D.cy);
+    T[2] = dfl::from_double(x0[2] - D.cz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nd[c] = dfl::from_double(nv[c]);
+    near_sum_df<KIND>(A.fpos32 + fo, A.fpos32lo + fo, A.nfine, A.fstr32 + fo, A.fstr32lo + fo, A.nfine, fn, T, nd,
+                      A.has_f, A.has_u, af);
+    near_sum_df<KIND>(A.src32 + D.src_off, A.src32lo + D.src_off, A.nsource, A.sstr32 + D.src_off,
+                      A.sstr32lo + D.src_off, A.nsource, D.ns, T, nd, A.has_f, A.has_u, au);
   } else {
     near_sum64<KIND>(A.fpos + fo, A.nfine, A.fstr + fo, A.nfine, fn, x0, nv, A.has_f, A.has_u, af);
     near_sum64<KIND>(A.src + D.src_off, A.nsource, A.sstr + D.src_off, A.nsource, D.ns, x0, nv, A.has_f,
@@ -339,6 +402,8 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
       (rc = grow(ctx, (void**)&N.fgeo32, &N.fgeo32_cap, sizeof(float) * 7 * nfine, "fine geometry")) ||
       (rc = grow(ctx, (void**)&N.fstr, &N.fstr_cap, sizeof(double) * 6 * nfine, "fine strengths")) ||
       (rc = grow(ctx, (void**)&N.fstr32, &N.fstr32_cap, sizeof(float) * 6 * nfine, "fine strengths")) ||
+      (rc = grow(ctx, (void**)&N.fgeo32lo, &N.fgeo32lo_cap, sizeof(float) * 7 * nfine, "fine geometry low parts")) ||
+      (rc = grow(ctx, (void**)&N.fstr32lo, &N.fstr32lo_cap, sizeof(float) * 6 * nfine, "fine strengths low parts")) ||
       (rc = grow(ctx, (void**)&N.foff_dev, &N.foff_cap, sizeof(int64_t) * 2 * nd, "fine offsets")))
     return rc;
   {
@@ -360,7 +425,8 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
     const int64_t n = N.fine_n_h[j];
     rc = sht_synth(ctx, fine, 3, xcoef + 3 * d.coef_off, d.nc, 7, tmp, 3 * n, n, nullptr, nullptr, s);
     if (rc == SHBIM_OK)
-      rc = geometry_kernel32(ctx, tmp, n, 3, fine, N.fgeo, N.fgeo32, nfine, N.fine_off_h[j], d.centre, s);
+      rc = geometry_kernel32(ctx, tmp, n, 3, fine, N.fgeo, N.fgeo32, nfine, N.fine_off_h[j], d.centre, s,
+                             N.fgeo32lo);
   }
   cudaStreamSynchronize(s);
   cudaFree(tmp);
@@ -373,15 +439,22 @@ int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out,
   auto& N = ctx->near;
   NearArgs A{N.pair_t, N.pair_j, N.foff_dev, N.foff_dev + ctx->n_drops, ctx->drops_dev, ctx->geo.tgt_drop,
              ctx->geo.tgt, ctx->ntarget, N.fgeo, N.fgeo32, N.fstr, N.fstr32, N.nfine, ctx->geo.src,
-             ctx->geo.src32, ctx->dens_up, ctx->dens_up32, ctx->nsource, has_f ? 1 : 0, has_u ? 1 : 0, out};
-  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+             ctx->geo.src32, ctx->dens_up, ctx->dens_up32, ctx->nsource, N.fgeo32lo, N.fstr32lo,
+             ctx->geo.src32lo, ctx->dens_up32lo, has_f ? 1 : 0, has_u ? 1 : 0, out};
+  const int mode = ctx->opts.precision == SHBIM_PREC_FP32_COMP ? 1 : (ctx->opts.precision == SHBIM_PREC_DF64 ? 2 : 0);
   const unsigned g = (unsigned)N.npairs;
   if (kind == 0) {
-    if (f32) k_near_direct<0, true><<<g, 256, 0, s>>>(A); else k_near_direct<0, false><<<g, 256, 0, s>>>(A);
+    if (mode == 1) k_near_direct<0, 1><<<g, 256, 0, s>>>(A);
+    else if (mode == 2) k_near_direct<0, 2><<<g, 256, 0, s>>>(A);
+    else k_near_direct<0, 0><<<g, 256, 0, s>>>(A);
   } else if (kind == 1) {
-    if (f32) k_near_direct<1, true><<<g, 256, 0, s>>>(A); else k_near_direct<1, false><<<g, 256, 0, s>>>(A);
+    if (mode == 1) k_near_direct<1, 1><<<g, 256, 0, s>>>(A);
+    else if (mode == 2) k_near_direct<1, 2><<<g, 256, 0, s>>>(A);
+    else k_near_direct<1, 0><<<g, 256, 0, s>>>(A);
   } else {
-    if (f32) k_near_direct<2, true><<<g, 256, 0, s>>>(A); else k_near_direct<2, false><<<g, 256, 0, s>>>(A);
+    if (mode == 1) k_near_direct<2, 1><<<g, 256, 0, s>>>(A);
+    else if (mode == 2) k_near_direct<2, 2><<<g, 256, 0, s>>>(A);
+    else k_near_direct<2, 0><<<g, 256, 0, s>>>(A);
   }
   SHBIM_CHECK_LAUNCH(ctx, "k_near_direct");
   return SHBIM_OK;
@@ -392,13 +465,15 @@ int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out,
 int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s) {
   auto& N = ctx->near;
   if (N.npairs == 0) return SHBIM_OK;
-  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
+  const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
   for (int j = 0; j < ctx->n_drops; ++j) {
     if (N.fine_off_h[j] < 0) continue;
     const Drop& d = ctx->drops[j];
     const int64_t o = N.fine_off_h[j];
     int rc = sht_synth_scaled(ctx, d.tab->fine, 1, dens + d.coef_off, d.nc, N.fstr + o, 0,
-                              N.fgeo + 6 * N.nfine + o, 1.0, f32 ? N.fstr32 + o : nullptr, s);
+                              N.fgeo + 6 * N.nfine + o, 1.0, f32 ? N.fstr32 + o : nullptr, s,
+                              lo ? N.fstr32lo + o : nullptr);
     if (rc) return rc;
   }
   return launch_direct(ctx, which == SHBIM_LAPLACE_SL ? 1 : 0, false, false, out, s);
@@ -407,7 +482,8 @@ int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* ou
 int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s) {
   auto& N = ctx->near;
   if (N.npairs == 0) return SHBIM_OK;
-  const bool f32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
+  const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
+  const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
   for (int j = 0; j < ctx->n_drops; ++j) {
     if (N.fine_off_h[j] < 0) continue;
     const Drop& d = ctx->drops[j];
@@ -415,11 +491,11 @@ int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* 
     const double* w = N.fgeo + 6 * N.nfine + o;
     int rc;
     if (f && (rc = sht_synth_scaled(ctx, d.tab->fine, 3, f + 3 * d.coef_off, d.nc, N.fstr + o, N.nfine, w, 1.0,
-                                    f32 ? N.fstr32 + o : nullptr, s)))
+                                    f32 ? N.fstr32 + o : nullptr, s, lo ? N.fstr32lo + o : nullptr)))
       return rc;
     if (u && (rc = sht_synth_scaled(ctx, d.tab->fine, 3, u + 3 * d.coef_off, d.nc, N.fstr + 3 * N.nfine + o,
                                     N.nfine, w, -6.0 * (d.lam - 1.0), f32 ? N.fstr32 + 3 * N.nfine + o : nullptr,
-                                    s)))
+                                    s, lo ? N.fstr32lo + 3 * N.nfine + o : nullptr)))
       return rc;
   }
   return launch_direct(ctx, 2, f != nullptr, u != nullptr, out, s);

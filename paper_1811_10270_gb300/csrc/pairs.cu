@@ -10,6 +10,12 @@
 // kernel adds the splits in a fixed order (deterministic). TPT and the split count are chosen per
 // kernel kind and drop layout by timing the candidates on the first FP32 launch (autotune).
 //
+// Double-float path (FP64-class accuracy on the FP32 pipe): every source coordinate, normal and
+// strength is the pair (FP32 copy, FP32 low part of the FP64 value), the target offset from the
+// source drop's centre likewise; differences, r^2, 1/r (Newton from the FP32 seed), products and
+// the running sums are double-float (~2^-44 relative per operation; error-free transformations
+// of Knuth and Dekker). On this GPU that is several times faster than FP64 arithmetic.
+//
 // FP32 path: sources are stored relative to their drop centre in FP32; for every (target,
 // source drop) the target offset x0 - c_j is formed in FP64 and kept as an unevaluated FP32
 // sum hi + lo, so xh = (hi - xs) + lo carries an error of order eps * r rather than
@@ -17,6 +23,7 @@
 // added to a (hi, lo) accumulator with the two-sum of Knuth (compensated accumulation).
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace shbim {
@@ -210,6 +217,114 @@ k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
   }
 }
 
+template <int KIND>
+__global__ void __launch_bounds__(kThreads)
+k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
+           const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ src32,
+           const float* __restrict__ src32lo, int64_t nsource, const float* __restrict__ dens32,
+           const float* __restrict__ dens32lo, int nsplit, int has_f, int has_u, double* __restrict__ part) {
+  using dfl::df;
+  constexpr int NC = (KIND == STO) ? 3 : 1;
+  constexpr int NV = (KIND == STO) ? 6 : 2;   // float4 per staged source
+  __shared__ float4 sh[NV][kTile];
+  PairTile tile;
+  if (!sub_tile<1>(tiles, tile)) return;
+  const int i = tile.drop;
+  const DropDev Di = drops[i];
+  const int64_t other = nsource - Di.ns;
+  const int64_t chunk = (other + nsplit - 1) / nsplit;
+  const int64_t v0 = (int64_t)blockIdx.y * chunk;
+  const int64_t v1 = min(other, v0 + chunk);
+  const int64_t tg = tile.t0 + threadIdx.x;
+  const bool ok = (int)threadIdx.x < tile.nt;
+  const int64_t t = ok ? tg : tile.t0;
+  double X0[3];
+  df N0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    X0[c] = tgt[c * ntarget + t];
+    N0[c] = dfl::from_double(tgt[(3 + c) * ntarget + t]);
+  }
+  dfl::acc A[NC];
+  for (int j = 0; j < n_drops; ++j) {
+    if (j == i) continue;
+    const DropDev Dj = drops[j];
+    const SrcRange rg = drop_range(Di, Dj, i, j, v0, v1);
+    if (rg.a >= rg.b) continue;
+    const df T0 = dfl::from_double(X0[0] - Dj.cx), T1 = dfl::from_double(X0[1] - Dj.cy),
+             T2 = dfl::from_double(X0[2] - Dj.cz);
+    for (int64_t base = rg.a; base < rg.b; base += kTile) {
+      const int cnt = (int)min((int64_t)kTile, rg.b - base);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += kThreads) {
+        const int64_t sI = base + e;
+        const float xh = src32[sI], yh = src32[nsource + sI], zh = src32[2 * nsource + sI];
+        const float xl = src32lo[sI], yl = src32lo[nsource + sI], zl = src32lo[2 * nsource + sI];
+        if (KIND != STO) {
+          sh[0][e] = make_float4(xh, yh, zh, xl);
+          sh[1][e] = make_float4(yl, zl, dens32[sI], dens32lo[sI]);
+        } else {
+          float fv[6], uv[6];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            fv[2 * c] = has_f ? dens32[c * nsource + sI] : 0.f;
+            fv[2 * c + 1] = has_f ? dens32lo[c * nsource + sI] : 0.f;
+            uv[2 * c] = has_u ? dens32[(3 + c) * nsource + sI] : 0.f;
+            uv[2 * c + 1] = has_u ? dens32lo[(3 + c) * nsource + sI] : 0.f;
+          }
+          sh[0][e] = make_float4(xh, yh, zh, xl);
+          sh[1][e] = make_float4(yl, zl, fv[0], fv[1]);
+          sh[2][e] = make_float4(fv[2], fv[3], fv[4], fv[5]);
+          sh[3][e] = make_float4(uv[0], uv[1], uv[2], uv[3]);
+          sh[4][e] = make_float4(uv[4], uv[5], src32[3 * nsource + sI], src32lo[3 * nsource + sI]);
+          sh[5][e] = make_float4(src32[4 * nsource + sI], src32lo[4 * nsource + sI], src32[5 * nsource + sI],
+                                 src32lo[5 * nsource + sI]);
+        }
+      }
+      __syncthreads();
+      for (int e = 0; e < cnt; ++e) {
+        const float4 a = sh[0][e], b = sh[1][e];
+        const df dx = dfl::diff(T0, df{a.x, a.w});
+        const df dy = dfl::diff(T1, df{a.y, b.x});
+        const df dz = dfl::diff(T2, df{a.z, b.y});
+        const df r2 = dfl::dot3(dx, dy, dz, dx, dy, dz);
+        const df ri = dfl::rsqrt(r2);
+        if (KIND == LSL) {
+          A[0].add_prod(df{b.z, b.w}, ri);
+        } else if (KIND == LDL) {
+          const df dn = dfl::dot3(dx, dy, dz, N0[0], N0[1], N0[2]);
+          const df ri3 = dfl::mul(dfl::sqr(ri), ri);
+          A[0].add_prod(dfl::mul(df{b.z, b.w}, ri3), dn);
+        } else {
+          const float4 c4 = sh[2][e], d4 = sh[3][e], e4 = sh[4][e], g4 = sh[5][e];
+          const df fx{b.z, b.w}, fy{c4.x, c4.y}, fz{c4.z, c4.w};
+          const df ux{d4.x, d4.y}, uy{d4.z, d4.w}, uz{e4.x, e4.y};
+          const df nx{e4.z, e4.w}, ny{g4.x, g4.y}, nz{g4.z, g4.w};
+          const df hf = dfl::dot3(dx, dy, dz, fx, fy, fz);
+          const df hu = dfl::dot3(dx, dy, dz, ux, uy, uz);
+          const df hn = dfl::dot3(dx, dy, dz, nx, ny, nz);
+          const df ri2 = dfl::sqr(ri);
+          const df ri3 = dfl::mul(ri2, ri);
+          const df tt = dfl::mul(ri3, dfl::add(hf, dfl::mul(dfl::mul(hu, hn), ri2)));
+          A[0].add_prod(fx, ri);
+          A[0].add_prod(dx, tt);
+          A[1].add_prod(fy, ri);
+          A[1].add_prod(dy, tt);
+          A[2].add_prod(fz, ri);
+          A[2].add_prod(dz, tt);
+        }
+      }
+    }
+  }
+  if (!ok) return;
+  double* P = part + (int64_t)blockIdx.y * NC * ntarget;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int64_t o = (NC == 1) ? tg : 3 * Di.tgt_off + (int64_t)c * Di.nt + (tg - Di.tgt_off);
+    P[o] = 0.07957747154594766788 * dfl::to_double(A[c].value());
+  }
+}
+
 template <int KIND, int kTPT>
 __global__ void __launch_bounds__(kThreads)
 k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
@@ -319,7 +434,11 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int6
 template <int KIND, int TPT>
 void launch_shape(shbim_ctx* ctx, bool has_f, bool has_u, int splits, cudaStream_t s) {
   dim3 grid((unsigned)(ctx->tiles.size() * (kMaxTPT / TPT)), splits);
-  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
+  if (ctx->opts.precision == SHBIM_PREC_DF64) {
+    k_pairs_df<KIND><<<dim3((unsigned)(ctx->tiles.size() * kMaxTPT), splits), kThreads, 0, s>>>(
+        ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt, ctx->ntarget, ctx->geo.src32,
+        ctx->geo.src32lo, ctx->nsource, ctx->dens_up32, ctx->dens_up32lo, splits, has_f, has_u, ctx->part);
+  } else if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
     k_pairs32<KIND, TPT><<<grid, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
                                                    ctx->ntarget, ctx->geo.src32, ctx->nsource, ctx->dens_up32,
                                                    splits, has_f, has_u, ctx->part);
@@ -393,9 +512,11 @@ int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
     int rc = autotune<KIND>(ctx, has_f, has_u, s);
     if (rc) return rc;
   }
-  // the FP64 kernels keep the layout's default shape (the FP64 pipe bounds them)
+  // the FP64 and double-float kernels keep the layout's default shape (4 CTAs per tile for
+  // double-float, one target per thread)
   const bool fp32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
-  const int tpt = fp32 ? C.tpt : 2, splits = fp32 ? C.splits : ctx->pair_splits;
+  const int tpt = fp32 ? C.tpt : (ctx->opts.precision == SHBIM_PREC_DF64 ? 1 : 2);
+  const int splits = fp32 ? C.splits : ctx->pair_splits;
   launch_raw<KIND>(ctx, has_f, has_u, tpt, splits, s);
   SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
   const int64_t n = NC * ctx->ntarget;

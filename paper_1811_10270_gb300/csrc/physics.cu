@@ -236,10 +236,12 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   // (ii) phi_q = S_L[(1 - 1/R) E_n]
   k_lincomb<<<nb(n), 256, 0, s>>>(q, En, 1.0 - 1.0 / R, En, 0.0, n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
-  // one-shot applications (not iterated by GMRES) always use FP64 sums: in mixed precision only
-  // the operator inside the inner GMRES runs in FP32
+  // one-shot applications (not iterated by GMRES) always use FP64-class sums: in mixed precision
+  // only the operator inside the inner GMRES runs in FP32, the rest uses the context's outer
+  // precision (FP64 or double-float)
   const int saved_prec = ctx->opts.precision;
-  ctx->opts.precision = SHBIM_PREC_FP64;
+  const int oneshot = saved_prec == SHBIM_PREC_FP32_COMP ? ctx->outer_prec : saved_prec;
+  ctx->opts.precision = oneshot;
   rc = shbim_eval_electric(ctx, SHBIM_LAPLACE_SL, q, phi, SHBIM_OUT_COEF, s);
   ctx->opts.precision = saved_prec;
   if (rc) return rc;
@@ -260,7 +262,7 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
     if ((rc = sht_analysis(ctx, g, 3, tv + o, NS, true, tco + 3 * d.coef_off, d.nc, s))) return rc;
   }
   // (vi) Stokes: (lam_i+1) u - sum (lam_j-1) D_j[u] = -sum_j S_j[f/Ca_E - f^E]
-  ctx->opts.precision = SHBIM_PREC_FP64;
+  ctx->opts.precision = oneshot;
   rc = shbim_eval_stokes(ctx, tco, nullptr, rhs_s, SHBIM_OUT_COEF, s);
   ctx->opts.precision = saved_prec;
   if (rc) return rc;

@@ -29,7 +29,8 @@ __device__ __forceinline__ int kind_of_slot(int kinds, int slot) {
 __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, int p, int q,
                         const double* __restrict__ alf, const double* __restrict__ trig, int kinds,
                         double* __restrict__ out, int64_t item_stride, int64_t kind_stride,
-                        const double* __restrict__ scale, double alpha, float* __restrict__ out32) {
+                        const double* __restrict__ scale, double alpha, float* __restrict__ out32,
+                        float* __restrict__ out32lo) {
   extern __shared__ double sm[];
   const int item = blockIdx.x;
   const int j = blockIdx.y;
@@ -85,7 +86,11 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
         if (kind == 0 && scale) v *= scale[node] * alpha;
         const int64_t o = (int64_t)item * item_stride + (int64_t)slot * kind_stride + node;
         out[o] = v;
-        if (out32) out32[o] = (float)v;
+        if (out32) {
+          const float h = (float)v;
+          out32[o] = h;
+          if (out32lo) out32lo[o] = (float)(v - (double)h);
+        }
       }
     }
     return;
@@ -118,7 +123,11 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
       if (kind == 0 && scale) v *= scale[node] * alpha;
       const int64_t o = (int64_t)item * item_stride + (int64_t)slot * kind_stride + node;
       out[o] = v;
-      if (out32) out32[o] = (float)v;
+      if (out32) {
+        const float h = (float)v;
+        out32[o] = h;
+        if (out32lo) out32lo[o] = (float)(v - (double)h);
+      }
     }
   }
 }
@@ -140,7 +149,7 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, kinds, out,
-                                  item_stride, kind_stride, scale, 1.0, out32);
+                                  item_stride, kind_stride, scale, 1.0, out32, nullptr);
   SHBIM_CHECK_LAUNCH(ctx, "k_synth");
   return SHBIM_OK;
 }
@@ -148,13 +157,13 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
 // Synthesis with a scalar factor on the scaled values (used for (lam_j - 1) strengths).
 int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
                      int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
-                     double alpha, float* out32, cudaStream_t s) {
+                     double alpha, float* out32, cudaStream_t s, float* out32lo) {
   if (n_items <= 0) return SHBIM_OK;
   const size_t smem = (size_t)(2 * (g.p + 1) + 3 * (2 * g.q + 2)) * sizeof(double);
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, 1, out, item_stride,
-                                  0, scale, alpha, out32);
+                                  0, scale, alpha, out32, out32 ? out32lo : nullptr);
   SHBIM_CHECK_LAUNCH(ctx, "k_synth");
   return SHBIM_OK;
 }

@@ -31,7 +31,7 @@ namespace shbim {
 __global__ void k_geometry(const double* __restrict__ tmp, int n, int nkind, int N,
                            const double* __restrict__ omega, int weighted, double* __restrict__ out,
                            int64_t ld, int64_t off, float* __restrict__ out32, double cx, double cy,
-                           double cz) {
+                           double cz, float* __restrict__ out32lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double X[3], Xt[3], Xp[3];
@@ -53,22 +53,27 @@ __global__ void k_geometry(const double* __restrict__ tmp, int n, int nkind, int
   if (out32) {
     const double r[7] = {X[0] - cx, X[1] - cy, X[2] - cz, v[3], v[4], v[5], w};
 #pragma unroll
-    for (int k = 0; k < 7; ++k) out32[k * ld + off + i] = (float)r[k];
+    for (int k = 0; k < 7; ++k) {
+      const float h = (float)r[k];
+      out32[k * ld + off + i] = h;
+      if (out32lo) out32lo[k * ld + off + i] = (float)(r[k] - (double)h);
+    }
   }
 }
 
 int geometry_kernel(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
                     int64_t ld, int64_t off, cudaStream_t s) {
   k_geometry<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(buf, (int)n, nkind, 2 * g.q + 2, g.omega, 1, out, ld, off,
-                                                         nullptr, 0.0, 0.0, 0.0);
+                                                         nullptr, 0.0, 0.0, 0.0, nullptr);
   SHBIM_CHECK_LAUNCH(ctx, "k_geometry");
   return SHBIM_OK;
 }
 
 int geometry_kernel32(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
-                      float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s) {
+                      float* out32, int64_t ld, int64_t off, const double* centre, cudaStream_t s,
+                      float* out32lo) {
   k_geometry<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(buf, (int)n, nkind, 2 * g.q + 2, g.omega, 1, out, ld, off,
-                                                         out32, centre[0], centre[1], centre[2]);
+                                                         out32, centre[0], centre[1], centre[2], out32lo);
   SHBIM_CHECK_LAUNCH(ctx, "k_geometry");
   return SHBIM_OK;
 }
@@ -97,7 +102,7 @@ int build_geometry(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
       const int64_t off = pass == 0 ? d.tgt_off : d.src_off;
       k_geometry<<<(n + 127) / 128, 128, 0, s>>>(buf, n, nkind, 2 * g.q + 2, g.omega, pass == 1 ? 1 : 0,
                                                  out, ld, off, out32, d.centre[0], d.centre[1],
-                                                 d.centre[2]);
+                                                 d.centre[2], pass == 0 ? nullptr : ctx->geo.src32lo);
       ctx->launches++;
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(ctx, e, "k_geometry");

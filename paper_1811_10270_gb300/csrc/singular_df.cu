@@ -1,0 +1,459 @@
+// Singular self rows (rotated-pole rule, Eq. mod_weights and Section 3.1) built in double-float
+// arithmetic on the FP32 pipe. Same algorithm as singular.cu, stage for stage:
+//   1. rotate the position coefficients so that the target is the north pole
+//      (b = D_R^T x with D_R = Dz(phi) Dq^T Dz(theta) Dq);
+//   2. synthesise the rotated x, x_theta, x_phi / sin on the degree 2p+1 grid and form the 14
+//      kernel weights mu J K / (4 pi) at every node (Laplace DL and SL, 6 Stokeslet and 6
+//      stresslet components);
+//   3. analyse the weights (Fourier stage folded four ways, then Legendre stage);
+//   4. rotate the coefficient rows back (row = D_R v) and store them in FP64.
+// Every sum and every pointwise operation is double-float (hi + lo FP32 pairs; Dekker products,
+// Knuth sums, Newton square roots), ~2^-44 relative per operation, so the rows agree with the
+// FP64 build to rounding level while the FP64 pipe (1/64 of the FP32 rate here) stays idle.
+#include <algorithm>
+
+#include "dfloat.cuh"
+#include "fourier.cuh"
+#include "internal.h"
+
+namespace shbim {
+
+namespace {
+
+using dfl::df;
+
+__device__ __forceinline__ df ld(const float2* p, int64_t i) {
+  const float2 v = p[i];
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ void st(float2* p, int64_t i, df v) { p[i] = make_float2(v.hi, v.lo); }
+
+__device__ __forceinline__ int isqrt_i(int o) {
+  int n = (int)sqrtf((float)o);
+  while ((n + 1) * (n + 1) <= o) ++n;
+  while (n * n > o) --n;
+  return n;
+}
+
+__device__ __forceinline__ int tri_off_i(int p, int m) { return m * (p + 1) - m * (m - 1) / 2; }
+
+// v <- Dz(sgn alpha) v with the (cos, sin)(m alpha) table cs = [2][p+1]
+__device__ void dz_df(float2* v, int p, const float2* __restrict__ cs, float sgn) {
+  const int nc = (p + 1) * (p + 1);
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+    const int n = isqrt_i(o);
+    const int m = o - n * n - n;
+    if (m <= 0) continue;
+    const df ca = ld(cs, m);
+    df sa = ld(cs, p + 1 + m);
+    if (sgn < 0) sa = dfl::neg(sa);
+    const df a = ld(v, o), b = ld(v, o - 2 * m);
+    st(v, o, dfl::sub(dfl::mul(ca, a), dfl::mul(sa, b)));
+    st(v, o - 2 * m, dfl::add(dfl::mul(sa, a), dfl::mul(ca, b)));
+  }
+}
+
+// out <- Dq in (transpose: Dq^T in), per degree block
+__device__ void dq_df(const float2* __restrict__ in, float2* __restrict__ out, int p, const float2* __restrict__ dq,
+                      const int* __restrict__ dq_off, bool transpose) {
+  const int nc = (p + 1) * (p + 1);
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+    const int n = isqrt_i(o);
+    const int m = o - n * n - n;
+    const int w = 2 * n + 1;
+    const float2* B = dq + dq_off[n];
+    const float2* x = in + n * n;
+    dfl::acc acc;
+    if (!transpose) {
+      const float2* row = B + (m + n) * w;
+      for (int c = 0; c < w; ++c) acc.add_prod(ld(row, c), ld(x, c));
+    } else {
+      const float2* col = B + (m + n);
+      for (int c = 0; c < w; ++c) acc.add_prod(ld(col, (int64_t)c * w), ld(x, c));
+    }
+    st(out, o, acc.value());
+  }
+}
+
+// b = D_R^T a for the position coefficients of target blockIdx.x, component blockIdx.y
+__global__ void k_rotate_fwd_df(const double* __restrict__ xc, int nc, int p, int t_begin,
+                                const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
+                                const float2* __restrict__ dq, const int* __restrict__ dq_off,
+                                float2* __restrict__ out) {
+  extern __shared__ float2 smf[];
+  float2* b0 = smf;
+  float2* b1 = smf + nc;
+  const int tl = t_begin + blockIdx.x;
+  const int f = blockIdx.y;
+  const int nlon = 2 * p + 2;
+  const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
+  const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) st(b0, o, dfl::from_double(xc[(int64_t)f * nc + o]));
+  __syncthreads();
+  dz_df(b0, p, cp, -1.f);
+  __syncthreads();
+  dq_df(b0, b1, p, dq, dq_off, false);
+  __syncthreads();
+  dz_df(b1, p, ct, -1.f);
+  __syncthreads();
+  dq_df(b1, out + ((int64_t)blockIdx.x * 3 + f) * nc, p, dq, dq_off, true);
+}
+
+// row = D_R v for target blockIdx.x and component blockIdx.y; stored in FP64
+__global__ void k_rotate_adj_df(const float2* __restrict__ vbuf, int nc, int p, int t_begin, int ncomp,
+                                const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
+                                const float2* __restrict__ dq, const int* __restrict__ dq_off,
+                                double* __restrict__ rows_lap, double* __restrict__ rows_sto) {
+  extern __shared__ float2 smf[];
+  float2* b0 = smf;
+  float2* b1 = smf + nc;
+  const int tl = t_begin + blockIdx.x;
+  const int c = blockIdx.y;
+  const int nlon = 2 * p + 2;
+  const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
+  const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
+  const float2* v = vbuf + ((int64_t)blockIdx.x * ncomp + c) * nc;
+  dq_df(v, b1, p, dq, dq_off, false);
+  __syncthreads();
+  dz_df(b1, p, ct, 1.f);
+  __syncthreads();
+  dq_df(b1, b0, p, dq, dq_off, true);
+  __syncthreads();
+  dz_df(b0, p, cp, 1.f);
+  __syncthreads();
+  double* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
+                            : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) dst[o] = dfl::to_double(ld(b0, o));
+}
+
+// Four-longitude Fourier synthesis (the parity folding of synth4) in double-float.
+__device__ void synth4_df(const float2* __restrict__ a, const float2* __restrict__ b, df a0, float beta, int p,
+                          int k, int N, const float2* __restrict__ tc, const float2* __restrict__ ts,
+                          float2* __restrict__ dst) {
+  dfl::acc ce, co, se, so;
+  int id = 0;
+  int m = 1;
+  for (; m + 1 <= p; m += 2) {
+    id += k;
+    if (id >= N) id -= N;
+    co.add_prod(ld(a, m), ld(tc, id));
+    so.add_prod(ld(b, m), ld(ts, id));
+    id += k;
+    if (id >= N) id -= N;
+    ce.add_prod(ld(a, m + 1), ld(tc, id));
+    se.add_prod(ld(b, m + 1), ld(ts, id));
+  }
+  if (m <= p) {
+    id += k;
+    if (id >= N) id -= N;
+    co.add_prod(ld(a, m), ld(tc, id));
+    so.add_prod(ld(b, m), ld(ts, id));
+  }
+  const df s2{1.41421353816986084f, 2.4203234971764687e-08f};  // sqrt(2) as hi + lo
+  const df CE = ce.value(), CO = co.value();
+  df SE = se.value(), SO = so.value();
+  if (beta < 0) {
+    SE = dfl::neg(SE);
+    SO = dfl::neg(SO);
+  } else if (beta == 0) {
+    SE = df{0.f, 0.f};
+    SO = df{0.f, 0.f};
+  }
+  const df c1 = dfl::add(CE, CO), s1 = dfl::add(SE, SO);
+  const df c2 = dfl::sub(CE, CO), s2v = dfl::sub(SO, SE);
+  const int h = N >> 1;
+  st(dst, k, dfl::add(a0, dfl::mul(s2, dfl::add(c1, s1))));
+  st(dst, (N - k) % N, dfl::add(a0, dfl::mul(s2, dfl::sub(c1, s1))));
+  st(dst, h - k, dfl::add(a0, dfl::mul(s2, dfl::add(c2, s2v))));
+  st(dst, h + k, dfl::add(a0, dfl::mul(s2, dfl::sub(c2, s2v))));
+}
+
+// For target blockIdx.x (chunk-local) and up-grid latitude blockIdx.y: synthesise the rotated
+// position and tangents, then the 14 kernel weights of every node of the latitude.
+__global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, const float2* __restrict__ alf,
+                                  const float2* __restrict__ trig, const double* __restrict__ mu,
+                                  const double* __restrict__ tgt, int64_t ntarget, int64_t tgt0,
+                                  float2* __restrict__ wbuf) {
+  extern __shared__ float2 smf[];
+  const int t = blockIdx.x;
+  const int j = blockIdx.y;
+  const int N = 2 * q + 2;
+  const int P1 = p + 1;
+  const int nc = P1 * P1;
+  const int nt = P1 * (p + 2) / 2;
+  float2* A = smf;            // [3 f][3 kind][2][P1]
+  float2* tc = A + 18 * P1;
+  float2* ts = tc + N;
+  float2* V = ts + N;         // [9][N]
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tc[i] = trig[i];
+    ts[i] = trig[N + i];
+  }
+  const float2* T = alf + (int64_t)j * 3 * nt;
+  const float2* cf = rot + (int64_t)t * 3 * nc;
+  for (int task = threadIdx.x; task < 18 * P1; task += blockDim.x) {
+    const int fk = task / (2 * P1);
+    const int r = task - fk * 2 * P1;
+    const int m = r >> 1;
+    const int cs = r & 1;
+    const int f = fk / 3, kind = fk - f * 3;
+    dfl::acc acc;
+    if (!(cs == 1 && m == 0)) {
+      const float2* col = T + kind * nt + tri_off_i(p, m);
+      const float2* c = cf + f * nc;
+      const int sg = cs ? -m : m;
+      for (int n = m; n <= p; ++n) acc.add_prod(ld(c, n * n + n + sg), ld(col, n - m));
+    }
+    st(A, (fk * 2 + cs) * P1 + m, acc.value());
+  }
+  __syncthreads();
+  const int Q4 = N >> 2;
+  for (int task = threadIdx.x; task < 9 * (Q4 + 1); task += blockDim.x) {
+    const int fk = task / (Q4 + 1);
+    const int k = task - fk * (Q4 + 1);
+    const float2* Ac = A + (fk * 2) * P1;
+    const float2* As = Ac + P1;
+    if (fk % 3 != 2)
+      synth4_df(Ac, As, ld(Ac, 0), 1.f, p, k, N, tc, ts, V + fk * N);
+    else
+      synth4_df(As, Ac, df{0.f, 0.f}, -1.f, p, k, N, tc, ts, V + fk * N);
+  }
+  __syncthreads();
+  const int64_t tg = tgt0 + t;
+  const df x0 = dfl::from_double(tgt[tg]), y0 = dfl::from_double(tgt[ntarget + tg]),
+           z0 = dfl::from_double(tgt[2 * ntarget + tg]);
+  const df n0x = dfl::from_double(tgt[3 * ntarget + tg]), n0y = dfl::from_double(tgt[4 * ntarget + tg]),
+           n0z = dfl::from_double(tgt[5 * ntarget + tg]);
+  const df w0 = dfl::from_double(mu[j] * 0.07957747154594766788);
+  const int64_t Ns = (int64_t)(q + 1) * N;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const df xt0 = ld(V, 1 * N + k), xt1 = ld(V, 4 * N + k), xt2 = ld(V, 7 * N + k);
+    const df xp0 = ld(V, 2 * N + k), xp1 = ld(V, 5 * N + k), xp2 = ld(V, 8 * N + k);
+    const df c0 = dfl::sub(dfl::mul(xt1, xp2), dfl::mul(xt2, xp1));
+    const df c1 = dfl::sub(dfl::mul(xt2, xp0), dfl::mul(xt0, xp2));
+    const df c2 = dfl::sub(dfl::mul(xt0, xp1), dfl::mul(xt1, xp0));
+    const df J2 = dfl::dot3(c0, c1, c2, c0, c1, c2);
+    const df rJ = dfl::rsqrt(J2);
+    const df J = dfl::mul(J2, rJ);
+    const df nx = dfl::mul(c0, rJ), ny = dfl::mul(c1, rJ), nz = dfl::mul(c2, rJ);
+    const df hx = dfl::diff(x0, ld(V, k)), hy = dfl::diff(y0, ld(V, 3 * N + k)), hz = dfl::diff(z0, ld(V, 6 * N + k));
+    const df r2 = dfl::dot3(hx, hy, hz, hx, hy, hz);
+    const df ri = dfl::rsqrt(r2);
+    const df ri2 = dfl::sqr(ri);
+    const df ri3 = dfl::mul(ri2, ri);
+    const df w = dfl::mul(w0, J);
+    const df hn = dfl::dot3(hx, hy, hz, nx, ny, nz);
+    const df d5 = dfl::mul(dfl::mul(dfl::mul_f(w, -6.f), hn), dfl::mul(ri3, ri2));
+    const df s3 = dfl::mul(w, ri3);
+    const df wr = dfl::mul(w, ri);
+    df out[14];
+    out[0] = dfl::mul(dfl::mul(w, dfl::dot3(hx, hy, hz, n0x, n0y, n0z)), ri3);
+    out[1] = wr;
+    const df sx = dfl::mul(s3, hx), sy = dfl::mul(s3, hy), sz = dfl::mul(s3, hz);
+    out[2] = dfl::add(wr, dfl::mul(sx, hx));
+    out[3] = dfl::mul(sx, hy);
+    out[4] = dfl::mul(sx, hz);
+    out[5] = dfl::add(wr, dfl::mul(sy, hy));
+    out[6] = dfl::mul(sy, hz);
+    out[7] = dfl::add(wr, dfl::mul(sz, hz));
+    const df dx = dfl::mul(d5, hx), dy = dfl::mul(d5, hy), dz = dfl::mul(d5, hz);
+    out[8] = dfl::mul(dx, hx);
+    out[9] = dfl::mul(dx, hy);
+    out[10] = dfl::mul(dx, hz);
+    out[11] = dfl::mul(dy, hy);
+    out[12] = dfl::mul(dy, hz);
+    out[13] = dfl::mul(dz, hz);
+    const int64_t node = (int64_t)j * N + k;
+#pragma unroll
+    for (int c = 0; c < 14; ++c) st(wbuf, ((int64_t)t * 14 + c) * Ns + node, out[c]);
+  }
+}
+
+// Fourier stage of the analysis, N divisible by 4, `rows` (item, latitude) rows per block:
+// F[row][cs][m] = sum_k v[k] (cos|sin)(m phi_k), folded k <-> N-k and k <-> N/2-k (unweighted).
+__global__ void k_analysis_f4_df(const float2* __restrict__ vals, int64_t val_stride, int p, int q,
+                                 const float2* __restrict__ trig, int64_t nrows, int rows, float2* __restrict__ F) {
+  extern __shared__ float2 smf[];
+  const int N = 2 * q + 2;
+  const int P1 = p + 1;
+  const int Q4 = N >> 2;
+  const int h = N >> 1;
+  float2* tc = smf;
+  float2* ts = tc + N;
+  float2* R = ts + N;  // per row: x[N] then the four folds [Q4 each]
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int nr = (int)min((int64_t)rows, nrows - r0);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tc[i] = trig[i];
+    ts[i] = trig[N + i];
+  }
+  for (int e = threadIdx.x; e < nr * N; e += blockDim.x) {
+    const int r = e / N, k = e - r * N;
+    const int64_t row = r0 + r;
+    const int64_t item = row / (q + 1), j = row - item * (q + 1);
+    R[r * 2 * N + k] = vals[item * val_stride + j * N + k];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * Q4; e += blockDim.x) {
+    const int r = e / Q4, k = e - r * Q4;
+    if (k == 0) continue;
+    const float2* x = R + r * 2 * N;
+    float2* ee = R + r * 2 * N + N;
+    const df xk = ld(x, k), xn = ld(x, N - k), xa = ld(x, h - k), xb = ld(x, h + k);
+    const df ek = dfl::add(xk, xn), ok = dfl::sub(xk, xn);
+    const df e2 = dfl::add(xa, xb), o2 = dfl::sub(xa, xb);
+    st(ee, k, dfl::add(ek, e2));
+    st(ee, Q4 + k, dfl::sub(ek, e2));
+    st(ee, 2 * Q4 + k, dfl::add(ok, o2));
+    st(ee, 3 * Q4 + k, dfl::sub(ok, o2));
+  }
+  __syncthreads();
+  for (int task = threadIdx.x; task < nr * 2 * P1; task += blockDim.x) {
+    const int r = task / (2 * P1);
+    const int tt = task - r * 2 * P1;
+    const int cs = tt / P1;
+    const int m = tt - cs * P1;
+    const float2* x = R + r * 2 * N;
+    const float2* fold = x + N;
+    const bool odd = m & 1;
+    const int r4 = m & 3;
+    dfl::acc acc;
+    const float2* src;
+    const float2* tb;
+    if (cs == 0) {
+      const df eq = dfl::add(ld(x, Q4), ld(x, 3 * Q4));
+      const df xh = ld(x, h);
+      acc.add(ld(x, 0));
+      acc.add(odd ? dfl::neg(xh) : xh);
+      if (r4 == 0) acc.add(eq);
+      if (r4 == 2) acc.add(dfl::neg(eq));
+      src = odd ? fold + Q4 : fold;
+      tb = tc;
+    } else {
+      const df oq = dfl::sub(ld(x, Q4), ld(x, 3 * Q4));
+      if (r4 == 1) acc.add(oq);
+      if (r4 == 3) acc.add(dfl::neg(oq));
+      src = odd ? fold + 2 * Q4 : fold + 3 * Q4;
+      tb = ts;
+    }
+    int id = 0;
+    for (int k = 1; k < Q4; ++k) {
+      id += m;
+      if (id >= N) id -= N;
+      acc.add_prod(ld(src, k), ld(tb, id));
+    }
+    st(F, (r0 + r) * 2 * P1 + tt, acc.value());
+  }
+}
+
+// Legendre stage: coef[item][n^2+n+-m] = s_m sum_j F[item][j][cs][m] Pbar_n^m(t_j)
+__global__ void k_analysis_leg_df(const float2* __restrict__ F, int p, int q, const float2* __restrict__ alf,
+                                  float2* __restrict__ coef, int64_t coef_stride) {
+  const int item = blockIdx.x;
+  const int nt = (p + 1) * (p + 2) / 2;
+  const int o = blockIdx.y * blockDim.x + threadIdx.x;
+  if (o >= nt) return;
+  int m = 0;
+  while (m < p && tri_off_i(p, m + 1) <= o) ++m;
+  const int n = m + (o - tri_off_i(p, m));
+  const int P1 = p + 1;
+  const float2* Fi = F + (int64_t)item * (q + 1) * 2 * P1;
+  dfl::acc ac, as;
+  for (int j = 0; j <= q; ++j) {
+    const df a = ld(alf, (int64_t)j * 3 * nt + o);
+    ac.add_prod(ld(Fi, (int64_t)j * 2 * P1 + m), a);
+    as.add_prod(ld(Fi, (int64_t)j * 2 * P1 + P1 + m), a);
+  }
+  float2* c = coef + (int64_t)item * coef_stride;
+  if (m == 0) {
+    st(c, n * n + n, ac.value());
+  } else {
+    const df s2{1.41421353816986084f, 2.4203234971764687e-08f};
+    st(c, n * n + n + m, dfl::mul(s2, ac.value()));
+    st(c, n * n + n - m, dfl::mul(s2, as.value()));
+  }
+}
+
+int ensure_d(shbim_ctx* ctx, double** buf, size_t* cap, size_t need, const char* what) {
+  if (need <= *cap) return SHBIM_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, need * sizeof(double)) != cudaSuccess)
+    return fail(ctx, SHBIM_ERR_NOMEM, std::string("cudaMalloc ") + what);
+  *cap = need;
+  return SHBIM_OK;
+}
+
+}  // namespace
+
+// Double-float build of every drop's singular rows (same buffers and chunking as the FP64 build;
+// a float2 occupies the bytes of one double).
+int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) {
+  const int ncomp = kNumLap + kNumSto;
+  for (auto& d : ctx->drops) {
+    const GridTables& up = d.tab->up;
+    const int64_t Ns = d.ns;
+    const int nc = d.nc;
+    const int N = 2 * d.q + 2;
+    if (N % 4) return fail(ctx, SHBIM_ERR_ARG, "double-float row build needs 4 | 2q+2");
+    int CT = (int)std::max<int64_t>(1, std::min<int64_t>(d.nt, (256ll << 20) / (ncomp * Ns * 8)));
+    int rc;
+    if ((rc = ensure_d(ctx, &ctx->rot_coef, &ctx->rot_elems, (size_t)CT * 3 * nc, "rotation buffer")) ||
+        (rc = ensure_d(ctx, &ctx->wbuf, &ctx->wbuf_elems, (size_t)CT * ncomp * Ns, "weight buffer")) ||
+        (rc = ensure_d(ctx, &ctx->vbuf, &ctx->vbuf_elems, (size_t)CT * ncomp * nc, "row buffer")))
+      return rc;
+    const size_t need = (size_t)CT * ncomp * (d.q + 1) * 2 * (d.p + 1);
+    if (need > ctx->sht_scratch_elems) {
+      SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+      cudaFree(ctx->sht_scratch);
+      ctx->sht_scratch = nullptr;
+      ctx->sht_scratch_elems = 0;
+      if (cudaMalloc(&ctx->sht_scratch, need * sizeof(double)) != cudaSuccess)
+        return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc transform scratch");
+      ctx->sht_scratch_elems = need;
+      ctx->geom_version++;
+    }
+    float2* rot = reinterpret_cast<float2*>(ctx->rot_coef);
+    float2* wb = reinterpret_cast<float2*>(ctx->wbuf);
+    float2* vb = reinterpret_cast<float2*>(ctx->vbuf);
+    float2* F = reinterpret_cast<float2*>(ctx->sht_scratch);
+    const double* xc = xcoef + 3 * d.coef_off;
+    const int rot_smem = 2 * nc * (int)sizeof(float2);
+    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_fwd_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
+    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_adj_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
+    const size_t w_smem = (size_t)(18 * (d.p + 1) + 11 * N) * sizeof(float2);
+    const int budget = 46 * 1024 / (int)sizeof(float2) - 2 * N;
+    const int rows = std::max(1, std::min(8, budget / (2 * N)));
+    const size_t f_smem = (size_t)(2 * N + rows * 2 * N) * sizeof(float2);
+    const int nt = (d.p + 1) * (d.p + 2) / 2;
+    for (int t0 = 0; t0 < d.nt; t0 += CT) {
+      const int ct = std::min(CT, d.nt - t0);
+      k_rotate_fwd_df<<<dim3(ct, 3), 128, rot_smem, s>>>(xc, nc, d.p, t0, d.tab->cs_theta_df, d.tab->cs_phi_df,
+                                                         d.tab->dq_df, d.tab->dq_off_dev, rot);
+      SHBIM_CHECK_LAUNCH(ctx, "k_rotate_fwd_df");
+      {
+        TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
+        k_self_weights_df<<<dim3(ct, d.q + 1), 128, w_smem, s>>>(rot, d.p, d.q, d.tab->up_alf_df, d.tab->up_trig_df,
+                                                                 up.mu, ctx->geo.tgt, ctx->ntarget, d.tgt_off + t0, wb);
+        SHBIM_CHECK_LAUNCH(ctx, "k_self_weights_df");
+      }
+      {
+        TimeScope ts(ctx, SHBIM_K_SELF_ANALYSIS, s);
+        const int64_t nrows = (int64_t)ct * ncomp * (d.q + 1);
+        k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, s>>>(wb, Ns, d.p, d.q,
+                                                                                  d.tab->up_trig_df, nrows, rows, F);
+        SHBIM_CHECK_LAUNCH(ctx, "k_analysis_f4_df");
+        k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
+        SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
+      }
+      k_rotate_adj_df<<<dim3(ct, ncomp), 128, rot_smem, s>>>(vb, nc, d.p, t0, ncomp, d.tab->cs_theta_df,
+                                                             d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
+                                                             d.rows_lap, d.rows_sto);
+      SHBIM_CHECK_LAUNCH(ctx, "k_rotate_adj_df");
+    }
+  }
+  return SHBIM_OK;
+}
+
+}  // namespace shbim

@@ -82,7 +82,23 @@ int upload(shbim_ctx* ctx, double** dst, const std::vector<double>& src) {
   return SHBIM_OK;
 }
 
-int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g) {
+// (hi, lo) = (fl32(v), fl32(v - hi)): the double-float copy of an FP64 value
+float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+int upload_df(shbim_ctx* ctx, float2** dst, const std::vector<float2>& src) {
+  cudaError_t e = cudaMalloc(dst, src.size() * sizeof(float2));
+  if (e != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc for tables failed");
+  e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy tables");
+  return SHBIM_OK;
+}
+
+// alf_df / trig_df (optional): double-float copies of the kinds 0..2 and of the trig table
+int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g, float2** alf_df = nullptr,
+               float2** trig_df = nullptr) {
   g.p = p;
   g.q = q;
   std::vector<double> t, wg;
@@ -132,6 +148,19 @@ int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g) {
     trig[N + k] = std::sin(2.0 * kPi * k / N);
   }
   int rc;
+  if (alf_df) {
+    std::vector<float2> a((size_t)(q + 1) * 3 * nt);
+    for (int j = 0; j <= q; ++j)
+      for (int k = 0; k < 3; ++k)
+        for (int o = 0; o < nt; ++o)
+          a[((size_t)j * 3 + k) * nt + o] = split_df(alf[((size_t)j * kNumTab + k) * nt + o]);
+    if ((rc = upload_df(ctx, alf_df, a))) return rc;
+  }
+  if (trig_df) {
+    std::vector<float2> tr(2 * N);
+    for (int k = 0; k < 2 * N; ++k) tr[k] = split_df(trig[k]);
+    if ((rc = upload_df(ctx, trig_df, tr))) return rc;
+  }
   if ((rc = upload(ctx, &g.alf, alf))) return rc;
   if ((rc = upload(ctx, &g.omega, om))) return rc;
   if ((rc = upload(ctx, &g.mu, mu))) return rc;
@@ -205,6 +234,30 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
   }
   int rc = upload(ctx, &T.dq, D);
   if (rc) return rc;
+  {
+    std::vector<float2> Ddf(D.size());
+    for (size_t i = 0; i < D.size(); ++i) Ddf[i] = split_df(D[i]);
+    if ((rc = upload_df(ctx, &T.dq_df, Ddf))) return rc;
+    // cos / sin (m alpha) at the base-grid latitudes and longitudes (the targets' rotation angles)
+    std::vector<double> tb, wb;
+    gauss_legendre(p + 1, tb, wb);
+    std::vector<float2> cth((size_t)(p + 1) * 2 * (p + 1)), cph((size_t)(2 * p + 2) * 2 * (p + 1));
+    for (int j = 0; j <= p; ++j) {
+      const double th = std::acos(tb[j]);
+      for (int m = 0; m <= p; ++m) {
+        cth[((size_t)j * 2) * (p + 1) + m] = split_df(std::cos(m * th));
+        cth[((size_t)j * 2 + 1) * (p + 1) + m] = split_df(std::sin(m * th));
+      }
+    }
+    for (int k = 0; k < 2 * p + 2; ++k) {
+      const double ph = kPi * k / (p + 1);
+      for (int m = 0; m <= p; ++m) {
+        cph[((size_t)k * 2) * (p + 1) + m] = split_df(std::cos(m * ph));
+        cph[((size_t)k * 2 + 1) * (p + 1) + m] = split_df(std::sin(m * ph));
+      }
+    }
+    if ((rc = upload_df(ctx, &T.cs_theta_df, cth)) || (rc = upload_df(ctx, &T.cs_phi_df, cph))) return rc;
+  }
   cudaError_t e = cudaMalloc(&T.dq_off_dev, T.dq_off.size() * sizeof(int));
   if (e != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc rotation offsets");
   e = cudaMemcpy(T.dq_off_dev, T.dq_off.data(), T.dq_off.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -218,7 +271,8 @@ int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out) {
   DegreeTables* T = new DegreeTables();
   T->p = p;
   int rc;
-  if ((rc = build_grid(ctx, p, p, T->base)) || (rc = build_grid(ctx, p, 2 * p + 1, T->up)) ||
+  if ((rc = build_grid(ctx, p, p, T->base)) ||
+      (rc = build_grid(ctx, p, 2 * p + 1, T->up, &T->up_alf_df, &T->up_trig_df)) ||
       (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine)) || (rc = build_rotation(ctx, p, *T))) {
     free_degree_tables(T);
     return rc;
@@ -242,6 +296,11 @@ void free_degree_tables(DegreeTables* t) {
   free_grid(t->fine);
   cudaFree(t->dq);
   cudaFree(t->dq_off_dev);
+  cudaFree(t->up_alf_df);
+  cudaFree(t->up_trig_df);
+  cudaFree(t->dq_df);
+  cudaFree(t->cs_theta_df);
+  cudaFree(t->cs_phi_df);
   delete t;
 }
 

@@ -164,7 +164,7 @@ def two_drops_p12():
     return cfg, oracle_system(cfg.drops)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32), (2, TOL64)])
 def test_laplace_two_drops_matches_oracle(S, two_drops_p12, precision, tol):
     cfg, sysm = two_drops_p12
     ctx = make(S, cfg.drops, precision, cfg.R)
@@ -182,7 +182,7 @@ def test_laplace_two_drops_matches_oracle(S, two_drops_p12, precision, tol):
     ctx.close()
 
 
-@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32)])
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32), (2, TOL64)])
 def test_stokes_two_drops_matches_oracle(S, two_drops_p12, precision, tol):
     cfg, sysm = two_drops_p12
     ctx = make(S, cfg.drops, precision, cfg.R)
@@ -215,7 +215,7 @@ def test_three_drops_uneven_degrees_match_oracle(S):
     sig = [inputs.random_density(d.p, rng)[0] for d in drops]
     u = [inputs.random_density(d.p, rng, 3) for d in drops]
     nc_tot = sum(sh.ncoef(d.p) for d in drops)
-    for precision, tol in ((S.FP64, TOL64), (S.FP32_COMP, TOL32)):
+    for precision, tol in ((S.FP64, TOL64), (S.FP32_COMP, TOL32), (S.DF64, TOL64)):
         ctx = make(S, drops, precision)
         co = torch.empty(nc_tot, device=DEV, dtype=torch.float64)
         ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), co, S.OUT_COEF)
@@ -226,6 +226,42 @@ def test_three_drops_uneven_degrees_match_oracle(S):
         ref = np.concatenate([a.ravel() for a in sysm.stokes_coef(u, u)])
         assert rel_err(co3.cpu().numpy(), ref) < tol
         ctx.close()
+
+
+def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
+    """The singular self rows built in double-float arithmetic (the default) against the rows of
+    the FP64 build and the oracle, on one perturbed drop (self term only) and on two drops."""
+    rng = np.random.default_rng(31)
+    one = [inputs.Drop(11, inputs.perturbed_coef(11, rng, 1.0, (0.1, -0.2, 0.3)), np.zeros(sh.ncoef(11)),
+                       2.5, np.array([0.1, -0.2, 0.3]), 1.0)]
+    two = _two_drop_cfg(8, seed=3, gap=0.3).drops
+    for drops in (one, two):
+        sysm = oracle_system(drops)
+        nc = sum(sh.ncoef(d.p) for d in drops)
+        sig = [inputs.random_density(d.p, rng)[0] for d in drops]
+        u = [inputs.random_density(d.p, rng, 3) for d in drops]
+        res = {}
+        for rows in (S.FP64, S.DF64):
+            ctx = S.Context(precision=S.FP64, R=2.0, gmres_tol=1e-12)
+            ctx.set_rows_precision(rows)
+            ctx.set_drops([d.p for d in drops], T(np.concatenate([d.xcoef.ravel() for d in drops])),
+                          [d.lam for d in drops])
+            out = []
+            for which in (S.LAPLACE_DL, S.LAPLACE_SL):
+                o = torch.empty(nc, device=DEV, dtype=torch.float64)
+                ctx.eval_electric(which, T(np.concatenate(sig)), o, S.OUT_COEF)
+                out.append(o.cpu().numpy())
+            o3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
+            U = T(np.concatenate([a.ravel() for a in u]))
+            ctx.eval_stokes(U, U, o3, S.OUT_COEF)
+            out.append(o3.cpu().numpy())
+            res[rows] = out
+            ctx.close()
+        refs = [np.concatenate(sysm.laplace_coef("ladl", sig)), np.concatenate(sysm.laplace_coef("lsl", sig)),
+                np.concatenate([a.ravel() for a in sysm.stokes_coef(u, u)])]
+        for a, b, ref in zip(res[S.DF64], res[S.FP64], refs):
+            assert rel_err(a, b) < 1e-12
+            assert rel_err(a, ref) < TOL64
 
 
 def test_every_pair_launch_shape_matches_oracle(S):
@@ -291,7 +327,7 @@ def test_full_size_two_drops_sampled_targets(S):
     for i, dg in enumerate(sysm.drops):
         gap_t = int(np.argmin(np.abs(dg.x0[2] - 0.0)))
         sel = sorted(set(picks + [gap_t]))
-        for precision, tol in ((0, TOL64), (1, TOL32)):
+        for precision, tol in ((0, TOL64), (1, TOL32), (2, TOL64)):
             ctx = make(S, cfg.drops, precision, cfg.R, near=False)
             out = torch.empty(2 * nt, device=DEV, dtype=torch.float64)
             ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), out, S.OUT_GRID)
@@ -375,10 +411,12 @@ def test_errors_are_reported_not_raised_by_the_library(S):
     ctx.close()
 
 
+@pytest.mark.parametrize("outer", ["df64", "fp64"])
 @pytest.mark.parametrize("system", ["electric", "stokes"])
-def test_refined_mixed_precision_solve_reaches_fp64_residual(S, system):
-    """Iterative refinement: FP32 compensated inner GMRES, FP64 outer residual; the result
-    satisfies the FP64 system to 1e-10 and equals the FP64 GMRES solution."""
+def test_refined_mixed_precision_solve_reaches_fp64_residual(S, system, outer):
+    """Iterative refinement: FP32 compensated inner GMRES, FP64-class outer residual (double-
+    float or native FP64); the result satisfies the system to 1e-10 and equals the oracle's
+    GMRES solution."""
     cfg = _two_drop_cfg(8, seed=5, gap=0.2)
     sysm = oracle_system(cfg.drops)
     rng = np.random.default_rng(8)
@@ -391,11 +429,12 @@ def test_refined_mixed_precision_solve_reaches_fp64_residual(S, system):
         ref, _ = gmres.gmres(sysm.stokes_matvec, b, tol=1e-13)
         sid = S.SYS_STOKES
     ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-10)
+    ctx.set_outer_precision(S.DF64 if outer == "df64" else S.FP64)
     ctx.set_drops([d.p for d in cfg.drops], T(np.concatenate([d.xcoef.ravel() for d in cfg.drops])),
                   [d.lam for d in cfg.drops])
     x = torch.empty(b.size, device=DEV, dtype=torch.float64)
-    inner, outer, res = ctx.gmres_solve_refined(sid, T(b), x, inner_tol=1e-5, max_outer=8)
-    assert res <= 1e-10 and 1 <= outer <= 4, (inner, outer, res)
+    inner, n_outer, res = ctx.gmres_solve_refined(sid, T(b), x, inner_tol=1e-5, max_outer=8)
+    assert res <= 1e-10 and 1 <= n_outer <= 4, (inner, n_outer, res)
     assert rel_err(x.cpu().numpy(), ref) < 1e-9
     ctx.close()
 
@@ -406,23 +445,25 @@ def test_near_pairs_and_corrected_operators_match_oracle(S):
     cfg = inputs.config2(p=8, seed=0, gap=0.1)
     cfg.drops[1].lam = 3.0
     sysm = oracle_system(cfg.drops)
-    ctx = make(S, cfg.drops, S.FP64, cfg.R)
-    assert ctx.near_pairs() == len(sysm.near_pairs()) > 0
     rng = np.random.default_rng(5)
     sig = [inputs.random_density(8, rng, decay=2.0)[0] for _ in cfg.drops]
     f = [inputs.random_density(8, rng, 3, decay=2.0) for _ in cfg.drops]
     nt = 2 * 9 * 18
-    for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
-        out = torch.empty(nt, device=DEV, dtype=torch.float64)
-        ctx.eval_electric(which, T(np.concatenate(sig)), out, S.OUT_GRID)
-        assert rel_err(out.cpu().numpy(), np.concatenate(sysm.laplace_grid(kind, sig))) < TOL64
-    out = torch.empty(3 * nt, device=DEV, dtype=torch.float64)
-    F = T(np.concatenate([a.ravel() for a in f]))
-    ctx.eval_stokes(F, F, out, S.OUT_GRID)
-    ref = np.concatenate([a.ravel() for a in sysm.stokes_grid(f, f)])
-    assert rel_err(out.cpu().numpy(), ref) < TOL64
+    ref_l = {kind: np.concatenate(sysm.laplace_grid(kind, sig)) for kind in ("ladl", "lsl")}
+    ref_s = np.concatenate([a.ravel() for a in sysm.stokes_grid(f, f)])
+    for precision, tol in ((S.FP64, TOL64), (S.DF64, TOL64), (S.FP32_COMP, TOL32)):
+        ctx = make(S, cfg.drops, precision, cfg.R)
+        assert ctx.near_pairs() == len(sysm.near_pairs()) > 0
+        for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
+            out = torch.empty(nt, device=DEV, dtype=torch.float64)
+            ctx.eval_electric(which, T(np.concatenate(sig)), out, S.OUT_GRID)
+            assert rel_err(out.cpu().numpy(), ref_l[kind]) < tol, (precision, kind)
+        out = torch.empty(3 * nt, device=DEV, dtype=torch.float64)
+        F = T(np.concatenate([a.ravel() for a in f]))
+        ctx.eval_stokes(F, F, out, S.OUT_GRID)
+        assert rel_err(out.cpu().numpy(), ref_s) < tol, precision
+        ctx.close()
     # without the correction the operators differ from the corrected oracle
-    ctx.close()
     ctx = make(S, cfg.drops, S.FP64, cfg.R, near=False)
     assert ctx.near_pairs() == 0
     out = torch.empty(nt, device=DEV, dtype=torch.float64)
@@ -439,7 +480,7 @@ def test_graph_replay_matches_direct_launches(S):
     b_s = T(np.concatenate([inputs.random_density(8, rng, 3).ravel() for _ in cfg.drops]))
     out = {}
     for graphs in (False, True):
-        for precision in (S.FP64, S.FP32_COMP):
+        for precision in (S.FP64, S.FP32_COMP, S.DF64):
             ctx = S.Context(precision=precision, R=cfg.R, gmres_tol=1e-10)
             ctx.set_graphs(graphs)
             ctx.set_autotune(False)     # the same FP32 summation order in both contexts
@@ -458,7 +499,7 @@ def test_graph_replay_matches_direct_launches(S):
                 sols.append((ie, is_, xe.cpu().numpy(), xs.cpu().numpy()))
             out[(graphs, precision)] = sols
             ctx.close()
-    for precision in (S.FP64, S.FP32_COMP):
+    for precision in (S.FP64, S.FP32_COMP, S.DF64):
         for a, b in zip(out[(False, precision)], out[(True, precision)]):
             assert a[0] == b[0] and a[1] == b[1]
             assert rel_err(b[2], a[2]) < 1e-10 and rel_err(b[3], a[3]) < 1e-10
