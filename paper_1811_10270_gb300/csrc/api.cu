@@ -163,6 +163,8 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->phys.grid);
   cudaFree(ctx->phys.state);
   cudaFree(ctx->phys.lb);
+  cudaFree(ctx->dens_split);
+  cudaFree(ctx->xdf);
   cudaFree(ctx->gm.xr);
   cudaFree(ctx->gm.rr);
   cudaFree(ctx->gm.dr);
@@ -308,8 +310,8 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
       (rc = dalloc(ctx, &ctx->xup, 3 * (size_t)kNumTab * so, "position derivatives")))
     return rc;
   for (auto& d : ctx->drops) {
-    if ((rc = dalloc(ctx, &d.rows_lap, (size_t)d.nt * kNumLap * d.nc, "laplace rows")) ||
-        (rc = dalloc(ctx, &d.rows_sto, (size_t)d.nt * kNumSto * d.nc, "stokes rows")))
+    if ((rc = dalloc(ctx, &d.rows_lap, 2 * (size_t)d.nt * kNumLap * d.nc, "laplace rows")) ||
+        (rc = dalloc(ctx, &d.rows_sto, 2 * (size_t)d.nt * kNumSto * d.nc, "stokes rows")))
       return rc;
   }
   {

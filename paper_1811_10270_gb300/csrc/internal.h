@@ -58,6 +58,7 @@ struct DegreeTables {
   float2* up_alf_df = nullptr;   // [2p+2 latitudes][3][ntri(p)]: Pbar, dPbar/dtheta, m Pbar/sin
   float2* up_trig_df = nullptr;  // [2][4p+4]: cos, sin of 2 pi k / (4p+4)
   float2* dq_df = nullptr;       // as dq
+  float2* dqT_df = nullptr;      // per degree block transposed (coalesced reads for Dq x)
   float2* cs_theta_df = nullptr; // [p+1 base latitudes][2][p+1]: cos(m theta_j), sin(m theta_j)
   float2* cs_phi_df = nullptr;   // [2p+2 base longitudes][2][p+1]: cos(m phi_k), sin(m phi_k)
 };
@@ -71,8 +72,10 @@ struct Drop {
   double lam = 1.0;
   double centre[3] = {0, 0, 0};
   DegreeTables* tab = nullptr;
-  double* rows_lap = nullptr;   // [nt][kNumLap][nc]
-  double* rows_sto = nullptr;   // [nt][kNumSto][nc]
+  // singular rows as two FP32 planes (hi, then lo = value - hi): the FP32 path reads the hi plane
+  // only, the FP64-class path both (double-float); same bytes as FP64 storage
+  float* rows_lap = nullptr;    // [2][nt][kNumLap][nc]
+  float* rows_sto = nullptr;    // [2][nt][kNumSto][nc]
 };
 
 // Per-drop description read by the kernels.
@@ -81,8 +84,8 @@ struct DropDev {
   int64_t coef_off, tgt_off, src_off;
   double lam;
   double cx, cy, cz;
-  const double* rows_lap;
-  const double* rows_sto;
+  const float* rows_lap;        // [2][nt][kNumLap][nc] (hi plane, lo plane)
+  const float* rows_sto;        // [2][nt][kNumSto][nc]
 };
 
 // Target tile of the all-pairs kernels: targets [t0, t0+nt) of one drop.
@@ -129,6 +132,10 @@ struct shbim_ctx {
     bool tuned = false;
   } pair_cfg[3];
   bool autotune = true;           // off: every layout keeps the default launch shape
+  double* xdf = nullptr;          // position coefficients of one drop as double-float (row build)
+  size_t xdf_cap = 0;
+  float* dens_split = nullptr;    // [2][3 ncoef] hi / lo planes of a density for the self GEMV
+  size_t dens_split_cap = 0;
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
   // workspaces

@@ -264,7 +264,12 @@ __global__ void __launch_bounds__(256) k_near_direct(NearArgs A) {
   const int64_t t = A.pair_t[pr];
   const int j = A.pair_j[pr];
   const DropDev D = A.drops[j];
-  const int64_t fo = A.fine_off[j], fn = A.fine_n[j];
+  // chunk blockIdx.y of gridDim.y of both grids' nodes (partial sums meet in the atomics)
+  const int64_t fn_all = A.fine_n[j];
+  const int64_t f0 = fn_all * blockIdx.y / gridDim.y, f1 = fn_all * (blockIdx.y + 1) / gridDim.y;
+  const int64_t s0 = (int64_t)D.ns * blockIdx.y / gridDim.y, s1 = (int64_t)D.ns * (blockIdx.y + 1) / gridDim.y;
+  const int64_t fo = A.fine_off[j] + f0, fn = f1 - f0;
+  const int64_t so = D.src_off + s0, sn = s1 - s0;
   double x0[3], nv[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -283,22 +288,31 @@ __global__ void __launch_bounds__(256) k_near_direct(NearArgs A) {
       n32[c] = (float)nv[c];
     }
     near_sum32<KIND>(A.fpos32 + fo, A.nfine, A.fstr32 + fo, A.nfine, fn, th, tl, n32, A.has_f, A.has_u, af);
-    near_sum32<KIND>(A.src32 + D.src_off, A.nsource, A.sstr32 + D.src_off, A.nsource, D.ns, th, tl, n32,
+    near_sum32<KIND>(A.src32 + so, A.nsource, A.sstr32 + so, A.nsource, sn, th, tl, n32,
                      A.has_f, A.has_u, au);
   } else if (MODE == 2) {
+    // the target offset and normal as double-float, converted once per block (FP64 pipe)
+    __shared__ float2 tv[6];
+    if (threadIdx.x < 6) {
+      const double cj[3] = {D.cx, D.cy, D.cz};
+      const int c = threadIdx.x % 3;
+      const dfl::df v = dfl::from_double(threadIdx.x < 3 ? x0[c] - cj[c] : nv[c]);
+      tv[threadIdx.x] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
     dfl::df T[3], nd[3];
-    T[0] = dfl::from_double(x0[0] - D.cx);
-    T[1] = dfl::from_double(x0[1] - D.cy);
-    T[2] = dfl::from_double(x0[2] - D.cz);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) nd[c] = dfl::from_double(nv[c]);
+    for (int c = 0; c < 3; ++c) {
+      T[c] = dfl::df{tv[c].x, tv[c].y};
+      nd[c] = dfl::df{tv[3 + c].x, tv[3 + c].y};
+    }
     near_sum_df<KIND>(A.fpos32 + fo, A.fpos32lo + fo, A.nfine, A.fstr32 + fo, A.fstr32lo + fo, A.nfine, fn, T, nd,
                       A.has_f, A.has_u, af);
-    near_sum_df<KIND>(A.src32 + D.src_off, A.src32lo + D.src_off, A.nsource, A.sstr32 + D.src_off,
-                      A.sstr32lo + D.src_off, A.nsource, D.ns, T, nd, A.has_f, A.has_u, au);
+    near_sum_df<KIND>(A.src32 + so, A.src32lo + so, A.nsource, A.sstr32 + so, A.sstr32lo + so, A.nsource, sn, T,
+                      nd, A.has_f, A.has_u, au);
   } else {
     near_sum64<KIND>(A.fpos + fo, A.nfine, A.fstr + fo, A.nfine, fn, x0, nv, A.has_f, A.has_u, af);
-    near_sum64<KIND>(A.src + D.src_off, A.nsource, A.sstr + D.src_off, A.nsource, D.ns, x0, nv, A.has_f,
+    near_sum64<KIND>(A.src + so, A.nsource, A.sstr + so, A.nsource, sn, x0, nv, A.has_f,
                      A.has_u, au);
   }
   const int nc = KIND == 2 ? 3 : 1;
@@ -442,7 +456,12 @@ int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out,
              ctx->geo.src32, ctx->dens_up, ctx->dens_up32, ctx->nsource, N.fgeo32lo, N.fstr32lo,
              ctx->geo.src32lo, ctx->dens_up32lo, has_f ? 1 : 0, has_u ? 1 : 0, out};
   const int mode = ctx->opts.precision == SHBIM_PREC_FP32_COMP ? 1 : (ctx->opts.precision == SHBIM_PREC_DF64 ? 2 : 0);
-  const unsigned g = (unsigned)N.npairs;
+  // enough CTAs for ~8 per SM: each near pair's sums are split into chunks of both grids
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(32, (8ll * nsm + N.npairs - 1) / N.npairs));
+  const dim3 g((unsigned)N.npairs, (unsigned)chunks);
   if (kind == 0) {
     if (mode == 1) k_near_direct<0, 1><<<g, 256, 0, s>>>(A);
     else if (mode == 2) k_near_direct<0, 2><<<g, 256, 0, s>>>(A);

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "dfloat.cuh"
 #include "internal.h"
 #include "fourier.cuh"
 
@@ -198,8 +199,8 @@ __global__ void k_rotate_fwd(const double* __restrict__ xc, int nc, int p, int t
 // row = D_R v for target blockIdx.x and component blockIdx.y
 __global__ void k_rotate_adj(const double* __restrict__ vbuf, int nc, int p, int t_begin, int ncomp,
                              const double* __restrict__ theta_base, const double* __restrict__ dq,
-                             const int* __restrict__ dq_off, double* __restrict__ rows_lap,
-                             double* __restrict__ rows_sto) {
+                             const int* __restrict__ dq_off, float* __restrict__ rows_lap,
+                             float* __restrict__ rows_sto, int nt_drop) {
   extern __shared__ double sm[];
   double* b0 = sm;
   double* b1 = sm + nc;
@@ -223,9 +224,14 @@ __global__ void k_rotate_adj(const double* __restrict__ vbuf, int nc, int p, int
   __syncthreads();
   dz_apply(b0, p, cp, sp, 1.0);
   __syncthreads();
-  double* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
-                            : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) dst[o] = b0[o];
+  float* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
+                           : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
+  const int64_t plane = (int64_t)nt_drop * (c < kNumLap ? kNumLap : kNumSto) * nc;
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+    const float h = (float)b0[o];
+    dst[o] = h;
+    dst[plane + o] = (float)(b0[o] - (double)h);
+  }
 }
 
 // ---------------------------------------------------------------- rotated-grid weights
@@ -377,7 +383,7 @@ int build_singular_rows(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
       }
       k_rotate_adj<<<dim3(ct, ncomp), 128, rot_smem, s>>>(
           ctx->vbuf, nc, d.p, t0, ncomp, d.tab->base.theta, d.tab->dq, d.tab->dq_off_dev,
-          d.rows_lap, d.rows_sto);
+          d.rows_lap, d.rows_sto, d.nt);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_adj");
     }
   }
@@ -392,88 +398,166 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Self GEMVs over the FP32 row planes. FP32 path (DF = false): hi plane and the FP32 copy of the
+// density, FP32 accumulation. FP64-class path (DF = true): both planes and both density planes,
+// double-float accumulation. One warp per target; HBM-bound in both forms (in FP64 arithmetic the
+// GEMV would be bound by the FP64 pipe: 2 flops per 8 bytes is above this GPU's FP64 balance).
+__global__ void k_split_density(const double* __restrict__ x, int64_t n, float* __restrict__ hi,
+                                float* __restrict__ lo) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float h = (float)x[e];
+  hi[e] = h;
+  lo[e] = (float)(x[e] - (double)h);
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <bool DF>
 __global__ void k_self_lap(const DropDev* __restrict__ drops, const int* __restrict__ tgt_drop,
-                           int64_t ntarget, int which, const double* __restrict__ dens,
-                           double* __restrict__ out) {
+                           int64_t ntarget, int which, const float* __restrict__ xh,
+                           const float* __restrict__ xl, double* __restrict__ out) {
   const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= ntarget) return;
   const DropDev D = drops[tgt_drop[t]];
   const int64_t tl = t - D.tgt_off;
-  const double* row = D.rows_lap + (tl * kNumLap + which) * D.nc;
-  const double* x = dens + D.coef_off;
-  double acc = 0.0;
-  for (int e = lane; e < D.nc; e += 32) acc = fma(row[e], x[e], acc);
-  acc = warp_sum(acc);
-  if (lane == 0) out[t] = acc;
+  const int64_t plane = (int64_t)D.nt * kNumLap * D.nc;
+  const float* rh = D.rows_lap + (tl * kNumLap + which) * D.nc;
+  const float* x = xh + D.coef_off;
+  double v;
+  if (!DF) {
+    float acc = 0.f;
+    for (int e = lane; e < D.nc; e += 32) acc = fmaf(rh[e], x[e], acc);
+    v = (double)warp_sum_f(acc);
+  } else {
+    const float* rl = rh + plane;
+    const float* x2 = xl + D.coef_off;
+    dfl::acc acc;
+    for (int e = lane; e < D.nc; e += 32) acc.add_prod(dfl::df{rh[e], rl[e]}, dfl::df{x[e], x2[e]});
+    v = warp_sum(dfl::to_double(acc.value()));
+  }
+  if (lane == 0) out[t] = v;
 }
 
-int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s) {
-  const int64_t threads = ctx->ntarget * 32;
-  k_self_lap<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop,
-                                                               ctx->ntarget, which, dens, out);
-  SHBIM_CHECK_LAUNCH(ctx, "k_self_lap");
-  return SHBIM_OK;
-}
-
+template <bool DF>
 __global__ void k_self_sto(const DropDev* __restrict__ drops, const int* __restrict__ tgt_drop,
-                           int64_t ntarget, const double* __restrict__ f, const double* __restrict__ u,
-                           double* __restrict__ out) {
+                           int64_t ntarget, const float* __restrict__ fh, const float* __restrict__ fl,
+                           const float* __restrict__ uh, const float* __restrict__ ul, double* __restrict__ out) {
   const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (t >= ntarget) return;
   const DropDev D = drops[tgt_drop[t]];
   const int64_t tl = t - D.tgt_off;
   const int nc = D.nc;
-  const double* rows = D.rows_sto + tl * kNumSto * nc;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  if (f) {
-    const double* fx = f + 3 * D.coef_off;
-    const double* fy = fx + nc;
-    const double* fz = fy + nc;
-    for (int e = lane; e < nc; e += 32) {
-      const double X = fx[e], Y = fy[e], Z = fz[e];
-      const double xx = rows[e], xy = rows[nc + e], xz = rows[2 * nc + e];
-      const double yy = rows[3 * nc + e], yz = rows[4 * nc + e], zz = rows[5 * nc + e];
-      a0 += xx * X + xy * Y + xz * Z;
-      a1 += xy * X + yy * Y + yz * Z;
-      a2 += xz * X + yz * Y + zz * Z;
+  const int64_t plane = (int64_t)D.nt * kNumSto * nc;
+  const float* rows = D.rows_sto + tl * kNumSto * nc;
+  double res[3] = {0.0, 0.0, 0.0};
+  for (int part = 0; part < 2; ++part) {
+    const float* vh = part == 0 ? fh : uh;
+    if (!vh || (part == 1 && D.lam == 1.0)) continue;
+    const float* vl = part == 0 ? fl : ul;
+    const float* r = rows + part * 6 * nc;
+    const float* Xh = vh + 3 * D.coef_off;
+    double s3[3];
+    if (!DF) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+      for (int e = lane; e < nc; e += 32) {
+        const float X = Xh[e], Y = Xh[nc + e], Z = Xh[2 * nc + e];
+        const float xx = r[e], xy = r[nc + e], xz = r[2 * nc + e];
+        const float yy = r[3 * nc + e], yz = r[4 * nc + e], zz = r[5 * nc + e];
+        a0 = fmaf(xx, X, fmaf(xy, Y, fmaf(xz, Z, a0)));
+        a1 = fmaf(xy, X, fmaf(yy, Y, fmaf(yz, Z, a1)));
+        a2 = fmaf(xz, X, fmaf(yz, Y, fmaf(zz, Z, a2)));
+      }
+      s3[0] = warp_sum_f(a0);
+      s3[1] = warp_sum_f(a1);
+      s3[2] = warp_sum_f(a2);
+    } else {
+      const float* Xl = vl + 3 * D.coef_off;
+      const float* q = r + plane;
+      dfl::acc a0, a1, a2;
+      for (int e = lane; e < nc; e += 32) {
+        const dfl::df X{Xh[e], Xl[e]}, Y{Xh[nc + e], Xl[nc + e]}, Z{Xh[2 * nc + e], Xl[2 * nc + e]};
+        const dfl::df xx{r[e], q[e]}, xy{r[nc + e], q[nc + e]}, xz{r[2 * nc + e], q[2 * nc + e]};
+        const dfl::df yy{r[3 * nc + e], q[3 * nc + e]}, yz{r[4 * nc + e], q[4 * nc + e]};
+        const dfl::df zz{r[5 * nc + e], q[5 * nc + e]};
+        a0.add_prod(xx, X);
+        a0.add_prod(xy, Y);
+        a0.add_prod(xz, Z);
+        a1.add_prod(xy, X);
+        a1.add_prod(yy, Y);
+        a1.add_prod(yz, Z);
+        a2.add_prod(xz, X);
+        a2.add_prod(yz, Y);
+        a2.add_prod(zz, Z);
+      }
+      s3[0] = warp_sum(dfl::to_double(a0.value()));
+      s3[1] = warp_sum(dfl::to_double(a1.value()));
+      s3[2] = warp_sum(dfl::to_double(a2.value()));
     }
+    const double w = part == 0 ? 1.0 : D.lam - 1.0;
+    for (int c = 0; c < 3; ++c) res[c] += w * s3[c];
   }
-  if (u && D.lam != 1.0) {
-    const double l1 = D.lam - 1.0;
-    const double* ux = u + 3 * D.coef_off;
-    const double* uy = ux + nc;
-    const double* uz = uy + nc;
-    const double* r = rows + 6 * nc;
-    double b0 = 0.0, b1 = 0.0, b2 = 0.0;
-    for (int e = lane; e < nc; e += 32) {
-      const double X = ux[e], Y = uy[e], Z = uz[e];
-      const double xx = r[e], xy = r[nc + e], xz = r[2 * nc + e];
-      const double yy = r[3 * nc + e], yz = r[4 * nc + e], zz = r[5 * nc + e];
-      b0 += xx * X + xy * Y + xz * Z;
-      b1 += xy * X + yy * Y + yz * Z;
-      b2 += xz * X + yz * Y + zz * Z;
-    }
-    a0 += l1 * b0;
-    a1 += l1 * b1;
-    a2 += l1 * b2;
-  }
-  a0 = warp_sum(a0);
-  a1 = warp_sum(a1);
-  a2 = warp_sum(a2);
   if (lane == 0) {
     double* o = out + 3 * D.tgt_off + tl;
-    o[0] = a0;
-    o[D.nt] = a1;
-    o[2 * D.nt] = a2;
+    o[0] = res[0];
+    o[D.nt] = res[1];
+    o[2 * D.nt] = res[2];
   }
 }
 
-int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s) {
+namespace {
+// hi / lo planes of n doubles into slot 0 or 1 (3 ncoef floats each) of the context's split buffer
+int split_density(shbim_ctx* ctx, const double* x, int64_t n, int slot, float** hi, float** lo, cudaStream_t s) {
+  const size_t need = (size_t)12 * ctx->ncoef;   // [hi, lo][slot 0, slot 1][3 ncoef]
+  if (ctx->dens_split_cap < need) {
+    cudaFree(ctx->dens_split);
+    ctx->dens_split = nullptr;
+    ctx->dens_split_cap = 0;
+    if (cudaMalloc(&ctx->dens_split, need * sizeof(float)) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc density split");
+    ctx->dens_split_cap = need;
+    ctx->geom_version++;  // captured operator graphs referenced the old buffer
+  }
+  *hi = ctx->dens_split + (int64_t)slot * 3 * ctx->ncoef;
+  *lo = *hi + 6 * ctx->ncoef;
+  k_split_density<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, *hi, *lo);
+  SHBIM_CHECK_LAUNCH(ctx, "k_split_density");
+  return SHBIM_OK;
+}
+}  // namespace
+
+int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s) {
+  float *xh, *xl;
+  int rc = split_density(ctx, dens, ctx->ncoef, 0, &xh, &xl, s);
+  if (rc) return rc;
   const int64_t threads = ctx->ntarget * 32;
-  k_self_sto<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop,
-                                                               ctx->ntarget, f, u, out);
+  const unsigned g = (unsigned)((threads + 255) / 256);
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP)
+    k_self_lap<false><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, which, xh, xl, out);
+  else
+    k_self_lap<true><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, which, xh, xl, out);
+  SHBIM_CHECK_LAUNCH(ctx, "k_self_lap");
+  return SHBIM_OK;
+}
+
+int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s) {
+  float *fh = nullptr, *fl = nullptr, *uh = nullptr, *ul = nullptr;
+  int rc;
+  const int64_t n3 = 3 * ctx->ncoef;
+  if (f && (rc = split_density(ctx, f, n3, 0, &fh, &fl, s))) return rc;
+  if (u && (rc = split_density(ctx, u, n3, 1, &uh, &ul, s))) return rc;
+  const int64_t threads = ctx->ntarget * 32;
+  const unsigned g = (unsigned)((threads + 255) / 256);
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP)
+    k_self_sto<false><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, fh, fl, uh, ul, out);
+  else
+    k_self_sto<true><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, fh, fl, uh, ul, out);
   SHBIM_CHECK_LAUNCH(ctx, "k_self_sto");
   return SHBIM_OK;
 }

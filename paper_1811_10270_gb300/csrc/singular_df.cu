@@ -6,7 +6,7 @@
 //      kernel weights mu J K / (4 pi) at every node (Laplace DL and SL, 6 Stokeslet and 6
 //      stresslet components);
 //   3. analyse the weights (Fourier stage folded four ways, then Legendre stage);
-//   4. rotate the coefficient rows back (row = D_R v) and store them in FP64.
+//   4. rotate the coefficient rows back (row = D_R v) and store them as (hi, lo) FP32 planes.
 // Every sum and every pointwise operation is double-float (hi + lo FP32 pairs; Dekker products,
 // Knuth sums, Newton square roots), ~2^-44 relative per operation, so the rows agree with the
 // FP64 build to rounding level while the FP64 pipe (1/64 of the FP32 rate here) stays idle.
@@ -53,33 +53,35 @@ __device__ void dz_df(float2* v, int p, const float2* __restrict__ cs, float sgn
   }
 }
 
-// out <- Dq in (transpose: Dq^T in), per degree block
+// out <- Dq in (transpose: Dq^T in), per degree block. Both products read a column of a stored
+// block (Dq^T for the plain product, Dq for the transposed one), so the threads of a warp, which
+// hold consecutive orders m, read consecutive addresses.
 __device__ void dq_df(const float2* __restrict__ in, float2* __restrict__ out, int p, const float2* __restrict__ dq,
-                      const int* __restrict__ dq_off, bool transpose) {
+                      const float2* __restrict__ dqT, const int* __restrict__ dq_off, bool transpose) {
   const int nc = (p + 1) * (p + 1);
   for (int o = threadIdx.x; o < nc; o += blockDim.x) {
     const int n = isqrt_i(o);
     const int m = o - n * n - n;
     const int w = 2 * n + 1;
-    const float2* B = dq + dq_off[n];
+    const float2* col = (transpose ? dq : dqT) + dq_off[n] + (m + n);
     const float2* x = in + n * n;
     dfl::acc acc;
-    if (!transpose) {
-      const float2* row = B + (m + n) * w;
-      for (int c = 0; c < w; ++c) acc.add_prod(ld(row, c), ld(x, c));
-    } else {
-      const float2* col = B + (m + n);
-      for (int c = 0; c < w; ++c) acc.add_prod(ld(col, (int64_t)c * w), ld(x, c));
-    }
+    for (int c = 0; c < w; ++c) acc.add_prod(ld(col, (int64_t)c * w), ld(x, c));
     st(out, o, acc.value());
   }
 }
 
-// b = D_R^T a for the position coefficients of target blockIdx.x, component blockIdx.y
-__global__ void k_rotate_fwd_df(const double* __restrict__ xc, int nc, int p, int t_begin,
+__global__ void k_to_df(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) st(out, e, dfl::from_double(x[e]));
+}
+
+// b = D_R^T a for the position coefficients (double-float copy) of target blockIdx.x, component
+// blockIdx.y
+__global__ void k_rotate_fwd_df(const float2* __restrict__ xc, int nc, int p, int t_begin,
                                 const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
-                                const float2* __restrict__ dq, const int* __restrict__ dq_off,
-                                float2* __restrict__ out) {
+                                const float2* __restrict__ dq, const float2* __restrict__ dqT,
+                                const int* __restrict__ dq_off, float2* __restrict__ out) {
   extern __shared__ float2 smf[];
   float2* b0 = smf;
   float2* b1 = smf + nc;
@@ -88,22 +90,23 @@ __global__ void k_rotate_fwd_df(const double* __restrict__ xc, int nc, int p, in
   const int nlon = 2 * p + 2;
   const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
   const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) st(b0, o, dfl::from_double(xc[(int64_t)f * nc + o]));
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) b0[o] = xc[(int64_t)f * nc + o];
   __syncthreads();
   dz_df(b0, p, cp, -1.f);
   __syncthreads();
-  dq_df(b0, b1, p, dq, dq_off, false);
+  dq_df(b0, b1, p, dq, dqT, dq_off, false);
   __syncthreads();
   dz_df(b1, p, ct, -1.f);
   __syncthreads();
-  dq_df(b1, out + ((int64_t)blockIdx.x * 3 + f) * nc, p, dq, dq_off, true);
+  dq_df(b1, out + ((int64_t)blockIdx.x * 3 + f) * nc, p, dq, dqT, dq_off, true);
 }
 
 // row = D_R v for target blockIdx.x and component blockIdx.y; stored in FP64
 __global__ void k_rotate_adj_df(const float2* __restrict__ vbuf, int nc, int p, int t_begin, int ncomp,
                                 const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
-                                const float2* __restrict__ dq, const int* __restrict__ dq_off,
-                                double* __restrict__ rows_lap, double* __restrict__ rows_sto) {
+                                const float2* __restrict__ dq, const float2* __restrict__ dqT,
+                                const int* __restrict__ dq_off, float* __restrict__ rows_lap,
+                                float* __restrict__ rows_sto, int nt_drop) {
   extern __shared__ float2 smf[];
   float2* b0 = smf;
   float2* b1 = smf + nc;
@@ -113,17 +116,22 @@ __global__ void k_rotate_adj_df(const float2* __restrict__ vbuf, int nc, int p, 
   const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
   const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
   const float2* v = vbuf + ((int64_t)blockIdx.x * ncomp + c) * nc;
-  dq_df(v, b1, p, dq, dq_off, false);
+  dq_df(v, b1, p, dq, dqT, dq_off, false);
   __syncthreads();
   dz_df(b1, p, ct, 1.f);
   __syncthreads();
-  dq_df(b1, b0, p, dq, dq_off, true);
+  dq_df(b1, b0, p, dq, dqT, dq_off, true);
   __syncthreads();
   dz_df(b0, p, cp, 1.f);
   __syncthreads();
-  double* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
-                            : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) dst[o] = dfl::to_double(ld(b0, o));
+  float* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
+                           : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
+  const int64_t plane = (int64_t)nt_drop * (c < kNumLap ? kNumLap : kNumSto) * nc;
+  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
+    const df v = ld(b0, o);     // already normalised: hi = fl32(value), |lo| <= ulp(hi) / 2
+    dst[o] = v.hi;
+    dst[plane + o] = v.lo;
+  }
 }
 
 // Four-longitude Fourier synthesis (the parity folding of synth4) in double-float.
@@ -219,12 +227,18 @@ __global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, 
       synth4_df(As, Ac, df{0.f, 0.f}, -1.f, p, k, N, tc, ts, V + fk * N);
   }
   __syncthreads();
-  const int64_t tg = tgt0 + t;
-  const df x0 = dfl::from_double(tgt[tg]), y0 = dfl::from_double(tgt[ntarget + tg]),
-           z0 = dfl::from_double(tgt[2 * ntarget + tg]);
-  const df n0x = dfl::from_double(tgt[3 * ntarget + tg]), n0y = dfl::from_double(tgt[4 * ntarget + tg]),
-           n0z = dfl::from_double(tgt[5 * ntarget + tg]);
-  const df w0 = dfl::from_double(mu[j] * 0.07957747154594766788);
+  // the target's position and normal and mu_j / (4 pi) as double-float, converted once per block
+  // (FP64 conversions run on the FP64 pipe)
+  __shared__ float2 tv[7];
+  if (threadIdx.x < 7) {
+    const int64_t tg = tgt0 + t;
+    const double v = threadIdx.x < 6 ? tgt[threadIdx.x * ntarget + tg] : mu[j] * 0.07957747154594766788;
+    st(tv, threadIdx.x, dfl::from_double(v));
+  }
+  __syncthreads();
+  const df x0 = ld(tv, 0), y0 = ld(tv, 1), z0 = ld(tv, 2);
+  const df n0x = ld(tv, 3), n0y = ld(tv, 4), n0z = ld(tv, 5);
+  const df w0 = ld(tv, 6);
   const int64_t Ns = (int64_t)(q + 1) * N;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const df xt0 = ld(V, 1 * N + k), xt1 = ld(V, 4 * N + k), xt2 = ld(V, 7 * N + k);
@@ -418,7 +432,10 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     float2* wb = reinterpret_cast<float2*>(ctx->wbuf);
     float2* vb = reinterpret_cast<float2*>(ctx->vbuf);
     float2* F = reinterpret_cast<float2*>(ctx->sht_scratch);
-    const double* xc = xcoef + 3 * d.coef_off;
+    if ((rc = ensure_d(ctx, &ctx->xdf, &ctx->xdf_cap, (size_t)3 * nc, "position copy"))) return rc;
+    float2* xc = reinterpret_cast<float2*>(ctx->xdf);
+    k_to_df<<<(unsigned)((3 * nc + 255) / 256), 256, 0, s>>>(xcoef + 3 * d.coef_off, 3 * nc, xc);
+    SHBIM_CHECK_LAUNCH(ctx, "k_to_df");
     const int rot_smem = 2 * nc * (int)sizeof(float2);
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_fwd_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_adj_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
@@ -430,7 +447,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     for (int t0 = 0; t0 < d.nt; t0 += CT) {
       const int ct = std::min(CT, d.nt - t0);
       k_rotate_fwd_df<<<dim3(ct, 3), 128, rot_smem, s>>>(xc, nc, d.p, t0, d.tab->cs_theta_df, d.tab->cs_phi_df,
-                                                         d.tab->dq_df, d.tab->dq_off_dev, rot);
+                                                         d.tab->dq_df, d.tab->dqT_df, d.tab->dq_off_dev, rot);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_fwd_df");
       {
         TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
@@ -448,8 +465,9 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
       }
       k_rotate_adj_df<<<dim3(ct, ncomp), 128, rot_smem, s>>>(vb, nc, d.p, t0, ncomp, d.tab->cs_theta_df,
-                                                             d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
-                                                             d.rows_lap, d.rows_sto);
+                                                             d.tab->cs_phi_df, d.tab->dq_df, d.tab->dqT_df,
+                                                             d.tab->dq_off_dev,
+                                                             d.rows_lap, d.rows_sto, d.nt);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_adj_df");
     }
   }

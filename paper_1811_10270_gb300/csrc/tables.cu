@@ -235,9 +235,14 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
   int rc = upload(ctx, &T.dq, D);
   if (rc) return rc;
   {
-    std::vector<float2> Ddf(D.size());
+    std::vector<float2> Ddf(D.size()), DTdf(D.size());
     for (size_t i = 0; i < D.size(); ++i) Ddf[i] = split_df(D[i]);
-    if ((rc = upload_df(ctx, &T.dq_df, Ddf))) return rc;
+    for (int n = 0; n <= p; ++n) {
+      const int w = 2 * n + 1, o = T.dq_off[n];
+      for (int a = 0; a < w; ++a)
+        for (int b = 0; b < w; ++b) DTdf[o + b * w + a] = Ddf[o + a * w + b];
+    }
+    if ((rc = upload_df(ctx, &T.dq_df, Ddf)) || (rc = upload_df(ctx, &T.dqT_df, DTdf))) return rc;
     // cos / sin (m alpha) at the base-grid latitudes and longitudes (the targets' rotation angles)
     std::vector<double> tb, wb;
     gauss_legendre(p + 1, tb, wb);
@@ -299,6 +304,7 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->up_alf_df);
   cudaFree(t->up_trig_df);
   cudaFree(t->dq_df);
+  cudaFree(t->dqT_df);
   cudaFree(t->cs_theta_df);
   cudaFree(t->cs_phi_df);
   delete t;
