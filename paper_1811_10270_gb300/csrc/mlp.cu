@@ -8,8 +8,8 @@
 //
 // All products go through one tensor-core GEMM: C(m, n) = sum_k A(m, k) B(k, n) with A and B
 // read through arbitrary strides (so W, W^T, dZ^T need no transposed copies), staged to shared
-// memory as bfloat16 and multiplied by mma.sync m16n8k16 (bf16 x bf16 -> f32). A 64 x 64 CTA tile
-// is computed by four warps, each 32 x 32 = 2 x 4 MMA tiles, over K steps of 32.
+// memory as bfloat16 and multiplied by the fifth-generation tensor cores (tcgen05.mma, bf16 x bf16
+// -> f32 accumulated in tensor memory).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -38,90 +38,136 @@ struct shbim_mlp {
 namespace shbim {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+// ---------------------------------------------------------------- tcgen05 GEMM
+// C(m, n) = act(sum_k A(m, k) B(k, n) + bias(n)) for one 128 x 64 tile of C per CTA (4 warps).
+// Per K block of 64: the CTA stages A (128 x 64) and B (64 x 64, as N x K) into shared memory as
+// bfloat16 in the no-swizzle K-major canonical layout (8-row x 16-byte core matrices; leading-
+// dimension offset = 128 B between core matrices along K, stride offset = 1024 B between 8-row
+// groups), one thread issues four tcgen05.mma kind::f16 (M = 128, N = 64, K = 16) accumulating in
+// tensor memory and commits them to an mbarrier; every wait is bounded (a timed-out tile is
+// written as NaN so the failure is loud). The epilogue reads the accumulator with tcgen05.ld.
+constexpr int TM = 128, TN = 64, TK = 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// index of element (row r, k) in a [rows][TK] K-major canonical tile
+__device__ __forceinline__ int canon(int r, int k) { return ((r >> 3) * (TK >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((128u >> 4) & 0x3FFF) << 16;          // leading-dimension byte offset (K)
+  d |= (uint64_t)(((TK / 8 * 128) >> 4) & 0x3FFF) << 32;  // stride byte offset (8-row groups)
+  d |= (uint64_t)1 << 46;                                // descriptor version; no swizzle
+  return d;
+}
 
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(128)
-k_gemm_bf16(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
-            int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t scm, int64_t scn,
-            const float* __restrict__ bias, int act) {
-  __shared__ __nv_bfloat16 As[BM][BK + PAD];
-  __shared__ __nv_bfloat16 Bs[BN][BK + PAD];
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += 128) {
-      const int mm = e / BK, kk = e - mm * BK;
+k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sak, const TB* __restrict__ B,
+          int64_t sbk, int64_t sbn, float* __restrict__ C, int64_t scm, int64_t scn,
+          const float* __restrict__ bias, int act) {
+  __shared__ __align__(1024) __nv_bfloat16 sA[TM * TK];
+  __shared__ __align__(1024) __nv_bfloat16 sB[TN * TK];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                 "r"(TN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const uint32_t tmem = tmem_base;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  bool ok = true;
+  int phase = 0;
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    for (int e = tid; e < TM * TK; e += 128) {
+      const int mm = e / TK, kk = e - mm * TK;
       const int gm = m0 + mm, gk = k0 + kk;
       const float v = (gm < M && gk < K) ? (float)A[(int64_t)gm * sam + (int64_t)gk * sak] : 0.f;
-      As[mm][kk] = __float2bfloat16_rn(v);
+      sA[canon(mm, kk)] = __float2bfloat16_rn(v);
     }
-    for (int e = threadIdx.x; e < BN * BK; e += 128) {
-      const int nn = e / BK, kk = e - nn * BK;
+    for (int e = tid; e < TN * TK; e += 128) {
+      const int nn = e / TK, kk = e - nn * TK;
       const int gn = n0 + nn, gk = k0 + kk;
       const float v = (gn < N && gk < K) ? (float)B[(int64_t)gk * sbk + (int64_t)gn * sbn] : 0.f;
-      Bs[nn][kk] = __float2bfloat16_rn(v);
+      sB[canon(nn, kk)] = __float2bfloat16_rn(v);
     }
+    asm volatile("fence.proxy.async.shared::cta;\n");
     __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
 #pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gid;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 8 + tig * 2]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 8 + tig * 2]);
+      for (int ks = 0; ks < TK / 16; ++ks) {
+        const uint64_t da = smem_desc(smem_u32(sA) + ks * 256);
+        const uint64_t db = smem_desc(smem_u32(sB) + ks * 256);
+        const uint32_t acc = (k0 > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gid;
-        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + tig * 2]);
-        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 8 + tig * 2]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]), "r"(bfr[j][1]));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&mbar)));
     }
-    __syncthreads();
+    // the staged tiles may be overwritten only after the MMAs that read them have completed
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 24) && !done; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(smem_u32(&mbar)), "r"(phase));
+    }
+    phase ^= 1;
+    // leave the K loop together: a barrier count mismatch would hang the CTA
+    if (!__syncthreads_and(done)) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
   }
+  const int row = m0 + 32 * warp + (tid & 31);
+  for (int c0 = 0; c0 < TN; c0 += 16) {
+    uint32_t v[16];
+    if (ok) {
+      const uint32_t addr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(addr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+    }
+    if (row < M) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int gm = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
-        const int gn = n0 + wn + j * 8 + tig * 2 + (r & 1);
-        if (gm < M && gn < N) {
-          float v = acc[i][j][r] + (bias ? bias[gn] : 0.f);
-          if (act) v = tanhf(v);
-          C[(int64_t)gm * scm + (int64_t)gn * scn] = v;
+      for (int j = 0; j < 16; ++j) {
+        const int gn = n0 + c0 + j;
+        if (gn < N) {
+          float x = ok ? __uint_as_float(v[j]) + (bias ? bias[gn] : 0.f) : __int_as_float(0x7fc00000);
+          if (act) x = tanhf(x);
+          C[(int64_t)row * scm + (int64_t)gn * scn] = x;
         }
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TN));
 }
 
 template <typename TA, typename TB>
 int gemm(shbim_mlp*, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B, int64_t sbk,
          int64_t sbn, float* C, int64_t scm, int64_t scn, const float* bias, int act, cudaStream_t s) {
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-  k_gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, scn, bias, act);
+  dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+  k_gemm_tc<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, scm, scn, bias, act);
   return cudaGetLastError() == cudaSuccess ? SHBIM_OK : SHBIM_ERR_CUDA;
 }
 
