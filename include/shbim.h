@@ -346,6 +346,11 @@ int shbim_set_autotune(shbim_ctx* ctx, int on);
  * SHBIM_PREC_FP64 (native). SHBIM_ERR_ARG otherwise. */
 int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
 
+/* Fourier stage of the double-float row build on the tensor cores (on by default): the GEMM of
+ * the rows' weights with the DFT table split into bfloat16 digits whose products accumulate exactly
+ * (error ~2^-42 of the sum of magnitudes per output). Off: the double-float FP32-pipe kernel. */
+int shbim_set_tensor_cores(shbim_ctx* ctx, int on);
+
 /* Pipe throughput probes (a measurement utility for roofline denominators; the paper has no
  * counterpart). Launches 4 CTAs of 256 threads per SM on the current device, each thread running
  * 8 independent dependency chains of one instruction for `iters` outer iterations, once to warm

@@ -42,7 +42,7 @@ EXPORTS = [
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
     "shbim_set_graphs", "shbim_laplace_beltrami", "shbim_set_diffusion",
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
-    "shbim_set_outer_precision", "shbim_set_rows_precision",
+    "shbim_set_outer_precision", "shbim_set_rows_precision", "shbim_set_tensor_cores",
 ]
 PROBE_FFMA = 0
 PROBE_DFMA = 1
@@ -125,6 +125,7 @@ def lib():
         "shbim_set_autotune": (i32, [vp, i32]),
         "shbim_set_outer_precision": (i32, [vp, i32]),
         "shbim_set_rows_precision": (i32, [vp, i32]),
+        "shbim_set_tensor_cores": (i32, [vp, i32]),
         "shbim_pair_shape": (i32, [vp, i32, P(i32), P(i32)]),
         "shbim_probe_peak": (i32, [i32, i64, P(dp), P(dp), vp]),
         "shbim_set_pair_shape": (i32, [vp, i32, i32, i32]),
@@ -328,6 +329,9 @@ class Context:
 
     def set_rows_precision(self, precision: int):
         self._check(self._L.shbim_set_rows_precision(self._h, int(precision)), "shbim_set_rows_precision")
+
+    def set_tensor_cores(self, on: bool):
+        self._check(self._L.shbim_set_tensor_cores(self._h, 1 if on else 0), "shbim_set_tensor_cores")
 
     def set_autotune(self, on: bool):
         self._check(self._L.shbim_set_autotune(self._h, 1 if on else 0), "shbim_set_autotune")

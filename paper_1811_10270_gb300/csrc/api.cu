@@ -165,6 +165,7 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->phys.lb);
   cudaFree(ctx->dens_split);
   cudaFree(ctx->xdf);
+  cudaFree(ctx->tc_err);
   cudaFree(ctx->gm.xr);
   cudaFree(ctx->gm.rr);
   cudaFree(ctx->gm.dr);
@@ -200,6 +201,12 @@ int shbim_set_rows_precision(shbim_ctx* ctx, int precision) {
   if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_DF64)
     return fail(ctx, SHBIM_ERR_ARG, "row precision must be SHBIM_PREC_FP64 or SHBIM_PREC_DF64");
   ctx->rows_prec = precision;
+  return SHBIM_OK;
+}
+
+int shbim_set_tensor_cores(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->tc_rows = on != 0;
   return SHBIM_OK;
 }
 

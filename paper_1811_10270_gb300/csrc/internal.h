@@ -61,6 +61,10 @@ struct DegreeTables {
   float2* dqT_df = nullptr;      // per degree block transposed (coalesced reads for Dq x)
   float2* cs_theta_df = nullptr; // [p+1 base latitudes][2][p+1]: cos(m theta_j), sin(m theta_j)
   float2* cs_phi_df = nullptr;   // [2p+2 base longitudes][2][p+1]: cos(m phi_k), sin(m phi_k)
+  // digit planes of the up-grid DFT table for the tensor-core Fourier analysis (dft_tc.cu):
+  // [n tile][K step][digit][80 outputs x 16 longitudes, K-major canonical layout], bfloat16
+  uint16_t* dft_digits = nullptr;
+  int dft_ntiles = 0, dft_ksteps = 0;
 };
 
 struct Drop {
@@ -138,6 +142,8 @@ struct shbim_ctx {
   size_t dens_split_cap = 0;
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
+  bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
+  int* tc_err = nullptr;          // device flag: a tensor-core kernel timed out
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
   float* dens_up32 = nullptr;     // [6][nsource] source strengths (FP32)
@@ -311,6 +317,15 @@ int geometry_kernel32(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, c
 
 // ---- surface Laplacian (physics.cu)
 int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream_t s);
+
+// ---- tensor-core Fourier analysis of double-float rows (dft_tc.cu)
+// F[r][cs][m] = sum_k W[r][k] (cos|sin)(m phi_k), r < rows, on drop d's degree 2p+1 grid; W and F
+// double-float (float2), W rows of 2q+2 values, F rows of 2(p+1) values.
+int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T);
+// the kernel holds a 128-row tile of W in shared memory: degrees up to 34
+bool dft_tc_fits(int p);
+int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, float2* F,
+                        cudaStream_t s);
 
 // ---- shape-dependent state for an unchanged layout (api.cu)
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);

@@ -5,7 +5,8 @@
 //   2. synthesise the rotated x, x_theta, x_phi / sin on the degree 2p+1 grid and form the 14
 //      kernel weights mu J K / (4 pi) at every node (Laplace DL and SL, 6 Stokeslet and 6
 //      stresslet components);
-//   3. analyse the weights (Fourier stage folded four ways, then Legendre stage);
+//   3. analyse the weights (Fourier stage on the tensor cores, dft_tc.cu, or folded four ways in
+//      double-float; then the Legendre stage);
 //   4. rotate the coefficient rows back (row = D_R v) and store them as (hi, lo) FP32 planes.
 // Every sum and every pointwise operation is double-float (hi + lo FP32 pairs; Dekker products,
 // Knuth sums, Newton square roots), ~2^-44 relative per operation, so the rows agree with the
@@ -458,9 +459,13 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
       {
         TimeScope ts(ctx, SHBIM_K_SELF_ANALYSIS, s);
         const int64_t nrows = (int64_t)ct * ncomp * (d.q + 1);
-        k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, s>>>(wb, Ns, d.p, d.q,
-                                                                                  d.tab->up_trig_df, nrows, rows, F);
-        SHBIM_CHECK_LAUNCH(ctx, "k_analysis_f4_df");
+        if (ctx->tc_rows && dft_tc_fits(d.p)) {
+          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, F, s))) return rc;
+        } else {
+          k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, s>>>(wb, Ns, d.p, d.q,
+                                                                                    d.tab->up_trig_df, nrows, rows, F);
+          SHBIM_CHECK_LAUNCH(ctx, "k_analysis_f4_df");
+        }
         k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
         SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
       }
@@ -469,6 +474,15 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
                                                              d.tab->dq_off_dev,
                                                              d.rows_lap, d.rows_sto, d.nt);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_adj_df");
+    }
+  }
+  if (ctx->tc_rows && ctx->tc_err) {
+    int flag = 0;
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+    if (flag) {
+      SHBIM_CUDA(ctx, cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s));
+      return fail(ctx, SHBIM_ERR_CUDA, "tensor-core Fourier analysis: a bounded wait expired");
     }
   }
   return SHBIM_OK;

@@ -278,7 +278,8 @@ int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out) {
   int rc;
   if ((rc = build_grid(ctx, p, p, T->base)) ||
       (rc = build_grid(ctx, p, 2 * p + 1, T->up, &T->up_alf_df, &T->up_trig_df)) ||
-      (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine)) || (rc = build_rotation(ctx, p, *T))) {
+      (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine)) || (rc = build_rotation(ctx, p, *T)) ||
+      (rc = dft_tc_digits(ctx, p, *T))) {
     free_degree_tables(T);
     return rc;
   }
@@ -305,6 +306,7 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->up_trig_df);
   cudaFree(t->dq_df);
   cudaFree(t->dqT_df);
+  cudaFree(t->dft_digits);
   cudaFree(t->cs_theta_df);
   cudaFree(t->cs_phi_df);
   delete t;

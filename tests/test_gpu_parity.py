@@ -229,8 +229,9 @@ def test_three_drops_uneven_degrees_match_oracle(S):
 
 
 def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
-    """The singular self rows built in double-float arithmetic (the default) against the rows of
-    the FP64 build and the oracle, on one perturbed drop (self term only) and on two drops."""
+    """The singular self rows built in double-float arithmetic (the default, with the Fourier stage
+    on the tensor cores, and without) against the rows of the FP64 build and the oracle, on one
+    perturbed drop (self term only) and on two drops."""
     rng = np.random.default_rng(31)
     one = [inputs.Drop(11, inputs.perturbed_coef(11, rng, 1.0, (0.1, -0.2, 0.3)), np.zeros(sh.ncoef(11)),
                        2.5, np.array([0.1, -0.2, 0.3]), 1.0)]
@@ -241,9 +242,10 @@ def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
         sig = [inputs.random_density(d.p, rng)[0] for d in drops]
         u = [inputs.random_density(d.p, rng, 3) for d in drops]
         res = {}
-        for rows in (S.FP64, S.DF64):
+        for rows, tc in ((S.FP64, False), (S.DF64, False), (S.DF64, True)):
             ctx = S.Context(precision=S.FP64, R=2.0, gmres_tol=1e-12)
             ctx.set_rows_precision(rows)
+            ctx.set_tensor_cores(tc)
             ctx.set_drops([d.p for d in drops], T(np.concatenate([d.xcoef.ravel() for d in drops])),
                           [d.lam for d in drops])
             out = []
@@ -255,13 +257,14 @@ def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
             U = T(np.concatenate([a.ravel() for a in u]))
             ctx.eval_stokes(U, U, o3, S.OUT_COEF)
             out.append(o3.cpu().numpy())
-            res[rows] = out
+            res[(rows, tc)] = out
             ctx.close()
         refs = [np.concatenate(sysm.laplace_coef("ladl", sig)), np.concatenate(sysm.laplace_coef("lsl", sig)),
                 np.concatenate([a.ravel() for a in sysm.stokes_coef(u, u)])]
-        for a, b, ref in zip(res[S.DF64], res[S.FP64], refs):
-            assert rel_err(a, b) < 1e-12
-            assert rel_err(a, ref) < TOL64
+        for key in ((S.DF64, False), (S.DF64, True)):
+            for a, b, ref in zip(res[key], res[(S.FP64, False)], refs):
+                assert rel_err(a, b) < 1e-11, key
+                assert rel_err(a, ref) < TOL64, key
 
 
 def test_every_pair_launch_shape_matches_oracle(S):
