@@ -151,7 +151,7 @@ int shbim_destroy(shbim_ctx* ctx) {
     auto& N = ctx->near;
     cudaFree(N.stats); cudaFree(N.det_t); cudaFree(N.det_j); cudaFree(N.pair_t); cudaFree(N.pair_j);
     cudaFree(N.fgeo); cudaFree(N.fgeo32); cudaFree(N.fstr); cudaFree(N.fstr32); cudaFree(N.foff_dev);
-    cudaFree(N.fgeo32lo); cudaFree(N.fstr32lo);
+    cudaFree(N.fgeo32lo); cudaFree(N.fstr32lo); cudaFree(N.groups);
   }
   for (auto& g : ctx->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);

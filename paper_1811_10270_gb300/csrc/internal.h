@@ -201,6 +201,8 @@ struct shbim_ctx {
     float* fgeo32lo = nullptr;  size_t fgeo32lo_cap = 0;  // low parts (double-float sums)
     float* fstr32lo = nullptr;  size_t fstr32lo_cap = 0;
     int64_t* foff_dev = nullptr; size_t foff_cap = 0; // [2][n_drops]: offset, count
+    int4* groups = nullptr;   size_t groups_cap = 0;  // runs of <= 128 pairs sharing a source drop:
+    int ngroups = 0;                                  // (first pair, count, drop, 0)
     std::vector<int64_t> fine_off_h, fine_n_h;
     int64_t nfine = 0;
   } near;

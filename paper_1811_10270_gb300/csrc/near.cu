@@ -17,8 +17,11 @@
 
 #include "dfloat.cuh"
 #include "internal.h"
+#include "pair_df.cuh"
 
 namespace shbim {
+
+constexpr int kNearGroup = 128;   // near targets per CTA of the tiled FP32 kernel
 
 namespace {
 
@@ -330,6 +333,195 @@ __global__ void __launch_bounds__(256) k_near_direct(NearArgs A) {
   }
 }
 
+// FP32 near correction, tiled: a CTA takes a group of near targets of one source drop j (one
+// target per thread) and a chunk of the concatenated node list [drop j's upsampled nodes, then
+// its degree-q nodes with the strengths negated]; nodes are staged through shared memory in
+// tiles and read as broadcasts (as in the all-pairs kernels), sums compensated by two-sum, each
+// chunk's result added to the target's output with an FP64 atomic.
+template <int KIND>
+__global__ void __launch_bounds__(kNearGroup)
+k_near_tiled32(NearArgs A, const int4* __restrict__ groups) {
+  constexpr int NC = KIND == 2 ? 3 : 1;
+  constexpr int TILE = 256;
+  __shared__ float4 sp[TILE];                  // x y z (relative to drop j's centre), strength 0
+  __shared__ float4 sq[KIND == 2 ? TILE : 1];  // strengths 1..4
+  __shared__ float4 sr[KIND == 2 ? TILE : 1];  // strength 5, normal
+  const int4 g = groups[blockIdx.x];
+  const int j = g.z;
+  const DropDev D = A.drops[j];
+  const int64_t fo = A.fine_off[j], fn = A.fine_n[j];
+  const int64_t ntot = fn + D.ns;
+  const int64_t c0 = ntot * blockIdx.y / gridDim.y, c1 = ntot * (blockIdx.y + 1) / gridDim.y;
+  const bool act = (int)threadIdx.x < g.y;
+  const int64_t t = A.pair_t[g.x + (act ? threadIdx.x : 0)];
+  float th[3], tl[3], nv[3];
+  {
+    const double cj[3] = {D.cx, D.cy, D.cz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double d = A.tgt[c * A.ntarget + t] - cj[c];
+      th[c] = (float)d;
+      tl[c] = (float)(d - (double)th[c]);
+      nv[c] = (float)A.tgt[(3 + c) * A.ntarget + t];
+    }
+  }
+  float hi[NC], lo[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) hi[c] = lo[c] = 0.f;
+  for (int64_t base = c0; base < c1; base += TILE) {
+    const int cnt = (int)min((int64_t)TILE, c1 - base);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int64_t v = base + e;
+      const bool fine = v < fn;
+      const float* pos = fine ? A.fpos32 + fo + v : A.src32 + D.src_off + (v - fn);
+      const float* str = fine ? A.fstr32 + fo + v : A.sstr32 + D.src_off + (v - fn);
+      const int64_t ps = fine ? A.nfine : A.nsource;
+      const float sg = fine ? 1.f : -1.f;
+      if (KIND != 2) {
+        sp[e] = make_float4(pos[0], pos[ps], pos[2 * ps], sg * str[0]);
+      } else {
+        const float f0 = A.has_f ? sg * str[0] : 0.f, f1 = A.has_f ? sg * str[ps] : 0.f, f2 = A.has_f ? sg * str[2 * ps] : 0.f;
+        const float u0 = A.has_u ? sg * str[3 * ps] : 0.f, u1 = A.has_u ? sg * str[4 * ps] : 0.f,
+                    u2 = A.has_u ? sg * str[5 * ps] : 0.f;
+        sp[e] = make_float4(pos[0], pos[ps], pos[2 * ps], f0);
+        sq[e] = make_float4(f1, f2, u0, u1);
+        sr[e] = make_float4(u2, pos[3 * ps], pos[4 * ps], pos[5 * ps]);
+      }
+    }
+    __syncthreads();
+    float acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.f;
+#pragma unroll 4
+    for (int e = 0; e < cnt; ++e) {
+      const float4 P = sp[e];
+      const float dx = (th[0] - P.x) + tl[0];
+      const float dy = (th[1] - P.y) + tl[1];
+      const float dz = (th[2] - P.z) + tl[2];
+      const float ri = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+      if (KIND == 1) {
+        acc[0] = fmaf(P.w, ri, acc[0]);
+      } else if (KIND == 0) {
+        const float dn = fmaf(dx, nv[0], fmaf(dy, nv[1], dz * nv[2]));
+        acc[0] = fmaf(P.w * ri * ri * ri, dn, acc[0]);
+      } else {
+        const float4 Q = sq[e], R = sr[e];
+        const float ri2 = ri * ri, ri3 = ri2 * ri;
+        const float hf = fmaf(dx, P.w, fmaf(dy, Q.x, dz * Q.y));
+        const float hu = fmaf(dx, Q.z, fmaf(dy, Q.w, dz * R.x));
+        const float hn = fmaf(dx, R.y, fmaf(dy, R.z, dz * R.w));
+        const float tt = ri3 * fmaf(hu * hn, ri2, hf);
+        acc[0] = fmaf(P.w, ri, fmaf(dx, tt, acc[0]));
+        acc[1] = fmaf(Q.x, ri, fmaf(dy, tt, acc[1]));
+        acc[2] = fmaf(Q.y, ri, fmaf(dz, tt, acc[2]));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) two_sum_f(hi[c], lo[c], acc[c]);
+  }
+  if (!act) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const double val = 0.07957747154594766788 * ((double)hi[c] + (double)lo[c]);
+    if (KIND != 2) {
+      atomicAdd(A.out + t, val);
+    } else {
+      const DropDev Di = A.drops[A.tgt_drop[t]];
+      atomicAdd(A.out + 3 * Di.tgt_off + (int64_t)c * Di.nt + (t - Di.tgt_off), val);
+    }
+  }
+}
+
+// Double-float near correction, tiled like k_near_tiled32 (FP64-class accuracy on the FP32 pipe);
+// the per-source terms are those of the double-float all-pairs kernel.
+template <int KIND>
+__global__ void __launch_bounds__(kNearGroup)
+k_near_tiled_df(NearArgs A, const int4* __restrict__ groups) {
+  constexpr int NC = KIND == 2 ? 3 : 1;
+  constexpr int NV = KIND == 2 ? 6 : 2;
+  constexpr int TILE = 128;
+  __shared__ float4 sh[NV][TILE];
+  __shared__ float2 tv[kNearGroup][6];   // per target: offset from drop j's centre, normal
+  const int4 g = groups[blockIdx.x];
+  const int j = g.z;
+  const DropDev D = A.drops[j];
+  const int64_t fo = A.fine_off[j], fn = A.fine_n[j];
+  const int64_t ntot = fn + D.ns;
+  const int64_t c0 = ntot * blockIdx.y / gridDim.y, c1 = ntot * (blockIdx.y + 1) / gridDim.y;
+  const bool act = (int)threadIdx.x < g.y;
+  const int64_t t = A.pair_t[g.x + (act ? threadIdx.x : 0)];
+  {
+    const double cj[3] = {D.cx, D.cy, D.cz};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const dfl::df a = dfl::from_double(A.tgt[c * A.ntarget + t] - cj[c]);
+      const dfl::df n = dfl::from_double(A.tgt[(3 + c) * A.ntarget + t]);
+      tv[threadIdx.x][c] = make_float2(a.hi, a.lo);
+      tv[threadIdx.x][3 + c] = make_float2(n.hi, n.lo);
+    }
+  }
+  dfl::df T[3], N0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T[c] = dfl::df{tv[threadIdx.x][c].x, tv[threadIdx.x][c].y};
+    N0[c] = dfl::df{tv[threadIdx.x][3 + c].x, tv[threadIdx.x][3 + c].y};
+  }
+  dfl::acc acc[3];
+  for (int64_t base = c0; base < c1; base += TILE) {
+    const int cnt = (int)min((int64_t)TILE, c1 - base);
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      const int64_t v = base + e;
+      const bool fine = v < fn;
+      const int64_t o = fine ? fo + v : D.src_off + (v - fn);
+      const float* ph = fine ? A.fpos32 : A.src32;
+      const float* pl = fine ? A.fpos32lo : A.src32lo;
+      const float* qh = fine ? A.fstr32 : A.sstr32;
+      const float* ql = fine ? A.fstr32lo : A.sstr32lo;
+      const int64_t ps = fine ? A.nfine : A.nsource;
+      const float sg = fine ? 1.f : -1.f;
+      sh[0][e] = make_float4(ph[o], ph[ps + o], ph[2 * ps + o], pl[o]);
+      if constexpr (KIND != 2) {
+        sh[1][e] = make_float4(pl[ps + o], pl[2 * ps + o], sg * qh[o], sg * ql[o]);
+      } else {
+        float fv[6], uv[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          fv[2 * c] = A.has_f ? sg * qh[c * ps + o] : 0.f;
+          fv[2 * c + 1] = A.has_f ? sg * ql[c * ps + o] : 0.f;
+          uv[2 * c] = A.has_u ? sg * qh[(3 + c) * ps + o] : 0.f;
+          uv[2 * c + 1] = A.has_u ? sg * ql[(3 + c) * ps + o] : 0.f;
+        }
+        sh[1][e] = make_float4(pl[ps + o], pl[2 * ps + o], fv[0], fv[1]);
+        sh[2][e] = make_float4(fv[2], fv[3], fv[4], fv[5]);
+        sh[3][e] = make_float4(uv[0], uv[1], uv[2], uv[3]);
+        sh[4][e] = make_float4(uv[4], uv[5], ph[3 * ps + o], pl[3 * ps + o]);
+        sh[5][e] = make_float4(ph[4 * ps + o], pl[4 * ps + o], ph[5 * ps + o], pl[5 * ps + o]);
+      }
+    }
+    __syncthreads();
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e = 0; e < cnt; ++e) {
+      if constexpr (KIND != 2)
+        df_term<KIND>(T, N0, sh[0][e], sh[1][e], z4, z4, z4, z4, acc);
+      else
+        df_term<KIND>(T, N0, sh[0][e], sh[1][e], sh[2][e], sh[3][e], sh[4][e], sh[5][e], acc);
+    }
+  }
+  if (!act) return;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const double val = 0.07957747154594766788 * dfl::to_double(acc[c].value());
+    if (KIND != 2) {
+      atomicAdd(A.out + t, val);
+    } else {
+      const DropDev Di = A.drops[A.tgt_drop[t]];
+      atomicAdd(A.out + 3 * Di.tgt_off + (int64_t)c * Di.nt + (t - Di.tgt_off), val);
+    }
+  }
+}
+
 int grow(shbim_ctx* ctx, void** p, size_t* cap, size_t bytes, const char* what) {
   if (bytes <= *cap) return SHBIM_OK;
   cudaFree(*p);
@@ -400,6 +592,19 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
   SHBIM_CUDA(ctx, cudaMemcpy(N.pair_t, pt.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice));
   SHBIM_CUDA(ctx, cudaMemcpy(N.pair_j, pj.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice));
   N.npairs = cnt;
+  {
+    // runs of pairs with the same source drop, cut into groups of at most kNearGroup targets
+    std::vector<int4> g;
+    for (int k = 0; k < cnt;) {
+      int e = k;
+      while (e < cnt && pj[e] == pj[k] && e - k < kNearGroup) ++e;
+      g.push_back(make_int4(k, e - k, pj[k], 0));
+      k = e;
+    }
+    if ((rc = grow(ctx, (void**)&N.groups, &N.groups_cap, sizeof(int4) * g.size(), "near groups"))) return rc;
+    SHBIM_CUDA(ctx, cudaMemcpy(N.groups, g.data(), sizeof(int4) * g.size(), cudaMemcpyHostToDevice));
+    N.ngroups = (int)g.size();
+  }
   // upsampled geometry of every drop that has near targets
   N.fine_off_h.assign(nd, -1);
   N.fine_n_h.assign(nd, 0);
@@ -462,6 +667,22 @@ int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out,
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(32, (8ll * nsm + N.npairs - 1) / N.npairs));
   const dim3 g((unsigned)N.npairs, (unsigned)chunks);
+  if (mode != 0) {
+    // FP32 and double-float: tiled over groups of targets sharing a source drop
+    const int gc = (int)std::max<int64_t>(1, std::min<int64_t>(64, (8ll * nsm + N.ngroups - 1) / N.ngroups));
+    const dim3 gg((unsigned)N.ngroups, (unsigned)gc);
+    if (mode == 1) {
+      if (kind == 0) k_near_tiled32<0><<<gg, kNearGroup, 0, s>>>(A, N.groups);
+      else if (kind == 1) k_near_tiled32<1><<<gg, kNearGroup, 0, s>>>(A, N.groups);
+      else k_near_tiled32<2><<<gg, kNearGroup, 0, s>>>(A, N.groups);
+    } else {
+      if (kind == 0) k_near_tiled_df<0><<<gg, kNearGroup, 0, s>>>(A, N.groups);
+      else if (kind == 1) k_near_tiled_df<1><<<gg, kNearGroup, 0, s>>>(A, N.groups);
+      else k_near_tiled_df<2><<<gg, kNearGroup, 0, s>>>(A, N.groups);
+    }
+    SHBIM_CHECK_LAUNCH(ctx, "k_near_tiled");
+    return SHBIM_OK;
+  }
   if (kind == 0) {
     if (mode == 1) k_near_direct<0, 1><<<g, 256, 0, s>>>(A);
     else if (mode == 2) k_near_direct<0, 2><<<g, 256, 0, s>>>(A);

@@ -25,6 +25,7 @@
 
 #include "dfloat.cuh"
 #include "internal.h"
+#include "pair_df.cuh"
 
 namespace shbim {
 
@@ -251,8 +252,8 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
     const DropDev Dj = drops[j];
     const SrcRange rg = drop_range(Di, Dj, i, j, v0, v1);
     if (rg.a >= rg.b) continue;
-    const df T0 = dfl::from_double(X0[0] - Dj.cx), T1 = dfl::from_double(X0[1] - Dj.cy),
-             T2 = dfl::from_double(X0[2] - Dj.cz);
+    const df T[3] = {dfl::from_double(X0[0] - Dj.cx), dfl::from_double(X0[1] - Dj.cy),
+                     dfl::from_double(X0[2] - Dj.cz)};
     for (int64_t base = rg.a; base < rg.b; base += kTile) {
       const int cnt = (int)min((int64_t)kTile, rg.b - base);
       __syncthreads();
@@ -283,36 +284,11 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
       }
       __syncthreads();
       for (int e = 0; e < cnt; ++e) {
-        const float4 a = sh[0][e], b = sh[1][e];
-        const df dx = dfl::diff(T0, df{a.x, a.w});
-        const df dy = dfl::diff(T1, df{a.y, b.x});
-        const df dz = dfl::diff(T2, df{a.z, b.y});
-        const df r2 = dfl::dot3(dx, dy, dz, dx, dy, dz);
-        const df ri = dfl::rsqrt(r2);
-        if (KIND == LSL) {
-          A[0].add_prod(df{b.z, b.w}, ri);
-        } else if (KIND == LDL) {
-          const df dn = dfl::dot3(dx, dy, dz, N0[0], N0[1], N0[2]);
-          const df ri3 = dfl::mul(dfl::sqr(ri), ri);
-          A[0].add_prod(dfl::mul(df{b.z, b.w}, ri3), dn);
-        } else {
-          const float4 c4 = sh[2][e], d4 = sh[3][e], e4 = sh[4][e], g4 = sh[5][e];
-          const df fx{b.z, b.w}, fy{c4.x, c4.y}, fz{c4.z, c4.w};
-          const df ux{d4.x, d4.y}, uy{d4.z, d4.w}, uz{e4.x, e4.y};
-          const df nx{e4.z, e4.w}, ny{g4.x, g4.y}, nz{g4.z, g4.w};
-          const df hf = dfl::dot3(dx, dy, dz, fx, fy, fz);
-          const df hu = dfl::dot3(dx, dy, dz, ux, uy, uz);
-          const df hn = dfl::dot3(dx, dy, dz, nx, ny, nz);
-          const df ri2 = dfl::sqr(ri);
-          const df ri3 = dfl::mul(ri2, ri);
-          const df tt = dfl::mul(ri3, dfl::add(hf, dfl::mul(dfl::mul(hu, hn), ri2)));
-          A[0].add_prod(fx, ri);
-          A[0].add_prod(dx, tt);
-          A[1].add_prod(fy, ri);
-          A[1].add_prod(dy, tt);
-          A[2].add_prod(fz, ri);
-          A[2].add_prod(dz, tt);
-        }
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (KIND != STO)
+          df_term<KIND>(T, N0, sh[0][e], sh[1][e], z4, z4, z4, z4, A);
+        else
+          df_term<KIND>(T, N0, sh[0][e], sh[1][e], sh[2][e], sh[3][e], sh[4][e], sh[5][e], A);
       }
     }
   }

@@ -135,6 +135,94 @@ __global__ void k_rotate_adj_df(const float2* __restrict__ vbuf, int nc, int p, 
   }
 }
 
+// Rotation of all components of one target (blockIdx.x) degree by degree: every stage of
+// D_R = Dz(phi) Dq^T Dz(theta) Dq acts within a degree block, so the block Dq_n is staged in shared
+// memory once and applied to the target's ncomp vectors.
+//   forward (adjoint = false): out = Dq^T Dz(-theta) Dq Dz(-phi) in   (position coefficients)
+//   adjoint (adjoint = true):  out = Dz(phi) Dq^T Dz(theta) Dq in     (rows, FP32 planes)
+template <bool ADJ>
+__global__ void __launch_bounds__(256)
+k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int ncomp,
+                const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
+                const float2* __restrict__ dq, const int* __restrict__ dq_off, float2* __restrict__ vout,
+                float* __restrict__ rows_lap, float* __restrict__ rows_sto, int nt_drop) {
+  extern __shared__ float2 smf[];
+  const int wmax = 2 * p + 1;
+  float2* D = smf;                        // [w][w] Dq_n
+  float2* X = D + wmax * wmax;            // [ncomp][w]
+  float2* Y = X + ncomp * wmax;           // [ncomp][w]
+  const int tl = t_begin + blockIdx.x;
+  const int nlon = 2 * p + 2;
+  const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
+  const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
+  const float2* vt = vin + (int64_t)blockIdx.x * in_stride;   // in_stride 0: one input for all
+  // Dz on the degree-n block of every component, in place: (a, b) = (v[m], v[-m]) rotated by m alpha
+  auto dz = [&](float2* V, int n, const float2* cs, bool neg) {
+    const int w = 2 * n + 1;
+    for (int task = threadIdx.x; task < ncomp * n; task += blockDim.x) {
+      const int c = task / n, m = task - c * n + 1;
+      const df ca = ld(cs, m);
+      df sa = ld(cs, p + 1 + m);
+      if (neg) sa = dfl::neg(sa);
+      float2* v = V + c * w;
+      const df a = ld(v, n + m), b = ld(v, n - m);
+      st(v, n + m, dfl::sub(dfl::mul(ca, a), dfl::mul(sa, b)));
+      st(v, n - m, dfl::add(dfl::mul(sa, a), dfl::mul(ca, b)));
+    }
+  };
+  // out[c][m] = sum_k M[m][k] in[c][k] with M = Dq_n (trans = false) or Dq_n^T (trans = true)
+  auto apply_dq = [&](const float2* in, float2* out, int n, bool trans) {
+    const int w = 2 * n + 1;
+    for (int task = threadIdx.x; task < ncomp * w; task += blockDim.x) {
+      const int c = task / w, m = task - c * w;
+      const float2* x = in + c * w;
+      dfl::acc acc;
+      if (!trans)
+        for (int k = 0; k < w; ++k) acc.add_prod(ld(D, m * w + k), ld(x, k));
+      else
+        for (int k = 0; k < w; ++k) acc.add_prod(ld(D, k * w + m), ld(x, k));
+      st(out, c * w + m, acc.value());
+    }
+  };
+  for (int n = 0; n <= p; ++n) {
+    const int w = 2 * n + 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < w * w; i += blockDim.x) D[i] = dq[dq_off[n] + i];
+    for (int i = threadIdx.x; i < ncomp * w; i += blockDim.x) {
+      const int c = i / w, k = i - c * w;
+      X[i] = vt[(int64_t)c * nc + n * n + k];
+    }
+    __syncthreads();
+    if (!ADJ) {
+      dz(X, n, cp, true);
+      __syncthreads();
+    }
+    apply_dq(X, Y, n, false);
+    __syncthreads();
+    dz(Y, n, ct, !ADJ);
+    __syncthreads();
+    apply_dq(Y, X, n, true);
+    __syncthreads();
+    if (ADJ) {
+      dz(X, n, cp, false);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < ncomp * w; i += blockDim.x) {
+      const int c = i / w, k = i - c * w;
+      const df v = ld(X, i);
+      if (!ADJ) {
+        vout[((int64_t)blockIdx.x * ncomp + c) * nc + n * n + k] = make_float2(v.hi, v.lo);
+      } else {
+        float* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
+                                 : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
+        const int64_t plane = (int64_t)nt_drop * (c < kNumLap ? kNumLap : kNumSto) * nc;
+        dst[n * n + k] = v.hi;
+        dst[plane + n * n + k] = v.lo;
+      }
+    }
+  }
+}
+
 // Four-longitude Fourier synthesis (the parity folding of synth4) in double-float.
 __device__ void synth4_df(const float2* __restrict__ a, const float2* __restrict__ b, df a0, float beta, int p,
                           int k, int N, const float2* __restrict__ tc, const float2* __restrict__ ts,
@@ -438,6 +526,11 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     k_to_df<<<(unsigned)((3 * nc + 255) / 256), 256, 0, s>>>(xcoef + 3 * d.coef_off, 3 * nc, xc);
     SHBIM_CHECK_LAUNCH(ctx, "k_to_df");
     const int rot_smem = 2 * nc * (int)sizeof(float2);
+    const int wmax = 2 * d.p + 1;
+    const int deg_smem3 = (wmax * wmax + 2 * 3 * wmax) * (int)sizeof(float2);
+    const int deg_smem14 = (wmax * wmax + 2 * ncomp * wmax) * (int)sizeof(float2);
+    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_deg_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, deg_smem3));
+    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_deg_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, deg_smem14));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_fwd_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_adj_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
     const size_t w_smem = (size_t)(18 * (d.p + 1) + 11 * N) * sizeof(float2);
@@ -447,9 +540,12 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int nt = (d.p + 1) * (d.p + 2) / 2;
     for (int t0 = 0; t0 < d.nt; t0 += CT) {
       const int ct = std::min(CT, d.nt - t0);
-      k_rotate_fwd_df<<<dim3(ct, 3), 128, rot_smem, s>>>(xc, nc, d.p, t0, d.tab->cs_theta_df, d.tab->cs_phi_df,
-                                                         d.tab->dq_df, d.tab->dqT_df, d.tab->dq_off_dev, rot);
-      SHBIM_CHECK_LAUNCH(ctx, "k_rotate_fwd_df");
+      {
+        // the position coefficients are the same for every target: zero input stride
+        k_rotate_deg_df<false><<<ct, 256, deg_smem3, s>>>(xc, 0, nc, d.p, t0, 3, d.tab->cs_theta_df, d.tab->cs_phi_df,
+                                                         d.tab->dq_df, d.tab->dq_off_dev, rot, nullptr, nullptr, d.nt);
+        SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+      }
       {
         TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
         k_self_weights_df<<<dim3(ct, d.q + 1), 128, w_smem, s>>>(rot, d.p, d.q, d.tab->up_alf_df, d.tab->up_trig_df,
@@ -469,11 +565,10 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
         SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
       }
-      k_rotate_adj_df<<<dim3(ct, ncomp), 128, rot_smem, s>>>(vb, nc, d.p, t0, ncomp, d.tab->cs_theta_df,
-                                                             d.tab->cs_phi_df, d.tab->dq_df, d.tab->dqT_df,
-                                                             d.tab->dq_off_dev,
-                                                             d.rows_lap, d.rows_sto, d.nt);
-      SHBIM_CHECK_LAUNCH(ctx, "k_rotate_adj_df");
+      k_rotate_deg_df<true><<<ct, 256, deg_smem14, s>>>(vb, (int64_t)ncomp * nc, nc, d.p, t0, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df,
+                                                       d.tab->dq_df, d.tab->dq_off_dev, nullptr, d.rows_lap,
+                                                       d.rows_sto, d.nt);
+      SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
     }
   }
   if (ctx->tc_rows && ctx->tc_err) {
