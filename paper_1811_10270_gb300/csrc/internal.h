@@ -44,6 +44,8 @@ struct GridTables {
   double* mu = nullptr;      // [q+1] modified weight omega_j 2 sin(theta_j/2) sum_{n<=q} P_n(t_j)
   double* trig = nullptr;    // [2][2q+2] cos, sin of 2 pi k / (2q+2)
   double* theta = nullptr;   // [q+1]
+  float* alf32 = nullptr;    // [q+1][ntri(p)] Pbar in FP32 (FP32 synthesis of strengths), or null
+  float* trig32 = nullptr;   // [2][2q+2] in FP32
 };
 
 struct DegreeTables {

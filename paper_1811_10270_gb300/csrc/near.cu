@@ -669,7 +669,12 @@ int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out,
   const dim3 g((unsigned)N.npairs, (unsigned)chunks);
   if (mode != 0) {
     // FP32 and double-float: tiled over groups of targets sharing a source drop
-    const int gc = (int)std::max<int64_t>(1, std::min<int64_t>(64, (8ll * nsm + N.ngroups - 1) / N.ngroups));
+    // chunks of at least 512 nodes, enough CTAs for ~8 per SM
+    int64_t nmax = 0;
+    for (int j = 0; j < ctx->n_drops; ++j)
+      if (N.fine_off_h[j] >= 0) nmax = std::max<int64_t>(nmax, N.fine_n_h[j] + ctx->drops[j].ns);
+    const int gc = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::max<int64_t>(1, nmax / 512), (8ll * nsm + N.ngroups - 1) / N.ngroups));
     const dim3 gg((unsigned)N.ngroups, (unsigned)gc);
     if (mode == 1) {
       if (kind == 0) k_near_tiled32<0><<<gg, kNearGroup, 0, s>>>(A, N.groups);

@@ -154,11 +154,85 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
   return SHBIM_OK;
 }
 
+// FP32 synthesis of values only, scaled per node, for the FP32 copies the FP32 sums read:
+// out32[item][node] = fl32(alpha scale[node]) * sum_nm c_nm S_nm(node), Legendre and four-fold Fourier
+// sums in FP32 (relative error ~1e-7, as the FP32 path allows).
+__global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, int p, int q,
+                          const float* __restrict__ alf32, const float* __restrict__ trig32, float* __restrict__ out32,
+                          int64_t item_stride, const double* __restrict__ scale, double alpha) {
+  extern __shared__ float smf32[];
+  const int item = blockIdx.x, j = blockIdx.y;
+  const int N = 2 * q + 2, P1 = p + 1, Q4 = N >> 2, h = N >> 1;
+  float* A = smf32;          // [2][P1]
+  float* tc = A + 2 * P1;    // [N]
+  float* ts = tc + N;        // [N]
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    tc[i] = trig32[i];
+    ts[i] = trig32[N + i];
+  }
+  const double* c = coef + (int64_t)item * coef_stride;
+  const int nt = P1 * (p + 2) / 2;
+  const float* T = alf32 + (int64_t)j * nt;
+  for (int task = threadIdx.x; task < 2 * P1; task += blockDim.x) {
+    const int m = task >> 1, cs = task & 1;
+    float acc = 0.f;
+    if (!(cs == 1 && m == 0)) {
+      const float* col = T + tri_off_d(p, m);
+      const int sgn = cs ? -m : m;
+      for (int n = m; n <= p; ++n) acc = fmaf((float)__ldg(c + n * n + n + sgn), col[n - m], acc);
+    }
+    A[cs * P1 + m] = acc;
+  }
+  __syncthreads();
+  const float* Ac = A;
+  const float* As = A + P1;
+  const float s2 = 1.41421356f;
+  float* out = out32 + (int64_t)item * item_stride + (int64_t)j * N;
+  const double* sc = scale + (int64_t)j * N;
+  for (int k = threadIdx.x; k <= Q4; k += blockDim.x) {
+    float ce = 0.f, co = 0.f, se = 0.f, so = 0.f;
+    int id = 0, m = 1;
+    for (; m + 1 <= p; m += 2) {
+      id += k;
+      if (id >= N) id -= N;
+      co = fmaf(Ac[m], tc[id], co);
+      so = fmaf(As[m], ts[id], so);
+      id += k;
+      if (id >= N) id -= N;
+      ce = fmaf(Ac[m + 1], tc[id], ce);
+      se = fmaf(As[m + 1], ts[id], se);
+    }
+    if (m <= p) {
+      id += k;
+      if (id >= N) id -= N;
+      co = fmaf(Ac[m], tc[id], co);
+      so = fmaf(As[m], ts[id], so);
+    }
+    const float c1 = ce + co, s1 = se + so, c2 = ce - co, s2v = so - se;
+    const int ks[4] = {k, (N - k) % N, h - k, h + k};
+    const float vs[4] = {Ac[0] + s2 * (c1 + s1), Ac[0] + s2 * (c1 - s1), Ac[0] + s2 * (c2 + s2v),
+                         Ac[0] + s2 * (c2 - s2v)};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      // k = 0 and k = N/4 produce some longitudes twice with equal values
+      out[ks[u]] = vs[u] * (float)(alpha * sc[ks[u]]);
+    }
+  }
+}
+
 // Synthesis with a scalar factor on the scaled values (used for (lam_j - 1) strengths).
 int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
                      int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
                      double alpha, float* out32, cudaStream_t s, float* out32lo) {
   if (n_items <= 0) return SHBIM_OK;
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP && out32 && !out32lo && g.alf32 && ((2 * g.q + 2) & 3) == 0) {
+    // only the FP32 copies are read in this mode: FP32 arithmetic
+    const size_t smem32 = (size_t)(2 * (g.p + 1) + 2 * (2 * g.q + 2)) * sizeof(float);
+    k_synth32<<<dim3(n_items, g.q + 1), 128, smem32, s>>>(coef, coef_stride, g.p, g.q, g.alf32, g.trig32, out32,
+                                                          item_stride, scale, alpha);
+    SHBIM_CHECK_LAUNCH(ctx, "k_synth32");
+    return SHBIM_OK;
+  }
   const size_t smem = (size_t)(2 * (g.p + 1) + 3 * (2 * g.q + 2)) * sizeof(double);
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);

@@ -135,89 +135,96 @@ __global__ void k_rotate_adj_df(const float2* __restrict__ vbuf, int nc, int p, 
   }
 }
 
-// Rotation of all components of one target (blockIdx.x) degree by degree: every stage of
+// Rotation of all components of TPB targets per CTA, degree by degree: every stage of
 // D_R = Dz(phi) Dq^T Dz(theta) Dq acts within a degree block, so the block Dq_n is staged in shared
-// memory once and applied to the target's ncomp vectors.
-//   forward (adjoint = false): out = Dq^T Dz(-theta) Dq Dz(-phi) in   (position coefficients)
-//   adjoint (adjoint = true):  out = Dz(phi) Dq^T Dz(theta) Dq in     (rows, FP32 planes)
+// memory once and applied to the TPB x ncomp vectors of the CTA.
+//   forward (ADJ = false): out = Dq^T Dz(-theta) Dq Dz(-phi) in   (position coefficients)
+//   adjoint (ADJ = true):  out = Dz(phi) Dq^T Dz(theta) Dq in     (rows, FP32 planes)
 template <bool ADJ>
 __global__ void __launch_bounds__(256)
-k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int ncomp,
-                const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
+k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int t_count,
+                int tpb, int ncomp, const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
                 const float2* __restrict__ dq, const int* __restrict__ dq_off, float2* __restrict__ vout,
                 float* __restrict__ rows_lap, float* __restrict__ rows_sto, int nt_drop) {
   extern __shared__ float2 smf[];
   const int wmax = 2 * p + 1;
-  float2* D = smf;                        // [w][w] Dq_n
-  float2* X = D + wmax * wmax;            // [ncomp][w]
-  float2* Y = X + ncomp * wmax;           // [ncomp][w]
-  const int tl = t_begin + blockIdx.x;
+  const int b0 = blockIdx.x * tpb;                      // first chunk-local target of the CTA
+  const int nb = min(tpb, t_count - b0);                // targets of this CTA
+  const int nv = nb * ncomp;                            // vectors
+  float2* D = smf;                                      // [w][w] Dq_n
+  float2* X = D + wmax * wmax;                          // [tpb * ncomp][w]
+  float2* Y = X + tpb * ncomp * wmax;                   // [tpb * ncomp][w]
   const int nlon = 2 * p + 2;
-  const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
-  const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
-  const float2* vt = vin + (int64_t)blockIdx.x * in_stride;   // in_stride 0: one input for all
-  // Dz on the degree-n block of every component, in place: (a, b) = (v[m], v[-m]) rotated by m alpha
-  auto dz = [&](float2* V, int n, const float2* cs, bool neg) {
+  auto cs_of = [&](int v, bool theta) {
+    const int tl = t_begin + b0 + v / ncomp;
+    return theta ? cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1) : cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
+  };
+  // Dz on the degree-n block of every vector, in place: (v[m], v[-m]) rotated by m alpha
+  auto dz = [&](float2* V, int n, bool theta, bool neg) {
     const int w = 2 * n + 1;
-    for (int task = threadIdx.x; task < ncomp * n; task += blockDim.x) {
-      const int c = task / n, m = task - c * n + 1;
+    for (int task = threadIdx.x; task < nv * n; task += blockDim.x) {
+      const int v = task / n, m = task - v * n + 1;
+      const float2* cs = cs_of(v, theta);
       const df ca = ld(cs, m);
       df sa = ld(cs, p + 1 + m);
       if (neg) sa = dfl::neg(sa);
-      float2* v = V + c * w;
-      const df a = ld(v, n + m), b = ld(v, n - m);
-      st(v, n + m, dfl::sub(dfl::mul(ca, a), dfl::mul(sa, b)));
-      st(v, n - m, dfl::add(dfl::mul(sa, a), dfl::mul(ca, b)));
+      float2* x = V + v * w;
+      const df a = ld(x, n + m), b = ld(x, n - m);
+      st(x, n + m, dfl::sub(dfl::mul(ca, a), dfl::mul(sa, b)));
+      st(x, n - m, dfl::add(dfl::mul(sa, a), dfl::mul(ca, b)));
     }
   };
-  // out[c][m] = sum_k M[m][k] in[c][k] with M = Dq_n (trans = false) or Dq_n^T (trans = true)
+  // out[v][m] = sum_k M[m][k] in[v][k] with M = Dq_n (trans = false) or Dq_n^T (trans = true)
   auto apply_dq = [&](const float2* in, float2* out, int n, bool trans) {
     const int w = 2 * n + 1;
-    for (int task = threadIdx.x; task < ncomp * w; task += blockDim.x) {
-      const int c = task / w, m = task - c * w;
-      const float2* x = in + c * w;
+    for (int task = threadIdx.x; task < nv * w; task += blockDim.x) {
+      const int v = task / w, m = task - v * w;
+      const float2* x = in + v * w;
       dfl::acc acc;
       if (!trans)
         for (int k = 0; k < w; ++k) acc.add_prod(ld(D, m * w + k), ld(x, k));
       else
         for (int k = 0; k < w; ++k) acc.add_prod(ld(D, k * w + m), ld(x, k));
-      st(out, c * w + m, acc.value());
+      st(out, v * w + m, acc.value());
     }
   };
   for (int n = 0; n <= p; ++n) {
     const int w = 2 * n + 1;
     __syncthreads();
     for (int i = threadIdx.x; i < w * w; i += blockDim.x) D[i] = dq[dq_off[n] + i];
-    for (int i = threadIdx.x; i < ncomp * w; i += blockDim.x) {
-      const int c = i / w, k = i - c * w;
-      X[i] = vt[(int64_t)c * nc + n * n + k];
+    for (int i = threadIdx.x; i < nv * w; i += blockDim.x) {
+      const int v = i / w, k = i - v * w;
+      const int b = v / ncomp, c = v - b * ncomp;
+      X[i] = vin[(int64_t)(b0 + b) * in_stride + (int64_t)c * nc + n * n + k];
     }
     __syncthreads();
     if (!ADJ) {
-      dz(X, n, cp, true);
+      dz(X, n, false, true);
       __syncthreads();
     }
     apply_dq(X, Y, n, false);
     __syncthreads();
-    dz(Y, n, ct, !ADJ);
+    dz(Y, n, true, !ADJ);
     __syncthreads();
     apply_dq(Y, X, n, true);
     __syncthreads();
     if (ADJ) {
-      dz(X, n, cp, false);
+      dz(X, n, false, false);
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < ncomp * w; i += blockDim.x) {
-      const int c = i / w, k = i - c * w;
-      const df v = ld(X, i);
+    for (int i = threadIdx.x; i < nv * w; i += blockDim.x) {
+      const int v = i / w, k = i - v * w;
+      const int b = v / ncomp, c = v - b * ncomp;
+      const df x = ld(X, i);
       if (!ADJ) {
-        vout[((int64_t)blockIdx.x * ncomp + c) * nc + n * n + k] = make_float2(v.hi, v.lo);
+        vout[((int64_t)(b0 + b) * ncomp + c) * nc + n * n + k] = make_float2(x.hi, x.lo);
       } else {
+        const int tl = t_begin + b0 + b;
         float* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
                                  : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
         const int64_t plane = (int64_t)nt_drop * (c < kNumLap ? kNumLap : kNumSto) * nc;
-        dst[n * n + k] = v.hi;
-        dst[plane + n * n + k] = v.lo;
+        dst[n * n + k] = x.hi;
+        dst[plane + n * n + k] = x.lo;
       }
     }
   }
@@ -527,8 +534,18 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     SHBIM_CHECK_LAUNCH(ctx, "k_to_df");
     const int rot_smem = 2 * nc * (int)sizeof(float2);
     const int wmax = 2 * d.p + 1;
-    const int deg_smem3 = (wmax * wmax + 2 * 3 * wmax) * (int)sizeof(float2);
-    const int deg_smem14 = (wmax * wmax + 2 * ncomp * wmax) * (int)sizeof(float2);
+    // targets per CTA of the rotations: as many as fit beside the Dq block in ~100 KB
+    const int per_t3 = 2 * 3 * wmax * (int)sizeof(float2), per_t14 = 2 * ncomp * wmax * (int)sizeof(float2);
+    const int dq_bytes = wmax * wmax * (int)sizeof(float2);
+    // ... and no more than keeps at least two CTAs per SM busy for a chunk of CT targets
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = std::max(1, CT / (2 * nsm));
+    const int tpb3 = std::max(1, std::min({16, (100 * 1024 - dq_bytes) / per_t3, occ}));
+    const int tpb14 = std::max(1, std::min({8, (100 * 1024 - dq_bytes) / per_t14, occ}));
+    const int deg_smem3 = dq_bytes + tpb3 * per_t3;
+    const int deg_smem14 = dq_bytes + tpb14 * per_t14;
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_deg_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, deg_smem3));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_deg_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, deg_smem14));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_fwd_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
@@ -542,8 +559,9 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
       const int ct = std::min(CT, d.nt - t0);
       {
         // the position coefficients are the same for every target: zero input stride
-        k_rotate_deg_df<false><<<ct, 256, deg_smem3, s>>>(xc, 0, nc, d.p, t0, 3, d.tab->cs_theta_df, d.tab->cs_phi_df,
-                                                         d.tab->dq_df, d.tab->dq_off_dev, rot, nullptr, nullptr, d.nt);
+        k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, s>>>(
+            xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
+            rot, nullptr, nullptr, d.nt);
         SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
       }
       {
@@ -565,9 +583,9 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
         SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
       }
-      k_rotate_deg_df<true><<<ct, 256, deg_smem14, s>>>(vb, (int64_t)ncomp * nc, nc, d.p, t0, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df,
-                                                       d.tab->dq_df, d.tab->dq_off_dev, nullptr, d.rows_lap,
-                                                       d.rows_sto, d.nt);
+      k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
+          vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df,
+          d.tab->dq_off_dev, nullptr, d.rows_lap, d.rows_sto, d.nt);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
     }
   }

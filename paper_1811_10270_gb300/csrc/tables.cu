@@ -97,8 +97,18 @@ int upload_df(shbim_ctx* ctx, float2** dst, const std::vector<float2>& src) {
 }
 
 // alf_df / trig_df (optional): double-float copies of the kinds 0..2 and of the trig table
+int upload_f(shbim_ctx* ctx, float** dst, const std::vector<float>& src) {
+  cudaError_t e = cudaMalloc(dst, src.size() * sizeof(float));
+  if (e != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc for tables failed");
+  e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy tables");
+  return SHBIM_OK;
+}
+
+// alf_df / trig_df (optional): double-float copies of the kinds 0..2 and of the trig table;
+// f32: FP32 copies of kind 0 and of the trig table
 int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g, float2** alf_df = nullptr,
-               float2** trig_df = nullptr) {
+               float2** trig_df = nullptr, bool f32 = false) {
   g.p = p;
   g.q = q;
   std::vector<double> t, wg;
@@ -160,6 +170,13 @@ int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g, float2** alf_df = nu
     std::vector<float2> tr(2 * N);
     for (int k = 0; k < 2 * N; ++k) tr[k] = split_df(trig[k]);
     if ((rc = upload_df(ctx, trig_df, tr))) return rc;
+  }
+  if (f32) {
+    std::vector<float> a((size_t)(q + 1) * nt), tr(2 * N);
+    for (int j = 0; j <= q; ++j)
+      for (int o = 0; o < nt; ++o) a[(size_t)j * nt + o] = (float)alf[(size_t)j * kNumTab * nt + o];
+    for (int k = 0; k < 2 * N; ++k) tr[k] = (float)trig[k];
+    if ((rc = upload_f(ctx, &g.alf32, a)) || (rc = upload_f(ctx, &g.trig32, tr))) return rc;
   }
   if ((rc = upload(ctx, &g.alf, alf))) return rc;
   if ((rc = upload(ctx, &g.omega, om))) return rc;
@@ -277,8 +294,8 @@ int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out) {
   T->p = p;
   int rc;
   if ((rc = build_grid(ctx, p, p, T->base)) ||
-      (rc = build_grid(ctx, p, 2 * p + 1, T->up, &T->up_alf_df, &T->up_trig_df)) ||
-      (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine)) || (rc = build_rotation(ctx, p, *T)) ||
+      (rc = build_grid(ctx, p, 2 * p + 1, T->up, &T->up_alf_df, &T->up_trig_df, true)) ||
+      (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine, nullptr, nullptr, true)) || (rc = build_rotation(ctx, p, *T)) ||
       (rc = dft_tc_digits(ctx, p, *T))) {
     free_degree_tables(T);
     return rc;
@@ -288,6 +305,8 @@ int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out) {
 }
 
 static void free_grid(GridTables& g) {
+  cudaFree(g.alf32);
+  cudaFree(g.trig32);
   cudaFree(g.alf);
   cudaFree(g.omega);
   cudaFree(g.mu);
