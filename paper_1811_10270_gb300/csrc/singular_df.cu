@@ -507,7 +507,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int nc = d.nc;
     const int N = 2 * d.q + 2;
     if (N % 4) return fail(ctx, SHBIM_ERR_ARG, "double-float row build needs 4 | 2q+2");
-    int CT = (int)std::max<int64_t>(1, std::min<int64_t>(d.nt, (256ll << 20) / (ncomp * Ns * 8)));
+    int CT = (int)std::max<int64_t>(1, std::min<int64_t>(d.nt, (1024ll << 20) / (ncomp * Ns * 8)));
     int rc;
     if ((rc = ensure_d(ctx, &ctx->rot_coef, &ctx->rot_elems, (size_t)CT * 3 * nc, "rotation buffer")) ||
         (rc = ensure_d(ctx, &ctx->wbuf, &ctx->wbuf_elems, (size_t)CT * ncomp * Ns, "weight buffer")) ||
