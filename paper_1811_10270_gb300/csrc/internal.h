@@ -61,6 +61,11 @@ struct DegreeTables {
   float2* up_trig_df = nullptr;  // [2][4p+4]: cos, sin of 2 pi k / (4p+4)
   float2* dq_df = nullptr;       // as dq
   float2* dqT_df = nullptr;      // per degree block transposed (coalesced reads for Dq x)
+  // nonzero pattern of the Dq blocks (about a quarter of the entries; parity structure of the
+  // quarter turn): per row and per column of every block, the nonzero entries as an arithmetic
+  // progression (start, count, step) of column (row) indices, indexed like the coefficients
+  int4* dq_rows = nullptr;       // [(p+1)^2]
+  int4* dq_cols = nullptr;       // [(p+1)^2]
   float2* cs_theta_df = nullptr; // [p+1 base latitudes][2][p+1]: cos(m theta_j), sin(m theta_j)
   float2* cs_phi_df = nullptr;   // [2p+2 base longitudes][2][p+1]: cos(m phi_k), sin(m phi_k)
   // digit planes of the up-grid DFT table for the tensor-core Fourier analysis (dft_tc.cu):

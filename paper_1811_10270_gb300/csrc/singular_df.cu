@@ -144,8 +144,9 @@ template <bool ADJ>
 __global__ void __launch_bounds__(256)
 k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int t_count,
                 int tpb, int ncomp, const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
-                const float2* __restrict__ dq, const int* __restrict__ dq_off, float2* __restrict__ vout,
-                float* __restrict__ rows_lap, float* __restrict__ rows_sto, int nt_drop) {
+                const float2* __restrict__ dq, const int* __restrict__ dq_off, const int4* __restrict__ dq_rows,
+                const int4* __restrict__ dq_cols, float2* __restrict__ vout, float* __restrict__ rows_lap,
+                float* __restrict__ rows_sto, int nt_drop) {
   extern __shared__ float2 smf[];
   const int wmax = 2 * p + 1;
   const int b0 = blockIdx.x * tpb;                      // first chunk-local target of the CTA
@@ -181,10 +182,12 @@ k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p
       const int v = task / w, m = task - v * w;
       const float2* x = in + v * w;
       dfl::acc acc;
+      // only the nonzero entries of row m (column m for the transpose)
+      const int4 pr = (trans ? dq_cols : dq_rows)[n * n + m];
       if (!trans)
-        for (int k = 0; k < w; ++k) acc.add_prod(ld(D, m * w + k), ld(x, k));
+        for (int i = 0, k = pr.x; i < pr.y; ++i, k += pr.z) acc.add_prod(ld(D, m * w + k), ld(x, k));
       else
-        for (int k = 0; k < w; ++k) acc.add_prod(ld(D, k * w + m), ld(x, k));
+        for (int i = 0, k = pr.x; i < pr.y; ++i, k += pr.z) acc.add_prod(ld(D, k * w + m), ld(x, k));
       st(out, v * w + m, acc.value());
     }
   };
@@ -561,7 +564,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         // the position coefficients are the same for every target: zero input stride
         k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, s>>>(
             xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
-            rot, nullptr, nullptr, d.nt);
+            d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
         SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
       }
       {
@@ -585,7 +588,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
       }
       k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
           vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df,
-          d.tab->dq_off_dev, nullptr, d.rows_lap, d.rows_sto, d.nt);
+          d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
       SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
     }
   }

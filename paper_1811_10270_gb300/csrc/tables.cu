@@ -260,6 +260,34 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
         for (int b = 0; b < w; ++b) DTdf[o + b * w + a] = Ddf[o + a * w + b];
     }
     if ((rc = upload_df(ctx, &T.dq_df, Ddf)) || (rc = upload_df(ctx, &T.dqT_df, DTdf))) return rc;
+    // nonzero progressions of every row and column (zeros of the block are exact, the quadrature
+    // leaves rounding noise far below the threshold); a row that is not a progression is dense
+    std::vector<int4> rows((size_t)(p + 1) * (p + 1)), cols((size_t)(p + 1) * (p + 1));
+    auto progression = [](const std::vector<int>& idx, int w) {
+      if (idx.empty()) return make_int4(0, 0, 1, 0);
+      const int step = idx.size() > 1 ? idx[1] - idx[0] : 1;
+      for (size_t k = 1; k < idx.size(); ++k)
+        if (idx[k] - idx[k - 1] != step) return make_int4(0, w, 1, 0);
+      return make_int4(idx[0], (int)idx.size(), step, 0);
+    };
+    for (int n = 0; n <= p; ++n) {
+      const int w = 2 * n + 1, o = T.dq_off[n];
+      for (int a = 0; a < w; ++a) {
+        std::vector<int> r, c;
+        for (int b = 0; b < w; ++b) {
+          if (std::fabs(D[o + a * w + b]) > 1e-12) r.push_back(b);
+          if (std::fabs(D[o + b * w + a]) > 1e-12) c.push_back(b);
+        }
+        rows[(size_t)n * n + a] = progression(r, w);
+        cols[(size_t)n * n + a] = progression(c, w);
+      }
+    }
+    for (auto* pr : {&rows, &cols}) {
+      int4** dst = pr == &rows ? &T.dq_rows : &T.dq_cols;
+      if (cudaMalloc(dst, pr->size() * sizeof(int4)) != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc Dq pattern");
+      if (cudaMemcpy(*dst, pr->data(), pr->size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(ctx, SHBIM_ERR_CUDA, "cudaMemcpy Dq pattern");
+    }
     // cos / sin (m alpha) at the base-grid latitudes and longitudes (the targets' rotation angles)
     std::vector<double> tb, wb;
     gauss_legendre(p + 1, tb, wb);
@@ -325,6 +353,8 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->up_trig_df);
   cudaFree(t->dq_df);
   cudaFree(t->dqT_df);
+  cudaFree(t->dq_rows);
+  cudaFree(t->dq_cols);
   cudaFree(t->dft_digits);
   cudaFree(t->cs_theta_df);
   cudaFree(t->cs_phi_df);
