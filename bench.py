@@ -136,6 +136,7 @@ def run_own(args):
     cfg, f = workload(args.p)
     prec = S.FP32_COMP if args.precision == "fp32comp" else S.FP64
     ctx = S.Context(precision=prec, R=cfg.R, gmres_tol=1e-8, gmres_restart=50)
+    ctx.set_concurrency(not args.serial)
     ps = [d.p for d in cfg.drops]
     lam = [d.lam for d in cfg.drops]
     x_host = np.concatenate([d.xcoef.ravel() for d in cfg.drops])
@@ -675,6 +676,8 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
     ap.add_argument("--only", choices=["pairs_at_scale", "config3", "config5", "peaks"],
                     help="run one measurement leg alone and print its JSON (for profiling)")
+    ap.add_argument("--serial", action="store_true",
+                    help="operator applications on the caller's stream alone (no side-stream branches)")
     ap.add_argument("--profile", action="store_true",
                     help="only the warm-up and timed steps (for launch lists under a profiler)")
     args = ap.parse_args()

@@ -329,9 +329,19 @@ int64_t shbim_launch_count(shbim_ctx* ctx);
 /* CUDA graphs for the operator applications inside GMRES (on by default): for each geometry,
  * system and precision the second application is captured on a stream owned by the library
  * and later ones replay it on the caller's stream, with the Krylov vector copied through fixed
- * staging buffers. Kernel timing (shbim_set_timing) disables the replay while it is on. If a
- * capture fails, the context falls back to direct launches. */
+ * staging buffers. Kernel timing (shbim_set_timing) does not see inside a replay. If a capture
+ * fails, the context falls back to direct launches. */
 int shbim_set_graphs(shbim_ctx* ctx, int on);
+
+/* Concurrent branches inside one operator application (on by default; used with two or more
+ * drops): the singular self rows and the near-field correction run on a second stream owned by
+ * the library while the caller's stream synthesises the source strengths and runs the
+ * all-pairs sums, which are added into the output after the two branches join. The side stream
+ * waits for everything queued earlier on the caller's stream and the caller's stream waits for
+ * the side stream before the call's last kernels, so the call behaves as if it ran on the
+ * caller's stream alone. The order in which the three contributions are added differs from the
+ * serial order (off), which changes results only by rounding. */
+int shbim_set_concurrency(shbim_ctx* ctx, int on);
 
 /* Launch-shape autotuning of the FP32 all-pairs kernels (on by default): on the first launch of
  * each kernel kind for a drop layout, every register blocking (1, 2 or 4 targets per thread)
@@ -379,9 +389,10 @@ int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits);
 int64_t shbim_operator_applications(shbim_ctx* ctx);
 
 /* Kernel timing (measurement support, off by default). When on, the library brackets every
- * launch of the timed kernel classes below with CUDA events on the launching stream.
- * shbim_kernel_stats synchronises the device and returns the summed milliseconds and the
- * number of launches of one class since timing was (re)enabled. */
+ * launch of the timed kernel classes below with CUDA events on the launching stream; launches
+ * inside a replayed CUDA graph (the GMRES operator applications, see shbim_set_graphs) are not
+ * bracketed. shbim_kernel_stats synchronises the device and returns the summed milliseconds and
+ * the number of bracketed launches of one class since timing was (re)enabled. */
 #define SHBIM_K_SELF_WEIGHTS 0      /* rotated-grid synthesis + kernel weights (singular rows) */
 #define SHBIM_K_SELF_ANALYSIS 1     /* analysis of the weights (singular rows) */
 #define SHBIM_K_PAIRS 2             /* all-pairs sums */

@@ -40,7 +40,7 @@ EXPORTS = [
     "shbim_rates", "shbim_step", "shbim_operator_applications", "shbim_set_near", "shbim_near_pairs",
     "shbim_mlp_create", "shbim_mlp_destroy", "shbim_mlp_set_layer", "shbim_mlp_get_layer",
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
-    "shbim_set_graphs", "shbim_laplace_beltrami", "shbim_set_diffusion",
+    "shbim_set_graphs", "shbim_set_concurrency", "shbim_laplace_beltrami", "shbim_set_diffusion",
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
     "shbim_set_outer_precision", "shbim_set_rows_precision", "shbim_set_tensor_cores",
 ]
@@ -122,6 +122,7 @@ def lib():
         "shbim_operator_applications": (i64, [vp]),
         "shbim_set_near": (i32, [vp, i32]),
         "shbim_set_graphs": (i32, [vp, i32]),
+        "shbim_set_concurrency": (i32, [vp, i32]),
         "shbim_set_autotune": (i32, [vp, i32]),
         "shbim_set_outer_precision": (i32, [vp, i32]),
         "shbim_set_rows_precision": (i32, [vp, i32]),
@@ -351,6 +352,11 @@ class Context:
 
     def set_graphs(self, on: bool):
         self._check(self._L.shbim_set_graphs(self._h, 1 if on else 0), "shbim_set_graphs")
+
+    def set_concurrency(self, on: bool):
+        """Run the self rows and near-field correction beside the all-pairs sums on a second
+        library stream (on by default)."""
+        self._check(self._L.shbim_set_concurrency(self._h, 1 if on else 0), "shbim_set_concurrency")
 
     def set_near(self, on: bool):
         self._check(self._L.shbim_set_near(self._h, 1 if on else 0), "shbim_set_near")

@@ -159,6 +159,10 @@ int shbim_destroy(shbim_ctx* ctx) {
     cudaFree(g.out);
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_coarse) cudaEventDestroy(ctx->ev_coarse);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   cudaFree(ctx->phys.buf);
   cudaFree(ctx->phys.grid);
   cudaFree(ctx->phys.state);
@@ -240,6 +244,13 @@ int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits) {
 int shbim_set_graphs(shbim_ctx* ctx, int on) {
   if (!ctx) return SHBIM_ERR_ARG;
   ctx->graphs_on = on != 0;
+  return SHBIM_OK;
+}
+
+int shbim_set_concurrency(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->concurrent = on != 0;
+  ctx->geom_version++;  // captured operator graphs have the other stream layout
   return SHBIM_OK;
 }
 
@@ -384,6 +395,44 @@ int shbim_sht(shbim_ctx* ctx, int drop, int dir, int grid, int n_fields, const d
   return fail(ctx, SHBIM_ERR_ARG, "bad direction");
 }
 
+}  // extern "C"
+
+namespace shbim {
+namespace {
+
+// Streams of one operator application. With two or more drops and concurrency on, the self rows
+// (which overwrite the output values) and then the near-field correction (which adds into them)
+// run on the library's side stream while the caller's stream synthesises the strengths and runs
+// the all-pairs sums; `coarse` marks the strengths as ready for the near-field sums and `join`
+// the side branch as done, before the pair partials are added into the output.
+struct Branches {
+  cudaStream_t side = nullptr;
+  cudaEvent_t coarse = nullptr, join = nullptr;
+};
+
+int fork_branches(shbim_ctx* ctx, cudaStream_t s, Branches* br) {
+  br->side = s;
+  if (ctx->n_drops < 2 || !ctx->concurrent) return SHBIM_OK;
+  if (!ctx->side) {
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_coarse, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(ctx, cudaGetLastError(), "side stream");
+  }
+  SHBIM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+  SHBIM_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  br->side = ctx->side;
+  br->coarse = ctx->ev_coarse;
+  br->join = ctx->ev_join;
+  return SHBIM_OK;
+}
+
+}  // namespace
+}  // namespace shbim
+
+extern "C" {
+
 int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, double* out_dev, int out_kind,
                         void* stream) {
   if (!ctx) return SHBIM_ERR_ARG;
@@ -396,6 +445,13 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
   int rc;
   ctx->applications++;
+  double* vals = out_kind == SHBIM_OUT_GRID ? out_dev : ctx->grid_out;
+  Branches br;
+  if ((rc = fork_branches(ctx, s, &br))) return rc;
+  {
+    TimeScope ts(ctx, SHBIM_K_SELF_GEMV, br.side);
+    if ((rc = apply_self_laplace(ctx, which, dens_dev, vals, br.side))) return rc;
+  }
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {
@@ -406,16 +462,13 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
       if (rc) return rc;
     }
   }
-  double* vals = out_kind == SHBIM_OUT_GRID ? out_dev : ctx->grid_out;
-  {
-    TimeScope ts(ctx, SHBIM_K_SELF_GEMV, s);
-    if ((rc = apply_self_laplace(ctx, which, dens_dev, vals, s))) return rc;
-  }
+  if (br.coarse) SHBIM_CUDA(ctx, cudaEventRecord(br.coarse, s));
+  if ((rc = apply_near_laplace(ctx, which, dens_dev, vals, br.side, br.coarse))) return rc;
+  if (br.join) SHBIM_CUDA(ctx, cudaEventRecord(br.join, br.side));
   {
     TimeScope ts(ctx, SHBIM_K_PAIRS, s);
-    if ((rc = pairs_laplace(ctx, which, vals, s))) return rc;
+    if ((rc = pairs_laplace(ctx, which, vals, s, br.join))) return rc;
   }
-  if ((rc = apply_near_laplace(ctx, which, dens_dev, vals, s))) return rc;
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {
@@ -439,6 +492,13 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   const int64_t NS = ctx->nsource;
   int rc;
   ctx->applications++;
+  double* vals = out_kind == SHBIM_OUT_GRID ? out_dev : ctx->grid_out;
+  Branches br;
+  if ((rc = fork_branches(ctx, s, &br))) return rc;
+  {
+    TimeScope ts(ctx, SHBIM_K_SELF_GEMV, br.side);
+    if ((rc = apply_self_stokes(ctx, f_dev, u_dev, vals, br.side))) return rc;
+  }
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {
@@ -458,16 +518,13 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
       }
     }
   }
-  double* vals = out_kind == SHBIM_OUT_GRID ? out_dev : ctx->grid_out;
-  {
-    TimeScope ts(ctx, SHBIM_K_SELF_GEMV, s);
-    if ((rc = apply_self_stokes(ctx, f_dev, u_dev, vals, s))) return rc;
-  }
+  if (br.coarse) SHBIM_CUDA(ctx, cudaEventRecord(br.coarse, s));
+  if ((rc = apply_near_stokes(ctx, f_dev, u_dev, vals, br.side, br.coarse))) return rc;
+  if (br.join) SHBIM_CUDA(ctx, cudaEventRecord(br.join, br.side));
   {
     TimeScope ts(ctx, SHBIM_K_PAIRS, s);
-    if ((rc = pairs_stokes(ctx, f_dev != nullptr, u_dev != nullptr, vals, s))) return rc;
+    if ((rc = pairs_stokes(ctx, f_dev != nullptr, u_dev != nullptr, vals, s, br.join))) return rc;
   }
-  if ((rc = apply_near_stokes(ctx, f_dev, u_dev, vals, s))) return rc;
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
     for (auto& d : ctx->drops) {
@@ -487,6 +544,9 @@ namespace shbim {
 
 TimeScope::TimeScope(shbim_ctx* c, int k, cudaStream_t st) : ctx(c), cls(k), s(st) {
   if (!ctx->timing) return;
+  // launches being captured into a graph are not timed (their replays run as one graph launch)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   cudaEvent_t a;
   if (ctx->event_pool.empty()) {
     cudaEventCreate(&a);

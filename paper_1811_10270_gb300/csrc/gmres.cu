@@ -167,7 +167,7 @@ int matvec_eager(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
 // through fixed staging buffers) and later ones replay the graph on the caller's stream.
 int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
   auto& G = ctx->gm;
-  if (!ctx->graphs_on || ctx->timing) return matvec_eager(ctx, v, out, s);
+  if (!ctx->graphs_on) return matvec_eager(ctx, v, out, s);
   auto& GR = ctx->graphs[G.sys * 3 + ctx->opts.precision];
   if (GR.version != ctx->geom_version || GR.n != G.n) {
     if (GR.exec) cudaGraphExecDestroy(GR.exec);

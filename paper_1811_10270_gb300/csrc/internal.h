@@ -72,6 +72,10 @@ struct DegreeTables {
   // [n tile][K step][digit][80 outputs x 16 longitudes, K-major canonical layout], bfloat16
   uint16_t* dft_digits = nullptr;
   int dft_ntiles = 0, dft_ksteps = 0;
+  // digit planes of Dq_n and Dq_n^T for the tensor-core rotations (rot_tc.cu), p <= 39:
+  // [2][p+1][K step][digit][Np x 16], with per-(g, n) offsets in 16-byte units
+  uint16_t* rot_digits = nullptr;
+  int* rot_toff = nullptr;
 };
 
 struct Drop {
@@ -150,6 +154,7 @@ struct shbim_ctx {
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
   bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
+  bool tc_rot = false;            // ... and the degree-block rotations (rot_tc.cu)
   int* tc_err = nullptr;          // device flag: a tensor-core kernel timed out
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
@@ -231,6 +236,11 @@ struct shbim_ctx {
   bool graphs_on = true;
   int64_t geom_version = 0;
   cudaStream_t cap_stream = nullptr;
+  // second library stream for the concurrent branches of an operator application (self rows
+  // and near-field correction beside the all-pairs sums), with its fork/join events
+  bool concurrent = true;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_coarse = nullptr, ev_join = nullptr;
   struct MatvecGraph {
     cudaGraphExec_t exec = nullptr;
     double* in = nullptr;
@@ -315,8 +325,10 @@ int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* 
 
 // ---- nearly-singular correction (near.cu)
 int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s);
-int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
-int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s);
+int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s,
+                       cudaEvent_t before_sums = nullptr);
+int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s,
+                      cudaEvent_t before_sums = nullptr);
 // geometry (x, n, w = omega J) of a grid from its synthesised x, x_theta, x_phi/sin (singular.cu)
 int geometry_kernel(shbim_ctx* ctx, const double* buf, int64_t n, int nkind, const GridTables& g, double* out,
                     int64_t ld, int64_t off, cudaStream_t s);
@@ -330,6 +342,11 @@ int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream
 // ---- tensor-core Fourier analysis of double-float rows (dft_tc.cu)
 // F[r][cs][m] = sum_k W[r][k] (cos|sin)(m phi_k), r < rows, on drop d's degree 2p+1 grid; W and F
 // double-float (float2), W rows of 2q+2 values, F rows of 2(p+1) values.
+bool rot_tc_fits(int p);
+int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, DegreeTables& T);
+int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2* vin, int64_t in_stride, int nc,
+              int t_begin, int ct, int ncomp, float2* vout, float* rows_lap, float* rows_sto, int nt_drop,
+              cudaStream_t s);
 int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T);
 // the kernel holds a 128-row tile of W in shared memory: degrees up to 34
 bool dft_tc_fits(int p);
@@ -340,8 +357,11 @@ int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, 
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 
 // ---- all-pairs sums (pairs.cu)
-int pairs_laplace(shbim_ctx* ctx, int which, double* out_accum, cudaStream_t s);
-int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out_accum, cudaStream_t s);
+// the sums go to partial buffers; `before_reduce` (optional) is waited for before they are
+// added into out_accum
+int pairs_laplace(shbim_ctx* ctx, int which, double* out_accum, cudaStream_t s, cudaEvent_t before_reduce = nullptr);
+int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out_accum, cudaStream_t s,
+                 cudaEvent_t before_reduce = nullptr);
 
 
 }  // namespace shbim

@@ -707,7 +707,8 @@ int launch_direct(shbim_ctx* ctx, int kind, bool has_f, bool has_u, double* out,
 
 }  // namespace
 
-int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s) {
+int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s,
+                       cudaEvent_t before_sums) {
   auto& N = ctx->near;
   if (N.npairs == 0) return SHBIM_OK;
   const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
@@ -721,10 +722,12 @@ int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* ou
                               lo ? N.fstr32lo + o : nullptr);
     if (rc) return rc;
   }
+  if (before_sums) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_sums, 0));
   return launch_direct(ctx, which == SHBIM_LAPLACE_SL ? 1 : 0, false, false, out, s);
 }
 
-int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s) {
+int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out, cudaStream_t s,
+                      cudaEvent_t before_sums) {
   auto& N = ctx->near;
   if (N.npairs == 0) return SHBIM_OK;
   const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
@@ -743,6 +746,7 @@ int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* 
                                     s, lo ? N.fstr32lo + 3 * N.nfine + o : nullptr)))
       return rc;
   }
+  if (before_sums) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_sums, 0));
   return launch_direct(ctx, 2, f != nullptr, u != nullptr, out, s);
 }
 

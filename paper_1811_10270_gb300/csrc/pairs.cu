@@ -480,9 +480,12 @@ int autotune(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
 }
 
 template <int KIND>
-int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s) {
+int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
   constexpr int NC = (KIND == STO) ? 3 : 1;
-  if (ctx->n_drops < 2 || ctx->tiles.empty()) return SHBIM_OK;
+  if (ctx->n_drops < 2 || ctx->tiles.empty()) {
+    if (before_reduce) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_reduce, 0));
+    return SHBIM_OK;
+  }
   auto& C = ctx->pair_cfg[KIND];
   if (!C.tuned) {
     int rc = autotune<KIND>(ctx, has_f, has_u, s);
@@ -495,6 +498,7 @@ int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
   const int splits = fp32 ? C.splits : ctx->pair_splits;
   launch_raw<KIND>(ctx, has_f, has_u, tpt, splits, s);
   SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
+  if (before_reduce) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_reduce, 0));
   const int64_t n = NC * ctx->ntarget;
   k_reduce_parts<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->part, splits, n, out);
   SHBIM_CHECK_LAUNCH(ctx, "k_reduce_parts");
@@ -503,13 +507,13 @@ int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
 
 }  // namespace
 
-int pairs_laplace(shbim_ctx* ctx, int which, double* out, cudaStream_t s) {
-  return which == SHBIM_LAPLACE_SL ? launch_pairs<LSL>(ctx, false, false, out, s)
-                                   : launch_pairs<LDL>(ctx, false, false, out, s);
+int pairs_laplace(shbim_ctx* ctx, int which, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
+  return which == SHBIM_LAPLACE_SL ? launch_pairs<LSL>(ctx, false, false, out, s, before_reduce)
+                                   : launch_pairs<LDL>(ctx, false, false, out, s, before_reduce);
 }
 
-int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s) {
-  return launch_pairs<STO>(ctx, has_f, has_u, out, s);
+int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
+  return launch_pairs<STO>(ctx, has_f, has_u, out, s, before_reduce);
 }
 
 int pairs_tile_targets() { return kTileTargets; }

@@ -298,10 +298,11 @@ __global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, 
   }
   const float2* T = alf + (int64_t)j * 3 * nt;
   const float2* cf = rot + (int64_t)t * 3 * nc;
+  // order m-major, so that the 32 lanes of a warp hold sums of (nearly) equal length p + 1 - m
   for (int task = threadIdx.x; task < 18 * P1; task += blockDim.x) {
-    const int fk = task / (2 * P1);
-    const int r = task - fk * 2 * P1;
-    const int m = r >> 1;
+    const int m = task / 18;
+    const int r = task - m * 18;
+    const int fk = r >> 1;
     const int cs = r & 1;
     const int f = fk / 3, kind = fk - f * 3;
     dfl::acc acc;
@@ -558,10 +559,13 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int rows = std::max(1, std::min(8, budget / (2 * N)));
     const size_t f_smem = (size_t)(2 * N + rows * 2 * N) * sizeof(float2);
     const int nt = (d.p + 1) * (d.p + 2) / 2;
+    const bool rot_tc = ctx->tc_rows && ctx->tc_rot && rot_tc_fits(d.p);
     for (int t0 = 0; t0 < d.nt; t0 += CT) {
       const int ct = std::min(CT, d.nt - t0);
-      {
-        // the position coefficients are the same for every target: zero input stride
+      // the position coefficients are the same for every target: zero input stride
+      if (rot_tc) {
+        if ((rc = rotate_tc(ctx, *d.tab, false, xc, 0, nc, t0, ct, 3, rot, nullptr, nullptr, d.nt, s))) return rc;
+      } else {
         k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, s>>>(
             xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
             d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
@@ -586,10 +590,16 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
         SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
       }
-      k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
-          vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df,
-          d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
-      SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+      if (rot_tc) {
+        if ((rc = rotate_tc(ctx, *d.tab, true, vb, (int64_t)ncomp * nc, nc, t0, ct, ncomp, nullptr, d.rows_lap,
+                            d.rows_sto, d.nt, s)))
+          return rc;
+      } else {
+        k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
+            vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df,
+            d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
+        SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+      }
     }
   }
   if (ctx->tc_rows && ctx->tc_err) {
@@ -598,7 +608,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
     if (flag) {
       SHBIM_CUDA(ctx, cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s));
-      return fail(ctx, SHBIM_ERR_CUDA, "tensor-core Fourier analysis: a bounded wait expired");
+      return fail(ctx, SHBIM_ERR_CUDA, "tensor-core row build: a bounded wait expired");
     }
   }
   return SHBIM_OK;

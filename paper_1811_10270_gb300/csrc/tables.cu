@@ -251,6 +251,7 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
   }
   int rc = upload(ctx, &T.dq, D);
   if (rc) return rc;
+  if ((rc = rot_tc_digits(ctx, p, D, T))) return rc;
   {
     std::vector<float2> Ddf(D.size()), DTdf(D.size());
     for (size_t i = 0; i < D.size(); ++i) Ddf[i] = split_df(D[i]);
@@ -356,6 +357,8 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->dq_rows);
   cudaFree(t->dq_cols);
   cudaFree(t->dft_digits);
+  cudaFree(t->rot_digits);
+  cudaFree(t->rot_toff);
   cudaFree(t->cs_theta_df);
   cudaFree(t->cs_phi_df);
   delete t;

@@ -506,3 +506,44 @@ def test_graph_replay_matches_direct_launches(S):
         for a, b in zip(out[(False, precision)], out[(True, precision)]):
             assert a[0] == b[0] and a[1] == b[1]
             assert rel_err(b[2], a[2]) < 1e-10 and rel_err(b[3], a[3]) < 1e-10
+
+
+def test_concurrent_branches_match_serial_order(S):
+    """Two drops 0.1 apart (near pairs exist): with the self rows and the near-field correction
+    on the library's second stream, every operator and a graph-replayed GMRES solve give the
+    serial results up to the rounding of the changed summation order."""
+    cfg = _two_drop_cfg(8, seed=2, gap=0.1)
+    rng = np.random.default_rng(11)
+    sig = T(np.concatenate([inputs.random_density(8, rng)[0] for _ in cfg.drops]))
+    F = T(np.concatenate([inputs.random_density(8, rng, 3).ravel() for _ in cfg.drops]))
+    for precision in (S.FP64, S.FP32_COMP, S.DF64):
+        res = {}
+        for conc in (False, True):
+            ctx = make(S, cfg.drops, precision, cfg.R)
+            assert ctx.near_pairs() > 0
+            ctx.set_autotune(False)
+            ctx.set_concurrency(conc)
+            outs = []
+            for which in (S.LAPLACE_DL, S.LAPLACE_SL):
+                out = torch.empty(sig.numel(), device=DEV, dtype=torch.float64)
+                ctx.eval_electric(which, sig, out, S.OUT_COEF)
+                outs.append(out.cpu().numpy())
+            for f, u in ((F, None), (None, F), (F, F)):
+                out = torch.empty(F.numel(), device=DEV, dtype=torch.float64)
+                ctx.eval_stokes(f, u, out, S.OUT_COEF)
+                outs.append(out.cpu().numpy())
+            ctx.close()
+            # GMRES with graph replay of the forked application (FP32: to its own accuracy)
+            ctx = S.Context(precision=precision, R=cfg.R, gmres_tol=1e-5 if precision == S.FP32_COMP else 1e-10)
+            ctx.set_autotune(False)
+            ctx.set_concurrency(conc)
+            ctx.set_drops([d.p for d in cfg.drops], T(np.concatenate([d.xcoef.ravel() for d in cfg.drops])),
+                          [d.lam for d in cfg.drops])
+            xs = torch.empty_like(F)
+            its, _ = ctx.gmres_solve(S.SYS_STOKES, F, xs)
+            outs.append(xs.cpu().numpy())
+            res[conc] = (outs, its)
+            ctx.close()
+        assert res[False][1] == res[True][1], precision
+        for a, b in zip(res[False][0], res[True][0]):
+            assert rel_err(b, a) < 1e-12, precision
