@@ -192,7 +192,8 @@ def run_own(args):
     cls_ms = {}
     cls_n = {}
     names = {S.K_SELF_WEIGHTS: "self_weights", S.K_SELF_ANALYSIS: "self_analysis",
-             S.K_PAIRS: "pairs", S.K_SELF_GEMV: "self_gemv", S.K_SHT: "sht"}
+             S.K_PAIRS: "pairs", S.K_SELF_GEMV: "self_gemv", S.K_SHT: "sht",
+             S.K_SELF_ROTATION: "self_rotation"}
     for k, nm in names.items():
         cls_ms[nm], cls_n[nm] = ctx.kernel_stats(k)
     ctx.set_timing(False)

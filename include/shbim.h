@@ -356,10 +356,16 @@ int shbim_set_autotune(shbim_ctx* ctx, int on);
  * SHBIM_PREC_FP64 (native). SHBIM_ERR_ARG otherwise. */
 int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
 
-/* Fourier stage of the double-float row build on the tensor cores (on by default): the GEMM of
- * the rows' weights with the DFT table split into bfloat16 digits whose products accumulate exactly
- * (error ~2^-42 of the sum of magnitudes per output). Off: the double-float FP32-pipe kernel. */
-int shbim_set_tensor_cores(shbim_ctx* ctx, int on);
+/* Tensor-core stages of the double-float row build (at the next shbim_set_drops), a bit mask:
+ * SHBIM_TC_FOURIER, the GEMM of the rows' weights with the DFT table; SHBIM_TC_ROTATION, the
+ * products with the quarter-turn blocks Dq_n in the pole rotations (degree p <= 39). Both split
+ * their operands into bfloat16 digits whose products accumulate exactly (error ~2^-42 of the sum
+ * of magnitudes per output). A stage that is off, or does not fit, runs as the double-float
+ * FP32-pipe kernel. Default SHBIM_TC_ALL; any other bit is SHBIM_ERR_ARG. */
+#define SHBIM_TC_FOURIER 1
+#define SHBIM_TC_ROTATION 2
+#define SHBIM_TC_ALL 3
+int shbim_set_tensor_cores(shbim_ctx* ctx, int mask);
 
 /* Pipe throughput probes (a measurement utility for roofline denominators; the paper has no
  * counterpart). Launches 4 CTAs of 256 threads per SM on the current device, each thread running
@@ -384,6 +390,16 @@ int shbim_probe_peak(int kind, int64_t iters, double* ops_per_s_host, double* ms
 int shbim_pair_shape(shbim_ctx* ctx, int kind, int* tpt_host, int* splits_host);
 int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits);
 
+/* Launch form of the FP32 all-pairs kernel of one kind: one CTA per work unit (a sub-tile of up to
+ * 512 targets of one drop x one source split; 0) or persistent CTAs, as many as are resident,
+ * taking units from an atomic counter in the order of the tile list, largest work first (1).
+ * Autotuning tries both. shbim_pair_queue returns the form (or an error code);
+ * shbim_set_pair_queue fixes it, like shbim_set_pair_shape. The counter lives in the context and
+ * is back at zero after every launch, so launches of one context must not overlap on the GPU
+ * (the library queues them on one stream). */
+int shbim_pair_queue(shbim_ctx* ctx, int kind);
+int shbim_set_pair_queue(shbim_ctx* ctx, int kind, int on);
+
 /* Number of layer-operator applications (calls of the electric or Stokes operator, including
  * those made inside GMRES and the time step) since the context was created. */
 int64_t shbim_operator_applications(shbim_ctx* ctx);
@@ -398,7 +414,8 @@ int64_t shbim_operator_applications(shbim_ctx* ctx);
 #define SHBIM_K_PAIRS 2             /* all-pairs sums */
 #define SHBIM_K_SELF_GEMV 3         /* application of the singular rows */
 #define SHBIM_K_SHT 4               /* transforms of densities and outputs */
-#define SHBIM_K_COUNT 5
+#define SHBIM_K_SELF_ROTATION 5     /* pole rotations of the singular-row build */
+#define SHBIM_K_COUNT 6
 int shbim_set_timing(shbim_ctx* ctx, int on);
 int shbim_kernel_stats(shbim_ctx* ctx, int kernel_class, double* ms_host, int64_t* launches_host);
 

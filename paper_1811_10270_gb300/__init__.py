@@ -28,6 +28,9 @@ GRID_UP = 1
 SYS_ELECTRIC = 0
 SYS_STOKES = 1
 SYS_DIFFUSION = 2
+TC_FOURIER = 1
+TC_ROTATION = 2
+TC_ALL = 3
 CONTINUE = 0
 CONVERGED = 1
 
@@ -40,7 +43,7 @@ EXPORTS = [
     "shbim_rates", "shbim_step", "shbim_operator_applications", "shbim_set_near", "shbim_near_pairs",
     "shbim_mlp_create", "shbim_mlp_destroy", "shbim_mlp_set_layer", "shbim_mlp_get_layer",
     "shbim_mlp_forward", "shbim_mlp_train_step", "shbim_electric_warm_start", "shbim_mlp_set_input_affine",
-    "shbim_set_graphs", "shbim_set_concurrency", "shbim_laplace_beltrami", "shbim_set_diffusion",
+    "shbim_set_graphs", "shbim_set_concurrency", "shbim_pair_queue", "shbim_set_pair_queue", "shbim_laplace_beltrami", "shbim_set_diffusion",
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
     "shbim_set_outer_precision", "shbim_set_rows_precision", "shbim_set_tensor_cores",
 ]
@@ -55,7 +58,8 @@ K_SELF_ANALYSIS = 1
 K_PAIRS = 2
 K_SELF_GEMV = 3
 K_SHT = 4
-K_COUNT = 5
+K_SELF_ROTATION = 5
+K_COUNT = 6
 
 
 class ShbimError(RuntimeError):
@@ -123,6 +127,8 @@ def lib():
         "shbim_set_near": (i32, [vp, i32]),
         "shbim_set_graphs": (i32, [vp, i32]),
         "shbim_set_concurrency": (i32, [vp, i32]),
+        "shbim_pair_queue": (i32, [vp, i32]),
+        "shbim_set_pair_queue": (i32, [vp, i32, i32]),
         "shbim_set_autotune": (i32, [vp, i32]),
         "shbim_set_outer_precision": (i32, [vp, i32]),
         "shbim_set_rows_precision": (i32, [vp, i32]),
@@ -331,8 +337,11 @@ class Context:
     def set_rows_precision(self, precision: int):
         self._check(self._L.shbim_set_rows_precision(self._h, int(precision)), "shbim_set_rows_precision")
 
-    def set_tensor_cores(self, on: bool):
-        self._check(self._L.shbim_set_tensor_cores(self._h, 1 if on else 0), "shbim_set_tensor_cores")
+    def set_tensor_cores(self, on):
+        """Tensor-core stages of the row build: True (all), False (none) or a mask of TC_FOURIER
+        and TC_ROTATION."""
+        mask = (TC_ALL if on else 0) if isinstance(on, bool) else int(on)
+        self._check(self._L.shbim_set_tensor_cores(self._h, mask), "shbim_set_tensor_cores")
 
     def set_autotune(self, on: bool):
         self._check(self._L.shbim_set_autotune(self._h, 1 if on else 0), "shbim_set_autotune")
@@ -349,6 +358,16 @@ class Context:
     def set_pair_shape(self, kind: int, tpt: int, splits: int):
         self._check(self._L.shbim_set_pair_shape(self._h, int(kind), int(tpt), int(splits)),
                     "shbim_set_pair_shape")
+
+    def pair_queue(self, kind: int) -> bool:
+        """True when the FP32 pair kernel `kind` runs as persistent CTAs on a work counter."""
+        rc = self._L.shbim_pair_queue(self._h, int(kind))
+        if rc < 0:
+            self._check(rc, "shbim_pair_queue")
+        return rc == 1
+
+    def set_pair_queue(self, kind: int, on: bool):
+        self._check(self._L.shbim_set_pair_queue(self._h, int(kind), 1 if on else 0), "shbim_set_pair_queue")
 
     def set_graphs(self, on: bool):
         self._check(self._L.shbim_set_graphs(self._h, 1 if on else 0), "shbim_set_graphs")

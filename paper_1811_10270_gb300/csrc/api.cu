@@ -159,6 +159,7 @@ int shbim_destroy(shbim_ctx* ctx) {
     cudaFree(g.out);
   }
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  cudaFree(ctx->pair_queue);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_coarse) cudaEventDestroy(ctx->ev_coarse);
@@ -208,9 +209,11 @@ int shbim_set_rows_precision(shbim_ctx* ctx, int precision) {
   return SHBIM_OK;
 }
 
-int shbim_set_tensor_cores(shbim_ctx* ctx, int on) {
+int shbim_set_tensor_cores(shbim_ctx* ctx, int mask) {
   if (!ctx) return SHBIM_ERR_ARG;
-  ctx->tc_rows = on != 0;
+  if (mask & ~SHBIM_TC_ALL) return fail(ctx, SHBIM_ERR_ARG, "unknown tensor-core stage bit");
+  ctx->tc_rows = (mask & SHBIM_TC_FOURIER) != 0;
+  ctx->tc_rot = (mask & SHBIM_TC_ROTATION) != 0;
   return SHBIM_OK;
 }
 
@@ -236,7 +239,23 @@ int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits) {
   if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
   if (tpt != 1 && tpt != 2 && tpt != 4) return fail(ctx, SHBIM_ERR_ARG, "targets per thread must be 1, 2 or 4");
   if (splits < 1 || splits > ctx->split_max) return fail(ctx, SHBIM_ERR_ARG, "split count out of range");
-  ctx->pair_cfg[kind] = shbim_ctx::PairCfg{tpt, splits, true};
+  ctx->pair_cfg[kind] = shbim_ctx::PairCfg{tpt, splits, true, ctx->pair_cfg[kind].queue};
+  ctx->geom_version++;
+  return SHBIM_OK;
+}
+
+int shbim_pair_queue(shbim_ctx* ctx, int kind) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  return ctx->pair_cfg[kind].queue ? 1 : 0;
+}
+
+int shbim_set_pair_queue(shbim_ctx* ctx, int kind, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  ctx->pair_cfg[kind].queue = on != 0;
+  ctx->pair_cfg[kind].tuned = true;
   ctx->geom_version++;
   return SHBIM_OK;
 }
@@ -350,6 +369,11 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
         ctx->tiles.push_back(PairTile{i, (int)(d.tgt_off + t0), std::min(TT, d.nt - t0)});
       min_other = std::min<int64_t>(min_other, so - d.ns);
     }
+    // largest work first (targets x other drops' sources): the grid's first CTAs and the
+    // persistent form's first units take the longest tiles
+    std::stable_sort(ctx->tiles.begin(), ctx->tiles.end(), [&](const PairTile& a, const PairTile& b) {
+      return (int64_t)a.nt * (so - ctx->drops[a.drop].ns) > (int64_t)b.nt * (so - ctx->drops[b.drop].ns);
+    });
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -367,6 +391,10 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
     ctx->pair_splits = std::min(ctx->pair_splits, ctx->split_max);
     for (auto& c : ctx->pair_cfg) c = shbim_ctx::PairCfg{1, ctx->pair_splits, !ctx->autotune};
     if ((rc = dalloc(ctx, &ctx->part, (size_t)ctx->split_max * 3 * to, "pair partials"))) return rc;
+    if (!ctx->pair_queue) {
+      if ((rc = dalloc(ctx, &ctx->pair_queue, 2, "pair work counter"))) return rc;
+      SHBIM_CUDA(ctx, cudaMemset(ctx->pair_queue, 0, 2 * sizeof(int)));
+    }
   }
   return rebuild_geometry(ctx, xcoef_dev, s);
 }

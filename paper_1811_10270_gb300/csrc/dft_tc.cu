@@ -157,7 +157,9 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
         break;
       }
     }
-    // per-row power-of-two scale, max |hi| < 2^e: warp w scans rows 16 w .. 16 w + 15
+    // per-row power-of-two scale, max |hi| < 2^e: warp w scans rows 16 w .. 16 w + 15 (four rows'
+    // reductions interleaved)
+#pragma unroll 4
     for (int rr = 0; rr < kMT / (kThreadsTC / 32); ++rr) {
       const int rl = warp * (kMT / (kThreadsTC / 32)) + rr;
       float mx = 0.f;

@@ -72,10 +72,12 @@ struct DegreeTables {
   // [n tile][K step][digit][80 outputs x 16 longitudes, K-major canonical layout], bfloat16
   uint16_t* dft_digits = nullptr;
   int dft_ntiles = 0, dft_ksteps = 0;
-  // digit planes of Dq_n and Dq_n^T for the tensor-core rotations (rot_tc.cu), p <= 39:
-  // [2][p+1][K step][digit][Np x 16], with per-(g, n) offsets in 16-byte units
+  // digit planes of Dq_n^T Dz(-+theta_j) Dq_n per base-grid latitude for the tensor-core rotations
+  // (rot_tc.cu), p <= 39: [2][p+1][p+1][K step][digit][Np x 16], with per-(direction, latitude,
+  // degree) offsets in 16-byte units
   uint16_t* rot_digits = nullptr;
   int* rot_toff = nullptr;
+  signed char* rot_exp = nullptr;   // [2][p+1][(p+1)^2] row exponents of the tables
 };
 
 struct Drop {
@@ -145,7 +147,9 @@ struct shbim_ctx {
     int tpt = 1;
     int splits = 1;
     bool tuned = false;
+    bool queue = false;           // persistent CTAs on an atomic work counter
   } pair_cfg[3];
+  int* pair_queue = nullptr;      // [2] work counter and finished-CTA count (zero between launches)
   bool autotune = true;           // off: every layout keeps the default launch shape
   double* xdf = nullptr;          // position coefficients of one drop as double-float (row build)
   size_t xdf_cap = 0;
@@ -154,7 +158,7 @@ struct shbim_ctx {
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
   bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
-  bool tc_rot = false;            // ... and the degree-block rotations (rot_tc.cu)
+  bool tc_rot = true;             // ... and the degree-block rotations (rot_tc.cu)
   int* tc_err = nullptr;          // device flag: a tensor-core kernel timed out
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
@@ -343,7 +347,8 @@ int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream
 // F[r][cs][m] = sum_k W[r][k] (cos|sin)(m phi_k), r < rows, on drop d's degree 2p+1 grid; W and F
 // double-float (float2), W rows of 2q+2 values, F rows of 2(p+1) values.
 bool rot_tc_fits(int p);
-int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, DegreeTables& T);
+int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, const std::vector<double>& theta,
+                  DegreeTables& T);
 int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2* vin, int64_t in_stride, int nc,
               int t_begin, int ct, int ncomp, float2* vout, float* rows_lap, float* rows_sto, int nt_drop,
               cudaStream_t s);

@@ -7,8 +7,9 @@
 // 128 threads x TPT targets of a tile (register blocking, TPT = 1, 2 or 4, so a tile takes 4/TPT
 // CTAs) and one split of the other drops' sources; sources are staged through shared memory in
 // tiles of 256 and read as warp-wide broadcasts. Each split writes its own partial sums; a second
-// kernel adds the splits in a fixed order (deterministic). TPT and the split count are chosen per
-// kernel kind and drop layout by timing the candidates on the first FP32 launch (autotune).
+// kernel adds the splits in a fixed order (deterministic). TPT, the split count and the launch
+// form (a CTA per unit, or persistent CTAs on an atomic work counter) are chosen per kernel kind
+// and drop layout by timing the candidates on the first FP32 launch (autotune).
 //
 // Double-float path (FP64-class accuracy on the FP32 pipe): every source coordinate, normal and
 // strength is the pair (FP32 copy, FP32 low part of the FP64 value), the target offset from the
@@ -62,36 +63,37 @@ __device__ __forceinline__ SrcRange drop_range(const DropDev& Di, const DropDev&
   return r;
 }
 
-// blockIdx.x = tile * (kMaxTPT / TPT) + sub-tile; returns false for a sub-tile past the tile's
-// last target (the whole CTA then exits before any barrier)
+// bx = tile * (kMaxTPT / TPT) + sub-tile; returns false for a sub-tile past the tile's last
+// target (the whole CTA then skips it, before any barrier)
 template <int TPT>
-__device__ __forceinline__ bool sub_tile(const PairTile* __restrict__ tiles, PairTile& t) {
+__device__ __forceinline__ bool sub_tile(const PairTile* __restrict__ tiles, PairTile& t, int bx) {
   constexpr int SUB = kMaxTPT / TPT;
-  const PairTile tile = tiles[blockIdx.x / SUB];
-  const int off = (int)(blockIdx.x % SUB) * kThreads * TPT;
+  const PairTile tile = tiles[bx / SUB];
+  const int off = (int)(bx % SUB) * kThreads * TPT;
   t.drop = tile.drop;
   t.t0 = tile.t0 + off;
   t.nt = tile.nt - off;
   return t.nt > 0;
 }
 
+// One work unit of the FP32 sums: sub-tile bx of the tile list, source split by. Returns at once
+// (uniformly for the CTA) for an empty sub-tile.
 template <int KIND, int kTPT>
-__global__ void __launch_bounds__(kThreads)
-k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
-          const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ src32,
-          int64_t nsource, const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
-          double* __restrict__ part) {
+__device__ __forceinline__ void pairs32_unit(int bx, int by, const PairTile* __restrict__ tiles,
+                                             const DropDev* __restrict__ drops, int n_drops,
+                                             const double* __restrict__ tgt, int64_t ntarget,
+                                             const float* __restrict__ src32, int64_t nsource,
+                                             const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
+                                             double* __restrict__ part, float4* __restrict__ sh0,
+                                             float4* __restrict__ sh1, float4* __restrict__ sh2) {
   constexpr int NC = (KIND == STO) ? 3 : 1;
-  __shared__ float4 sh0[kTile];
-  __shared__ float4 sh1[KIND == STO ? kTile : 1];
-  __shared__ float4 sh2[KIND == STO ? kTile : 1];
   PairTile tile;
-  if (!sub_tile<kTPT>(tiles, tile)) return;
+  if (!sub_tile<kTPT>(tiles, tile, bx)) return;
   const int i = tile.drop;
   const DropDev Di = drops[i];
   const int64_t other = nsource - Di.ns;
   const int64_t chunk = (other + nsplit - 1) / nsplit;
-  const int64_t v0 = (int64_t)blockIdx.y * chunk;
+  const int64_t v0 = (int64_t)by * chunk;
   const int64_t v1 = min(other, v0 + chunk);
 
   int64_t tg[kTPT];
@@ -205,7 +207,7 @@ k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
         for (int c = 0; c < NC; ++c) two_sum_acc(hi[k][c], lo[k][c], acc[k][c]);
     }
   }
-  double* P = part + (int64_t)blockIdx.y * NC * ntarget;
+  double* P = part + (int64_t)by * NC * ntarget;
 #pragma unroll
   for (int k = 0; k < kTPT; ++k) {
     if (!ok[k]) continue;
@@ -214,6 +216,52 @@ k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
       const double v = 0.07957747154594766788 * ((double)hi[k][c] + (double)lo[k][c]);
       const int64_t o = (NC == 1) ? tg[k] : 3 * Di.tgt_off + (int64_t)c * Di.nt + (tg[k] - Di.tgt_off);
       P[o] = v;
+    }
+  }
+}
+
+// one CTA per work unit (grid = sub-tiles x splits)
+template <int KIND, int kTPT>
+__global__ void __launch_bounds__(kThreads)
+k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
+          const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ src32,
+          int64_t nsource, const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
+          double* __restrict__ part) {
+  __shared__ float4 sh0[kTile];
+  __shared__ float4 sh1[KIND == STO ? kTile : 1];
+  __shared__ float4 sh2[KIND == STO ? kTile : 1];
+  pairs32_unit<KIND, kTPT>(blockIdx.x, blockIdx.y, tiles, drops, n_drops, tgt, ntarget, src32, nsource, dens32,
+                           nsplit, has_f, has_u, part, sh0, sh1, sh2);
+}
+
+// Persistent form: resident CTAs take work units from an atomic counter, in the order of the tile
+// list (sorted by cost, largest first), splits of a sub-tile consecutively. The last CTA to
+// finish puts the counter back to zero for the next launch on the stream. No CTA waits on another.
+template <int KIND, int kTPT>
+__global__ void __launch_bounds__(kThreads)
+k_pairs32_queue(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
+                const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ src32,
+                int64_t nsource, const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
+                double* __restrict__ part, int nunits, int* __restrict__ queue) {
+  __shared__ float4 sh0[kTile];
+  __shared__ float4 sh1[KIND == STO ? kTile : 1];
+  __shared__ float4 sh2[KIND == STO ? kTile : 1];
+  __shared__ int s_unit;
+  for (;;) {
+    __syncthreads();   // every thread is done with the previous unit's shared tiles and index
+    if (threadIdx.x == 0) s_unit = atomicAdd(queue, 1);
+    __syncthreads();
+    const int u = s_unit;
+    if (u >= nunits) break;
+    pairs32_unit<KIND, kTPT>(u / nsplit, u - (u / nsplit) * nsplit, tiles, drops, n_drops, tgt, ntarget, src32,
+                             nsource, dens32, nsplit, has_f, has_u, part, sh0, sh1, sh2);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+      queue[0] = 0;
+      queue[1] = 0;
+      __threadfence();
     }
   }
 }
@@ -229,7 +277,7 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
   constexpr int NV = (KIND == STO) ? 6 : 2;   // float4 per staged source
   __shared__ float4 sh[NV][kTile];
   PairTile tile;
-  if (!sub_tile<1>(tiles, tile)) return;
+  if (!sub_tile<1>(tiles, tile, blockIdx.x)) return;
   const int i = tile.drop;
   const DropDev Di = drops[i];
   const int64_t other = nsource - Di.ns;
@@ -311,7 +359,7 @@ k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
   constexpr int NF = (KIND == STO) ? 12 : 4;
   __shared__ double sh[NF][kTile];
   PairTile tile;
-  if (!sub_tile<kTPT>(tiles, tile)) return;
+  if (!sub_tile<kTPT>(tiles, tile, blockIdx.x)) return;
   const int i = tile.drop;
   const DropDev Di = drops[i];
   const int64_t other = nsource - Di.ns;
@@ -407,9 +455,32 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nsplit, int6
   out[e] += s;
 }
 
+// resident CTAs of the persistent pair kernel on this device
 template <int KIND, int TPT>
-void launch_shape(shbim_ctx* ctx, bool has_f, bool has_u, int splits, cudaStream_t s) {
+int queue_grid() {
+  static int g = 0;
+  if (!g) {
+    int dev = 0, nsm = 152, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs32_queue<KIND, TPT>, kThreads, 0) != cudaSuccess)
+      per = 1;
+    g = std::max(1, per) * nsm;
+  }
+  return g;
+}
+
+template <int KIND, int TPT>
+void launch_shape(shbim_ctx* ctx, bool has_f, bool has_u, int splits, bool queue, cudaStream_t s) {
   dim3 grid((unsigned)(ctx->tiles.size() * (kMaxTPT / TPT)), splits);
+  if (queue && ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
+    const int nunits = (int)(grid.x * grid.y);
+    const int g = std::min(nunits, queue_grid<KIND, TPT>());
+    k_pairs32_queue<KIND, TPT><<<g, kThreads, 0, s>>>(ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt,
+                                                       ctx->ntarget, ctx->geo.src32, ctx->nsource, ctx->dens_up32,
+                                                       splits, has_f, has_u, ctx->part, nunits, ctx->pair_queue);
+    return;
+  }
   if (ctx->opts.precision == SHBIM_PREC_DF64) {
     k_pairs_df<KIND><<<dim3((unsigned)(ctx->tiles.size() * kMaxTPT), splits), kThreads, 0, s>>>(
         ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt, ctx->ntarget, ctx->geo.src32,
@@ -426,16 +497,17 @@ void launch_shape(shbim_ctx* ctx, bool has_f, bool has_u, int splits, cudaStream
 }
 
 template <int KIND>
-void launch_raw(shbim_ctx* ctx, bool has_f, bool has_u, int tpt, int splits, cudaStream_t s) {
-  if (tpt == 4) launch_shape<KIND, 4>(ctx, has_f, has_u, splits, s);
-  else if (tpt == 2) launch_shape<KIND, 2>(ctx, has_f, has_u, splits, s);
-  else launch_shape<KIND, 1>(ctx, has_f, has_u, splits, s);
+void launch_raw(shbim_ctx* ctx, bool has_f, bool has_u, int tpt, int splits, bool queue, cudaStream_t s) {
+  if (tpt == 4) launch_shape<KIND, 4>(ctx, has_f, has_u, splits, queue, s);
+  else if (tpt == 2) launch_shape<KIND, 2>(ctx, has_f, has_u, splits, queue, s);
+  else launch_shape<KIND, 1>(ctx, has_f, has_u, splits, queue, s);
 }
 
-// Choose the register blocking (targets per thread) and the source-split count of one FP32
-// kernel kind for this drop layout: every TPT in {1, 2, 4} with split counts in powers of two
-// around the layout's default (times 1/4 ... 4, at most the partial-buffer capacity) is launched
-// twice and the second launch timed with CUDA events; the fastest is kept.
+// Choose the register blocking (targets per thread), the source-split count and the launch form
+// (one CTA per work unit, or resident CTAs taking units from an atomic counter) of one FP32 kernel
+// kind for this drop layout: every TPT in {1, 2, 4} with split counts in powers of two around the
+// layout's default (times 1/4 ... 4, at most the partial-buffer capacity), in both forms, is
+// launched twice and the second launch timed with CUDA events; the fastest is kept.
 template <int KIND>
 int autotune(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
   auto& C = ctx->pair_cfg[KIND];
@@ -451,28 +523,32 @@ int autotune(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
   }
   const int lo = std::max(1, ctx->pair_splits / 4), hi = std::min(ctx->split_max, 4 * ctx->pair_splits);
   int best_t = C.tpt, best_s = C.splits;
+  bool best_q = C.queue;
   float best_ms = 1e30f;
   int sp0 = 1;
   while (2 * sp0 <= lo) sp0 *= 2;
-  for (int tpt = 1; tpt <= kMaxTPT; tpt *= 2) {
-    for (int sp = sp0; sp <= hi; sp *= 2) {
-      launch_raw<KIND>(ctx, has_f, has_u, tpt, sp, s);  // warm
-      cudaEventRecord(a, s);
-      launch_raw<KIND>(ctx, has_f, has_u, tpt, sp, s);
-      cudaEventRecord(b, s);
-      cudaEventSynchronize(b);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, a, b);
-      ctx->launches += 2;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_t = tpt;
-        best_s = sp;
+  for (int q = 0; q < 2; ++q)
+    for (int tpt = 1; tpt <= kMaxTPT; tpt *= 2) {
+      for (int sp = sp0; sp <= hi; sp *= 2) {
+        launch_raw<KIND>(ctx, has_f, has_u, tpt, sp, q != 0, s);  // warm
+        cudaEventRecord(a, s);
+        launch_raw<KIND>(ctx, has_f, has_u, tpt, sp, q != 0, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        ctx->launches += 2;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_t = tpt;
+          best_s = sp;
+          best_q = q != 0;
+        }
       }
     }
-  }
   C.tpt = best_t;
   C.splits = best_s;
+  C.queue = best_q;
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   cudaError_t e = cudaGetLastError();
@@ -496,7 +572,7 @@ int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
   const bool fp32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
   const int tpt = fp32 ? C.tpt : (ctx->opts.precision == SHBIM_PREC_DF64 ? 1 : 2);
   const int splits = fp32 ? C.splits : ctx->pair_splits;
-  launch_raw<KIND>(ctx, has_f, has_u, tpt, splits, s);
+  launch_raw<KIND>(ctx, has_f, has_u, tpt, splits, fp32 && C.queue, s);
   SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
   if (before_reduce) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_reduce, 0));
   const int64_t n = NC * ctx->ntarget;

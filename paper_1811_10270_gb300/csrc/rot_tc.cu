@@ -1,21 +1,26 @@
 // Pole rotation of the singular-row build (Section 3.1) on the fifth-generation tensor cores, with
-// FP64-class accuracy: the two products with the quarter-turn block Dq_n of every degree n are
-// GEMMs of (vectors x 2n+1) by a fixed (2n+1) x (2n+1) table, split into exact bfloat16 digit
-// products (tc.cuh); the z rotations between them act on the double-float values in shared memory.
+// FP64-class accuracy.
 //   forward (ADJ = false): out = Dq^T Dz(-theta) Dq Dz(-phi) in   (position coefficients)
 //   adjoint (ADJ = true):  out = Dz(phi) Dq^T Dz(theta) Dq in     (rows, FP32 planes)
 // theta, phi are the base-grid angles of each vector's target; Dz(a) turns the pair of real
-// coefficients (n, m), (n, -m) by the angle m a.
+// coefficients (n, m), (n, -m) by the angle m a; Dq is the real-basis block of the quarter turn
+// Rx(pi/2). Every target of one latitude shares M(+-theta) = Dq^T Dz(+-theta) Dq, so the middle
+// three factors are one fixed (2n+1) x (2n+1) matrix per (latitude, degree, direction), formed in
+// FP64 on the host: the rotation of the vectors of one latitude is a GEMM by that table, split into
+// exact bfloat16 digit products (tc.cuh), followed (adjoint) or preceded (forward) by Dz(phi) on
+// the double-float values in shared memory.
 //
 // Work decomposition: persistent CTAs (one per SM, 256 threads, all 512 tensor-memory columns:
-// six accumulators of up to 80 columns) loop over items (128 vectors, one degree), largest degree
-// first. Per item: the rows' degree block is read into shared memory as double-float; for each of
-// the two products the rows get a power-of-two scale, per K step of 16 their digit planes and the
-// table's pre-laid-out planes (one bulk copy) fill one of two stages and one thread issues the 21
-// MMAs; the epilogue combines the six accumulators in double-float back into shared memory, where
-// the z rotation follows. Every wait is bounded; a timeout sets the error flag and the CTA stops.
-// Degrees with 2n+1 <= 80 (p <= 39) only: larger blocks use the FP32-pipe kernel.
+// six accumulators of up to 80 columns) loop over items (up to 128 vectors of one latitude, one
+// degree), largest degree first. Per item: the rows' degree block and their targets' phi tables are
+// copied asynchronously into shared memory; the rows get a power-of-two scale; per K step of 16
+// their digit planes and the table's pre-laid-out planes (bulk copies, prefetched a step ahead)
+// fill one of two stages and one thread issues the 21 MMAs; the epilogue combines the six
+// accumulators in double-float. Every wait is bounded; a timeout sets the error flag and the CTA
+// stops. Degrees with 2n+1 <= 80 (p <= 39) only: larger blocks use the FP32-pipe kernel.
 #include <algorithm>
+#include <climits>
+#include <cmath>
 #include <vector>
 
 #include "dfloat.cuh"
@@ -44,25 +49,75 @@ __device__ __forceinline__ void sts(float2* p, int i, df v) { p[i] = make_float2
 
 __host__ __device__ inline int padded(int w) { return w <= 16 ? 16 : (w + 15) / 16 * 16; }
 
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// most targets one item's 128 vectors can touch, with ncomp components per target
+__host__ __device__ inline int max_targets(int ncomp) { return kMT / ncomp + 2; }
+
+// The items of one launch: latitudes lat0 .. lat0 + L - 1 of the chunk, T tiles of 128 vectors per
+// latitude, degrees p .. 0.
+struct Items {
+  int p, nlon, ncomp, t_begin, ct, lat0, L, T;
+  int64_t total;
+  __host__ __device__ Items(int p_, int ncomp_, int t_begin_, int ct_)
+      : p(p_), nlon(2 * p_ + 2), ncomp(ncomp_), t_begin(t_begin_), ct(ct_) {
+    lat0 = t_begin / nlon;
+    L = (t_begin + ct - 1) / nlon - lat0 + 1;
+    T = (nlon * ncomp + kMT - 1) / kMT;
+    total = (int64_t)(p + 1) * L * T;
+  }
+  // degree, latitude and chunk-local vector range [va, vb) of an item (empty if va >= vb)
+  __device__ void decode(int64_t it, int& n, int& lat, int& va, int& vb) const {
+    const int64_t per_n = (int64_t)L * T;
+    n = p - (int)(it / per_n);
+    const int rem = (int)(it - (int64_t)(p - n) * per_n);
+    lat = lat0 + rem / T;
+    const int tile = rem - (rem / T) * T;
+    const int ta = max(t_begin, lat * nlon) - t_begin, tb = min(t_begin + ct, (lat + 1) * nlon) - t_begin;
+    va = ta * ncomp + tile * kMT;
+    vb = min(tb * ncomp, va + kMT);
+  }
+  // the first non-empty item at or after `it` in steps of `stride` (total if none)
+  __device__ int64_t next(int64_t it, int64_t stride) const {
+    for (; it < total; it += stride) {
+      int n, lat, va, vb;
+      decode(it, n, lat, va, vb);
+      if (va < vb) return it;
+    }
+    return total;
+  }
+};
+
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1)
 k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int ct, int ncomp,
-            const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi, const uint4* __restrict__ tdig,
-            const int* __restrict__ toff, float2* __restrict__ vout, float* __restrict__ rows_lap,
+            const float2* __restrict__ cs_phi, const uint4* __restrict__ tdig, const int* __restrict__ toff,
+            const signed char* __restrict__ texp, float2* __restrict__ vout, float* __restrict__ rows_lap,
             float* __restrict__ rows_sto, int nt_drop, int* __restrict__ err) {
+  // dynamic shared memory: [two MMA stages][value block 128 x (2p+1)][(cos, sin)(m phi) of the
+  // item's targets, 2 (p+1) each]
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ __align__(8) uint64_t bbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int rowexp[kMT];
-  __shared__ int rowlat[kMT], rowlon[kMT];
+  __shared__ int rowtgt[kMT];
+  __shared__ int colexp[kNmax];
   const int WS = 2 * p + 1;   // row stride of the value block (odd: conflict-free column access)
+  const int CS = 2 * (p + 1); // one angle table
   float2* sX = reinterpret_cast<float2*>(smem + 2 * kStageBytes);
+  float2* sCS = sX + kMT * WS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nlon = 2 * p + 2;
-  const int64_t nvec = (int64_t)ct * ncomp;
-  const int64_t tiles_v = (nvec + kMT - 1) / kMT;
-  const int64_t total = tiles_v * (p + 1);
+  const Items I(p, ncomp, t_begin, ct);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTmemCols));
@@ -80,15 +135,34 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = tmem_base;
   uint32_t phase[2] = {0u, 0u}, bphase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
+  bool pending[2] = {false, false};   // MMAs committed on the stage and not yet waited for
+  bool bpend[2] = {false, false};     // table copy issued into the stage and not yet waited for
   bool abort_all = false;
   const int r_loc = tid & (kMT - 1), half = tid >> 7;
-
-  // z rotation of every row's degree-n block, in place: angle index from the row's target
-  auto dz = [&](int n, bool theta, bool neg) {
-    const int li = theta ? rowlat[r_loc] : rowlon[r_loc];
-    if (li < 0) return;
-    const float2* cs = (theta ? cs_theta : cs_phi) + (int64_t)li * 2 * (p + 1);
+  // table planes of (latitude, degree), K step ks, into stage st (thread 0)
+  auto issue_b = [&](int lat, int n, int ks, int st) {
+    const int Np = padded(2 * n + 1);
+    const uint32_t bytes = (uint32_t)(kDig * Np * kKS * 2);
+    const int64_t o = toff[((ADJ ? 1 : 0) * (p + 1) + lat) * (p + 1) + n];
+    bulk_load(smem + st * kStageBytes + kDig * kPlaneA * 2, tdig + o + (int64_t)ks * (bytes / 16), bytes, &bbar[st]);
+  };
+  // the first two K steps' table planes of item `it` (both stages free)
+  auto prefetch = [&](int64_t it) {
+    int n, lat, va, vb;
+    I.decode(it, n, lat, va, vb);
+    const bool two = padded(2 * n + 1) > kKS;
+    if (tid == 0) {
+      issue_b(lat, n, 0, 0);
+      if (two) issue_b(lat, n, 1, 1);
+    }
+    bpend[0] = true;
+    bpend[1] = two;
+  };
+  // Dz(+-phi) on every row's degree-n block, in place, with the row's target's table
+  auto dz = [&](int n, bool neg) {
+    const int rt = rowtgt[r_loc];
+    if (rt < 0) return;
+    const float2* cs = sCS + rt * CS;
     float2* x = sX + r_loc * WS;
     for (int m = 1 + half; m <= n; m += 2) {
       const float2 c2 = cs[m], s2 = cs[p + 1 + m];
@@ -100,183 +174,192 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
     }
   };
 
-  for (int64_t item = blockIdx.x; item < total && !abort_all; item += gridDim.x) {
-    const int n = p - (int)(item / tiles_v);
-    const int64_t tv = item - (int64_t)(p - n) * tiles_v;
+  int64_t item = I.next(blockIdx.x, gridDim.x);
+  if (item < I.total) prefetch(item);
+  while (item < I.total && !abort_all) {
+    int n, lat, va, vb;
+    I.decode(item, n, lat, va, vb);
     const int w = 2 * n + 1;
     const int Np = padded(w);
     const int ksteps = Np / kKS;
     const uint32_t idesc = idesc_bf16(Np);
-    // rows of the item: vector v = (chunk-local target b, component c)
+    const int b_lo = va / ncomp;
+    const int nb = (vb - 1) / ncomp - b_lo + 1;
+    // rows of the item (vector v = chunk-local target b, component c), their targets' phi tables
+    // and degree blocks: asynchronous copies, one wait
     if (tid < kMT) {
-      const int64_t v = tv * kMT + tid;
-      if (v < nvec) {
-        const int tl = t_begin + (int)(v / ncomp);
-        rowlat[tid] = tl / nlon;
-        rowlon[tid] = tl - (tl / nlon) * nlon;
-      } else {
-        rowlat[tid] = rowlon[tid] = -1;
-      }
+      const int v = va + tid;
+      rowtgt[tid] = v < vb ? v / ncomp - b_lo : -1;
     }
-    // the degree block of every row (warp per row, lanes along the block: coalesced)
+    if (tid < w) colexp[tid] = texp[((int64_t)(ADJ ? 1 : 0) * (p + 1) + lat) * (p + 1) * (p + 1) + n * n + tid];
+    for (int e = tid; e < nb * (CS / 2); e += kThreads) {
+      const int bt = e / (CS / 2), k2 = e - bt * (CS / 2);   // target, 16-byte piece of its table
+      const int tl = t_begin + b_lo + bt;
+      const float2* src = cs_phi + (int64_t)(tl % I.nlon) * CS;
+      cp_async16(sCS + bt * CS + 2 * k2, src + 2 * k2);
+    }
     for (int r = warp; r < kMT; r += kThreads / 32) {
-      const int64_t v = tv * kMT + r;
-      if (v < nvec) {
-        const int64_t b = v / ncomp, c = v - b * ncomp;
-        const float2* src = vin + b * in_stride + c * nc + (int64_t)n * n;
-        for (int k = lane; k < w; k += 32) sX[r * WS + k] = src[k];
+      const int v = va + r;
+      if (v < vb) {
+        const int b = v / ncomp, c = v - b * ncomp;
+        const float2* src = vin + (int64_t)b * in_stride + (int64_t)c * nc + (int64_t)n * n;
+        for (int k = lane; k < w; k += 32) cp_async8(sX + r * WS + k, src + k);
       } else {
         for (int k = lane; k < w; k += 32) sX[r * WS + k] = make_float2(0.f, 0.f);
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     if (!ADJ) {
-      dz(n, false, true);
+      dz(n, true);
       __syncthreads();
     }
-    for (int g = 0; g < 2 && !abort_all; ++g) {
-      // per-row power-of-two scale, max |hi| < 2^e: warp w scans rows 16 w .. 16 w + 15
-      for (int rr = 0; rr < kMT / (kThreads / 32); ++rr) {
-        const int rl = warp * (kMT / (kThreads / 32)) + rr;
-        float mx = 0.f;
-        for (int k = lane; k < w; k += 32) mx = fmaxf(mx, fabsf(sX[rl * WS + k].x));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) {
-          int e = 0;
-          frexpf(mx, &e);
-          rowexp[rl] = max(e, -120);
+    // per-row power-of-two scale, max |hi| < 2^e: one thread per row (odd row stride: no bank
+    // conflicts)
+    if (tid < kMT) {
+      float mx = 0.f;
+      const float2* xr = sX + tid * WS;
+      for (int k = 0; k < w; ++k) mx = fmaxf(mx, fabsf(xr[k].x));
+      int e = 0;
+      frexpf(mx, &e);
+      rowexp[tid] = max(e, -120);
+    }
+    __syncthreads();
+    const int e_r = rowexp[r_loc];
+    const float2* xrow = sX + r_loc * WS;
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int st = ks & 1;
+      if (pending[st]) {
+        const bool ok = mbar_wait(&mbar[st], phase[st]);
+        phase[st] ^= 1u;
+        pending[st] = false;
+        if (__syncthreads_or(!ok)) {
+          abort_all = true;
+          break;
         }
       }
-      __syncthreads();
-      const int e_r = rowexp[r_loc];
-      const float2* xrow = sX + r_loc * WS;
-      const uint4* tab = tdig + toff[g * (p + 1) + n];
-      const uint32_t bbytes = (uint32_t)(kDig * Np * kKS * 2);
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const int st = ks & 1;
-        if (pending[st]) {
-          const bool ok = mbar_wait(&mbar[st], phase[st]);
-          phase[st] ^= 1u;
-          pending[st] = false;
-          if (__syncthreads_or(!ok)) {
-            abort_all = true;
-            break;
-          }
-        }
-        uint8_t* base = smem + st * kStageBytes;
-        if (tid == 0) bulk_load(base + kDig * kPlaneA * 2, tab + (int64_t)ks * (bbytes / 16), bbytes, &bbar[st]);
-        {
-          const float sc = __int_as_float((127 + 7 - e_r) << 23);   // 2^(7 - e), exact
-          float d[kDig][8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int k = ks * kKS + half * 8 + i;
-            const float2 v = k < w ? xrow[k] : make_float2(0.f, 0.f);
-            float yh = v.x * sc, yl = v.y * sc;
-#pragma unroll
-            for (int j = kDig - 1; j >= 0; --j) {
-              const float dj = rintf(yh);
-              d[j][i] = dj;
-              const df r = dfl::two_sum(dfl::sub_rn(yh, dj), yl);
-              yh = r.hi * 128.f;
-              yl = r.lo * 128.f;
-            }
-          }
-          const int off = canon16(r_loc, half * 8) * 2;
-#pragma unroll
-          for (int j = 0; j < kDig; ++j) {
-            uint4 q;
-            q.x = pack_bf16f(d[j][0], d[j][1]);
-            q.y = pack_bf16f(d[j][2], d[j][3]);
-            q.z = pack_bf16f(d[j][4], d[j][5]);
-            q.w = pack_bf16f(d[j][6], d[j][7]);
-            *reinterpret_cast<uint4*>(base + j * kPlaneA * 2 + off) = q;
-          }
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n");
-        __syncthreads();
-        if (tid == 0) {
-          if (!mbar_wait(&bbar[st], bphase[st])) atomicExch(err, 1);
-          asm volatile("tcgen05.fence::after_thread_sync;\n");
-          const uint32_t a0 = smem_u32(base), b0 = smem_u32(base + kDig * kPlaneA * 2);
-#pragma unroll
-          for (int ja = 0; ja < kDig; ++ja)
-#pragma unroll
-            for (int jb = 0; jb < kDig; ++jb) {
-              if (ja + jb < kDig - 1) continue;
-              const int dgl = ja + jb - (kDig - 1);
-              const uint32_t acc = (ks > 0 || jb != kDig - 1) ? 1u : 0u;
-              mma_bf16(tmem + (uint32_t)(dgl * Np), desc_k16(a0 + ja * kPlaneA * 2),
-                       desc_k16(b0 + jb * Np * kKS * 2), idesc, acc);
-            }
-          mma_commit(&mbar[st]);
-        }
-        bphase[st] ^= 1u;
-        pending[st] = true;
-      }
-      if (abort_all) break;
-      bool ok = true;
-      for (int st = 0; st < 2; ++st)
-        if (pending[st]) {
-          ok = ok && mbar_wait(&mbar[st], phase[st]);
-          phase[st] ^= 1u;
-          pending[st] = false;
-        }
-      if (__syncthreads_or(!ok)) {
-        abort_all = true;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      // epilogue: warp w reads lanes 32 (w % 4) .. +31; column blocks of 16 split between w and w+4
+      uint8_t* base = smem + st * kStageBytes;
       {
-        const int lq = warp & 3, wh = warp >> 2;
-        const int rl = 32 * lq + lane;
-        const int ee = rowexp[rl];
-        for (int cb = wh; cb < Np / 16; cb += 2) {
-          uint32_t a[kDig][16];
+        const float sc = __int_as_float((127 + 7 - e_r) << 23);   // 2^(7 - e), exact
+        float d[kDig][8];
 #pragma unroll
-          for (int dg = 0; dg < kDig; ++dg)
-            tmem_ld16(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * Np + cb * 16), a[dg]);
-          asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+        for (int i = 0; i < 8; ++i) {
+          const int k = ks * kKS + half * 8 + i;
+          const float2 v = k < w ? xrow[k] : make_float2(0.f, 0.f);
+          float yh = v.x * sc, yl = v.y * sc;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            df r{__uint_as_float(a[kDig - 1][j]), 0.f};
-            float wt = 1.f;
-#pragma unroll
-            for (int dg = kDig - 2; dg >= 0; --dg) {
-              wt *= 0.0078125f;   // 2^-7
-              r = dfl::add_f(r, __uint_as_float(a[dg][j]) * wt);
-            }
-            const int o = cb * 16 + j;
-            if (o < w) sX[rl * WS + o] = make_float2(ldexpf(r.hi, ee - 13), ldexpf(r.lo, ee - 13));
+          for (int j = kDig - 1; j >= 0; --j) {
+            const float dj = rintf(yh);
+            d[j][i] = dj;
+            const df r = dfl::two_sum(dfl::sub_rn(yh, dj), yl);
+            yh = r.hi * 128.f;
+            yl = r.lo * 128.f;
           }
         }
+        const int off = canon16(r_loc, half * 8) * 2;
+#pragma unroll
+        for (int j = 0; j < kDig; ++j) {
+          uint4 q;
+          q.x = pack_bf16f(d[j][0], d[j][1]);
+          q.y = pack_bf16f(d[j][2], d[j][3]);
+          q.z = pack_bf16f(d[j][4], d[j][5]);
+          q.w = pack_bf16f(d[j][6], d[j][7]);
+          *reinterpret_cast<uint4*>(base + j * kPlaneA * 2 + off) = q;
+        }
       }
-      // the next products overwrite the accumulators only after every read
-      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      asm volatile("fence.proxy.async.shared::cta;\n");
       __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      if (g == 0) {
-        dz(n, true, !ADJ);
-        __syncthreads();
-      } else if (ADJ) {
-        dz(n, false, false);
-        __syncthreads();
+      if (tid == 0) {
+        // the table planes have landed (bounded; on expiry the products are skipped and the
+        // caller sees the error flag)
+        if (!mbar_wait(&bbar[st], bphase[st])) atomicExch(err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const uint32_t a0 = smem_u32(base), b0 = smem_u32(base + kDig * kPlaneA * 2);
+#pragma unroll
+        for (int ja = 0; ja < kDig; ++ja)
+#pragma unroll
+          for (int jb = 0; jb < kDig; ++jb) {
+            if (ja + jb < kDig - 1) continue;
+            const int dgl = ja + jb - (kDig - 1);
+            const uint32_t acc = (ks > 0 || jb != kDig - 1) ? 1u : 0u;
+            mma_bf16(tmem + (uint32_t)(dgl * Np), desc_k16(a0 + ja * kPlaneA * 2), desc_k16(b0 + jb * Np * kKS * 2),
+                     idesc, acc);
+          }
+        mma_commit(&mbar[st]);
+        // the table planes of K step ks + 1 go to the other stage once its products are done
+        // (step 1's planes were issued with step 0's)
+        if (ks >= 1 && ks + 1 < ksteps) {
+          mbar_wait(&mbar[st ^ 1], phase[st ^ 1]);
+          issue_b(lat, n, ks + 1, st ^ 1);
+        }
       }
+      bphase[st] ^= 1u;
+      bpend[st] = false;
+      if (ks >= 1 && ks + 1 < ksteps) bpend[st ^ 1] = true;
+      pending[st] = true;
     }
     if (abort_all) break;
+    bool ok = true;
+    for (int st = 0; st < 2; ++st)
+      if (pending[st]) {
+        ok = ok && mbar_wait(&mbar[st], phase[st]);
+        phase[st] ^= 1u;
+        pending[st] = false;
+      }
+    if (__syncthreads_or(!ok)) {
+      abort_all = true;
+      break;
+    }
+    // both stages are free: the next item's first table planes travel during the epilogue
+    const int64_t next = I.next(item + gridDim.x, gridDim.x);
+    if (next < I.total) prefetch(next);
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    // epilogue: warp w reads lanes 32 (w % 4) .. +31; column blocks of 16 split between w and w+4
+    {
+      const int lq = warp & 3, wh = warp >> 2;
+      const int rl = 32 * lq + lane;
+      const int ee = rowexp[rl];
+      for (int cb = wh; cb < Np / 16; cb += 2) {
+        uint32_t a[kDig][16];
+#pragma unroll
+        for (int dg = 0; dg < kDig; ++dg)
+          tmem_ld16(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * Np + cb * 16), a[dg]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          df r{__uint_as_float(a[kDig - 1][j]), 0.f};
+          float wt = 1.f;
+#pragma unroll
+          for (int dg = kDig - 2; dg >= 0; --dg) {
+            wt *= 0.0078125f;   // 2^-7
+            r = dfl::add_f(r, __uint_as_float(a[dg][j]) * wt);
+          }
+          const int o = cb * 16 + j;
+          if (o < w) {
+            const int sh = ee + colexp[o] - 14;
+            sX[rl * WS + o] = make_float2(ldexpf(r.hi, sh), ldexpf(r.lo, sh));
+          }
+        }
+      }
+    }
+    // the next products overwrite the accumulators only after every read
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (ADJ) {
+      dz(n, false);
+      __syncthreads();
+    }
     // store (warp per row, lanes along the block)
     for (int r = warp; r < kMT; r += kThreads / 32) {
-      const int64_t v = tv * kMT + r;
-      if (v >= nvec) continue;
-      const int64_t b = v / ncomp;
-      const int c = (int)(v - b * ncomp);
+      const int v = va + r;
+      if (v >= vb) continue;
+      const int b = v / ncomp, c = v - b * ncomp;
       if (!ADJ) {
-        float2* dst = vout + (b * ncomp + c) * nc + (int64_t)n * n;
+        float2* dst = vout + ((int64_t)b * ncomp + c) * nc + (int64_t)n * n;
         for (int k = lane; k < w; k += 32) dst[k] = sX[r * WS + k];
       } else {
-        const int64_t tl = t_begin + b;
+        const int64_t tl = (int64_t)t_begin + b;
         float* dst = c < kNumLap ? rows_lap + (tl * kNumLap + c) * nc : rows_sto + (tl * kNumSto + (c - kNumLap)) * nc;
         const int64_t plane = (int64_t)nt_drop * (c < kNumLap ? kNumLap : kNumSto) * nc;
         for (int k = lane; k < w; k += 32) {
@@ -287,57 +370,106 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
       }
     }
     __syncthreads();
+    item = next;
   }
-  if (abort_all) {
-    for (int st = 0; st < 2; ++st)
-      if (pending[st]) mbar_wait(&mbar[st], phase[st]);
-    if (tid == 0) atomicExch(err, 1);
+  // let products and copies still in flight finish (bounded) before the memory is released
+  for (int st = 0; st < 2; ++st) {
+    if (pending[st]) mbar_wait(&mbar[st], phase[st]);
+    if (bpend[st] && tid == 0) mbar_wait(&bbar[st], bphase[st]);
   }
+  if (abort_all && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
 }
 
-int rot_tc_smem(int p) { return 2 * kStageBytes + kMT * (2 * p + 1) * (int)sizeof(float2); }
+int rot_tc_smem(int p, int ncomp) {
+  return 2 * kStageBytes + (kMT * (2 * p + 1) + max_targets(ncomp) * 2 * (p + 1)) * (int)sizeof(float2);
+}
 
 }  // namespace
 
-bool rot_tc_fits(int p) { return padded(2 * p + 1) <= kNmax && rot_tc_smem(p) + 4096 <= 227 * 1024; }
+// the forward rotation (3 components per target) needs the most angle tables
+bool rot_tc_fits(int p) { return padded(2 * p + 1) <= kNmax && rot_tc_smem(p, 3) + 4096 <= 227 * 1024; }
 
-// Digit planes of Dq_n (g = 0, B[m][k] = Dq_n[m][k]) and its transpose (g = 1) for every degree:
-// [g][n][K step][digit][Np x 16, K-major canonical], offsets in 16-byte units per (g, n).
-int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, DegreeTables& T) {
+// Digit planes of M = Dq_n^T Dz(-theta_j) Dq_n (forward, dir 0) and Dq_n^T Dz(theta_j) Dq_n
+// (adjoint, dir 1) for every base-grid latitude j and degree n, as the B operand B[m][k] = M[m][k]:
+// [dir][j][n][K step][digit][Np x 16, K-major canonical], offsets in 16-byte units per (dir, j, n).
+// Row m is split after its own power-of-two scale 2^-e_m (e_m stored per (dir, j, n, m)), so the
+// digits keep ~42 bits of every row whatever its size.
+int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, const std::vector<double>& theta,
+                  DegreeTables& T) {
   if (!rot_tc_fits(p)) return SHBIM_OK;
-  std::vector<int> off(2 * (p + 1));
-  size_t total = 0;
-  for (int g = 0; g < 2; ++g)
+  const int P1 = p + 1;
+  std::vector<int64_t> off((size_t)2 * P1 * P1);
+  int64_t total = 0;   // uint16 elements
+  for (int dir = 0; dir < 2; ++dir)
+    for (int j = 0; j < P1; ++j)
+      for (int n = 0; n <= p; ++n) {
+        off[((size_t)dir * P1 + j) * P1 + n] = total / 8;
+        const int Np = padded(2 * n + 1);
+        total += (int64_t)(Np / kKS) * kDig * Np * kKS;
+      }
+  if (total / 8 > INT_MAX) return fail(ctx, SHBIM_ERR_ARG, "rotation digit table too large");
+  std::vector<uint16_t> h((size_t)total, 0);
+  std::vector<signed char> ex((size_t)2 * P1 * P1 * P1, 0);   // [dir][j][(p+1)^2] row exponents
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int dj = 0; dj < 2 * P1; ++dj) {
+    const int dir = dj / P1, j = dj - dir * P1;
+    const double a = dir == 0 ? -theta[j] : theta[j];
+    std::vector<double> Z, M;
     for (int n = 0; n <= p; ++n) {
-      off[g * (p + 1) + n] = (int)(total / 8);   // uint16 -> 16-byte units
-      const int Np = padded(2 * n + 1);
-      total += (size_t)(Np / kKS) * kDig * Np * kKS;
-    }
-  std::vector<uint16_t> h(total, 0);
-  for (int g = 0; g < 2; ++g)
-    for (int n = 0; n <= p; ++n) {
-      const int w = 2 * n + 1, Np = padded(w), o = T.dq_off[n];
-      uint16_t* dst = h.data() + (size_t)off[g * (p + 1) + n] * 8;
+      const int w = 2 * n + 1, Np = padded(w);
+      const double* Dn = &D[T.dq_off[n]];
+      // Z = Dz(a) Dq_n: rows (n + m, n - m) turned by m a
+      Z.assign(Dn, Dn + (size_t)w * w);
+      for (int m = 1; m <= n; ++m) {
+        const double c = std::cos(m * a), s = std::sin(m * a);
+        for (int k = 0; k < w; ++k) {
+          const double x = Dn[(size_t)(n + m) * w + k], y = Dn[(size_t)(n - m) * w + k];
+          Z[(size_t)(n + m) * w + k] = c * x - s * y;
+          Z[(size_t)(n - m) * w + k] = s * x + c * y;
+        }
+      }
+      // M = Dq_n^T Z
+      M.assign((size_t)w * w, 0.0);
+      for (int k = 0; k < w; ++k)
+        for (int r = 0; r < w; ++r) {
+          const double dkr = Dn[(size_t)k * w + r];
+          if (dkr == 0.0) continue;
+          for (int c2 = 0; c2 < w; ++c2) M[(size_t)r * w + c2] += dkr * Z[(size_t)k * w + c2];
+        }
+      // a power-of-two scale per row m of M (max_k |M[m][k]| < 2^e_m), undone per output column
+      std::vector<int> em(Np, 0);
+      for (int m = 0; m < w; ++m) {
+        double mx = 0.0;
+        for (int k = 0; k < w; ++k) mx = std::max(mx, std::fabs(M[(size_t)m * w + k]));
+        int e = 0;
+        std::frexp(mx, &e);
+        em[m] = std::max(e, -60);
+        ex[((size_t)dj * P1) * P1 + (size_t)n * n + m] = (signed char)em[m];
+      }
+      uint16_t* dst = h.data() + off[(size_t)dj * P1 + n] * 8;
       for (int ks = 0; ks < Np / kKS; ++ks)
         for (int m = 0; m < Np; ++m)
           for (int kk = 0; kk < kKS; ++kk) {
             const int k = ks * kKS + kk;
-            double v = 0.0;
-            if (m < w && k < w) v = g == 0 ? D[o + (size_t)m * w + k] : D[o + (size_t)k * w + m];
+            const double v = (m < w && k < w) ? M[(size_t)m * w + k] : 0.0;
             int dg[kDig];
-            digits_host(v, 1, dg);   // |Dq| <= 1 < 2^1
-            for (int j = 0; j < kDig; ++j)
-              dst[((size_t)ks * kDig + j) * Np * kKS + canon16(m, kk)] = bf16_int(dg[j]);
+            digits_host(v, em[m], dg);
+            for (int jd = 0; jd < kDig; ++jd)
+              dst[((size_t)ks * kDig + jd) * Np * kKS + canon16(m, kk)] = bf16_int(dg[jd]);
           }
     }
+  }
+  std::vector<int> off32(off.begin(), off.end());
   if (cudaMalloc(&T.rot_digits, h.size() * sizeof(uint16_t)) != cudaSuccess ||
-      cudaMalloc(&T.rot_toff, off.size() * sizeof(int)) != cudaSuccess)
+      cudaMalloc(&T.rot_toff, off32.size() * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&T.rot_exp, ex.size()) != cudaSuccess)
     return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc rotation digit table");
   if (cudaMemcpy(T.rot_digits, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(T.rot_toff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      cudaMemcpy(T.rot_toff, off32.data(), off32.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(T.rot_exp, ex.data(), ex.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(ctx, SHBIM_ERR_CUDA, "cudaMemcpy rotation digit table");
   return SHBIM_OK;
 }
@@ -353,23 +485,23 @@ int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2*
     SHBIM_CUDA(ctx, cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s));
   }
   const int p = T.p;
-  const int smem = rot_tc_smem(p);
+  const int smem = rot_tc_smem(p, ncomp);
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t items = (((int64_t)ct * ncomp + kMT - 1) / kMT) * (p + 1);
-  const unsigned grid = (unsigned)std::min<int64_t>(items, nsm);
+  const Items I(p, ncomp, t_begin, ct);
+  const unsigned grid = (unsigned)std::min<int64_t>(I.total, nsm);
   const uint4* tdig = reinterpret_cast<const uint4*>(T.rot_digits);
   if (adjoint) {
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rotate_tc<true><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_theta_df,
-                                                   T.cs_phi_df, tdig, T.rot_toff, vout, rows_lap, rows_sto, nt_drop,
+    k_rotate_tc<true><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_phi_df, tdig,
+                                                   T.rot_toff, T.rot_exp, vout, rows_lap, rows_sto, nt_drop,
                                                    ctx->tc_err);
   } else {
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rotate_tc<false><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_theta_df,
-                                                    T.cs_phi_df, tdig, T.rot_toff, vout, rows_lap, rows_sto, nt_drop,
-                                                    ctx->tc_err);
+    k_rotate_tc<false><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_phi_df, tdig,
+                                                    T.rot_toff, T.rot_exp, vout, rows_lap, rows_sto, nt_drop,
+                                                   ctx->tc_err);
   }
   SHBIM_CHECK_LAUNCH(ctx, "k_rotate_tc");
   return SHBIM_OK;

@@ -8,6 +8,7 @@
 //   3. analyse the weights (Fourier stage on the tensor cores, dft_tc.cu, or folded four ways in
 //      double-float; then the Legendre stage);
 //   4. rotate the coefficient rows back (row = D_R v) and store them as (hi, lo) FP32 planes.
+// The rotations of steps 1 and 4 run on the tensor cores (rot_tc.cu) where the degree fits.
 // Every sum and every pointwise operation is double-float (hi + lo FP32 pairs; Dekker products,
 // Knuth sums, Newton square roots), ~2^-44 relative per operation, so the rows agree with the
 // FP64 build to rounding level while the FP64 pipe (1/64 of the FP32 rate here) stays idle.
@@ -559,17 +560,20 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int rows = std::max(1, std::min(8, budget / (2 * N)));
     const size_t f_smem = (size_t)(2 * N + rows * 2 * N) * sizeof(float2);
     const int nt = (d.p + 1) * (d.p + 2) / 2;
-    const bool rot_tc = ctx->tc_rows && ctx->tc_rot && rot_tc_fits(d.p);
+    const bool rot_tc = ctx->tc_rot && rot_tc_fits(d.p);
     for (int t0 = 0; t0 < d.nt; t0 += CT) {
       const int ct = std::min(CT, d.nt - t0);
       // the position coefficients are the same for every target: zero input stride
-      if (rot_tc) {
-        if ((rc = rotate_tc(ctx, *d.tab, false, xc, 0, nc, t0, ct, 3, rot, nullptr, nullptr, d.nt, s))) return rc;
-      } else {
-        k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, s>>>(
-            xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
-            d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
-        SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+      {
+        TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, s);
+        if (rot_tc) {
+          if ((rc = rotate_tc(ctx, *d.tab, false, xc, 0, nc, t0, ct, 3, rot, nullptr, nullptr, d.nt, s))) return rc;
+        } else {
+          k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, s>>>(
+              xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
+              d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
+          SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+        }
       }
       {
         TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
@@ -590,19 +594,22 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
         SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
       }
-      if (rot_tc) {
-        if ((rc = rotate_tc(ctx, *d.tab, true, vb, (int64_t)ncomp * nc, nc, t0, ct, ncomp, nullptr, d.rows_lap,
-                            d.rows_sto, d.nt, s)))
-          return rc;
-      } else {
-        k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
-            vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df,
-            d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
-        SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+      {
+        TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, s);
+        if (rot_tc) {
+          if ((rc = rotate_tc(ctx, *d.tab, true, vb, (int64_t)ncomp * nc, nc, t0, ct, ncomp, nullptr, d.rows_lap,
+                              d.rows_sto, d.nt, s)))
+            return rc;
+        } else {
+          k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
+              vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df,
+              d.tab->dq_df, d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
+          SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
+        }
       }
     }
   }
-  if (ctx->tc_rows && ctx->tc_err) {
+  if ((ctx->tc_rows || ctx->tc_rot) && ctx->tc_err) {
     int flag = 0;
     SHBIM_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SHBIM_CUDA(ctx, cudaStreamSynchronize(s));

@@ -251,7 +251,6 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
   }
   int rc = upload(ctx, &T.dq, D);
   if (rc) return rc;
-  if ((rc = rot_tc_digits(ctx, p, D, T))) return rc;
   {
     std::vector<float2> Ddf(D.size()), DTdf(D.size());
     for (size_t i = 0; i < D.size(); ++i) Ddf[i] = split_df(D[i]);
@@ -308,6 +307,9 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
       }
     }
     if ((rc = upload_df(ctx, &T.cs_theta_df, cth)) || (rc = upload_df(ctx, &T.cs_phi_df, cph))) return rc;
+    std::vector<double> theta(p + 1);
+    for (int j = 0; j <= p; ++j) theta[j] = std::acos(tb[j]);
+    if ((rc = rot_tc_digits(ctx, p, D, theta, T))) return rc;
   }
   cudaError_t e = cudaMalloc(&T.dq_off_dev, T.dq_off.size() * sizeof(int));
   if (e != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc rotation offsets");
@@ -359,6 +361,7 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->dft_digits);
   cudaFree(t->rot_digits);
   cudaFree(t->rot_toff);
+  cudaFree(t->rot_exp);
   cudaFree(t->cs_theta_df);
   cudaFree(t->cs_phi_df);
   delete t;

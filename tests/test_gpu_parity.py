@@ -230,8 +230,8 @@ def test_three_drops_uneven_degrees_match_oracle(S):
 
 def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
     """The singular self rows built in double-float arithmetic (the default, with the Fourier stage
-    on the tensor cores, and without) against the rows of the FP64 build and the oracle, on one
-    perturbed drop (self term only) and on two drops."""
+    and the rotations on the tensor cores; each alone; neither) against the rows of the FP64 build
+    and the oracle, on one perturbed drop (self term only) and on two drops."""
     rng = np.random.default_rng(31)
     one = [inputs.Drop(11, inputs.perturbed_coef(11, rng, 1.0, (0.1, -0.2, 0.3)), np.zeros(sh.ncoef(11)),
                        2.5, np.array([0.1, -0.2, 0.3]), 1.0)]
@@ -242,7 +242,8 @@ def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
         sig = [inputs.random_density(d.p, rng)[0] for d in drops]
         u = [inputs.random_density(d.p, rng, 3) for d in drops]
         res = {}
-        for rows, tc in ((S.FP64, False), (S.DF64, False), (S.DF64, True)):
+        variants = ((S.FP64, 0), (S.DF64, 0), (S.DF64, S.TC_FOURIER), (S.DF64, S.TC_ROTATION), (S.DF64, S.TC_ALL))
+        for rows, tc in variants:
             ctx = S.Context(precision=S.FP64, R=2.0, gmres_tol=1e-12)
             ctx.set_rows_precision(rows)
             ctx.set_tensor_cores(tc)
@@ -261,15 +262,17 @@ def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
             ctx.close()
         refs = [np.concatenate(sysm.laplace_coef("ladl", sig)), np.concatenate(sysm.laplace_coef("lsl", sig)),
                 np.concatenate([a.ravel() for a in sysm.stokes_coef(u, u)])]
-        for key in ((S.DF64, False), (S.DF64, True)):
-            for a, b, ref in zip(res[key], res[(S.FP64, False)], refs):
+        for key in variants[1:]:
+            for a, b, ref in zip(res[key], res[(S.FP64, 0)], refs):
                 assert rel_err(a, b) < 1e-11, key
                 assert rel_err(a, ref) < TOL64, key
 
 
 def test_every_pair_launch_shape_matches_oracle(S):
-    """Each register blocking (1, 2, 4 targets per thread) with one and several source splits:
-    drops of 200, 98 and 50 targets leave ragged and empty sub-tiles in every shape."""
+    """Each register blocking (1, 2, 4 targets per thread) with one and several source splits, as
+    a CTA per work unit and as persistent CTAs on the work counter (the same sums to the bit, also
+    on a second launch after the counter reset): drops of 200, 98 and 50 targets leave ragged and
+    empty sub-tiles in every shape."""
     rng = np.random.default_rng(21)
     drops = []
     for p, ctr, lam in ((9, (0, 0, 0), 2.0), (6, (2.4, 0.3, -0.2), 0.5), (4, (-0.4, -2.3, 0.5), 4.0)):
@@ -290,17 +293,29 @@ def test_every_pair_launch_shape_matches_oracle(S):
     assert not fixed                      # nothing launched yet: the shape is not chosen
     for tpt in (1, 2, 4):
         for splits in sorted({1, max(1, default_splits)}):
-            for kind in (0, 1, 2):
-                ctx.set_pair_shape(kind, tpt, splits)
-                assert ctx.pair_shape(kind) == (tpt, splits, True)
-            out = torch.empty(nc, device=DEV, dtype=torch.float64)
-            ctx.eval_electric(S.LAPLACE_DL, sig_d, out, S.OUT_COEF)
-            assert rel_err(out.cpu().numpy(), ref[0]) < TOL32, (tpt, splits)
-            ctx.eval_electric(S.LAPLACE_SL, sig_d, out, S.OUT_COEF)
-            assert rel_err(out.cpu().numpy(), ref[1]) < TOL32, (tpt, splits)
-            out3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
-            ctx.eval_stokes(f_d, u_d, out3, S.OUT_COEF)
-            assert rel_err(out3.cpu().numpy(), ref[2]) < TOL32, (tpt, splits)
+            got = {}
+            for queue in (False, True):
+                for kind in (0, 1, 2):
+                    ctx.set_pair_shape(kind, tpt, splits)
+                    ctx.set_pair_queue(kind, queue)
+                    assert ctx.pair_shape(kind) == (tpt, splits, True) and ctx.pair_queue(kind) == queue
+                outs = []
+                for rep in range(2 if queue else 1):
+                    out = torch.empty(nc, device=DEV, dtype=torch.float64)
+                    ctx.eval_electric(S.LAPLACE_DL, sig_d, out, S.OUT_COEF)
+                    dl = out.cpu().numpy()
+                    ctx.eval_electric(S.LAPLACE_SL, sig_d, out, S.OUT_COEF)
+                    sl = out.cpu().numpy()
+                    out3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
+                    ctx.eval_stokes(f_d, u_d, out3, S.OUT_COEF)
+                    outs.append((dl, sl, out3.cpu().numpy()))
+                    for k in range(3):
+                        assert rel_err(outs[-1][k], ref[k]) < TOL32, (tpt, splits, queue, k)
+                got[queue] = outs
+            for a, b in zip(got[False][0], got[True][0]):
+                assert np.array_equal(a, b), (tpt, splits)
+            for a, b in zip(got[True][0], got[True][1]):
+                assert np.array_equal(a, b), (tpt, splits)
     with pytest.raises(S.ShbimError):
         ctx.set_pair_shape(0, 3, 1)
     with pytest.raises(S.ShbimError):
@@ -311,7 +326,7 @@ def test_every_pair_launch_shape_matches_oracle(S):
     out3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
     ctx.eval_stokes(f_d, u_d, out3, S.OUT_COEF)
     tpt, splits, fixed = ctx.pair_shape(2)
-    assert fixed and tpt in (1, 2, 4) and splits >= 1
+    assert fixed and tpt in (1, 2, 4) and splits >= 1 and ctx.pair_queue(2) in (False, True)
     assert rel_err(out3.cpu().numpy(), ref[2]) < TOL32
     ctx.close()
 
