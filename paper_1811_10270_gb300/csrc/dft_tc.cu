@@ -5,11 +5,11 @@
 // (o = p+1+m), phi_k = 2 pi k / (2q+2): a GEMM with the row count of a chunk of weights
 // (targets x 14 components x latitudes) and a fixed table. Every double-float value is split,
 // after scaling by a power of two per row (per table for T), into six integer digits exactly
-// representable in bfloat16: X = round(x 2^42) = sum_j d_j 128^j with d_0..d_4 in [-64, 63]
-// (balanced base 2^7) and the top digit d_5 the rest (|d_5| <= 128). The 21 digit products with
+// representable in bfloat16: X ~ x 2^42 = sum_j d_j 128^j, balanced base 2^7 (|d_j| <= 72) with the
+// top digit d_5 the rest (|d_5| <= 128; tc.cuh). The 21 digit products with
 // j_a + j_b >= 5 are tensor-core GEMMs (tcgen05.mma kind::f16, bf16 x bf16 -> f32); products of
 // equal j_a + j_b share one accumulator, and every accumulator sums integers below 2^24, so the
-// FP32 accumulation in tensor memory is exact. The epilogue combines the six accumulators in
+// FP32 accumulation in tensor memory is exact. The epilogue combines the six accumulators into a
 // double-float. The neglected products (j_a + j_b < 5) and the rounding of the digits bound the
 // error by ~2^-42 of sum_k |W[r][k]| (Ozaki-style error-free splitting of a matrix product).
 //
@@ -29,77 +29,20 @@
 
 #include "dfloat.cuh"
 #include "internal.h"
+#include "tc.cuh"
 
 namespace shbim {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kNT = 80;                       // outputs per tile (MMA N)
-constexpr int kMT = 128;                      // rows per tile (MMA M = tensor-memory lanes)
-constexpr int kKS = 16;                       // longitudes per K step (MMA K)
-constexpr int kDig = 6;                       // digits per value
 constexpr int kThreadsTC = 256;
 constexpr int kPlaneA = kMT * kKS;            // bf16 per row-digit plane (4096 B)
 constexpr int kPlaneB = kNT * kKS;            // bf16 per table-digit plane (2560 B)
 constexpr int kStageBytes = kDig * (kPlaneA + kPlaneB) * 2;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kWaitLimit = 1 << 24;
-
-// digits of x 2^(42 - e), |x| < 2^e: d_0..d_4 balanced base 2^7, d_5 the rest
-void digits_host(double x, int e, int d[kDig]) {
-  long long X = std::llrint(std::ldexp(x, 42 - e));
-  for (int j = 0; j < kDig - 1; ++j) {
-    const long long dj = ((X + 64) & 127) - 64;
-    d[j] = (int)dj;
-    X = (X - dj) / 128;
-  }
-  d[kDig - 1] = (int)X;
-}
-
-// bfloat16 bits of a small integer (|v| <= 256 is exact: the low 16 bits of the float are zero)
-uint16_t bf16_int(int v) {
-  const float f = (float)v;
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  return (uint16_t)(u >> 16);
-}
-
-// element (row n, k) of one K-major canonical plane of K = 16: 8-row x 16-byte core matrices,
-// [row group][k chunk][row % 8][k % 8]
-__host__ __device__ inline int canon16(int n, int k) { return ((n >> 3) * 2 + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t desc_k16(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128u >> 4) << 16;   // leading-dimension byte offset: next 8-element k chunk
-  d |= (uint64_t)(256u >> 4) << 32;   // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;             // descriptor version; no swizzle
-  return d;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity));
-  }
-  return done != 0;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16f(float a, float b) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // small integers: exact
-  return *reinterpret_cast<const uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes));
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar)));
-}
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const uint4* __restrict__ tdig,
@@ -203,15 +146,10 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
         for (int i = 0; i < 8; ++i) {
           const int k = ks * kKS + half * 8 + i;
           const float2 v = (rv && k < nlon) ? wrow[k] : make_float2(0.f, 0.f);
-          float yh = v.x * sc, yl = v.y * sc;
+          float dd[kDig];
+          digits6(v.x * sc, v.y * sc, dd);
 #pragma unroll
-          for (int j = kDig - 1; j >= 0; --j) {
-            const float dj = rintf(yh);
-            d[j][i] = dj;
-            const dfl::df r = dfl::two_sum(dfl::sub_rn(yh, dj), yl);
-            yh = r.hi * 128.f;
-            yl = r.lo * 128.f;
-          }
+          for (int j = 0; j < kDig; ++j) d[j][i] = dd[j];
         }
         const int off = canon16(r_loc, half * 8) * 2;   // bytes; 16-byte aligned
 #pragma unroll
@@ -297,16 +235,10 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
       asm volatile("tcgen05.wait::ld.sync.aligned;\n");
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        // sum_s acc_s 2^(7 (s - smax)) in double-float, from the top diagonal down
-        dfl::df r{__uint_as_float(a[kDig - 1][j]), 0.f};
-        float w = 1.f;
-#pragma unroll
-        for (int dg = kDig - 2; dg >= 0; --dg) {
-          w *= 0.0078125f;   // 2^-7
-          r = dfl::add_f(r, __uint_as_float(a[dg][j]) * w);
-        }
+        const dfl::df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
+                                   __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));
         const int o = tn * kNT + cb * 16 + j;
-        if (rowe < rows && o < nout) F[rowe * nout + o] = make_float2(ldexpf(r.hi, ee - 13), ldexpf(r.lo, ee - 13));
+        if (rowe < rows && o < nout) F[rowe * nout + o] = scale2(r, ee - 13);
       }
     }
     // the next tile's first products overwrite the accumulators only after every read

@@ -246,15 +246,10 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
         for (int i = 0; i < 8; ++i) {
           const int k = ks * kKS + half * 8 + i;
           const float2 v = k < w ? xrow[k] : make_float2(0.f, 0.f);
-          float yh = v.x * sc, yl = v.y * sc;
+          float dd[kDig];
+          digits6(v.x * sc, v.y * sc, dd);
 #pragma unroll
-          for (int j = kDig - 1; j >= 0; --j) {
-            const float dj = rintf(yh);
-            d[j][i] = dj;
-            const df r = dfl::two_sum(dfl::sub_rn(yh, dj), yl);
-            yh = r.hi * 128.f;
-            yl = r.lo * 128.f;
-          }
+          for (int j = 0; j < kDig; ++j) d[j][i] = dd[j];
         }
         const int off = canon16(r_loc, half * 8) * 2;
 #pragma unroll
@@ -327,17 +322,11 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
         asm volatile("tcgen05.wait::ld.sync.aligned;\n");
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          df r{__uint_as_float(a[kDig - 1][j]), 0.f};
-          float wt = 1.f;
-#pragma unroll
-          for (int dg = kDig - 2; dg >= 0; --dg) {
-            wt *= 0.0078125f;   // 2^-7
-            r = dfl::add_f(r, __uint_as_float(a[dg][j]) * wt);
-          }
           const int o = cb * 16 + j;
           if (o < w) {
-            const int sh = ee + colexp[o] - 14;
-            sX[rl * WS + o] = make_float2(ldexpf(r.hi, sh), ldexpf(r.lo, sh));
+            const df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
+                                  __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));
+            sX[rl * WS + o] = scale2(r, ee + colexp[o] - 14);
           }
         }
       }

@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <cstring>
 
+#include "dfloat.cuh"
+
 namespace shbim {
 namespace tc {
 
@@ -110,6 +112,46 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&a)[16]) {
       : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
         "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
       : "r"(addr));
+}
+
+// Six balanced base-2^7 digits of y = yh + yl (|yh| < 128, |yl| <= ulp(yh) / 2), top first:
+// d5 = rint(y), then the digits of the remainder times 128, and so on. The top three come from yh
+// alone (every remainder exact); yl joins through one two-sum at the scale of d2; the last two come
+// from an FP32 remainder whose rounding (< 2^-25 of d2's unit) stays far below d0's half unit.
+// Bounds: |d5| <= 128, |d4|, |d3| <= 64, |d2| <= 72, |d1|, |d0| <= 65.
+__device__ __forceinline__ void digits6(float yh, float yl, float (&d)[kDig]) {
+  float t = yh;
+  d[5] = rintf(t);
+  t = (t - d[5]) * 128.f;
+  d[4] = rintf(t);
+  t = (t - d[4]) * 128.f;
+  d[3] = rintf(t);
+  t = (t - d[3]) * 128.f;
+  const dfl::df u = dfl::two_sum(t, yl * 2097152.f);   // yl at the scale of d2 (2^21)
+  d[2] = rintf(u.hi);
+  float r = ((u.hi - d[2]) + u.lo) * 128.f;
+  d[1] = rintf(r);
+  r = (r - d[1]) * 128.f;
+  d[0] = rintf(r);
+}
+
+// sum_s acc_s 2^(7 (s - 5)) as a double-float from the six exact FP32 diagonal sums
+// (|acc_s| < 2^24): the three top terms are exact in FP32 and joined by two-sums; the three lowest
+// (weights 2^-21 and below) are summed in plain FP32, rounding below 2^-21 units of the top term.
+__device__ __forceinline__ dfl::df combine6(float a5, float a4, float a3, float a2, float a1, float a0) {
+  const float low = fmaf(a0, 0x1p-35f, fmaf(a1, 0x1p-28f, a2 * 0x1p-21f));
+  const dfl::df s1 = dfl::two_sum(a5, a4 * 0x1p-7f);
+  const dfl::df s2 = dfl::two_sum(s1.hi, a3 * 0x1p-14f);
+  return dfl::quick_two_sum(s2.hi, (s1.lo + s2.lo) + low);
+}
+
+// x 2^sh for a double-float (exact power-of-two scaling; ldexpf only where 2^sh is not normal)
+__device__ __forceinline__ float2 scale2(dfl::df x, int sh) {
+  if (sh >= -126 && sh <= 127) {
+    const float f = __int_as_float((127 + sh) << 23);
+    return make_float2(x.hi * f, x.lo * f);
+  }
+  return make_float2(ldexpf(x.hi, sh), ldexpf(x.lo, sh));
 }
 
 }  // namespace tc
