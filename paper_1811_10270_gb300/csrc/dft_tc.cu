@@ -13,13 +13,14 @@
 // double-float. The neglected products (j_a + j_b < 5) and the rounding of the digits bound the
 // error by ~2^-42 of sum_k |W[r][k]| (Ozaki-style error-free splitting of a matrix product).
 //
-// Work decomposition: persistent CTAs (one per SM, 256 threads; the six accumulators of an
-// 80-column tile take 480 of the SM's 512 tensor-memory columns) loop over tiles of 128 rows x 80
-// outputs. Per K step of 16 longitudes the threads write the rows' digit planes into one of two
-// shared-memory stages (two threads per row, eight values each), copy the table's pre-laid-out
-// digit planes, and one thread issues the 21 MMAs and commits them to the stage's mbarrier; the
-// other stage is filled meanwhile. Every wait is bounded; a timeout sets the error flag and the
-// kernel stops issuing work.
+// Work decomposition: persistent CTAs (one per SM, 256 threads; the six accumulators of the
+// 80-output tile take 480 of the SM's 512 tensor-memory columns) loop over tiles of 128 rows. The
+// table's pre-laid-out digit planes (all K steps, up to 150 KB) are copied into shared memory once
+// per CTA. Per tile two threads per row find the row's scale, then per K step of 16 longitudes
+// each thread turns eight values (read from global memory one step ahead) into digit planes in one
+// of two shared-memory stages and one thread issues the 21 MMAs and commits them to the stage's
+// mbarrier; the other stage is filled meanwhile. Every wait is bounded; a timeout sets the error
+// flag and the kernel stops issuing work. Degrees with 2p + 2 <= 80 (p <= 39).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,116 +39,120 @@ namespace {
 using namespace tc;
 
 constexpr int kNT = 80;                       // outputs per tile (MMA N)
-constexpr int kThreadsTC = 256;
+constexpr int kProducers = 256;                // digit-writing and epilogue threads (8 warps)
+constexpr int kThreadsTC = kProducers + 32;    // + one warp that issues the MMAs
 constexpr int kPlaneA = kMT * kKS;            // bf16 per row-digit plane (4096 B)
 constexpr int kPlaneB = kNT * kKS;            // bf16 per table-digit plane (2560 B)
-constexpr int kStageBytes = kDig * (kPlaneA + kPlaneB) * 2;
 constexpr uint32_t kTmemCols = 512;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const uint4* __restrict__ tdig,
-         int ntiles_n, int ksteps, float2* __restrict__ F, int* __restrict__ err) {
-  // dynamic shared memory: [two MMA stages][the current 128-row tile of W, rows contiguous]
+         int ksteps, float2* __restrict__ F, int* __restrict__ err) {
+  // dynamic shared memory: [the table's digit planes for every K step, resident][two stages of row
+  // digit planes]
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[2];    // stage written by the 256 producers
+  __shared__ __align__(8) uint64_t empty[2];   // stage's products done (tcgen05.commit)
   __shared__ __align__(8) uint64_t tbar;
-  __shared__ __align__(8) uint64_t bbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int rowexp[kMT];
-  const float2* tileb = reinterpret_cast<const float2*>(smem + 2 * kStageBytes);
+  __shared__ float rowmax[2][kMT];
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + (size_t)ksteps * kDig * kPlaneB * 2;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int64_t tiles_m = (rows + kMT - 1) / kMT;
-  const int64_t total = tiles_m * ntiles_n;
+  const bool producer = tid < kProducers;
+  const int64_t total = (rows + kMT - 1) / kMT;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&mbar[1])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&tbar)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&bbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&bbar[1])), "r"(1));
+    mbar_init(&full[0], kProducers);
+    mbar_init(&full[1], kProducers);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    mbar_init(&tbar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
-  // the first tile's rows: one bulk (TMA) copy of contiguous memory
-  auto issue_tile = [&](int64_t tile) {
-    const int64_t r0 = (tile / ntiles_n) * kMT;
-    const int64_t nr = min((int64_t)kMT, rows - r0);
-    bulk_load(smem + 2 * kStageBytes, W + r0 * nlon, (uint32_t)(nr * nlon * sizeof(float2)), &tbar);
-  };
-  if (tid == 0 && (int64_t)blockIdx.x < total) issue_tile(blockIdx.x);
+  // the whole table (one bulk copy), waited for once
+  const uint32_t tbytes = (uint32_t)ksteps * kDig * kPlaneB * 2;
+  if (tid == 0 && (int64_t)blockIdx.x < total) bulk_load(sB, tdig, tbytes, &tbar);
+  bool table_ok = true;
+  if ((int64_t)blockIdx.x < total) table_ok = mbar_wait(&tbar, 0);
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNT >> 3) << 17) | ((uint32_t)(kMT >> 4) << 24);
-  uint32_t phase[2] = {0u, 0u}, tphase = 0u, bphase[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  bool tile_pending = (int64_t)blockIdx.x < total;
-  bool abort_all = false;
-  const int r_loc = tid & (kMT - 1), half = tid >> 7;
-  for (int64_t tile = blockIdx.x; tile < total && !abort_all; tile += gridDim.x) {
-    const int64_t tm = tile / ntiles_n;
-    const int tn = (int)(tile - tm * ntiles_n);
-    {
-      const bool ok = mbar_wait(&tbar, tphase);
-      tphase ^= 1u;
-      tile_pending = false;
-      if (__syncthreads_or(!ok)) {
-        abort_all = true;
-        break;
-      }
-    }
-    // per-row power-of-two scale, max |hi| < 2^e: warp w scans rows 16 w .. 16 w + 15 (four rows'
-    // reductions interleaved)
-#pragma unroll 4
-    for (int rr = 0; rr < kMT / (kThreadsTC / 32); ++rr) {
-      const int rl = warp * (kMT / (kThreadsTC / 32)) + rr;
+  const uint32_t idesc = idesc_bf16(kNT);
+  // uses of each stage so far (the same count in every thread): fill u waits for the products of
+  // fill u - 1 (parity (u - 1) & 1 of `empty`), the MMA warp waits for fill u (parity u & 1 of `full`)
+  uint32_t uses[2] = {0u, 0u};
+  bool abort_all = __syncthreads_or(!table_ok);
+  const int r_loc = tid & (kMT - 1), half = (tid >> 7) & 1;
+  for (int64_t tm = blockIdx.x; tm < total && !abort_all; tm += gridDim.x) {
+    const int64_t row = tm * kMT + r_loc;
+    const bool rv = producer && row < rows;
+    const float2* wrow = W + (rv ? row : 0) * nlon;
+    // per-row power-of-two scale, max |hi| < 2^e: two threads per row, a half row each
+    if (producer) {
       float mx = 0.f;
-      if (tm * kMT + rl < rows)
-        for (int k = tid & 31; k < nlon; k += 32) mx = fmaxf(mx, fabsf(tileb[rl * nlon + k].x));
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if ((tid & 31) == 0) {
-        int e = 0;
-        frexpf(mx, &e);
-        rowexp[rl] = max(e, -120);   // keeps 2^(7 - e) a normal float; smaller rows scale the same
-      }
-    }
-    __syncthreads();
-    const int e_r = rowexp[r_loc];
-    const bool rv = tm * kMT + r_loc < rows;
-    const float2* wrow = tileb + r_loc * nlon;
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int st = ks & 1;
-      if (pending[st]) {
-        const bool ok = mbar_wait(&mbar[st], phase[st]);
-        phase[st] ^= 1u;
-        pending[st] = false;
-        if (__syncthreads_or(!ok)) {
-          abort_all = true;
-          break;
+      if (rv) {
+        const int h = nlon >> 1, k0 = half * h;
+#pragma unroll 4
+        for (int k = k0; k < k0 + h; k += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(wrow + k);
+          mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
         }
       }
-      uint8_t* base = smem + st * kStageBytes;
-      // table digits of this (n tile, K step): a bulk copy of the pre-laid-out planes, in flight
-      // while the row digits are formed
-      if (tid == 0)
-        bulk_load(base + kDig * kPlaneA * 2, tdig + ((int64_t)tn * ksteps + ks) * (kDig * kPlaneB / 8),
-                  (uint32_t)(kDig * kPlaneB * 2), &bbar[st]);
-      // row digits, top down in FP32: y = x 2^(7 - e); d = rint(y.hi); y = (y - d) 128 with the
-      // residual kept exactly as a double-float; d_5 (|d_5| <= 128) .. d_0 (|d_j| <= 64)
-      {
-        const float sc = __int_as_float((127 + 7 - e_r) << 23);   // 2^(7 - e), exact
+      rowmax[half][r_loc] = mx;
+    }
+    __syncthreads();
+    if (tid < kMT) {
+      int e = 0;
+      frexpf(fmaxf(rowmax[0][tid], rowmax[1][tid]), &e);
+      rowexp[tid] = max(e, -120);   // keeps 2^(7 - e) a normal float; smaller rows scale the same
+    }
+    __syncthreads();
+    bool bad = false;
+    if (producer) {
+      const float sc = __int_as_float((127 + 7 - rowexp[r_loc]) << 23);   // 2^(7 - e), exact
+      // eight values per K step (two per 16-byte load; nlon is a multiple of 4, so a pair lies
+      // wholly inside or wholly past the row), read one step ahead
+      float4 nxt[4];
+#pragma unroll
+      for (int i2 = 0; i2 < 4; ++i2) {
+        const int k = half * 8 + 2 * i2;
+        nxt[i2] = (rv && k < nlon) ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int ks = 0; ks < ksteps && !bad; ++ks) {
+        const int st = ks & 1;
+        float4 cur[4];
+#pragma unroll
+        for (int i2 = 0; i2 < 4; ++i2) cur[i2] = nxt[i2];
+        if (ks + 1 < ksteps) {
+#pragma unroll
+          for (int i2 = 0; i2 < 4; ++i2) {
+            const int k = (ks + 1) * kKS + half * 8 + 2 * i2;
+            nxt[i2] = (rv && k < nlon) ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+        if (uses[st] > 0 && !mbar_wait(&empty[st], (uses[st] - 1) & 1)) {
+          bad = true;
+          break;
+        }
+        uint8_t* base = sA + st * (kDig * kPlaneA * 2);
         float d[kDig][8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          const int k = ks * kKS + half * 8 + i;
-          const float2 v = (rv && k < nlon) ? wrow[k] : make_float2(0.f, 0.f);
+          const float4 v4 = cur[i >> 1];
+          const float vh = (i & 1) ? v4.z : v4.x, vl = (i & 1) ? v4.w : v4.y;
           float dd[kDig];
-          digits6(v.x * sc, v.y * sc, dd);
+          digits6(vh * sc, vl * sc, dd);
 #pragma unroll
           for (int j = 0; j < kDig; ++j) d[j][i] = dd[j];
         }
@@ -161,15 +166,21 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
           q.w = pack_bf16f(d[j][6], d[j][7]);
           *reinterpret_cast<uint4*>(base + j * kPlaneA * 2 + off) = q;
         }
+        // the writes become visible to the tensor cores' (async-proxy) reads, then the stage is
+        // reported full
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(&full[st]);
+        ++uses[st];
       }
-      asm volatile("fence.proxy.async.shared::cta;\n");
-      __syncthreads();
-      if (tid == 0) {
-        // the table planes have landed (bounded; on expiry the products are skipped and the
-        // caller sees the error flag)
-        if (!mbar_wait(&bbar[st], bphase[st])) atomicExch(err, 1);
+    } else if (tid == kProducers) {
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int st = ks & 1;
+        if (!mbar_wait(&full[st], uses[st] & 1)) {
+          bad = true;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const uint32_t a0 = smem_u32(base), b0 = smem_u32(base + kDig * kPlaneA * 2);
+        const uint32_t a0 = smem_u32(sA + st * (kDig * kPlaneA * 2)), b0 = smem_u32(sB + (size_t)ks * kDig * kPlaneB * 2);
 #pragma unroll
         for (int ja = 0; ja < kDig; ++ja)
 #pragma unroll
@@ -179,66 +190,49 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
             // the first product of each diagonal (j_b = 5 in this loop order) in the first K step
             // overwrites the accumulator
             const uint32_t acc = (ks > 0 || jb != kDig - 1) ? 1u : 0u;
-            const uint64_t da = desc_k16(a0 + ja * kPlaneA * 2);
-            const uint64_t db = desc_k16(b0 + jb * kPlaneB * 2);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(dgl * kNT)),
-                "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            mma_bf16(tmem + (uint32_t)(dgl * kNT), desc_k16(a0 + ja * kPlaneA * 2), desc_k16(b0 + jb * kPlaneB * 2),
+                     idesc, acc);
           }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(&mbar[st])));
+        mma_commit(&empty[st]);
+        ++uses[st];
       }
-      bphase[st] ^= 1u;
-      pending[st] = true;
+    } else {
+      for (int ks = 0; ks < ksteps; ++ks) ++uses[ks & 1];
     }
-    if (abort_all) break;
-    // every thread is done with this tile's rows: the next tile's copy overlaps the epilogue
-    __syncthreads();
-    if (tile + gridDim.x < total) {
-      tile_pending = true;
-      if (tid == 0) {
-        asm volatile("fence.proxy.async.shared::cta;\n");
-        issue_tile(tile + gridDim.x);
-      }
-    }
-    // all products of the tile complete
-    bool ok = true;
-    for (int st = 0; st < 2; ++st)
-      if (pending[st]) {
-        ok = ok && mbar_wait(&mbar[st], phase[st]);
-        phase[st] ^= 1u;
-        pending[st] = false;
-      }
-    if (__syncthreads_or(!ok)) {
+    if (__syncthreads_or(bad)) {
       abort_all = true;
       break;
     }
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    // epilogue: warp w reads lanes 32 (w % 4) .. +31; column blocks of 16 split between w and w+4
-    const int lq = warp & 3, wh = warp >> 2;
-    const int rl = 32 * lq + (tid & 31);
-    const int64_t rowe = tm * kMT + rl;
-    const int ee = rowexp[rl];
-    for (int cb = wh; cb < kNT / 16; cb += 2) {
-      uint32_t a[kDig][16];
-#pragma unroll
-      for (int dg = 0; dg < kDig; ++dg) {
-        const uint32_t addr = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * kNT + cb * 16);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(a[dg][0]), "=r"(a[dg][1]), "=r"(a[dg][2]), "=r"(a[dg][3]), "=r"(a[dg][4]), "=r"(a[dg][5]),
-              "=r"(a[dg][6]), "=r"(a[dg][7]), "=r"(a[dg][8]), "=r"(a[dg][9]), "=r"(a[dg][10]), "=r"(a[dg][11]),
-              "=r"(a[dg][12]), "=r"(a[dg][13]), "=r"(a[dg][14]), "=r"(a[dg][15])
-            : "r"(addr));
+    // all products of the tile complete: the last commit covers every earlier product
+    {
+      const int st = (ksteps - 1) & 1;
+      if (__syncthreads_or(!mbar_wait(&empty[st], (uses[st] - 1) & 1))) {
+        abort_all = true;
+        break;
       }
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    // epilogue: warp w (< 8) reads lanes 32 (w % 4) .. +31; column blocks of 16 split between w and w+4
+    if (producer) {
+      const int lq = warp & 3, wh = warp >> 2;
+      const int rl = 32 * lq + (tid & 31);
+      const int64_t rowe = tm * kMT + rl;
+      const int ee = rowexp[rl];
+      for (int cb = wh; cb < kNT / 16; cb += 2) {
+        uint32_t a[kDig][16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const dfl::df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
-                                   __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));
-        const int o = tn * kNT + cb * 16 + j;
-        if (rowe < rows && o < nout) F[rowe * nout + o] = scale2(r, ee - 13);
+        for (int dg = 0; dg < kDig; ++dg)
+          tmem_ld16(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * kNT + cb * 16), a[dg]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int o = cb * 16 + j;
+          if (rowe < rows && o < nout) {
+            const dfl::df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
+                                       __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));
+            F[rowe * nout + o] = scale2(r, ee - 13);
+          }
+        }
       }
     }
     // the next tile's first products overwrite the accumulators only after every read
@@ -246,11 +240,11 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
   }
+  // let products and copies still in flight finish (bounded) before resources are released
   if (abort_all) {
-    // let products and copies still in flight finish (bounded) before resources are released
     for (int st = 0; st < 2; ++st)
-      if (pending[st]) mbar_wait(&mbar[st], phase[st]);
-    if (tile_pending) mbar_wait(&tbar, tphase);
+      if (uses[st] > 0) mbar_wait(&empty[st], (uses[st] - 1) & 1);
+    if (!table_ok && tid == 0) mbar_wait(&tbar, 0);
     if (tid == 0) atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -260,9 +254,12 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
 
 }  // namespace
 
-int dft_tc_smem(int p) { return 2 * kStageBytes + kMT * 4 * (p + 1) * (int)sizeof(float2); }
+int dft_tc_ksteps(int p) { return (4 * (p + 1) + kKS - 1) / kKS; }
 
-bool dft_tc_fits(int p) { return dft_tc_smem(p) + 4096 <= 227 * 1024; }
+int dft_tc_smem(int p) { return (dft_tc_ksteps(p) * kPlaneB + 2 * kPlaneA) * kDig * 2; }
+
+// one 80-output tile (2p + 2 <= 80) with the table resident beside two row stages
+bool dft_tc_fits(int p) { return 2 * (p + 1) <= kNT && dft_tc_smem(p) + 4096 <= 227 * 1024; }
 
 int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T) {
   const int nlon = 4 * (p + 1), nout = 2 * (p + 1);
@@ -307,10 +304,12 @@ int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, 
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = ((rows + kMT - 1) / kMT) * T.dft_ntiles;
+  if (!dft_tc_fits(p) || T.dft_ntiles != 1 || T.dft_ksteps != dft_tc_ksteps(p))
+    return fail(ctx, SHBIM_ERR_ARG, "tensor-core Fourier stage: degree out of range");
+  const int64_t tiles = (rows + kMT - 1) / kMT;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
   k_dft_tc<<<grid, kThreadsTC, smem, s>>>(W, rows, nlon, nout, reinterpret_cast<const uint4*>(T.dft_digits),
-                                          T.dft_ntiles, T.dft_ksteps, F, ctx->tc_err);
+                                          T.dft_ksteps, F, ctx->tc_err);
   SHBIM_CHECK_LAUNCH(ctx, "k_dft_tc");
   return SHBIM_OK;
 }
