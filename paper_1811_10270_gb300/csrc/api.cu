@@ -170,6 +170,7 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->phys.lb);
   cudaFree(ctx->dens_split);
   cudaFree(ctx->xdf);
+  cudaFree(ctx->rexp);
   cudaFree(ctx->tc_err);
   cudaFree(ctx->gm.xr);
   cudaFree(ctx->gm.rr);

@@ -16,7 +16,8 @@
 // Work decomposition: persistent CTAs (one per SM, 256 threads; the six accumulators of the
 // 80-output tile take 480 of the SM's 512 tensor-memory columns) loop over tiles of 128 rows. The
 // table's pre-laid-out digit planes (all K steps, up to 150 KB) are copied into shared memory once
-// per CTA. Per tile two threads per row find the row's scale, then per K step of 16 longitudes
+// per CTA; the next tile's rows are prefetched into L2. Per tile the rows' scales come with the
+// rows (or two threads per row find them), then per K step of 16 longitudes
 // each thread turns eight values (read from global memory one step ahead) into digit planes in one
 // of two shared-memory stages and one thread issues the 21 MMAs and commits them to the stage's
 // mbarrier; the other stage is filled meanwhile. Every wait is bounded; a timeout sets the error
@@ -51,7 +52,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const uint4* __restrict__ tdig,
-         int ksteps, float2* __restrict__ F, int* __restrict__ err) {
+         int ksteps, const int* __restrict__ rexp, float2* __restrict__ F, int* __restrict__ err) {
   // dynamic shared memory: [the table's digit planes for every K step, resident][two stages of row
   // digit planes]
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -98,8 +99,19 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
     const int64_t row = tm * kMT + r_loc;
     const bool rv = producer && row < rows;
     const float2* wrow = W + (rv ? row : 0) * nlon;
-    // per-row power-of-two scale, max |hi| < 2^e: two threads per row, a half row each
-    if (producer) {
+    // the next tile's rows start moving from HBM into L2 now
+    if (tid == kProducers && tm + gridDim.x < total) {
+      const int64_t r1 = (tm + gridDim.x) * kMT;
+      const int64_t bytes = min((int64_t)kMT, rows - r1) * nlon * (int64_t)sizeof(float2);
+      for (int64_t off = 0; off < bytes; off += 32768)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(reinterpret_cast<const char*>(W + r1 * nlon) + off),
+                     "r"((uint32_t)min((int64_t)32768, bytes - off)));
+    }
+    // per-row power-of-two scale, max |hi| < 2^e: given by the producer of W, or two threads per
+    // row scanning a half row each
+    if (rexp) {
+      if (tid < kMT) rowexp[tid] = tm * kMT + tid < rows ? rexp[tm * kMT + tid] : 0;
+    } else if (producer) {
       float mx = 0.f;
       if (rv) {
         const int h = nlon >> 1, k0 = half * h;
@@ -112,7 +124,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
       rowmax[half][r_loc] = mx;
     }
     __syncthreads();
-    if (tid < kMT) {
+    if (!rexp && tid < kMT) {
       int e = 0;
       frexpf(fmaxf(rowmax[0][tid], rowmax[1][tid]), &e);
       rowexp[tid] = max(e, -120);   // keeps 2^(7 - e) a normal float; smaller rows scale the same
@@ -290,8 +302,8 @@ int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T) {
   return SHBIM_OK;
 }
 
-int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, float2* F,
-                        cudaStream_t s) {
+int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, const int* rexp,
+                        float2* F, cudaStream_t s) {
   if (rows <= 0) return SHBIM_OK;
   if (!ctx->tc_err) {
     if (cudaMalloc(&ctx->tc_err, sizeof(int)) != cudaSuccess)
@@ -309,7 +321,7 @@ int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, 
   const int64_t tiles = (rows + kMT - 1) / kMT;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
   k_dft_tc<<<grid, kThreadsTC, smem, s>>>(W, rows, nlon, nout, reinterpret_cast<const uint4*>(T.dft_digits),
-                                          T.dft_ksteps, F, ctx->tc_err);
+                                          T.dft_ksteps, rexp, F, ctx->tc_err);
   SHBIM_CHECK_LAUNCH(ctx, "k_dft_tc");
   return SHBIM_OK;
 }

@@ -153,6 +153,8 @@ struct shbim_ctx {
   bool autotune = true;           // off: every layout keeps the default launch shape
   double* xdf = nullptr;          // position coefficients of one drop as double-float (row build)
   size_t xdf_cap = 0;
+  double* rexp = nullptr;         // int row exponents of a chunk of weights (row build), as doubles' storage
+  size_t rexp_cap = 0;
   float* dens_split = nullptr;    // [2][3 ncoef] hi / lo planes of a density for the self GEMV
   size_t dens_split_cap = 0;
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
@@ -355,8 +357,8 @@ int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2*
 int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T);
 // the kernel holds a 128-row tile of W in shared memory: degrees up to 34
 bool dft_tc_fits(int p);
-int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, float2* F,
-                        cudaStream_t s);
+int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, const int* rexp,
+                        float2* F, cudaStream_t s);
 
 // ---- shape-dependent state for an unchanged layout (api.cu)
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);

@@ -281,7 +281,7 @@ __device__ void synth4_df(const float2* __restrict__ a, const float2* __restrict
 __global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, const float2* __restrict__ alf,
                                   const float2* __restrict__ trig, const double* __restrict__ mu,
                                   const double* __restrict__ tgt, int64_t ntarget, int64_t tgt0,
-                                  float2* __restrict__ wbuf) {
+                                  float2* __restrict__ wbuf, int* __restrict__ rexp) {
   extern __shared__ float2 smf[];
   const int t = blockIdx.x;
   const int j = blockIdx.y;
@@ -317,15 +317,17 @@ __global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, 
   }
   __syncthreads();
   const int Q4 = N >> 2;
+  // field fastest: the lanes of a warp read the same few trig entries (broadcasts) instead of
+  // entries m k apart (bank conflicts)
   for (int task = threadIdx.x; task < 9 * (Q4 + 1); task += blockDim.x) {
-    const int fk = task / (Q4 + 1);
-    const int k = task - fk * (Q4 + 1);
+    const int k = task / 9;
+    const int fk = task - k * 9;
     const float2* Ac = A + (fk * 2) * P1;
     const float2* As = Ac + P1;
-    if (fk % 3 != 2)
-      synth4_df(Ac, As, ld(Ac, 0), 1.f, p, k, N, tc, ts, V + fk * N);
-    else
-      synth4_df(As, Ac, df{0.f, 0.f}, -1.f, p, k, N, tc, ts, V + fk * N);
+    // the phi-derivative kind swaps the cos / sin roles: selected per lane, one code path
+    const bool dphi = fk % 3 == 2;
+    synth4_df(dphi ? As : Ac, dphi ? Ac : As, dphi ? df{0.f, 0.f} : ld(Ac, 0), dphi ? -1.f : 1.f, p, k, N, tc, ts,
+              V + fk * N);
   }
   __syncthreads();
   // the target's position and normal and mu_j / (4 pi) as double-float, converted once per block
@@ -341,6 +343,9 @@ __global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, 
   const df n0x = ld(tv, 3), n0y = ld(tv, 4), n0z = ld(tv, 5);
   const df w0 = ld(tv, 6);
   const int64_t Ns = (int64_t)(q + 1) * N;
+  float mx[14];
+#pragma unroll
+  for (int c = 0; c < 14; ++c) mx[c] = 0.f;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const df xt0 = ld(V, 1 * N + k), xt1 = ld(V, 4 * N + k), xt2 = ld(V, 7 * N + k);
     const df xp0 = ld(V, 2 * N + k), xp1 = ld(V, 5 * N + k), xp2 = ld(V, 8 * N + k);
@@ -380,7 +385,31 @@ __global__ void k_self_weights_df(const float2* __restrict__ rot, int p, int q, 
     out[13] = dfl::mul(dz, hz);
     const int64_t node = (int64_t)j * N + k;
 #pragma unroll
-    for (int c = 0; c < 14; ++c) st(wbuf, ((int64_t)t * 14 + c) * Ns + node, out[c]);
+    for (int c = 0; c < 14; ++c) {
+      st(wbuf, ((int64_t)t * 14 + c) * Ns + node, out[c]);
+      mx[c] = fmaxf(mx[c], fabsf(out[c].hi));
+    }
+  }
+  // power-of-two scale of each (component, latitude) row for the tensor-core analysis: max |hi|
+  // < 2^e over the row's N nodes
+  if (rexp) {
+    __shared__ float red[4][14];   // blockDim.x <= 128
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 14; ++c) {
+      float v = mx[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+      if (lane == 0) red[wp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 14) {
+      float v = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmaxf(v, red[w][threadIdx.x]);
+      int e = 0;
+      frexpf(v, &e);
+      rexp[((int64_t)t * 14 + threadIdx.x) * (q + 1) + j] = max(e, -120);
+    }
   }
 }
 
@@ -561,6 +590,14 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const size_t f_smem = (size_t)(2 * N + rows * 2 * N) * sizeof(float2);
     const int nt = (d.p + 1) * (d.p + 2) / 2;
     const bool rot_tc = ctx->tc_rot && rot_tc_fits(d.p);
+    const bool dft_tc = ctx->tc_rows && dft_tc_fits(d.p);
+    // row exponents of the weights for the tensor-core analysis, written by the weights kernel
+    int* rexp = nullptr;
+    if (dft_tc) {
+      if ((rc = ensure_d(ctx, &ctx->rexp, &ctx->rexp_cap, ((size_t)CT * ncomp * (d.q + 1) + 1) / 2, "row exponents")))
+        return rc;
+      rexp = reinterpret_cast<int*>(ctx->rexp);
+    }
     for (int t0 = 0; t0 < d.nt; t0 += CT) {
       const int ct = std::min(CT, d.nt - t0);
       // the position coefficients are the same for every target: zero input stride
@@ -578,14 +615,15 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
       {
         TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
         k_self_weights_df<<<dim3(ct, d.q + 1), 128, w_smem, s>>>(rot, d.p, d.q, d.tab->up_alf_df, d.tab->up_trig_df,
-                                                                 up.mu, ctx->geo.tgt, ctx->ntarget, d.tgt_off + t0, wb);
+                                                                 up.mu, ctx->geo.tgt, ctx->ntarget, d.tgt_off + t0, wb,
+                                                                 dft_tc ? rexp : nullptr);
         SHBIM_CHECK_LAUNCH(ctx, "k_self_weights_df");
       }
       {
         TimeScope ts(ctx, SHBIM_K_SELF_ANALYSIS, s);
         const int64_t nrows = (int64_t)ct * ncomp * (d.q + 1);
-        if (ctx->tc_rows && dft_tc_fits(d.p)) {
-          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, F, s))) return rc;
+        if (dft_tc) {
+          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, s))) return rc;
         } else {
           k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, s>>>(wb, Ns, d.p, d.q,
                                                                                     d.tab->up_trig_df, nrows, rows, F);
