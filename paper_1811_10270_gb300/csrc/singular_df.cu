@@ -490,31 +490,44 @@ __global__ void k_analysis_f4_df(const float2* __restrict__ vals, int64_t val_st
   }
 }
 
-// Legendre stage: coef[item][n^2+n+-m] = s_m sum_j F[item][j][cs][m] Pbar_n^m(t_j)
-__global__ void k_analysis_leg_df(const float2* __restrict__ F, int p, int q, const float2* __restrict__ alf,
-                                  float2* __restrict__ coef, int64_t coef_stride) {
+// Legendre stage: coef[item][n^2+n+-m] = s_m sum_j F[item][j][cs][m] Pbar_n^m(t_j), one CTA per
+// item: the item's Fourier coefficients (q + 1 latitudes x 2 x (p + 1) double-float values) are
+// copied once into shared memory, where every output reads them as broadcasts; the Legendre table
+// comes through L1 (shared by all CTAs).
+__global__ void __launch_bounds__(288)
+k_analysis_leg_item_df(const float2* __restrict__ F, int p, int q, const float2* __restrict__ alf,
+                       float2* __restrict__ coef, int64_t coef_stride) {
+  extern __shared__ __align__(16) float2 sF[];
   const int item = blockIdx.x;
   const int nt = (p + 1) * (p + 2) / 2;
-  const int o = blockIdx.y * blockDim.x + threadIdx.x;
-  if (o >= nt) return;
-  int m = 0;
-  while (m < p && tri_off_i(p, m + 1) <= o) ++m;
-  const int n = m + (o - tri_off_i(p, m));
   const int P1 = p + 1;
-  const float2* Fi = F + (int64_t)item * (q + 1) * 2 * P1;
-  dfl::acc ac, as;
-  for (int j = 0; j <= q; ++j) {
-    const df a = ld(alf, (int64_t)j * 3 * nt + o);
-    ac.add_prod(ld(Fi, (int64_t)j * 2 * P1 + m), a);
-    as.add_prod(ld(Fi, (int64_t)j * 2 * P1 + P1 + m), a);
-  }
+  const int nF = (q + 1) * 2 * P1;   // float2, a multiple of 2 (16-byte pieces)
+  const float2* Fi = F + (int64_t)item * nF;
+  for (int e = threadIdx.x; e < nF / 2; e += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(sF + 2 * e)),
+                 "l"(Fi + 2 * e));
+  asm volatile("cp.async.commit_group;\n");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
   float2* c = coef + (int64_t)item * coef_stride;
-  if (m == 0) {
-    st(c, n * n + n, ac.value());
-  } else {
-    const df s2{1.41421353816986084f, 2.4203234971764687e-08f};
-    st(c, n * n + n + m, dfl::mul(s2, ac.value()));
-    st(c, n * n + n - m, dfl::mul(s2, as.value()));
+  for (int o = threadIdx.x; o < nt; o += blockDim.x) {
+    int m = 0;
+    while (m < p && tri_off_i(p, m + 1) <= o) ++m;
+    const int n = m + (o - tri_off_i(p, m));
+    dfl::acc ac, as;
+#pragma unroll 4
+    for (int j = 0; j <= q; ++j) {
+      const df a = ld(alf, (int64_t)j * 3 * nt + o);
+      ac.add_prod(ld(sF, j * 2 * P1 + m), a);
+      as.add_prod(ld(sF, j * 2 * P1 + P1 + m), a);
+    }
+    if (m == 0) {
+      st(c, n * n + n, ac.value());
+    } else {
+      const df s2{1.41421353816986084f, 2.4203234971764687e-08f};
+      st(c, n * n + n + m, dfl::mul(s2, ac.value()));
+      st(c, n * n + n - m, dfl::mul(s2, as.value()));
+    }
   }
 }
 
@@ -588,8 +601,9 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int budget = 46 * 1024 / (int)sizeof(float2) - 2 * N;
     const int rows = std::max(1, std::min(8, budget / (2 * N)));
     const size_t f_smem = (size_t)(2 * N + rows * 2 * N) * sizeof(float2);
-    const int nt = (d.p + 1) * (d.p + 2) / 2;
     const bool rot_tc = ctx->tc_rot && rot_tc_fits(d.p);
+    const int leg_smem = (d.q + 1) * 2 * (d.p + 1) * (int)sizeof(float2);
+    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_analysis_leg_item_df, cudaFuncAttributeMaxDynamicSharedMemorySize, leg_smem));
     const bool dft_tc = ctx->tc_rows && dft_tc_fits(d.p);
     // row exponents of the weights for the tensor-core analysis, written by the weights kernel
     int* rexp = nullptr;
@@ -629,8 +643,8 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
                                                                                     d.tab->up_trig_df, nrows, rows, F);
           SHBIM_CHECK_LAUNCH(ctx, "k_analysis_f4_df");
         }
-        k_analysis_leg_df<<<dim3(ct * ncomp, (nt + 127) / 128), 128, 0, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
-        SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_df");
+        k_analysis_leg_item_df<<<ct * ncomp, 288, leg_smem, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
+        SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_item_df");
       }
       {
         TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, s);
