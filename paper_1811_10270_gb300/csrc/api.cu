@@ -67,6 +67,8 @@ void free_drop_state(shbim_ctx* ctx) {
   ctx->tiles_dev = nullptr;
   cudaFree(ctx->drops_dev);
   ctx->drops_dev = nullptr;
+  cudaFree(ctx->lamm1_dev);
+  ctx->lamm1_dev = nullptr;
   cudaFree(ctx->dens_up);
   ctx->dens_up = nullptr;
   cudaFree(ctx->dens_up32);
@@ -297,7 +299,12 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
   for (int i = 0; same && i < n_drops; ++i) same = ctx->drops[i].p == p_host[i];
   if (same) {
     // same layout: keep every allocation, refresh the shape-dependent state only
-    for (int i = 0; i < n_drops; ++i) ctx->drops[i].lam = lambda_host ? lambda_host[i] : 1.0;
+    std::vector<double> lm1(n_drops);
+    for (int i = 0; i < n_drops; ++i) {
+      ctx->drops[i].lam = lambda_host ? lambda_host[i] : 1.0;
+      lm1[i] = ctx->drops[i].lam - 1.0;
+    }
+    SHBIM_CUDA(ctx, cudaMemcpy(ctx->lamm1_dev, lm1.data(), n_drops * sizeof(double), cudaMemcpyHostToDevice));
     return rebuild_geometry(ctx, xcoef_dev, s);
   }
   free_drop_state(ctx);
@@ -359,6 +366,10 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
                 tdrop.begin() + ctx->drops[i].tgt_off + ctx->drops[i].nt, i);
     SHBIM_CUDA(ctx, cudaMemcpy(ctx->geo.tgt_drop, tdrop.data(), to * sizeof(int), cudaMemcpyHostToDevice));
     if ((rc = dalloc(ctx, &ctx->drops_dev, n_drops, "drop table"))) return rc;
+    std::vector<double> lm1(n_drops);
+    for (int i = 0; i < n_drops; ++i) lm1[i] = ctx->drops[i].lam - 1.0;
+    if ((rc = dalloc(ctx, &ctx->lamm1_dev, n_drops, "viscosity contrasts"))) return rc;
+    SHBIM_CUDA(ctx, cudaMemcpy(ctx->lamm1_dev, lm1.data(), n_drops * sizeof(double), cudaMemcpyHostToDevice));
   }
   // all-pairs tiling: tiles never cross a drop; sources split so that the grid fills the GPU
   {
@@ -429,6 +440,14 @@ int shbim_sht(shbim_ctx* ctx, int drop, int dir, int grid, int n_fields, const d
 namespace shbim {
 namespace {
 
+// Number of consecutive drops from drop a on with the same degree (their coefficients, targets and
+// sources are contiguous, so one launch transforms them all).
+int same_degree_run(const shbim_ctx* ctx, size_t a) {
+  size_t b = a + 1;
+  while (b < ctx->drops.size() && ctx->drops[b].tab == ctx->drops[a].tab) ++b;
+  return (int)(b - a);
+}
+
 // Streams of one operator application. With two or more drops and concurrency on, the self rows
 // (which overwrite the output values) and then the near-field correction (which adds into them)
 // run on the library's side stream while the caller's stream synthesises the strengths and runs
@@ -483,11 +502,13 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   }
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (auto& d : ctx->drops) {
-      rc = sht_synth_scaled(ctx, d.tab->up, 1, dens_dev + d.coef_off, d.nc, ctx->dens_up + d.src_off, 0,
-                            ctx->geo.src + 6 * ctx->nsource + d.src_off, 1.0,
-                            f32 ? ctx->dens_up32 + d.src_off : nullptr, s,
-                            lo ? ctx->dens_up32lo + d.src_off : nullptr);
+    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
+      const Drop& d = ctx->drops[a];
+      const int nb = same_degree_run(ctx, a);
+      b = a + nb;
+      rc = sht_synth_drops(ctx, d.tab->up, nb, 1, dens_dev + d.coef_off, d.nc, ctx->dens_up + d.src_off, 0, d.ns,
+                           ctx->geo.src + 6 * ctx->nsource + d.src_off, 1.0, nullptr,
+                           f32 ? ctx->dens_up32 + d.src_off : nullptr, s, lo ? ctx->dens_up32lo + d.src_off : nullptr);
       if (rc) return rc;
     }
   }
@@ -500,8 +521,11 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   }
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (auto& d : ctx->drops) {
-      rc = sht_analysis(ctx, d.tab->base, 1, vals + d.tgt_off, d.nt, true, out_dev + d.coef_off, d.nc, s);
+    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
+      const Drop& d = ctx->drops[a];
+      const int nb = same_degree_run(ctx, a);
+      b = a + nb;
+      rc = sht_analysis(ctx, d.tab->base, nb, vals + d.tgt_off, d.nt, true, out_dev + d.coef_off, d.nc, s);
       if (rc) return rc;
     }
   }
@@ -530,19 +554,22 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   }
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (auto& d : ctx->drops) {
+    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
+      const Drop& d = ctx->drops[a];
+      const int nb = same_degree_run(ctx, a);
+      b = a + nb;
       const double* w = ctx->geo.src + 6 * NS + d.src_off;
       if (f_dev) {
-        rc = sht_synth_scaled(ctx, d.tab->up, 3, f_dev + 3 * d.coef_off, d.nc, ctx->dens_up + d.src_off, NS,
-                              w, 1.0, f32 ? ctx->dens_up32 + d.src_off : nullptr, s,
-                              lo ? ctx->dens_up32lo + d.src_off : nullptr);
+        rc = sht_synth_drops(ctx, d.tab->up, nb, 3, f_dev + 3 * d.coef_off, d.nc, ctx->dens_up + d.src_off, NS, d.ns,
+                             w, 1.0, nullptr, f32 ? ctx->dens_up32 + d.src_off : nullptr, s,
+                             lo ? ctx->dens_up32lo + d.src_off : nullptr);
         if (rc) return rc;
       }
       if (u_dev) {
-        rc = sht_synth_scaled(ctx, d.tab->up, 3, u_dev + 3 * d.coef_off, d.nc,
-                              ctx->dens_up + 3 * NS + d.src_off, NS, w, -6.0 * (d.lam - 1.0),
-                              f32 ? ctx->dens_up32 + 3 * NS + d.src_off : nullptr, s,
-                              lo ? ctx->dens_up32lo + 3 * NS + d.src_off : nullptr);
+        // strength -6 (lambda_j - 1) u per drop
+        rc = sht_synth_drops(ctx, d.tab->up, nb, 3, u_dev + 3 * d.coef_off, d.nc, ctx->dens_up + 3 * NS + d.src_off,
+                             NS, d.ns, w, -6.0, ctx->lamm1_dev + a, f32 ? ctx->dens_up32 + 3 * NS + d.src_off : nullptr,
+                             s, lo ? ctx->dens_up32lo + 3 * NS + d.src_off : nullptr);
         if (rc) return rc;
       }
     }
@@ -556,9 +583,11 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   }
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (auto& d : ctx->drops) {
-      rc = sht_analysis(ctx, d.tab->base, 3, vals + 3 * d.tgt_off, d.nt, true, out_dev + 3 * d.coef_off,
-                        d.nc, s);
+    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
+      const Drop& d = ctx->drops[a];
+      const int nb = same_degree_run(ctx, a);
+      b = a + nb;
+      rc = sht_analysis(ctx, d.tab->base, 3 * nb, vals + 3 * d.tgt_off, d.nt, true, out_dev + 3 * d.coef_off, d.nc, s);
       if (rc) return rc;
     }
   }

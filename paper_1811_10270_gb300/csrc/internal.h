@@ -138,6 +138,7 @@ struct shbim_ctx {
   shbim::Geometry geo;
   std::vector<shbim::PairTile> tiles;
   shbim::PairTile* tiles_dev = nullptr;
+  double* lamm1_dev = nullptr;    // lambda_j - 1 per drop
   shbim::DropDev* drops_dev = nullptr;
   int pair_splits = 1;            // default source-split count of the layout
   int split_max = 1;              // capacity of the partial-sum buffer in splits
@@ -313,6 +314,9 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
 int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
                      int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
                      double alpha, float* out32, cudaStream_t s, float* out32lo = nullptr);
+int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const double* coef, int64_t coef_stride,
+                    double* out, int64_t comp_stride, int64_t drop_stride, const double* scale, double alpha,
+                    const double* alpha_drop, float* out32, cudaStream_t s, float* out32lo = nullptr);
 // Analysis: coef[item] = sum_nodes w(node) vals[item][node] S_nm(node) with w = omega_j when
 // weighted, else 1. Uses ctx->sht_scratch (grown as needed).
 int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double* vals,

@@ -26,13 +26,21 @@ __device__ __forceinline__ int kind_of_slot(int kinds, int slot) {
   return 0;
 }
 
+// Items are (drop d, component c) with item = d kpd + c: coefficients at item * coef_stride,
+// values at d drop_stride + c item_stride (+ kind slot * kind_stride), the per-node scale at
+// d drop_stride, the factor alpha (times alpha_drop[d] when given).
 __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, int p, int q,
                         const double* __restrict__ alf, const double* __restrict__ trig, int kinds,
                         double* __restrict__ out, int64_t item_stride, int64_t kind_stride,
                         const double* __restrict__ scale, double alpha, float* __restrict__ out32,
-                        float* __restrict__ out32lo) {
+                        float* __restrict__ out32lo, int kpd, int64_t drop_stride,
+                        const double* __restrict__ alpha_drop) {
   extern __shared__ double sm[];
   const int item = blockIdx.x;
+  const int dl = item / kpd, ci = item - dl * kpd;
+  const int64_t obase = (int64_t)dl * drop_stride + (int64_t)ci * item_stride;
+  if (scale) scale += (int64_t)dl * drop_stride;
+  if (alpha_drop) alpha *= alpha_drop[dl];
   const int j = blockIdx.y;
   const int nk = __popc(kinds);
   const int N = 2 * q + 2;
@@ -84,7 +92,7 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
         const int kind = kind_of_slot(kinds, slot);
         double v = V[slot * N + k];
         if (kind == 0 && scale) v *= scale[node] * alpha;
-        const int64_t o = (int64_t)item * item_stride + (int64_t)slot * kind_stride + node;
+        const int64_t o = obase + (int64_t)slot * kind_stride + node;
         out[o] = v;
         if (out32) {
           const float h = (float)v;
@@ -121,7 +129,7 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
         v = s2 * v;
       }
       if (kind == 0 && scale) v *= scale[node] * alpha;
-      const int64_t o = (int64_t)item * item_stride + (int64_t)slot * kind_stride + node;
+      const int64_t o = obase + (int64_t)slot * kind_stride + node;
       out[o] = v;
       if (out32) {
         const float h = (float)v;
@@ -149,7 +157,7 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, kinds, out,
-                                  item_stride, kind_stride, scale, 1.0, out32, nullptr);
+                                  item_stride, kind_stride, scale, 1.0, out32, nullptr, n_items, 0, nullptr);
   SHBIM_CHECK_LAUNCH(ctx, "k_synth");
   return SHBIM_OK;
 }
@@ -159,9 +167,13 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
 // sums in FP32 (relative error ~1e-7, as the FP32 path allows).
 __global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, int p, int q,
                           const float* __restrict__ alf32, const float* __restrict__ trig32, float* __restrict__ out32,
-                          int64_t item_stride, const double* __restrict__ scale, double alpha) {
+                          int64_t item_stride, const double* __restrict__ scale, double alpha, int kpd,
+                          int64_t drop_stride, const double* __restrict__ alpha_drop) {
   extern __shared__ float smf32[];
   const int item = blockIdx.x, j = blockIdx.y;
+  const int dl = item / kpd, ci = item - dl * kpd;
+  scale += (int64_t)dl * drop_stride;
+  if (alpha_drop) alpha *= alpha_drop[dl];
   const int N = 2 * q + 2, P1 = p + 1, Q4 = N >> 2, h = N >> 1;
   float* A = smf32;          // [2][P1]
   float* tc = A + 2 * P1;    // [N]
@@ -187,7 +199,7 @@ __global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, 
   const float* Ac = A;
   const float* As = A + P1;
   const float s2 = 1.41421356f;
-  float* out = out32 + (int64_t)item * item_stride + (int64_t)j * N;
+  float* out = out32 + (int64_t)dl * drop_stride + (int64_t)ci * item_stride + (int64_t)j * N;
   const double* sc = scale + (int64_t)j * N;
   for (int k = threadIdx.x; k <= Q4; k += blockDim.x) {
     float ce = 0.f, co = 0.f, se = 0.f, so = 0.f;
@@ -224,12 +236,24 @@ __global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, 
 int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
                      int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
                      double alpha, float* out32, cudaStream_t s, float* out32lo) {
+  return sht_synth_drops(ctx, g, 1, n_items, coef, coef_stride, out, item_stride, 0, scale, alpha, nullptr, out32, s,
+                         out32lo);
+}
+
+// The same for nb consecutive drops of one degree in one launch: kpd items per drop, component c
+// of drop d at d drop_stride + c comp_stride in the value arrays, the scale at d drop_stride, the
+// factor alpha alpha_drop[d] (alpha_drop may be null).
+int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const double* coef, int64_t coef_stride,
+                    double* out, int64_t comp_stride, int64_t drop_stride, const double* scale, double alpha,
+                    const double* alpha_drop, float* out32, cudaStream_t s, float* out32lo) {
+  const int n_items = nb * kpd;
+  const int64_t item_stride = comp_stride;
   if (n_items <= 0) return SHBIM_OK;
   if (ctx->opts.precision == SHBIM_PREC_FP32_COMP && out32 && !out32lo && g.alf32 && ((2 * g.q + 2) & 3) == 0) {
     // only the FP32 copies are read in this mode: FP32 arithmetic
     const size_t smem32 = (size_t)(2 * (g.p + 1) + 2 * (2 * g.q + 2)) * sizeof(float);
     k_synth32<<<dim3(n_items, g.q + 1), 128, smem32, s>>>(coef, coef_stride, g.p, g.q, g.alf32, g.trig32, out32,
-                                                          item_stride, scale, alpha);
+                                                          item_stride, scale, alpha, kpd, drop_stride, alpha_drop);
     SHBIM_CHECK_LAUNCH(ctx, "k_synth32");
     return SHBIM_OK;
   }
@@ -237,7 +261,7 @@ int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const dou
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, 1, out, item_stride,
-                                  0, scale, alpha, out32, out32 ? out32lo : nullptr);
+                                  0, scale, alpha, out32, out32 ? out32lo : nullptr, kpd, drop_stride, alpha_drop);
   SHBIM_CHECK_LAUNCH(ctx, "k_synth");
   return SHBIM_OK;
 }
