@@ -99,6 +99,20 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
     const int64_t row = tm * kMT + r_loc;
     const bool rv = producer && row < rows;
     const float2* wrow = W + (rv ? row : 0) * nlon;
+    // eight values per K step (two per 16-byte load; nlon is a multiple of 4, so a pair lies wholly
+    // inside or wholly past the row), read two steps ahead; the first two steps are requested
+    // before the row scales arrive
+    auto load_step = [&](int ks, float4 (&v)[4]) {
+#pragma unroll
+      for (int i2 = 0; i2 < 4; ++i2) {
+        const int k = ks * kKS + half * 8 + 2 * i2;
+        v[i2] = (rv && ks < ksteps && k < nlon) ? *reinterpret_cast<const float4*>(wrow + k)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    float4 q0[4], q1[4];
+    load_step(0, q0);
+    load_step(1, q1);
     // the next tile's rows start moving from HBM into L2 now
     if (tid == kProducers && tm + gridDim.x < total) {
       const int64_t r1 = (tm + gridDim.x) * kMT;
@@ -133,26 +147,15 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
     bool bad = false;
     if (producer) {
       const float sc = __int_as_float((127 + 7 - rowexp[r_loc]) << 23);   // 2^(7 - e), exact
-      // eight values per K step (two per 16-byte load; nlon is a multiple of 4, so a pair lies
-      // wholly inside or wholly past the row), read one step ahead
-      float4 nxt[4];
-#pragma unroll
-      for (int i2 = 0; i2 < 4; ++i2) {
-        const int k = half * 8 + 2 * i2;
-        nxt[i2] = (rv && k < nlon) ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
       for (int ks = 0; ks < ksteps && !bad; ++ks) {
         const int st = ks & 1;
         float4 cur[4];
 #pragma unroll
-        for (int i2 = 0; i2 < 4; ++i2) cur[i2] = nxt[i2];
-        if (ks + 1 < ksteps) {
-#pragma unroll
-          for (int i2 = 0; i2 < 4; ++i2) {
-            const int k = (ks + 1) * kKS + half * 8 + 2 * i2;
-            nxt[i2] = (rv && k < nlon) ? *reinterpret_cast<const float4*>(wrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+        for (int i2 = 0; i2 < 4; ++i2) {
+          cur[i2] = q0[i2];
+          q0[i2] = q1[i2];
         }
+        load_step(ks + 2, q1);
         if (uses[st] > 0 && !mbar_wait(&empty[st], (uses[st] - 1) & 1)) {
           bad = true;
           break;
