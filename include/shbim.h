@@ -357,14 +357,17 @@ int shbim_set_autotune(shbim_ctx* ctx, int on);
 int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
 
 /* Tensor-core stages of the double-float row build (at the next shbim_set_drops), a bit mask:
- * SHBIM_TC_FOURIER, the GEMM of the rows' weights with the DFT table; SHBIM_TC_ROTATION, the
- * products with the quarter-turn blocks Dq_n in the pole rotations (degree p <= 39). Both split
+ * SHBIM_TC_FOURIER, the GEMM of the rows' weights with the DFT table; SHBIM_TC_LEGENDRE, the
+ * Legendre stage that follows it (used only together with SHBIM_TC_FOURIER); SHBIM_TC_ROTATION,
+ * the pole rotations, one GEMM per latitude and degree. All apply for degrees p <= 39. They split
  * their operands into bfloat16 digits whose products accumulate exactly (error ~2^-42 of the sum
  * of magnitudes per output). A stage that is off, or does not fit, runs as the double-float
- * FP32-pipe kernel. Default SHBIM_TC_ALL; any other bit is SHBIM_ERR_ARG. */
+ * FP32-pipe kernel. Default SHBIM_TC_FOURIER | SHBIM_TC_ROTATION (the tensor-core Legendre stage
+ * measured no faster than the FP32-pipe one at p = 32); any other bit is SHBIM_ERR_ARG. */
 #define SHBIM_TC_FOURIER 1
 #define SHBIM_TC_ROTATION 2
-#define SHBIM_TC_ALL 3
+#define SHBIM_TC_LEGENDRE 4
+#define SHBIM_TC_ALL 7
 int shbim_set_tensor_cores(shbim_ctx* ctx, int mask);
 
 /* Pipe throughput probes (a measurement utility for roofline denominators; the paper has no

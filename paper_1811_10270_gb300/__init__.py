@@ -30,7 +30,8 @@ SYS_STOKES = 1
 SYS_DIFFUSION = 2
 TC_FOURIER = 1
 TC_ROTATION = 2
-TC_ALL = 3
+TC_LEGENDRE = 4
+TC_ALL = 7
 CONTINUE = 0
 CONVERGED = 1
 
@@ -338,9 +339,9 @@ class Context:
         self._check(self._L.shbim_set_rows_precision(self._h, int(precision)), "shbim_set_rows_precision")
 
     def set_tensor_cores(self, on):
-        """Tensor-core stages of the row build: True (all), False (none) or a mask of TC_FOURIER
-        and TC_ROTATION."""
-        mask = (TC_ALL if on else 0) if isinstance(on, bool) else int(on)
+        """Tensor-core stages of the row build: True (the default set, TC_FOURIER | TC_ROTATION),
+        False (none) or a mask of TC_FOURIER, TC_ROTATION and TC_LEGENDRE."""
+        mask = ((TC_FOURIER | TC_ROTATION) if on else 0) if isinstance(on, bool) else int(on)
         self._check(self._L.shbim_set_tensor_cores(self._h, mask), "shbim_set_tensor_cores")
 
     def set_autotune(self, on: bool):

@@ -217,6 +217,7 @@ int shbim_set_tensor_cores(shbim_ctx* ctx, int mask) {
   if (mask & ~SHBIM_TC_ALL) return fail(ctx, SHBIM_ERR_ARG, "unknown tensor-core stage bit");
   ctx->tc_rows = (mask & SHBIM_TC_FOURIER) != 0;
   ctx->tc_rot = (mask & SHBIM_TC_ROTATION) != 0;
+  ctx->tc_leg = (mask & SHBIM_TC_LEGENDRE) != 0;
   return SHBIM_OK;
 }
 

@@ -2,6 +2,7 @@
 // tensor cores, with FP64-class accuracy.
 //
 // F[r][o] = sum_k W[r][k] T[o][k], T[o][k] = cos(m phi_k) (o = m <= p) or sin(m phi_k)
+// (stored row-major, or order-major F[o][r] for the tensor-core Legendre stage)
 // (o = p+1+m), phi_k = 2 pi k / (2q+2): a GEMM with the row count of a chunk of weights
 // (targets x 14 components x latitudes) and a fixed table. Every double-float value is split,
 // after scaling by a power of two per row (per table for T), into six integer digits exactly
@@ -52,7 +53,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const uint4* __restrict__ tdig,
-         int ksteps, const int* __restrict__ rexp, float2* __restrict__ F, int* __restrict__ err) {
+         int ksteps, const int* __restrict__ rexp, float2* __restrict__ F, int omajor, int* __restrict__ err) {
   // dynamic shared memory: [the table's digit planes for every K step, resident][two stages of row
   // digit planes]
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -245,7 +246,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
           if (rowe < rows && o < nout) {
             const dfl::df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
                                        __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));
-            F[rowe * nout + o] = scale2(r, ee - 13);
+            F[omajor ? (int64_t)o * rows + rowe : rowe * nout + o] = scale2(r, ee - 13);
           }
         }
       }
@@ -306,7 +307,7 @@ int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T) {
 }
 
 int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, const int* rexp,
-                        float2* F, cudaStream_t s) {
+                        float2* F, cudaStream_t s, bool omajor) {
   if (rows <= 0) return SHBIM_OK;
   if (!ctx->tc_err) {
     if (cudaMalloc(&ctx->tc_err, sizeof(int)) != cudaSuccess)
@@ -324,7 +325,7 @@ int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, 
   const int64_t tiles = (rows + kMT - 1) / kMT;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
   k_dft_tc<<<grid, kThreadsTC, smem, s>>>(W, rows, nlon, nout, reinterpret_cast<const uint4*>(T.dft_digits),
-                                          T.dft_ksteps, rexp, F, ctx->tc_err);
+                                          T.dft_ksteps, rexp, F, omajor ? 1 : 0, ctx->tc_err);
   SHBIM_CHECK_LAUNCH(ctx, "k_dft_tc");
   return SHBIM_OK;
 }

@@ -78,6 +78,11 @@ struct DegreeTables {
   uint16_t* rot_digits = nullptr;
   int* rot_toff = nullptr;
   signed char* rot_exp = nullptr;   // [2][p+1][(p+1)^2] row exponents of the tables
+  // digit planes of Pbar_n^m at the degree 2p+1 grid latitudes for the tensor-core Legendre stage
+  // (leg_tc.cu), p <= 39: [m][K step][digit][Np x 16], offsets per m, row exponents [m][p+1]
+  uint16_t* leg_digits = nullptr;
+  int* leg_toff = nullptr;
+  signed char* leg_exp = nullptr;
 };
 
 struct Drop {
@@ -162,6 +167,7 @@ struct shbim_ctx {
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
   bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
   bool tc_rot = true;             // ... and the degree-block rotations (rot_tc.cu)
+  bool tc_leg = false;            // ... and the Legendre stage of the analysis (leg_tc.cu; opt-in)
   int* tc_err = nullptr;          // device flag: a tensor-core kernel timed out
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
@@ -362,7 +368,11 @@ int dft_tc_digits(shbim_ctx* ctx, int p, DegreeTables& T);
 // the kernel holds a 128-row tile of W in shared memory: degrees up to 34
 bool dft_tc_fits(int p);
 int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, int64_t rows, const int* rexp,
-                        float2* F, cudaStream_t s);
+                        float2* F, cudaStream_t s, bool omajor = false);
+bool leg_tc_fits(int p);
+int leg_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& alf0, DegreeTables& T);
+int analysis_legendre_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* FT, int64_t nitems, float2* coef,
+                         int64_t coef_stride, cudaStream_t s);
 
 // ---- shape-dependent state for an unchanged layout (api.cu)
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);

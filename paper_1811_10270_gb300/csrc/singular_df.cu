@@ -605,6 +605,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int leg_smem = (d.q + 1) * 2 * (d.p + 1) * (int)sizeof(float2);
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_analysis_leg_item_df, cudaFuncAttributeMaxDynamicSharedMemorySize, leg_smem));
     const bool dft_tc = ctx->tc_rows && dft_tc_fits(d.p);
+    const bool leg_tc = dft_tc && ctx->tc_leg && leg_tc_fits(d.p);   // reads the order-major Fourier output
     // row exponents of the weights for the tensor-core analysis, written by the weights kernel
     int* rexp = nullptr;
     if (dft_tc) {
@@ -636,15 +637,21 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
       {
         TimeScope ts(ctx, SHBIM_K_SELF_ANALYSIS, s);
         const int64_t nrows = (int64_t)ct * ncomp * (d.q + 1);
-        if (dft_tc) {
+        if (leg_tc) {
+          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, s, true)) ||
+              (rc = analysis_legendre_tc(ctx, *d.tab, F, (int64_t)ct * ncomp, vb, nc, s)))
+            return rc;
+        } else if (dft_tc) {
           if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, s))) return rc;
         } else {
           k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, s>>>(wb, Ns, d.p, d.q,
                                                                                     d.tab->up_trig_df, nrows, rows, F);
           SHBIM_CHECK_LAUNCH(ctx, "k_analysis_f4_df");
         }
-        k_analysis_leg_item_df<<<ct * ncomp, 288, leg_smem, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
-        SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_item_df");
+        if (!leg_tc) {
+          k_analysis_leg_item_df<<<ct * ncomp, 288, leg_smem, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
+          SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_item_df");
+        }
       }
       {
         TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, s);
@@ -661,7 +668,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
       }
     }
   }
-  if ((ctx->tc_rows || ctx->tc_rot) && ctx->tc_err) {
+  if ((ctx->tc_rows || ctx->tc_rot || ctx->tc_leg) && ctx->tc_err) {
     int flag = 0;
     SHBIM_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     SHBIM_CUDA(ctx, cudaStreamSynchronize(s));

@@ -108,7 +108,7 @@ int upload_f(shbim_ctx* ctx, float** dst, const std::vector<float>& src) {
 // alf_df / trig_df (optional): double-float copies of the kinds 0..2 and of the trig table;
 // f32: FP32 copies of kind 0 and of the trig table
 int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g, float2** alf_df = nullptr,
-               float2** trig_df = nullptr, bool f32 = false) {
+               float2** trig_df = nullptr, bool f32 = false, std::vector<double>* alf0_out = nullptr) {
   g.p = p;
   g.q = q;
   std::vector<double> t, wg;
@@ -158,6 +158,11 @@ int build_grid(shbim_ctx* ctx, int p, int q, GridTables& g, float2** alf_df = nu
     trig[N + k] = std::sin(2.0 * kPi * k / N);
   }
   int rc;
+  if (alf0_out) {
+    alf0_out->assign((size_t)(q + 1) * nt, 0.0);
+    for (int j = 0; j <= q; ++j)
+      for (int o = 0; o < nt; ++o) (*alf0_out)[(size_t)j * nt + o] = alf[(size_t)j * kNumTab * nt + o];
+  }
   if (alf_df) {
     std::vector<float2> a((size_t)(q + 1) * 3 * nt);
     for (int j = 0; j <= q; ++j)
@@ -324,8 +329,10 @@ int build_degree_tables(shbim_ctx* ctx, int p, DegreeTables** out) {
   DegreeTables* T = new DegreeTables();
   T->p = p;
   int rc;
+  std::vector<double> alf_up;
   if ((rc = build_grid(ctx, p, p, T->base)) ||
-      (rc = build_grid(ctx, p, 2 * p + 1, T->up, &T->up_alf_df, &T->up_trig_df, true)) ||
+      (rc = build_grid(ctx, p, 2 * p + 1, T->up, &T->up_alf_df, &T->up_trig_df, true, &alf_up)) ||
+      (rc = leg_tc_digits(ctx, p, alf_up, *T)) ||
       (rc = build_grid(ctx, p, 4 * (2 * p + 2) - 1, T->fine, nullptr, nullptr, true)) || (rc = build_rotation(ctx, p, *T)) ||
       (rc = dft_tc_digits(ctx, p, *T))) {
     free_degree_tables(T);
@@ -362,6 +369,9 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->rot_digits);
   cudaFree(t->rot_toff);
   cudaFree(t->rot_exp);
+  cudaFree(t->leg_digits);
+  cudaFree(t->leg_toff);
+  cudaFree(t->leg_exp);
   cudaFree(t->cs_theta_df);
   cudaFree(t->cs_phi_df);
   delete t;

@@ -229,9 +229,9 @@ def test_three_drops_uneven_degrees_match_oracle(S):
 
 
 def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
-    """The singular self rows built in double-float arithmetic (the default, with the Fourier stage
-    and the rotations on the tensor cores; each alone; neither) against the rows of the FP64 build
-    and the oracle, on one perturbed drop (self term only) and on two drops."""
+    """The singular self rows built in double-float arithmetic (the default, with the Fourier and
+    Legendre stages and the rotations on the tensor cores; subsets; none) against the rows of the
+    FP64 build and the oracle, on one perturbed drop (self term only) and on two drops."""
     rng = np.random.default_rng(31)
     one = [inputs.Drop(11, inputs.perturbed_coef(11, rng, 1.0, (0.1, -0.2, 0.3)), np.zeros(sh.ncoef(11)),
                        2.5, np.array([0.1, -0.2, 0.3]), 1.0)]
@@ -242,7 +242,8 @@ def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
         sig = [inputs.random_density(d.p, rng)[0] for d in drops]
         u = [inputs.random_density(d.p, rng, 3) for d in drops]
         res = {}
-        variants = ((S.FP64, 0), (S.DF64, 0), (S.DF64, S.TC_FOURIER), (S.DF64, S.TC_ROTATION), (S.DF64, S.TC_ALL))
+        variants = ((S.FP64, 0), (S.DF64, 0), (S.DF64, S.TC_FOURIER), (S.DF64, S.TC_FOURIER | S.TC_LEGENDRE),
+                    (S.DF64, S.TC_ROTATION), (S.DF64, S.TC_ALL))
         for rows, tc in variants:
             ctx = S.Context(precision=S.FP64, R=2.0, gmres_tol=1e-12)
             ctx.set_rows_precision(rows)
