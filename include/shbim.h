@@ -252,20 +252,22 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, cons
                double dt, double* x_out_dev, double* gamma_out_dev, double* err_host, int* iters_host,
                void* stream);
 
-/* Mixed-precision solve by iterative refinement: every outer step forms the residual
- * r = b - A x with FP64 all-pairs sums, solves A d = r by GMRES with FP32 compensated sums to
- * the relative tolerance inner_tol (e.g. 1e-5), and updates x += d, until the FP64 relative
- * residual reaches gmres_tol or max_outer steps were taken (SHBIM_ERR_NOT_CONVERGED).
- * The outer residuals use the context's outer precision (shbim_set_outer_precision).
- * Only the electric and Stokes systems (the diffusion system has no all-pairs sums;
- * SHBIM_ERR_ARG). The context's precision setting is restored on return. Reports the total inner Arnoldi
- * steps, the outer steps and the final FP64 relative residual (each pointer may be NULL). */
 /* FP64-class arithmetic used where mixed precision needs it: the residuals of
  * shbim_gmres_solve_refined and the one-shot applications of shbim_rates / shbim_step in
  * SHBIM_PREC_FP32_COMP mode. SHBIM_PREC_DF64 (default: double-float on the FP32 pipe) or
  * SHBIM_PREC_FP64 (native); SHBIM_ERR_ARG otherwise. */
 int shbim_set_outer_precision(shbim_ctx* ctx, int precision);
 
+/* Mixed-precision solve by iterative refinement: every outer step forms the residual
+ * r = b - A x with FP64-class all-pairs sums, solves A d = r by GMRES with FP32 compensated sums,
+ * and updates x += d, until the FP64-class relative residual reaches gmres_tol or max_outer steps
+ * were taken (SHBIM_ERR_NOT_CONVERGED). The inner relative tolerance is inner_tol (e.g. 1e-5),
+ * except where the step can finish the solve: then it is 0.5 gmres_tol / (current relative
+ * residual), looser than inner_tol on the last step, and down to inner_tol / 20 after a good
+ * initial guess. The outer residuals use the context's outer precision (shbim_set_outer_precision).
+ * Only the electric and Stokes systems (the diffusion system has no all-pairs sums;
+ * SHBIM_ERR_ARG). The context's precision setting is restored on return. Reports the total inner Arnoldi
+ * steps, the outer steps and the final FP64 relative residual (each pointer may be NULL). */
 int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                               double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
                               int* outer_iters_host, double* resid_host, void* stream);

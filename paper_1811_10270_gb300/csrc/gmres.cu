@@ -568,9 +568,14 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
       rc = fail(ctx, SHBIM_ERR_NOT_CONVERGED, "refinement reached max_outer");
       break;
     }
-    // inner solve A d = r with FP32 sums
+    // inner solve A d = r with FP32 sums. The tolerance that would finish in this step is
+    // 0.5 tol / rel: when it is looser than inner_tol (typically the last step) it is used as is;
+    // when it is tighter but within a factor 20 (a good initial guess) it is used too, so the solve
+    // ends one outer step earlier; otherwise the step reduces the residual by inner_tol.
+    const double need = 0.5 * tol / rel;
+    const double tau = need >= inner_tol ? std::min(need, 0.5) : (need >= 0.05 * inner_tol ? need : inner_tol);
     ctx->opts.precision = SHBIM_PREC_FP32_COMP;
-    ctx->opts.gmres_tol = inner_tol;
+    ctx->opts.gmres_tol = tau;
     int it = 0;
     rc = shbim_gmres_solve(ctx, sys, G.rr, nullptr, G.dr, &it, nullptr, stream);
     ctx->opts.gmres_tol = saved_tol;
