@@ -35,9 +35,10 @@ import inputs  # noqa: E402
 METRIC = "target-source kernel pairs/s, GMRES time-to-1e-8 per step: mixed/batched vs FP64"
 UNIT = "pairs/s"
 FP64_PEAK_TFLOPS = 1.25         # GB300 FP64 rate (vector and tensor), see the design doc
-# DRAM bytes per launch from one ncu capture of the same kernel and workload (profiles/);
-# None once the kernel has changed since the capture.
-TRAFFIC = {"self_weights": 8154624 + 211138560}
+# DRAM bytes (read + write) per launch from one ncu capture of the same kernel and workload
+# (profiles/row_build_kernels_two_drops_p32.md: launches of 1 100 and 1 078 targets, mean); to be
+# dropped once the kernel changes after the capture.
+TRAFFIC = {"self_weights_df": 1.175e9}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 

@@ -60,7 +60,6 @@ struct DegreeTables {
   float2* up_alf_df = nullptr;   // [2p+2 latitudes][3][ntri(p)]: Pbar, dPbar/dtheta, m Pbar/sin
   float2* up_trig_df = nullptr;  // [2][4p+4]: cos, sin of 2 pi k / (4p+4)
   float2* dq_df = nullptr;       // as dq
-  float2* dqT_df = nullptr;      // per degree block transposed (coalesced reads for Dq x)
   // nonzero pattern of the Dq blocks (about a quarter of the entries; parity structure of the
   // quarter turn): per row and per column of every block, the nonzero entries as an arithmetic
   // progression (start, count, step) of column (row) indices, indexed like the coefficients

@@ -6,12 +6,13 @@
 //      kernel weights mu J K / (4 pi) at every node (Laplace DL and SL, 6 Stokeslet and 6
 //      stresslet components);
 //   3. analyse the weights (Fourier stage on the tensor cores, dft_tc.cu, or folded four ways in
-//      double-float; then the Legendre stage);
+//      double-float; then the Legendre stage, here or, opt-in, on the tensor cores, leg_tc.cu);
 //   4. rotate the coefficient rows back (row = D_R v) and store them as (hi, lo) FP32 planes.
 // The rotations of steps 1 and 4 run on the tensor cores (rot_tc.cu) where the degree fits.
-// Every sum and every pointwise operation is double-float (hi + lo FP32 pairs; Dekker products,
-// Knuth sums, Newton square roots), ~2^-44 relative per operation, so the rows agree with the
-// FP64 build to rounding level while the FP64 pipe (1/64 of the FP32 rate here) stays idle.
+// Every sum and every pointwise operation here is double-float (hi + lo FP32 pairs; Dekker
+// products, Knuth sums, Newton square roots), ~2^-44 relative per operation; the tensor-core stages
+// split their operands into exact digit products (~2^-42 of the sum of magnitudes). The rows agree
+// with the FP64 build to rounding level while the FP64 pipe (1/64 of the FP32 rate here) stays idle.
 #include <algorithm>
 
 #include "dfloat.cuh"
@@ -30,110 +31,11 @@ __device__ __forceinline__ df ld(const float2* p, int64_t i) {
 }
 __device__ __forceinline__ void st(float2* p, int64_t i, df v) { p[i] = make_float2(v.hi, v.lo); }
 
-__device__ __forceinline__ int isqrt_i(int o) {
-  int n = (int)sqrtf((float)o);
-  while ((n + 1) * (n + 1) <= o) ++n;
-  while (n * n > o) --n;
-  return n;
-}
-
 __device__ __forceinline__ int tri_off_i(int p, int m) { return m * (p + 1) - m * (m - 1) / 2; }
-
-// v <- Dz(sgn alpha) v with the (cos, sin)(m alpha) table cs = [2][p+1]
-__device__ void dz_df(float2* v, int p, const float2* __restrict__ cs, float sgn) {
-  const int nc = (p + 1) * (p + 1);
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
-    const int n = isqrt_i(o);
-    const int m = o - n * n - n;
-    if (m <= 0) continue;
-    const df ca = ld(cs, m);
-    df sa = ld(cs, p + 1 + m);
-    if (sgn < 0) sa = dfl::neg(sa);
-    const df a = ld(v, o), b = ld(v, o - 2 * m);
-    st(v, o, dfl::sub(dfl::mul(ca, a), dfl::mul(sa, b)));
-    st(v, o - 2 * m, dfl::add(dfl::mul(sa, a), dfl::mul(ca, b)));
-  }
-}
-
-// out <- Dq in (transpose: Dq^T in), per degree block. Both products read a column of a stored
-// block (Dq^T for the plain product, Dq for the transposed one), so the threads of a warp, which
-// hold consecutive orders m, read consecutive addresses.
-__device__ void dq_df(const float2* __restrict__ in, float2* __restrict__ out, int p, const float2* __restrict__ dq,
-                      const float2* __restrict__ dqT, const int* __restrict__ dq_off, bool transpose) {
-  const int nc = (p + 1) * (p + 1);
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
-    const int n = isqrt_i(o);
-    const int m = o - n * n - n;
-    const int w = 2 * n + 1;
-    const float2* col = (transpose ? dq : dqT) + dq_off[n] + (m + n);
-    const float2* x = in + n * n;
-    dfl::acc acc;
-    for (int c = 0; c < w; ++c) acc.add_prod(ld(col, (int64_t)c * w), ld(x, c));
-    st(out, o, acc.value());
-  }
-}
 
 __global__ void k_to_df(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) st(out, e, dfl::from_double(x[e]));
-}
-
-// b = D_R^T a for the position coefficients (double-float copy) of target blockIdx.x, component
-// blockIdx.y
-__global__ void k_rotate_fwd_df(const float2* __restrict__ xc, int nc, int p, int t_begin,
-                                const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
-                                const float2* __restrict__ dq, const float2* __restrict__ dqT,
-                                const int* __restrict__ dq_off, float2* __restrict__ out) {
-  extern __shared__ float2 smf[];
-  float2* b0 = smf;
-  float2* b1 = smf + nc;
-  const int tl = t_begin + blockIdx.x;
-  const int f = blockIdx.y;
-  const int nlon = 2 * p + 2;
-  const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
-  const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) b0[o] = xc[(int64_t)f * nc + o];
-  __syncthreads();
-  dz_df(b0, p, cp, -1.f);
-  __syncthreads();
-  dq_df(b0, b1, p, dq, dqT, dq_off, false);
-  __syncthreads();
-  dz_df(b1, p, ct, -1.f);
-  __syncthreads();
-  dq_df(b1, out + ((int64_t)blockIdx.x * 3 + f) * nc, p, dq, dqT, dq_off, true);
-}
-
-// row = D_R v for target blockIdx.x and component blockIdx.y; stored in FP64
-__global__ void k_rotate_adj_df(const float2* __restrict__ vbuf, int nc, int p, int t_begin, int ncomp,
-                                const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
-                                const float2* __restrict__ dq, const float2* __restrict__ dqT,
-                                const int* __restrict__ dq_off, float* __restrict__ rows_lap,
-                                float* __restrict__ rows_sto, int nt_drop) {
-  extern __shared__ float2 smf[];
-  float2* b0 = smf;
-  float2* b1 = smf + nc;
-  const int tl = t_begin + blockIdx.x;
-  const int c = blockIdx.y;
-  const int nlon = 2 * p + 2;
-  const float2* ct = cs_theta + (int64_t)(tl / nlon) * 2 * (p + 1);
-  const float2* cp = cs_phi + (int64_t)(tl % nlon) * 2 * (p + 1);
-  const float2* v = vbuf + ((int64_t)blockIdx.x * ncomp + c) * nc;
-  dq_df(v, b1, p, dq, dqT, dq_off, false);
-  __syncthreads();
-  dz_df(b1, p, ct, 1.f);
-  __syncthreads();
-  dq_df(b1, b0, p, dq, dqT, dq_off, true);
-  __syncthreads();
-  dz_df(b0, p, cp, 1.f);
-  __syncthreads();
-  float* dst = c < kNumLap ? rows_lap + ((int64_t)tl * kNumLap + c) * nc
-                           : rows_sto + ((int64_t)tl * kNumSto + (c - kNumLap)) * nc;
-  const int64_t plane = (int64_t)nt_drop * (c < kNumLap ? kNumLap : kNumSto) * nc;
-  for (int o = threadIdx.x; o < nc; o += blockDim.x) {
-    const df v = ld(b0, o);     // already normalised: hi = fl32(value), |lo| <= ulp(hi) / 2
-    dst[o] = v.hi;
-    dst[plane + o] = v.lo;
-  }
 }
 
 // Rotation of all components of TPB targets per CTA, degree by degree: every stage of
@@ -579,7 +481,6 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     float2* xc = reinterpret_cast<float2*>(ctx->xdf);
     k_to_df<<<(unsigned)((3 * nc + 255) / 256), 256, 0, s>>>(xcoef + 3 * d.coef_off, 3 * nc, xc);
     SHBIM_CHECK_LAUNCH(ctx, "k_to_df");
-    const int rot_smem = 2 * nc * (int)sizeof(float2);
     const int wmax = 2 * d.p + 1;
     // targets per CTA of the rotations: as many as fit beside the Dq block in ~100 KB
     const int per_t3 = 2 * 3 * wmax * (int)sizeof(float2), per_t14 = 2 * ncomp * wmax * (int)sizeof(float2);
@@ -595,8 +496,6 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int deg_smem14 = dq_bytes + tpb14 * per_t14;
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_deg_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, deg_smem3));
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_deg_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, deg_smem14));
-    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_fwd_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
-    SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_adj_df, cudaFuncAttributeMaxDynamicSharedMemorySize, rot_smem));
     const size_t w_smem = (size_t)(18 * (d.p + 1) + 11 * N) * sizeof(float2);
     const int budget = 46 * 1024 / (int)sizeof(float2) - 2 * N;
     const int rows = std::max(1, std::min(8, budget / (2 * N)));

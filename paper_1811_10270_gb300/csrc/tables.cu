@@ -257,14 +257,9 @@ int build_rotation(shbim_ctx* ctx, int p, DegreeTables& T) {
   int rc = upload(ctx, &T.dq, D);
   if (rc) return rc;
   {
-    std::vector<float2> Ddf(D.size()), DTdf(D.size());
+    std::vector<float2> Ddf(D.size());
     for (size_t i = 0; i < D.size(); ++i) Ddf[i] = split_df(D[i]);
-    for (int n = 0; n <= p; ++n) {
-      const int w = 2 * n + 1, o = T.dq_off[n];
-      for (int a = 0; a < w; ++a)
-        for (int b = 0; b < w; ++b) DTdf[o + b * w + a] = Ddf[o + a * w + b];
-    }
-    if ((rc = upload_df(ctx, &T.dq_df, Ddf)) || (rc = upload_df(ctx, &T.dqT_df, DTdf))) return rc;
+    if ((rc = upload_df(ctx, &T.dq_df, Ddf))) return rc;
     // nonzero progressions of every row and column (zeros of the block are exact, the quadrature
     // leaves rounding noise far below the threshold); a row that is not a progression is dense
     std::vector<int4> rows((size_t)(p + 1) * (p + 1)), cols((size_t)(p + 1) * (p + 1));
@@ -362,7 +357,6 @@ void free_degree_tables(DegreeTables* t) {
   cudaFree(t->up_alf_df);
   cudaFree(t->up_trig_df);
   cudaFree(t->dq_df);
-  cudaFree(t->dqT_df);
   cudaFree(t->dq_rows);
   cudaFree(t->dq_cols);
   cudaFree(t->dft_digits);
