@@ -335,14 +335,17 @@ int64_t shbim_launch_count(shbim_ctx* ctx);
  * fails, the context falls back to direct launches. */
 int shbim_set_graphs(shbim_ctx* ctx, int on);
 
-/* Concurrent branches inside one operator application (on by default; used with two or more
- * drops): the singular self rows and the near-field correction run on a second stream owned by
- * the library while the caller's stream synthesises the source strengths and runs the
- * all-pairs sums, which are added into the output after the two branches join. The side stream
- * waits for everything queued earlier on the caller's stream and the caller's stream waits for
- * the side stream before the call's last kernels, so the call behaves as if it ran on the
- * caller's stream alone. The order in which the three contributions are added differs from the
- * serial order (off), which changes results only by rounding. */
+/* Concurrency on a second stream owned by the library (on by default):
+ * - inside one operator application (two or more drops): the singular self rows and the
+ *   near-field correction run on the side stream while the caller's stream synthesises the source
+ *   strengths and runs the all-pairs sums, which are added into the output after the two branches
+ *   join; the order in which the three contributions are added differs from the serial order,
+ *   which changes results only by rounding;
+ * - in the double-float singular-row build (two or more chunks of targets): every other chunk runs
+ *   on the side stream with its own work buffers (the same rows, bit for bit).
+ * The side stream waits for everything queued earlier on the caller's stream and the caller's
+ * stream waits for the side stream before the call's last kernels, so each call behaves as if it
+ * ran on the caller's stream alone. Off: everything on the caller's stream. */
 int shbim_set_concurrency(shbim_ctx* ctx, int on);
 
 /* Launch-shape autotuning of the FP32 all-pairs kernels (on by default): on the first launch of

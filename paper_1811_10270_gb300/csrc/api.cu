@@ -171,8 +171,14 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->phys.state);
   cudaFree(ctx->phys.lb);
   cudaFree(ctx->dens_split);
-  cudaFree(ctx->xdf);
-  cudaFree(ctx->rexp);
+  for (auto& L : ctx->lanes) {
+    cudaFree(L.rot);
+    cudaFree(L.w);
+    cudaFree(L.v);
+    cudaFree(L.F);
+    cudaFree(L.xdf);
+    cudaFree(L.rexp);
+  }
   cudaFree(ctx->tc_err);
   cudaFree(ctx->gm.xr);
   cudaFree(ctx->gm.rr);
@@ -449,6 +455,20 @@ int same_degree_run(const shbim_ctx* ctx, size_t a) {
   return (int)(b - a);
 }
 
+}  // namespace
+
+int ensure_side_stream(shbim_ctx* ctx) {
+  if (ctx->side) return SHBIM_OK;
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_coarse, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_fail(ctx, cudaGetLastError(), "side stream");
+  return SHBIM_OK;
+}
+
+namespace {
+
 // Streams of one operator application. With two or more drops and concurrency on, the self rows
 // (which overwrite the output values) and then the near-field correction (which adds into them)
 // run on the library's side stream while the caller's stream synthesises the strengths and runs
@@ -462,13 +482,7 @@ struct Branches {
 int fork_branches(shbim_ctx* ctx, cudaStream_t s, Branches* br) {
   br->side = s;
   if (ctx->n_drops < 2 || !ctx->concurrent) return SHBIM_OK;
-  if (!ctx->side) {
-    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_coarse, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
-      return cuda_fail(ctx, cudaGetLastError(), "side stream");
-  }
+  if (int rc = ensure_side_stream(ctx)) return rc;
   SHBIM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
   SHBIM_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
   br->side = ctx->side;

@@ -156,10 +156,14 @@ struct shbim_ctx {
   } pair_cfg[3];
   int* pair_queue = nullptr;      // [2] work counter and finished-CTA count (zero between launches)
   bool autotune = true;           // off: every layout keeps the default launch shape
-  double* xdf = nullptr;          // position coefficients of one drop as double-float (row build)
-  size_t xdf_cap = 0;
-  double* rexp = nullptr;         // int row exponents of a chunk of weights (row build), as doubles' storage
-  size_t rexp_cap = 0;
+  // the double-float row build's two lanes (chunks alternate between the caller's stream and the
+  // side stream): per lane the rotated positions, weights, Fourier output, rows, position copy
+  // (of drop xdrop) and row exponents, sized in doubles
+  struct RowLane {
+    double *rot = nullptr, *w = nullptr, *F = nullptr, *v = nullptr, *xdf = nullptr, *rexp = nullptr;
+    size_t rot_n = 0, w_n = 0, F_n = 0, v_n = 0, xdf_n = 0, rexp_n = 0;
+    int xdrop = -1;
+  } lanes[2];
   float* dens_split = nullptr;    // [2][3 ncoef] hi / lo planes of a density for the self GEMV
   size_t dens_split_cap = 0;
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
@@ -333,6 +337,7 @@ int build_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 int build_singular_rows(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 // the same rows computed in double-float arithmetic on the FP32 pipe (singular_df.cu)
 int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef_dev);
+int ensure_side_stream(shbim_ctx* ctx);
 // out[t] (+)= self rows . density for every target (scalar Laplace kind or Stokes tensors).
 int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* out, cudaStream_t s);
 int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* out,

@@ -450,45 +450,64 @@ int ensure_d(shbim_ctx* ctx, double** buf, size_t* cap, size_t need, const char*
 // a float2 occupies the bytes of one double).
 int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) {
   const int ncomp = kNumLap + kNumSto;
+  int rc;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // chunks of targets (weights of at most 1 GB) and the lane buffers sized for the largest drop
+  auto chunk_of = [&](const Drop& d) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(d.nt, (1024ll << 20) / (ncomp * (int64_t)d.ns * 8)));
+  };
+  size_t need_rot = 0, need_w = 0, need_F = 0, need_v = 0, need_x = 0, need_e = 0;
+  int chunks = 0;
   for (auto& d : ctx->drops) {
+    if ((2 * d.q + 2) % 4) return fail(ctx, SHBIM_ERR_ARG, "double-float row build needs 4 | 2q+2");
+    const size_t CT = (size_t)chunk_of(d);
+    need_rot = std::max(need_rot, CT * 3 * d.nc);
+    need_w = std::max(need_w, CT * ncomp * d.ns);
+    need_F = std::max(need_F, CT * ncomp * (d.q + 1) * 2 * (d.p + 1));
+    need_v = std::max(need_v, CT * ncomp * d.nc);
+    need_x = std::max(need_x, (size_t)3 * d.nc);
+    need_e = std::max(need_e, (CT * ncomp * (d.q + 1) + 1) / 2);
+    chunks += (int)((d.nt + CT - 1) / CT);
+  }
+  // with two or more chunks, odd chunks run on the library's side stream, each lane with its own
+  // buffers: the latency-bound tensor-core stages of one chunk overlap the FP32-pipe stages of the
+  // other; the side lane starts after everything queued on s, and s waits for it at the end
+  const bool two = ctx->concurrent && chunks > 1;
+  cudaStream_t ls[2] = {s, s};
+  if (two) {
+    if ((rc = ensure_side_stream(ctx))) return rc;
+    ls[1] = ctx->side;
+  }
+  for (int l = 0; l < (two ? 2 : 1); ++l) {
+    auto& L = ctx->lanes[l];
+    if ((rc = ensure_d(ctx, &L.rot, &L.rot_n, need_rot, "rotation buffer")) ||
+        (rc = ensure_d(ctx, &L.w, &L.w_n, need_w, "weight buffer")) ||
+        (rc = ensure_d(ctx, &L.F, &L.F_n, need_F, "Fourier buffer")) ||
+        (rc = ensure_d(ctx, &L.v, &L.v_n, need_v, "row buffer")) ||
+        (rc = ensure_d(ctx, &L.xdf, &L.xdf_n, need_x, "position copy")) ||
+        (rc = ensure_d(ctx, &L.rexp, &L.rexp_n, need_e, "row exponents")))
+      return rc;
+    L.xdrop = -1;
+  }
+  if (two) {
+    SHBIM_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+    SHBIM_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  }
+  int c = 0;
+  for (size_t di = 0; di < ctx->drops.size(); ++di) {
+    const Drop& d = ctx->drops[di];
     const GridTables& up = d.tab->up;
     const int64_t Ns = d.ns;
     const int nc = d.nc;
     const int N = 2 * d.q + 2;
-    if (N % 4) return fail(ctx, SHBIM_ERR_ARG, "double-float row build needs 4 | 2q+2");
-    int CT = (int)std::max<int64_t>(1, std::min<int64_t>(d.nt, (1024ll << 20) / (ncomp * Ns * 8)));
-    int rc;
-    if ((rc = ensure_d(ctx, &ctx->rot_coef, &ctx->rot_elems, (size_t)CT * 3 * nc, "rotation buffer")) ||
-        (rc = ensure_d(ctx, &ctx->wbuf, &ctx->wbuf_elems, (size_t)CT * ncomp * Ns, "weight buffer")) ||
-        (rc = ensure_d(ctx, &ctx->vbuf, &ctx->vbuf_elems, (size_t)CT * ncomp * nc, "row buffer")))
-      return rc;
-    const size_t need = (size_t)CT * ncomp * (d.q + 1) * 2 * (d.p + 1);
-    if (need > ctx->sht_scratch_elems) {
-      SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
-      cudaFree(ctx->sht_scratch);
-      ctx->sht_scratch = nullptr;
-      ctx->sht_scratch_elems = 0;
-      if (cudaMalloc(&ctx->sht_scratch, need * sizeof(double)) != cudaSuccess)
-        return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc transform scratch");
-      ctx->sht_scratch_elems = need;
-      ctx->geom_version++;
-    }
-    float2* rot = reinterpret_cast<float2*>(ctx->rot_coef);
-    float2* wb = reinterpret_cast<float2*>(ctx->wbuf);
-    float2* vb = reinterpret_cast<float2*>(ctx->vbuf);
-    float2* F = reinterpret_cast<float2*>(ctx->sht_scratch);
-    if ((rc = ensure_d(ctx, &ctx->xdf, &ctx->xdf_cap, (size_t)3 * nc, "position copy"))) return rc;
-    float2* xc = reinterpret_cast<float2*>(ctx->xdf);
-    k_to_df<<<(unsigned)((3 * nc + 255) / 256), 256, 0, s>>>(xcoef + 3 * d.coef_off, 3 * nc, xc);
-    SHBIM_CHECK_LAUNCH(ctx, "k_to_df");
+    const int CT = chunk_of(d);
     const int wmax = 2 * d.p + 1;
-    // targets per CTA of the rotations: as many as fit beside the Dq block in ~100 KB
+    // targets per CTA of the FP32-pipe rotations: as many as fit beside the Dq block in ~100 KB,
+    // and no more than keeps at least two CTAs per SM busy for a chunk of CT targets
     const int per_t3 = 2 * 3 * wmax * (int)sizeof(float2), per_t14 = 2 * ncomp * wmax * (int)sizeof(float2);
     const int dq_bytes = wmax * wmax * (int)sizeof(float2);
-    // ... and no more than keeps at least two CTAs per SM busy for a chunk of CT targets
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int occ = std::max(1, CT / (2 * nsm));
     const int tpb3 = std::max(1, std::min({16, (100 * 1024 - dq_bytes) / per_t3, occ}));
     const int tpb14 = std::max(1, std::min({8, (100 * 1024 - dq_bytes) / per_t14, occ}));
@@ -505,67 +524,79 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_analysis_leg_item_df, cudaFuncAttributeMaxDynamicSharedMemorySize, leg_smem));
     const bool dft_tc = ctx->tc_rows && dft_tc_fits(d.p);
     const bool leg_tc = dft_tc && ctx->tc_leg && leg_tc_fits(d.p);   // reads the order-major Fourier output
-    // row exponents of the weights for the tensor-core analysis, written by the weights kernel
-    int* rexp = nullptr;
-    if (dft_tc) {
-      if ((rc = ensure_d(ctx, &ctx->rexp, &ctx->rexp_cap, ((size_t)CT * ncomp * (d.q + 1) + 1) / 2, "row exponents")))
-        return rc;
-      rexp = reinterpret_cast<int*>(ctx->rexp);
-    }
-    for (int t0 = 0; t0 < d.nt; t0 += CT) {
+    for (int t0 = 0; t0 < d.nt; t0 += CT, ++c) {
       const int ct = std::min(CT, d.nt - t0);
+      const int lane = two ? (c & 1) : 0;
+      cudaStream_t st = ls[lane];
+      auto& L = ctx->lanes[lane];
+      float2* rot = reinterpret_cast<float2*>(L.rot);
+      float2* wb = reinterpret_cast<float2*>(L.w);
+      float2* vb = reinterpret_cast<float2*>(L.v);
+      float2* F = reinterpret_cast<float2*>(L.F);
+      float2* xc = reinterpret_cast<float2*>(L.xdf);
+      // row exponents of the weights for the tensor-core analysis, written by the weights kernel
+      int* rexp = dft_tc ? reinterpret_cast<int*>(L.rexp) : nullptr;
+      if (L.xdrop != (int)di) {
+        k_to_df<<<(unsigned)((3 * nc + 255) / 256), 256, 0, st>>>(xcoef + 3 * d.coef_off, 3 * nc, xc);
+        SHBIM_CHECK_LAUNCH(ctx, "k_to_df");
+        L.xdrop = (int)di;
+      }
       // the position coefficients are the same for every target: zero input stride
       {
-        TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, s);
+        TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, st);
         if (rot_tc) {
-          if ((rc = rotate_tc(ctx, *d.tab, false, xc, 0, nc, t0, ct, 3, rot, nullptr, nullptr, d.nt, s))) return rc;
+          if ((rc = rotate_tc(ctx, *d.tab, false, xc, 0, nc, t0, ct, 3, rot, nullptr, nullptr, d.nt, st))) return rc;
         } else {
-          k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, s>>>(
+          k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, st>>>(
               xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
               d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
           SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
         }
       }
       {
-        TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, s);
-        k_self_weights_df<<<dim3(ct, d.q + 1), 128, w_smem, s>>>(rot, d.p, d.q, d.tab->up_alf_df, d.tab->up_trig_df,
-                                                                 up.mu, ctx->geo.tgt, ctx->ntarget, d.tgt_off + t0, wb,
-                                                                 dft_tc ? rexp : nullptr);
+        TimeScope ts(ctx, SHBIM_K_SELF_WEIGHTS, st);
+        k_self_weights_df<<<dim3(ct, d.q + 1), 128, w_smem, st>>>(rot, d.p, d.q, d.tab->up_alf_df, d.tab->up_trig_df,
+                                                                  up.mu, ctx->geo.tgt, ctx->ntarget, d.tgt_off + t0, wb,
+                                                                  rexp);
         SHBIM_CHECK_LAUNCH(ctx, "k_self_weights_df");
       }
       {
-        TimeScope ts(ctx, SHBIM_K_SELF_ANALYSIS, s);
+        TimeScope ts(ctx, SHBIM_K_SELF_ANALYSIS, st);
         const int64_t nrows = (int64_t)ct * ncomp * (d.q + 1);
         if (leg_tc) {
-          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, s, true)) ||
-              (rc = analysis_legendre_tc(ctx, *d.tab, F, (int64_t)ct * ncomp, vb, nc, s)))
+          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, st, true)) ||
+              (rc = analysis_legendre_tc(ctx, *d.tab, F, (int64_t)ct * ncomp, vb, nc, st)))
             return rc;
         } else if (dft_tc) {
-          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, s))) return rc;
+          if ((rc = analysis_fourier_tc(ctx, *d.tab, wb, nrows, rexp, F, st))) return rc;
         } else {
-          k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, s>>>(wb, Ns, d.p, d.q,
-                                                                                    d.tab->up_trig_df, nrows, rows, F);
+          k_analysis_f4_df<<<(unsigned)((nrows + rows - 1) / rows), 128, f_smem, st>>>(wb, Ns, d.p, d.q,
+                                                                                     d.tab->up_trig_df, nrows, rows, F);
           SHBIM_CHECK_LAUNCH(ctx, "k_analysis_f4_df");
         }
         if (!leg_tc) {
-          k_analysis_leg_item_df<<<ct * ncomp, 288, leg_smem, s>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
+          k_analysis_leg_item_df<<<ct * ncomp, 288, leg_smem, st>>>(F, d.p, d.q, d.tab->up_alf_df, vb, nc);
           SHBIM_CHECK_LAUNCH(ctx, "k_analysis_leg_item_df");
         }
       }
       {
-        TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, s);
+        TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, st);
         if (rot_tc) {
           if ((rc = rotate_tc(ctx, *d.tab, true, vb, (int64_t)ncomp * nc, nc, t0, ct, ncomp, nullptr, d.rows_lap,
-                              d.rows_sto, d.nt, s)))
+                              d.rows_sto, d.nt, st)))
             return rc;
         } else {
-          k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, s>>>(
+          k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, st>>>(
               vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df,
               d.tab->dq_df, d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
           SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
         }
       }
     }
+  }
+  if (two) {
+    SHBIM_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+    SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
   }
   if ((ctx->tc_rows || ctx->tc_rot || ctx->tc_leg) && ctx->tc_err) {
     int flag = 0;
