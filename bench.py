@@ -178,7 +178,6 @@ def run_own(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    ctx.set_timing(True)
     launches0 = ctx.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -195,6 +194,19 @@ def run_own(args):
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - launches0
+    clk = clocks.stop()
+    if args.profile:
+        ctx.close()
+        print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps, "applications": sum(r[0] for r in stats)}))
+        return
+    # Per-kernel-class durations (phases, roofline) with CUDA events on the launching streams, in
+    # the same number of extra steps with the library's second stream off: in the timed steps the
+    # row build's two lanes overlap, so a kernel's bracketed time there includes the other lane's.
+    ctx.set_concurrency(False)
+    ctx.set_timing(True)
+    for _ in range(args.steps):
+        step(xc, gc)
+    torch.cuda.synchronize()
     cls_ms = {}
     cls_n = {}
     names = {S.K_SELF_WEIGHTS: "self_weights", S.K_SELF_ANALYSIS: "self_analysis",
@@ -203,7 +215,7 @@ def run_own(args):
     for k, nm in names.items():
         cls_ms[nm], cls_n[nm] = ctx.kernel_stats(k)
     ctx.set_timing(False)
-    clk = clocks.stop()
+    ctx.set_concurrency(not args.serial)
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -212,11 +224,6 @@ def run_own(args):
         torch.distributed.all_reduce(a)
         apps_total = int(a.item())
     value = apps_total * P / (ms / 1e3)
-
-    if args.profile:
-        ctx.close()
-        print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps, "applications": apps_total}))
-        return
 
     # end to end: the state is copied in from pinned host memory and the new state read back
     x_pin = torch.tensor(x_host).pin_memory()
@@ -276,6 +283,10 @@ def run_own(args):
                    "l2": "working set (singular rows 0.53 GB) exceeds the 129 MB L2; no flush",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "phase_ms_per_step": {k: v / args.steps for k, v in cls_ms.items()},
+        "kernel_timing": "phases and the roofline's launch durations: CUDA events around the kernel classes in "
+                         "%d extra steps of the same workload with the library's second stream off (in the timed "
+                         "steps the row build's two lanes overlap); GMRES applications replayed from CUDA graphs "
+                         "are not bracketed" % args.steps,
         "time_to_1e-8": tts,
         "pairs_at_scale": scale,
         "learned_warm_start": learned,
