@@ -33,20 +33,21 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// per drop: area (sum of w over the source grid) and radius (max |x - c|); one block per drop
+// per drop: area (sum of w over the source grid) and radius (max |x - c|, one square root of the
+// largest squared distance); one block per drop
 __global__ void k_drop_stats(const DropDev* __restrict__ drops, const double* __restrict__ src, int64_t nsource,
                              double* __restrict__ out /* [n][2] */) {
   const DropDev D = drops[blockIdx.x];
-  double a = 0.0, r = 0.0;
+  double a = 0.0, r2 = 0.0;
   for (int64_t e = threadIdx.x; e < D.ns; e += blockDim.x) {
     const int64_t s = D.src_off + e;
     const double dx = src[s] - D.cx, dy = src[nsource + s] - D.cy, dz = src[2 * nsource + s] - D.cz;
     a += src[6 * nsource + s];
-    r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+    r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
   }
   __shared__ double sa[256], sr[256];
   sa[threadIdx.x] = a;
-  sr[threadIdx.x] = r;
+  sr[threadIdx.x] = r2;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
@@ -57,18 +58,21 @@ __global__ void k_drop_stats(const DropDev* __restrict__ drops, const double* __
   }
   if (threadIdx.x == 0) {
     out[2 * blockIdx.x] = sa[0];
-    out[2 * blockIdx.x + 1] = sr[0];
+    out[2 * blockIdx.x + 1] = sqrt(sr[0]);
   }
 }
 
 // Near test in FP32 on centre-relative coordinates (a target within rounding of the 6 h_j
-// threshold may land on either side; there the two rules agree to ~1e-11 anyway).
+// threshold may land on either side; there the two rules agree to ~1e-11 anyway). One warp per
+// target: for each candidate drop the lanes test 32 consecutive source nodes at a time (coalesced
+// loads) and stop together at the first chunk that holds a node below the threshold.
 __global__ void k_near_detect(const double* __restrict__ tgt, int64_t ntarget, const int* __restrict__ tgt_drop,
                               const DropDev* __restrict__ drops, int n_drops, const float* __restrict__ src32,
                               int64_t nsource, const double* __restrict__ stats /* area, R, lim per drop */,
                               int* __restrict__ count, int64_t* __restrict__ pair_t, int* __restrict__ pair_j,
                               int cap) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // uniform over the warp
+  const int lane = threadIdx.x & 31;
   if (t >= ntarget) return;
   const int i = tgt_drop[t];
   const double x = tgt[t], y = tgt[ntarget + t], z = tgt[2 * ntarget + t];
@@ -81,12 +85,20 @@ __global__ void k_near_detect(const double* __restrict__ tgt, int64_t ntarget, c
     const float rx = (float)dcx, ry = (float)dcy, rz = (float)dcz;
     const float lim2 = (float)(lim * lim);
     bool near = false;
-    for (int64_t e = 0; e < D.ns && !near; ++e) {
-      const int64_t s = D.src_off + e;
-      const float dx = rx - src32[s], dy = ry - src32[nsource + s], dz = rz - src32[2 * nsource + s];
-      near = dx * dx + dy * dy + dz * dz < lim2;
+    for (int64_t e0 = 0; e0 < D.ns; e0 += 32) {
+      const int64_t e = e0 + lane;
+      bool hit = false;
+      if (e < D.ns) {
+        const int64_t s = D.src_off + e;
+        const float dx = rx - src32[s], dy = ry - src32[nsource + s], dz = rz - src32[2 * nsource + s];
+        hit = dx * dx + dy * dy + dz * dz < lim2;
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+        near = true;
+        break;
+      }
     }
-    if (near) {
+    if (near && lane == 0) {
       const int k = atomicAdd(count, 1);
       if (k < cap) {
         pair_t[k] = t;
@@ -542,15 +554,14 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
   const int nd = ctx->n_drops;
   int rc;
   // per-drop area, radius and near limit 6 h_j
-  if ((rc = grow(ctx, (void**)&N.stats, &N.stats_cap, sizeof(double) * 3 * nd, "near stats"))) return rc;
-  double* tmp2 = nullptr;
-  if (cudaMalloc(&tmp2, sizeof(double) * 2 * nd) != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "near stats");
+  // [3 nd] stats the detection reads, then [2 nd] (area, radius) from the device
+  if ((rc = grow(ctx, (void**)&N.stats, &N.stats_cap, sizeof(double) * 5 * nd, "near stats"))) return rc;
+  double* tmp2 = N.stats + 3 * nd;
   k_drop_stats<<<nd, 256, 0, s>>>(ctx->drops_dev, ctx->geo.src, ctx->nsource, tmp2);
   SHBIM_CHECK_LAUNCH(ctx, "k_drop_stats");
   std::vector<double> st2(2 * nd), st3(3 * nd);
   SHBIM_CUDA(ctx, cudaMemcpyAsync(st2.data(), tmp2, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, s));
   SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
-  cudaFree(tmp2);
   for (int j = 0; j < nd; ++j) {
     st3[3 * j] = st2[2 * j];
     st3[3 * j + 1] = st2[2 * j + 1];
@@ -564,7 +575,7 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
     return rc;
   int* count = N.det_j + cap;
   SHBIM_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int), s));
-  k_near_detect<<<nb(ctx->ntarget), 256, 0, s>>>(ctx->geo.tgt, ctx->ntarget, ctx->geo.tgt_drop, ctx->drops_dev, nd,
+  k_near_detect<<<nb(ctx->ntarget * 32), 256, 0, s>>>(ctx->geo.tgt, ctx->ntarget, ctx->geo.tgt_drop, ctx->drops_dev, nd,
                                                  ctx->geo.src32, ctx->nsource, N.stats, count, N.det_t, N.det_j, cap);
   SHBIM_CHECK_LAUNCH(ctx, "k_near_detect");
   int cnt = 0;
