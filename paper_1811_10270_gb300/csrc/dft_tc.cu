@@ -14,15 +14,16 @@
 // double-float. The neglected products (j_a + j_b < 5) and the rounding of the digits bound the
 // error by ~2^-42 of sum_k |W[r][k]| (Ozaki-style error-free splitting of a matrix product).
 //
-// Work decomposition: persistent CTAs (one per SM, 256 threads; the six accumulators of the
-// 80-output tile take 480 of the SM's 512 tensor-memory columns) loop over tiles of 128 rows. The
-// table's pre-laid-out digit planes (all K steps, up to 150 KB) are copied into shared memory once
-// per CTA; the next tile's rows are prefetched into L2. Per tile the rows' scales come with the
-// rows (or two threads per row find them), then per K step of 16 longitudes
-// each thread turns eight values (read from global memory one step ahead) into digit planes in one
-// of two shared-memory stages and one thread issues the 21 MMAs and commits them to the stage's
-// mbarrier; the other stage is filled meanwhile. Every wait is bounded; a timeout sets the error
-// flag and the kernel stops issuing work. Degrees with 2p + 2 <= 80 (p <= 39).
+// Work decomposition: persistent CTAs (one per SM, 16 producer warps + one MMA warp; the six
+// accumulators of the 80-output tile take 480 of the SM's 512 tensor-memory columns) loop over
+// tiles of 128 rows. The table's pre-laid-out digit planes (all K steps, up to 150 KB) are copied
+// into shared memory once per CTA; the next tile's rows are prefetched into L2. Per tile the rows'
+// scales come with the rows (or four threads per row find them), then per K step of 16 longitudes
+// each producer thread turns four values (read from global memory two steps ahead) into digit
+// planes in one of two shared-memory stages, and one thread of the MMA warp issues the 21 digit
+// products as 9 MMAs (one row digit against up to three table digits, N <= 240) and commits them to
+// the stage's mbarrier; the other stage is filled meanwhile. Every wait is bounded; a timeout sets
+// the error flag and the kernel stops issuing work. Degrees with 2p + 2 <= 80 (p <= 39).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,7 +42,7 @@ namespace {
 using namespace tc;
 
 constexpr int kNT = 80;                       // outputs per tile (MMA N)
-constexpr int kProducers = 256;                // digit-writing and epilogue threads (8 warps)
+constexpr int kProducers = 512;                // digit-writing and epilogue threads (16 warps)
 constexpr int kThreadsTC = kProducers + 32;    // + one warp that issues the MMAs
 constexpr int kPlaneA = kMT * kKS;            // bf16 per row-digit plane (4096 B)
 constexpr int kPlaneB = kNT * kKS;            // bf16 per table-digit plane (2560 B)
@@ -62,7 +63,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
   __shared__ __align__(8) uint64_t tbar;
   __shared__ uint32_t tmem_base;
   __shared__ int rowexp[kMT];
-  __shared__ float rowmax[2][kMT];
+  __shared__ float rowmax[4][kMT];
   uint8_t* sB = smem;
   uint8_t* sA = smem + (size_t)ksteps * kDig * kPlaneB * 2;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -90,28 +91,27 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
   bool table_ok = true;
   if ((int64_t)blockIdx.x < total) table_ok = mbar_wait(&tbar, 0);
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = idesc_bf16(kNT);
   // uses of each stage so far (the same count in every thread): fill u waits for the products of
   // fill u - 1 (parity (u - 1) & 1 of `empty`), the MMA warp waits for fill u (parity u & 1 of `full`)
   uint32_t uses[2] = {0u, 0u};
   bool abort_all = __syncthreads_or(!table_ok);
-  const int r_loc = tid & (kMT - 1), half = (tid >> 7) & 1;
+  const int r_loc = tid & (kMT - 1), qt = (tid >> 7) & 3;   // row of the tile, quarter of a K step
   for (int64_t tm = blockIdx.x; tm < total && !abort_all; tm += gridDim.x) {
     const int64_t row = tm * kMT + r_loc;
     const bool rv = producer && row < rows;
     const float2* wrow = W + (rv ? row : 0) * nlon;
-    // eight values per K step (two per 16-byte load; nlon is a multiple of 4, so a pair lies wholly
+    // four values per K step (two per 16-byte load; nlon is a multiple of 4, so a pair lies wholly
     // inside or wholly past the row), read two steps ahead; the first two steps are requested
     // before the row scales arrive
-    auto load_step = [&](int ks, float4 (&v)[4]) {
+    auto load_step = [&](int ks, float4 (&v)[2]) {
 #pragma unroll
-      for (int i2 = 0; i2 < 4; ++i2) {
-        const int k = ks * kKS + half * 8 + 2 * i2;
+      for (int i2 = 0; i2 < 2; ++i2) {
+        const int k = ks * kKS + qt * 4 + 2 * i2;
         v[i2] = (rv && ks < ksteps && k < nlon) ? *reinterpret_cast<const float4*>(wrow + k)
                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    float4 q0[4], q1[4];
+    float4 q0[2], q1[2];
     load_step(0, q0);
     load_step(1, q1);
     // the next tile's rows start moving from HBM into L2 now
@@ -122,26 +122,25 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(reinterpret_cast<const char*>(W + r1 * nlon) + off),
                      "r"((uint32_t)min((int64_t)32768, bytes - off)));
     }
-    // per-row power-of-two scale, max |hi| < 2^e: given by the producer of W, or two threads per
-    // row scanning a half row each
+    // per-row power-of-two scale, max |hi| < 2^e: given by the producer of W, or four threads per
+    // row scanning every fourth pair of its values each
     if (rexp) {
       if (tid < kMT) rowexp[tid] = tm * kMT + tid < rows ? rexp[tm * kMT + tid] : 0;
     } else if (producer) {
       float mx = 0.f;
       if (rv) {
-        const int h = nlon >> 1, k0 = half * h;
 #pragma unroll 4
-        for (int k = k0; k < k0 + h; k += 2) {
+        for (int k = 2 * qt; k < nlon; k += 8) {
           const float4 v = *reinterpret_cast<const float4*>(wrow + k);
           mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
         }
       }
-      rowmax[half][r_loc] = mx;
+      rowmax[qt][r_loc] = mx;
     }
     __syncthreads();
     if (!rexp && tid < kMT) {
       int e = 0;
-      frexpf(fmaxf(rowmax[0][tid], rowmax[1][tid]), &e);
+      frexpf(fmaxf(fmaxf(rowmax[0][tid], rowmax[1][tid]), fmaxf(rowmax[2][tid], rowmax[3][tid])), &e);
       rowexp[tid] = max(e, -120);   // keeps 2^(7 - e) a normal float; smaller rows scale the same
     }
     __syncthreads();
@@ -150,9 +149,9 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
       const float sc = __int_as_float((127 + 7 - rowexp[r_loc]) << 23);   // 2^(7 - e), exact
       for (int ks = 0; ks < ksteps && !bad; ++ks) {
         const int st = ks & 1;
-        float4 cur[4];
+        float4 cur[2];
 #pragma unroll
-        for (int i2 = 0; i2 < 4; ++i2) {
+        for (int i2 = 0; i2 < 2; ++i2) {
           cur[i2] = q0[i2];
           q0[i2] = q1[i2];
         }
@@ -162,9 +161,9 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
           break;
         }
         uint8_t* base = sA + st * (kDig * kPlaneA * 2);
-        float d[kDig][8];
+        float d[kDig][4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < 4; ++i) {
           const float4 v4 = cur[i >> 1];
           const float vh = (i & 1) ? v4.z : v4.x, vl = (i & 1) ? v4.w : v4.y;
           float dd[kDig];
@@ -172,15 +171,13 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
 #pragma unroll
           for (int j = 0; j < kDig; ++j) d[j][i] = dd[j];
         }
-        const int off = canon16(r_loc, half * 8) * 2;   // bytes; 16-byte aligned
+        const int off = canon16(r_loc, qt * 4) * 2;   // bytes; 8-byte aligned
 #pragma unroll
         for (int j = 0; j < kDig; ++j) {
-          uint4 q;
+          uint2 q;
           q.x = pack_bf16f(d[j][0], d[j][1]);
           q.y = pack_bf16f(d[j][2], d[j][3]);
-          q.z = pack_bf16f(d[j][4], d[j][5]);
-          q.w = pack_bf16f(d[j][6], d[j][7]);
-          *reinterpret_cast<uint4*>(base + j * kPlaneA * 2 + off) = q;
+          *reinterpret_cast<uint2*>(base + j * kPlaneA * 2 + off) = q;
         }
         // the writes become visible to the tensor cores' (async-proxy) reads, then the stage is
         // reported full
@@ -197,17 +194,19 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t a0 = smem_u32(sA + st * (kDig * kPlaneA * 2)), b0 = smem_u32(sB + (size_t)ks * kDig * kPlaneB * 2);
+        // A digit j_a times up to three consecutive table digits j_b .. j_b + g - 1 in one MMA of
+        // N = 80 g: the table's digit planes lie one after the other like the rows of one operand,
+        // and their products go to the consecutive accumulators j_a + j_b - 5 .. + g - 1. The two
+        // products of j_a = 5 come first and, in the first K step, overwrite all six accumulators.
 #pragma unroll
-        for (int ja = 0; ja < kDig; ++ja)
+        for (int ja = kDig - 1; ja >= 0; --ja)
 #pragma unroll
-          for (int jb = 0; jb < kDig; ++jb) {
-            if (ja + jb < kDig - 1) continue;
-            const int dgl = ja + jb - (kDig - 1);
-            // the first product of each diagonal (j_b = 5 in this loop order) in the first K step
-            // overwrites the accumulator
-            const uint32_t acc = (ks > 0 || jb != kDig - 1) ? 1u : 0u;
-            mma_bf16(tmem + (uint32_t)(dgl * kNT), desc_k16(a0 + ja * kPlaneA * 2), desc_k16(b0 + jb * kPlaneB * 2),
-                     idesc, acc);
+          for (int jb0 = kDig - 1 - ja; jb0 < kDig; jb0 += 3) {
+            const int g = min(3, kDig - jb0);
+            const int dgl = ja + jb0 - (kDig - 1);
+            const uint32_t acc = (ks > 0 || ja != kDig - 1) ? 1u : 0u;
+            mma_bf16(tmem + (uint32_t)(dgl * kNT), desc_k16(a0 + ja * kPlaneA * 2), desc_k16(b0 + jb0 * kPlaneB * 2),
+                     idesc_bf16(kNT * g), acc);
           }
         mma_commit(&empty[st]);
         ++uses[st];
@@ -228,21 +227,22 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
       }
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    // epilogue: warp w (< 8) reads lanes 32 (w % 4) .. +31; column blocks of 16 split between w and w+4
+    // epilogue: warp w (< 16) reads lanes 32 (w % 4) .. +31; column blocks of 8 split among w, w+4,
+    // w+8 and w+12
     if (producer) {
-      const int lq = warp & 3, wh = warp >> 2;
+      const int lq = warp & 3, wq = warp >> 2;
       const int rl = 32 * lq + (tid & 31);
       const int64_t rowe = tm * kMT + rl;
       const int ee = rowexp[rl];
-      for (int cb = wh; cb < kNT / 16; cb += 2) {
-        uint32_t a[kDig][16];
+      for (int cb = wq; cb < (nout + 7) / 8; cb += 4) {
+        uint32_t a[kDig][8];
 #pragma unroll
         for (int dg = 0; dg < kDig; ++dg)
-          tmem_ld16(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * kNT + cb * 16), a[dg]);
+          tmem_ld8(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * kNT + cb * 8), a[dg]);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int o = cb * 16 + j;
+        for (int j = 0; j < 8; ++j) {
+          const int o = cb * 8 + j;
           if (rowe < rows && o < nout) {
             const dfl::df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
                                        __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));

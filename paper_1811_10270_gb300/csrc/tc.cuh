@@ -114,6 +114,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&a)[16]) {
       : "r"(addr));
 }
 
+// 8 consecutive FP32 columns of the warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&a)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7])
+               : "r"(addr));
+}
+
 // Six balanced base-2^7 digits of y = yh + yl (|yh| < 128, |yl| <= ulp(yh) / 2), top first:
 // d5 = rint(y), then the digits of the remainder times 128, and so on. The top three come from yh
 // alone (every remainder exact); yl joins through one two-sum at the scale of d2; the last two come
