@@ -10,12 +10,13 @@
 // exact bfloat16 digit products (tc.cuh), followed (adjoint) or preceded (forward) by Dz(phi) on
 // the double-float values in shared memory.
 //
-// Work decomposition: persistent CTAs (one per SM, 256 threads, all 512 tensor-memory columns:
+// Work decomposition: persistent CTAs (one per SM, 512 threads, all 512 tensor-memory columns:
 // six accumulators of up to 80 columns) loop over items (up to 128 vectors of one latitude, one
 // degree), largest degree first. Per item: the rows' degree block and their targets' phi tables are
 // copied asynchronously into shared memory; the rows get a power-of-two scale; per K step of 16
 // their digit planes and the table's pre-laid-out planes (bulk copies, prefetched a step ahead)
-// fill one of two stages and one thread issues the 21 MMAs; the epilogue combines the six
+// fill one of two stages and one thread issues the 21 digit products as 9 MMAs (one row digit
+// against up to three table digits, N <= 240); the epilogue combines the six
 // accumulators in double-float. Every wait is bounded; a timeout sets the error flag and the CTA
 // stops. Degrees with 2n+1 <= 80 (p <= 39) only: larger blocks use the FP32-pipe kernel.
 #include <algorithm>
@@ -34,7 +35,7 @@ namespace {
 using dfl::df;
 using namespace tc;
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kNmax = 80;                                  // largest padded block (N and K)
 constexpr int kPlaneA = kMT * kKS;                          // bf16 per row-digit plane
 constexpr int kPlaneBmax = kNmax * kKS;                     // bf16 per table-digit plane
@@ -138,7 +139,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
   bool pending[2] = {false, false};   // MMAs committed on the stage and not yet waited for
   bool bpend[2] = {false, false};     // table copy issued into the stage and not yet waited for
   bool abort_all = false;
-  const int r_loc = tid & (kMT - 1), half = tid >> 7;
+  const int r_loc = tid & (kMT - 1), qt = tid >> 7;   // row of the tile, quarter of a K step
   // table planes of (latitude, degree), K step ks, into stage st (thread 0)
   auto issue_b = [&](int lat, int n, int ks, int st) {
     const int Np = padded(2 * n + 1);
@@ -164,7 +165,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
     if (rt < 0) return;
     const float2* cs = sCS + rt * CS;
     float2* x = sX + r_loc * WS;
-    for (int m = 1 + half; m <= n; m += 2) {
+    for (int m = 1 + qt; m <= n; m += 4) {
       const float2 c2 = cs[m], s2 = cs[p + 1 + m];
       const df ca{c2.x, c2.y};
       const df sa = neg ? df{-s2.x, -s2.y} : df{s2.x, s2.y};
@@ -182,7 +183,6 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
     const int w = 2 * n + 1;
     const int Np = padded(w);
     const int ksteps = Np / kKS;
-    const uint32_t idesc = idesc_bf16(Np);
     const int b_lo = va / ncomp;
     const int nb = (vb - 1) / ncomp - b_lo + 1;
     // rows of the item (vector v = chunk-local target b, component c), their targets' phi tables
@@ -241,25 +241,23 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
       uint8_t* base = smem + st * kStageBytes;
       {
         const float sc = __int_as_float((127 + 7 - e_r) << 23);   // 2^(7 - e), exact
-        float d[kDig][8];
+        float d[kDig][4];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int k = ks * kKS + half * 8 + i;
+        for (int i = 0; i < 4; ++i) {
+          const int k = ks * kKS + qt * 4 + i;
           const float2 v = k < w ? xrow[k] : make_float2(0.f, 0.f);
           float dd[kDig];
           digits6(v.x * sc, v.y * sc, dd);
 #pragma unroll
           for (int j = 0; j < kDig; ++j) d[j][i] = dd[j];
         }
-        const int off = canon16(r_loc, half * 8) * 2;
+        const int off = canon16(r_loc, qt * 4) * 2;   // bytes; 8-byte aligned
 #pragma unroll
         for (int j = 0; j < kDig; ++j) {
-          uint4 q;
+          uint2 q;
           q.x = pack_bf16f(d[j][0], d[j][1]);
           q.y = pack_bf16f(d[j][2], d[j][3]);
-          q.z = pack_bf16f(d[j][4], d[j][5]);
-          q.w = pack_bf16f(d[j][6], d[j][7]);
-          *reinterpret_cast<uint4*>(base + j * kPlaneA * 2 + off) = q;
+          *reinterpret_cast<uint2*>(base + j * kPlaneA * 2 + off) = q;
         }
       }
       asm volatile("fence.proxy.async.shared::cta;\n");
@@ -270,15 +268,18 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
         if (!mbar_wait(&bbar[st], bphase[st])) atomicExch(err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t a0 = smem_u32(base), b0 = smem_u32(base + kDig * kPlaneA * 2);
+        // row digit j_a against up to three consecutive table digits in one MMA of N = Np g (the
+        // planes lie one after the other like the rows of one operand; their products go to the
+        // consecutive accumulators j_a + j_b - 5 ..); j_a = 5 first, overwriting all six in step 0
 #pragma unroll
-        for (int ja = 0; ja < kDig; ++ja)
+        for (int ja = kDig - 1; ja >= 0; --ja)
 #pragma unroll
-          for (int jb = 0; jb < kDig; ++jb) {
-            if (ja + jb < kDig - 1) continue;
-            const int dgl = ja + jb - (kDig - 1);
-            const uint32_t acc = (ks > 0 || jb != kDig - 1) ? 1u : 0u;
-            mma_bf16(tmem + (uint32_t)(dgl * Np), desc_k16(a0 + ja * kPlaneA * 2), desc_k16(b0 + jb * Np * kKS * 2),
-                     idesc, acc);
+          for (int jb0 = kDig - 1 - ja; jb0 < kDig; jb0 += 3) {
+            const int g = min(3, kDig - jb0);
+            const int dgl = ja + jb0 - (kDig - 1);
+            const uint32_t acc = (ks > 0 || ja != kDig - 1) ? 1u : 0u;
+            mma_bf16(tmem + (uint32_t)(dgl * Np), desc_k16(a0 + ja * kPlaneA * 2), desc_k16(b0 + jb0 * Np * kKS * 2),
+                     idesc_bf16(Np * g), acc);
           }
         mma_commit(&mbar[st]);
         // the table planes of K step ks + 1 go to the other stage once its products are done
@@ -309,20 +310,20 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
     const int64_t next = I.next(item + gridDim.x, gridDim.x);
     if (next < I.total) prefetch(next);
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    // epilogue: warp w reads lanes 32 (w % 4) .. +31; column blocks of 16 split between w and w+4
+    // epilogue: warp w reads lanes 32 (w % 4) .. +31; column blocks of 8 split among w, w+4, w+8, w+12
     {
-      const int lq = warp & 3, wh = warp >> 2;
+      const int lq = warp & 3, wq = warp >> 2;
       const int rl = 32 * lq + lane;
       const int ee = rowexp[rl];
-      for (int cb = wh; cb < Np / 16; cb += 2) {
-        uint32_t a[kDig][16];
+      for (int cb = wq; cb < Np / 8; cb += 4) {
+        uint32_t a[kDig][8];
 #pragma unroll
         for (int dg = 0; dg < kDig; ++dg)
-          tmem_ld16(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * Np + cb * 16), a[dg]);
+          tmem_ld8(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(dg * Np + cb * 8), a[dg]);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n");
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int o = cb * 16 + j;
+        for (int j = 0; j < 8; ++j) {
+          const int o = cb * 8 + j;
           if (o < w) {
             const df r = combine6(__uint_as_float(a[5][j]), __uint_as_float(a[4][j]), __uint_as_float(a[3][j]),
                                   __uint_as_float(a[2][j]), __uint_as_float(a[1][j]), __uint_as_float(a[0][j]));
