@@ -662,18 +662,19 @@ def run_reference(args):
     if rank != 0:
         return
     vals = []
-    for _ in range(args.warmup if args.warmup < 1 else 1):
+    for _ in range(args.warmup):   # untimed warm-up samples (2 targets per drop each)
         cpu_baseline(args.p, 2)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         vals.append(cpu_baseline(args.p, args.cpu_targets))
     wall = time.perf_counter() - t0
     v = float(np.mean([x["value"] for x in vals]))
-    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "two drops p=%d gap=0.1, FP64 CPU oracle on a bounded sample" % args.p},
+           "config": {"workload": "two drops p=%d gap=0.1, FP64 CPU oracle on a bounded sample" % args.p,
+                      "device": "host CPU cores (rank 0 only); no GPU work"},
            "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"],
                             "value": v, "unit": UNIT},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
