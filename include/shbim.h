@@ -5,7 +5,7 @@
  * electrohydrodynamics of surfactant-covered drops": the Laplace layer operators of the
  * leaky-dielectric problem (Eqs. BIE01, E_n, dl_op_laplace), the Stokes single and double
  * layer (Eqs. main_eq, GandT, op_stokes) and their Galerkin projections (Eqs. BIM_galerkin,
- * galerkin_En), discretised with spherical harmonics on Gaussian grids (Section 3), the
+ * galerkin_En), discretised with spherical harmonics on Gaussian grids (Section 2), the
  * regular rule (Eq. reg_quadrature) and the rotated-pole singular rule (Eq. mod_weights).
  *
  * Conventions shared by every call
@@ -109,8 +109,8 @@ int shbim_set_R(shbim_ctx* ctx, double R);
 
 /* Define the drops and build everything that depends only on their shapes:
  * transform tables per distinct degree, target and source geometry (x, outward normal n,
- * area element; Section 2 and Eq. reg_quadrature) and the singular self rows of every
- * kernel (rotated-pole rule, Section 3.1).
+ * area element; Section 1 and Eq. reg_quadrature) and the singular self rows of every
+ * kernel (rotated-pole rule, Section 2.1).
  *   n_drops      number of drops (>= 1)
  *   p_host       degree of each drop, 1 <= p <= 64
  *   lambda_host  viscosity ratio of each drop (Eq. main_eq); may be NULL (all 1)
@@ -122,7 +122,7 @@ int shbim_set_R(shbim_ctx* ctx, double R);
 int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const double* lambda_host,
                     const double* xcoef_dev, void* stream);
 
-/* Nearly-singular correction (Section 3.1; on by default). When on, shbim_set_drops also finds
+/* Nearly-singular correction (Section 2.1; on by default). When on, shbim_set_drops also finds
  * every target closer than 6 h_j to another drop j's source nodes (h_j = sqrt(area_j / N_s),
  * the spacing of drop j's degree 2p+1 grid) and, for each such pair, builds correction rows
  * so that drop j's contribution there comes from the regular rule on drop j's grid upsampled
@@ -148,7 +148,7 @@ int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream);
 int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, double* out_dev,
                        void* stream);
 
-/* Spherical-harmonic transform of n_fields fields of one drop's degree (Section 3).
+/* Spherical-harmonic transform of n_fields fields of one drop's degree (Section 2).
  *   drop         index of the drop whose degree p (and grid) is used
  *   dir          SHBIM_SHT_INVERSE: in = n_fields x (p+1)^2 coefficients,
  *                                  out = n_fields x grid values
@@ -197,7 +197,7 @@ int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* str
 int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                       double* x_dev, int* iters_host, double* resid_host, void* stream);
 
-/* Physical parameters of the drop problem (Section 2).
+/* Physical parameters of the drop problem (Section 1).
  * E_n is solved with R; the traction uses Q and R (Eq. el_force, eps = 1); the capillary
  * force is scaled by 1/Ca_E (Eq. main_eq); the tension follows the Langmuir law normalised so
  * that gamma(1) = 1, gamma = (1 + beta ln(1 - x_s Gamma)) / (1 + beta ln(1 - x_s))
@@ -213,7 +213,7 @@ typedef struct shbim_phys {
   double Pe;            /* surfactant Peclet number; 0 or infinity: no diffusion */
 } shbim_phys;
 
-/* Velocity and surfactant rate for the current drop shapes (steps i-vi of Section 2):
+/* Velocity and surfactant rate for the current drop shapes (steps i-vi of Section 1):
  * solves for E_n, forms E_t = -grad_S(phi_inf + S_L[(1-1/R) E_n]), the electric and
  * interfacial forces on each drop's degree 2p+1 grid (products de-aliased by projection to
  * degree p), solves the Stokes system with right-hand side -sum_j S_j[f/Ca_E - f^E] and forms
@@ -356,7 +356,7 @@ int shbim_set_concurrency(shbim_ctx* ctx, int on);
  * FP32 results reproducible across contexts. Takes effect immediately. */
 int shbim_set_autotune(shbim_ctx* ctx, int on);
 
-/* Arithmetic of the singular-row build (Section 3.1; once per geometry, at the next
+/* Arithmetic of the singular-row build (Section 2.1; once per geometry, at the next
  * shbim_set_drops): SHBIM_PREC_DF64 (default: double-float on the FP32 pipe, FP64-class rows) or
  * SHBIM_PREC_FP64 (native). SHBIM_ERR_ARG otherwise. */
 int shbim_set_rows_precision(shbim_ctx* ctx, int precision);

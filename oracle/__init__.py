@@ -7,12 +7,14 @@ the paper it follows (Sorgentone, Tornberg & Vlahovska, "A 3D boundary integral 
 the electrohydrodynamics of surfactant-covered drops").
 
 Modules:
-    sh         Gaussian grid, normalised Legendre functions, real harmonics, SHT (Section 3)
-    geometry   surface position, tangents, normal, area element (Section 2, Section 3.1)
+    sh         Gaussian grid, normalised Legendre functions, real harmonics, SHT (Section 2)
+    geometry   surface position, tangents, normal, area element (Section 1, Section 2.1)
     quadrature regular rule (Eq. reg_quadrature), modified weights (Eq. mod_weights),
-               rotated-pole singular self-integration (Section 3.1)
+               rotated-pole singular self-integration (Section 2.1)
     operators  Laplace and Stokes layer operators and their Galerkin projections
                (Eqs. op_stokes, dl_op_laplace, BIM_galerkin, galerkin_En)
     gmres      restarted GMRES used to solve the Galerkin systems
-    theory     closed forms used as pins (small-perturbation theory of Section 4)
+    nearsing   nearly-singular correction by upsampling (Section 2.1)
+    physics    forces, rates and the midpoint time step (Section 1, Algorithm 1)
+    mlp        the warm-start network (forward, backward, Adam)
 """

@@ -1,10 +1,10 @@
 """Surface geometry from position coefficients, plain FP64 numpy (test infrastructure only).
 
-Each position component is a degree-p expansion (Section 3, Eq. spharm_ex). At any
+Each position component is a degree-p expansion (Section 2, Eq. spharm_ex). At any
 parameter point the oracle evaluates x, the tangents x_theta and x_phi/sin(theta), and
     c = x_theta x (x_phi / sin theta),   J = |c|,   n = c / J,
 so J is the area element relative to the unit sphere (W / sin theta with W the element of
-Eq. reg_quadrature) and n the outward unit normal of Section 2 (for the standard
+Eq. reg_quadrature) and n the outward unit normal of Section 1 (for the standard
 orientation, where the unit sphere gives J = 1 and n = x).
 """
 from __future__ import annotations

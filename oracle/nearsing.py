@@ -1,6 +1,6 @@
 """Nearly-singular correction, plain FP64 numpy (test infrastructure only).
 
-Section 3.1 (last paragraph) treats targets close to another drop's surface with the regular
+Section 2.1 (last paragraph) treats targets close to another drop's surface with the regular
 rule on an upsampled grid ("with a reasonable upsampling rate") for points far enough from the
 surface, combined with the on-surface rule and 1D interpolation for the closest ones. The paper
 gives no parameters; the reading used here:

@@ -1,11 +1,11 @@
 """Multi-drop layer operators and their Galerkin systems, plain FP64 numpy (test infrastructure only).
 
 Targets of drop i are the nodes of its degree-p grid; sources of drop j are the nodes of its
-degree q = 2p+1 grid (upsampled rule, Section 3.1). For a target on drop i the value is
+degree q = 2p+1 grid (upsampled rule, Section 2.1). For a target on drop i the value is
     sum over j != i of the regular rule (Eq. reg_quadrature) on drop j
   + the singular self-integration on drop i (Eq. mod_weights, rotated pole).
 Galerkin coefficients are the forward transform of the target values on drop i's degree-p
-grid (inner products (., Y_nm) of Section 3).
+grid (inner products (., Y_nm) of Section 2).
 
 Systems (readings of the paper's sign conventions are listed in the design notes):
   electric (Eq. galerkin_En):  1/2 E_n - (R-1)/(R+1) sum_j L_j[E_n] = R/(R+1) E_inf . n

@@ -1,6 +1,6 @@
 """Forces, surfactant rates and the time step, plain FP64 numpy (test infrastructure only).
 
-Follows Section 2 (steps i-viii) and Algorithm 1 of the paper:
+Follows Section 1 (steps i-viii) and Algorithm 1 of the paper:
   * E_n from the Galerkin electric system (Eq. galerkin_En); the charge q = (1 - 1/R) E_n
     (jump of E_n with Eq. EneEni) and its single-layer potential phi_q = S_L[q] (Eq. BIE01
     as a potential); the tangential mean field E_t = -grad_S (phi_inf + phi_q) (Eq. E_t).
@@ -159,7 +159,7 @@ def far_field(x, prm: Params):
 
 def rates(xcoefs, gcoefs, ps, lams, prm: Params, info=None, near: bool = True):
     """Velocity and surfactant-rate coefficients of every drop for one geometry
-    (steps i-vi of Section 2 and the explicit rate g_E of Algorithm 1); near=True applies the
+    (steps i-vi of Section 1 and the explicit rate g_E of Algorithm 1); near=True applies the
     nearly-singular correction of oracle.nearsing to every layer operator."""
     drops = [operators.DropGeom(xc, p, lam) for xc, p, lam in zip(xcoefs, ps, lams)]
     sysm = operators.System(drops, near=near)

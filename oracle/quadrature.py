@@ -10,7 +10,7 @@ of the operator definitions:
 
 Regular rule (Eq. reg_quadrature) on the degree-q source grid: int y dS = sum omega_j y J.
 
-Singular self-integration (Section 3.1, Eq. mod_weights): the parametrisation is rotated so
+Singular self-integration (Section 2.1, Eq. mod_weights): the parametrisation is rotated so
 that the target is the north pole, and the rotated grid is summed with the modified weights
     mu_j = omega_j * 2 sin(theta_j / 2) * sum_{n=0}^{q} P_n(cos theta_j),
 which integrate g / |north pole - y| exactly for g of degree <= q on the unit sphere

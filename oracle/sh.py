@@ -1,6 +1,6 @@
 """Spherical-harmonic machinery of the method, plain FP64 numpy (test infrastructure only).
 
-Follows Section 3 of the paper:
+Follows Section 2 of the paper:
   * Gaussian grid (Eq. spharm_ex): 2q+2 equispaced longitudes phi_k = pi k/(q+1) and q+1
     Gauss-Legendre latitudes theta_j = acos(t_j). Latitudes are ordered by increasing theta
     (t_j decreasing), longitudes by k, values stored [j][k] row-major.
@@ -10,7 +10,7 @@ Follows Section 3 of the paper:
   * Regular weights: the surface rule of Eq. reg_quadrature written relative to the unit
     sphere, omega_j = (pi/(q+1)) w_j^G (the paper prints pi/p; with 2q+2 longitudes the
     trapezoid spacing is pi/(q+1), which is what makes the weights sum to 4 pi).
-  * Forward transform = the Galerkin inner product (y, Y_nm) of Section 3 evaluated with
+  * Forward transform = the Galerkin inner product (y, Y_nm) of Section 2 evaluated with
     that rule; inverse transform = the truncated sum of Eq. spharm_ex.
 """
 from __future__ import annotations

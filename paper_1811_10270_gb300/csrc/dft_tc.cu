@@ -1,4 +1,4 @@
-// Fourier stage of the analysis of the singular-row weights (Section 3.1) on the fifth-generation
+// Fourier stage of the analysis of the singular-row weights (Section 2.1) on the fifth-generation
 // tensor cores, with FP64-class accuracy.
 //
 // F[r][o] = sum_k W[r][k] T[o][k], T[o][k] = cos(m phi_k) (o = m <= p) or sin(m phi_k)

@@ -1,4 +1,4 @@
-// Legendre stage of the analysis of the singular-row weights (Section 3.1) on the fifth-generation
+// Legendre stage of the analysis of the singular-row weights (Section 2.1) on the fifth-generation
 // tensor cores, with FP64-class accuracy:
 //   v[item][n^2 + n +- m] = s_m sum_j F[(cs, m)][item][j] Pbar_n^m(t_j),   s_0 = 1, s_m = sqrt(2),
 // the cosine part (cs = 0) giving order +m and the sine part (cs = 1) order -m. For one (cs, m) it

@@ -1,4 +1,4 @@
-// Nearly-singular correction (Section 3.1): targets close to another drop's surface take that
+// Nearly-singular correction (Section 2.1): targets close to another drop's surface take that
 // drop's contribution from the regular rule (Eq. reg_quadrature) on its grid upsampled four
 // times per direction, degree q_n = 4(q+1) - 1.
 //

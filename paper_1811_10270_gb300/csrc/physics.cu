@@ -1,4 +1,4 @@
-// Forces, surfactant rate and the midpoint time step (Section 2 steps i-viii, Algorithm 1).
+// Forces, surfactant rate and the midpoint time step (Section 1 steps i-viii, Algorithm 1).
 //
 // rates(): for the current drop shapes and a surfactant distribution Gamma,
 //   (i)   solve the electric system for E_n (Eq. galerkin_En);

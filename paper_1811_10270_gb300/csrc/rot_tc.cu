@@ -1,4 +1,4 @@
-// Pole rotation of the singular-row build (Section 3.1) on the fifth-generation tensor cores, with
+// Pole rotation of the singular-row build (Section 2.1) on the fifth-generation tensor cores, with
 // FP64-class accuracy.
 //   forward (ADJ = false): out = Dq^T Dz(-theta) Dq Dz(-phi) in   (position coefficients)
 //   adjoint (ADJ = true):  out = Dz(phi) Dq^T Dz(theta) Dq in     (rows, FP32 planes)

@@ -1,4 +1,4 @@
-// Spherical-harmonic transforms on Gaussian grids (Section 3, Eq. spharm_ex), FP64.
+// Spherical-harmonic transforms on Gaussian grids (Section 2, Eq. spharm_ex), FP64.
 //
 // Synthesis splits into a Legendre stage (per latitude j and order m: sum over degree n of
 // coefficient x table) and a Fourier stage (per longitude: sum over m of cos / sin terms),

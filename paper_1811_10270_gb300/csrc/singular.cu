@@ -1,4 +1,4 @@
-// Geometry and the singular self-integration (Section 3.1), FP64.
+// Geometry and the singular self-integration (Section 2.1), FP64.
 //
 // Geometry: x, x_theta, x_phi/sin(theta) on a grid by synthesis with derivative tables;
 // n = (x_theta x x_phi/sin) / J with J = |x_theta x x_phi/sin| the area element relative to

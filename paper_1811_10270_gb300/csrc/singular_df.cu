@@ -1,4 +1,4 @@
-// Singular self rows (rotated-pole rule, Eq. mod_weights and Section 3.1) built in double-float
+// Singular self rows (rotated-pole rule, Eq. mod_weights and Section 2.1) built in double-float
 // arithmetic on the FP32 pipe. Same algorithm as singular.cu, stage for stage:
 //   1. rotate the position coefficients so that the target is the north pole
 //      (b = D_R^T x with D_R = Dz(phi) Dq^T Dz(theta) Dq);

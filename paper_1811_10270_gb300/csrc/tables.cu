@@ -1,7 +1,7 @@
 // Transform and quadrature tables, computed on the host in FP64 once per degree.
 //
 // * Gauss-Legendre nodes and weights (Newton on P_N) for the latitudes of the Gaussian grid
-//   (Section 3, Eq. spharm_ex).
+//   (Section 2, Eq. spharm_ex).
 // * Normalised associated Legendre functions with the Condon-Shortley phase
 //   (Eqs. normalized_spharm, pneg) and the derivative tables the transforms need,
 //   d/dtheta Pbar_n^m = (n t Pbar_n^m - sqrt((2n+1)/(2n-1) (n^2-m^2)) Pbar_{n-1}^m) / sin,
@@ -12,7 +12,7 @@
 //   (Eq. mod_weights on the degree-q grid).
 // * The real-basis rotation matrix of the fixed rotation Rx(pi/2), per degree n, obtained
 //   exactly by quadrature of S_nm(Q y) S_nm'(y) on the degree-p grid. Composed with
-//   z-rotations it rotates any target to the north pole (Section 3.1).
+//   z-rotations it rotates any target to the north pole (Section 2.1).
 #include <cmath>
 #include <cstring>
 #include <mutex>

@@ -1,4 +1,4 @@
-"""Parity of the forces, rates and time step (Section 2, Algorithm 1) with the FP64 oracle."""
+"""Parity of the forces, rates and time step (Section 1, Algorithm 1) with the FP64 oracle."""
 import math
 import os
 

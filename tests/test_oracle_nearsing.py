@@ -1,4 +1,4 @@
-"""Pins of the oracle's nearly-singular correction (Section 3.1): at targets close to another
+"""Pins of the oracle's nearly-singular correction (Section 2.1): at targets close to another
 drop, the corrected value equals brute force -- the regular rule with the sources upsampled
 sixteen times per direction -- while the plain degree-q rule does not."""
 import math

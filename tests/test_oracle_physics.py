@@ -1,4 +1,4 @@
-"""Pins of the oracle's force, surfactant and time-step code (Section 2, Algorithm 1)."""
+"""Pins of the oracle's force, surfactant and time-step code (Section 1, Algorithm 1)."""
 import math
 
 import numpy as np
@@ -136,3 +136,46 @@ def test_imex_step_is_exact_for_pure_diffusion_on_a_sphere():
     k = dt * nn * (nn + 1) / prm.Pe
     np.testing.assert_allclose(gn[0], g0 * (1 - k / 2) / (1 + k / 2), atol=1e-12)
     np.testing.assert_allclose(xn[0], inputs.sphere_coef(p), atol=1e-12)
+
+
+def _deformation(xc, p):
+    """D = (a_par - a_perp) / (a_par + a_perp) of an axisymmetric drop about z (Section 3): pole and
+    equator radii, evaluated from the coefficients at the poles and at two equator points."""
+    th = np.array([0.0, math.pi, math.pi / 2, math.pi / 2])
+    ph = np.array([0.0, 0.0, 0.0, math.pi / 2])
+    r = np.linalg.norm(xc @ sh.basis(p, np.cos(th), np.sin(th), ph), axis=0)
+    a_par, a_perp = r[0] + r[1], r[2] + r[3]
+    return (a_par - a_perp) / (a_par + a_perp)
+
+
+def test_surfactant_drop_steady_deformation_follows_second_order_theory():
+    """A non-diffusing surfactant-covered drop (Pe = inf, Langmuir beta = 0.2, x_s = 0.5) in a uniform
+    field, R = 0.1, Q = 1, Ca_E = 0.05, started as a unit sphere and stepped with Algorithm 1 to its
+    steady state (Aitken's extrapolation of D at t = 1, 1.25, 1.5). Eq. DS2 (small-deformation theory
+    for this case, Section 3.2) gives D = -0.0177934 to first order and -0.0179450 to second order in
+    Ca_E; the computed steady D is far closer to the second-order value, as the paper reports for its
+    runs (Section 4.1), and the surfactant mass stays put. This exercises the electric solve, the
+    electric and Marangoni tractions, the Stokes solve and the surface transport together."""
+    p, dt = 5, 0.025
+    R, Q, Ca = 0.1, 1.0, 0.05
+    prm = P.Params(R=R, Q=Q, Ca_E=Ca, beta=0.2, x_s=0.5, gmres_tol=1e-11)
+    x = inputs.sphere_coef(p)
+    g = np.zeros(sh.ncoef(p))
+    g[0] = math.sqrt(4 * math.pi)
+    m0 = P.surfactant_mass(x, g, p)
+    samples = []
+    for k in range(1, 61):
+        xs, gs, _, _ = P.step([x], [g], [p], [1.0], dt, prm, near=False)
+        x, g = xs[0], gs[0]
+        if k in (40, 50, 60):
+            samples.append(_deformation(x, p))
+    d0, d1, d2 = samples
+    D = d2 - (d2 - d1) ** 2 / ((d2 - d1) - (d1 - d0))
+    f = 9 * ((1 + R) ** 2 - 4 * Q) / (16 * (2 + R) ** 2)
+    c2 = (R * (R * (139 * R + 264) - 696 * Q + 111) + 336 * Q - 154) / (80 * (R + 2) ** 3)
+    D1, D2 = f * Ca, f * (Ca + Ca * Ca * c2)
+    assert abs(D1 - -0.0177934) < 1e-7 and abs(D2 - -0.0179450) < 1e-7
+    assert d0 > d1 > d2 > D2 * 1.01        # flattening monotonically towards the steady state
+    assert abs(D - D2) < abs(D - D1) / 3
+    assert abs(D - D2) < 0.005 * abs(D2)
+    assert abs(P.surfactant_mass(x, g, p) - m0) / m0 < 1e-4
