@@ -11,7 +11,7 @@
 // The rotations of steps 1 and 4 run on the tensor cores (rot_tc.cu) where the degree fits.
 // Every sum and every pointwise operation here is double-float (hi + lo FP32 pairs; Dekker
 // products, Knuth sums, Newton square roots), ~2^-44 relative per operation; the tensor-core stages
-// split their operands into exact digit products (~2^-42 of the sum of magnitudes). The rows agree
+// split their operands into exact digit products (~2^-40 of the sum of magnitudes). The rows agree
 // with the FP64 build to rounding level while the FP64 pipe (1/64 of the FP32 rate here) stays idle.
 #include <algorithm>
 
