@@ -119,3 +119,16 @@ def test_digit_split_product_matches_exact_dot_products(tcd):
             # the neglected products (j_a + j_b < 5) and the digits' rounding stay near 2^-40 of
             # sum |x||T| (2^-40.0 at worst here); leaving out the lowest kept diagonal costs 2^-34
             assert abs(got - exact) <= Fraction(1, 2 ** 39) * bound
+
+
+def test_diagonal_sums_stay_exact_at_the_largest_k():
+    """Worst case of every diagonal sum from the digit bounds (row digits d5..d0 up to 128, 64, 64, 72,
+    65, 65; table digits up to 128 and 64) at the longest K each tensor-core kernel runs: 160
+    longitudes (Fourier stage, p = 39), 80 (rotations: blocks up to 2p+1 padded; Legendre stage:
+    up to 80 latitudes). Below 2^24, FP32 accumulation in tensor memory is exact."""
+    a_max = {5: 128, 4: 64, 3: 64, 2: 72, 1: 65, 0: 65}
+    b_max = {5: 128, 4: 64, 3: 64, 2: 64, 1: 64, 0: 64}
+    for K in (160, 80):
+        for s in range(6):
+            worst = K * sum(a_max[ja] * b_max[s + 5 - ja] for ja in range(6) if 0 <= s + 5 - ja <= 5)
+            assert worst < 2 ** 24, (K, s, worst)
