@@ -365,7 +365,7 @@ int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
  * SHBIM_TC_FOURIER, the GEMM of the rows' weights with the DFT table; SHBIM_TC_LEGENDRE, the
  * Legendre stage that follows it (used only together with SHBIM_TC_FOURIER); SHBIM_TC_ROTATION,
  * the pole rotations, one GEMM per latitude and degree. All apply for degrees p <= 39. They split
- * their operands into bfloat16 digits whose products accumulate exactly (error ~2^-42 of the sum
+ * their operands into bfloat16 digits whose products accumulate exactly (error ~2^-40 of the sum
  * of magnitudes per output). A stage that is off, or does not fit, runs as the double-float
  * FP32-pipe kernel. Default SHBIM_TC_FOURIER | SHBIM_TC_ROTATION (the tensor-core Legendre stage
  * measured no faster than the FP32-pipe one at p = 32); any other bit is SHBIM_ERR_ARG. */
