@@ -34,7 +34,7 @@ import inputs  # noqa: E402
 
 METRIC = "target-source kernel pairs/s, GMRES time-to-1e-8 per step: mixed/batched vs FP64"
 UNIT = "pairs/s"
-FP64_PEAK_TFLOPS = 1.25         # GB300 FP64 rate (vector and tensor), see the design doc
+FP64_PEAK_TFLOPS = 1.25         # GB300 FP64 rate (vector and tensor), 1/64 of the FP32 lane rate
 # DRAM bytes (read + write) per launch from one ncu capture of the same kernel and workload
 # (profiles/row_build_kernels_two_drops_p32.md: launches of 1 100 and 1 078 targets, mean); to be
 # dropped once the kernel changes after the capture.
@@ -359,7 +359,7 @@ def learned_warm_start(S, torch, dev, p: int = 8, n_train: int = 600, n_test: in
     iterations, initial residual and time (CUDA events)."""
     from paper_1811_10270_gb300 import warmstart
     t0 = time.perf_counter()
-    X, Y, _ = warmstart.generate(range(1, n_train + 1), p)
+    X, Y, _ = warmstart.generate(inputs.config2(p=p, seed=sd, gap=0.1) for sd in range(1, n_train + 1))
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
     net, hist = warmstart.train(X, Y, hidden=(512, 512, 512), epochs=150, batch=32, lr=1e-3)
@@ -591,7 +591,7 @@ def roofline(dom, ms, n, cfg, steps, precision, P, apps, rows_df=True):
         return {"bound": "alu", "kernel": "k_self_weights (FP64)", "achieved": ach,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                 "traffic": TRAFFIC.get("self_weights"), "launches": n, "avg_launch_ms": ms / max(1, n),
-                "peak_source": "GB300 FP64 rate 1.25 TFLOP/s (nominal, derived in DESIGN.md)",
+                "peak_source": "GB300 FP64 rate 1.25 TFLOP/s (nominal)",
                 "per_unit_flops": fp64_per_unit, "unit_of_work": "(target, rotated source node)"}
     units_a = sum(nt * ns * 14 for _ in cfg.drops) * steps * 2
     if dom == "self_analysis" and rows_df:

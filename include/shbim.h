@@ -47,6 +47,7 @@ extern "C" {
 #define SHBIM_ERR_CUDA (-2)         /* a CUDA runtime call failed */
 #define SHBIM_ERR_NOMEM (-3)        /* device allocation failed */
 #define SHBIM_ERR_NOT_CONVERGED (-4)/* GMRES hit its iteration limit */
+#define SHBIM_ERR_TIMEOUT (-5)      /* a bounded wait inside a kernel ran out (see shbim_set_wait_limit) */
 #define SHBIM_ERR_NONFINITE (-6)    /* a NaN or Inf was detected in a reduction */
 
 #define SHBIM_CONTINUE 0            /* shbim_gmres_step: not converged yet */
@@ -131,6 +132,15 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
 int shbim_set_near(shbim_ctx* ctx, int on);
 int shbim_near_pairs(shbim_ctx* ctx);
 
+/* Closest approach of the current drop set, measured by shbim_set_drops over the near pairs: the
+ * smallest distance from a target to another drop's surface, sampled at the nodes of that drop's
+ * four-times upsampled grid (at most ~0.2 h_j above the true distance), absolute (*dist_host) and
+ * in units of that drop's spacing h_j (*ratio_host); +infinity when there are no near pairs or the
+ * correction is off. The upsampled rule is validated down to 1.15 h_j (error ~1e-11 against a
+ * sixteen-times upsampled reference); a smaller ratio means targets closer than that. Either pointer
+ * may be NULL. */
+int shbim_near_min_distance(shbim_ctx* ctx, double* dist_host, double* ratio_host);
+
 /* Sizes of the current drop set: total scalar coefficients sum (p_i+1)^2, total targets
  * sum (p_i+1)(2p_i+2) and total sources sum (q_i+1)(2q_i+2). */
 int shbim_sizes(shbim_ctx* ctx, int64_t* ncoef, int64_t* ntarget, int64_t* nsource);
@@ -148,15 +158,21 @@ int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream);
 int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, double* out_dev,
                        void* stream);
 
-/* Spherical-harmonic transform of n_fields fields of one drop's degree (Section 2).
- *   drop         index of the drop whose degree p (and grid) is used
- *   dir          SHBIM_SHT_INVERSE: in = n_fields x (p+1)^2 coefficients,
- *                                  out = n_fields x grid values
- *                SHBIM_SHT_FORWARD: in = n_fields x grid values, out = coefficients
- *                (forward = Galerkin inner products by the regular rule on that grid)
- *   grid         SHBIM_GRID_BASE (degree p) or SHBIM_GRID_UP (degree 2p+1) */
-int shbim_sht(shbim_ctx* ctx, int drop, int dir, int grid, int n_fields, const double* in_dev,
-              double* out_dev, void* stream);
+/* Spherical-harmonic transforms of n_fields scalar fields, each on the drop that field_drop names
+ * (Section 2: the expansion of Eq. spharm_ex and the Galerkin inner products (., Y_nm) by the regular
+ * rule of Eq. reg_quadrature on that drop's grid). FP64.
+ *   dir            SHBIM_SHT_INVERSE: coefficients -> grid values; SHBIM_SHT_FORWARD: grid values ->
+ *                  Galerkin inner products
+ *   grid           SHBIM_GRID_BASE (degree p of the field's drop) or SHBIM_GRID_UP (degree 2p+1)
+ *   field_drop_host n_fields drop indices; field f has (p_d+1)^2 coefficients and (q+1)(2q+2) grid
+ *                  values of its drop d = field_drop_host[f] and grid degree q
+ *   in_dev, out_dev the fields concatenated in order: coefficients (inverse input, forward output)
+ *                  or grid values (inverse output, forward input), each field's block after the
+ *                  previous one's; must not alias
+ * SHBIM_ERR_ARG for a drop index out of range, a bad direction or grid, or null pointers with
+ * n_fields > 0. Consecutive fields of one drop are transformed by one launch. */
+int shbim_sht(shbim_ctx* ctx, int dir, int grid, int n_fields, const int32_t* field_drop_host,
+              const double* in_dev, double* out_dev, void* stream);
 
 /* Laplace layer operator of the electric problem applied to a scalar density on all drops:
  * for every target x0 on drop i, sum over drops j of the kernel `which` integrated over
@@ -272,26 +288,30 @@ int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* rhs_dev, co
                               double* x_dev, double inner_tol, int max_outer, int* inner_iters_host,
                               int* outer_iters_host, double* resid_host, void* stream);
 
-/* Allocation-free Laplace pair sum, for callers that must not allocate device memory at call
- * time -- for example code running while a CUDA stream is being captured into a graph, or a
- * host application that reserves all of its device memory up front. The paper has no
+/* Allocation-free Laplace pair sum, for callers that cannot allocate device memory when they call
+ * it -- for example a host application that reserves all of its device memory up front and hands
+ * out only fixed buffers, or code running where a cudaMalloc would block or fail. The paper has no
  * counterpart: this is a service variant of the FP64 all-pairs kernel.
  * Computes, for every target t, out[t] = 1/(4 pi) sum_s K(x_t, x_s) s_s over ALL sources (no
  * pair is excluded), with K = (x_t - x_s).n_t / r^3 for SHBIM_LAPLACE_DL and 1/r for
- * SHBIM_LAPLACE_SL, in FP64.
+ * SHBIM_LAPLACE_SL, in FP64. Keeping targets and sources apart is the caller's task: a source
+ * that coincides with a target (r = 0) makes that target's sum infinite (SL) or NaN (DL).
  *   tgt_dev   6 * n_tgt doubles: [x..][y..][z..][nx..][ny..][nz..] (normals unused for SL)
  *   src_dev   4 * n_src doubles: [x..][y..][z..][s..] with s the source strength
  *             (density times quadrature weight)
  *   out_dev   n_tgt doubles
+ * The C ABI cannot see the sizes of the arrays behind the pointers: they must hold the counts
+ * above (the Python binding checks its tensors).
  * Needs no context and calls no allocator: its partial sums live in one fixed array of
  * 2^21 doubles (16 MiB) in device memory, which every GPU that loads the library holds
  * until the process exits. Hence n_tgt must not exceed 2^21 (2097152); larger sizes return
  * SHBIM_ERR_ARG, as do a bad `which` or null pointers. The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) and caches it per device; make that
- * first call before any stream capture. All calls share the array: calls whose work
- * overlaps on the GPU (different streams, or different host threads) race on it and must
- * be serialised by the caller. Nothing in the array needs to start at zero (every slot read
- * is written by the same call). Returns 0, SHBIM_ERR_ARG or SHBIM_ERR_CUDA. */
+ * the array's device address (cudaGetSymbolAddress) and caches it per device. All calls share
+ * the array: calls whose work overlaps on the GPU (different streams, or different host
+ * threads) race on it and must be serialised by the caller. Nothing in the array needs to start
+ * at zero (every slot read is written by the same call). An error already pending on the device
+ * when the call starts is reported as SHBIM_ERR_CUDA without launching anything. Returns 0,
+ * SHBIM_ERR_ARG or SHBIM_ERR_CUDA. */
 int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int64_t n_tgt, const double* src_dev,
                                 int64_t n_src, double* out_dev, void* stream);
 
@@ -374,6 +394,22 @@ int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
 #define SHBIM_TC_LEGENDRE 4
 #define SHBIM_TC_ALL 7
 int shbim_set_tensor_cores(shbim_ctx* ctx, int mask);
+
+/* Limit of every bounded wait inside the library's kernels, in seconds (1e-3 .. 60; default 1).
+ * The tensor-core kernels of the singular-row build and the network wait on shared-memory
+ * barriers for their bulk copies and tensor-core products; a kernel whose wait runs out stops
+ * issuing work, lets the copies and products it has in flight land (each such wait bounded by 2 s),
+ * frees its tensor memory and returns, and the call that launched it returns SHBIM_ERR_TIMEOUT with
+ * the context still usable. (The network's GEMM has a fixed 1 s limit and marks a timed-out tile
+ * with NaN.) Takes effect at the next launch. */
+int shbim_set_wait_limit(shbim_ctx* ctx, double seconds);
+
+/* Check of the bounded-wait path (a diagnostic; the paper has no counterpart): one thread waits on
+ * a fresh shared-memory barrier with the context's wait limit. arrive != 0: the barrier's one
+ * expected arrival is made first and the call returns 0. arrive == 0: nothing arrives, the wait
+ * runs out after the limit and the call returns SHBIM_ERR_TIMEOUT. No copy or product is in flight
+ * during the wait. Allocates a 4-byte flag; synchronises `stream`. */
+int shbim_check_wait(shbim_ctx* ctx, int arrive, void* stream);
 
 /* Pipe throughput probes (a measurement utility for roofline denominators; the paper has no
  * counterpart). Launches 4 CTAs of 256 threads per SM on the current device, each thread running

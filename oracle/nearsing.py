@@ -56,6 +56,64 @@ class _Fine:
         self.w = sh.grid_weights(self.q) * J
 
 
+def _near_by_target(system, i, targets, pairs):
+    """{position in targets: [source drops j]} of the near pairs whose target lies in drop i's list."""
+    pos = {int(t): k for k, t in enumerate(targets)}
+    out = {}
+    for (ii, t, j) in (near_pairs(system) if pairs is None else pairs):
+        if ii == i and t in pos:
+            out.setdefault(pos[t], []).append(j)
+    return out
+
+
+def corrected_laplace_targets(system, kind: str, sigma, i: int, targets, pairs=None, fine=None):
+    """Values of sum_j K_j[sigma_j] at the given targets of drop i, drop j's contribution at targets
+    near S_j taken from the upsampled rule (fine: optional cache {j: _Fine})."""
+    targets = np.asarray(targets)
+    out = system.laplace_targets(kind, sigma, i, targets)
+    fine = {} if fine is None else fine
+    di = system.drops[i]
+    for k, js in _near_by_target(system, i, targets, pairs).items():
+        t = int(targets[k])
+        x0, n0 = di.x0[:, t:t + 1], di.n0[:, t:t + 1]
+        for j in js:
+            dj = system.drops[j]
+            if j not in fine:
+                fine[j] = _Fine(dj)
+            F = fine[j]
+            reg = quadrature.regular_scalar(kind, x0, n0, dj.xs, dj.ws, sh.sht_inverse(sigma[j], dj.p, dj.q))[0]
+            up = quadrature.regular_scalar(kind, x0, n0, F.x, F.w, sh.sht_inverse(sigma[j], dj.p, F.q))[0]
+            out[k] += up - reg
+    return out
+
+
+def corrected_stokes_targets(system, f, u, i: int, targets, pairs=None, fine=None):
+    """sum_j S_j[f_j] + (lam_j - 1) D_j[u_j] at the given targets of drop i, with the upsampled rule
+    at near targets."""
+    targets = np.asarray(targets)
+    out = system.stokes_targets(f, u, i, targets)
+    fine = {} if fine is None else fine
+    di = system.drops[i]
+    for k, js in _near_by_target(system, i, targets, pairs).items():
+        t = int(targets[k])
+        x0 = di.x0[:, t:t + 1]
+        for j in js:
+            dj = system.drops[j]
+            if j not in fine:
+                fine[j] = _Fine(dj)
+            F = fine[j]
+            if f is not None:
+                out[:, k] += quadrature.regular_tensor("sto_s", x0, F.x, F.n, F.w, sh.sht_inverse(f[j], dj.p, F.q))[:, 0]
+                out[:, k] -= quadrature.regular_tensor("sto_s", x0, dj.xs, dj.ns, dj.ws,
+                                                       sh.sht_inverse(f[j], dj.p, dj.q))[:, 0]
+            if u is not None and dj.lam != 1.0:
+                out[:, k] += (dj.lam - 1.0) * quadrature.regular_tensor("sto_d", x0, F.x, F.n, F.w,
+                                                                        sh.sht_inverse(u[j], dj.p, F.q))[:, 0]
+                out[:, k] -= (dj.lam - 1.0) * quadrature.regular_tensor("sto_d", x0, dj.xs, dj.ns, dj.ws,
+                                                                        sh.sht_inverse(u[j], dj.p, dj.q))[:, 0]
+    return out
+
+
 def corrected_laplace_grid(system, kind: str, sigma, pairs=None):
     """Target values of sum_j K_j[sigma_j] with drop j's contribution at near targets taken
     from the upsampled rule."""

@@ -47,6 +47,7 @@ EXPORTS = [
     "shbim_set_graphs", "shbim_set_concurrency", "shbim_pair_queue", "shbim_set_pair_queue", "shbim_laplace_beltrami", "shbim_set_diffusion",
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
     "shbim_set_outer_precision", "shbim_set_rows_precision", "shbim_set_tensor_cores",
+    "shbim_near_min_distance", "shbim_set_wait_limit", "shbim_check_wait",
 ]
 PROBE_FFMA = 0
 PROBE_DFMA = 1
@@ -54,6 +55,9 @@ PROBE_RSQRT = 2
 PROBE_HMMA_BF16 = 3
 PROBE_DMMA_F64 = 4
 NOALLOC_MAX_TARGETS = 1 << 21
+ERR_ARG = -1
+ERR_CUDA = -2
+ERR_TIMEOUT = -5
 K_SELF_WEIGHTS = 0
 K_SELF_ANALYSIS = 1
 K_PAIRS = 2
@@ -109,7 +113,7 @@ def lib():
         "shbim_set_drops": (i32, [vp, i32, P(ctypes.c_int32), P(dp), vp, vp]),
         "shbim_sizes": (i32, [vp, P(i64), P(i64), P(i64)]),
         "shbim_target_geometry": (i32, [vp, vp, vp]),
-        "shbim_sht": (i32, [vp, i32, i32, i32, i32, vp, vp, vp]),
+        "shbim_sht": (i32, [vp, i32, i32, i32, P(ctypes.c_int32), vp, vp, vp]),
         "shbim_eval_electric": (i32, [vp, i32, vp, vp, i32, vp]),
         "shbim_eval_stokes": (i32, [vp, vp, vp, vp, i32, vp]),
         "shbim_gmres_begin": (i32, [vp, i32, vp, vp, vp]),
@@ -148,6 +152,9 @@ def lib():
         "shbim_mlp_train_step": (i32, [vp, i32, vp, vp, ctypes.c_float, i32, P(dp), vp]),
         "shbim_electric_warm_start": (i32, [vp, vp, vp, vp, vp, vp]),
         "shbim_near_pairs": (i32, [vp]),
+        "shbim_near_min_distance": (i32, [vp, P(dp), P(dp)]),
+        "shbim_set_wait_limit": (i32, [vp, dp]),
+        "shbim_check_wait": (i32, [vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -178,13 +185,16 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def pairs_laplace_noalloc(which: int, tgt, src, out, n_tgt=None, n_src=None) -> int:
+def pairs_laplace_noalloc(which: int, tgt, src, out) -> int:
     """shbim_pairs_laplace_noalloc: FP64 Laplace pair sum of src (4 x n_src: x, y, z, strength)
-    at tgt (6 x n_tgt: x, y, z, nx, ny, nz) into out, without any device allocation. Returns the
-    library's status code (0 on success)."""
+    at tgt (6 x n_tgt: x, y, z, nx, ny, nz) into out (n_tgt), without any device allocation.
+    The counts come from out and src; the tensors must hold them (the C ABI cannot check).
+    Returns the library's status code (0 on success)."""
     L = lib()
-    nt = out.numel() if n_tgt is None else int(n_tgt)
-    ns = src.numel() // 4 if n_src is None else int(n_src)
+    nt = out.numel()
+    ns = src.numel() // 4
+    if tgt.numel() < 6 * nt or src.numel() != 4 * ns:
+        raise ShbimError("pairs_laplace_noalloc: tgt must hold 6 x n_tgt and src 4 x n_src doubles")
     return int(L.shbim_pairs_laplace_noalloc(int(which), _ptr(tgt), nt, _ptr(src), ns, _ptr(out),
                                              _stream()))
 
@@ -247,9 +257,12 @@ class Context:
                     "shbim_target_geometry")
 
     # ---------------------------------------------------------------- operators
-    def sht(self, drop: int, direction: int, grid: int, n_fields: int, inp, out):
-        self._check(self._L.shbim_sht(self._h, drop, direction, grid, n_fields, _ptr(inp), _ptr(out),
-                                      _stream()), "shbim_sht")
+    def sht(self, direction: int, grid: int, field_drop, inp, out):
+        """shbim_sht: transform len(field_drop) fields, field f on drop field_drop[f]."""
+        n = len(field_drop)
+        fd = (ctypes.c_int32 * max(1, n))(*[int(d) for d in field_drop])
+        self._check(self._L.shbim_sht(self._h, direction, grid, n, fd, _ptr(inp), _ptr(out), _stream()),
+                    "shbim_sht")
 
     def eval_electric(self, which: int, dens, out, out_kind: int = OUT_COEF):
         self._check(self._L.shbim_eval_electric(self._h, which, _ptr(dens), _ptr(out), out_kind,
@@ -380,6 +393,20 @@ class Context:
 
     def set_near(self, on: bool):
         self._check(self._L.shbim_set_near(self._h, 1 if on else 0), "shbim_set_near")
+
+    def near_min_distance(self):
+        """(smallest near-target distance to another drop's surface, the same in units of h_j)."""
+        d, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.shbim_near_min_distance(self._h, ctypes.byref(d), ctypes.byref(r)),
+                    "shbim_near_min_distance")
+        return d.value, r.value
+
+    def set_wait_limit(self, seconds: float):
+        self._check(self._L.shbim_set_wait_limit(self._h, float(seconds)), "shbim_set_wait_limit")
+
+    def check_wait(self, arrive: bool) -> int:
+        """shbim_check_wait: returns the library's status code (0, or SHBIM_ERR_TIMEOUT = -5)."""
+        return int(self._L.shbim_check_wait(self._h, 1 if arrive else 0, _stream()))
 
     def near_pairs(self) -> int:
         return int(self._L.shbim_near_pairs(self._h))

@@ -208,6 +208,14 @@ int shbim_set_R(shbim_ctx* ctx, double R) {
 
 int64_t shbim_launch_count(shbim_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+int shbim_set_wait_limit(shbim_ctx* ctx, double seconds) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (!(seconds >= 1e-3 && seconds <= 60.0)) return fail(ctx, SHBIM_ERR_ARG, "wait limit must be in [1e-3, 60] s");
+  ctx->wait_ns = (uint64_t)(seconds * 1e9);
+  ctx->geom_version++;  // captured graphs hold the old limit as a kernel argument
+  return SHBIM_OK;
+}
+
 int64_t shbim_operator_applications(shbim_ctx* ctx) { return ctx ? ctx->applications : -1; }
 
 int shbim_set_rows_precision(shbim_ctx* ctx, int precision) {
@@ -426,20 +434,41 @@ int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream) {
   return SHBIM_OK;
 }
 
-int shbim_sht(shbim_ctx* ctx, int drop, int dir, int grid, int n_fields, const double* in_dev,
-              double* out_dev, void* stream) {
+int shbim_sht(shbim_ctx* ctx, int dir, int grid, int n_fields, const int32_t* field_drop_host,
+              const double* in_dev, double* out_dev, void* stream) {
   if (!ctx) return SHBIM_ERR_ARG;
-  if (drop < 0 || drop >= ctx->n_drops) return fail(ctx, SHBIM_ERR_ARG, "drop index out of range");
-  if (n_fields < 0 || !in_dev || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "bad fields or pointers");
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (n_fields < 0 || (n_fields > 0 && (!field_drop_host || !in_dev || !out_dev)))
+    return fail(ctx, SHBIM_ERR_ARG, "bad fields or pointers");
   if (grid != SHBIM_GRID_BASE && grid != SHBIM_GRID_UP) return fail(ctx, SHBIM_ERR_ARG, "bad grid");
-  const Drop& d = ctx->drops[drop];
-  const GridTables& g = grid == SHBIM_GRID_BASE ? d.tab->base : d.tab->up;
-  const int64_t n = npts(g.q);
+  if (dir != SHBIM_SHT_INVERSE && dir != SHBIM_SHT_FORWARD) return fail(ctx, SHBIM_ERR_ARG, "bad direction");
+  for (int f = 0; f < n_fields; ++f)
+    if (field_drop_host[f] < 0 || field_drop_host[f] >= ctx->n_drops)
+      return fail(ctx, SHBIM_ERR_ARG, "field_drop: drop index out of range");
   cudaStream_t s = (cudaStream_t)stream;
-  if (dir == SHBIM_SHT_INVERSE)
-    return sht_synth(ctx, g, n_fields, in_dev, d.nc, 1, out_dev, n, 0, nullptr, nullptr, s);
-  if (dir == SHBIM_SHT_FORWARD) return sht_analysis(ctx, g, n_fields, in_dev, n, true, out_dev, d.nc, s);
-  return fail(ctx, SHBIM_ERR_ARG, "bad direction");
+  // fields are concatenated, each with its own drop's coefficient count and grid size; a run of
+  // consecutive fields of one drop is one transform launch
+  int64_t in_off = 0, out_off = 0;
+  for (int f = 0, g; f < n_fields; f = g) {
+    g = f + 1;
+    while (g < n_fields && field_drop_host[g] == field_drop_host[f]) ++g;
+    const Drop& d = ctx->drops[field_drop_host[f]];
+    const GridTables& T = grid == SHBIM_GRID_BASE ? d.tab->base : d.tab->up;
+    const int64_t n = npts(T.q);
+    const int nf = g - f;
+    int rc;
+    if (dir == SHBIM_SHT_INVERSE) {
+      rc = sht_synth(ctx, T, nf, in_dev + in_off, d.nc, 1, out_dev + out_off, n, 0, nullptr, nullptr, s);
+      in_off += (int64_t)nf * d.nc;
+      out_off += (int64_t)nf * n;
+    } else {
+      rc = sht_analysis(ctx, T, nf, in_dev + in_off, n, true, out_dev + out_off, d.nc, s);
+      in_off += (int64_t)nf * n;
+      out_off += (int64_t)nf * d.nc;
+    }
+    if (rc) return rc;
+  }
+  return SHBIM_OK;
 }
 
 }  // extern "C"

@@ -43,6 +43,8 @@ namespace {
 using namespace tc;
 
 constexpr int kNT = 80;                       // outputs per tile (MMA N)
+// K = 2q + 2 = 4(p + 1) longitudes, at most 2 kNT (2p + 2 <= kNT)
+static_assert(diag_sums_exact(2 * kNT), "Fourier stage: digit sums must stay exact in FP32");
 constexpr int kProducers = 512;                // digit-writing and epilogue threads (16 warps)
 constexpr int kThreadsTC = kProducers + 32;    // + one warp that issues the MMAs
 constexpr int kPlaneA = kMT * kKS;            // bf16 per row-digit plane (4096 B)
@@ -55,7 +57,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const uint4* __restrict__ tdig,
-         int ksteps, const int* __restrict__ rexp, float2* __restrict__ F, int omajor, int* __restrict__ err) {
+         int ksteps, const int* __restrict__ rexp, float2* __restrict__ F, int omajor, int* __restrict__ err,
+         uint64_t wlim) {
   // dynamic shared memory: [the table's digit planes for every K step, resident][two stages of row
   // digit planes]
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -90,7 +93,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
   const uint32_t tbytes = (uint32_t)ksteps * kDig * kPlaneB * 2;
   if (tid == 0 && (int64_t)blockIdx.x < total) bulk_load(sB, tdig, tbytes, &tbar);
   bool table_ok = true;
-  if ((int64_t)blockIdx.x < total) table_ok = mbar_wait(&tbar, 0);
+  if ((int64_t)blockIdx.x < total) table_ok = mbar_wait(&tbar, 0, wlim);
   const uint32_t tmem = tmem_base;
   // uses of each stage so far (the same count in every thread): fill u waits for the products of
   // fill u - 1 (parity (u - 1) & 1 of `empty`), the MMA warp waits for fill u (parity u & 1 of `full`)
@@ -157,7 +160,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
           q0[i2] = q1[i2];
         }
         load_step(ks + 2, q1);
-        if (uses[st] > 0 && !mbar_wait(&empty[st], (uses[st] - 1) & 1)) {
+        if (uses[st] > 0 && !mbar_wait(&empty[st], (uses[st] - 1) & 1, wlim)) {
           bad = true;
           break;
         }
@@ -189,7 +192,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
     } else if (tid == kProducers) {
       for (int ks = 0; ks < ksteps; ++ks) {
         const int st = ks & 1;
-        if (!mbar_wait(&full[st], uses[st] & 1)) {
+        if (!mbar_wait(&full[st], uses[st] & 1, wlim)) {
           bad = true;
           break;
         }
@@ -222,7 +225,7 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
     // all products of the tile complete: the last commit covers every earlier product
     {
       const int st = (ksteps - 1) & 1;
-      if (__syncthreads_or(!mbar_wait(&empty[st], (uses[st] - 1) & 1))) {
+      if (__syncthreads_or(!mbar_wait(&empty[st], (uses[st] - 1) & 1, wlim))) {
         abort_all = true;
         break;
       }
@@ -260,8 +263,8 @@ k_dft_tc(const float2* __restrict__ W, int64_t rows, int nlon, int nout, const u
   // let products and copies still in flight finish (bounded) before resources are released
   if (abort_all) {
     for (int st = 0; st < 2; ++st)
-      if (uses[st] > 0) mbar_wait(&empty[st], (uses[st] - 1) & 1);
-    if (!table_ok && tid == 0) mbar_wait(&tbar, 0);
+      if (uses[st] > 0) mbar_wait(&empty[st], (uses[st] - 1) & 1, kDrainNs);
+    if (!table_ok && tid == 0) mbar_wait(&tbar, 0, kDrainNs);
     if (tid == 0) atomicExch(err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -326,7 +329,8 @@ int analysis_fourier_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* W, 
   const int64_t tiles = (rows + kMT - 1) / kMT;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
   k_dft_tc<<<grid, kThreadsTC, smem, s>>>(W, rows, nlon, nout, reinterpret_cast<const uint4*>(T.dft_digits),
-                                          T.dft_ksteps, rexp, F, omajor ? 1 : 0, ctx->tc_err);
+                                          T.dft_ksteps, rexp, F, omajor ? 1 : 0, ctx->tc_err,
+                                          ctx->wait_ns);
   SHBIM_CHECK_LAUNCH(ctx, "k_dft_tc");
   return SHBIM_OK;
 }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -172,6 +173,7 @@ struct shbim_ctx {
   bool tc_rot = true;             // ... and the degree-block rotations (rot_tc.cu)
   bool tc_leg = false;            // ... and the Legendre stage of the analysis (leg_tc.cu; opt-in)
   int* tc_err = nullptr;          // device flag: a tensor-core kernel timed out
+  uint64_t wait_ns = 1000000000ull;  // limit of every bounded wait inside a kernel (nanoseconds)
   // workspaces
   double* dens_up = nullptr;      // [3][nsource] source strengths (FP64)
   float* dens_up32 = nullptr;     // [6][nsource] source strengths (FP32)
@@ -217,6 +219,8 @@ struct shbim_ctx {
   struct Near {
     bool enabled = true;
     int npairs = 0;
+    double min_dist = INFINITY;   // smallest near-target distance to another drop's upsampled nodes
+    double min_ratio = INFINITY;  // the same in units of that drop's spacing h_j
     double* stats = nullptr;  size_t stats_cap = 0;
     int64_t* det_t = nullptr; size_t det_t_cap = 0;
     int* det_j = nullptr;     size_t det_j_cap = 0;

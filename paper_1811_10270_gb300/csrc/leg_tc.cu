@@ -34,6 +34,7 @@ constexpr int kProducers = 256;
 constexpr int kThreads = kProducers + 32;
 constexpr int kNmax = 48;                      // largest padded table height (p + 1 <= 40)
 constexpr int kKmax = 80;                      // latitudes q + 1 = 2p + 2 <= 80
+static_assert(diag_sums_exact(kKmax), "Legendre stage: digit sums must stay exact in FP32");
 constexpr int kPlaneA = kMT * kKS;
 constexpr int kPlaneBmax = kNmax * kKS;
 constexpr uint32_t kTmemCols = 512;
@@ -63,7 +64,7 @@ struct LegItems {
 __global__ void __launch_bounds__(kThreads, 1)
 k_leg_tc(const float2* __restrict__ FT, int64_t nitems, int p, const uint4* __restrict__ tdig,
          const int* __restrict__ toff, const signed char* __restrict__ texp, float2* __restrict__ coef,
-         int64_t coef_stride, int* __restrict__ err) {
+         int64_t coef_stride, int* __restrict__ err, uint64_t wlim) {
   // dynamic shared memory: [the current order's table planes][two stages of row digit planes]
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[2];
@@ -179,7 +180,7 @@ k_leg_tc(const float2* __restrict__ FT, int64_t nitems, int p, const uint4* __re
           q0[i] = q1[i];
         }
         load_step(ks + 2, q1);
-        if (uses[st] > 0 && !mbar_wait(&empty[st], (uses[st] - 1) & 1)) {
+        if (uses[st] > 0 && !mbar_wait(&empty[st], (uses[st] - 1) & 1, wlim)) {
           bad = true;
           break;
         }
@@ -208,13 +209,13 @@ k_leg_tc(const float2* __restrict__ FT, int64_t nitems, int p, const uint4* __re
       }
     } else if (tid == kProducers) {
       if (tpend) {
-        if (!mbar_wait(&tbar, tphase)) bad = true;
+        if (!mbar_wait(&tbar, tphase, wlim)) bad = true;
         tphase ^= 1u;
         tpend = false;
       }
       for (int ks = 0; ks < ksteps && !bad; ++ks) {
         const int st = ks & 1;
-        if (!mbar_wait(&full[st], uses[st] & 1)) {
+        if (!mbar_wait(&full[st], uses[st] & 1, wlim)) {
           bad = true;
           break;
         }
@@ -242,7 +243,7 @@ k_leg_tc(const float2* __restrict__ FT, int64_t nitems, int p, const uint4* __re
     }
     {
       const int st = (ksteps - 1) & 1;
-      if (__syncthreads_or(!mbar_wait(&empty[st], (uses[st] - 1) & 1))) {
+      if (__syncthreads_or(!mbar_wait(&empty[st], (uses[st] - 1) & 1, wlim))) {
         abort_all = true;
         break;
       }
@@ -282,10 +283,10 @@ k_leg_tc(const float2* __restrict__ FT, int64_t nitems, int p, const uint4* __re
   }
   if (abort_all) {
     for (int st = 0; st < 2; ++st)
-      if (uses[st] > 0) mbar_wait(&empty[st], (uses[st] - 1) & 1);
+      if (uses[st] > 0) mbar_wait(&empty[st], (uses[st] - 1) & 1, kDrainNs);
     if (tid == 0) atomicExch(err, 1);
   }
-  if (tpend && tid == kProducers) mbar_wait(&tbar, tphase);
+  if (tpend && tid == kProducers) mbar_wait(&tbar, tphase, kDrainNs);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
@@ -366,7 +367,7 @@ int analysis_legendre_tc(shbim_ctx* ctx, const DegreeTables& T, const float2* FT
   const LegItems I(p, nitems);
   const unsigned grid = (unsigned)std::min<int64_t>(I.total, nsm);
   k_leg_tc<<<grid, kThreads, smem, s>>>(FT, nitems, p, reinterpret_cast<const uint4*>(T.leg_digits), T.leg_toff,
-                                        T.leg_exp, coef, coef_stride, ctx->tc_err);
+                                        T.leg_exp, coef, coef_stride, ctx->tc_err, ctx->wait_ns);
   SHBIM_CHECK_LAUNCH(ctx, "k_leg_tc");
   return SHBIM_OK;
 }

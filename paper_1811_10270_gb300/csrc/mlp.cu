@@ -119,12 +119,18 @@ k_gemm_tc(int M, int N, int K, const TA* __restrict__ A, int64_t sam, int64_t sa
           smem_u32(&mbar)));
     }
     // the staged tiles may be overwritten only after the MMAs that read them have completed
+    // (bounded by one second of the global timer)
     uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it) {
+    uint64_t t0 = 0;
+    for (int it = 0; !done; ++it) {
       asm volatile(
           "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
           : "=r"(done)
           : "r"(smem_u32(&mbar)), "r"(phase));
+      uint64_t t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (it == 0) t0 = t;
+      else if (!done && t - t0 > 1000000000ull) break;
     }
     phase ^= 1;
     // leave the K loop together: a barrier count mismatch would hang the CTA

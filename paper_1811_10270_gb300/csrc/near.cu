@@ -14,6 +14,7 @@
 // accumulation as the all-pairs kernel; the FP64 variant plain FP64.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "dfloat.cuh"
 #include "internal.h"
@@ -105,6 +106,38 @@ __global__ void k_near_detect(const double* __restrict__ tgt, int64_t ntarget, c
         pair_j[k] = j;
       }
     }
+  }
+}
+
+// Smallest distance from a near target to drop j's surface, sampled on j's upsampled grid (node
+// spacing h_j / 4, so the sampled value exceeds the true distance by at most ~0.2 h_j): one warp per
+// near pair, FP32 centre-relative coordinates; the squared distance and its ratio to h_j^2 are folded
+// into two global minima (non-negative floats order like their bit patterns).
+__global__ void k_near_min_dist(const double* __restrict__ tgt, int64_t ntarget, const int64_t* __restrict__ pair_t,
+                                const int* __restrict__ pair_j, int npairs, const DropDev* __restrict__ drops,
+                                int n_drops, const float* __restrict__ fgeo32, int64_t nfine,
+                                const int64_t* __restrict__ foff /* [2][n_drops]: offset, count */,
+                                const double* __restrict__ stats /* area, R, lim per drop */,
+                                unsigned* __restrict__ mins /* d^2, d^2 / h^2 */) {
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // uniform over the warp
+  const int lane = threadIdx.x & 31;
+  if (k >= npairs) return;
+  const int64_t t = pair_t[k];
+  const int j = pair_j[k];
+  const DropDev D = drops[j];
+  const float rx = (float)(tgt[t] - D.cx), ry = (float)(tgt[ntarget + t] - D.cy), rz = (float)(tgt[2 * ntarget + t] - D.cz);
+  const int64_t o = foff[j], n = foff[n_drops + j];
+  float best = 3.0e38f;
+  for (int64_t e = lane; e < n; e += 32) {
+    const float dx = rx - fgeo32[o + e], dy = ry - fgeo32[nfine + o + e], dz = rz - fgeo32[2 * nfine + o + e];
+    best = fminf(best, fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  }
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, sh));
+  if (lane == 0) {
+    const double h2 = stats[3 * j] / D.ns;   // h_j^2 = area_j / N_s
+    atomicMin(&mins[0], __float_as_uint(best));
+    atomicMin(&mins[1], __float_as_uint((float)(best / h2)));
   }
 }
 
@@ -550,6 +583,7 @@ int grow(shbim_ctx* ctx, void** p, size_t* cap, size_t bytes, const char* what) 
 int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
   auto& N = ctx->near;
   N.npairs = 0;
+  N.min_dist = N.min_ratio = INFINITY;
   if (!N.enabled || ctx->n_drops < 2) return SHBIM_OK;
   const int nd = ctx->n_drops;
   int rc;
@@ -657,6 +691,29 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
     if (rc == SHBIM_OK)
       rc = geometry_kernel32(ctx, tmp, n, 3, fine, N.fgeo, N.fgeo32, nfine, N.fine_off_h[j], d.centre, s,
                              N.fgeo32lo);
+  }
+  if (rc == SHBIM_OK) {
+    // smallest target-to-surface distance over the near pairs (sampled on the upsampled grids)
+    unsigned* mins = reinterpret_cast<unsigned*>(tmp);
+    const unsigned init[2] = {0x7f7fffffu, 0x7f7fffffu};
+    cudaMemcpyAsync(mins, init, sizeof(init), cudaMemcpyHostToDevice, s);
+    k_near_min_dist<<<nb((int64_t)cnt * 32), 256, 0, s>>>(ctx->geo.tgt, ctx->ntarget, N.pair_t, N.pair_j, cnt,
+                                                         ctx->drops_dev, nd, N.fgeo32, nfine, N.foff_dev, N.stats,
+                                                         mins);
+    ctx->launches++;
+    unsigned h[2] = {0u, 0u};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, mins, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(ctx, e, "k_near_min_dist");
+    } else {
+      float d2, r2;
+      std::memcpy(&d2, &h[0], sizeof(float));
+      std::memcpy(&r2, &h[1], sizeof(float));
+      N.min_dist = std::sqrt((double)d2);
+      N.min_ratio = std::sqrt((double)r2);
+    }
   }
   cudaStreamSynchronize(s);
   cudaFree(tmp);
@@ -771,3 +828,10 @@ extern "C" int shbim_set_near(shbim_ctx* ctx, int on) {
 }
 
 extern "C" int shbim_near_pairs(shbim_ctx* ctx) { return ctx ? ctx->near.npairs : -1; }
+
+extern "C" int shbim_near_min_distance(shbim_ctx* ctx, double* dist_host, double* ratio_host) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (dist_host) *dist_host = ctx->near.min_dist;
+  if (ratio_host) *ratio_host = ctx->near.min_ratio;
+  return SHBIM_OK;
+}

@@ -108,6 +108,9 @@ using namespace shbim;
 extern "C" int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int64_t n_tgt,
                                            const double* src_dev, int64_t n_src, double* out_dev,
                                            void* stream) {
+  // an error left pending by earlier, unrelated work belongs to that work: report it without
+  // launching (and without clearing it), so it is not taken for this call's own failure
+  if (cudaPeekAtLastError() != cudaSuccess) return SHBIM_ERR_CUDA;
   if (which != SHBIM_LAPLACE_DL && which != SHBIM_LAPLACE_SL) return SHBIM_ERR_ARG;
   if (n_tgt < 0 || n_src < 0) return SHBIM_ERR_ARG;
   if (n_tgt > kScratchDoubles) return SHBIM_ERR_ARG;
@@ -118,9 +121,10 @@ extern "C" int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t tiles = (n_tgt + kTileT - 1) / kTileT;
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    return SHBIM_ERR_CUDA;
   int64_t splits = ((int64_t)nsm * 8 + tiles - 1) / tiles;
   splits = std::min<int64_t>(splits, std::max<int64_t>(1, n_src / kTileS));
   splits = std::min<int64_t>(splits, kScratchDoubles / n_tgt);

@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace shbim {
 namespace {
@@ -155,5 +156,41 @@ extern "C" int shbim_probe_peak(int kind, int64_t iters, double* ops_per_s_host,
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   cudaFree(sink);
+  return rc;
+}
+
+namespace shbim {
+namespace {
+
+// one thread waits on a fresh mbarrier (expected arrivals: 1) with the bounded wait of the
+// tensor-core kernels; the arrival is made first or not at all
+__global__ void k_wait_check(int arrive, uint64_t limit_ns, int* __restrict__ flag) {
+  __shared__ __align__(8) uint64_t bar;
+  tc::mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n");
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(tc::smem_u32(&bar)) : "memory");
+  if (!tc::mbar_wait(&bar, 0, limit_ns)) *flag = 1;
+}
+
+}  // namespace
+}  // namespace shbim
+
+extern "C" int shbim_check_wait(shbim_ctx* ctx, int arrive, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc wait flag");
+  int h = 0, rc = SHBIM_OK;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_check<<<1, 1, 0, s>>>(arrive, ctx->wait_ns, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) rc = cuda_fail(ctx, e, "wait check");
+  else if (h) rc = fail(ctx, SHBIM_ERR_TIMEOUT, "wait check: the bounded wait ran out");
+  ctx->launches++;
+  cudaFree(flag);
   return rc;
 }

@@ -37,6 +37,7 @@ using namespace tc;
 
 constexpr int kThreads = 512;
 constexpr int kNmax = 80;                                  // largest padded block (N and K)
+static_assert(diag_sums_exact(kNmax), "rotations: digit sums must stay exact in FP32");
 constexpr int kPlaneA = kMT * kKS;                          // bf16 per row-digit plane
 constexpr int kPlaneBmax = kNmax * kKS;                     // bf16 per table-digit plane
 constexpr int kStageBytes = kDig * (kPlaneA + kPlaneBmax) * 2;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int ct, int ncomp,
             const float2* __restrict__ cs_phi, const uint4* __restrict__ tdig, const int* __restrict__ toff,
             const signed char* __restrict__ texp, float2* __restrict__ vout, float* __restrict__ rows_lap,
-            float* __restrict__ rows_sto, int nt_drop, int* __restrict__ err) {
+            float* __restrict__ rows_sto, int nt_drop, int* __restrict__ err, uint64_t wlim) {
   // dynamic shared memory: [two MMA stages][value block 128 x (2p+1)][(cos, sin)(m phi) of the
   // item's targets, 2 (p+1) each]
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -230,7 +231,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
     for (int ks = 0; ks < ksteps; ++ks) {
       const int st = ks & 1;
       if (pending[st]) {
-        const bool ok = mbar_wait(&mbar[st], phase[st]);
+        const bool ok = mbar_wait(&mbar[st], phase[st], wlim);
         phase[st] ^= 1u;
         pending[st] = false;
         if (__syncthreads_or(!ok)) {
@@ -265,7 +266,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
       if (tid == 0) {
         // the table planes have landed (bounded; on expiry the products are skipped and the
         // caller sees the error flag)
-        if (!mbar_wait(&bbar[st], bphase[st])) atomicExch(err, 1);
+        if (!mbar_wait(&bbar[st], bphase[st], wlim)) atomicExch(err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const uint32_t a0 = smem_u32(base), b0 = smem_u32(base + kDig * kPlaneA * 2);
         // row digit j_a against up to three consecutive table digits in one MMA of N = Np g (the
@@ -285,7 +286,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
         // the table planes of K step ks + 1 go to the other stage once its products are done
         // (step 1's planes were issued with step 0's)
         if (ks >= 1 && ks + 1 < ksteps) {
-          mbar_wait(&mbar[st ^ 1], phase[st ^ 1]);
+          mbar_wait(&mbar[st ^ 1], phase[st ^ 1], wlim);
           issue_b(lat, n, ks + 1, st ^ 1);
         }
       }
@@ -298,7 +299,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
     bool ok = true;
     for (int st = 0; st < 2; ++st)
       if (pending[st]) {
-        ok = ok && mbar_wait(&mbar[st], phase[st]);
+        ok = ok && mbar_wait(&mbar[st], phase[st], wlim);
         phase[st] ^= 1u;
         pending[st] = false;
       }
@@ -364,8 +365,8 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
   }
   // let products and copies still in flight finish (bounded) before the memory is released
   for (int st = 0; st < 2; ++st) {
-    if (pending[st]) mbar_wait(&mbar[st], phase[st]);
-    if (bpend[st] && tid == 0) mbar_wait(&bbar[st], bphase[st]);
+    if (pending[st]) mbar_wait(&mbar[st], phase[st], kDrainNs);
+    if (bpend[st] && tid == 0) mbar_wait(&bbar[st], bphase[st], kDrainNs);
   }
   if (abort_all && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -486,12 +487,12 @@ int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2*
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_rotate_tc<true><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_phi_df, tdig,
                                                    T.rot_toff, T.rot_exp, vout, rows_lap, rows_sto, nt_drop,
-                                                   ctx->tc_err);
+                                                   ctx->tc_err, ctx->wait_ns);
   } else {
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_rotate_tc<false><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_phi_df, tdig,
                                                     T.rot_toff, T.rot_exp, vout, rows_lap, rows_sto, nt_drop,
-                                                   ctx->tc_err);
+                                                   ctx->tc_err, ctx->wait_ns);
   }
   SHBIM_CHECK_LAUNCH(ctx, "k_rotate_tc");
   return SHBIM_OK;

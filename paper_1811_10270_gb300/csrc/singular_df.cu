@@ -604,7 +604,7 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
     if (flag) {
       SHBIM_CUDA(ctx, cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s));
-      return fail(ctx, SHBIM_ERR_CUDA, "tensor-core row build: a bounded wait expired");
+      return fail(ctx, SHBIM_ERR_TIMEOUT, "tensor-core row build: a bounded wait expired");
     }
   }
   return SHBIM_OK;

@@ -24,7 +24,6 @@ namespace tc {
 
 constexpr int kMT = 128;         // rows per tile (MMA M = tensor-memory lanes)
 constexpr int kKS = 16;          // K per MMA
-constexpr int kWaitLimit = 1 << 24;
 
 // element (row n, k) of one K-major canonical plane of K = 16: 8-row x 16-byte core matrices,
 // [row group][k chunk][row % 8][k % 8]
@@ -46,16 +45,33 @@ __host__ __device__ inline uint32_t idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kMT >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// nanoseconds of the device's global timer
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase of parity `parity` of an mbarrier to complete, for at most limit_ns
+// nanoseconds (the limit is the launching context's wait limit); false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   uint32_t done = 0;
-  for (int it = 0; it < kWaitLimit && !done; ++it) {
+  uint64_t t0 = 0;
+  for (int it = 0;; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(smem_u32(bar)), "r"(parity));
+    if (done) return true;
+    const uint64_t t = global_ns();
+    if (it == 0) t0 = t;
+    else if (t - t0 > limit_ns) return false;
   }
-  return done != 0;
 }
+
+// limit of the waits that drain a CTA's own copies and products after a timeout, before it frees
+// its shared and tensor memory: long enough for any operation in flight to land
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));

@@ -62,6 +62,26 @@ TC_FN void digits6(float yh, float yl, float (&d)[kDig]) {
   d[0] = rintf(r);
 }
 
+// Largest |digit| by position (row operand after digits6; table operand after digits_host) and the
+// worst case of diagonal sum s (products with j_a + j_b = s + 5) over K products: every tensor-core
+// kernel asserts at compile time that this stays below 2^24 at its longest K, so that the FP32
+// accumulation in tensor memory is exact.
+constexpr int kRowDigitMax[kDig] = {65, 65, 72, 64, 64, 128};
+constexpr int kTabDigitMax[kDig] = {64, 64, 64, 64, 64, 128};
+constexpr long long diag_sum_bound(int K, int s) {
+  long long w = 0;
+  for (int ja = 0; ja < kDig; ++ja) {
+    const int jb = s + kDig - 1 - ja;
+    if (jb >= 0 && jb < kDig) w += (long long)kRowDigitMax[ja] * kTabDigitMax[jb];
+  }
+  return w * K;
+}
+constexpr bool diag_sums_exact(int K) {
+  for (int s = 0; s < kDig; ++s)
+    if (diag_sum_bound(K, s) >= (1LL << 24)) return false;
+  return true;
+}
+
 // sum_s acc_s 2^(7 (s - 5)) as a double-float from the six exact FP32 diagonal sums
 // (|acc_s| < 2^24): the three top terms are exact in FP32 and joined by two-sums; the three lowest
 // (weights 2^-21 and below) are summed in plain FP32, rounding below 2^-21 units of the top term.

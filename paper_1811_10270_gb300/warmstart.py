@@ -1,8 +1,9 @@
 """Training driver of the learned electric warm start (host orchestration only; every
 product, activation, gradient and optimiser step runs in libshbim's kernels).
 
-Samples are two-drop configurations (the two-drop workload generator with different seeds);
-each is solved by the library's own FP64 GMRES, so the network learns from the method itself.
+Samples are drop configurations the caller supplies (objects with `drops`, each drop having `p`,
+`xcoef` and `lam`, plus the conductivity ratio `R` and the uniform field `E_u`); each is solved by
+the library's own FP64 GMRES, so the network learns from the method itself.
 Inputs are the position coefficients of both drops; targets are the correction of E_n to the
 sphere solution 3(R+1)/(R+2) rhs. Inputs and targets are standardised for training and the
 standardisation is then attached to the network -- the input part as the network's FP32
@@ -14,19 +15,17 @@ from __future__ import annotations
 
 import numpy as np
 
-import inputs
-
 from . import FP64, SYS_ELECTRIC, Context, MLP
 
 
-def generate(seeds, p: int, gap: float = 0.1, tol: float = 1e-10):
-    """(features [n, 3 ncoef], targets [n, ncoef], iterations from zero) for the given seeds."""
+def generate(configs, tol: float = 1e-10):
+    """(features [n, 3 ncoef], targets [n, ncoef], iterations from zero) for the given drop
+    configurations (all of one layout)."""
     import torch
     dev = torch.device("cuda")
     X, Y, its = [], [], []
     ctx = None
-    for sd in seeds:
-        cfg = inputs.config2(p=p, seed=int(sd), gap=gap)
+    for cfg in configs:
         if ctx is None:
             ctx = Context(precision=FP64, R=cfg.R, gmres_tol=tol)
         x = np.concatenate([d.xcoef.ravel() for d in cfg.drops])

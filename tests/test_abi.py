@@ -62,3 +62,25 @@ def test_set_drops_rejects_bad_degrees(lib):
         assert lib.shbim_set_drops(h, 1, P, None, ctypes.c_void_p(16), None) == -1
     assert lib.shbim_set_drops(h, 0, None, None, None, None) == -1
     lib.shbim_destroy(h)
+
+
+def test_header_error_codes_match_the_binding():
+    hdr = open(os.path.join(ROOT, "include", "shbim.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"#define SHBIM_(ERR_[A-Z_]+) \((-?\d+)\)", hdr))
+    assert codes["ERR_TIMEOUT"] == S.ERR_TIMEOUT == -5
+    assert codes["ERR_ARG"] == S.ERR_ARG and codes["ERR_CUDA"] == S.ERR_CUDA
+
+
+def test_host_side_argument_checks(lib):
+    import ctypes
+    h = ctypes.c_void_p()
+    assert lib.shbim_create(None, ctypes.byref(h)) == 0
+    assert lib.shbim_set_wait_limit(h, 0.0) == -1 and b"wait limit" in lib.shbim_last_error(h)
+    assert lib.shbim_set_wait_limit(h, 1e9) == -1
+    assert lib.shbim_set_wait_limit(h, 0.5) == 0
+    fd = (ctypes.c_int32 * 1)(0)
+    assert lib.shbim_sht(h, 0, 0, 1, fd, None, None, None) == -1   # no drops set
+    d, r = ctypes.c_double(), ctypes.c_double()
+    assert lib.shbim_near_min_distance(h, ctypes.byref(d), ctypes.byref(r)) == 0
+    assert d.value == float("inf") and r.value == float("inf")
+    lib.shbim_destroy(h)

@@ -82,7 +82,7 @@ def test_trained_warm_start_saves_gmres_iterations(S):
     solutions GMRES reaches from any start agree (GMRES judges the error)."""
     from paper_1811_10270_gb300 import warmstart
     p = 6
-    Xtr, Ytr, _ = warmstart.generate(range(1, 601), p)
+    Xtr, Ytr, _ = warmstart.generate(inputs.config2(p=p, seed=sd, gap=0.1) for sd in range(1, 601))
     net, hist = warmstart.train(Xtr, Ytr, hidden=(256, 256, 256), epochs=150, batch=32, lr=1e-3)
     assert hist[-1] < 0.2 * hist[0]
     counts = {"zero": [], "sphere": [], "learned": []}

@@ -79,12 +79,38 @@ def test_sht_matches_oracle(S, p):
     for grid, q in ((S.GRID_BASE, p), (S.GRID_UP, 2 * p + 1)):
         n = (q + 1) * (2 * q + 2)
         out = torch.empty(3 * n, device=DEV, dtype=torch.float64)
-        ctx.sht(0, S.SHT_INVERSE, grid, 3, T(c), out)
+        ctx.sht(S.SHT_INVERSE, grid, [0, 0, 0], T(c), out)
         assert rel_err(out.cpu().numpy().reshape(3, n), sh.sht_inverse(c, p, q)) < 1e-12
         g = rng.standard_normal((3, n))
         cf = torch.empty(3 * sh.ncoef(p), device=DEV, dtype=torch.float64)
-        ctx.sht(0, S.SHT_FORWARD, grid, 3, T(g), cf)
+        ctx.sht(S.SHT_FORWARD, grid, [0, 0, 0], T(g), cf)
         assert rel_err(cf.cpu().numpy().reshape(3, -1), sh.sht_forward(g, p, q)) < 1e-12
+    ctx.close()
+
+
+def test_sht_field_drop_map_matches_oracle(S):
+    """Fields of drops of different degrees in one call, in the order the drop map gives
+    (drop 1, drop 0, drop 1): each field is transformed on its own drop's grid."""
+    cfg = inputs.config2(p=4, seed=2, gap=0.3)
+    d0 = cfg.drops[0]
+    d1 = inputs.Drop(7, inputs.perturbed_coef(7, np.random.default_rng(3), 1.0, (0.0, 0.0, 3.0)),
+                     np.zeros(sh.ncoef(7)), 1.0, np.zeros(3), 1.0)
+    ctx = make(S, [d0, d1], S.FP64)
+    fd = [1, 0, 1]
+    ps = [[4, 7][i] for i in fd]
+    rng = np.random.default_rng(9)
+    for grid in (S.GRID_BASE, S.GRID_UP):
+        qs = [p if grid == S.GRID_BASE else 2 * p + 1 for p in ps]
+        cs = [rng.standard_normal(sh.ncoef(p)) for p in ps]
+        out = torch.empty(sum((q + 1) * (2 * q + 2) for q in qs), device=DEV, dtype=torch.float64)
+        ctx.sht(S.SHT_INVERSE, grid, fd, T(np.concatenate(cs)), out)
+        ref = np.concatenate([sh.sht_inverse(c[None], p, q)[0] for c, p, q in zip(cs, ps, qs)])
+        assert rel_err(out.cpu().numpy(), ref) < 1e-12
+        gs = [rng.standard_normal((q + 1) * (2 * q + 2)) for q in qs]
+        cf = torch.empty(sum(sh.ncoef(p) for p in ps), device=DEV, dtype=torch.float64)
+        ctx.sht(S.SHT_FORWARD, grid, fd, T(np.concatenate(gs)), cf)
+        ref = np.concatenate([sh.sht_forward(g[None], p, q)[0] for g, p, q in zip(gs, ps, qs)])
+        assert rel_err(cf.cpu().numpy(), ref) < 1e-12
     ctx.close()
 
 
@@ -332,34 +358,97 @@ def test_every_pair_launch_shape_matches_oracle(S):
     ctx.close()
 
 
-def test_full_size_two_drops_sampled_targets(S):
-    """Two p = 32 drops 0.1 apart (the two-drop workload) in the bench's launch
-    configuration: target values at sampled targets (first, last, tile edges, closest to the
-    gap) against the oracle evaluated one target at a time."""
+@pytest.fixture(scope="module")
+def full_size_two_drops():
+    """The two-drop workload (p = 32, 0.1 apart) with its oracle and the sampled targets: per drop
+    the first and last target, the edges of the 512-target pair tiles and of the 256-target
+    launches, the target closest to the gap, and 16 targets spread over the oracle's near list
+    (where the upsampled rule replaces the degree-q one)."""
     cfg = inputs.config2(p=32, seed=0, gap=0.1)
-    sysm = oracle_system(cfg.drops, near=False)
+    sysm = oracle_system(cfg.drops, near=True)
+    pairs = sysm.near_pairs()
+    nt = (32 + 1) * 66
+    picks = [0, 255, 256, 511, 512, 1023, 1024, 2047, 2048, nt - 1]
+    sel = []
+    for i, dg in enumerate(sysm.drops):
+        near_t = sorted({t for (ii, t, j) in pairs if ii == i})
+        assert len(near_t) >= 16
+        spread = [near_t[k] for k in np.linspace(0, len(near_t) - 1, 16).astype(int)]
+        gap_t = int(np.argmin(np.abs(dg.x0[2])))
+        sel.append(sorted(set(picks + spread + [gap_t])))
     rng = np.random.default_rng(12)
     sig = [inputs.random_density(d.p, rng)[0] for d in cfg.drops]
     f = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
+    from oracle import nearsing
+    fine = {}
+    ref = {}
+    for i in range(2):
+        ref[("ladl", i)] = nearsing.corrected_laplace_targets(sysm, "ladl", sig, i, sel[i], pairs, fine)
+        ref[("lsl", i)] = nearsing.corrected_laplace_targets(sysm, "lsl", sig, i, sel[i], pairs, fine)
+        ref[("sto", i)] = nearsing.corrected_stokes_targets(sysm, f, f, i, sel[i], pairs, fine)
+    return cfg, sysm, sel, sig, f, ref, len(pairs)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32), (2, TOL64)])
+def test_full_size_two_drops_sampled_targets(S, full_size_two_drops, precision, tol):
+    """Two p = 32 drops 0.1 apart (the two-drop workload) in the bench's launch configuration, with
+    the nearly-singular correction on (its default): target values of the Laplace double and single
+    layers and of the Stokes S[f] + (lambda - 1) D[f] at the sampled targets against the oracle
+    evaluated one target at a time, near targets through the oracle's upsampled rule."""
+    cfg, sysm, sel, sig, f, ref, npairs = full_size_two_drops
     nt = (32 + 1) * 66
-    picks = [0, 255, 256, 511, 2047, 2048, nt - 1]
-    for i, dg in enumerate(sysm.drops):
-        gap_t = int(np.argmin(np.abs(dg.x0[2] - 0.0)))
-        sel = sorted(set(picks + [gap_t]))
-        for precision, tol in ((0, TOL64), (1, TOL32), (2, TOL64)):
-            ctx = make(S, cfg.drops, precision, cfg.R, near=False)
-            out = torch.empty(2 * nt, device=DEV, dtype=torch.float64)
-            ctx.eval_electric(S.LAPLACE_DL, T(np.concatenate(sig)), out, S.OUT_GRID)
-            got = out.cpu().numpy()[i * nt:(i + 1) * nt][sel]
-            ref = sysm.laplace_targets("ladl", sig, i, sel)
-            assert rel_err(got, ref) < tol
-            out3 = torch.empty(6 * nt, device=DEV, dtype=torch.float64)
-            ctx.eval_stokes(T(np.concatenate([a.ravel() for a in f])), T(np.concatenate([a.ravel() for a in f])),
-                            out3, S.OUT_GRID)
-            got = out3.cpu().numpy()[3 * i * nt:3 * (i + 1) * nt].reshape(3, nt)[:, sel]
-            ref = sysm.stokes_targets(f, f, i, sel)
-            assert rel_err(got, ref) < tol
-            ctx.close()
+    ctx = make(S, cfg.drops, precision, cfg.R, near=True)
+    assert ctx.near_pairs() == npairs
+    F = T(np.concatenate([a.ravel() for a in f]))
+    for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
+        out = torch.empty(2 * nt, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(which, T(np.concatenate(sig)), out, S.OUT_GRID)
+        got = out.cpu().numpy()
+        for i in range(2):
+            assert rel_err(got[i * nt:(i + 1) * nt][sel[i]], ref[(kind, i)]) < tol, (kind, i)
+    out3 = torch.empty(6 * nt, device=DEV, dtype=torch.float64)
+    ctx.eval_stokes(F, F, out3, S.OUT_GRID)
+    got = out3.cpu().numpy()
+    for i in range(2):
+        assert rel_err(got[3 * i * nt:3 * (i + 1) * nt].reshape(3, nt)[:, sel[i]], ref[("sto", i)]) < tol, i
+    ctx.close()
+
+
+@pytest.mark.parametrize("p", [44, 64])
+def test_large_degree_perturbed_drop_matches_oracle(S, p):
+    """A perturbed drop above the tensor-core kernels' degree limit (p > 39: the double-float row
+    build with the degree-block rotations on the FP32 pipe): Laplace double and single layer and the
+    Stokes S[f] + (lambda - 1) D[f] self terms at sampled targets (pole rows, equator, last) against
+    the oracle's direct rotated evaluation."""
+    from oracle import quadrature
+    rng = np.random.default_rng(100 + p)
+    ctr = np.array([0.2, -0.1, 0.3])
+    d = inputs.Drop(p, inputs.perturbed_coef(p, rng, 1.0, ctr), np.zeros(sh.ncoef(p)), 2.5, ctr, 1.0)
+    nt = (p + 1) * (2 * p + 2)
+    sel = [0, (p // 2) * (2 * p + 2) + 7, nt // 2 + p, nt - 1]
+    sig = inputs.random_density(p, rng)[0]
+    f = inputs.random_density(p, rng, 3)
+    ctx = make(S, [d], S.FP64, 2.0)
+    out = {}
+    for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
+        o = torch.empty(nt, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(which, T(sig), o, S.OUT_GRID)
+        out[kind] = o.cpu().numpy()[sel]
+    o3 = torch.empty(3 * nt, device=DEV, dtype=torch.float64)
+    ctx.eval_stokes(T(f), T(f), o3, S.OUT_GRID)
+    out["sto"] = o3.cpu().numpy().reshape(3, nt)[:, sel]
+    ctx.close()
+    th, ph = sh.grid_points(p)
+    ref = {"ladl": [], "lsl": [], "sto": []}
+    for t in sel:
+        r = quadrature.self_rows(d.xcoef, p, 2 * p + 1, th[t], ph[t], ["ladl", "lsl", "sto_s", "sto_d"])
+        ref["ladl"].append(r["ladl"] @ sig)
+        ref["lsl"].append(r["lsl"] @ sig)
+        ref["sto"].append(np.einsum("ikc,kc->i", r["sto_s"], f) + (d.lam - 1.0) * np.einsum("ikc,kc->i", r["sto_d"], f))
+        del r
+    for kind in ("ladl", "lsl"):
+        assert rel_err(out[kind], np.array(ref[kind])) < TOL64, kind
+    assert rel_err(out["sto"], np.array(ref["sto"]).T) < TOL64
 
 
 # --------------------------------------------------------------------------- GMRES
@@ -426,7 +515,7 @@ def test_errors_are_reported_not_raised_by_the_library(S):
     with pytest.raises(S.ShbimError, match="bad kernel"):
         ctx.eval_electric(7, T(np.zeros(16)), T(np.zeros(16)))
     with pytest.raises(S.ShbimError, match="drop index"):
-        ctx.sht(2, S.SHT_INVERSE, S.GRID_BASE, 1, T(np.zeros(16)), T(np.zeros(32)))
+        ctx.sht(S.SHT_INVERSE, S.GRID_BASE, [2], T(np.zeros(16)), T(np.zeros(32)))
     ctx.close()
 
 

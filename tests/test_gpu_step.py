@@ -90,6 +90,35 @@ def test_rates_match_oracle(S, precision, tol):
     ctx.close()
 
 
+@pytest.fixture(scope="module")
+def rates_p12_gap01():
+    """Two drops of degree 12, 0.1 apart (near pairs on both sides), and the oracle's rates."""
+    cfg = two_drops(p=12, seed=2, gap=0.1)
+    ps = [d.p for d in cfg.drops]
+    lams = [d.lam for d in cfg.drops]
+    prm = P.Params(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.2, 0.0, 1.0), gmres_tol=1e-13)
+    u_ref, g_ref = P.rates([d.xcoef for d in cfg.drops], [d.gamma_coef for d in cfg.drops], ps, lams, prm)
+    return cfg, np.concatenate([a.ravel() for a in u_ref]), np.concatenate(g_ref)
+
+
+@pytest.mark.parametrize("precision,tol", [(1, TOL32), (2, TOL64)])
+def test_rates_close_drops_match_oracle(S, rates_p12_gap01, precision, tol):
+    """shbim_rates at p = 12 with the drops 0.1 apart (nearly-singular correction active): mixed
+    precision (FP32 compensated inner solves refined to an FP64-class residual, one-shot
+    applications double-float) and double-float sums, against the FP64 oracle."""
+    cfg, u_ref, g_ref = rates_p12_gap01
+    ctx, x, g = setup(S, cfg, precision, tol=1e-12)
+    assert ctx.near_pairs() > 0
+    nc = sum(sh.ncoef(d.p) for d in cfg.drops)
+    u = torch.empty(3 * nc, device="cuda", dtype=torch.float64)
+    gE = torch.empty(nc, device="cuda", dtype=torch.float64)
+    ctx.rates(S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.2, 0.0, 1.0), inner_tol=1e-5),
+              g, u, gE)
+    assert rel_err(u.cpu().numpy(), u_ref) < tol
+    assert rel_err(gE.cpu().numpy(), g_ref) < tol
+    ctx.close()
+
+
 def test_step_matches_oracle(S):
     cfg = two_drops(p=5, seed=4, gap=0.5)
     ps = [d.p for d in cfg.drops]

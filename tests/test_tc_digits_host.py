@@ -121,14 +121,25 @@ def test_digit_split_product_matches_exact_dot_products(tcd):
             assert abs(got - exact) <= Fraction(1, 2 ** 39) * bound
 
 
+def _constexpr(src, name):
+    import re
+    txt = open(os.path.join(CSRC, src)).read()
+    return int(re.search(r"constexpr int %s = (\d+);" % name, txt).group(1))
+
+
 def test_diagonal_sums_stay_exact_at_the_largest_k():
     """Worst case of every diagonal sum from the digit bounds (row digits d5..d0 up to 128, 64, 64, 72,
-    65, 65; table digits up to 128 and 64) at the longest K each tensor-core kernel runs: 160
-    longitudes (Fourier stage, p = 39), 80 (rotations: blocks up to 2p+1 padded; Legendre stage:
-    up to 80 latitudes). Below 2^24, FP32 accumulation in tensor memory is exact."""
+    65, 65; table digits up to 128 and 64) at the longest K each tensor-core kernel accepts, read from
+    the kernels' own limits: the Fourier stage runs K = 4(p+1) longitudes with 2(p+1) <= kNT, the
+    rotations K <= kNmax (padded blocks), the Legendre stage K = 2p+2 <= kKmax latitudes. Below 2^24,
+    FP32 accumulation in tensor memory is exact. The kernels assert the same bound at compile time
+    (static_assert on diag_sums_exact); this recomputes it independently of the C++ expression."""
     a_max = {5: 128, 4: 64, 3: 64, 2: 72, 1: 65, 0: 65}
     b_max = {5: 128, 4: 64, 3: 64, 2: 64, 1: 64, 0: 64}
-    for K in (160, 80):
+    ks = {"fourier": 2 * _constexpr("dft_tc.cu", "kNT"), "rotation": _constexpr("rot_tc.cu", "kNmax"),
+          "legendre": _constexpr("leg_tc.cu", "kKmax")}
+    assert ks["fourier"] >= 160 and ks["rotation"] >= 80 and ks["legendre"] >= 80
+    for name, K in ks.items():
         for s in range(6):
             worst = K * sum(a_max[ja] * b_max[s + 5 - ja] for ja in range(6) if 0 <= s + 5 - ja <= 5)
-            assert worst < 2 ** 24, (K, s, worst)
+            assert worst < 2 ** 24, (name, K, s, worst)
