@@ -263,16 +263,26 @@ int shbim_set_diffusion(shbim_ctx* ctx, double c);
  * With 0 < Pe < infinity the surfactant follows the IMEX scheme of Algorithm 1: the half step
  * solves (I - dt/(2 Pe) Delta_S) Gamma_half = Gamma + dt/2 g_E(t) on the half-step surface and
  * the full step uses g_E(t+dt/2) + Delta_S Gamma_half / Pe.
+ * The Stokes solve of the second stage starts from the first stage's velocity (the two differ by
+ * O(dt)); every other solve starts from zero.
  * After the call the context holds the geometry of the half step. */
 int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, const double* gamma_dev,
                double dt, double* x_out_dev, double* gamma_out_dev, double* err_host, int* iters_host,
                void* stream);
 
 /* FP64-class arithmetic used where mixed precision needs it: the residuals of
- * shbim_gmres_solve_refined and the one-shot applications of shbim_rates / shbim_step in
- * SHBIM_PREC_FP32_COMP mode. SHBIM_PREC_DF64 (default: double-float on the FP32 pipe) or
- * SHBIM_PREC_FP64 (native); SHBIM_ERR_ARG otherwise. */
+ * shbim_gmres_solve_refined in SHBIM_PREC_FP32_COMP mode. SHBIM_PREC_DF64 (default: double-float on
+ * the FP32 pipe) or SHBIM_PREC_FP64 (native); SHBIM_ERR_ARG otherwise. */
 int shbim_set_outer_precision(shbim_ctx* ctx, int precision);
+
+/* Arithmetic of the one-shot layer-operator applications of shbim_rates / shbim_step in
+ * SHBIM_PREC_FP32_COMP mode (the charge potential S_L[q] and the Stokes right-hand side
+ * S[f/Ca_E - f^E], applied once each and not iterated by GMRES): SHBIM_PREC_DF64 (default) or
+ * SHBIM_PREC_FP64 give FP64-class results; SHBIM_PREC_FP32_COMP is faster but its ~1e-7 relative error
+ * of S[f/Ca_E - f^E] is amplified in u and its surface divergence, because the single layer of the
+ * capillary traction nearly cancels over each drop (a sphere under uniform tension does not move):
+ * measured ~1e-5 relative in the surfactant rate of two p = 6 drops. SHBIM_ERR_ARG otherwise. */
+int shbim_set_oneshot_precision(shbim_ctx* ctx, int precision);
 
 /* Mixed-precision solve by iterative refinement: every outer step forms the residual
  * r = b - A x with FP64-class all-pairs sums, solves A d = r by GMRES with FP32 compensated sums,
@@ -280,7 +290,10 @@ int shbim_set_outer_precision(shbim_ctx* ctx, int precision);
  * were taken (SHBIM_ERR_NOT_CONVERGED). The inner relative tolerance is inner_tol (e.g. 1e-5),
  * except where the step can finish the solve: then it is 0.5 gmres_tol / (current relative
  * residual), looser than inner_tol on the last step, and down to inner_tol / 20 after a good
- * initial guess. The outer residuals use the context's outer precision (shbim_set_outer_precision).
+ * initial guess. From a zero start the first inner solve aims at 0.5 gmres_tol at once (one
+ * FP64-class residual per solve) for as long as that has succeeded for the system on this context;
+ * after the first miss the system's later solves use the two-step form. The outer residuals use the
+ * context's outer precision (shbim_set_outer_precision).
  * Only the electric and Stokes systems (the diffusion system has no all-pairs sums;
  * SHBIM_ERR_ARG). The context's precision setting is restored on return. Reports the total inner Arnoldi
  * steps, the outer steps and the final FP64 relative residual (each pointer may be NULL). */
@@ -381,6 +394,14 @@ int shbim_set_autotune(shbim_ctx* ctx, int on);
  * SHBIM_PREC_FP64 (native). SHBIM_ERR_ARG otherwise. */
 int shbim_set_rows_precision(shbim_ctx* ctx, int precision);
 
+/* Arithmetic of the singular self-row application (a GEMV with the stored rows) when the context's
+ * precision is SHBIM_PREC_FP32_COMP: SHBIM_PREC_DF64 (default) reads both FP32 planes of the rows and
+ * of the density and accumulates in double-float, so the self term, which is of the size of the whole
+ * operator value, carries FP64-class accuracy (the rows are HBM-bound: twice the bytes of the
+ * alternative); SHBIM_PREC_FP32_COMP reads the high planes only and accumulates in FP32 (~1e-7
+ * relative). The other precisions always use the double-float form. SHBIM_ERR_ARG otherwise. */
+int shbim_set_self_precision(shbim_ctx* ctx, int precision);
+
 /* Tensor-core stages of the double-float row build (at the next shbim_set_drops), a bit mask:
  * SHBIM_TC_FOURIER, the GEMM of the rows' weights with the DFT table; SHBIM_TC_LEGENDRE, the
  * Legendre stage that follows it (used only together with SHBIM_TC_FOURIER); SHBIM_TC_ROTATION,
@@ -425,7 +446,9 @@ int shbim_check_wait(shbim_ctx* ctx, int arrive, void* stream);
 #define SHBIM_PROBE_DMMA_F64 4   /* mma.sync m8n8k4 f64 */
 int shbim_probe_peak(int kind, int64_t iters, double* ops_per_s_host, double* ms_host, void* stream);
 
-/* Launch shape of the FP32 all-pairs kernel of one kind (0 Laplace DL, 1 Laplace SL, 2 Stokes)
+/* Launch shape of the FP32 all-pairs kernel of one kind (0 Laplace DL, 1 Laplace SL, 2 Stokes S[f] and
+ * D[u] together, 3 Stokes S[f] alone, 4 Stokes D[u] alone; shbim_eval_stokes picks 2, 3 or 4 from the
+ * densities it is given, and the single-term kinds skip the other term's arithmetic)
  * for the current layout. shbim_pair_shape writes targets per thread and the split count (either
  * pointer may be NULL) and returns 1 once the shape is fixed (tuned or set), 0 before, or an
  * error code. shbim_set_pair_shape fixes it (tpt in {1, 2, 4}, 1 <= splits <= the layout's
@@ -455,13 +478,22 @@ int64_t shbim_operator_applications(shbim_ctx* ctx);
  * the number of bracketed launches of one class since timing was (re)enabled. */
 #define SHBIM_K_SELF_WEIGHTS 0      /* rotated-grid synthesis + kernel weights (singular rows) */
 #define SHBIM_K_SELF_ANALYSIS 1     /* analysis of the weights (singular rows) */
-#define SHBIM_K_PAIRS 2             /* all-pairs sums */
+#define SHBIM_K_PAIRS 2             /* all-pairs sums in FP32 (compensated) */
 #define SHBIM_K_SELF_GEMV 3         /* application of the singular rows */
 #define SHBIM_K_SHT 4               /* transforms of densities and outputs */
 #define SHBIM_K_SELF_ROTATION 5     /* pole rotations of the singular-row build */
-#define SHBIM_K_COUNT 6
+#define SHBIM_K_PAIRS_FP64CLASS 6   /* all-pairs sums in double-float or FP64 */
+#define SHBIM_K_NEAR 7              /* nearly-singular corrections (upsampled sums at near targets) */
+#define SHBIM_K_COUNT 8
 int shbim_set_timing(shbim_ctx* ctx, int on);
 int shbim_kernel_stats(shbim_ctx* ctx, int kernel_class, double* ms_host, int64_t* launches_host);
+/* Algorithmic work of the bracketed launches of one class since timing was (re)enabled, in
+ * floating-point operations of the method's formulas (an add or a multiply is 1, a fused
+ * multiply-add 2, a reciprocal square root 1), whatever arithmetic the kernel uses to carry them out:
+ * for the all-pairs classes, target-source pairs of other drops times the operations of one kernel
+ * term (Laplace single layer 11, target-normal double layer 19, Stokeslet 29, stresslet 30, both
+ * Stokes terms 42); 0 for the other classes. Synchronises the device like shbim_kernel_stats. */
+int shbim_kernel_work(shbim_ctx* ctx, int kernel_class, double* flops_host);
 
 #ifdef __cplusplus
 }

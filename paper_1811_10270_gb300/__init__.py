@@ -47,7 +47,8 @@ EXPORTS = [
     "shbim_set_graphs", "shbim_set_concurrency", "shbim_pair_queue", "shbim_set_pair_queue", "shbim_laplace_beltrami", "shbim_set_diffusion",
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
     "shbim_set_outer_precision", "shbim_set_rows_precision", "shbim_set_tensor_cores",
-    "shbim_near_min_distance", "shbim_set_wait_limit", "shbim_check_wait",
+    "shbim_near_min_distance", "shbim_set_wait_limit", "shbim_check_wait", "shbim_set_self_precision", "shbim_set_oneshot_precision",
+    "shbim_kernel_work",
 ]
 PROBE_FFMA = 0
 PROBE_DFMA = 1
@@ -64,7 +65,9 @@ K_PAIRS = 2
 K_SELF_GEMV = 3
 K_SHT = 4
 K_SELF_ROTATION = 5
-K_COUNT = 6
+K_PAIRS_FP64CLASS = 6
+K_NEAR = 7
+K_COUNT = 8
 
 
 class ShbimError(RuntimeError):
@@ -155,6 +158,9 @@ def lib():
         "shbim_near_min_distance": (i32, [vp, P(dp), P(dp)]),
         "shbim_set_wait_limit": (i32, [vp, dp]),
         "shbim_check_wait": (i32, [vp, i32, vp]),
+        "shbim_set_self_precision": (i32, [vp, i32]),
+        "shbim_set_oneshot_precision": (i32, [vp, i32]),
+        "shbim_kernel_work": (i32, [vp, i32, P(dp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -305,6 +311,12 @@ class Context:
     def set_timing(self, on: bool):
         self._check(self._L.shbim_set_timing(self._h, 1 if on else 0), "shbim_set_timing")
 
+    def kernel_work(self, cls: int) -> float:
+        """Algorithmic flops of the bracketed launches of one class (shbim_kernel_work)."""
+        w = ctypes.c_double()
+        self._check(self._L.shbim_kernel_work(self._h, cls, ctypes.byref(w)), "shbim_kernel_work")
+        return w.value
+
     def kernel_stats(self, cls: int):
         ms = ctypes.c_double()
         n = ctypes.c_int64()
@@ -350,6 +362,12 @@ class Context:
 
     def set_rows_precision(self, precision: int):
         self._check(self._L.shbim_set_rows_precision(self._h, int(precision)), "shbim_set_rows_precision")
+
+    def set_oneshot_precision(self, precision: int):
+        self._check(self._L.shbim_set_oneshot_precision(self._h, precision), "shbim_set_oneshot_precision")
+
+    def set_self_precision(self, precision: int):
+        self._check(self._L.shbim_set_self_precision(self._h, precision), "shbim_set_self_precision")
 
     def set_tensor_cores(self, on):
         """Tensor-core stages of the row build: True (the default set, TC_FOURIER | TC_ROTATION),

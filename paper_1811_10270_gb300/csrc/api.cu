@@ -226,6 +226,15 @@ int shbim_set_rows_precision(shbim_ctx* ctx, int precision) {
   return SHBIM_OK;
 }
 
+int shbim_set_self_precision(shbim_ctx* ctx, int precision) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (precision != SHBIM_PREC_FP32_COMP && precision != SHBIM_PREC_DF64)
+    return fail(ctx, SHBIM_ERR_ARG, "self-row precision must be SHBIM_PREC_FP32_COMP or SHBIM_PREC_DF64");
+  if (precision != ctx->self_prec) ctx->geom_version++;  // captured graphs hold the other kernel
+  ctx->self_prec = precision;
+  return SHBIM_OK;
+}
+
 int shbim_set_tensor_cores(shbim_ctx* ctx, int mask) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (mask & ~SHBIM_TC_ALL) return fail(ctx, SHBIM_ERR_ARG, "unknown tensor-core stage bit");
@@ -245,7 +254,7 @@ int shbim_set_autotune(shbim_ctx* ctx, int on) {
 
 int shbim_pair_shape(shbim_ctx* ctx, int kind, int* tpt_host, int* splits_host) {
   if (!ctx) return SHBIM_ERR_ARG;
-  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  if (kind < 0 || kind > 4) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL), 2 (Stokes S + D), 3 (S) or 4 (D)");
   if (tpt_host) *tpt_host = ctx->pair_cfg[kind].tpt;
   if (splits_host) *splits_host = ctx->pair_cfg[kind].splits;
   return ctx->pair_cfg[kind].tuned ? 1 : 0;
@@ -254,7 +263,7 @@ int shbim_pair_shape(shbim_ctx* ctx, int kind, int* tpt_host, int* splits_host) 
 int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
-  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  if (kind < 0 || kind > 4) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL), 2 (Stokes S + D), 3 (S) or 4 (D)");
   if (tpt != 1 && tpt != 2 && tpt != 4) return fail(ctx, SHBIM_ERR_ARG, "targets per thread must be 1, 2 or 4");
   if (splits < 1 || splits > ctx->split_max) return fail(ctx, SHBIM_ERR_ARG, "split count out of range");
   ctx->pair_cfg[kind] = shbim_ctx::PairCfg{tpt, splits, true, ctx->pair_cfg[kind].queue};
@@ -264,14 +273,14 @@ int shbim_set_pair_shape(shbim_ctx* ctx, int kind, int tpt, int splits) {
 
 int shbim_pair_queue(shbim_ctx* ctx, int kind) {
   if (!ctx) return SHBIM_ERR_ARG;
-  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  if (kind < 0 || kind > 4) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL), 2 (Stokes S + D), 3 (S) or 4 (D)");
   return ctx->pair_cfg[kind].queue ? 1 : 0;
 }
 
 int shbim_set_pair_queue(shbim_ctx* ctx, int kind, int on) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
-  if (kind < 0 || kind > 2) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL) or 2 (Stokes)");
+  if (kind < 0 || kind > 4) return fail(ctx, SHBIM_ERR_ARG, "kind must be 0 (Laplace DL), 1 (SL), 2 (Stokes S + D), 3 (S) or 4 (D)");
   ctx->pair_cfg[kind].queue = on != 0;
   ctx->pair_cfg[kind].tuned = true;
   ctx->geom_version++;
@@ -413,6 +422,8 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
     if ((rc = dalloc(ctx, &ctx->tiles_dev, ctx->tiles.size(), "tiles"))) return rc;
     SHBIM_CUDA(ctx, cudaMemcpy(ctx->tiles_dev, ctx->tiles.data(), ctx->tiles.size() * sizeof(PairTile),
                                cudaMemcpyHostToDevice));
+    ctx->cross_pairs = 0;
+    for (const Drop& d : ctx->drops) ctx->cross_pairs += (int64_t)d.nt * (so - d.ns);
     ctx->split_max = (int)std::max<int64_t>(1, std::min<int64_t>(4 * splits, std::max<int64_t>(1, min_other / 64)));
     ctx->split_max = std::min(ctx->split_max, 256);
     ctx->pair_splits = std::min(ctx->pair_splits, ctx->split_max);
@@ -508,6 +519,11 @@ struct Branches {
   cudaEvent_t coarse = nullptr, join = nullptr;
 };
 
+// timing class of the all-pairs sums at the context's precision
+int pair_class(const shbim_ctx* ctx) {
+  return ctx->opts.precision == SHBIM_PREC_FP32_COMP ? SHBIM_K_PAIRS : SHBIM_K_PAIRS_FP64CLASS;
+}
+
 int fork_branches(shbim_ctx* ctx, cudaStream_t s, Branches* br) {
   br->side = s;
   if (ctx->n_drops < 2 || !ctx->concurrent) return SHBIM_OK;
@@ -557,10 +573,14 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
     }
   }
   if (br.coarse) SHBIM_CUDA(ctx, cudaEventRecord(br.coarse, s));
-  if ((rc = apply_near_laplace(ctx, which, dens_dev, vals, br.side, br.coarse))) return rc;
+  {
+    TimeScope ts(ctx, SHBIM_K_NEAR, br.side);
+    if ((rc = apply_near_laplace(ctx, which, dens_dev, vals, br.side, br.coarse))) return rc;
+  }
   if (br.join) SHBIM_CUDA(ctx, cudaEventRecord(br.join, br.side));
   {
-    TimeScope ts(ctx, SHBIM_K_PAIRS, s);
+    TimeScope ts(ctx, pair_class(ctx), s);
+    ts.work = pairs_work(ctx, which == SHBIM_LAPLACE_SL ? 1 : 0);
     if ((rc = pairs_laplace(ctx, which, vals, s, br.join))) return rc;
   }
   if (out_kind == SHBIM_OUT_COEF) {
@@ -619,10 +639,14 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
     }
   }
   if (br.coarse) SHBIM_CUDA(ctx, cudaEventRecord(br.coarse, s));
-  if ((rc = apply_near_stokes(ctx, f_dev, u_dev, vals, br.side, br.coarse))) return rc;
+  {
+    TimeScope ts(ctx, SHBIM_K_NEAR, br.side);
+    if ((rc = apply_near_stokes(ctx, f_dev, u_dev, vals, br.side, br.coarse))) return rc;
+  }
   if (br.join) SHBIM_CUDA(ctx, cudaEventRecord(br.join, br.side));
   {
-    TimeScope ts(ctx, SHBIM_K_PAIRS, s);
+    TimeScope ts(ctx, pair_class(ctx), s);
+    ts.work = pairs_work(ctx, f_dev && u_dev ? 2 : (f_dev ? 3 : 4));
     if ((rc = pairs_stokes(ctx, f_dev != nullptr, u_dev != nullptr, vals, s, br.join))) return rc;
   }
   if (out_kind == SHBIM_OUT_COEF) {
@@ -670,7 +694,7 @@ TimeScope::~TimeScope() {
     ctx->event_pool.pop_back();
   }
   cudaEventRecord(e, s);
-  ctx->timed.push_back(shbim_ctx::TimedRange{cls, b, e});
+  ctx->timed.push_back(shbim_ctx::TimedRange{cls, b, e, work});
 }
 
 namespace {
@@ -699,26 +723,43 @@ int shbim_set_timing(shbim_ctx* ctx, int on) {
   for (int k = 0; k < SHBIM_K_COUNT; ++k) {
     ctx->class_ms[k] = 0.0;
     ctx->class_launches[k] = 0;
+    ctx->class_work[k] = 0.0;
   }
   ctx->timing = on != 0;
   return SHBIM_OK;
 }
 
-int shbim_kernel_stats(shbim_ctx* ctx, int cls, double* ms, int64_t* launches) {
-  if (!ctx) return SHBIM_ERR_ARG;
-  if (cls < 0 || cls >= SHBIM_K_COUNT) return fail(ctx, SHBIM_ERR_ARG, "bad kernel class");
+namespace {
+int collect_timing(shbim_ctx* ctx) {
   SHBIM_CUDA(ctx, cudaDeviceSynchronize());
   for (auto& r : ctx->timed) {
     float t = 0.f;
     SHBIM_CUDA(ctx, cudaEventElapsedTime(&t, r.a, r.b));
     ctx->class_ms[r.cls] += t;
     ctx->class_launches[r.cls] += 1;
+    ctx->class_work[r.cls] += r.work;
     ctx->event_pool.push_back(r.a);
     ctx->event_pool.push_back(r.b);
   }
   ctx->timed.clear();
+  return SHBIM_OK;
+}
+}  // namespace
+
+int shbim_kernel_stats(shbim_ctx* ctx, int cls, double* ms, int64_t* launches) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (cls < 0 || cls >= SHBIM_K_COUNT) return fail(ctx, SHBIM_ERR_ARG, "bad kernel class");
+  if (int rc = collect_timing(ctx)) return rc;
   if (ms) *ms = ctx->class_ms[cls];
   if (launches) *launches = ctx->class_launches[cls];
+  return SHBIM_OK;
+}
+
+int shbim_kernel_work(shbim_ctx* ctx, int cls, double* flops) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (cls < 0 || cls >= SHBIM_K_COUNT) return fail(ctx, SHBIM_ERR_ARG, "bad kernel class");
+  if (int rc = collect_timing(ctx)) return rc;
+  if (flops) *flops = ctx->class_work[cls];
   return SHBIM_OK;
 }
 

@@ -482,6 +482,14 @@ int shbim_set_outer_precision(shbim_ctx* ctx, int precision) {
   return SHBIM_OK;
 }
 
+int shbim_set_oneshot_precision(shbim_ctx* ctx, int precision) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_DF64 && precision != SHBIM_PREC_FP32_COMP)
+    return fail(ctx, SHBIM_ERR_ARG, "one-shot precision must be SHBIM_PREC_FP64, SHBIM_PREC_DF64 or SHBIM_PREC_FP32_COMP");
+  ctx->oneshot_prec = precision;
+  return SHBIM_OK;
+}
+
 int shbim_set_diffusion(shbim_ctx* ctx, double c) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (!(c >= 0.0) || !std::isfinite(c)) return fail(ctx, SHBIM_ERR_ARG, "diffusion coefficient must be >= 0");
@@ -526,6 +534,7 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
   const double tol = saved_tol;
   int inner_total = 0, outer = 0, rc = SHBIM_OK;
   double rel = 1.0;
+  bool attempted_direct = false;
   if (x0_dev) {
     SHBIM_CUDA(ctx, cudaMemcpyAsync(G.xr, x0_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
@@ -563,6 +572,7 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
       rc = fail(ctx, SHBIM_ERR_NONFINITE, "non-finite residual in refinement");
       break;
     }
+    if (outer == 1 && attempted_direct && rel > tol) ctx->refine_direct[sys] = false;
     if (rel <= tol) break;
     if (outer >= max_outer) {
       rc = fail(ctx, SHBIM_ERR_NOT_CONVERGED, "refinement reached max_outer");
@@ -571,9 +581,17 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
     // inner solve A d = r with FP32 sums. The tolerance that would finish in this step is
     // 0.5 tol / rel: when it is looser than inner_tol (typically the last step) it is used as is;
     // when it is tighter but within a factor 20 (a good initial guess) it is used too, so the solve
-    // ends one outer step earlier; otherwise the step reduces the residual by inner_tol.
+    // ends one outer step earlier; otherwise the step reduces the residual by inner_tol. From a zero
+    // start the first step also aims straight at the end (one FP64-class residual instead of two)
+    // while this system's FP32 operator has been accurate enough for that; the first time the
+    // FP64-class check after such a step misses the tolerance, later solves of the system go back
+    // to the two-step form.
     const double need = 0.5 * tol / rel;
-    const double tau = need >= inner_tol ? std::min(need, 0.5) : (need >= 0.05 * inner_tol ? need : inner_tol);
+    const bool direct = outer == 0 && !x0_dev && ctx->refine_direct[sys];
+    const double tau = direct ? need
+                              : need >= inner_tol ? std::min(need, 0.5)
+                                                  : (need >= 0.05 * inner_tol ? need : inner_tol);
+    attempted_direct = direct;
     ctx->opts.precision = SHBIM_PREC_FP32_COMP;
     ctx->opts.gmres_tol = tau;
     int it = 0;

@@ -147,14 +147,15 @@ struct shbim_ctx {
   shbim::DropDev* drops_dev = nullptr;
   int pair_splits = 1;            // default source-split count of the layout
   int split_max = 1;              // capacity of the partial-sum buffer in splits
-  // shape of the FP32 all-pairs launches per kernel kind (Laplace DL, Laplace SL, Stokes):
+  // shape of the FP32 all-pairs launches per kernel kind (Laplace DL, Laplace SL, Stokes S + D, Stokes S,
+  // Stokes D):
   // targets per thread and source splits, autotuned on the first launch of a layout
   struct PairCfg {
     int tpt = 1;
     int splits = 1;
     bool tuned = false;
     bool queue = false;           // persistent CTAs on an atomic work counter
-  } pair_cfg[3];
+  } pair_cfg[5];
   int* pair_queue = nullptr;      // [2] work counter and finished-CTA count (zero between launches)
   bool autotune = true;           // off: every layout keeps the default launch shape
   // the double-float row build's two lanes (chunks alternate between the caller's stream and the
@@ -169,6 +170,9 @@ struct shbim_ctx {
   size_t dens_split_cap = 0;
   int outer_prec = SHBIM_PREC_DF64;  // FP64-class applications: refinement residuals, one-shot sums
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
+  int self_prec = SHBIM_PREC_DF64;   // self-row application in FP32 mode: both planes (double-float) or hi only
+  int oneshot_prec = SHBIM_PREC_DF64;  // one-shot applications of shbim_rates in FP32 mode
+  bool refine_direct[2] = {true, true};     // refined solves (electric, Stokes): first inner solve aims at the end
   bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
   bool tc_rot = true;             // ... and the degree-block rotations (rot_tc.cu)
   bool tc_leg = false;            // ... and the Legendre stage of the analysis (leg_tc.cu; opt-in)
@@ -276,11 +280,14 @@ struct shbim_ctx {
   struct TimedRange {
     int cls;
     cudaEvent_t a, b;
+    double work;                // algorithmic flops of the bracketed launch (pair classes)
   };
   std::vector<TimedRange> timed;
   std::vector<cudaEvent_t> event_pool;
   double class_ms[SHBIM_K_COUNT] = {0};
   int64_t class_launches[SHBIM_K_COUNT] = {0};
+  double class_work[SHBIM_K_COUNT] = {0};
+  int64_t cross_pairs = 0;        // target-source pairs of different drops per all-pairs launch
 };
 
 namespace shbim {
@@ -306,6 +313,7 @@ struct TimeScope {
   int cls;
   cudaStream_t s;
   cudaEvent_t b = nullptr;
+  double work = 0.0;            // algorithmic flops of what the scope brackets (set by the caller)
   TimeScope(shbim_ctx* c, int k, cudaStream_t st);
   ~TimeScope();
 };
@@ -391,6 +399,9 @@ int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 int pairs_laplace(shbim_ctx* ctx, int which, double* out_accum, cudaStream_t s, cudaEvent_t before_reduce = nullptr);
 int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out_accum, cudaStream_t s,
                  cudaEvent_t before_reduce = nullptr);
+// algorithmic flops of one all-pairs launch: cross pairs times the operations of one kernel term
+// (kind 0 Laplace DL, 1 SL, 2 Stokes S + D, 3 S, 4 D)
+double pairs_work(const shbim_ctx* ctx, int kind);
 
 
 }  // namespace shbim

@@ -3,7 +3,8 @@
 // quantity, positions relative to the source drop's centre):
 //   Laplace (KIND 0 target-normal double layer, 1 single layer):
 //     a = (x, y, z, x_lo), b = (y_lo, z_lo, s, s_lo)
-//   Stokes (KIND 2, Stokeslet on f and stresslet on u with the source normal n):
+//   Stokes (KIND 2, Stokeslet on f and stresslet on u with the source normal n; KIND 3 the Stokeslet
+//   alone, KIND 4 the stresslet alone):
 //     a = (x, y, z, x_lo), b = (y_lo, z_lo, fx, fx_lo), c = (fy, fy_lo, fz, fz_lo),
 //     d = (ux, ux_lo, uy, uy_lo), e = (uz, uz_lo, nx, nx_lo), g = (ny, ny_lo, nz, nz_lo)
 // T is the target's offset from the drop centre, N0 its normal; the accumulators collect the
@@ -29,16 +30,33 @@ __device__ __forceinline__ void df_term(const dfl::df T[3], const dfl::df N0[3],
     const df dn = dfl::dot3(dx, dy, dz, N0[0], N0[1], N0[2]);
     const df ri3 = dfl::mul(dfl::sqr(ri), ri);
     A[0].add_prod(dfl::mul(df{b.z, b.w}, ri3), dn);
-  } else {
-    const df fx{b.z, b.w}, fy{c.x, c.y}, fz{c.z, c.w};
+  } else if (KIND == 4) {
+    // stresslet on u alone
     const df ux{d.x, d.y}, uy{d.z, d.w}, uz{e.x, e.y};
     const df nx{e.z, e.w}, ny{g.x, g.y}, nz{g.z, g.w};
-    const df hf = dfl::dot3(dx, dy, dz, fx, fy, fz);
     const df hu = dfl::dot3(dx, dy, dz, ux, uy, uz);
     const df hn = dfl::dot3(dx, dy, dz, nx, ny, nz);
     const df ri2 = dfl::sqr(ri);
+    const df tt = dfl::mul(dfl::mul(hu, hn), dfl::mul(dfl::mul(ri2, ri2), ri));
+    A[0].add_prod(dx, tt);
+    A[1].add_prod(dy, tt);
+    A[2].add_prod(dz, tt);
+  } else {
+    // KIND 2: Stokeslet on f and stresslet on u; KIND 3: Stokeslet alone
+    const df fx{b.z, b.w}, fy{c.x, c.y}, fz{c.z, c.w};
+    const df hf = dfl::dot3(dx, dy, dz, fx, fy, fz);
+    const df ri2 = dfl::sqr(ri);
     const df ri3 = dfl::mul(ri2, ri);
-    const df tt = dfl::mul(ri3, dfl::add(hf, dfl::mul(dfl::mul(hu, hn), ri2)));
+    df tt;
+    if (KIND == 3) {
+      tt = dfl::mul(ri3, hf);
+    } else {
+      const df ux{d.x, d.y}, uy{d.z, d.w}, uz{e.x, e.y};
+      const df nx{e.z, e.w}, ny{g.x, g.y}, nz{g.z, g.w};
+      const df hu = dfl::dot3(dx, dy, dz, ux, uy, uz);
+      const df hn = dfl::dot3(dx, dy, dz, nx, ny, nz);
+      tt = dfl::mul(ri3, dfl::add(hf, dfl::mul(dfl::mul(hu, hn), ri2)));
+    }
     A[0].add_prod(fx, ri);
     A[0].add_prod(dx, tt);
     A[1].add_prod(fy, ri);

@@ -37,7 +37,10 @@ constexpr int kThreads = 128;
 constexpr int kMaxTPT = 4;                         // largest register blocking
 constexpr int kTileTargets = kThreads * kMaxTPT;   // targets per tile of the tile list
 
-enum Kind { LDL = 0, LSL = 1, STO = 2 };
+// Stokes kinds: both terms (STO), the Stokeslet on f alone (STS: right-hand sides) and the stresslet on u
+// alone (STD: the GMRES operator); the single-term kinds skip the other term's arithmetic
+enum Kind { LDL = 0, LSL = 1, STO = 2, STS = 3, STD = 4 };
+__host__ __device__ constexpr bool stokes_kind(int k) { return k >= STO; }
 
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float a) {
   const float s = hi + a;
@@ -86,7 +89,7 @@ __device__ __forceinline__ void pairs32_unit(int bx, int by, const PairTile* __r
                                              const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
                                              double* __restrict__ part, float4* __restrict__ sh0,
                                              float4* __restrict__ sh1, float4* __restrict__ sh2) {
-  constexpr int NC = (KIND == STO) ? 3 : 1;
+  constexpr int NC = stokes_kind(KIND) ? 3 : 1;
   PairTile tile;
   if (!sub_tile<kTPT>(tiles, tile, bx)) return;
   const int i = tile.drop;
@@ -139,7 +142,7 @@ __device__ __forceinline__ void pairs32_unit(int bx, int by, const PairTile* __r
       for (int e = threadIdx.x; e < cnt; e += kThreads) {
         const int64_t sI = base + e;
         const float x = src32[sI], y = src32[nsource + sI], z = src32[2 * nsource + sI];
-        if (KIND != STO) {
+        if (!stokes_kind(KIND)) {
           sh0[e] = make_float4(x, y, z, dens32[sI]);
         } else {
           const float fx = has_f ? dens32[sI] : 0.f;
@@ -163,7 +166,7 @@ __device__ __forceinline__ void pairs32_unit(int bx, int by, const PairTile* __r
 #pragma unroll 4
       for (int e = 0; e < cnt; ++e) {
         const float4 A = sh0[e];
-        if (KIND != STO) {
+        if (!stokes_kind(KIND)) {
 #pragma unroll
           for (int k = 0; k < kTPT; ++k) {
             const float dx = (th[k][0] - A.x) + tl[k][0];
@@ -191,13 +194,27 @@ __device__ __forceinline__ void pairs32_unit(int bx, int by, const PairTile* __r
             const float ri = rsqrtf(r2);
             const float ri2 = ri * ri;
             const float ri3 = ri2 * ri;
-            const float hf = fmaf(dx, A.w, fmaf(dy, B.x, dz * B.y));
-            const float hu = fmaf(dx, B.z, fmaf(dy, B.w, dz * C.x));
-            const float hn = fmaf(dx, C.y, fmaf(dy, C.z, dz * C.w));
-            const float t = ri3 * fmaf(hu * hn, ri2, hf);
-            acc[k][0] = fmaf(A.w, ri, fmaf(dx, t, acc[k][0]));
-            acc[k][1] = fmaf(B.x, ri, fmaf(dy, t, acc[k][1]));
-            acc[k][2] = fmaf(B.y, ri, fmaf(dz, t, acc[k][2]));
+            if (KIND == STD) {
+              const float hu = fmaf(dx, B.z, fmaf(dy, B.w, dz * C.x));
+              const float hn = fmaf(dx, C.y, fmaf(dy, C.z, dz * C.w));
+              const float t = (hu * hn) * (ri3 * ri2);
+              acc[k][0] = fmaf(dx, t, acc[k][0]);
+              acc[k][1] = fmaf(dy, t, acc[k][1]);
+              acc[k][2] = fmaf(dz, t, acc[k][2]);
+            } else {
+              const float hf = fmaf(dx, A.w, fmaf(dy, B.x, dz * B.y));
+              float t;
+              if (KIND == STS) {
+                t = ri3 * hf;
+              } else {
+                const float hu = fmaf(dx, B.z, fmaf(dy, B.w, dz * C.x));
+                const float hn = fmaf(dx, C.y, fmaf(dy, C.z, dz * C.w));
+                t = ri3 * fmaf(hu * hn, ri2, hf);
+              }
+              acc[k][0] = fmaf(A.w, ri, fmaf(dx, t, acc[k][0]));
+              acc[k][1] = fmaf(B.x, ri, fmaf(dy, t, acc[k][1]));
+              acc[k][2] = fmaf(B.y, ri, fmaf(dz, t, acc[k][2]));
+            }
           }
         }
       }
@@ -228,8 +245,8 @@ k_pairs32(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
           int64_t nsource, const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
           double* __restrict__ part) {
   __shared__ float4 sh0[kTile];
-  __shared__ float4 sh1[KIND == STO ? kTile : 1];
-  __shared__ float4 sh2[KIND == STO ? kTile : 1];
+  __shared__ float4 sh1[stokes_kind(KIND) ? kTile : 1];
+  __shared__ float4 sh2[stokes_kind(KIND) ? kTile : 1];
   pairs32_unit<KIND, kTPT>(blockIdx.x, blockIdx.y, tiles, drops, n_drops, tgt, ntarget, src32, nsource, dens32,
                            nsplit, has_f, has_u, part, sh0, sh1, sh2);
 }
@@ -244,8 +261,8 @@ k_pairs32_queue(const PairTile* __restrict__ tiles, const DropDev* __restrict__ 
                 int64_t nsource, const float* __restrict__ dens32, int nsplit, int has_f, int has_u,
                 double* __restrict__ part, int nunits, int* __restrict__ queue) {
   __shared__ float4 sh0[kTile];
-  __shared__ float4 sh1[KIND == STO ? kTile : 1];
-  __shared__ float4 sh2[KIND == STO ? kTile : 1];
+  __shared__ float4 sh1[stokes_kind(KIND) ? kTile : 1];
+  __shared__ float4 sh2[stokes_kind(KIND) ? kTile : 1];
   __shared__ int s_unit;
   for (;;) {
     __syncthreads();   // every thread is done with the previous unit's shared tiles and index
@@ -273,8 +290,8 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
            const float* __restrict__ src32lo, int64_t nsource, const float* __restrict__ dens32,
            const float* __restrict__ dens32lo, int nsplit, int has_f, int has_u, double* __restrict__ part) {
   using dfl::df;
-  constexpr int NC = (KIND == STO) ? 3 : 1;
-  constexpr int NV = (KIND == STO) ? 6 : 2;   // float4 per staged source
+  constexpr int NC = stokes_kind(KIND) ? 3 : 1;
+  constexpr int NV = stokes_kind(KIND) ? 6 : 2;   // float4 per staged source
   __shared__ float4 sh[NV][kTile];
   PairTile tile;
   if (!sub_tile<1>(tiles, tile, blockIdx.x)) return;
@@ -309,7 +326,7 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
         const int64_t sI = base + e;
         const float xh = src32[sI], yh = src32[nsource + sI], zh = src32[2 * nsource + sI];
         const float xl = src32lo[sI], yl = src32lo[nsource + sI], zl = src32lo[2 * nsource + sI];
-        if (KIND != STO) {
+        if (!stokes_kind(KIND)) {
           sh[0][e] = make_float4(xh, yh, zh, xl);
           sh[1][e] = make_float4(yl, zl, dens32[sI], dens32lo[sI]);
         } else {
@@ -333,7 +350,7 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
       __syncthreads();
       for (int e = 0; e < cnt; ++e) {
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (KIND != STO)
+        if constexpr (!stokes_kind(KIND))
           df_term<KIND>(T, N0, sh[0][e], sh[1][e], z4, z4, z4, z4, A);
         else
           df_term<KIND>(T, N0, sh[0][e], sh[1][e], sh[2][e], sh[3][e], sh[4][e], sh[5][e], A);
@@ -355,8 +372,8 @@ k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
           const double* __restrict__ tgt, int64_t ntarget, const double* __restrict__ src,
           int64_t nsource, const double* __restrict__ dens, int nsplit, int has_f, int has_u,
           double* __restrict__ part) {
-  constexpr int NC = (KIND == STO) ? 3 : 1;
-  constexpr int NF = (KIND == STO) ? 12 : 4;
+  constexpr int NC = stokes_kind(KIND) ? 3 : 1;
+  constexpr int NF = stokes_kind(KIND) ? 12 : 4;
   __shared__ double sh[NF][kTile];
   PairTile tile;
   if (!sub_tile<kTPT>(tiles, tile, blockIdx.x)) return;
@@ -395,7 +412,7 @@ k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
         sh[0][e] = src[sI];
         sh[1][e] = src[nsource + sI];
         sh[2][e] = src[2 * nsource + sI];
-        if (KIND != STO) {
+        if (!stokes_kind(KIND)) {
           sh[3][e] = dens[sI];
         } else {
 #pragma unroll
@@ -422,13 +439,19 @@ k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops,
           } else {
             const double ri2 = ri * ri, ri3 = ri2 * ri;
             const double fx = sh[3][e], fy = sh[4][e], fz = sh[5][e];
-            const double hf = dx * fx + dy * fy + dz * fz;
-            const double hu = dx * sh[6][e] + dy * sh[7][e] + dz * sh[8][e];
-            const double hn = dx * sh[9][e] + dy * sh[10][e] + dz * sh[11][e];
+            const double hf = KIND == STD ? 0.0 : dx * fx + dy * fy + dz * fz;
+            const double hu = KIND == STS ? 0.0 : dx * sh[6][e] + dy * sh[7][e] + dz * sh[8][e];
+            const double hn = KIND == STS ? 0.0 : dx * sh[9][e] + dy * sh[10][e] + dz * sh[11][e];
             const double t = ri3 * (hf + hu * hn * ri2);
-            acc[k][0] += fx * ri + dx * t;
-            acc[k][1] += fy * ri + dy * t;
-            acc[k][2] += fz * ri + dz * t;
+            if (KIND == STD) {
+              acc[k][0] += dx * t;
+              acc[k][1] += dy * t;
+              acc[k][2] += dz * t;
+            } else {
+              acc[k][0] += fx * ri + dx * t;
+              acc[k][1] += fy * ri + dy * t;
+              acc[k][2] += fz * ri + dz * t;
+            }
           }
         }
       }
@@ -557,7 +580,7 @@ int autotune(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
 
 template <int KIND>
 int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
-  constexpr int NC = (KIND == STO) ? 3 : 1;
+  constexpr int NC = stokes_kind(KIND) ? 3 : 1;
   if (ctx->n_drops < 2 || ctx->tiles.empty()) {
     if (before_reduce) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_reduce, 0));
     return SHBIM_OK;
@@ -589,9 +612,24 @@ int pairs_laplace(shbim_ctx* ctx, int which, double* out, cudaStream_t s, cudaEv
 }
 
 int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
-  return launch_pairs<STO>(ctx, has_f, has_u, out, s, before_reduce);
+  if (has_f && has_u) return launch_pairs<STO>(ctx, true, true, out, s, before_reduce);
+  if (has_f) return launch_pairs<STS>(ctx, true, false, out, s, before_reduce);
+  return launch_pairs<STD>(ctx, false, true, out, s, before_reduce);
 }
 
 int pairs_tile_targets() { return kTileTargets; }
+
+// Operations of one kernel term in the method's formulas (add or multiply 1, fused multiply-add 2,
+// reciprocal square root 1), d = x0 - x: d 3, r^2 = d.d 5, 1/r 1, then
+//   single layer   s (1/r) accumulated 2                                          -> 11
+//   double layer   1/r^3 2, d.n0 5, s/r^3 1, times d.n0 accumulated 2             -> 19
+//   Stokeslet      1/r^2 1, 1/r^3 1, d.f 5, t = d.f/r^3 1, per component f/r + d t accumulated 4 -> 29
+//   stresslet      1/r^2 1, 1/r^5 2, d.u 5, d.n 5, t = (d.u)(d.n)/r^5 2, per component d t accumulated 2 -> 30
+//   both           1/r^2 1, 1/r^3 1, d.f, d.u, d.n 15, t 4, per component 4       -> 42
+// (the 1/(4 pi) and the stresslet's -6 (lambda - 1) are applied per target or folded into strengths)
+double pairs_work(const shbim_ctx* ctx, int kind) {
+  static const double kFlops[5] = {19.0, 11.0, 42.0, 29.0, 30.0};
+  return kind >= 0 && kind < 5 ? kFlops[kind] * (double)ctx->cross_pairs : 0.0;
+}
 
 }  // namespace shbim

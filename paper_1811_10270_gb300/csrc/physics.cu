@@ -197,21 +197,22 @@ int ensure_buf(shbim_ctx* ctx, double** p, size_t* cap, size_t need) {
   return SHBIM_OK;
 }
 
-int solve(shbim_ctx* ctx, int sys, const double* rhs, double* x, double inner_tol, int* iters,
+int solve(shbim_ctx* ctx, int sys, const double* rhs, const double* x0, double* x, double inner_tol, int* iters,
           cudaStream_t s) {
   if (ctx->opts.precision == SHBIM_PREC_FP32_COMP) {
     int inner = 0, outer = 0;
-    int rc = shbim_gmres_solve_refined(ctx, sys, rhs, nullptr, x, inner_tol, 20, &inner, &outer, nullptr, s);
+    int rc = shbim_gmres_solve_refined(ctx, sys, rhs, x0, x, inner_tol, 20, &inner, &outer, nullptr, s);
     if (iters) *iters = inner;
     return rc;
   }
-  return shbim_gmres_solve(ctx, sys, rhs, nullptr, x, iters, nullptr, s);
+  return shbim_gmres_solve(ctx, sys, rhs, x0, x, iters, nullptr, s);
 }
 
 }  // namespace
 
+// u_guess (may be null): initial guess of the Stokes solve (the other stage's velocity in a time step)
 int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, double* gE, int* it_e,
-          int* it_s, cudaStream_t s) {
+          int* it_s, cudaStream_t s, const double* u_guess = nullptr) {
   const int64_t n = ctx->ncoef, NS = ctx->nsource;
   auto& W = ctx->phys;
   int rc;
@@ -232,15 +233,17 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   ctx->opts.R = R;
   // (i) E_n
   if ((rc = shbim_electric_rhs(ctx, ph.E_u, ph.E_q, rhs_e, s))) return rc;
-  if ((rc = solve(ctx, SHBIM_SYS_ELECTRIC, rhs_e, En, ph.inner_tol, it_e, s))) return rc;
+  if ((rc = solve(ctx, SHBIM_SYS_ELECTRIC, rhs_e, nullptr, En, ph.inner_tol, it_e, s))) return rc;
   // (ii) phi_q = S_L[(1 - 1/R) E_n]
   k_lincomb<<<nb(n), 256, 0, s>>>(q, En, 1.0 - 1.0 / R, En, 0.0, n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
-  // one-shot applications (not iterated by GMRES) always use FP64-class sums: in mixed precision
-  // only the operator inside the inner GMRES runs in FP32, the rest uses the context's outer
-  // precision (FP64 or double-float)
+  // one-shot applications (not iterated by GMRES): in mixed precision their arithmetic is the
+  // context's one-shot precision (FP64-class by default: the single layer of the capillary traction
+  // nearly cancels over a drop -- a sphere under uniform tension does not move -- so an FP32 sum's
+  // ~1e-7 relative error of S[f/Ca_E] is a much larger relative error of the velocity); otherwise
+  // the context's precision
   const int saved_prec = ctx->opts.precision;
-  const int oneshot = saved_prec == SHBIM_PREC_FP32_COMP ? ctx->outer_prec : saved_prec;
+  const int oneshot = saved_prec == SHBIM_PREC_FP32_COMP ? ctx->oneshot_prec : saved_prec;
   ctx->opts.precision = oneshot;
   rc = shbim_eval_electric(ctx, SHBIM_LAPLACE_SL, q, phi, SHBIM_OUT_COEF, s);
   ctx->opts.precision = saved_prec;
@@ -268,7 +271,7 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   if (rc) return rc;
   k_lincomb<<<nb(3 * n), 256, 0, s>>>(rhs_s, rhs_s, -1.0, rhs_s, 0.0, 3 * n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
-  if ((rc = solve(ctx, SHBIM_SYS_STOKES, rhs_s, u, ph.inner_tol, it_s, s))) return rc;
+  if ((rc = solve(ctx, SHBIM_SYS_STOKES, rhs_s, u_guess, u, ph.inner_tol, it_s, s))) return rc;
   // surfactant rate -Gamma div_S u, projected to degree p
   for (auto& d : ctx->drops) {
     const GridTables& g = d.tab->up;
@@ -388,7 +391,8 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* ph, const double* x_dev, const 
     if ((rc = shbim_set_diffusion(ctx, 0.5 * dt / ph->Pe))) return rc;
     if ((rc = shbim_gmres_solve(ctx, SHBIM_SYS_DIFFUSION, gh, nullptr, gh, nullptr, nullptr, s))) return rc;
   }
-  if ((rc = rates(ctx, *ph, gh, u1, g1, &its[2], &its[3], s))) return rc;
+  // the second stage's Stokes solve starts from the first stage's velocity
+  if ((rc = rates(ctx, *ph, gh, u1, g1, &its[2], &its[3], s, u0))) return rc;
   if (diffuse) {
     double* lg = W.state + 12 * n;
     if ((rc = laplace_beltrami(ctx, gh, lg, s))) return rc;

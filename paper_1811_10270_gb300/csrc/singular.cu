@@ -538,7 +538,7 @@ int apply_self_laplace(shbim_ctx* ctx, int which, const double* dens, double* ou
   if (rc) return rc;
   const int64_t threads = ctx->ntarget * 32;
   const unsigned g = (unsigned)((threads + 255) / 256);
-  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP)
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP && ctx->self_prec == SHBIM_PREC_FP32_COMP)
     k_self_lap<false><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, which, xh, xl, out);
   else
     k_self_lap<true><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, which, xh, xl, out);
@@ -554,7 +554,7 @@ int apply_self_stokes(shbim_ctx* ctx, const double* f, const double* u, double* 
   if (u && (rc = split_density(ctx, u, n3, 1, &uh, &ul, s))) return rc;
   const int64_t threads = ctx->ntarget * 32;
   const unsigned g = (unsigned)((threads + 255) / 256);
-  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP)
+  if (ctx->opts.precision == SHBIM_PREC_FP32_COMP && ctx->self_prec == SHBIM_PREC_FP32_COMP)
     k_self_sto<false><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, fh, fl, uh, ul, out);
   else
     k_self_sto<true><<<g, 256, 0, s>>>(ctx->drops_dev, ctx->geo.tgt_drop, ctx->ntarget, fh, fl, uh, ul, out);

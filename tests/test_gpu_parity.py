@@ -310,7 +310,9 @@ def test_every_pair_launch_shape_matches_oracle(S):
     u = [inputs.random_density(d.p, rng, 3) for d in drops]
     f = [inputs.random_density(d.p, rng, 3) for d in drops]
     ref = {0: np.concatenate(sysm.laplace_coef("ladl", sig)), 1: np.concatenate(sysm.laplace_coef("lsl", sig)),
-           2: np.concatenate([a.ravel() for a in sysm.stokes_coef(f, u)])}
+           2: np.concatenate([a.ravel() for a in sysm.stokes_coef(f, u)]),
+           3: np.concatenate([a.ravel() for a in sysm.stokes_coef(f, None)]),
+           4: np.concatenate([a.ravel() for a in sysm.stokes_coef(None, u)])}
     nc = sum(sh.ncoef(d.p) for d in drops)
     ctx = make(S, drops, S.FP32_COMP, near=False)
     sig_d = T(np.concatenate(sig))
@@ -322,7 +324,7 @@ def test_every_pair_launch_shape_matches_oracle(S):
         for splits in sorted({1, max(1, default_splits)}):
             got = {}
             for queue in (False, True):
-                for kind in (0, 1, 2):
+                for kind in (0, 1, 2, 3, 4):
                     ctx.set_pair_shape(kind, tpt, splits)
                     ctx.set_pair_queue(kind, queue)
                     assert ctx.pair_shape(kind) == (tpt, splits, True) and ctx.pair_queue(kind) == queue
@@ -335,8 +337,12 @@ def test_every_pair_launch_shape_matches_oracle(S):
                     sl = out.cpu().numpy()
                     out3 = torch.empty(3 * nc, device=DEV, dtype=torch.float64)
                     ctx.eval_stokes(f_d, u_d, out3, S.OUT_COEF)
-                    outs.append((dl, sl, out3.cpu().numpy()))
-                    for k in range(3):
+                    sd = out3.cpu().numpy()
+                    ctx.eval_stokes(f_d, None, out3, S.OUT_COEF)
+                    so = out3.cpu().numpy()
+                    ctx.eval_stokes(None, u_d, out3, S.OUT_COEF)
+                    outs.append((dl, sl, sd, so, out3.cpu().numpy()))
+                    for k in range(5):
                         assert rel_err(outs[-1][k], ref[k]) < TOL32, (tpt, splits, queue, k)
                 got[queue] = outs
             for a, b in zip(got[False][0], got[True][0]):
