@@ -269,7 +269,8 @@ def run_own(args):
     clk = clocks.stop()
     if args.profile:
         ctx.close()
-        print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps, "applications": apps_total}))
+        print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps, "applications": apps_total,
+                          "launches_before_timed": launches0, "launches_timed": launches}))
         return
     if world > 1:
         t = torch.tensor([ms], device=dev)

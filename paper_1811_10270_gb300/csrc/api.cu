@@ -82,6 +82,14 @@ void free_drop_state(shbim_ctx* ctx) {
   cudaFree(ctx->xup);
   ctx->xup = nullptr;
   ctx->tiles.clear();
+  for (auto& g : ctx->groups) {
+    cudaFree(g.idx);
+    cudaFree(g.coef);
+    cudaFree(g.src);
+    cudaFree(g.tgt);
+    cudaFree(g.tgt3);
+  }
+  ctx->groups.clear();
   ctx->n_drops = 0;
   ctx->ncoef = ctx->ntarget = ctx->nsource = 0;
 }
@@ -154,6 +162,9 @@ int shbim_destroy(shbim_ctx* ctx) {
     cudaFree(N.stats); cudaFree(N.det_t); cudaFree(N.det_j); cudaFree(N.pair_t); cudaFree(N.pair_j);
     cudaFree(N.fgeo); cudaFree(N.fgeo32); cudaFree(N.fstr); cudaFree(N.fstr32); cudaFree(N.foff_dev);
     cudaFree(N.fgeo32lo); cudaFree(N.fstr32lo); cudaFree(N.groups);
+    for (auto& g : N.groups_d) {
+      cudaFree(g.idx); cudaFree(g.coef); cudaFree(g.fine);
+    }
   }
   for (auto& g : ctx->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -383,6 +394,42 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
         (rc = dalloc(ctx, &d.rows_sto, 2 * (size_t)d.nt * kNumSto * d.nc, "stokes rows")))
       return rc;
   }
+  // drops grouped by degree: the transforms of an operator application take one launch per degree
+  {
+    std::vector<int> order;
+    for (int i = 0; i < n_drops; ++i) {
+      bool seen = false;
+      for (int k : order) seen = seen || ctx->drops[k].p == ctx->drops[i].p;
+      if (!seen) order.push_back(i);
+    }
+    for (int first : order) {
+      std::vector<int> idx;
+      std::vector<int64_t> co, sr, tg, tg3;
+      for (int i = 0; i < n_drops; ++i)
+        if (ctx->drops[i].p == ctx->drops[first].p) {
+          idx.push_back(i);
+          co.push_back(ctx->drops[i].coef_off);
+          sr.push_back(ctx->drops[i].src_off);
+          tg.push_back(ctx->drops[i].tgt_off);
+          tg3.push_back(3 * ctx->drops[i].tgt_off);
+        }
+      DegreeGroup G;
+      G.tab = ctx->drops[first].tab;
+      G.n = (int)idx.size();
+      G.first = first;
+      ctx->groups.push_back(G);
+      DegreeGroup& g = ctx->groups.back();
+      if ((rc = dalloc(ctx, &g.idx, idx.size(), "degree group")) || (rc = dalloc(ctx, &g.coef, co.size(), "degree group")) ||
+          (rc = dalloc(ctx, &g.src, sr.size(), "degree group")) || (rc = dalloc(ctx, &g.tgt, tg.size(), "degree group")) ||
+          (rc = dalloc(ctx, &g.tgt3, tg3.size(), "degree group")))
+        return rc;
+      SHBIM_CUDA(ctx, cudaMemcpy(g.tgt3, tg3.data(), tg3.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      SHBIM_CUDA(ctx, cudaMemcpy(g.idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+      SHBIM_CUDA(ctx, cudaMemcpy(g.coef, co.data(), co.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      SHBIM_CUDA(ctx, cudaMemcpy(g.src, sr.data(), sr.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+      SHBIM_CUDA(ctx, cudaMemcpy(g.tgt, tg.data(), tg.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+  }
   {
     std::vector<int> tdrop(to);
     for (int i = 0; i < n_drops; ++i)
@@ -487,14 +534,6 @@ int shbim_sht(shbim_ctx* ctx, int dir, int grid, int n_fields, const int32_t* fi
 namespace shbim {
 namespace {
 
-// Number of consecutive drops from drop a on with the same degree (their coefficients, targets and
-// sources are contiguous, so one launch transforms them all).
-int same_degree_run(const shbim_ctx* ctx, size_t a) {
-  size_t b = a + 1;
-  while (b < ctx->drops.size() && ctx->drops[b].tab == ctx->drops[a].tab) ++b;
-  return (int)(b - a);
-}
-
 }  // namespace
 
 int ensure_side_stream(shbim_ctx* ctx) {
@@ -562,13 +601,11 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   }
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
-      const Drop& d = ctx->drops[a];
-      const int nb = same_degree_run(ctx, a);
-      b = a + nb;
-      rc = sht_synth_drops(ctx, d.tab->up, nb, 1, dens_dev + d.coef_off, d.nc, ctx->dens_up + d.src_off, 0, d.ns,
-                           ctx->geo.src + 6 * ctx->nsource + d.src_off, 1.0, nullptr,
-                           f32 ? ctx->dens_up32 + d.src_off : nullptr, s, lo ? ctx->dens_up32lo + d.src_off : nullptr);
+    for (const DegreeGroup& G : ctx->groups) {
+      const DropList L = G.sources();
+      const int nc = ncoef(G.tab->p);
+      rc = sht_synth_drops(ctx, G.tab->up, G.n, 1, dens_dev, nc, ctx->dens_up, 0, 0, ctx->geo.src + 6 * ctx->nsource,
+                           1.0, nullptr, f32 ? ctx->dens_up32 : nullptr, s, lo ? ctx->dens_up32lo : nullptr, &L);
       if (rc) return rc;
     }
   }
@@ -585,11 +622,9 @@ int shbim_eval_electric(shbim_ctx* ctx, int which, const double* dens_dev, doubl
   }
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
-      const Drop& d = ctx->drops[a];
-      const int nb = same_degree_run(ctx, a);
-      b = a + nb;
-      rc = sht_analysis(ctx, d.tab->base, nb, vals + d.tgt_off, d.nt, true, out_dev + d.coef_off, d.nc, s);
+    for (const DegreeGroup& G : ctx->groups) {
+      const DropList L = G.targets();
+      rc = sht_analysis(ctx, G.tab->base, G.n, vals, 0, true, out_dev, ncoef(G.tab->p), s, 1, &L);
       if (rc) return rc;
     }
   }
@@ -618,22 +653,19 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   }
   if (ctx->n_drops > 1) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
-      const Drop& d = ctx->drops[a];
-      const int nb = same_degree_run(ctx, a);
-      b = a + nb;
-      const double* w = ctx->geo.src + 6 * NS + d.src_off;
+    for (const DegreeGroup& G : ctx->groups) {
+      const DropList L = G.sources();
+      const int nc = ncoef(G.tab->p);
+      const double* w = ctx->geo.src + 6 * NS;
       if (f_dev) {
-        rc = sht_synth_drops(ctx, d.tab->up, nb, 3, f_dev + 3 * d.coef_off, d.nc, ctx->dens_up + d.src_off, NS, d.ns,
-                             w, 1.0, nullptr, f32 ? ctx->dens_up32 + d.src_off : nullptr, s,
-                             lo ? ctx->dens_up32lo + d.src_off : nullptr);
+        rc = sht_synth_drops(ctx, G.tab->up, G.n, 3, f_dev, nc, ctx->dens_up, NS, 0, w, 1.0, nullptr,
+                             f32 ? ctx->dens_up32 : nullptr, s, lo ? ctx->dens_up32lo : nullptr, &L);
         if (rc) return rc;
       }
       if (u_dev) {
         // strength -6 (lambda_j - 1) u per drop
-        rc = sht_synth_drops(ctx, d.tab->up, nb, 3, u_dev + 3 * d.coef_off, d.nc, ctx->dens_up + 3 * NS + d.src_off,
-                             NS, d.ns, w, -6.0, ctx->lamm1_dev + a, f32 ? ctx->dens_up32 + 3 * NS + d.src_off : nullptr,
-                             s, lo ? ctx->dens_up32lo + 3 * NS + d.src_off : nullptr);
+        rc = sht_synth_drops(ctx, G.tab->up, G.n, 3, u_dev, nc, ctx->dens_up + 3 * NS, NS, 0, w, -6.0, ctx->lamm1_dev,
+                             f32 ? ctx->dens_up32 + 3 * NS : nullptr, s, lo ? ctx->dens_up32lo + 3 * NS : nullptr, &L);
         if (rc) return rc;
       }
     }
@@ -651,11 +683,10 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
   }
   if (out_kind == SHBIM_OUT_COEF) {
     TimeScope ts(ctx, SHBIM_K_SHT, s);
-    for (size_t a = 0, b; a < ctx->drops.size(); a = b) {
-      const Drop& d = ctx->drops[a];
-      const int nb = same_degree_run(ctx, a);
-      b = a + nb;
-      rc = sht_analysis(ctx, d.tab->base, 3 * nb, vals + 3 * d.tgt_off, d.nt, true, out_dev + 3 * d.coef_off, d.nc, s);
+    for (const DegreeGroup& G : ctx->groups) {
+      const DropList L = G.targets3();
+      const int p = G.tab->p;
+      rc = sht_analysis(ctx, G.tab->base, 3 * G.n, vals, npts(p), true, out_dev, ncoef(p), s, 3, &L);
       if (rc) return rc;
     }
   }
@@ -772,9 +803,9 @@ int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, doubl
   k_field_normal<<<(unsigned)((ctx->ntarget + 255) / 256), 256, 0, s>>>(
       ctx->geo.tgt, ctx->ntarget, E_u_host[0], E_u_host[1], E_u_host[2], E_q, R / (R + 1.0), ctx->grid_out);
   SHBIM_CHECK_LAUNCH(ctx, "k_field_normal");
-  for (auto& d : ctx->drops) {
-    int rc = sht_analysis(ctx, d.tab->base, 1, ctx->grid_out + d.tgt_off, d.nt, true, out_dev + d.coef_off,
-                          d.nc, s);
+  for (const DegreeGroup& G : ctx->groups) {
+    const DropList L = G.targets();
+    int rc = sht_analysis(ctx, G.tab->base, G.n, ctx->grid_out, 0, true, out_dev, ncoef(G.tab->p), s, 1, &L);
     if (rc) return rc;
   }
   return SHBIM_OK;

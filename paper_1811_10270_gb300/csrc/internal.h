@@ -100,6 +100,15 @@ struct Drop {
   float* rows_sto = nullptr;    // [2][nt][kNumSto][nc]
 };
 
+// The drops of one degree, wherever they lie in the layout: transforms over a list take one launch per
+// distinct degree. Entry l is drop idx[l]; its scalar coefficients start at coef_off[l] (vector fields
+// at 3 coef_off[l]) and its grid values at val_off[l] (a source, target or upsampled-grid offset).
+struct DropList {
+  const int* idx = nullptr;
+  const int64_t* coef_off = nullptr;
+  const int64_t* val_off = nullptr;
+};
+
 // Per-drop description read by the kernels.
 struct DropDev {
   int p, q, nt, ns, nc;
@@ -115,6 +124,21 @@ struct PairTile {
   int drop;
   int t0;      // global target index
   int nt;
+};
+
+// Drops grouped by degree (set up with the layout): device lists with source and target offsets.
+struct DegreeGroup {
+  DegreeTables* tab = nullptr;
+  int n = 0;                 // drops of this degree
+  int first = 0;             // first of them in the layout (for host-side per-drop data)
+  int* idx = nullptr;        // [n] device
+  int64_t* coef = nullptr;   // [n] device
+  int64_t* src = nullptr;    // [n] device
+  int64_t* tgt = nullptr;    // [n] device
+  int64_t* tgt3 = nullptr;   // [n] device: 3 tgt (vector fields on the targets, component-major per drop)
+  DropList sources() const { return DropList{idx, coef, src}; }
+  DropList targets() const { return DropList{idx, coef, tgt}; }
+  DropList targets3() const { return DropList{idx, coef, tgt3}; }
 };
 
 struct Geometry {
@@ -142,6 +166,7 @@ struct shbim_ctx {
   std::map<int, shbim::DegreeTables*> tables;
   shbim::Geometry geo;
   std::vector<shbim::PairTile> tiles;
+  std::vector<shbim::DegreeGroup> groups;  // drops by degree, in order of first appearance
   shbim::PairTile* tiles_dev = nullptr;
   double* lamm1_dev = nullptr;    // lambda_j - 1 per drop
   shbim::DropDev* drops_dev = nullptr;
@@ -241,6 +266,16 @@ struct shbim_ctx {
     int ngroups = 0;                                  // (first pair, count, drop, 0)
     std::vector<int64_t> fine_off_h, fine_n_h;
     int64_t nfine = 0;
+    // drops with near targets grouped by degree (one upsampled-strength launch per degree): device
+    // lists of drop index, coefficient offset and upsampled-grid offset
+    struct DegGroup {
+      shbim::DegreeTables* tab = nullptr;
+      int n = 0;
+      int* idx = nullptr;
+      int64_t* coef = nullptr;
+      int64_t* fine = nullptr;
+    };
+    std::vector<DegGroup> groups_d;
   } near;
   // physics workspaces (forces, rates, step state)
   struct Phys {
@@ -328,21 +363,29 @@ void free_degree_tables(DegreeTables* t);
 // out[item * item_stride + kind_slot * kind_stride + node]; kinds are packed in order.
 // If scale != nullptr, each node value is multiplied by scale[node] (values only).
 // If out32 != nullptr the result is also written as float to out32 at the same index.
+// With a drop list L: n_items = L's length x kpd, item l kpd + c reads coef + kpd L.coef_off[l] +
+// c coef_stride and writes out + L.val_off[l] + c item_stride (+ kind slot * kind_stride).
 int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
               int64_t coef_stride, int kinds, double* out, int64_t item_stride,
-              int64_t kind_stride, const double* scale, float* out32, cudaStream_t s);
+              int64_t kind_stride, const double* scale, float* out32, cudaStream_t s,
+              int kpd = 0, const DropList* L = nullptr);
 // out32lo (optional) receives value - (double)out32 as float (the low part of a double-float copy)
 int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
                      int64_t coef_stride, double* out, int64_t item_stride, const double* scale,
                      double alpha, float* out32, cudaStream_t s, float* out32lo = nullptr);
+// With a drop list L (non-null), the nb drops are L's entries instead of consecutive drops: coef, out,
+// scale and alpha_drop are then the bases of the whole layout's arrays (drop_stride is unused).
 int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const double* coef, int64_t coef_stride,
                     double* out, int64_t comp_stride, int64_t drop_stride, const double* scale, double alpha,
-                    const double* alpha_drop, float* out32, cudaStream_t s, float* out32lo = nullptr);
+                    const double* alpha_drop, float* out32, cudaStream_t s, float* out32lo = nullptr,
+                    const DropList* L = nullptr);
 // Analysis: coef[item] = sum_nodes w(node) vals[item][node] S_nm(node) with w = omega_j when
 // weighted, else 1. Uses ctx->sht_scratch (grown as needed).
+// With a drop list L, n_items = L's length x kpd: item l kpd + c reads vals + L.val_off[l] + c val_stride
+// and writes coef + kpd L.coef_off[l] + c coef_stride.
 int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double* vals,
                  int64_t val_stride, bool weighted, double* coef, int64_t coef_stride,
-                 cudaStream_t s);
+                 cudaStream_t s, int kpd = 1, const DropList* L = nullptr);
 
 // ---- geometry / singular rows (singular.cu)
 int build_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);

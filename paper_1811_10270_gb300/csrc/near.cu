@@ -678,6 +678,38 @@ int build_near(shbim_ctx* ctx, const double* xcoef, cudaStream_t s) {
     }
     SHBIM_CUDA(ctx, cudaMemcpy(N.foff_dev, both.data(), sizeof(int64_t) * 2 * nd, cudaMemcpyHostToDevice));
   }
+  // near drops grouped by degree for the per-application upsampled strengths
+  for (auto& g : N.groups_d) {
+    cudaFree(g.idx);
+    cudaFree(g.coef);
+    cudaFree(g.fine);
+  }
+  N.groups_d.clear();
+  for (int j = 0; j < nd; ++j) {
+    if (N.fine_off_h[j] < 0) continue;
+    bool seen = false;
+    for (const auto& g : N.groups_d) seen = seen || g.tab == ctx->drops[j].tab;
+    if (seen) continue;
+    std::vector<int> idx;
+    std::vector<int64_t> co, fo;
+    for (int k = j; k < nd; ++k)
+      if (N.fine_off_h[k] >= 0 && ctx->drops[k].tab == ctx->drops[j].tab) {
+        idx.push_back(k);
+        co.push_back(ctx->drops[k].coef_off);
+        fo.push_back(N.fine_off_h[k]);
+      }
+    N.groups_d.push_back(shbim_ctx::Near::DegGroup{});
+    auto& g = N.groups_d.back();
+    g.tab = ctx->drops[j].tab;
+    g.n = (int)idx.size();
+    if (cudaMalloc(&g.idx, idx.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&g.coef, co.size() * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&g.fine, fo.size() * sizeof(int64_t)) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "near degree groups");
+    SHBIM_CUDA(ctx, cudaMemcpy(g.idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SHBIM_CUDA(ctx, cudaMemcpy(g.coef, co.data(), co.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    SHBIM_CUDA(ctx, cudaMemcpy(g.fine, fo.data(), fo.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
   int64_t maxn = 0;
   for (int j = 0; j < nd; ++j) maxn = std::max(maxn, N.fine_n_h[j]);
   double* tmp = nullptr;
@@ -781,13 +813,10 @@ int apply_near_laplace(shbim_ctx* ctx, int which, const double* dens, double* ou
   if (N.npairs == 0) return SHBIM_OK;
   const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
   const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
-  for (int j = 0; j < ctx->n_drops; ++j) {
-    if (N.fine_off_h[j] < 0) continue;
-    const Drop& d = ctx->drops[j];
-    const int64_t o = N.fine_off_h[j];
-    int rc = sht_synth_scaled(ctx, d.tab->fine, 1, dens + d.coef_off, d.nc, N.fstr + o, 0,
-                              N.fgeo + 6 * N.nfine + o, 1.0, f32 ? N.fstr32 + o : nullptr, s,
-                              lo ? N.fstr32lo + o : nullptr);
+  for (const auto& g : N.groups_d) {
+    const DropList L{g.idx, g.coef, g.fine};
+    int rc = sht_synth_drops(ctx, g.tab->fine, g.n, 1, dens, ncoef(g.tab->p), N.fstr, 0, 0, N.fgeo + 6 * N.nfine, 1.0,
+                             nullptr, f32 ? N.fstr32 : nullptr, s, lo ? N.fstr32lo : nullptr, &L);
     if (rc) return rc;
   }
   if (before_sums) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_sums, 0));
@@ -800,18 +829,18 @@ int apply_near_stokes(shbim_ctx* ctx, const double* f, const double* u, double* 
   if (N.npairs == 0) return SHBIM_OK;
   const bool f32 = ctx->opts.precision != SHBIM_PREC_FP64;
   const bool lo = ctx->opts.precision == SHBIM_PREC_DF64;
-  for (int j = 0; j < ctx->n_drops; ++j) {
-    if (N.fine_off_h[j] < 0) continue;
-    const Drop& d = ctx->drops[j];
-    const int64_t o = N.fine_off_h[j];
-    const double* w = N.fgeo + 6 * N.nfine + o;
+  for (const auto& g : N.groups_d) {
+    const DropList L{g.idx, g.coef, g.fine};
+    const int nc = ncoef(g.tab->p);
+    const double* w = N.fgeo + 6 * N.nfine;
     int rc;
-    if (f && (rc = sht_synth_scaled(ctx, d.tab->fine, 3, f + 3 * d.coef_off, d.nc, N.fstr + o, N.nfine, w, 1.0,
-                                    f32 ? N.fstr32 + o : nullptr, s, lo ? N.fstr32lo + o : nullptr)))
+    if (f && (rc = sht_synth_drops(ctx, g.tab->fine, g.n, 3, f, nc, N.fstr, N.nfine, 0, w, 1.0, nullptr,
+                                   f32 ? N.fstr32 : nullptr, s, lo ? N.fstr32lo : nullptr, &L)))
       return rc;
-    if (u && (rc = sht_synth_scaled(ctx, d.tab->fine, 3, u + 3 * d.coef_off, d.nc, N.fstr + 3 * N.nfine + o,
-                                    N.nfine, w, -6.0 * (d.lam - 1.0), f32 ? N.fstr32 + 3 * N.nfine + o : nullptr,
-                                    s, lo ? N.fstr32lo + 3 * N.nfine + o : nullptr)))
+    // strength -6 (lambda_j - 1) u per drop
+    if (u && (rc = sht_synth_drops(ctx, g.tab->fine, g.n, 3, u, nc, N.fstr + 3 * N.nfine, N.nfine, 0, w, -6.0,
+                                   ctx->lamm1_dev, f32 ? N.fstr32 + 3 * N.nfine : nullptr, s,
+                                   lo ? N.fstr32lo + 3 * N.nfine : nullptr, &L)))
       return rc;
   }
   if (before_sums) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_sums, 0));

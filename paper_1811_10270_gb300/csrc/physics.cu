@@ -251,18 +251,25 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   // (iii)-(v) traction on every drop's upsampled grid, projected to degree p
   PhysDev P{ph.R, ph.Q, ph.Ca_E, ph.beta, ph.x_s, ph.E_u[0], ph.E_u[1], ph.E_u[2], ph.E_q,
             1.0 + ph.beta * std::log(1.0 - ph.x_s)};
-  for (auto& d : ctx->drops) {
-    const GridTables& g = d.tab->up;
-    const int64_t o = d.src_off;
-    if ((rc = sht_synth(ctx, g, 1, En + d.coef_off, d.nc, 1 << 0, fl + o, 0, NS, nullptr, nullptr, s)) ||
-        (rc = sht_synth(ctx, g, 1, phi + d.coef_off, d.nc, (1 << 1) | (1 << 6), fl + NS + o, 0, NS, nullptr,
-                        nullptr, s)) ||
-        (rc = sht_synth(ctx, g, 1, gamma + d.coef_off, d.nc, (1 << 0) | (1 << 1) | (1 << 6), fl + 3 * NS + o, 0,
-                        NS, nullptr, nullptr, s)))
+  // fields on every drop's upsampled grid, one launch per degree
+  for (const DegreeGroup& G : ctx->groups) {
+    const GridTables& g = G.tab->up;
+    const DropList L = G.sources();
+    const int nc = ncoef(G.tab->p);
+    if ((rc = sht_synth(ctx, g, G.n, En, nc, 1 << 0, fl, 0, NS, nullptr, nullptr, s, 1, &L)) ||
+        (rc = sht_synth(ctx, g, G.n, phi, nc, (1 << 1) | (1 << 6), fl + NS, 0, NS, nullptr, nullptr, s, 1, &L)) ||
+        (rc = sht_synth(ctx, g, G.n, gamma, nc, (1 << 0) | (1 << 1) | (1 << 6), fl + 3 * NS, 0, NS, nullptr, nullptr,
+                        s, 1, &L)))
       return rc;
+  }
+  for (auto& d : ctx->drops) {
+    const int64_t o = d.src_off;
     k_traction<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, fl + o, NS, P, tv + o, NS);
     SHBIM_CHECK_LAUNCH(ctx, "k_traction");
-    if ((rc = sht_analysis(ctx, g, 3, tv + o, NS, true, tco + 3 * d.coef_off, d.nc, s))) return rc;
+  }
+  for (const DegreeGroup& G : ctx->groups) {
+    const DropList L = G.sources();
+    if ((rc = sht_analysis(ctx, G.tab->up, 3 * G.n, tv, NS, true, tco, ncoef(G.tab->p), s, 3, &L))) return rc;
   }
   // (vi) Stokes: (lam_i+1) u - sum (lam_j-1) D_j[u] = -sum_j S_j[f/Ca_E - f^E]
   ctx->opts.precision = oneshot;
@@ -273,15 +280,20 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
   if ((rc = solve(ctx, SHBIM_SYS_STOKES, rhs_s, u_guess, u, ph.inner_tol, it_s, s))) return rc;
   // surfactant rate -Gamma div_S u, projected to degree p
-  for (auto& d : ctx->drops) {
-    const GridTables& g = d.tab->up;
-    const int64_t o = d.src_off;
-    if ((rc = sht_synth(ctx, g, 3, u + 3 * d.coef_off, d.nc, (1 << 1) | (1 << 6), uf + o, 2 * NS, NS, nullptr,
-                        nullptr, s)))
+  for (const DegreeGroup& G : ctx->groups) {
+    const DropList L = G.sources();
+    if ((rc = sht_synth(ctx, G.tab->up, 3 * G.n, u, ncoef(G.tab->p), (1 << 1) | (1 << 6), uf, 2 * NS, NS, nullptr,
+                        nullptr, s, 3, &L)))
       return rc;
+  }
+  for (auto& d : ctx->drops) {
+    const int64_t o = d.src_off;
     k_surf_rate<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, uf + o, NS, fl + 3 * NS + o, gv + o);
     SHBIM_CHECK_LAUNCH(ctx, "k_surf_rate");
-    if ((rc = sht_analysis(ctx, g, 1, gv + o, NS, true, gE + d.coef_off, d.nc, s))) return rc;
+  }
+  for (const DegreeGroup& G : ctx->groups) {
+    const DropList L = G.sources();
+    if ((rc = sht_analysis(ctx, G.tab->up, G.n, gv, 0, true, gE, ncoef(G.tab->p), s, 1, &L))) return rc;
   }
   return SHBIM_OK;
 }

@@ -34,13 +34,14 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
                         double* __restrict__ out, int64_t item_stride, int64_t kind_stride,
                         const double* __restrict__ scale, double alpha, float* __restrict__ out32,
                         float* __restrict__ out32lo, int kpd, int64_t drop_stride,
-                        const double* __restrict__ alpha_drop) {
+                        const double* __restrict__ alpha_drop, DropList L) {
   extern __shared__ double sm[];
   const int item = blockIdx.x;
   const int dl = item / kpd, ci = item - dl * kpd;
-  const int64_t obase = (int64_t)dl * drop_stride + (int64_t)ci * item_stride;
-  if (scale) scale += (int64_t)dl * drop_stride;
-  if (alpha_drop) alpha *= alpha_drop[dl];
+  const int64_t dbase = L.idx ? L.val_off[dl] : (int64_t)dl * drop_stride;
+  const int64_t obase = dbase + (int64_t)ci * item_stride;
+  if (scale) scale += dbase;
+  if (alpha_drop) alpha *= alpha_drop[L.idx ? L.idx[dl] : dl];
   const int j = blockIdx.y;
   const int nk = __popc(kinds);
   const int N = 2 * q + 2;
@@ -52,7 +53,8 @@ __global__ void k_synth(const double* __restrict__ coef, int64_t coef_stride, in
     tc[i] = trig[i];
     ts[i] = trig[N + i];
   }
-  const double* c = coef + (int64_t)item * coef_stride;
+  const double* c = coef + (L.idx ? (int64_t)kpd * L.coef_off[dl] + (int64_t)ci * coef_stride
+                                   : (int64_t)item * coef_stride);
   const int nt = (p + 1) * (p + 2) / 2;
   const double* T = alf + (int64_t)j * kNumTab * nt;
   const int ntask = nk * 2 * P1;
@@ -150,14 +152,16 @@ int synth_smem_ok(shbim_ctx* ctx, size_t smem) {
 
 int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* coef,
               int64_t coef_stride, int kinds, double* out, int64_t item_stride,
-              int64_t kind_stride, const double* scale, float* out32, cudaStream_t s) {
+              int64_t kind_stride, const double* scale, float* out32, cudaStream_t s, int kpd,
+              const DropList* L) {
   if (n_items <= 0) return SHBIM_OK;
   const int nk = __builtin_popcount(kinds);
   const size_t smem = (size_t)(nk * 2 * (g.p + 1) + (2 + nk) * (2 * g.q + 2)) * sizeof(double);
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, kinds, out,
-                                  item_stride, kind_stride, scale, 1.0, out32, nullptr, n_items, 0, nullptr);
+                                  item_stride, kind_stride, scale, 1.0, out32, nullptr, L ? kpd : n_items, 0, nullptr,
+                                  L ? *L : DropList{});
   SHBIM_CHECK_LAUNCH(ctx, "k_synth");
   return SHBIM_OK;
 }
@@ -168,12 +172,13 @@ int sht_synth(shbim_ctx* ctx, const GridTables& g, int n_items, const double* co
 __global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, int p, int q,
                           const float* __restrict__ alf32, const float* __restrict__ trig32, float* __restrict__ out32,
                           int64_t item_stride, const double* __restrict__ scale, double alpha, int kpd,
-                          int64_t drop_stride, const double* __restrict__ alpha_drop) {
+                          int64_t drop_stride, const double* __restrict__ alpha_drop, DropList L) {
   extern __shared__ float smf32[];
   const int item = blockIdx.x, j = blockIdx.y;
   const int dl = item / kpd, ci = item - dl * kpd;
-  scale += (int64_t)dl * drop_stride;
-  if (alpha_drop) alpha *= alpha_drop[dl];
+  const int64_t dbase = L.idx ? L.val_off[dl] : (int64_t)dl * drop_stride;
+  scale += dbase;
+  if (alpha_drop) alpha *= alpha_drop[L.idx ? L.idx[dl] : dl];
   const int N = 2 * q + 2, P1 = p + 1, Q4 = N >> 2, h = N >> 1;
   float* A = smf32;          // [2][P1]
   float* tc = A + 2 * P1;    // [N]
@@ -182,7 +187,8 @@ __global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, 
     tc[i] = trig32[i];
     ts[i] = trig32[N + i];
   }
-  const double* c = coef + (int64_t)item * coef_stride;
+  const double* c = coef + (L.idx ? (int64_t)kpd * L.coef_off[dl] + (int64_t)ci * coef_stride
+                                   : (int64_t)item * coef_stride);
   const int nt = P1 * (p + 2) / 2;
   const float* T = alf32 + (int64_t)j * nt;
   for (int task = threadIdx.x; task < 2 * P1; task += blockDim.x) {
@@ -199,7 +205,7 @@ __global__ void k_synth32(const double* __restrict__ coef, int64_t coef_stride, 
   const float* Ac = A;
   const float* As = A + P1;
   const float s2 = 1.41421356f;
-  float* out = out32 + (int64_t)dl * drop_stride + (int64_t)ci * item_stride + (int64_t)j * N;
+  float* out = out32 + dbase + (int64_t)ci * item_stride + (int64_t)j * N;
   const double* sc = scale + (int64_t)j * N;
   for (int k = threadIdx.x; k <= Q4; k += blockDim.x) {
     float ce = 0.f, co = 0.f, se = 0.f, so = 0.f;
@@ -245,7 +251,8 @@ int sht_synth_scaled(shbim_ctx* ctx, const GridTables& g, int n_items, const dou
 // factor alpha alpha_drop[d] (alpha_drop may be null).
 int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const double* coef, int64_t coef_stride,
                     double* out, int64_t comp_stride, int64_t drop_stride, const double* scale, double alpha,
-                    const double* alpha_drop, float* out32, cudaStream_t s, float* out32lo) {
+                    const double* alpha_drop, float* out32, cudaStream_t s, float* out32lo, const DropList* L) {
+  const DropList list = L ? *L : DropList{};
   const int n_items = nb * kpd;
   const int64_t item_stride = comp_stride;
   if (n_items <= 0) return SHBIM_OK;
@@ -253,7 +260,8 @@ int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const 
     // only the FP32 copies are read in this mode: FP32 arithmetic
     const size_t smem32 = (size_t)(2 * (g.p + 1) + 2 * (2 * g.q + 2)) * sizeof(float);
     k_synth32<<<dim3(n_items, g.q + 1), 128, smem32, s>>>(coef, coef_stride, g.p, g.q, g.alf32, g.trig32, out32,
-                                                          item_stride, scale, alpha, kpd, drop_stride, alpha_drop);
+                                                          item_stride, scale, alpha, kpd, drop_stride, alpha_drop,
+                                                          list);
     SHBIM_CHECK_LAUNCH(ctx, "k_synth32");
     return SHBIM_OK;
   }
@@ -261,7 +269,8 @@ int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const 
   if (int rc = synth_smem_ok(ctx, smem)) return rc;
   dim3 grid(n_items, g.q + 1);
   k_synth<<<grid, 128, smem, s>>>(coef, coef_stride, g.p, g.q, g.alf, g.trig, 1, out, item_stride,
-                                  0, scale, alpha, out32, out32 ? out32lo : nullptr, kpd, drop_stride, alpha_drop);
+                                  0, scale, alpha, out32, out32 ? out32lo : nullptr, kpd, drop_stride, alpha_drop,
+                                  list);
   SHBIM_CHECK_LAUNCH(ctx, "k_synth");
   return SHBIM_OK;
 }
@@ -269,7 +278,7 @@ int sht_synth_drops(shbim_ctx* ctx, const GridTables& g, int nb, int kpd, const 
 // Fourier stage of the analysis: F[item][j][cs][m] = (omega_j) sum_k v[j][k] (cos|sin)(m phi_k)
 __global__ void k_analysis_fourier(const double* __restrict__ vals, int64_t val_stride, int p, int q,
                                    const double* __restrict__ trig, const double* __restrict__ omega,
-                                   int weighted, double* __restrict__ F) {
+                                   int weighted, double* __restrict__ F, int kpd, DropList L) {
   extern __shared__ double sm[];
   const int item = blockIdx.x;
   const int j = blockIdx.y;
@@ -278,7 +287,8 @@ __global__ void k_analysis_fourier(const double* __restrict__ vals, int64_t val_
   double* row = sm;
   double* tc = row + N;
   double* ts = tc + N;
-  const double* v = vals + (int64_t)item * val_stride + (int64_t)j * N;
+  const int64_t ib = L.idx ? L.val_off[item / kpd] + (int64_t)(item % kpd) * val_stride : (int64_t)item * val_stride;
+  const double* v = vals + ib + (int64_t)j * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     row[i] = v[i];
     tc[i] = trig[i];
@@ -307,7 +317,8 @@ __global__ void k_analysis_fourier(const double* __restrict__ vals, int64_t val_
 // output sums N/4-1 terms instead of N: four times fewer FP64 FMAs than the plain sum.
 __global__ void k_analysis_fourier4(const double* __restrict__ vals, int64_t val_stride, int p, int q,
                                     const double* __restrict__ trig, const double* __restrict__ omega,
-                                    int weighted, int64_t nrows, int rows, double* __restrict__ F) {
+                                    int weighted, int64_t nrows, int rows, double* __restrict__ F, int kpd,
+                                    DropList L) {
   extern __shared__ double sm[];
   const int N = 2 * q + 2;
   const int P1 = p + 1;
@@ -326,7 +337,8 @@ __global__ void k_analysis_fourier4(const double* __restrict__ vals, int64_t val
     const int r = e / N, k = e - r * N;
     const int64_t row = r0 + r;
     const int64_t item = row / (q + 1), j = row - item * (q + 1);
-    R[r * 2 * N + k] = vals[item * val_stride + j * N + k];
+    const int64_t ib = L.idx ? L.val_off[item / kpd] + (item % kpd) * val_stride : item * val_stride;
+    R[r * 2 * N + k] = vals[ib + j * N + k];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * Q4; e += blockDim.x) {
@@ -380,7 +392,7 @@ __global__ void k_analysis_fourier4(const double* __restrict__ vals, int64_t val
 // Legendre stage: coef[item][n^2+n+-m] = s_m sum_j F[item][j][cs][m] Pbar_n^m(t_j)
 __global__ void k_analysis_legendre(const double* __restrict__ F, int p, int q,
                                     const double* __restrict__ alf, double* __restrict__ coef,
-                                    int64_t coef_stride) {
+                                    int64_t coef_stride, int kpd, DropList L) {
   const int item = blockIdx.x;
   const int nt = (p + 1) * (p + 2) / 2;
   const int o = blockIdx.y * blockDim.x + threadIdx.x;
@@ -396,7 +408,8 @@ __global__ void k_analysis_legendre(const double* __restrict__ F, int p, int q,
     ac = fma(Fi[(int64_t)j * 2 * P1 + m], a, ac);
     as = fma(Fi[(int64_t)j * 2 * P1 + P1 + m], a, as);
   }
-  double* c = coef + (int64_t)item * coef_stride;
+  double* c = coef + (L.idx ? (int64_t)kpd * L.coef_off[item / kpd] + (int64_t)(item % kpd) * coef_stride
+                             : (int64_t)item * coef_stride);
   if (m == 0) {
     c[n * n + n] = ac;
   } else {
@@ -408,8 +421,9 @@ __global__ void k_analysis_legendre(const double* __restrict__ F, int p, int q,
 
 int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double* vals,
                  int64_t val_stride, bool weighted, double* coef, int64_t coef_stride,
-                 cudaStream_t s) {
+                 cudaStream_t s, int kpd, const DropList* L) {
   if (n_items <= 0) return SHBIM_OK;
+  const DropList list = L ? *L : DropList{};
   const size_t need = (size_t)n_items * (g.q + 1) * 2 * (g.p + 1);
   if (need > ctx->sht_scratch_elems) {
     // growing scratch: wait for queued users of the old buffer before freeing it
@@ -430,18 +444,18 @@ int sht_analysis(shbim_ctx* ctx, const GridTables& g, int n_items, const double*
     const int64_t nrows = (int64_t)n_items * (g.q + 1);
     const size_t smem = (size_t)(2 * N + rows * 2 * N) * sizeof(double);
     k_analysis_fourier4<<<(unsigned)((nrows + rows - 1) / rows), 128, smem, s>>>(
-        vals, val_stride, g.p, g.q, g.trig, g.omega, weighted ? 1 : 0, nrows, rows, ctx->sht_scratch);
+        vals, val_stride, g.p, g.q, g.trig, g.omega, weighted ? 1 : 0, nrows, rows, ctx->sht_scratch, kpd, list);
     SHBIM_CHECK_LAUNCH(ctx, "k_analysis_fourier4");
   } else {
     dim3 g1(n_items, g.q + 1);
     k_analysis_fourier<<<g1, 64, 3 * N * sizeof(double), s>>>(vals, val_stride, g.p, g.q, g.trig,
                                                               g.omega, weighted ? 1 : 0,
-                                                              ctx->sht_scratch);
+                                                              ctx->sht_scratch, kpd, list);
     SHBIM_CHECK_LAUNCH(ctx, "k_analysis_fourier");
   }
   const int nt = ntri(g.p);
   dim3 g2(n_items, (nt + 127) / 128);
-  k_analysis_legendre<<<g2, 128, 0, s>>>(ctx->sht_scratch, g.p, g.q, g.alf, coef, coef_stride);
+  k_analysis_legendre<<<g2, 128, 0, s>>>(ctx->sht_scratch, g.p, g.q, g.alf, coef, coef_stride, kpd, list);
   SHBIM_CHECK_LAUNCH(ctx, "k_analysis_legendre");
   return SHBIM_OK;
 }
