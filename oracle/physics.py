@@ -133,7 +133,9 @@ class Params:
     beta: float = 0.2
     x_s: float = 0.5
     E_u: tuple = (0.0, 0.0, 1.0)
-    E_q: float = 0.0            # linear field E_q (x, -y, 0) added to the uniform one
+    E_q: float = 0.0            # strength of the linear field E_q G x added to the uniform one
+    E_G: tuple = ((1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.0, 0.0, 0.0))   # its shape G (symmetric,
+    # traceless); the quadrupole field of Section 3, phi = -E_q r^2 P_2, is diag(-1, -1, 2)
     gmres_tol: float = 1e-12
     Pe: float = math.inf        # surfactant Peclet number (infinity: no diffusion)
 
@@ -154,7 +156,7 @@ def electric_traction(En, Et, n, R: float, Q: float):
 
 def far_field(x, prm: Params):
     Eu = np.asarray(prm.E_u, dtype=np.float64)[:, None]
-    return Eu + prm.E_q * np.stack([x[0], -x[1], np.zeros_like(x[2])])
+    return Eu + prm.E_q * (np.asarray(prm.E_G, dtype=np.float64) @ x)
 
 
 def rates(xcoefs, gcoefs, ps, lams, prm: Params, info=None, near: bool = True):

@@ -179,3 +179,32 @@ def test_surfactant_drop_steady_deformation_follows_second_order_theory():
     assert abs(D - D2) < abs(D - D1) / 3
     assert abs(D - D2) < 0.005 * abs(D2)
     assert abs(P.surfactant_mass(x, g, p) - m0) / m0 < 1e-4
+
+
+def _random_field_shape(rng):
+    """A random symmetric traceless 3 x 3 matrix (the shape of a harmonic linear field)."""
+    A = rng.standard_normal((3, 3))
+    G = A + A.T
+    return G - np.trace(G) / 3.0 * np.eye(3)
+
+
+@pytest.mark.parametrize("R", [0.5, 2.0])
+def test_electric_solution_unit_sphere_linear_field(R):
+    """The far field E_q G x (G symmetric, traceless) is the gradient of the degree-2 harmonic
+    E_q x.Gx / 2. On the unit sphere the interior/exterior solution of Section 1 (continuity of the
+    potential, R times the interior normal field equal to the exterior one) gives for a degree-l field
+    E_n = l (2l+1) R / (R l + l + 1) times the far-field potential's surface harmonic, i.e. for l = 2
+    E_n = 5R/(2R+3) n.Gn; with G = diag(-1, -1, 2) (the quadrupole of Section 3) this is
+    10R/(2R+3) P_2(cos theta)."""
+    p = 6
+    rng = np.random.default_rng(7)
+    for G in (np.diag([-1.0, -1.0, 2.0]), _random_field_shape(rng)):
+        prm = P.Params(R=R, Q=1.0, Ca_E=0.1, beta=0.0, E_u=(0.0, 0.0, 0.0), E_q=0.7, E_G=tuple(map(tuple, G)),
+                       gmres_tol=1e-13)
+        info = {}
+        P.rates([inputs.sphere_coef(p)], [np.zeros(sh.ncoef(p))], [p], [1.0], prm, info=info)
+        En = sh.sht_inverse(info["En"][0], p, p)
+        th, ph = sh.grid_points(p)
+        n = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+        expect = 0.7 * 5 * R / (2 * R + 3) * (n * (G @ n)).sum(axis=0)
+        np.testing.assert_allclose(En, expect, atol=1e-12)
