@@ -216,10 +216,11 @@ def run_own(args):
         legs = {"pairs_at_scale": lambda: pairs_at_scale(S, torch, dev),
                 "peaks": lambda: pipe_peaks(S),
                 "learned": lambda: learned_warm_start(S, torch, dev, p=args.learned_p, n_train=args.learned_train,
-                                                      n_test=args.learned_test),
+                                                      n_test=args.learned_test, epochs=args.learned_epochs),
                 "config2": lambda: config2_leg(S, torch, dev),
                 "config3_fp64": lambda: time_to_solution_c3(S, torch, dev, fp64_full=True),
-                "config5": lambda: config5_leg(S, torch, dev)}
+                "config5": lambda: config5_leg(S, torch, dev),
+                "apps_config2": lambda: apps_config2(S, torch, dev)}
         print(json.dumps({args.only: legs[args.only]()}))
         return
 
@@ -319,11 +320,22 @@ def run_own(args):
     ms_e2e, apps_e2e = cuda_time(torch, e2e_run)
     e2e_value = apps_e2e * P / (ms_e2e / 1e3)
 
+    # reparametrisation after an accepted step (Section 2.2): 20 flow steps of the positions and the
+    # concentration on the same layout, timed on its own (not part of the step above)
+    xr, gr = x.clone(), g.clone()
+    l0 = ctx.launch_count()
+    ms_rep, e_rep = cuda_time(torch, lambda: ctx.reparametrize(xr, gr, steps=20, a=4.0, c=0.5))
+    rep = {"flow_steps": 20, "a": 4.0, "c": 0.5, "ms": ms_rep, "ms_per_flow_step": ms_rep / 20,
+           "launches": ctx.launch_count() - l0, "energy_ratio": e_rep[-1] / e_rep[0],
+           "note": "shbim_reparametrize on the step's layout (positions and surfactant), FP64"}
+
     peaks = pipe_peaks(S)
     roof = roofline(cls_ms, cls_n, cls_work, cfg, peaks)
     tts = time_to_solution_c3(S, torch, dev, fp64_full=args.fp64_full, ctx=ctx, cfg=cfg)
     apps_c3 = applications_by_kind(S, torch, dev, ctx, with_fp64=not args.no_fp64_apps)
     c2 = config2_leg(S, torch, dev) if not args.no_config2 else None
+    learned = None if args.no_learned else learned_warm_start(S, torch, dev, p=args.learned_p, n_train=args.learned_train,
+                                                              n_test=args.learned_test, epochs=args.learned_epochs)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -349,6 +361,8 @@ def run_own(args):
         "time_to_1e-8": tts,
         "applications": apps_c3,
         "config2": c2,
+        "learned_warm_start": learned,
+        "reparametrization": rep,
         "roofline": roof,
         "pipe_peaks_measured": peaks,
         "clocks": clk,
@@ -498,6 +512,19 @@ def config2_leg(S, torch, dev, steps=5):
     return res
 
 
+def apps_config2(S, torch, dev):
+    """One application of each kernel kind (Laplace DL, SL, Stokes D, S) in FP32, double-float and FP64 on
+    the two-drop workload (p = 32, gap 0.1): a short program of a few hundred launches, for profiling
+    single kernels."""
+    cfg = inputs.config2(p=32, seed=0, gap=0.1)
+    ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8)
+    x, _ = upload(torch, dev, cfg)
+    ctx.set_drops([d.p for d in cfg.drops], x, [d.lam for d in cfg.drops])
+    res = applications_by_kind(S, torch, dev, ctx, with_fp64=True)
+    ctx.close()
+    return res
+
+
 def config5_leg(S, torch, dev):
     """16 drops of degree 64 in the quadrupole field (x, -y, 0), Pe = 10: geometry build, one mixed
     precision IMEX step (Algorithm 1) and the time to 1e-8, mixed vs FP64."""
@@ -560,58 +587,72 @@ def pairs_at_scale(S, torch, dev, reps: int = 10):
     return res
 
 
-def learned_warm_start(S, torch, dev, p: int = 8, n_train: int = 600, n_test: int = 16):
-    """The learned warm start at the given scale (two-drop inputs of degree p; the network and its training
-    run in the library's kernels): on held-out seeds, the electric solve to an FP64-class residual of
-    1e-8 from zero, from the sphere solution and from sphere + network -- iterations, initial residual
-    and time (CUDA events)."""
+def learned_warm_start(S, torch, dev, p: int = 32, n_train: int = 1000, n_test: int = 16, epochs: int = 60):
+    """The learned warm start (config-4 style: two drops of degree p; the features, the network and its training
+    run in the library's kernels). Trained on the method's own solutions of n_train seeds; on n_test held-out
+    seeds the electric solve (field right-hand side) and the Stokes solve (right-hand side from the converged
+    E_n, shbim_stokes_rhs) are timed to a 1e-8 residual checked in FP64-class arithmetic: mixed precision from
+    zero, mixed precision from the network's guess (features and inference included), and plain FP64 GMRES
+    from zero."""
     from paper_1811_10270_gb300 import warmstart
     t0 = time.perf_counter()
-    X, Y, _ = warmstart.generate(inputs.config2(p=p, seed=sd, gap=0.1) for sd in range(1, n_train + 1))
+    X, Y, its0 = warmstart.generate(inputs.config2(p=p, seed=sd, gap=0.1) for sd in range(1, n_train + 1))
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    net, hist = warmstart.train(X, Y, hidden=(512, 512, 512), epochs=150, batch=32, lr=1e-3)
+    net, hist = warmstart.train(X, Y, hidden=(512, 512, 512), epochs=epochs, batch=32, lr=1e-3)
     t_train = time.perf_counter() - t0
-    names = ("zero", "sphere", "learned")
-    it = {k: [] for k in names}
-    r0 = {k: [] for k in names}
-    ms = {k: 0.0 for k in names}
+    kinds = ("zero", "learned", "fp64")
+    ms = {sysn: {k: [] for k in kinds} for sysn in ("electric", "stokes")}
+    its = {sysn: {k: [] for k in kinds} for sysn in ("electric", "stokes")}
+    r0 = {"electric": [], "stokes": []}
     for sd in range(100000, 100000 + n_test):
         cfg = inputs.config2(p=p, seed=sd, gap=0.1)
-        ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8)
-        x, _ = upload(torch, dev, cfg)
-        ctx.set_drops([p, p], x, [d.lam for d in cfg.drops])
+        x, g = upload(torch, dev, cfg)
         nc = x.numel() // 3
-        rhs = torch.empty(nc, device=dev, dtype=torch.float64)
-        ctx.electric_rhs(cfg.E_u, rhs)
-        sol = torch.empty_like(rhs)
-        ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs, sol)       # warm the graphs of this geometry
-        for k in names:
-            def run():
-                x0 = None
-                if k == "sphere":
-                    x0 = 3.0 * (cfg.R + 1) / (cfg.R + 2) * rhs
-                elif k == "learned":
-                    x0 = torch.empty_like(rhs)
-                    S.electric_warm_start(ctx, net, x, rhs, x0)
-                return x0, ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs, sol, x0=x0)
-            t, (x0, (inner, outer, res)) = cuda_time(torch, run)
-            ms[k] += t
-            it[k].append(inner)
-            if x0 is None:
-                r0[k].append(1.0)
-            else:
-                Lx = torch.empty_like(rhs)
-                ctx.eval_electric(S.LAPLACE_DL, x0, Lx, S.OUT_COEF)
-                r = rhs - (0.5 * x0 - (cfg.R - 1) / (cfg.R + 1) * Lx)
-                r0[k].append(float(torch.linalg.norm(r) / torch.linalg.norm(rhs)))
+        ph = warmstart.phys_of(cfg)
+        ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8)
+        ctx.set_drops([p, p], x, [d.lam for d in cfg.drops])
+        rhs_e = torch.empty(nc, device=dev, dtype=torch.float64)
+        ctx.electric_rhs(cfg.E_u, rhs_e)
+        feat = torch.empty(ctx.warm_start_feature_count(), device=dev, dtype=torch.float32)
+        En0 = torch.empty_like(rhs_e)
+        u0 = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+        En = torch.empty_like(rhs_e)
+        ctx.gmres_solve_refined(S.SYS_ELECTRIC, rhs_e, En)          # graphs of this geometry; E_n for the Stokes rhs
+        rhs_s = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+        ctx.stokes_rhs(ph, g, En, rhs_s)
+        u = torch.empty_like(rhs_s)
+        ctx.gmres_solve_refined(S.SYS_STOKES, rhs_s, u)
+        for sysn, sysk, rhs, sol, guess in (("electric", S.SYS_ELECTRIC, rhs_e, En, En0),
+                                           ("stokes", S.SYS_STOKES, rhs_s, u, u0)):
+            for k in kinds:
+                def run():
+                    if k == "fp64":
+                        ctx.set_precision(S.FP64)
+                        it, _ = ctx.gmres_solve(sysk, rhs, sol)
+                        ctx.set_precision(S.FP32_COMP)
+                        return it
+                    x0 = None
+                    if k == "learned":
+                        ctx.warm_start_features(x, g, ph, feat)
+                        ctx.learned_guess(net, feat, rhs_e, En0, u0)
+                        x0 = guess
+                    inner, outer, _ = ctx.gmres_solve_refined(sysk, rhs, sol, x0=x0)
+                    return inner
+                t, it = cuda_time(torch, run)
+                ms[sysn][k].append(t)
+                its[sysn][k].append(it)
+            r0[sysn].append(float(torch.linalg.norm(guess - sol) / torch.linalg.norm(sol)))
         ctx.close()
     net.close()
-    return {"scale": "p=%d two-drop inputs, %d training solves, %d held out" % (p, n_train, n_test),
-            "train_s": t_train, "generate_s": t_gen, "final_loss_ratio": hist[-1] / hist[0],
-            "mean_inner_iters": {k: float(np.mean(v)) for k, v in it.items()},
-            "mean_initial_resid": {k: float(np.mean(v)) for k, v in r0.items()},
-            "mean_ms_to_1e-8": {k: v / n_test for k, v in ms.items()}}
+    return {"scale": "p=%d two-drop inputs (config-2 style), %d training solves, %d held out, %d epochs"
+                     % (p, n_train, n_test, epochs),
+            "generate_s": t_gen, "train_s": t_train, "final_loss_ratio": hist[-1] / hist[0],
+            "mean_ms_to_1e-8": {s_: {k: float(np.mean(v)) for k, v in d.items()} for s_, d in ms.items()},
+            "mean_iterations": {s_: {k: float(np.mean(v)) for k, v in d.items()} for s_, d in its.items()},
+            "mean_guess_rel_error": {s_: float(np.mean(v)) for s_, v in r0.items()},
+            "note": "zero and learned: mixed precision (FP32 inner GMRES, double-float residuals), iterations are "
+                    "inner Arnoldi steps; fp64: plain FP64 GMRES from zero; learned includes features and inference"}
 
 
 # outer iterations per probe: about 50 ms each on a GB300
@@ -677,12 +718,10 @@ def oracle_sample():
 def cpu_baseline():
     """The oracle on its sample (oracle_sample) with all host cores available to its BLAS calls and with
     one thread, as pairs/s of one application of the batched workload (extrapolated)."""
-    from threadpoolctl import threadpool_limits
     cfg = batched_workload()
     P = pairs_per_application(cfg)
     t_all, info_all = oracle_sample()
-    with threadpool_limits(limits=1):
-        t_one, info_one = oracle_sample()
+    t_one, info_one = oracle_sample_one_thread()
     cores = threads_used()
     return {"value": P / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "FP64 numpy oracle, Laplace double layer of the batched workload: one drop per degree, "
@@ -691,6 +730,20 @@ def cpu_baseline():
                       "%.0f s on 1 thread" % (P, t_all, cores, t_one),
             "extrapolated_application_s": {"all_cores": t_all, "one_core": t_one},
             "value_one_core": P / t_one, "measured": {"all_cores": info_all, "one_core": info_one}}
+
+
+def oracle_sample_one_thread():
+    """oracle_sample in a child interpreter whose BLAS pools are limited to one thread (the limit has to be
+    set before numpy loads its BLAS)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = "import json, bench; t, info = bench.oracle_sample(); print(json.dumps([t, info]))"
+    r = subprocess.run([sys.executable, "-c", code], cwd=os.path.dirname(os.path.abspath(__file__)), env=env,
+                       capture_output=True, text=True, check=True)
+    t, info = json.loads(r.stdout.strip().splitlines()[-1])
+    return t, info
 
 
 def threads_used():
@@ -745,10 +798,13 @@ def main():
     ap.add_argument("--no-config2", action="store_true", help="skip the two-drop leg")
     ap.add_argument("--no-fp64-apps", action="store_true", help="skip the FP64 single applications")
     ap.add_argument("--fp64-full", action="store_true", help="time the FP64 Stokes solve in full (minutes)")
-    ap.add_argument("--learned-p", type=int, default=8, help="degree of the learned warm-start leg")
-    ap.add_argument("--learned-train", type=int, default=600, help="training solves of the learned leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start leg")
+    ap.add_argument("--learned-p", type=int, default=32, help="degree of the learned warm-start leg")
+    ap.add_argument("--learned-train", type=int, default=1000, help="training solves of the learned leg")
     ap.add_argument("--learned-test", type=int, default=16, help="held-out solves of the learned leg")
-    ap.add_argument("--only", choices=["pairs_at_scale", "peaks", "learned", "config2", "config3_fp64", "config5"],
+    ap.add_argument("--learned-epochs", type=int, default=60, help="training epochs of the learned leg")
+    ap.add_argument("--only", choices=["pairs_at_scale", "peaks", "learned", "config2", "config3_fp64", "config5",
+                                       "apps_config2"],
                     help="run one measurement leg alone and print its JSON")
     ap.add_argument("--serial", action="store_true",
                     help="operator applications on the caller's stream alone (no side-stream branches)")

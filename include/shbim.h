@@ -150,10 +150,18 @@ int shbim_sizes(shbim_ctx* ctx, int64_t* ncoef, int64_t* ntarget, int64_t* nsour
  * out [x..][y..][z..][nx..][ny..][nz..][J..] (7 * ntarget doubles in out_dev). */
 int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream);
 
+/* Shape of the linear part of the far field (Section 1, Eq. potential): E_inf(x) = E_u + E_q G x with
+ * G a symmetric, traceless 3 x 3 matrix (row-major, 9 doubles read from the host), so that E_inf is
+ * the gradient of a harmonic potential. The paper's quadrupole field, phi_inf = -E_q r^2 P_2(cos theta),
+ * is G = diag(-1, -1, 2), i.e. E_inf = E_q (-x, -y, 2z) (Section 3); the default is diag(1, -1, 0),
+ * the planar field E_q (x, -y, 0). SHBIM_ERR_ARG for a non-finite, non-symmetric or non-traceless G
+ * (relative tolerance 1e-12). Applies to shbim_electric_rhs, shbim_rates and shbim_step. */
+int shbim_set_field_shape(shbim_ctx* ctx, const double* G_host);
+
 /* Right-hand side of the electric system (Eq. galerkin_En): Galerkin coefficients of
- * R/(R+1) E_inf . n on every drop, for the far field E_inf(x) = E_u + E_q (x, -y, 0)
- * (a uniform part E_u, a 3-vector read from the host, plus a linear field of strength E_q;
- * the paper's uniform and quadrupole fields are both of this form up to orientation).
+ * R/(R+1) E_inf . n on every drop, for the far field E_inf(x) = E_u + E_q G x
+ * (a uniform part E_u, a 3-vector read from the host, plus a linear field of strength E_q whose
+ * shape G is the context's, shbim_set_field_shape).
  *   out_dev   ncoef coefficients */
 int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, double* out_dev,
                        void* stream);
@@ -208,6 +216,15 @@ int shbim_eval_stokes(shbim_ctx* ctx, const double* f_dev, const double* u_dev, 
  *   relative residual ||b - A x|| / ||b|| in *resid_host. */
 int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
                       void* stream);
+/* Convergence control of shbim_gmres_solve (and of the solves inside shbim_gmres_solve_refined,
+ * shbim_rates and shbim_step) on the device (on by default, with CUDA graphs on): after the first
+ * Arnoldi step, each GMRES cycle is one CUDA graph whose conditional 'while' node repeats the Arnoldi
+ * step -- operator application, classical Gram-Schmidt twice, normalisation, Givens rotation and the
+ * residual test, all in kernels -- until the residual estimate reaches the tolerance, the Krylov space is
+ * full or gmres_maxiter steps were taken; the least-squares update of x follows in the same graph. The
+ * host synchronises once per cycle instead of once per step. Off, or where the graph cannot be built:
+ * every step on the host as shbim_gmres_step. Both give the same iterates up to rounding. */
+int shbim_set_device_gmres(shbim_ctx* ctx, int on);
 int shbim_gmres_step(shbim_ctx* ctx, double* resid_host, void* stream);
 int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* stream);
 int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
@@ -217,7 +234,8 @@ int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
  * E_n is solved with R; the traction uses Q and R (Eq. el_force, eps = 1); the capillary
  * force is scaled by 1/Ca_E (Eq. main_eq); the tension follows the Langmuir law normalised so
  * that gamma(1) = 1, gamma = (1 + beta ln(1 - x_s Gamma)) / (1 + beta ln(1 - x_s))
- * (Eq. langmuir; beta = 0 is a clean drop). The far field is E_u + E_q (x, -y, 0).
+ * (Eq. langmuir; beta = 0 is a clean drop). The far field is E_u + E_q G x, G the context's field
+ * shape (shbim_set_field_shape).
  * inner_tol is the FP32 inner tolerance of the refined solves used when the context's
  * precision is SHBIM_PREC_FP32_COMP (otherwise plain FP64 GMRES). */
 typedef struct shbim_phys {
@@ -241,6 +259,15 @@ typedef struct shbim_phys {
  * Synchronises `stream` (GMRES reads residuals back). */
 int shbim_rates(shbim_ctx* ctx, const shbim_phys* phys, const double* gamma_dev, double* u_dev,
                 double* gE_dev, int* iters_host, void* stream);
+
+/* Right-hand side of the Stokes system for given E_n coefficients (steps ii-v of Section 1):
+ * the charge potential phi_q = S_L[(1 - 1/R) E_n], E_t = -grad_S(phi_inf + phi_q), the electric and
+ * interfacial tractions (Eqs. el_force, interfacial_force, langmuir) on each drop's degree 2p+1 grid
+ * (projected to degree p) and rhs = -sum_j S_j[f/Ca_E - f^E] (Eq. main_eq) -- what shbim_rates solves
+ * the Stokes system with. The one-shot applications use the context's precision (in FP32_COMP mode its
+ * one-shot precision). gamma_dev, En_dev: ncoef coefficients; rhs_dev: 3 ncoef (out). */
+int shbim_stokes_rhs(shbim_ctx* ctx, const shbim_phys* phys, const double* gamma_dev, const double* En_dev,
+                     double* rhs_dev, void* stream);
 
 /* Surface Laplacian Delta_S (Laplace-Beltrami operator, the diffusion term of Eq. surfactant0)
  * of a scalar on every drop of the current shapes, in Galerkin form:
@@ -270,6 +297,26 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* phys, const double* x_dev, cons
                double dt, double* x_out_dev, double* gamma_out_dev, double* err_host, int* iters_host,
                void* stream);
 
+/* Reparametrisation of the drop surfaces (Section 2.2: applied after every accepted step of
+ * Algorithm 1 to keep the spherical-harmonic representation resolved). The paper builds it on an
+ * optimisation of the node distribution and does not restate it; this library takes `steps` explicit
+ * steps of the tangential gradient flow of the spectral energy E = sum_{n>=1,m} n^a |x_nm|^2 (three
+ * components), each on every drop's degree 2p+1 grid:
+ *   h = sum n^a x_nm S_nm,  t = h - (h . n) n,  x <- x - tau t,  tau = c / p^a,
+ * projected back to degree p by the regular rule; the nodes move along the surface, which stays in
+ * place to first order in tau per step. The surfactant concentration moves with the nodes:
+ *   Gamma <- Gamma - tau grad_S Gamma . t   (then projected to degree p).
+ *   steps       number of flow steps, 0..100000 (0: only the energy is computed)
+ *   a           energy exponent, 0 <= a <= 8 (4 is usual);  c  step factor, 0 < c <= 1 (stable range)
+ *   x_dev       3 ncoef position coefficients in the context's layout (device, in/out)
+ *   gamma_dev   ncoef concentration coefficients (device, in/out) or NULL; must not overlap x_dev
+ *   energy_host steps+1 doubles (host, out) or NULL: E before the first and after every step
+ * Works in FP64 on the drop layout of shbim_set_drops and leaves the context's geometry as it was
+ * (the next shbim_set_drops or shbim_step takes the new positions). SHBIM_ERR_ARG for arguments
+ * outside these ranges or no drops set. Synchronises `stream`. */
+int shbim_reparametrize(shbim_ctx* ctx, int steps, double a, double c, double* x_dev, double* gamma_dev,
+                        double* energy_host, void* stream);
+
 /* FP64-class arithmetic used where mixed precision needs it: the residuals of
  * shbim_gmres_solve_refined in SHBIM_PREC_FP32_COMP mode. SHBIM_PREC_DF64 (default: double-float on
  * the FP32 pipe) or SHBIM_PREC_FP64 (native); SHBIM_ERR_ARG otherwise. */
@@ -289,10 +336,12 @@ int shbim_set_oneshot_precision(shbim_ctx* ctx, int precision);
  * and updates x += d, until the FP64-class relative residual reaches gmres_tol or max_outer steps
  * were taken (SHBIM_ERR_NOT_CONVERGED). The inner relative tolerance is inner_tol (e.g. 1e-5),
  * except where the step can finish the solve: then it is 0.5 gmres_tol / (current relative
- * residual), looser than inner_tol on the last step, and down to inner_tol / 20 after a good
- * initial guess. From a zero start the first inner solve aims at 0.5 gmres_tol at once (one
- * FP64-class residual per solve) for as long as that has succeeded for the system on this context;
- * after the first miss the system's later solves use the two-step form. The outer residuals use the
+ * residual), looser than inner_tol on the last step. The first inner solve aims at 0.5 gmres_tol at
+ * once (one FP64-class residual per solve) for as long as that has succeeded for the system on this
+ * context; after the first miss the system's later solves use the two-step form. With an initial guess
+ * x0 the first residual b - A x0 is formed with the FP32 operator (the first inner solve cannot get
+ * below the FP32 operator's accuracy anyway), so a guess adds no FP64-class residual: the solve takes
+ * as many of them as from a zero start, and fewer inner steps when the guess is good. The outer residuals use the
  * context's outer precision (shbim_set_outer_precision).
  * Only the electric and Stokes systems (the diffusion system has no all-pairs sums;
  * SHBIM_ERR_ARG). The context's precision setting is restored on return. Reports the total inner Arnoldi
@@ -357,6 +406,26 @@ int shbim_mlp_train_step(shbim_mlp* net, int batch, const float* x_dev, const fl
                          int update, double* loss_host, void* stream);
 int shbim_electric_warm_start(shbim_ctx* ctx, shbim_mlp* net, const double* xcoef_dev,
                               const double* rhs_dev, double* x0_dev, void* stream);
+
+/* Learned initial guesses for both solves of shbim_rates (an extension of the method: the network only
+ * proposes, GMRES solves to its tolerance from there).
+ * shbim_warm_start_features: the network's input for the current drop set, FP32, laid out
+ *   [position coefficients, 3 ncoef][Gamma coefficients, ncoef][E_u (3), E_q][lambda per drop][R, Q, Ca_E],
+ *   shbim_warm_start_feature_count(ctx) = 4 ncoef + 7 + n_drops values (-1 without drops).
+ * shbim_learned_guess: y = net(features) with 4 ncoef outputs; writes the electric guess
+ *   E_n0 = 3(R+1)/(R+2) rhs_e + y[0, ncoef) (the sphere solution 3R/(R+2) E.n through the right-hand side
+ *   plus the learned correction) to En0_dev and the velocity guess u0 = y[ncoef, 4 ncoef) to u0_dev;
+ *   either output may be NULL (rhs_e_dev is needed only for E_n0). SHBIM_ERR_ARG if the network's widths
+ *   do not match.
+ * shbim_set_warm_start: a network that shbim_rates and shbim_step use for these guesses (NULL: none;
+ *   the context does not own it). In the mixed-precision solves a guess costs no extra FP64-class
+ *   residual while the system's FP32 operator allows finishing in one step (shbim_gmres_solve_refined). */
+int64_t shbim_warm_start_feature_count(shbim_ctx* ctx);
+int shbim_warm_start_features(shbim_ctx* ctx, const double* xcoef_dev, const double* gamma_dev,
+                              const shbim_phys* phys, float* feat_dev, void* stream);
+int shbim_learned_guess(shbim_ctx* ctx, shbim_mlp* net, const float* feat_dev, const double* rhs_e_dev,
+                        double* En0_dev, double* u0_dev, void* stream);
+int shbim_set_warm_start(shbim_ctx* ctx, shbim_mlp* net);
 
 /* Number of kernel launches the library has queued since the context was created. */
 int64_t shbim_launch_count(shbim_ctx* ctx);

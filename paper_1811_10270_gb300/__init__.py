@@ -48,7 +48,9 @@ EXPORTS = [
     "shbim_set_autotune", "shbim_pair_shape", "shbim_set_pair_shape", "shbim_probe_peak",
     "shbim_set_outer_precision", "shbim_set_rows_precision", "shbim_set_tensor_cores",
     "shbim_near_min_distance", "shbim_set_wait_limit", "shbim_check_wait", "shbim_set_self_precision", "shbim_set_oneshot_precision",
-    "shbim_kernel_work",
+    "shbim_kernel_work", "shbim_warm_start_feature_count", "shbim_warm_start_features", "shbim_learned_guess",
+    "shbim_set_warm_start", "shbim_stokes_rhs", "shbim_set_device_gmres", "shbim_reparametrize",
+    "shbim_set_field_shape",
 ]
 PROBE_FFMA = 0
 PROBE_DFMA = 1
@@ -161,6 +163,14 @@ def lib():
         "shbim_set_self_precision": (i32, [vp, i32]),
         "shbim_set_oneshot_precision": (i32, [vp, i32]),
         "shbim_kernel_work": (i32, [vp, i32, P(dp)]),
+        "shbim_warm_start_feature_count": (i64, [vp]),
+        "shbim_warm_start_features": (i32, [vp, vp, vp, P(Phys), vp, vp]),
+        "shbim_learned_guess": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "shbim_set_warm_start": (i32, [vp, vp]),
+        "shbim_stokes_rhs": (i32, [vp, P(Phys), vp, vp, vp, vp]),
+        "shbim_set_device_gmres": (i32, [vp, i32]),
+        "shbim_reparametrize": (i32, [vp, i32, dp, dp, vp, vp, P(dp), vp]),
+        "shbim_set_field_shape": (i32, [vp, P(dp)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -350,9 +360,31 @@ class Context:
                     "shbim_step")
         return err.value, list(it)
 
+    def reparametrize(self, x, gamma=None, steps: int = 20, a: float = 4.0, c: float = 0.5):
+        """shbim_reparametrize: `steps` tangential flow steps on x (3 ncoef, in place) and gamma (ncoef, in place,
+        or None); returns the energies before the first and after every step."""
+        e = (ctypes.c_double * (int(steps) + 1))()
+        self._check(self._L.shbim_reparametrize(self._h, int(steps), float(a), float(c), _ptr(x),
+                                                None if gamma is None else _ptr(gamma), e, _stream()),
+                    "shbim_reparametrize")
+        return list(e)
+
+    def stokes_rhs(self, ph, gamma, En, out):
+        """shbim_stokes_rhs: -sum_j S_j[f/Ca_E - f^E] for the given E_n (3 ncoef coefficients into out)."""
+        self._check(self._L.shbim_stokes_rhs(self._h, ctypes.byref(ph), _ptr(gamma), _ptr(En), _ptr(out), _stream()),
+                    "shbim_stokes_rhs")
+
     def laplace_beltrami(self, coef, out):
         self._check(self._L.shbim_laplace_beltrami(self._h, _ptr(coef), _ptr(out), _stream()),
                     "shbim_laplace_beltrami")
+
+    def set_field_shape(self, G):
+        """shbim_set_field_shape: E_inf = E_u + E_q G x (G symmetric and traceless, 3 x 3)."""
+        rows = [list(r) for r in G]
+        if len(rows) != 3 or any(len(r) != 3 for r in rows):
+            raise ValueError("field shape must be 3 x 3")
+        g = (ctypes.c_double * 9)(*[float(v) for r in rows for v in r])
+        self._check(self._L.shbim_set_field_shape(self._h, g), "shbim_set_field_shape")
 
     def set_diffusion(self, c: float):
         self._check(self._L.shbim_set_diffusion(self._h, float(c)), "shbim_set_diffusion")
@@ -401,6 +433,9 @@ class Context:
     def set_pair_queue(self, kind: int, on: bool):
         self._check(self._L.shbim_set_pair_queue(self._h, int(kind), 1 if on else 0), "shbim_set_pair_queue")
 
+    def set_device_gmres(self, on: bool):
+        self._check(self._L.shbim_set_device_gmres(self._h, 1 if on else 0), "shbim_set_device_gmres")
+
     def set_graphs(self, on: bool):
         self._check(self._L.shbim_set_graphs(self._h, 1 if on else 0), "shbim_set_graphs")
 
@@ -425,6 +460,22 @@ class Context:
     def check_wait(self, arrive: bool) -> int:
         """shbim_check_wait: returns the library's status code (0, or SHBIM_ERR_TIMEOUT = -5)."""
         return int(self._L.shbim_check_wait(self._h, 1 if arrive else 0, _stream()))
+
+    def warm_start_feature_count(self) -> int:
+        return int(self._L.shbim_warm_start_feature_count(self._h))
+
+    def warm_start_features(self, xcoef, gamma, ph, feat):
+        """shbim_warm_start_features into a CUDA float32 tensor of warm_start_feature_count() values."""
+        self._check(self._L.shbim_warm_start_features(self._h, _ptr(xcoef), _ptr(gamma), ctypes.byref(ph),
+                                                      _ptr32(feat), _stream()), "shbim_warm_start_features")
+
+    def learned_guess(self, net, feat, rhs_e=None, En0=None, u0=None):
+        self._check(self._L.shbim_learned_guess(self._h, net._h, _ptr32(feat), _ptr(rhs_e), _ptr(En0), _ptr(u0),
+                                                _stream()), "shbim_learned_guess")
+
+    def set_warm_start(self, net):
+        """Network used by rates() and step() for the initial guesses of both solves (None: none)."""
+        self._check(self._L.shbim_set_warm_start(self._h, None if net is None else net._h), "shbim_set_warm_start")
 
     def near_pairs(self) -> int:
         return int(self._L.shbim_near_pairs(self._h))

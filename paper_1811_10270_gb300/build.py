@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libshbim.so")
-SOURCES = ["tables.cu", "sht.cu", "singular.cu", "pairs.cu", "api.cu", "gmres.cu", "physics.cu", "near.cu", "mlp.cu", "noalloc.cu", "peaks.cu", "singular_df.cu", "dft_tc.cu", "rot_tc.cu", "leg_tc.cu"]
+SOURCES = ["tables.cu", "sht.cu", "singular.cu", "pairs.cu", "api.cu", "gmres.cu", "physics.cu", "near.cu", "mlp.cu", "noalloc.cu", "peaks.cu", "singular_df.cu", "dft_tc.cu", "rot_tc.cu", "leg_tc.cu", "reparam.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

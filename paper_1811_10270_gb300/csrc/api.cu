@@ -25,6 +25,7 @@ int pairs_tile_targets();
 int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
   SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
   ctx->geom_version++;  // invalidates captured operator graphs
+  ctx->xcoef_cur = xcoef_dev;
   for (auto& d : ctx->drops) {
     double c00[3];
     for (int c = 0; c < 3; ++c)
@@ -171,6 +172,11 @@ int shbim_destroy(shbim_ctx* ctx) {
     cudaFree(g.in);
     cudaFree(g.out);
   }
+  for (auto& c : ctx->cycles)
+    if (c.exec) cudaGraphExecDestroy(c.exec);
+  cudaFree(ctx->gm.dstate);
+  cudaFree(ctx->gm.istate);
+  cudaFree(ctx->gm.vstage);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   cudaFree(ctx->pair_queue);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -181,6 +187,9 @@ int shbim_destroy(shbim_ctx* ctx) {
   cudaFree(ctx->phys.grid);
   cudaFree(ctx->phys.state);
   cudaFree(ctx->phys.lb);
+  cudaFree(ctx->phys.feat);
+  cudaFree(ctx->phys.guess);
+  cudaFree(ctx->phys.rep);
   cudaFree(ctx->dens_split);
   for (auto& L : ctx->lanes) {
     cudaFree(L.rot);
@@ -729,13 +738,21 @@ TimeScope::~TimeScope() {
 }
 
 namespace {
+struct FieldShape {
+  double g[6];   // xx, xy, xz, yy, yz, zz
+};
+
+// scale (E_u + eq G x) . n on every target
 __global__ void k_field_normal(const double* __restrict__ tgt, int64_t ntarget, double ex, double ey,
-                               double ez, double eq, double scale, double* __restrict__ out) {
+                               double ez, double eq, FieldShape G, double scale, double* __restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntarget) return;
-  const double x = tgt[t], y = tgt[ntarget + t];
+  const double x = tgt[t], y = tgt[ntarget + t], z = tgt[2 * ntarget + t];
   const double nx = tgt[3 * ntarget + t], ny = tgt[4 * ntarget + t], nz = tgt[5 * ntarget + t];
-  out[t] = scale * ((ex + eq * x) * nx + (ey - eq * y) * ny + ez * nz);
+  const double Ex = ex + eq * (G.g[0] * x + G.g[1] * y + G.g[2] * z);
+  const double Ey = ey + eq * (G.g[1] * x + G.g[3] * y + G.g[4] * z);
+  const double Ez = ez + eq * (G.g[2] * x + G.g[4] * y + G.g[5] * z);
+  out[t] = scale * (Ex * nx + Ey * ny + Ez * nz);
 }
 }  // namespace
 
@@ -794,14 +811,36 @@ int shbim_kernel_work(shbim_ctx* ctx, int cls, double* flops) {
   return SHBIM_OK;
 }
 
+int shbim_set_field_shape(shbim_ctx* ctx, const double* G_host) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (!G_host) return fail(ctx, SHBIM_ERR_ARG, "null field shape");
+  double mx = 0.0;
+  for (int k = 0; k < 9; ++k) {
+    if (!std::isfinite(G_host[k])) return fail(ctx, SHBIM_ERR_ARG, "field shape not finite");
+    mx = std::max(mx, std::fabs(G_host[k]));
+  }
+  const double tol = 1e-12 * mx;
+  if (std::fabs(G_host[1] - G_host[3]) > tol || std::fabs(G_host[2] - G_host[6]) > tol ||
+      std::fabs(G_host[5] - G_host[7]) > tol)
+    return fail(ctx, SHBIM_ERR_ARG, "field shape not symmetric (the far field must be curl-free)");
+  if (std::fabs(G_host[0] + G_host[4] + G_host[8]) > tol)
+    return fail(ctx, SHBIM_ERR_ARG, "field shape not traceless (the far field must be divergence-free)");
+  const double g[6] = {G_host[0], 0.5 * (G_host[1] + G_host[3]), 0.5 * (G_host[2] + G_host[6]), G_host[4],
+                       0.5 * (G_host[5] + G_host[7]), G_host[8]};
+  std::memcpy(ctx->field_g, g, sizeof(g));
+  return SHBIM_OK;
+}
+
 int shbim_electric_rhs(shbim_ctx* ctx, const double* E_u_host, double E_q, double* out_dev, void* stream) {
   if (!ctx) return SHBIM_ERR_ARG;
   if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
   if (!E_u_host || !out_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
   cudaStream_t s = (cudaStream_t)stream;
   const double R = ctx->opts.R;
+  FieldShape G;
+  std::memcpy(G.g, ctx->field_g, sizeof(G.g));
   k_field_normal<<<(unsigned)((ctx->ntarget + 255) / 256), 256, 0, s>>>(
-      ctx->geo.tgt, ctx->ntarget, E_u_host[0], E_u_host[1], E_u_host[2], E_q, R / (R + 1.0), ctx->grid_out);
+      ctx->geo.tgt, ctx->ntarget, E_u_host[0], E_u_host[1], E_u_host[2], E_q, G, R / (R + 1.0), ctx->grid_out);
   SHBIM_CHECK_LAUNCH(ctx, "k_field_normal");
   for (const DegreeGroup& G : ctx->groups) {
     const DropList L = G.targets();

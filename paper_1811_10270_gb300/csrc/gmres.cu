@@ -138,6 +138,133 @@ __global__ void k_div(double* __restrict__ y, const double* __restrict__ a, cons
 
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// ---- GMRES cycles on the device (the state of a cycle lives in device memory; every kernel reads the
+// Arnoldi index k from it, so one captured graph serves every step of a cycle)
+struct DevCycle {
+  double* H;    // (m+1) x m, column-major: column k at k (m+1)
+  double* cs;   // m
+  double* sn;   // m
+  double* g;    // m+1
+  double* y;    // m
+  double* sc;   // 0 residual estimate, 1 ||b||, 2 tolerance, 3 beta
+  int* is;      // 0 k, 1 total Arnoldi steps, 2 flags (bit 0: non-finite), 3 step budget
+  int m;
+};
+
+DevCycle dev_cycle(double* dstate, int* istate, int m) {
+  DevCycle C;
+  C.H = dstate;
+  C.cs = C.H + (size_t)(m + 1) * m;
+  C.sn = C.cs + m;
+  C.g = C.sn + m;
+  C.y = C.g + m + 1;
+  C.sc = C.y + m;
+  C.is = istate;
+  C.m = m;
+  return C;
+}
+
+size_t dev_cycle_doubles(int m) { return (size_t)(m + 1) * m + 3 * (size_t)m + (m + 1) + 8; }
+
+__device__ __forceinline__ unsigned cycle_go(const DevCycle& C) {
+  return (C.is[2] == 0 && C.sc[0] > C.sc[2] && C.is[0] < C.m && C.is[1] < C.is[3]) ? 1u : 0u;
+}
+
+__global__ void k_cycle_cond(cudaGraphConditionalHandle h, DevCycle C) { cudaGraphSetConditional(h, cycle_go(C)); }
+
+__global__ void k_stage_vk(const double* __restrict__ V, int64_t n, const int* __restrict__ is, double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = V[(int64_t)is[0] * n + e];
+}
+
+// h[i] = V_i . w for i <= k (one block per vector; blocks past k return)
+__global__ void k_dots_k(const double* __restrict__ V, int64_t n, const double* __restrict__ w,
+                         double* __restrict__ h, const int* __restrict__ is) {
+  if ((int)blockIdx.x > is[0]) return;
+  const double* v = V + (int64_t)blockIdx.x * n;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(v[e], w[e], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) h[blockIdx.x] = acc;
+}
+
+__global__ void k_orth_update_k(double* __restrict__ w, const double* __restrict__ V, int64_t n,
+                                const double* __restrict__ h, double* __restrict__ hacc, int first,
+                                const int* __restrict__ is) {
+  const int nvec = is[0] + 1;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e == 0) {
+    for (int i = 0; i < nvec; ++i) hacc[i] = first ? h[i] : hacc[i] + h[i];
+  }
+  if (e >= n) return;
+  double acc = w[e];
+  for (int i = 0; i < nvec; ++i) acc = fma(-h[i], V[(int64_t)i * n + e], acc);
+  w[e] = acc;
+}
+
+__global__ void k_norm2_k(const double* __restrict__ w, int64_t n, double* __restrict__ hacc, const int* __restrict__ is) {
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc = fma(w[e], w[e], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) hacc[is[0] + 1] = acc;
+}
+
+__global__ void k_normalize_k(const double* __restrict__ w, const double* __restrict__ hacc, double* __restrict__ V,
+                              int64_t n, const int* __restrict__ is) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double nr = hacc[is[0] + 1];
+  const double sc = nr > 0.0 ? 1.0 / sqrt(nr) : 0.0;
+  V[(int64_t)(is[0] + 1) * n + e] = w[e] * sc;
+}
+
+// the new Hessenberg column, its Givens rotation, the residual estimate and the loop condition
+__global__ void k_givens(cudaGraphConditionalHandle h, DevCycle C, const double* __restrict__ hacc) {
+  const int k = C.is[0], ld = C.m + 1;
+  double* Hc = C.H + (size_t)k * ld;
+  for (int i = 0; i <= k; ++i) Hc[i] = hacc[i];
+  Hc[k + 1] = sqrt(fmax(0.0, hacc[k + 1]));
+  bool finite = true;
+  for (int i = 0; i <= k + 1; ++i) finite = finite && isfinite(Hc[i]);
+  for (int i = 0; i < k; ++i) {
+    const double a = Hc[i], b = Hc[i + 1];
+    Hc[i] = C.cs[i] * a + C.sn[i] * b;
+    Hc[i + 1] = -C.sn[i] * a + C.cs[i] * b;
+  }
+  const double den = hypot(Hc[k], Hc[k + 1]);
+  C.cs[k] = den > 0.0 ? Hc[k] / den : 1.0;
+  C.sn[k] = den > 0.0 ? Hc[k + 1] / den : 0.0;
+  Hc[k] = den;
+  Hc[k + 1] = 0.0;
+  C.g[k + 1] = -C.sn[k] * C.g[k];
+  C.g[k] = C.cs[k] * C.g[k];
+  C.is[0] = k + 1;
+  C.is[1] += 1;
+  C.sc[0] = C.sc[1] > 0.0 ? fabs(C.g[k + 1]) / C.sc[1] : 0.0;
+  if (!finite || !isfinite(C.sc[0])) C.is[2] |= 1;
+  cudaGraphSetConditional(h, cycle_go(C));
+}
+
+// y = R^{-1} g for the current k
+__global__ void k_backsolve(DevCycle C) {
+  const int k = C.is[0], ld = C.m + 1;
+  for (int i = k - 1; i >= 0; --i) {
+    double acc = C.g[i];
+    for (int c = i + 1; c < k; ++c) acc -= C.H[(size_t)c * ld + i] * C.y[c];
+    C.y[i] = acc / C.H[(size_t)i * ld + i];
+  }
+}
+
+__global__ void k_xupdate_k(double* __restrict__ x, const double* __restrict__ V, const double* __restrict__ y,
+                            const int* __restrict__ is, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int k = is[0];
+  double acc = x[e];
+  for (int i = 0; i < k; ++i) acc = fma(y[i], V[(int64_t)i * n + e], acc);
+  x[e] = acc;
+}
+
 inline int64_t system_size(const shbim_ctx* ctx, int sys) {
   return sys == SHBIM_SYS_STOKES ? 3 * ctx->ncoef : ctx->ncoef;
 }
@@ -260,6 +387,156 @@ int start_cycle(shbim_ctx* ctx, bool x_is_zero, cudaStream_t s) {
   return SHBIM_OK;
 }
 
+// Build (or reuse) the graph of one device cycle of the current system at the context's precision:
+// a kernel that sets the loop condition, the conditional 'while' node whose body is one Arnoldi step
+// (stage V_k, operator application, two Gram-Schmidt passes, norm, normalisation, Givens rotation and
+// the convergence test that sets the condition), then the back substitution and the update of x.
+// Returns false (and marks the slot) if the graph cannot be built; the caller then steps on the host.
+bool cycle_graph(shbim_ctx* ctx, cudaStream_t s) {
+  auto& G = ctx->gm;
+  auto& CG = ctx->cycles[G.sys * 3 + ctx->opts.precision];
+  if (CG.failed) return false;
+  if (CG.exec && CG.version == ctx->geom_version && CG.n == G.n && CG.m == G.m) return true;
+  if (CG.exec) cudaGraphExecDestroy(CG.exec);
+  CG.exec = nullptr;
+  // the operator's workspaces must exist before capture: one eager application per slot and geometry
+  auto& GR = ctx->graphs[G.sys * 3 + ctx->opts.precision];
+  if (GR.version != ctx->geom_version || !GR.warm) return false;
+  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    CG.failed = true;
+    return false;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+  const DevCycle C = dev_cycle(G.dstate, G.istate, G.m);
+  const int64_t n = G.n;
+  double* hacc = hacc_ptr(ctx);
+  double* htmp = G.h;
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle handle;
+  cudaGraphNode_t pre = nullptr, cond = nullptr;
+  size_t nn = 1;
+  const int64_t l0 = ctx->launches, a0 = ctx->applications;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&handle, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  // the condition for the first step
+  ok = ok && cudaStreamBeginCaptureToGraph(ctx->cap_stream, graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    k_cycle_cond<<<1, 1, 0, ctx->cap_stream>>>(handle, C);
+    ok = cudaStreamEndCapture(ctx->cap_stream, &graph) == cudaSuccess;
+  }
+  ok = ok && cudaGraphGetNodes(graph, &pre, &nn) == cudaSuccess && nn == 1;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  ok = ok && cudaGraphAddNode(&cond, graph, &pre, nullptr, 1, &cp) == cudaSuccess;
+  int64_t body_kernels = 0;
+  if (ok) {
+    // the body: one Arnoldi step
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      cudaStream_t cs = ctx->cap_stream;
+      const int64_t b0 = ctx->launches;
+      k_stage_vk<<<nb(n), 256, 0, cs>>>(G.V, n, G.istate, G.vstage);
+      int rc = matvec_eager(ctx, G.vstage, G.w, cs);
+      for (int pass = 0; pass < 2 && rc == SHBIM_OK; ++pass) {
+        k_dots_k<<<G.m + 1, 256, 0, cs>>>(G.V, n, G.w, htmp, G.istate);
+        k_orth_update_k<<<nb(n), 256, 0, cs>>>(G.w, G.V, n, htmp, hacc, pass == 0, G.istate);
+      }
+      k_norm2_k<<<1, 256, 0, cs>>>(G.w, n, hacc, G.istate);
+      k_normalize_k<<<nb(n), 256, 0, cs>>>(G.w, hacc, G.V, n, G.istate);
+      k_givens<<<1, 1, 0, cs>>>(handle, C, hacc);
+      body_kernels = ctx->launches - b0 + 8;
+      cudaGraph_t b2 = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(cs, &b2);
+      ok = rc == SHBIM_OK && e == cudaSuccess;
+    }
+  }
+  // back substitution and the update of x after the loop
+  ok = ok && cudaStreamBeginCaptureToGraph(ctx->cap_stream, graph, &cond, nullptr, 1,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    k_backsolve<<<1, 1, 0, ctx->cap_stream>>>(C);
+    k_xupdate_k<<<nb(n), 256, 0, ctx->cap_stream>>>(G.x, G.V, C.y, G.istate, n);
+    ok = cudaStreamEndCapture(ctx->cap_stream, &graph) == cudaSuccess;
+  }
+  ok = ok && cudaGraphInstantiate(&CG.exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  ctx->launches = l0;
+  ctx->applications = a0;
+  if (!ok) {
+    if (CG.exec) cudaGraphExecDestroy(CG.exec);
+    CG.exec = nullptr;
+    CG.failed = true;
+    cudaGetLastError();
+    return false;
+  }
+  CG.version = ctx->geom_version;
+  CG.n = G.n;
+  CG.m = G.m;
+  CG.body_kernels = body_kernels;
+  return true;
+}
+
+// Run the current solve's remaining steps as device cycles, from whatever state the host holds (the
+// Hessenberg columns, rotations and g of the cycle so far are copied to the device first). *done = true
+// when the solve converged; false when the graph is unavailable (nothing changed: the caller steps on
+// the host).
+int device_cycles(shbim_ctx* ctx, cudaStream_t s, bool* done) {
+  auto& G = ctx->gm;
+  *done = false;
+  if (G.resid <= ctx->opts.gmres_tol) {
+    *done = true;
+    return SHBIM_OK;
+  }
+  if (!cycle_graph(ctx, s)) return SHBIM_OK;
+  auto& CG = ctx->cycles[G.sys * 3 + ctx->opts.precision];
+  const DevCycle C = dev_cycle(G.dstate, G.istate, G.m);
+  double* sc_h = G.h_host + 2 * (G.m + 2);
+  int* is_h = reinterpret_cast<int*>(sc_h + 4);
+  for (;;) {
+    // the host's state of the current cycle
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(C.H, G.H.data(), G.H.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(C.cs, G.cs.data(), G.m * sizeof(double), cudaMemcpyHostToDevice, s));
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(C.sn, G.sn.data(), G.m * sizeof(double), cudaMemcpyHostToDevice, s));
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(C.g, G.g.data(), (G.m + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+    sc_h[0] = G.resid;
+    sc_h[1] = G.bnorm;
+    sc_h[2] = ctx->opts.gmres_tol;
+    sc_h[3] = G.g[0];
+    is_h[0] = G.k;
+    is_h[1] = G.total;
+    is_h[2] = 0;
+    is_h[3] = ctx->opts.gmres_maxiter;
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(C.sc, sc_h, 4 * sizeof(double), cudaMemcpyHostToDevice, s));
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(C.is, is_h, 4 * sizeof(int), cudaMemcpyHostToDevice, s));
+    SHBIM_CUDA(ctx, cudaGraphLaunch(CG.exec, s));
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(is_h, C.is, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    SHBIM_CUDA(ctx, cudaMemcpyAsync(sc_h, C.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+    const int steps = is_h[1] - G.total;
+    G.total = is_h[1];
+    G.resid = sc_h[0];
+    G.k = 0;  // the graph has already added V y to x
+    ctx->launches += 3 + (int64_t)steps * CG.body_kernels;
+    if (G.sys != SHBIM_SYS_DIFFUSION) ctx->applications += steps;
+    if (is_h[2] & 1) return fail(ctx, SHBIM_ERR_NONFINITE, "non-finite Arnoldi column");
+    if (G.resid <= ctx->opts.gmres_tol) break;
+    if (G.total >= ctx->opts.gmres_maxiter)
+      return fail(ctx, SHBIM_ERR_NOT_CONVERGED, "GMRES reached its iteration limit");
+    // Krylov space full: restart from the true residual
+    int rc = start_cycle(ctx, false, s);
+    if (rc) return rc;
+    if (G.resid <= ctx->opts.gmres_tol) break;
+  }
+  *done = true;
+  return SHBIM_OK;
+}
+
 // y = R^{-1} g for the rotated Hessenberg matrix of the current cycle, x += V y
 int update_x(shbim_ctx* ctx, cudaStream_t s) {
   auto& G = ctx->gm;
@@ -302,9 +579,10 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
   if (n * (m + 1) > G.cap || m != G.m || !G.V) {
     SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
     cudaFree(G.V); cudaFree(G.w); cudaFree(G.x); cudaFree(G.b); cudaFree(G.h); cudaFree(G.Av);
-    cudaFree(G.diag); cudaFree(G.tmp); cudaFree(G.y);
+    cudaFree(G.diag); cudaFree(G.tmp); cudaFree(G.y); cudaFree(G.dstate); cudaFree(G.istate); cudaFree(G.vstage);
     if (G.h_host) cudaFreeHost(G.h_host);
-    G.V = G.w = G.x = G.b = G.h = G.Av = G.diag = G.tmp = G.y = G.h_host = nullptr;
+    G.V = G.w = G.x = G.b = G.h = G.Av = G.diag = G.tmp = G.y = G.h_host = G.dstate = G.vstage = nullptr;
+    G.istate = nullptr;
     const int64_t ncap = std::max<int64_t>(n, 3 * ctx->ncoef);
     if (cudaMalloc(&G.V, (size_t)ncap * (m + 1) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.w, ncap * sizeof(double)) != cudaSuccess ||
@@ -315,7 +593,10 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
         cudaMalloc(&G.tmp, ncap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.y, (m + 2) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&G.h, 2 * (m + 2) * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&G.h_host, 2 * (m + 2) * sizeof(double)) != cudaSuccess)
+        cudaMalloc(&G.dstate, dev_cycle_doubles(m) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G.istate, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&G.vstage, ncap * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&G.h_host, (2 * (m + 2) + 8) * sizeof(double)) != cudaSuccess)
       return fail(ctx, SHBIM_ERR_NOMEM, "GMRES workspace allocation failed");
     G.cap = ncap * (m + 1);
     G.m = m;
@@ -448,7 +729,16 @@ int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
                       int* iters_host, double* resid_host, void* stream) {
   int rc = shbim_gmres_begin(ctx, sys, rhs_dev, x0_dev, stream);
   if (rc) return rc;
-  for (;;) {
+  bool done = false;
+  if (ctx->graphs_on && ctx->device_gmres) {
+    // the first step on the host warms the operator's graph slot (workspaces, captured application);
+    // the rest of the solve runs as device cycles
+    rc = shbim_gmres_step(ctx, nullptr, stream);
+    if (rc == SHBIM_CONVERGED) done = true;
+    else if (rc != SHBIM_CONTINUE) return rc;
+    if (!done && (rc = device_cycles(ctx, (cudaStream_t)stream, &done))) return rc;
+  }
+  while (!done) {
     rc = shbim_gmres_step(ctx, nullptr, stream);
     if (rc == SHBIM_CONVERGED) break;
     if (rc != SHBIM_CONTINUE) return rc;
@@ -479,6 +769,12 @@ int shbim_set_outer_precision(shbim_ctx* ctx, int precision) {
   if (precision != SHBIM_PREC_FP64 && precision != SHBIM_PREC_DF64)
     return fail(ctx, SHBIM_ERR_ARG, "outer precision must be SHBIM_PREC_FP64 or SHBIM_PREC_DF64");
   ctx->outer_prec = precision;
+  return SHBIM_OK;
+}
+
+int shbim_set_device_gmres(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->device_gmres = on != 0;
   return SHBIM_OK;
 }
 
@@ -557,7 +853,13 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
       // x = 0: the residual is b itself, no operator application needed
       SHBIM_CUDA(ctx, cudaMemcpyAsync(G.rr, rhs_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     } else {
+      // the first residual of an initial guess is formed in FP32: the first inner solve only has to
+      // bring the residual down to the FP32 operator's accuracy, and the FP64-class residuals that
+      // follow are the same as from a zero start (one for a system that finishes in one step, two
+      // otherwise)
+      if (outer == 0) ctx->opts.precision = SHBIM_PREC_FP32_COMP;
       rc = system_matvec(ctx, G.xr, G.w, s);
+      ctx->opts.precision = ctx->outer_prec;
       if (rc) break;
       k_sub<<<nb(n), 256, 0, s>>>(rhs_dev, G.w, G.rr, n);
       SHBIM_CHECK_LAUNCH(ctx, "k_sub");
@@ -573,24 +875,22 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
       break;
     }
     if (outer == 1 && attempted_direct && rel > tol) ctx->refine_direct[sys] = false;
-    if (rel <= tol) break;
+    // an FP32 first residual (see above) cannot end the solve: only an FP64-class one can
+    if (rel <= tol && !(outer == 0 && x0_dev)) break;
     if (outer >= max_outer) {
       rc = fail(ctx, SHBIM_ERR_NOT_CONVERGED, "refinement reached max_outer");
       break;
     }
     // inner solve A d = r with FP32 sums. The tolerance that would finish in this step is
     // 0.5 tol / rel: when it is looser than inner_tol (typically the last step) it is used as is;
-    // when it is tighter but within a factor 20 (a good initial guess) it is used too, so the solve
-    // ends one outer step earlier; otherwise the step reduces the residual by inner_tol. From a zero
-    // start the first step also aims straight at the end (one FP64-class residual instead of two)
-    // while this system's FP32 operator has been accurate enough for that; the first time the
-    // FP64-class check after such a step misses the tolerance, later solves of the system go back
-    // to the two-step form.
+    // otherwise the step reduces the residual by inner_tol. The first inner solve (from a zero start
+    // or from an initial guess) aims straight at the end (one FP64-class residual instead of two) while
+    // this system's FP32 operator has been accurate enough for that; the first time the FP64-class
+    // check after such a step misses the tolerance, later solves of the system go back to the
+    // two-step form.
     const double need = 0.5 * tol / rel;
-    const bool direct = outer == 0 && !x0_dev && ctx->refine_direct[sys];
-    const double tau = direct ? need
-                              : need >= inner_tol ? std::min(need, 0.5)
-                                                  : (need >= 0.05 * inner_tol ? need : inner_tol);
+    const bool direct = outer == 0 && ctx->refine_direct[sys];
+    const double tau = direct ? std::min(need, 0.5) : (need >= inner_tol ? std::min(need, 0.5) : inner_tol);
     attempted_direct = direct;
     ctx->opts.precision = SHBIM_PREC_FP32_COMP;
     ctx->opts.gmres_tol = tau;

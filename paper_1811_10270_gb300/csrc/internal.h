@@ -197,7 +197,12 @@ struct shbim_ctx {
   int rows_prec = SHBIM_PREC_DF64;   // arithmetic of the singular-row build (FP64 or double-float)
   int self_prec = SHBIM_PREC_DF64;   // self-row application in FP32 mode: both planes (double-float) or hi only
   int oneshot_prec = SHBIM_PREC_DF64;  // one-shot applications of shbim_rates in FP32 mode
+  // shape G of the linear part of the far field E_u + E_q G x (symmetric, traceless):
+  // xx, xy, xz, yy, yz, zz
+  double field_g[6] = {1.0, 0.0, 0.0, -1.0, 0.0, 0.0};
   bool refine_direct[2] = {true, true};     // refined solves (electric, Stokes): first inner solve aims at the end
+  shbim_mlp* warm_net = nullptr;  // learned initial guesses of shbim_rates (shbim_set_warm_start), not owned
+  const double* xcoef_cur = nullptr;  // position coefficients of the current geometry (during a rates call)
   bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
   bool tc_rot = true;             // ... and the degree-block rotations (rot_tc.cu)
   bool tc_leg = false;            // ... and the Legendre stage of the analysis (leg_tc.cu; opt-in)
@@ -236,6 +241,9 @@ struct shbim_ctx {
     double* rr = nullptr;       // [n] refinement: outer residual
     double* dr = nullptr;       // [n] refinement: correction
     double* tmp = nullptr;      // [n] diffusion system: preconditioned vector M^{-1} v
+    double* dstate = nullptr;   // device cycle state: H [(m+1) m], cs [m], sn [m], g [m+1], y [m], scalars [8]
+    int* istate = nullptr;      // device cycle state: k, total, flags, spare
+    double* vstage = nullptr;   // [n] operator input staged for the device cycle
     std::vector<double> H;      // (m+1) x m, column-major k*(m+1)+i
     std::vector<double> cs, sn, g;
     int k = 0;                  // Arnoldi steps in the current cycle
@@ -287,6 +295,12 @@ struct shbim_ctx {
     size_t state_cap = 0;
     double* lb = nullptr;       // surface Laplacian workspace [6][nsource]
     size_t lb_cap = 0;
+    float* feat = nullptr;      // learned warm start: features [feature count]
+    size_t feat_cap = 0;
+    double* guess = nullptr;    // learned warm start: E_n and u guesses [4 ncoef]
+    size_t guess_cap = 0;
+    double* rep = nullptr;      // reparametrisation workspace
+    size_t rep_cap = 0;
   } phys;
   int64_t launches = 0;
   int64_t applications = 0;
@@ -309,6 +323,20 @@ struct shbim_ctx {
     int64_t kernels = 0;   // kernel nodes per replay
     bool warm = false;
   } graphs[9];                    // [system][precision]
+  // GMRES cycles run on the device: one graph per (system, precision, geometry) whose conditional
+  // 'while' node repeats an Arnoldi step -- operator application, two classical Gram-Schmidt passes,
+  // normalisation, Givens rotation and the convergence test, all in kernels -- until the residual
+  // estimate reaches the tolerance, the Krylov space is full or the step budget is spent; then the
+  // least-squares solution and the update of x. The host reads the state back once per cycle.
+  struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t version = -1;
+    int64_t n = 0;
+    int m = 0;
+    int64_t body_kernels = 0;     // kernel launches per Arnoldi step
+    bool failed = false;          // building failed once: host-driven steps for this slot
+  } cycles[9];
+  bool device_gmres = true;       // shbim_gmres_solve runs its cycles as device graphs
   double diff_c = 0.0;            // coefficient of the diffusion system
   // optional per-class kernel timing
   bool timing = false;

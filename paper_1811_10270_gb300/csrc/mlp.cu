@@ -237,6 +237,33 @@ __global__ void k_warm(const float* __restrict__ y, const double* __restrict__ r
 
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// the scalar tail of the warm-start features: E_u (3), E_q, lambda per drop, R, Q, Ca_E
+__global__ void k_feature_tail(float* __restrict__ f, double e0, double e1, double e2, double eq,
+                               const double* __restrict__ lamm1, int n_drops, double R, double Q, double ca) {
+  const int i = threadIdx.x;
+  if (i == 0) {
+    f[0] = (float)e0;
+    f[1] = (float)e1;
+    f[2] = (float)e2;
+    f[3] = (float)eq;
+    f[4 + n_drops] = (float)R;
+    f[5 + n_drops] = (float)Q;
+    f[6 + n_drops] = (float)ca;
+  }
+  for (int d = i; d < n_drops; d += blockDim.x) f[4 + d] = (float)(lamm1[d] + 1.0);
+}
+
+__global__ void k_guess(const float* __restrict__ y, const double* __restrict__ rhs, double c, double* __restrict__ En0,
+                        double* __restrict__ u0, int64_t nc) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 4 * nc) return;
+  if (e < nc) {
+    if (En0) En0[e] = c * rhs[e] + (double)y[e];
+  } else if (u0) {
+    u0[e - nc] = (double)y[e];
+  }
+}
+
 __global__ void k_affine(const float* __restrict__ x, const float* __restrict__ shift, const float* __restrict__ scale,
                          int64_t n, int w, float* __restrict__ out) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -254,13 +281,65 @@ const float* input_of(shbim_mlp* net, int B, const float* x, cudaStream_t s) {
   return net->xin;
 }
 
+// Inference of a few rows (B <= 4), where a layer is a matrix-vector product bound by reading the
+// weights once from HBM: y[b][n] = act(sum_k bf16(x[b][k]) W[n][k] + bias[n]), the same function as
+// the tensor-core forward (inputs rounded to bfloat16, products exact in FP32, FP32 sums). The rows
+// of x sit in shared memory; two warps per output split K and read W's row coalesced.
+constexpr int kGemvRows = 4;
+constexpr int kGemvOut = 4;            // outputs per CTA (8 warps)
+__global__ void __launch_bounds__(256)
+k_gemv_bf16(int B, int N, int K, const float* __restrict__ x, const __nv_bfloat16* __restrict__ W,
+            const float* __restrict__ bias, int act, float* __restrict__ y) {
+  extern __shared__ float xs[];        // [B][K] bf16-rounded inputs
+  __shared__ float part[8][kGemvRows];
+  for (int e = threadIdx.x; e < B * K; e += blockDim.x) xs[e] = __bfloat162float(__float2bfloat16_rn(x[e]));
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = blockIdx.x * kGemvOut + (warp >> 1);
+  const int half = (K + 1) / 2;
+  const int k0 = (warp & 1) * half, k1 = min(K, k0 + half);
+  float acc[kGemvRows] = {0.f, 0.f, 0.f, 0.f};
+  if (n < N) {
+    const __nv_bfloat16* w = W + (int64_t)n * K;
+    for (int k = k0 + lane; k < k1; k += 32) {
+      const float wv = __bfloat162float(w[k]);
+#pragma unroll
+      for (int b = 0; b < kGemvRows; ++b)
+        if (b < B) acc[b] = fmaf(wv, xs[b * K + k], acc[b]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < kGemvRows; ++b)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], o);
+  if (lane == 0)
+#pragma unroll
+    for (int b = 0; b < kGemvRows; ++b) part[warp][b] = acc[b];
+  __syncthreads();
+  if (!(warp & 1) && lane < B && n < N) {
+    float v = part[warp][lane] + part[warp + 1][lane] + (bias ? bias[n] : 0.f);
+    if (act) v = tanhf(v);
+    y[(int64_t)lane * N + n] = v;
+  }
+}
+
 int forward(shbim_mlp* net, int B, const float* x, cudaStream_t s) {
   const float* in = x;
   for (int l = 0; l < net->L; ++l) {
     const int K = net->w[l], N = net->w[l + 1];
-    int rc = gemm<float, __nv_bfloat16>(net, B, N, K, in, K, 1, net->Wh[l], 1, K, net->H[l + 1], N, 1, net->b[l],
-                                        l < net->L - 1 ? 1 : 0, s);
-    if (rc) return rc;
+    const size_t smem = (size_t)B * K * sizeof(float);
+    if (B <= kGemvRows && smem <= 200 * 1024) {
+      if (smem > 48 * 1024 &&
+          cudaFuncSetAttribute(k_gemv_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return SHBIM_ERR_CUDA;
+      k_gemv_bf16<<<(unsigned)((N + kGemvOut - 1) / kGemvOut), 256, smem, s>>>(B, N, K, in, net->Wh[l], net->b[l],
+                                                                              l < net->L - 1 ? 1 : 0, net->H[l + 1]);
+      if (cudaGetLastError() != cudaSuccess) return SHBIM_ERR_CUDA;
+    } else {
+      int rc = gemm<float, __nv_bfloat16>(net, B, N, K, in, K, 1, net->Wh[l], 1, K, net->H[l + 1], N, 1, net->b[l],
+                                          l < net->L - 1 ? 1 : 0, s);
+      if (rc) return rc;
+    }
     in = net->H[l + 1];
   }
   return SHBIM_OK;
@@ -445,6 +524,51 @@ int shbim_electric_warm_start(shbim_ctx* ctx, shbim_mlp* n, const double* xcoef_
   // spherical baseline E_n = 3R/(R+2) E.n, i.e. 3(R+1)/(R+2) times the right-hand side
   k_warm<<<nb(ctx->ncoef), 256, 0, s>>>(n->H[n->L], rhs_dev, 3.0 * (R + 1.0) / (R + 2.0), x0_dev, ctx->ncoef);
   SHBIM_CHECK_LAUNCH(ctx, "k_warm");
+  return SHBIM_OK;
+}
+
+int64_t shbim_warm_start_feature_count(shbim_ctx* ctx) {
+  if (!ctx || ctx->n_drops == 0) return -1;
+  return 4 * ctx->ncoef + 7 + ctx->n_drops;
+}
+
+int shbim_warm_start_features(shbim_ctx* ctx, const double* xcoef_dev, const double* gamma_dev,
+                              const shbim_phys* phys, float* feat_dev, void* stream) {
+  if (!ctx || !xcoef_dev || !gamma_dev || !phys || !feat_dev) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nc = ctx->ncoef;
+  k_to_f32<<<nb(3 * nc), 256, 0, s>>>(xcoef_dev, feat_dev, 3 * nc);
+  SHBIM_CHECK_LAUNCH(ctx, "k_to_f32");
+  k_to_f32<<<nb(nc), 256, 0, s>>>(gamma_dev, feat_dev + 3 * nc, nc);
+  SHBIM_CHECK_LAUNCH(ctx, "k_to_f32");
+  k_feature_tail<<<1, 128, 0, s>>>(feat_dev + 4 * nc, phys->E_u[0], phys->E_u[1], phys->E_u[2], phys->E_q,
+                                   ctx->lamm1_dev, ctx->n_drops, phys->R, phys->Q, phys->Ca_E);
+  SHBIM_CHECK_LAUNCH(ctx, "k_feature_tail");
+  return SHBIM_OK;
+}
+
+int shbim_learned_guess(shbim_ctx* ctx, shbim_mlp* n, const float* feat_dev, const double* rhs_e_dev, double* En0_dev,
+                        double* u0_dev, void* stream) {
+  if (!ctx || !n || !feat_dev) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (En0_dev && !rhs_e_dev) return fail(ctx, SHBIM_ERR_ARG, "the electric guess needs the right-hand side");
+  if (n->w[0] != shbim_warm_start_feature_count(ctx) || n->w[n->L] != 4 * ctx->ncoef)
+    return fail(ctx, SHBIM_ERR_ARG, "network widths do not match the warm-start features and 4 ncoef outputs");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = forward(n, 1, input_of(n, 1, feat_dev, s), s);
+  if (rc) return cuda_fail(ctx, cudaGetLastError(), "mlp forward");
+  ctx->launches += 2 * n->L;
+  const double R = ctx->opts.R;
+  k_guess<<<nb(4 * ctx->ncoef), 256, 0, s>>>(n->H[n->L], rhs_e_dev, 3.0 * (R + 1.0) / (R + 2.0), En0_dev, u0_dev,
+                                              ctx->ncoef);
+  SHBIM_CHECK_LAUNCH(ctx, "k_guess");
+  return SHBIM_OK;
+}
+
+int shbim_set_warm_start(shbim_ctx* ctx, shbim_mlp* n) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->warm_net = n;
   return SHBIM_OK;
 }
 

@@ -36,6 +36,7 @@ namespace {
 
 struct PhysDev {
   double R, Q, Ca_E, beta, x_s, eu0, eu1, eu2, eq, lnorm;
+  double g[6];   // field shape (xx, xy, xz, yy, yz, zz): E_inf = E_u + eq G x
 };
 
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -96,7 +97,9 @@ __global__ void k_traction(const double* __restrict__ xup, int64_t ns, const dou
   double gphi[3], gG[3];
   surf_grad(f, pt, pp, gphi);
   surf_grad(f, Gt, Gp, gG);
-  const double Ei[3] = {P.eu0 + P.eq * f.x[0], P.eu1 - P.eq * f.x[1], P.eu2};
+  const double Ei[3] = {P.eu0 + P.eq * (P.g[0] * f.x[0] + P.g[1] * f.x[1] + P.g[2] * f.x[2]),
+                        P.eu1 + P.eq * (P.g[1] * f.x[0] + P.g[3] * f.x[1] + P.g[4] * f.x[2]),
+                        P.eu2 + P.eq * (P.g[2] * f.x[0] + P.g[4] * f.x[1] + P.g[5] * f.x[2])};
   const double Ein = Ei[0] * f.n[0] + Ei[1] * f.n[1] + Ei[2] * f.n[2];
   double Et[3];
 #pragma unroll
@@ -210,32 +213,42 @@ int solve(shbim_ctx* ctx, int sys, const double* rhs, const double* x0, double* 
 
 }  // namespace
 
-// u_guess (may be null): initial guess of the Stokes solve (the other stage's velocity in a time step)
-int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, double* gE, int* it_e,
-          int* it_s, cudaStream_t s, const double* u_guess = nullptr) {
+// Workspace of the rates (W.buf): coefficient vectors, then grid fields on the degree 2p+1 grids.
+struct RatesWork {
+  double *rhs_e, *En, *q, *phi, *tco, *rhs_s, *fl, *tv, *uf, *gv;
+};
+
+int rates_work(shbim_ctx* ctx, RatesWork* w) {
   const int64_t n = ctx->ncoef, NS = ctx->nsource;
   auto& W = ctx->phys;
-  int rc;
   const size_t need = (size_t)(4 * n + 6 * n) + (size_t)(6 + 3 + 6 + 1) * NS;
-  if ((rc = ensure_buf(ctx, &W.buf, &W.cap, need))) return rc;
-  double* rhs_e = W.buf;
-  double* En = rhs_e + n;
-  double* q = En + n;
-  double* phi = q + n;
-  double* tco = phi + n;       // 3n
-  double* rhs_s = tco + 3 * n;  // 3n
-  double* fl = rhs_s + 3 * n;   // 6 NS
-  double* tv = fl + 6 * NS;     // 3 NS
-  double* uf = tv + 3 * NS;     // 6 NS
-  double* gv = uf + 6 * NS;     // NS
+  if (int rc = ensure_buf(ctx, &W.buf, &W.cap, need)) return rc;
+  w->rhs_e = W.buf;
+  w->En = w->rhs_e + n;
+  w->q = w->En + n;
+  w->phi = w->q + n;
+  w->tco = w->phi + n;        // 3n
+  w->rhs_s = w->tco + 3 * n;  // 3n
+  w->fl = w->rhs_s + 3 * n;   // 6 NS: E_n, phi_theta, phi_phi, Gamma, Gamma_theta, Gamma_phi
+  w->tv = w->fl + 6 * NS;     // 3 NS
+  w->uf = w->tv + 3 * NS;     // 6 NS
+  w->gv = w->uf + 6 * NS;     // NS
+  return SHBIM_OK;
+}
+
+// Right-hand side of the Stokes system for a given E_n (steps ii-v of Section 1): the charge potential
+// phi_q = S_L[(1 - 1/R) E_n], E_t = -grad_S(phi_inf + phi_q), the electric and interfacial tractions on
+// every drop's degree 2p+1 grid (products de-aliased by projection to degree p) and
+// rhs = -sum_j S_j[f/Ca_E - f^E]. Leaves Gamma and its derivatives on the grids in the workspace.
+int stokes_rhs(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, const double* En, double* rhs_s,
+               cudaStream_t s) {
+  const int64_t n = ctx->ncoef, NS = ctx->nsource;
+  RatesWork w;
+  int rc;
+  if ((rc = rates_work(ctx, &w))) return rc;
   const double R = ph.R;
-  if (R != ctx->opts.R) ctx->geom_version++;
-  ctx->opts.R = R;
-  // (i) E_n
-  if ((rc = shbim_electric_rhs(ctx, ph.E_u, ph.E_q, rhs_e, s))) return rc;
-  if ((rc = solve(ctx, SHBIM_SYS_ELECTRIC, rhs_e, nullptr, En, ph.inner_tol, it_e, s))) return rc;
   // (ii) phi_q = S_L[(1 - 1/R) E_n]
-  k_lincomb<<<nb(n), 256, 0, s>>>(q, En, 1.0 - 1.0 / R, En, 0.0, n);
+  k_lincomb<<<nb(n), 256, 0, s>>>(w.q, En, 1.0 - 1.0 / R, En, 0.0, n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
   // one-shot applications (not iterated by GMRES): in mixed precision their arithmetic is the
   // context's one-shot precision (FP64-class by default: the single layer of the capillary traction
@@ -245,55 +258,94 @@ int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, 
   const int saved_prec = ctx->opts.precision;
   const int oneshot = saved_prec == SHBIM_PREC_FP32_COMP ? ctx->oneshot_prec : saved_prec;
   ctx->opts.precision = oneshot;
-  rc = shbim_eval_electric(ctx, SHBIM_LAPLACE_SL, q, phi, SHBIM_OUT_COEF, s);
+  rc = shbim_eval_electric(ctx, SHBIM_LAPLACE_SL, w.q, w.phi, SHBIM_OUT_COEF, s);
   ctx->opts.precision = saved_prec;
   if (rc) return rc;
   // (iii)-(v) traction on every drop's upsampled grid, projected to degree p
   PhysDev P{ph.R, ph.Q, ph.Ca_E, ph.beta, ph.x_s, ph.E_u[0], ph.E_u[1], ph.E_u[2], ph.E_q,
             1.0 + ph.beta * std::log(1.0 - ph.x_s)};
+  std::memcpy(P.g, ctx->field_g, sizeof(P.g));
   // fields on every drop's upsampled grid, one launch per degree
   for (const DegreeGroup& G : ctx->groups) {
     const GridTables& g = G.tab->up;
     const DropList L = G.sources();
     const int nc = ncoef(G.tab->p);
-    if ((rc = sht_synth(ctx, g, G.n, En, nc, 1 << 0, fl, 0, NS, nullptr, nullptr, s, 1, &L)) ||
-        (rc = sht_synth(ctx, g, G.n, phi, nc, (1 << 1) | (1 << 6), fl + NS, 0, NS, nullptr, nullptr, s, 1, &L)) ||
-        (rc = sht_synth(ctx, g, G.n, gamma, nc, (1 << 0) | (1 << 1) | (1 << 6), fl + 3 * NS, 0, NS, nullptr, nullptr,
+    if ((rc = sht_synth(ctx, g, G.n, En, nc, 1 << 0, w.fl, 0, NS, nullptr, nullptr, s, 1, &L)) ||
+        (rc = sht_synth(ctx, g, G.n, w.phi, nc, (1 << 1) | (1 << 6), w.fl + NS, 0, NS, nullptr, nullptr, s, 1, &L)) ||
+        (rc = sht_synth(ctx, g, G.n, gamma, nc, (1 << 0) | (1 << 1) | (1 << 6), w.fl + 3 * NS, 0, NS, nullptr, nullptr,
                         s, 1, &L)))
       return rc;
   }
   for (auto& d : ctx->drops) {
     const int64_t o = d.src_off;
-    k_traction<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, fl + o, NS, P, tv + o, NS);
+    k_traction<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, w.fl + o, NS, P, w.tv + o, NS);
     SHBIM_CHECK_LAUNCH(ctx, "k_traction");
   }
   for (const DegreeGroup& G : ctx->groups) {
     const DropList L = G.sources();
-    if ((rc = sht_analysis(ctx, G.tab->up, 3 * G.n, tv, NS, true, tco, ncoef(G.tab->p), s, 3, &L))) return rc;
+    if ((rc = sht_analysis(ctx, G.tab->up, 3 * G.n, w.tv, NS, true, w.tco, ncoef(G.tab->p), s, 3, &L))) return rc;
   }
-  // (vi) Stokes: (lam_i+1) u - sum (lam_j-1) D_j[u] = -sum_j S_j[f/Ca_E - f^E]
+  // (vi) right-hand side of (lam_i+1) u - sum (lam_j-1) D_j[u] = -sum_j S_j[f/Ca_E - f^E]
   ctx->opts.precision = oneshot;
-  rc = shbim_eval_stokes(ctx, tco, nullptr, rhs_s, SHBIM_OUT_COEF, s);
+  rc = shbim_eval_stokes(ctx, w.tco, nullptr, rhs_s, SHBIM_OUT_COEF, s);
   ctx->opts.precision = saved_prec;
   if (rc) return rc;
   k_lincomb<<<nb(3 * n), 256, 0, s>>>(rhs_s, rhs_s, -1.0, rhs_s, 0.0, 3 * n);
   SHBIM_CHECK_LAUNCH(ctx, "k_lincomb");
-  if ((rc = solve(ctx, SHBIM_SYS_STOKES, rhs_s, u_guess, u, ph.inner_tol, it_s, s))) return rc;
+  return SHBIM_OK;
+}
+
+// u_guess (may be null): initial guess of the Stokes solve (the other stage's velocity in a time step)
+int rates(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, double* u, double* gE, int* it_e,
+          int* it_s, cudaStream_t s, const double* u_guess = nullptr) {
+  const int64_t n = ctx->ncoef, NS = ctx->nsource;
+  auto& W = ctx->phys;
+  RatesWork w;
+  int rc;
+  if ((rc = rates_work(ctx, &w))) return rc;
+  const double R = ph.R;
+  if (R != ctx->opts.R) ctx->geom_version++;
+  ctx->opts.R = R;
+  // (i) E_n
+  if ((rc = shbim_electric_rhs(ctx, ph.E_u, ph.E_q, w.rhs_e, s))) return rc;
+  // learned initial guesses of both solves (the network only proposes; GMRES solves to its tolerance)
+  const double* En0 = nullptr;
+  const double* u_net = nullptr;
+  if (ctx->warm_net && ctx->xcoef_cur) {
+    const int64_t nf = shbim_warm_start_feature_count(ctx);
+    if ((size_t)nf > W.feat_cap) {
+      cudaFree(W.feat);
+      W.feat = nullptr;
+      W.feat_cap = 0;
+      if (cudaMalloc(&W.feat, nf * sizeof(float)) != cudaSuccess) return fail(ctx, SHBIM_ERR_NOMEM, "warm-start features");
+      W.feat_cap = nf;
+    }
+    if ((rc = ensure_buf(ctx, &W.guess, &W.guess_cap, 4 * (size_t)n))) return rc;
+    if ((rc = shbim_warm_start_features(ctx, ctx->xcoef_cur, gamma, &ph, W.feat, s)) ||
+        (rc = shbim_learned_guess(ctx, ctx->warm_net, W.feat, w.rhs_e, W.guess, W.guess + n, s)))
+      return rc;
+    En0 = W.guess;
+    u_net = W.guess + n;
+  }
+  if ((rc = solve(ctx, SHBIM_SYS_ELECTRIC, w.rhs_e, En0, w.En, ph.inner_tol, it_e, s))) return rc;
+  // (ii)-(vi) the Stokes right-hand side, then the Stokes solve
+  if ((rc = stokes_rhs(ctx, ph, gamma, w.En, w.rhs_s, s))) return rc;
+  if ((rc = solve(ctx, SHBIM_SYS_STOKES, w.rhs_s, u_guess ? u_guess : u_net, u, ph.inner_tol, it_s, s))) return rc;
   // surfactant rate -Gamma div_S u, projected to degree p
   for (const DegreeGroup& G : ctx->groups) {
     const DropList L = G.sources();
-    if ((rc = sht_synth(ctx, G.tab->up, 3 * G.n, u, ncoef(G.tab->p), (1 << 1) | (1 << 6), uf, 2 * NS, NS, nullptr,
+    if ((rc = sht_synth(ctx, G.tab->up, 3 * G.n, u, ncoef(G.tab->p), (1 << 1) | (1 << 6), w.uf, 2 * NS, NS, nullptr,
                         nullptr, s, 3, &L)))
       return rc;
   }
   for (auto& d : ctx->drops) {
     const int64_t o = d.src_off;
-    k_surf_rate<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, uf + o, NS, fl + 3 * NS + o, gv + o);
+    k_surf_rate<<<nb(d.ns), 256, 0, s>>>(ctx->xup + 3 * kNumTab * o, d.ns, w.uf + o, NS, w.fl + 3 * NS + o, w.gv + o);
     SHBIM_CHECK_LAUNCH(ctx, "k_surf_rate");
   }
   for (const DegreeGroup& G : ctx->groups) {
     const DropList L = G.sources();
-    if ((rc = sht_analysis(ctx, G.tab->up, G.n, gv, 0, true, gE, ncoef(G.tab->p), s, 1, &L))) return rc;
+    if ((rc = sht_analysis(ctx, G.tab->up, G.n, w.gv, 0, true, gE, ncoef(G.tab->p), s, 1, &L))) return rc;
   }
   return SHBIM_OK;
 }
@@ -428,6 +480,18 @@ int shbim_step(shbim_ctx* ctx, const shbim_phys* ph, const double* x_dev, const 
   if (iters_host)
     for (int k = 0; k < 4; ++k) iters_host[k] = its[k];
   return SHBIM_OK;
+}
+
+int shbim_stokes_rhs(shbim_ctx* ctx, const shbim_phys* ph, const double* gamma_dev, const double* En_dev,
+                     double* rhs_dev, void* stream) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (ctx->n_drops == 0) return fail(ctx, SHBIM_ERR_ARG, "no drops set");
+  if (!ph || !gamma_dev || !En_dev || !rhs_dev) return fail(ctx, SHBIM_ERR_ARG, "null pointer");
+  if (!(ph->R > 0.0) || !(ph->Ca_E > 0.0) || ph->beta < 0.0 || !(ph->x_s >= 0.0 && ph->x_s < 1.0))
+    return fail(ctx, SHBIM_ERR_ARG, "bad physical parameters");
+  if (ph->R != ctx->opts.R) ctx->geom_version++;
+  ctx->opts.R = ph->R;
+  return stokes_rhs(ctx, *ph, gamma_dev, En_dev, rhs_dev, (cudaStream_t)stream);
 }
 
 int shbim_laplace_beltrami(shbim_ctx* ctx, const double* coef_dev, double* out_dev, void* stream) {

@@ -1,44 +1,60 @@
-"""Training driver of the learned electric warm start (host orchestration only; every
-product, activation, gradient and optimiser step runs in libshbim's kernels).
+"""Training driver of the learned warm start (host orchestration only; every feature, product,
+activation, gradient and optimiser step runs in libshbim's kernels).
 
 Samples are drop configurations the caller supplies (objects with `drops`, each drop having `p`,
-`xcoef` and `lam`, plus the conductivity ratio `R` and the uniform field `E_u`); each is solved by
-the library's own FP64 GMRES, so the network learns from the method itself.
-Inputs are the position coefficients of both drops; targets are the correction of E_n to the
-sphere solution 3(R+1)/(R+2) rhs. Inputs and targets are standardised for training and the
-standardisation is then attached to the network -- the input part as the network's FP32
-input affine (applied before the first bfloat16 rounding: raw coefficients near 2 would lose
-the 0.05-sized perturbations to bfloat16), the output part folded into the last layer -- so
-that the deployed network maps raw coefficients to the raw correction.
+`xcoef`, `gamma_coef` and `lam`, plus `R`, `Q`, `Ca_E`, `E_u` and `E_quad`), all of one layout. Each is
+solved by the library itself to a tight tolerance, so the network learns from the method: the features
+are the library's warm-start features (positions, surfactant, field, lambda, R, Q, Ca_E); the targets are
+the electric solution's correction to the sphere solution 3(R+1)/(R+2) rhs and the velocity of the
+Stokes solve (shbim_rates), 4 ncoef values. Inputs and targets are standardised for training and the
+standardisation is attached to the network afterwards -- the input part as the network's FP32 input
+affine (applied before the first bfloat16 rounding: raw coefficients near 2 would lose the
+0.05-sized perturbations to bfloat16), the output part folded into the last layer -- so the deployed
+network maps raw features to raw guesses (shbim_learned_guess).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
-from . import FP64, SYS_ELECTRIC, Context, MLP
+from . import FP32_COMP, SYS_ELECTRIC, Context, MLP, phys
+
+
+def phys_of(cfg, inner_tol: float = 1e-5):
+    """The physical parameters of a configuration (Langmuir beta 0.2, x_s 0.5)."""
+    return phys(R=cfg.R, Q=cfg.Q, Ca_E=cfg.Ca_E, beta=0.2, x_s=0.5, E_u=tuple(cfg.E_u), E_q=cfg.E_quad,
+                inner_tol=inner_tol, Pe=math.inf)
 
 
 def generate(configs, tol: float = 1e-10):
-    """(features [n, 3 ncoef], targets [n, ncoef], iterations from zero) for the given drop
-    configurations (all of one layout)."""
+    """(features [n, F], targets [n, 4 ncoef], inner iterations from zero [n, 2]) for the given drop
+    configurations (all of one layout): mixed-precision solves refined to `tol`."""
     import torch
     dev = torch.device("cuda")
     X, Y, its = [], [], []
     ctx = None
     for cfg in configs:
         if ctx is None:
-            ctx = Context(precision=FP64, R=cfg.R, gmres_tol=tol)
-        x = np.concatenate([d.xcoef.ravel() for d in cfg.drops])
-        xd = torch.tensor(x, device=dev)
-        ctx.set_drops([d.p for d in cfg.drops], xd, [d.lam for d in cfg.drops])
-        nc = xd.numel() // 3
+            ctx = Context(precision=FP32_COMP, R=cfg.R, gmres_tol=tol)
+        x = torch.tensor(np.concatenate([d.xcoef.ravel() for d in cfg.drops]), device=dev)
+        g = torch.tensor(np.concatenate([d.gamma_coef for d in cfg.drops]), device=dev)
+        ctx.set_drops([d.p for d in cfg.drops], x, [d.lam for d in cfg.drops])
+        nc = x.numel() // 3
+        ph = phys_of(cfg)
+        feat = torch.empty(ctx.warm_start_feature_count(), device=dev, dtype=torch.float32)
+        ctx.warm_start_features(x, g, ph, feat)
         rhs = torch.empty(nc, device=dev, dtype=torch.float64)
-        ctx.electric_rhs(cfg.E_u, rhs)
-        sol = torch.empty_like(rhs)
-        it, _ = ctx.gmres_solve(SYS_ELECTRIC, rhs, sol)
+        ctx.set_R(cfg.R)
+        ctx.electric_rhs(cfg.E_u, rhs, E_q=cfg.E_quad)
+        En = torch.empty_like(rhs)
+        ctx.gmres_solve_refined(SYS_ELECTRIC, rhs, En)
+        u = torch.empty(3 * nc, device=dev, dtype=torch.float64)
+        gE = torch.empty(nc, device=dev, dtype=torch.float64)
+        it = ctx.rates(ph, g, u, gE)
         c = 3.0 * (cfg.R + 1.0) / (cfg.R + 2.0)
-        X.append(x.astype(np.float32))
-        Y.append((sol - c * rhs).cpu().numpy().astype(np.float32))
+        X.append(feat.cpu().numpy())
+        Y.append(torch.cat([En - c * rhs, u]).cpu().numpy().astype(np.float32))
         its.append(it)
     ctx.close()
     return np.stack(X), np.stack(Y), np.array(its)
@@ -55,12 +71,15 @@ def init_layers(widths, rng: np.random.Generator):
 
 def train(X, Y, hidden=(512, 512, 512), epochs: int = 200, batch: int = 64, lr: float = 1e-3, seed: int = 0):
     """Train on (X, Y); returns (net, history of epoch losses). The returned network takes raw
-    inputs and produces raw targets."""
+    features and produces raw targets. Targets are standardised per output (the electric and velocity
+    blocks have different sizes)."""
     import torch
     dev = torch.device("cuda")
     mu, sd = X.mean(0), X.std(0)
     sd = np.where(sd > 1e-6, sd, 1.0).astype(np.float32)
-    ym, ys = Y.mean(0), float(Y.std()) + 1e-12
+    ym = Y.mean(0)
+    ys = Y.std(0)
+    ys = np.where(ys > 1e-3 * (ys.max() + 1e-30), ys, 1e-3 * (ys.max() + 1e-30)).astype(np.float32)
     Xn = torch.tensor((X - mu) / sd, device=dev)
     Yn = torch.tensor((Y - ym) / ys, device=dev)
     widths = [X.shape[1], *hidden, Y.shape[1]]
@@ -81,5 +100,5 @@ def train(X, Y, hidden=(512, 512, 512), epochs: int = 200, batch: int = 64, lr: 
     L = len(widths) - 1
     net.set_input_affine(mu.astype(np.float32), (1.0 / sd).astype(np.float32))
     WL, bL, _, _ = net.get_layer(L - 1)
-    net.set_layer(L - 1, WL * ys, bL * ys + ym)
+    net.set_layer(L - 1, WL * ys[:, None], bL * ys + ym)
     return net, hist

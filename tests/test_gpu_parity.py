@@ -512,6 +512,45 @@ def test_gmres_restart_and_warm_start(S):
     ctx.close()
 
 
+@pytest.mark.parametrize("restart", [50, 4])
+def test_device_cycles_match_host_steps(S, restart):
+    """GMRES with the convergence control on the device (one graph per cycle, a conditional while node
+    around the Arnoldi step) against every step on the host: the electric, Stokes and diffusion systems,
+    with and without restarts (Krylov dimension 4 forces several cycles); the same number of steps and
+    the same solution up to rounding, and the oracle's solution."""
+    cfg = _two_drop_cfg(6, seed=7, gap=0.3)
+    sysm = oracle_system(cfg.drops)
+    rng = np.random.default_rng(8)
+    nc = sum(sh.ncoef(d.p) for d in cfg.drops)
+    b_e = sysm.electric_rhs(cfg.R, cfg.E_u)
+    b_s = rng.standard_normal(3 * nc)
+    b_d = rng.standard_normal(nc)
+    res = {}
+    for device in (True, False):
+        ctx = S.Context(precision=S.FP64, R=cfg.R, gmres_tol=1e-11, gmres_restart=restart)
+        ctx.set_device_gmres(device)
+        ctx.set_drops([d.p for d in cfg.drops], T(np.concatenate([d.xcoef.ravel() for d in cfg.drops])),
+                      [d.lam for d in cfg.drops])
+        ctx.set_diffusion(0.05)
+        out = {}
+        for name, sys_, b in (("electric", S.SYS_ELECTRIC, b_e), ("stokes", S.SYS_STOKES, b_s),
+                              ("diffusion", S.SYS_DIFFUSION, b_d)):
+            x = torch.empty(b.size, device=DEV, dtype=torch.float64)
+            for rep in range(2):      # the second solve reuses the cycle graph of the first
+                it, r = ctx.gmres_solve(sys_, T(b), x)
+                assert r < 1e-10, (device, name, r)
+            out[name] = (it, x.cpu().numpy())
+        res[device] = out
+        ctx.close()
+    for name in ("electric", "stokes", "diffusion"):
+        it_d, x_d = res[True][name]
+        it_h, x_h = res[False][name]
+        assert abs(it_d - it_h) <= 1, (name, it_d, it_h)
+        assert rel_err(x_d, x_h) < 1e-9, name
+    x_ref, _ = gmres.gmres(lambda v: sysm.electric_matvec(cfg.R, v), b_e, tol=1e-13)
+    assert rel_err(res[True]["electric"][1], x_ref) < 1e-9
+
+
 def test_errors_are_reported_not_raised_by_the_library(S):
     ctx = S.Context()
     with pytest.raises(S.ShbimError, match="no drops"):

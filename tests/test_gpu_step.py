@@ -90,6 +90,69 @@ def test_rates_match_oracle(S, precision, tol):
     ctx.close()
 
 
+def test_field_shape_rates_match_oracle(S):
+    """The quadrupole field of Section 3, E_q (-x, -y, 2z) (shbim_set_field_shape with
+    diag(-1, -1, 2)), and a random symmetric traceless shape, through shbim_rates against the oracle
+    (FP64), plus the unit-sphere closed form E_n = 5R/(2R+3) E_q n.Gn through shbim_electric_rhs."""
+    cfg = two_drops()
+    ps = [d.p for d in cfg.drops]
+    lams = [d.lam for d in cfg.drops]
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((3, 3))
+    Gr = A + A.T
+    Gr -= np.trace(Gr) / 3.0 * np.eye(3)
+    for G in (np.diag([-1.0, -1.0, 2.0]), Gr):
+        prm = P.Params(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.1, 0.0), E_q=0.8,
+                       E_G=tuple(map(tuple, G)), gmres_tol=1e-13)
+        u_ref, g_ref = P.rates([d.xcoef for d in cfg.drops], [d.gamma_coef for d in cfg.drops], ps, lams, prm)
+        ctx, x, g = setup(S, cfg, S.FP64)
+        ctx.set_field_shape(G)
+        nc = sum(sh.ncoef(p) for p in ps)
+        u = torch.empty(3 * nc, device="cuda", dtype=torch.float64)
+        gE = torch.empty(nc, device="cuda", dtype=torch.float64)
+        ctx.rates(S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.1, 0.0), E_q=0.8), g, u, gE)
+        assert rel_err(u.cpu().numpy(), np.concatenate([a.ravel() for a in u_ref])) < TOL64
+        assert rel_err(gE.cpu().numpy(), np.concatenate(g_ref)) < TOL64
+        ctx.close()
+    p, R = 12, 2.0
+    ctx = S.Context(precision=S.FP64, R=R, gmres_tol=1e-13)
+    ctx.set_drops([p], T(inputs.sphere_coef(p).ravel()), [1.0])
+    ctx.set_field_shape(Gr)
+    b = torch.empty(sh.ncoef(p), device="cuda", dtype=torch.float64)
+    ctx.electric_rhs((0.0, 0.0, 0.0), b, E_q=0.8)
+    En = torch.empty_like(b)
+    ctx.gmres_solve(S.SYS_ELECTRIC, b, En)
+    th, ph = sh.grid_points(p)
+    n = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    expect = 0.8 * 5 * R / (2 * R + 3) * (n * (Gr @ n)).sum(axis=0)
+    assert np.abs(sh.sht_inverse(En.cpu().numpy(), p, p) - expect).max() < 1e-11
+    for bad in (np.diag([1.0, 1.0, 1.0]), np.array([[0, 1.0, 0], [0, 0, 0], [0, 0, 0]])):
+        with pytest.raises(S.ShbimError):
+            ctx.set_field_shape(bad)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_stokes_rhs_matches_oracle(S, precision):
+    """shbim_stokes_rhs for the oracle's E_n: -sum_j S_j[f/Ca_E - f^E] with the charge potential, the
+    electric and the Langmuir tractions of Section 1, against the oracle's right-hand side."""
+    from oracle import operators
+    cfg = two_drops()
+    ps = [d.p for d in cfg.drops]
+    lams = [d.lam for d in cfg.drops]
+    prm = P.Params(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.2, 0.0, 1.0), gmres_tol=1e-13)
+    info = {}
+    P.rates([d.xcoef for d in cfg.drops], [d.gamma_coef for d in cfg.drops], ps, lams, prm, info=info)
+    sysm = operators.System([operators.DropGeom(d.xcoef, d.p, d.lam) for d in cfg.drops], near=True)
+    ref = -np.concatenate([a.ravel() for a in sysm.stokes_coef(info["traction"], None)])
+    ctx, x, g = setup(S, cfg, precision)
+    En = T(np.concatenate(info["En"]))
+    out = torch.empty(3 * En.numel(), device="cuda", dtype=torch.float64)
+    ctx.stokes_rhs(S.phys(R=cfg.R, Q=cfg.Q, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.2, 0.0, 1.0)), g, En, out)
+    assert rel_err(out.cpu().numpy(), ref) < TOL64
+    ctx.close()
+
+
 @pytest.fixture(scope="module")
 def rates_p12_gap01():
     """Two drops of degree 12, 0.1 apart (near pairs on both sides), and the oracle's rates."""
