@@ -138,6 +138,7 @@ class Params:
     # traceless); the quadrupole field of Section 3, phi = -E_q r^2 P_2, is diag(-1, -1, 2)
     gmres_tol: float = 1e-12
     Pe: float = math.inf        # surfactant Peclet number (infinity: no diffusion)
+    eos: str = "langmuir"       # equation of state: "langmuir" (beta, x_s) or "linear" (beta as beta_t)
 
 
 def langmuir(G, beta: float, x_s: float):
@@ -146,6 +147,22 @@ def langmuir(G, beta: float, x_s: float):
     g = (1.0 + beta * np.log(1.0 - x_s * G)) / den
     dg = (-beta * x_s / (1.0 - x_s * G)) / den
     return g, dg
+
+
+def linear_tension(G, beta_t: float):
+    """The linear equation of state of Section 1, gamma = 1 + beta_t (1 - Gamma) (normalised on the
+    equilibrium tension); returns gamma and d gamma / d Gamma."""
+    G = np.asarray(G, dtype=np.float64)
+    return 1.0 + beta_t * (1.0 - G), np.full_like(G, -beta_t)
+
+
+def tension(G, prm: "Params"):
+    """The tension law the parameters select."""
+    if prm.eos == "linear":
+        return linear_tension(G, prm.beta)
+    if prm.eos != "langmuir":
+        raise ValueError("unknown equation of state %r" % prm.eos)
+    return langmuir(G, prm.beta, prm.x_s)
 
 
 def electric_traction(En, Et, n, R: float, Q: float):
@@ -184,7 +201,7 @@ def rates(xcoefs, gcoefs, ps, lams, prm: Params, info=None, near: bool = True):
         Et = (Einf - (Einf * sg.n).sum(axis=0) * sg.n) - sg.grad(ph)
         fE = electric_traction(sg.values(e), Et, sg.n, R, prm.Q)
         Gv = sg.values(g)
-        gam, dgam = langmuir(Gv, prm.beta, prm.x_s)
+        gam, dgam = tension(Gv, prm)
         f = 2.0 * gam * sg.H * sg.n - dgam * sg.grad(g)
         t_coefs.append(sg.project(f / prm.Ca_E - fE))
     # (vi) Stokes: (lam_i+1) u - sum (lam_j-1) D_j[u] = -sum S_j[t]
