@@ -153,11 +153,13 @@ def weights_flops_per_unit(p: int) -> float:
     return 2 * (18 * ntri + 9 * (N // 4 + 1) * 2 * p) / N + 70
 
 
-def roofline(cls_ms, cls_n, cls_work, cfg, peaks):
-    """Roofline of the dominant kernel class of one step (largest summed duration in the timing pass),
-    from the method's own work: the all-pairs classes count the flops of the kernel formulas per
-    target-source pair (shbim_kernel_work), the row build the FP64 flops of the weights stage."""
-    dom = max(cls_ms, key=lambda k: cls_ms[k])
+def roofline(cls_ms, cls_n, cls_work, cfg, peaks, dom=None):
+    """Roofline of the dominant kernel class of one step (largest summed duration in the timing pass), or
+    of class `dom`, from the method's own work: the all-pairs classes count the flops of the kernel
+    formulas per target-source pair (shbim_kernel_work), the row build the FP64 flops of the weights
+    stage."""
+    if dom is None:
+        dom = max(cls_ms, key=lambda k: cls_ms[k])
     ms, n = cls_ms[dom], cls_n[dom]
     ffma = peaks["ffma"]["value"]       # measured FP32 FMA rate, TFLOP/s
     out = {"kernel_class": dom, "launches": n, "avg_launch_ms": ms / max(1, n),
@@ -171,7 +173,7 @@ def roofline(cls_ms, cls_n, cls_work, cfg, peaks):
                     "work": "flops of the kernel formulas per target-source pair (Laplace SL 11, DL 19, Stokeslet 29, "
                             "stresslet 30, both 42) x pairs of different drops per launch",
                     "kernel": "k_pairs32 / k_pairs32_queue (FP32, compensated)" if dom == "pairs_fp32"
-                              else "k_pairs_df (double-float on the FP32 pipe)"})
+                              else "k_pairs_dq (double-float terms on quantised positions, FP32 pipe)"})
         if dom == "pairs_fp64class":
             out["frac_of_fp64_nominal"] = ach / FP64_NOMINAL_TFLOPS
         return out
@@ -220,7 +222,8 @@ def run_own(args):
                 "config2": lambda: config2_leg(S, torch, dev),
                 "config3_fp64": lambda: time_to_solution_c3(S, torch, dev, fp64_full=True),
                 "config5": lambda: config5_leg(S, torch, dev),
-                "apps_config2": lambda: apps_config2(S, torch, dev)}
+                "apps_config2": lambda: apps_config2(S, torch, dev),
+                "apps_batched_p16": lambda: apps_batched_p16(S, torch, dev)}
         print(json.dumps({args.only: legs[args.only]()}))
         return
 
@@ -331,6 +334,7 @@ def run_own(args):
 
     peaks = pipe_peaks(S)
     roof = roofline(cls_ms, cls_n, cls_work, cfg, peaks)
+    roof_pairs = {k: roofline(cls_ms, cls_n, cls_work, cfg, peaks, dom=k) for k in ("pairs_fp32", "pairs_fp64class")}
     tts = time_to_solution_c3(S, torch, dev, fp64_full=args.fp64_full, ctx=ctx, cfg=cfg)
     apps_c3 = applications_by_kind(S, torch, dev, ctx, with_fp64=not args.no_fp64_apps)
     c2 = config2_leg(S, torch, dev) if not args.no_config2 else None
@@ -364,6 +368,7 @@ def run_own(args):
         "learned_warm_start": learned,
         "reparametrization": rep,
         "roofline": roof,
+        "roofline_pair_classes": roof_pairs,
         "pipe_peaks_measured": peaks,
         "clocks": clk,
         "gpu_launches": launches,
@@ -521,6 +526,20 @@ def apps_config2(S, torch, dev):
     x, _ = upload(torch, dev, cfg)
     ctx.set_drops([d.p for d in cfg.drops], x, [d.lam for d in cfg.drops])
     res = applications_by_kind(S, torch, dev, ctx, with_fp64=True)
+    ctx.close()
+    return res
+
+
+def apps_batched_p16(S, torch, dev):
+    """One application of each kernel kind (Laplace DL, SL, Stokes D, S) in FP32 and FP64-class arithmetic on
+    64 drops of degree 16 in the batched workload's box (5.4e9 cross pairs, near correction off): a short
+    program of a few hundred launches for profiling the all-pairs kernels at scale."""
+    cfg = inputs.config3(seed=3, degrees=(16,))
+    ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8)
+    ctx.set_near(False)
+    x, _ = upload(torch, dev, cfg)
+    ctx.set_drops([d.p for d in cfg.drops], x, [d.lam for d in cfg.drops])
+    res = applications_by_kind(S, torch, dev, ctx, with_fp64=False)
     ctx.close()
     return res
 
@@ -804,7 +823,7 @@ def main():
     ap.add_argument("--learned-test", type=int, default=16, help="held-out solves of the learned leg")
     ap.add_argument("--learned-epochs", type=int, default=60, help="training epochs of the learned leg")
     ap.add_argument("--only", choices=["pairs_at_scale", "peaks", "learned", "config2", "config3_fp64", "config5",
-                                       "apps_config2"],
+                                       "apps_config2", "apps_batched_p16"],
                     help="run one measurement leg alone and print its JSON")
     ap.add_argument("--serial", action="store_true",
                     help="operator applications on the caller's stream alone (no side-stream branches)")

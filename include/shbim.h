@@ -158,6 +158,23 @@ int shbim_target_geometry(shbim_ctx* ctx, double* out_dev, void* stream);
  * (relative tolerance 1e-12). Applies to shbim_electric_rhs, shbim_rates and shbim_step. */
 int shbim_set_field_shape(shbim_ctx* ctx, const double* G_host);
 
+/* Form of the FP64-class (SHBIM_PREC_DF64) all-pairs sums. On (default): for pairs of drops whose
+ * surfaces are at least 2^(19-Q) apart, positions relative to each drop's centre are split on a
+ * power-of-two quantum 2^-Q chosen per geometry (the largest offsets of the layout stay below 2^(23-Q))
+ * so that coordinate differences are exact in FP32, and the rest of each kernel term is double-float
+ * arithmetic (about 2^-42 relative per term, fewer instructions per pair); closer pairs, and every
+ * pair when off, use the general double-float form (about 2^-45 per term). */
+int shbim_set_quantized_pairs(shbim_ctx* ctx, int on);
+
+/* Equation of state of the surfactant (Section 1) used by shbim_rates, shbim_stokes_rhs and
+ * shbim_step: SHBIM_EOS_LANGMUIR (default), the Langmuir law of Eq. langmuir normalised so that
+ * gamma(1) = 1, with shbim_phys.beta and x_s; or SHBIM_EOS_LINEAR, the linear law
+ * gamma = 1 + beta_t (1 - Gamma) (Eq. lin_eq_state, tension normalised on its equilibrium value), with
+ * shbim_phys.beta read as the elasticity beta_t (x_s unused). SHBIM_ERR_ARG for any other value. */
+#define SHBIM_EOS_LANGMUIR 0
+#define SHBIM_EOS_LINEAR 1
+int shbim_set_equation_of_state(shbim_ctx* ctx, int law);
+
 /* Right-hand side of the electric system (Eq. galerkin_En): Galerkin coefficients of
  * R/(R+1) E_inf . n on every drop, for the far field E_inf(x) = E_u + E_q G x
  * (a uniform part E_u, a 3-vector read from the host, plus a linear field of strength E_q whose
@@ -225,6 +242,18 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
  * host synchronises once per cycle instead of once per step. Off, or where the graph cannot be built:
  * every step on the host as shbim_gmres_step. Both give the same iterates up to rounding. */
 int shbim_set_device_gmres(shbim_ctx* ctx, int on);
+/* Right preconditioner of the Stokes system (SHBIM_SYS_STOKES), on by default. Per drop i, with
+ * Q_i an orthonormal basis (coefficient inner product) of its six rigid-body motions (translations,
+ * and rotations e_k x x of its current shape) and r_i the radial field of the parameter sphere
+ * orthogonalised against them:
+ *   P_i^{-1} v = v/(lam_i+1) + (1/2 - 1/(lam_i+1)) Q_i Q_i^T v + (1/(2 lam_i) - 1/(lam_i+1)) r_i r_i^T v.
+ * On a closed surface the double layer reproduces rigid motions (Eq. main_eq's self part maps them to
+ * 2 u) and on a sphere maps the normal field to -1 times itself (self part 2 lam_i u); all other modes
+ * of the self part lie near lam_i + 1, so P^{-1} clusters the spectrum at 1 and GMRES needs fewer steps
+ * for drops of large or small viscosity ratio. GMRES iterates y = P x on A P^{-1}; solutions, residual
+ * checks and the refinement's residuals are those of the system itself. Rebuilt with every geometry
+ * (FP64, on the host: 7 vectors of 3 (p+1)^2 per drop). Off: plain GMRES. */
+int shbim_set_stokes_preconditioner(shbim_ctx* ctx, int on);
 int shbim_gmres_step(shbim_ctx* ctx, double* resid_host, void* stream);
 int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* stream);
 int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev,
@@ -234,7 +263,8 @@ int shbim_gmres_solve(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
  * E_n is solved with R; the traction uses Q and R (Eq. el_force, eps = 1); the capillary
  * force is scaled by 1/Ca_E (Eq. main_eq); the tension follows the Langmuir law normalised so
  * that gamma(1) = 1, gamma = (1 + beta ln(1 - x_s Gamma)) / (1 + beta ln(1 - x_s))
- * (Eq. langmuir; beta = 0 is a clean drop). The far field is E_u + E_q G x, G the context's field
+ * (Eq. langmuir; beta = 0 is a clean drop), or the linear law with beta as its elasticity
+ * (shbim_set_equation_of_state). The far field is E_u + E_q G x, G the context's field
  * shape (shbim_set_field_shape).
  * inner_tol is the FP32 inner tolerance of the refined solves used when the context's
  * precision is SHBIM_PREC_FP32_COMP (otherwise plain FP64 GMRES). */

@@ -34,6 +34,8 @@ TC_LEGENDRE = 4
 TC_ALL = 7
 CONTINUE = 0
 CONVERGED = 1
+EOS_LANGMUIR = 0
+EOS_LINEAR = 1
 
 EXPORTS = [
     "shbim_create", "shbim_destroy", "shbim_last_error", "shbim_set_precision", "shbim_set_R",
@@ -50,7 +52,8 @@ EXPORTS = [
     "shbim_near_min_distance", "shbim_set_wait_limit", "shbim_check_wait", "shbim_set_self_precision", "shbim_set_oneshot_precision",
     "shbim_kernel_work", "shbim_warm_start_feature_count", "shbim_warm_start_features", "shbim_learned_guess",
     "shbim_set_warm_start", "shbim_stokes_rhs", "shbim_set_device_gmres", "shbim_reparametrize",
-    "shbim_set_field_shape",
+    "shbim_set_field_shape", "shbim_set_equation_of_state", "shbim_set_quantized_pairs",
+    "shbim_set_stokes_preconditioner",
 ]
 PROBE_FFMA = 0
 PROBE_DFMA = 1
@@ -171,6 +174,9 @@ def lib():
         "shbim_set_device_gmres": (i32, [vp, i32]),
         "shbim_reparametrize": (i32, [vp, i32, dp, dp, vp, vp, P(dp), vp]),
         "shbim_set_field_shape": (i32, [vp, P(dp)]),
+        "shbim_set_equation_of_state": (i32, [vp, i32]),
+        "shbim_set_quantized_pairs": (i32, [vp, i32]),
+        "shbim_set_stokes_preconditioner": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -385,6 +391,19 @@ class Context:
             raise ValueError("field shape must be 3 x 3")
         g = (ctypes.c_double * 9)(*[float(v) for r in rows for v in r])
         self._check(self._L.shbim_set_field_shape(self._h, g), "shbim_set_field_shape")
+
+    def set_stokes_preconditioner(self, on: bool):
+        """shbim_set_stokes_preconditioner: right preconditioner of the Stokes system (rigid and normal modes)."""
+        self._check(self._L.shbim_set_stokes_preconditioner(self._h, 1 if on else 0),
+                    "shbim_set_stokes_preconditioner")
+
+    def set_quantized_pairs(self, on: bool):
+        """shbim_set_quantized_pairs: FP64-class pair sums on quantised positions (True) or general double-float."""
+        self._check(self._L.shbim_set_quantized_pairs(self._h, 1 if on else 0), "shbim_set_quantized_pairs")
+
+    def set_equation_of_state(self, law: int):
+        """shbim_set_equation_of_state: EOS_LANGMUIR (beta, x_s) or EOS_LINEAR (gamma = 1 + beta (1 - Gamma))."""
+        self._check(self._L.shbim_set_equation_of_state(self._h, int(law)), "shbim_set_equation_of_state")
 
     def set_diffusion(self, c: float):
         self._check(self._L.shbim_set_diffusion(self._h, float(c)), "shbim_set_diffusion")

@@ -42,6 +42,8 @@ int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
   SHBIM_CUDA(ctx, cudaMemcpy(ctx->drops_dev, dd.data(), dd.size() * sizeof(DropDev), cudaMemcpyHostToDevice));
   int rc;
   if ((rc = build_geometry(ctx, xcoef_dev, s))) return rc;
+  if ((rc = build_quantized_sources(ctx, s))) return rc;
+  if ((rc = build_stokes_preconditioner(ctx, xcoef_dev, s))) return rc;
   if ((rc = ctx->rows_prec == SHBIM_PREC_DF64 ? build_singular_rows_df(ctx, s, xcoef_dev)
                                               : build_singular_rows(ctx, xcoef_dev, s)))
     return rc;
@@ -62,6 +64,7 @@ void free_drop_state(shbim_ctx* ctx) {
   cudaFree(ctx->geo.tgt32);
   cudaFree(ctx->geo.src32);
   cudaFree(ctx->geo.src32lo);
+  cudaFree(ctx->geo.srcq);
   cudaFree(ctx->geo.tgt_drop);
   ctx->geo = Geometry{};
   cudaFree(ctx->tiles_dev);
@@ -70,6 +73,10 @@ void free_drop_state(shbim_ctx* ctx) {
   ctx->drops_dev = nullptr;
   cudaFree(ctx->lamm1_dev);
   ctx->lamm1_dev = nullptr;
+  cudaFree(ctx->prec_basis);
+  cudaFree(ctx->prec_dots);
+  cudaFree(ctx->prec_fac);
+  ctx->prec_basis = ctx->prec_dots = ctx->prec_fac = nullptr;
   cudaFree(ctx->dens_up);
   ctx->dens_up = nullptr;
   cudaFree(ctx->dens_up32);
@@ -146,6 +153,8 @@ int shbim_destroy(shbim_ctx* ctx) {
   free_drop_state(ctx);
   for (auto& kv : ctx->tables) free_degree_tables(kv.second);
   cudaFree(ctx->sht_scratch);
+  cudaFree(ctx->dq_ext_dev);
+  cudaFree(ctx->dq_far);
   cudaFree(ctx->rot_coef);
   cudaFree(ctx->wbuf);
   cudaFree(ctx->vbuf);
@@ -391,6 +400,7 @@ int shbim_set_drops(shbim_ctx* ctx, int n_drops, const int32_t* p_host, const do
       (rc = dalloc(ctx, &ctx->geo.tgt32, 7 * (size_t)to, "targets32")) ||
       (rc = dalloc(ctx, &ctx->geo.src32, 7 * (size_t)so, "sources32")) ||
       (rc = dalloc(ctx, &ctx->geo.src32lo, 7 * (size_t)so, "sources32 low parts")) ||
+      (rc = dalloc(ctx, &ctx->geo.srcq, 6 * (size_t)so, "quantised source positions")) ||
       (rc = dalloc(ctx, &ctx->geo.tgt_drop, (size_t)to, "target drop ids")) ||
       (rc = dalloc(ctx, &ctx->dens_up, 6 * (size_t)so, "source strengths")) ||
       (rc = dalloc(ctx, &ctx->dens_up32, 6 * (size_t)so, "source strengths32")) ||
@@ -828,6 +838,20 @@ int shbim_set_field_shape(shbim_ctx* ctx, const double* G_host) {
   const double g[6] = {G_host[0], 0.5 * (G_host[1] + G_host[3]), 0.5 * (G_host[2] + G_host[6]), G_host[4],
                        0.5 * (G_host[5] + G_host[7]), G_host[8]};
   std::memcpy(ctx->field_g, g, sizeof(g));
+  return SHBIM_OK;
+}
+
+int shbim_set_quantized_pairs(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->dq_pairs = on != 0;
+  ctx->geom_version++;  // captured operator graphs hold the other kernel
+  return SHBIM_OK;
+}
+
+int shbim_set_equation_of_state(shbim_ctx* ctx, int law) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  if (law != SHBIM_EOS_LANGMUIR && law != SHBIM_EOS_LINEAR) return fail(ctx, SHBIM_ERR_ARG, "unknown equation of state");
+  ctx->eos = law;
   return SHBIM_OK;
 }
 

@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <vector>
+
 #include "internal.h"
 
 namespace shbim {
@@ -265,6 +267,77 @@ __global__ void k_xupdate_k(double* __restrict__ x, const double* __restrict__ V
   x[e] = acc;
 }
 
+// ---- Stokes preconditioner (right). On drop i the self part of the Stokes system,
+// (lam_i+1) u - (lam_i-1) D_i[u], maps the six rigid-body motions of the drop to 2 u (D reproduces a
+// rigid motion on a closed surface) and, on a sphere, the normal field to 2 lam_i u (the double layer's
+// eigenvalue -1); the other modes have eigenvalues (lam_i+1) - (lam_i-1) mu with |mu| <= 3/5, clustered
+// near lam_i + 1. With Q_i an orthonormal basis of the rigid motions (coefficient inner product) and r_i
+// the unit normal mode of the parameter sphere orthogonalised against them,
+//   P_i^{-1} v = v/(lam_i+1) + (1/2 - 1/(lam_i+1)) Q_i Q_i^T v + (1/(2 lam_i) - 1/(lam_i+1)) r_i r_i^T v
+// maps those outlying eigenvalues to 1 and the cluster near 1 (P_i is the same form with the inverse
+// factors). GMRES iterates y = P x and applies A P^{-1}; the solution is x = P^{-1} y.
+
+// dots[drop][k] = basis_k . v over the drop's 3 nc coefficients (one block per drop, fixed order)
+__global__ void k_prec_dots(const double* __restrict__ v, const double* __restrict__ basis,
+                            const DropDev* __restrict__ drops, double* __restrict__ dots) {
+  __shared__ double red[7][32];
+  const DropDev D = drops[blockIdx.x];
+  const int64_t n3 = 3 * (int64_t)D.nc;
+  const double* vv = v + 3 * D.coef_off;
+  const double* B = basis + 21 * D.coef_off;
+  double acc[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) acc[k] = 0.0;
+  for (int64_t e = threadIdx.x; e < n3; e += blockDim.x) {
+    const double x = vv[e];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc[k] = fma(B[k * n3 + e], x, acc[k]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    double a = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) red[k][wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += red[threadIdx.x][w];
+    dots[7 * blockIdx.x + threadIdx.x] = a;
+  }
+}
+
+// out = f0 v + f1 Q Q^T v + f2 r r^T v per drop (f: inverse or forward factors)
+__global__ void k_prec_apply(const double* __restrict__ v, const double* __restrict__ basis,
+                             const DropDev* __restrict__ drops, const double* __restrict__ dots,
+                             const double* __restrict__ fac, int forward, double* __restrict__ out) {
+  const DropDev D = drops[blockIdx.y];
+  const int64_t n3 = 3 * (int64_t)D.nc;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n3) return;
+  const double* f = fac + 6 * blockIdx.y + (forward ? 3 : 0);
+  const double* B = basis + 21 * D.coef_off;
+  const double* z = dots + 7 * blockIdx.y;
+  double q = 0.0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) q = fma(z[k], B[k * n3 + e], q);
+  const int64_t o = 3 * D.coef_off + e;
+  out[o] = f[0] * v[o] + f[1] * q + f[2] * (z[6] * B[6 * n3 + e]);
+}
+
+int prec_apply(shbim_ctx* ctx, const double* v, double* out, bool forward, cudaStream_t s) {
+  int maxn3 = 0;
+  for (const auto& d : ctx->drops) maxn3 = std::max(maxn3, 3 * d.nc);
+  k_prec_dots<<<ctx->n_drops, 256, 0, s>>>(v, ctx->prec_basis, ctx->drops_dev, ctx->prec_dots);
+  SHBIM_CHECK_LAUNCH(ctx, "k_prec_dots");
+  k_prec_apply<<<dim3((unsigned)((maxn3 + 255) / 256), (unsigned)ctx->n_drops), 256, 0, s>>>(
+      v, ctx->prec_basis, ctx->drops_dev, ctx->prec_dots, ctx->prec_fac, forward ? 1 : 0, out);
+  SHBIM_CHECK_LAUNCH(ctx, "k_prec_apply");
+  return SHBIM_OK;
+}
+
 inline int64_t system_size(const shbim_ctx* ctx, int sys) {
   return sys == SHBIM_SYS_STOKES ? 3 * ctx->ncoef : ctx->ncoef;
 }
@@ -280,6 +353,14 @@ int matvec_eager(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
     SHBIM_CHECK_LAUNCH(ctx, "k_system");
     return SHBIM_OK;  // not a layer-operator application
   }
+  if (G.sys == SHBIM_SYS_STOKES && G.prec && !G.raw) {
+    // A P^{-1} v
+    int rc = prec_apply(ctx, v, G.tmp, false, s);
+    if (rc || (rc = shbim_eval_stokes(ctx, nullptr, G.tmp, G.Av, SHBIM_OUT_COEF, s))) return rc;
+    k_system<<<nb(G.n), 256, 0, s>>>(G.diag, G.offdiag, G.tmp, G.Av, out, G.n);
+    SHBIM_CHECK_LAUNCH(ctx, "k_system");
+    return SHBIM_OK;
+  }
   int rc = G.sys == SHBIM_SYS_ELECTRIC
                ? shbim_eval_electric(ctx, SHBIM_LAPLACE_DL, v, G.Av, SHBIM_OUT_COEF, s)
                : shbim_eval_stokes(ctx, nullptr, v, G.Av, SHBIM_OUT_COEF, s);
@@ -294,7 +375,8 @@ int matvec_eager(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
 // through fixed staging buffers) and later ones replay the graph on the caller's stream.
 int system_matvec(shbim_ctx* ctx, const double* v, double* out, cudaStream_t s) {
   auto& G = ctx->gm;
-  if (!ctx->graphs_on) return matvec_eager(ctx, v, out, s);
+  // applications of the system itself (refinement residuals) are not the captured preconditioned form
+  if (!ctx->graphs_on || G.raw) return matvec_eager(ctx, v, out, s);
   auto& GR = ctx->graphs[G.sys * 3 + ctx->opts.precision];
   if (GR.version != ctx->geom_version || GR.n != G.n) {
     if (GR.exec) cudaGraphExecDestroy(GR.exec);
@@ -560,11 +642,82 @@ int update_x(shbim_ctx* ctx, cudaStream_t s) {
 
 }  // namespace
 
+// Basis of the Stokes preconditioner for the current geometry: per drop the translations e_k (constant
+// fields, coefficient sqrt(4 pi) on Y_00), the rotations e_k x x (from the position coefficients) and
+// the parameter sphere's radial field r^ (degree 1), orthonormalised in that order in FP64 (modified
+// Gram-Schmidt, twice); factors from the drop's viscosity ratio.
+int build_stokes_preconditioner(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s) {
+  const int64_t nc_all = ctx->ncoef;
+  if (!ctx->prec_basis) {
+    if (cudaMalloc(&ctx->prec_basis, (size_t)21 * nc_all * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->prec_dots, (size_t)7 * ctx->n_drops * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->prec_fac, (size_t)6 * ctx->n_drops * sizeof(double)) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "Stokes preconditioner allocation failed");
+  }
+  std::vector<double> x((size_t)3 * nc_all), B((size_t)21 * nc_all, 0.0), F((size_t)6 * ctx->n_drops);
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(x.data(), xcoef_dev, x.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  const double s4pi = std::sqrt(4.0 * kPi), s4pi3 = std::sqrt(4.0 * kPi / 3.0);
+  for (int i = 0; i < ctx->n_drops; ++i) {
+    const Drop& d = ctx->drops[i];
+    const int64_t nc = d.nc, n3 = 3 * nc;
+    const double* xc = x.data() + 3 * d.coef_off;
+    double* b = B.data() + 21 * d.coef_off;
+    for (int k = 0; k < 3; ++k) b[k * n3 + k * nc] = s4pi;
+    for (int k = 0; k < 3; ++k) {
+      double* v = b + (3 + k) * n3;
+      const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+      // (e_k x x)_{k1} = -x_{k2}, (e_k x x)_{k2} = x_{k1}
+      for (int64_t j = 0; j < nc; ++j) {
+        v[k1 * nc + j] = -xc[k2 * nc + j];
+        v[k2 * nc + j] = xc[k1 * nc + j];
+      }
+    }
+    double* r = b + 6 * n3;
+    r[0 * nc + 3] = -s4pi3;   // x: -sqrt(4 pi/3) on the (1, 1) harmonic
+    r[1 * nc + 1] = -s4pi3;   // y: -sqrt(4 pi/3) on the (1, -1) harmonic
+    r[2 * nc + 2] = s4pi3;    // z:  sqrt(4 pi/3) on the (1, 0) harmonic
+    for (int k = 0; k < 7; ++k) {
+      double* v = b + k * n3;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int l = 0; l < k; ++l) {
+          const double* u = b + l * n3;
+          double dot = 0.0;
+          for (int64_t j = 0; j < n3; ++j) dot += u[j] * v[j];
+          for (int64_t j = 0; j < n3; ++j) v[j] -= dot * u[j];
+        }
+      double nrm = 0.0;
+      for (int64_t j = 0; j < n3; ++j) nrm += v[j] * v[j];
+      nrm = std::sqrt(nrm);
+      if (!(nrm > 1e-12)) return fail(ctx, SHBIM_ERR_ARG, "degenerate drop shape for the Stokes preconditioner");
+      for (int64_t j = 0; j < n3; ++j) v[j] /= nrm;
+    }
+    const double lam = d.lam, a = 1.0 / (lam + 1.0);
+    double* f = F.data() + 6 * i;
+    f[0] = a;
+    f[1] = 0.5 - a;
+    f[2] = 0.5 / lam - a;
+    f[3] = lam + 1.0;
+    f[4] = 2.0 - (lam + 1.0);
+    f[5] = 2.0 * lam - (lam + 1.0);
+  }
+  SHBIM_CUDA(ctx, cudaMemcpy(ctx->prec_basis, B.data(), B.size() * sizeof(double), cudaMemcpyHostToDevice));
+  SHBIM_CUDA(ctx, cudaMemcpy(ctx->prec_fac, F.data(), F.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return SHBIM_OK;
+}
+
 }  // namespace shbim
 
 using namespace shbim;
 
 extern "C" {
+
+int shbim_set_stokes_preconditioner(shbim_ctx* ctx, int on) {
+  if (!ctx) return SHBIM_ERR_ARG;
+  ctx->stokes_prec = on != 0;
+  ctx->geom_version++;  // captured applications and device cycles hold the other form
+  return SHBIM_OK;
+}
 
 int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const double* x0_dev, void* stream) {
   if (!ctx) return SHBIM_ERR_ARG;
@@ -620,10 +773,14 @@ int shbim_gmres_begin(shbim_ctx* ctx, int sys, const double* rhs_dev, const doub
     k_fill_diag<<<nb(n), 256, 0, s>>>(G.diag, ctx->drops_dev, ctx->n_drops, sys, n);
     SHBIM_CHECK_LAUNCH(ctx, "k_fill_diag");
   }
+  G.raw = false;
+  G.prec = sys == SHBIM_SYS_STOKES && ctx->stokes_prec && ctx->prec_basis;
   SHBIM_CUDA(ctx, cudaMemcpyAsync(G.b, rhs_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (x0_dev && sys == SHBIM_SYS_DIFFUSION) {  // the iterate is y = M x
     k_div<<<nb(n), 256, 0, s>>>(G.x, x0_dev, G.diag, n);
     SHBIM_CHECK_LAUNCH(ctx, "k_div");
+  } else if (x0_dev && G.prec) {  // the iterate is y = P x
+    if (int rc = prec_apply(ctx, x0_dev, G.x, true, s)) return rc;
   } else if (x0_dev) {
     SHBIM_CUDA(ctx, cudaMemcpyAsync(G.x, x0_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else {
@@ -718,6 +875,8 @@ int shbim_gmres_finish(shbim_ctx* ctx, double* x_dev, int* iters_host, void* str
   if (G.sys == SHBIM_SYS_DIFFUSION) {
     k_mul<<<nb(G.n), 256, 0, s>>>(x_dev, G.diag, G.x, G.n);
     SHBIM_CHECK_LAUNCH(ctx, "k_mul");
+  } else if (G.sys == SHBIM_SYS_STOKES && G.prec) {
+    if ((rc = prec_apply(ctx, G.x, x_dev, false, s))) return rc;
   } else {
     SHBIM_CUDA(ctx, cudaMemcpyAsync(x_dev, G.x, G.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
@@ -858,7 +1017,9 @@ extern "C" int shbim_gmres_solve_refined(shbim_ctx* ctx, int sys, const double* 
       // follow are the same as from a zero start (one for a system that finishes in one step, two
       // otherwise)
       if (outer == 0) ctx->opts.precision = SHBIM_PREC_FP32_COMP;
+      G.raw = true;
       rc = system_matvec(ctx, G.xr, G.w, s);
+      G.raw = false;
       ctx->opts.precision = ctx->outer_prec;
       if (rc) break;
       k_sub<<<nb(n), 256, 0, s>>>(rhs_dev, G.w, G.rr, n);

@@ -150,6 +150,9 @@ struct Geometry {
   float* tgt32 = nullptr;   // x y z nx ny nz  relative position + normal, each [ntarget]
   float* src32 = nullptr;   // x y z nx ny nz w, each [nsource]
   float* src32lo = nullptr; // low parts: value - (double)src32, same layout (double-float sums)
+  // positions relative to the drop centre split on the quantum 2^-Q of the FP64-class pair sums
+  // (pair_dq.cuh): [xq yq zq][xl yl zl], each [nsource]
+  float* srcq = nullptr;
   int* tgt_drop = nullptr;  // [ntarget]
   double* centres = nullptr;// [n_drops][3]
   int64_t* src_start = nullptr;  // [n_drops+1]
@@ -200,6 +203,18 @@ struct shbim_ctx {
   // shape G of the linear part of the far field E_u + E_q G x (symmetric, traceless):
   // xx, xy, xz, yy, yz, zz
   double field_g[6] = {1.0, 0.0, 0.0, -1.0, 0.0, 0.0};
+  // Stokes preconditioner (gmres.cu): per drop an orthonormal basis of its six rigid-body motions and
+  // its normal mode, [7][3 nc] at 7 * 3 coef_off (FP64, rebuilt per geometry), and the drop's factors
+  bool stokes_prec = true;
+  double* prec_basis = nullptr;
+  double* prec_dots = nullptr;    // [n_drops][7]
+  double* prec_fac = nullptr;     // [n_drops][6]: inverse (1/(lam+1), 1/2 - ., 1/(2 lam) - .), forward (lam+1, ...)
+  bool dq_pairs = true;           // FP64-class pair sums on quantised positions (k_pairs_dq) or general double-float
+  double dq_scale = 0.0;          // 2^Q of the quantised positions (0: not built for this geometry)
+  unsigned* dq_ext_dev = nullptr; // [n_drops] largest |x - c| over each drop's sources (float bits)
+  unsigned char* dq_far = nullptr; // [n_drops][n_drops]: the drop pair uses the quantised form
+  int dq_cap = 0;                 // drops the two tables above hold
+  int eos = SHBIM_EOS_LANGMUIR;      // tension law of shbim_rates / shbim_step (shbim_set_equation_of_state)
   bool refine_direct[2] = {true, true};     // refined solves (electric, Stokes): first inner solve aims at the end
   shbim_mlp* warm_net = nullptr;  // learned initial guesses of shbim_rates (shbim_set_warm_start), not owned
   const double* xcoef_cur = nullptr;  // position coefficients of the current geometry (during a rates call)
@@ -240,7 +255,9 @@ struct shbim_ctx {
     double* xr = nullptr;       // [n] refinement: outer iterate
     double* rr = nullptr;       // [n] refinement: outer residual
     double* dr = nullptr;       // [n] refinement: correction
-    double* tmp = nullptr;      // [n] diffusion system: preconditioned vector M^{-1} v
+    double* tmp = nullptr;      // [n] preconditioned vector (diffusion: M^{-1} v; Stokes: P^{-1} v)
+    bool prec = false;          // Stokes system solved right-preconditioned (iterate y = P x)
+    bool raw = false;           // the next applications are of the system itself (refinement residuals)
     double* dstate = nullptr;   // device cycle state: H [(m+1) m], cs [m], sn [m], g [m+1], y [m], scalars [8]
     int* istate = nullptr;      // device cycle state: k, total, flags, spare
     double* vstage = nullptr;   // [n] operator input staged for the device cycle
@@ -467,6 +484,10 @@ int rebuild_geometry(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
 // ---- all-pairs sums (pairs.cu)
 // the sums go to partial buffers; `before_reduce` (optional) is waited for before they are
 // added into out_accum
+// Stokes preconditioner basis and factors of the current geometry (gmres.cu)
+int build_stokes_preconditioner(shbim_ctx* ctx, const double* xcoef_dev, cudaStream_t s);
+// quantised source positions of the FP64-class pair sums (once per geometry)
+int build_quantized_sources(shbim_ctx* ctx, cudaStream_t s);
 int pairs_laplace(shbim_ctx* ctx, int which, double* out_accum, cudaStream_t s, cudaEvent_t before_reduce = nullptr);
 int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out_accum, cudaStream_t s,
                  cudaEvent_t before_reduce = nullptr);

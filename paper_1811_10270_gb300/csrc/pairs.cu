@@ -23,10 +23,13 @@
 // eps * |x0 - c_j| (drops 0.1 apart stay accurate). Each source tile is summed in FP32 and
 // added to a (hi, lo) accumulator with the two-sum of Knuth (compensated accumulation).
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "dfloat.cuh"
 #include "internal.h"
 #include "pair_df.cuh"
+#include "pair_dq.cuh"
 
 namespace shbim {
 
@@ -366,6 +369,117 @@ k_pairs_df(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops
   }
 }
 
+// FP64-class sums, per source drop either on quantised positions (pair_dq.cuh) or in general
+// double-float (pair_df.cuh): dq_far[i * n_drops + j] != 0 selects the quantised form for targets of drop
+// i against sources of drop j. Its positions are exact to ~2^-(Q+25) absolute (the FP32 remainder below
+// the quantum 2^-Q), which is double-float accuracy relative to r only for pairs at least ~2^(19-Q)
+// apart: the host sets the flag for drop pairs whose surfaces are that far apart. The choice is uniform
+// for a CTA (its targets are on one drop). Quantised copy srcq: [xq yq zq][xl yl zl], each [nsource];
+// qs = 2^Q, qi = 2^-Q.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads)
+k_pairs_dq(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
+           const double* __restrict__ tgt, int64_t ntarget, const float* __restrict__ srcq,
+           const float* __restrict__ src32, const float* __restrict__ src32lo, int64_t nsource,
+           const float* __restrict__ dens32, const float* __restrict__ dens32lo, int nsplit, int has_f, int has_u,
+           double qs, double qi, const unsigned char* __restrict__ dq_far, double* __restrict__ part) {
+  using dfl::df;
+  constexpr int NC = stokes_kind(KIND) ? 3 : 1;
+  constexpr int NV = stokes_kind(KIND) ? 6 : 2;   // float4 per staged source
+  __shared__ float4 sh[NV][kTile];
+  PairTile tile;
+  if (!sub_tile<1>(tiles, tile, blockIdx.x)) return;
+  const int i = tile.drop;
+  const DropDev Di = drops[i];
+  const int64_t other = nsource - Di.ns;
+  const int64_t chunk = (other + nsplit - 1) / nsplit;
+  const int64_t v0 = (int64_t)blockIdx.y * chunk;
+  const int64_t v1 = min(other, v0 + chunk);
+  const int64_t tg = tile.t0 + threadIdx.x;
+  const bool ok = (int)threadIdx.x < tile.nt;
+  const int64_t t = ok ? tg : tile.t0;
+  double X0[3];
+  df N0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    X0[c] = tgt[c * ntarget + t];
+    N0[c] = dfl::from_double(tgt[(3 + c) * ntarget + t]);
+  }
+  dfl::acc A[NC];
+  for (int j = 0; j < n_drops; ++j) {
+    if (j == i) continue;
+    const DropDev Dj = drops[j];
+    const SrcRange rg = drop_range(Di, Dj, i, j, v0, v1);
+    if (rg.a >= rg.b) continue;
+    const bool far = dq_far[(int64_t)i * n_drops + j] != 0;
+    const double cj[3] = {Dj.cx, Dj.cy, Dj.cz};
+    float Th[3], Tl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double v = X0[c] - cj[c];
+      const double h = far ? rint(v * qs) * qi : (double)(float)v;
+      Th[c] = (float)h;
+      Tl[c] = (float)(v - h);
+    }
+    const float* phi = far ? srcq : src32;
+    const float* plo = far ? srcq + 3 * nsource : src32lo;
+    for (int64_t base = rg.a; base < rg.b; base += kTile) {
+      const int cnt = (int)min((int64_t)kTile, rg.b - base);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt; e += kThreads) {
+        const int64_t sI = base + e;
+        const float xh = phi[sI], yh = phi[nsource + sI], zh = phi[2 * nsource + sI];
+        const float xl = plo[sI], yl = plo[nsource + sI], zl = plo[2 * nsource + sI];
+        if (!stokes_kind(KIND)) {
+          sh[0][e] = make_float4(xh, yh, zh, xl);
+          sh[1][e] = make_float4(yl, zl, dens32[sI], dens32lo[sI]);
+        } else {
+          float fv[6], uv[6];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            fv[2 * c] = has_f ? dens32[c * nsource + sI] : 0.f;
+            fv[2 * c + 1] = has_f ? dens32lo[c * nsource + sI] : 0.f;
+            uv[2 * c] = has_u ? dens32[(3 + c) * nsource + sI] : 0.f;
+            uv[2 * c + 1] = has_u ? dens32lo[(3 + c) * nsource + sI] : 0.f;
+          }
+          sh[0][e] = make_float4(xh, yh, zh, xl);
+          sh[1][e] = make_float4(yl, zl, fv[0], fv[1]);
+          sh[2][e] = make_float4(fv[2], fv[3], fv[4], fv[5]);
+          sh[3][e] = make_float4(uv[0], uv[1], uv[2], uv[3]);
+          sh[4][e] = make_float4(uv[4], uv[5], src32[3 * nsource + sI], src32lo[3 * nsource + sI]);
+          sh[5][e] = make_float4(src32[4 * nsource + sI], src32lo[4 * nsource + sI], src32[5 * nsource + sI],
+                                 src32lo[5 * nsource + sI]);
+        }
+      }
+      __syncthreads();
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (far) {
+        for (int e = 0; e < cnt; ++e) {
+          if constexpr (!stokes_kind(KIND))
+            dq_term<KIND>(Th, Tl, N0, sh[0][e], sh[1][e], z4, z4, z4, z4, A);
+          else
+            dq_term<KIND>(Th, Tl, N0, sh[0][e], sh[1][e], sh[2][e], sh[3][e], sh[4][e], sh[5][e], A);
+        }
+      } else {
+        const df T[3] = {df{Th[0], Tl[0]}, df{Th[1], Tl[1]}, df{Th[2], Tl[2]}};
+        for (int e = 0; e < cnt; ++e) {
+          if constexpr (!stokes_kind(KIND))
+            df_term<KIND>(T, N0, sh[0][e], sh[1][e], z4, z4, z4, z4, A);
+          else
+            df_term<KIND>(T, N0, sh[0][e], sh[1][e], sh[2][e], sh[3][e], sh[4][e], sh[5][e], A);
+        }
+      }
+    }
+  }
+  if (!ok) return;
+  double* P = part + (int64_t)blockIdx.y * NC * ntarget;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int64_t o = (NC == 1) ? tg : 3 * Di.tgt_off + (int64_t)c * Di.nt + (tg - Di.tgt_off);
+    P[o] = 0.07957747154594766788 * dfl::to_double(A[c].value());
+  }
+}
+
 template <int KIND, int kTPT>
 __global__ void __launch_bounds__(kThreads)
 k_pairs64(const PairTile* __restrict__ tiles, const DropDev* __restrict__ drops, int n_drops,
@@ -504,7 +618,12 @@ void launch_shape(shbim_ctx* ctx, bool has_f, bool has_u, int splits, bool queue
                                                        splits, has_f, has_u, ctx->part, nunits, ctx->pair_queue);
     return;
   }
-  if (ctx->opts.precision == SHBIM_PREC_DF64) {
+  if (ctx->opts.precision == SHBIM_PREC_DF64 && ctx->dq_pairs && ctx->dq_scale > 0.0) {
+    k_pairs_dq<KIND><<<dim3((unsigned)(ctx->tiles.size() * kMaxTPT), splits), kThreads, 0, s>>>(
+        ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt, ctx->ntarget, ctx->geo.srcq, ctx->geo.src32,
+        ctx->geo.src32lo, ctx->nsource, ctx->dens_up32, ctx->dens_up32lo, splits, has_f, has_u, ctx->dq_scale,
+        1.0 / ctx->dq_scale, ctx->dq_far, ctx->part);
+  } else if (ctx->opts.precision == SHBIM_PREC_DF64) {
     k_pairs_df<KIND><<<dim3((unsigned)(ctx->tiles.size() * kMaxTPT), splits), kThreads, 0, s>>>(
         ctx->tiles_dev, ctx->drops_dev, ctx->n_drops, ctx->geo.tgt, ctx->ntarget, ctx->geo.src32,
         ctx->geo.src32lo, ctx->nsource, ctx->dens_up32, ctx->dens_up32lo, splits, has_f, has_u, ctx->part);
@@ -604,6 +723,39 @@ int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
   return SHBIM_OK;
 }
 
+// Largest |x - c| (Euclidean) over the sources of every drop: one CTA row per drop; the maximum goes to
+// out[drop] as the bit pattern of a non-negative float (integer order = float order), rounded up.
+__global__ void k_src_extent(const double* __restrict__ src, int64_t nsource, const DropDev* __restrict__ drops,
+                             unsigned* __restrict__ out) {
+  const DropDev D = drops[blockIdx.y];
+  float m = 0.0f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < D.ns; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sI = D.src_off + e;
+    const double dx = src[sI] - D.cx, dy = src[nsource + sI] - D.cy, dz = src[2 * nsource + sI] - D.cz;
+    m = fmaxf(m, __double2float_ru(sqrt(dx * dx + dy * dy + dz * dz)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.y, __float_as_uint(m));
+}
+
+// v = x - c split as the multiple vq of qi = 2^-Q nearest to v and the FP32 remainder vl = v - vq
+__global__ void k_quantize_src(const double* __restrict__ src, int64_t nsource, const DropDev* __restrict__ drops,
+                               double qs, double qi, float* __restrict__ srcq) {
+  const DropDev D = drops[blockIdx.y];
+  const double c[3] = {D.cx, D.cy, D.cz};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < D.ns; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sI = D.src_off + e;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double v = src[k * nsource + sI] - c[k];
+      const double h = rint(v * qs) * qi;
+      srcq[k * nsource + sI] = (float)h;
+      srcq[(3 + k) * nsource + sI] = (float)(v - h);
+    }
+  }
+}
+
 }  // namespace
 
 int pairs_laplace(shbim_ctx* ctx, int which, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
@@ -618,6 +770,76 @@ int pairs_stokes(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
 }
 
 int pairs_tile_targets() { return kTileTargets; }
+
+// Quantum of the FP64-class pair sums for the current geometry (pair_dq.cuh) and the drop pairs that
+// use it. With ext_j the largest |x - c_j| of drop j's nodes, B = max over pairs of drops of
+// |c_i - c_j| (per component) + 1.01 ext_i + ext_j bounds every target offset |x0 - c_j|, every source
+// offset and every difference of the two (targets lie on the degree-p grids of the same surfaces: 1 %
+// is allowed for them). With Q = 23 - ceil(log2 B), B <= 2^(23-Q), so every quantised offset and every
+// difference of two is an integer multiple of 2^-Q below 2^24 quanta: exact in FP32. The FP32
+// remainders below the quantum are good to ~2^-(Q+23) absolute, ~2^-42 relative to r for r >= 2^(19-Q):
+// the quantised form is used for drop pairs whose surfaces are at least that far apart,
+// |c_i - c_j| - 1.01 ext_i - ext_j >= 2^(19-Q); closer pairs keep the general double-float form.
+int build_quantized_sources(shbim_ctx* ctx, cudaStream_t s) {
+  ctx->dq_scale = 0.0;
+  const int nd = ctx->n_drops;
+  if (nd < 2 || !ctx->geo.srcq) return SHBIM_OK;
+  if (ctx->dq_cap < nd) {
+    cudaFree(ctx->dq_ext_dev);
+    cudaFree(ctx->dq_far);
+    ctx->dq_ext_dev = nullptr;
+    ctx->dq_far = nullptr;
+    if (cudaMalloc(&ctx->dq_ext_dev, (size_t)nd * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&ctx->dq_far, (size_t)nd * nd) != cudaSuccess)
+      return fail(ctx, SHBIM_ERR_NOMEM, "cudaMalloc quantisation tables");
+    ctx->dq_cap = nd;
+  }
+  int maxns = 0;
+  for (const auto& d : ctx->drops) maxns = std::max(maxns, d.ns);
+  const dim3 grid((unsigned)std::min(64, (maxns + 255) / 256), (unsigned)nd);
+  SHBIM_CUDA(ctx, cudaMemsetAsync(ctx->dq_ext_dev, 0, (size_t)nd * sizeof(unsigned), s));
+  k_src_extent<<<grid, 256, 0, s>>>(ctx->geo.src, ctx->nsource, ctx->drops_dev, ctx->dq_ext_dev);
+  SHBIM_CHECK_LAUNCH(ctx, "k_src_extent");
+  std::vector<unsigned> bits(nd);
+  SHBIM_CUDA(ctx, cudaMemcpyAsync(bits.data(), ctx->dq_ext_dev, (size_t)nd * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  SHBIM_CUDA(ctx, cudaStreamSynchronize(s));
+  std::vector<double> ext(nd);
+  for (int i = 0; i < nd; ++i) {
+    float e;
+    std::memcpy(&e, &bits[i], sizeof(e));
+    ext[i] = (double)e;
+  }
+  double B = 0.0;
+  for (int i = 0; i < nd; ++i)
+    for (int j = 0; j < nd; ++j) {
+      if (i == j) continue;
+      double dc = 0.0;
+      for (int k = 0; k < 3; ++k) dc = std::max(dc, std::fabs(ctx->drops[i].centre[k] - ctx->drops[j].centre[k]));
+      B = std::max(B, dc + 1.01 * ext[i] + ext[j]);
+    }
+  if (!std::isfinite(B) || !(B > 0.0)) return fail(ctx, SHBIM_ERR_NONFINITE, "non-finite drop extent");
+  const int Q = 23 - (int)std::ceil(std::log2(B));
+  const double gap_min = std::ldexp(1.0, 19 - Q);
+  std::vector<unsigned char> far((size_t)nd * nd, 0);
+  for (int i = 0; i < nd; ++i)
+    for (int j = 0; j < nd; ++j) {
+      if (i == j) continue;
+      double d2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double dc = ctx->drops[i].centre[k] - ctx->drops[j].centre[k];
+        d2 += dc * dc;
+      }
+      far[(size_t)i * nd + j] = std::sqrt(d2) - 1.01 * ext[i] - ext[j] >= gap_min ? 1 : 0;
+    }
+  SHBIM_CUDA(ctx, cudaMemcpy(ctx->dq_far, far.data(), far.size(), cudaMemcpyHostToDevice));
+  ctx->dq_scale = std::ldexp(1.0, Q);
+  k_quantize_src<<<grid, 256, 0, s>>>(ctx->geo.src, ctx->nsource, ctx->drops_dev, ctx->dq_scale,
+                                      std::ldexp(1.0, -Q), ctx->geo.srcq);
+  SHBIM_CHECK_LAUNCH(ctx, "k_quantize_src");
+  ctx->launches += 2;
+  return SHBIM_OK;
+}
+
 
 // Operations of one kernel term in the method's formulas (add or multiply 1, fused multiply-add 2,
 // reciprocal square root 1), d = x0 - x: d 3, r^2 = d.d 5, 1/r 1, then

@@ -37,6 +37,7 @@ namespace {
 struct PhysDev {
   double R, Q, Ca_E, beta, x_s, eu0, eu1, eu2, eq, lnorm;
   double g[6];   // field shape (xx, xy, xz, yy, yz, zz): E_inf = E_u + eq G x
+  int eos;       // SHBIM_EOS_LANGMUIR or SHBIM_EOS_LINEAR (beta read as the elasticity beta_t)
 };
 
 inline unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -107,8 +108,11 @@ __global__ void k_traction(const double* __restrict__ xup, int64_t ns, const dou
   const double Et2 = Et[0] * Et[0] + Et[1] * Et[1] + Et[2] * Et[2];
   const double fn = 0.5 * ((1.0 - P.Q / (P.R * P.R)) * En * En - (1.0 - P.Q) * Et2);
   const double ft = (1.0 - P.Q / P.R) * En;
-  const double gam = (1.0 + P.beta * log(1.0 - P.x_s * Gm)) / P.lnorm;
-  const double dgam = (-P.beta * P.x_s / (1.0 - P.x_s * Gm)) / P.lnorm;
+  // tension and its derivative in Gamma: the normalised Langmuir law (Eq. langmuir) or the linear law of
+  // Section 1, gamma = 1 + beta_t (1 - Gamma)
+  const bool lin = P.eos == SHBIM_EOS_LINEAR;
+  const double gam = lin ? 1.0 + P.beta * (1.0 - Gm) : (1.0 + P.beta * log(1.0 - P.x_s * Gm)) / P.lnorm;
+  const double dgam = lin ? -P.beta : (-P.beta * P.x_s / (1.0 - P.x_s * Gm)) / P.lnorm;
   const double inv_ca = 1.0 / P.Ca_E;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -265,6 +269,7 @@ int stokes_rhs(shbim_ctx* ctx, const shbim_phys& ph, const double* gamma, const 
   PhysDev P{ph.R, ph.Q, ph.Ca_E, ph.beta, ph.x_s, ph.E_u[0], ph.E_u[1], ph.E_u[2], ph.E_q,
             1.0 + ph.beta * std::log(1.0 - ph.x_s)};
   std::memcpy(P.g, ctx->field_g, sizeof(P.g));
+  P.eos = ctx->eos;
   // fields on every drop's upsampled grid, one launch per degree
   for (const DegreeGroup& G : ctx->groups) {
     const GridTables& g = G.tab->up;

@@ -295,6 +295,48 @@ def test_double_float_singular_rows_match_fp64_rows_and_oracle(S):
                 assert rel_err(a, ref) < TOL64, key
 
 
+def test_quantized_double_float_pairs_match_fp64(S):
+    """The FP64-class pair sums on quantised positions (shbim_set_quantized_pairs, the default) and the
+    general double-float form against native FP64 sums, target by target on the grid, for every kernel
+    kind (Laplace DL and SL, Stokes S + D, S alone, D alone): two drops 0.1 apart (close pairs, ragged
+    tiles) and six small drops spread over a 40-wide box (a coarse quantum: the largest offsets set it).
+    Both forms stay within the FP64 tolerance (about 1e-11 of the largest value is measured with these
+    oscillating densities, whose terms cancel), and the quantised form is not much less accurate than
+    the general one."""
+    rng = np.random.default_rng(41)
+    close = _two_drop_cfg(12, seed=5, gap=0.1).drops
+    spread = []
+    for k, ctr in enumerate(((0, 0, 0), (19.0, -3.0, 1.0), (-18.5, 4.0, 2.0), (2.0, 19.5, -1.0),
+                             (1.0, -19.0, 18.0), (3.1, 0.2, -0.4))):
+        p = 4 + k
+        spread.append(inputs.Drop(p, inputs.perturbed_coef(p, rng, 1.0, ctr), np.zeros(sh.ncoef(p)),
+                                  0.5 + k, np.asarray(ctr, float), 1.0))
+    for drops in (close, spread):
+        nt = sum((d.p + 1) * (2 * d.p + 2) for d in drops)
+        sig = T(np.concatenate([inputs.random_density(d.p, rng)[0] for d in drops]))
+        F = T(np.concatenate([inputs.random_density(d.p, rng, 3).ravel() for d in drops]))
+        U = T(np.concatenate([inputs.random_density(d.p, rng, 3).ravel() for d in drops]))
+        res = {}
+        for key, prec, dq in (("fp64", S.FP64, True), ("df", S.DF64, False), ("dq", S.DF64, True)):
+            ctx = make(S, drops, prec, near=False)
+            ctx.set_quantized_pairs(dq)
+            outs = []
+            for which in (S.LAPLACE_DL, S.LAPLACE_SL):
+                o = torch.empty(nt, device=DEV, dtype=torch.float64)
+                ctx.eval_electric(which, sig, o, S.OUT_GRID)
+                outs.append(o.cpu().numpy())
+            for f, u in ((F, U), (F, None), (None, U)):
+                o = torch.empty(3 * nt, device=DEV, dtype=torch.float64)
+                ctx.eval_stokes(f, u, o, S.OUT_GRID)
+                outs.append(o.cpu().numpy())
+            res[key] = outs
+            ctx.close()
+        for k, (a, b, c) in enumerate(zip(res["dq"], res["fp64"], res["df"])):
+            e_dq, e_df = rel_err(a, b), rel_err(c, b)
+            assert e_dq < TOL64 and e_df < TOL64, (k, e_dq, e_df)
+            assert e_dq < 10.0 * e_df + 1e-12, (k, e_dq, e_df)
+
+
 def test_every_pair_launch_shape_matches_oracle(S):
     """Each register blocking (1, 2, 4 targets per thread) with one and several source splits, as
     a CTA per work unit and as persistent CTAs on the work counter (the same sums to the bit, also
@@ -510,6 +552,63 @@ def test_gmres_restart_and_warm_start(S):
     it2, res2 = ctx.gmres_solve(S.SYS_ELECTRIC, T(b), torch.empty_like(x), x0=x)
     assert it2 <= 1 and res2 < 1e-11
     ctx.close()
+
+
+def _spread_drops(rng, nd, p, box=2.6, min_dist=2.35):
+    """nd perturbed unit drops of degree p, centres rejection-sampled in [-box, box]^3 at least min_dist
+    apart, viscosity ratios U(0.5, 10)."""
+    centres = []
+    while len(centres) < nd:
+        c = rng.uniform(-box, box, 3)
+        if all(np.linalg.norm(c - d) > min_dist for d in centres):
+            centres.append(c)
+    return [inputs.Drop(p, inputs.perturbed_coef(p, rng, 1.0, c), np.zeros(sh.ncoef(p)), float(rng.uniform(0.5, 10.0)),
+                        np.asarray(c), 1.0) for c in centres]
+
+
+def test_stokes_preconditioner_keeps_the_solution_and_cuts_iterations(S):
+    """The right preconditioner of the Stokes system (rigid motions and normal mode per drop,
+    shbim_set_stokes_preconditioner) on eight drops of viscosity ratios U(0.5, 10): plain and
+    preconditioned GMRES reach the oracle's solution, the preconditioned one in at most 3/4 of the
+    steps; a warm start, a small Krylov space (restarts every 4 steps) and the mixed-precision refined
+    solve keep the solution."""
+    rng = np.random.default_rng(12)
+    drops = _spread_drops(rng, 8, 5)
+    sysm = oracle_system(drops, near=False)
+    b = np.concatenate([inputs.random_density(d.p, rng, 3).ravel() for d in drops])
+    ref, info = gmres.gmres(sysm.stokes_matvec, b, tol=1e-13)
+    its = {}
+    for prec in (False, True):
+        ctx = make(S, drops, S.FP64, near=False)
+        ctx.set_stokes_preconditioner(prec)
+        x = torch.empty(b.size, device=DEV, dtype=torch.float64)
+        it, res = ctx.gmres_solve(S.SYS_STOKES, T(b), x)
+        assert res < 1e-11
+        assert rel_err(x.cpu().numpy(), ref) < 1e-9
+        its[prec] = it
+        if prec:
+            # warm start from a perturbed solution
+            x0 = T(ref * (1.0 + 1e-3 * rng.standard_normal(ref.size)))
+            it2, res2 = ctx.gmres_solve(S.SYS_STOKES, T(b), x, x0=x0)
+            assert res2 < 1e-11 and it2 < it
+            assert rel_err(x.cpu().numpy(), ref) < 1e-9
+            ctx.close()
+            # restarts every 4 steps
+            ctx = S.Context(precision=S.FP64, R=2.0, gmres_tol=1e-11, gmres_restart=4)
+            ctx.set_near(False)
+            ctx.set_drops([d.p for d in drops], T(np.concatenate([d.xcoef.ravel() for d in drops])),
+                          [d.lam for d in drops])
+            it3, res3 = ctx.gmres_solve(S.SYS_STOKES, T(b), x)
+            assert res3 < 1e-11
+            assert rel_err(x.cpu().numpy(), ref) < 1e-9
+            ctx.close()
+            # refined mixed-precision solve (FP32 inner solves in one Krylov space)
+            ctx = make(S, drops, S.FP32_COMP, near=False)
+            inner, outer, r = ctx.gmres_solve_refined(S.SYS_STOKES, T(b), x, inner_tol=1e-5)
+            assert r < 1e-8
+            assert rel_err(x.cpu().numpy(), ref) < 1e-7
+        ctx.close()
+    assert its[True] <= 0.75 * its[False], its
 
 
 @pytest.mark.parametrize("restart", [50, 4])
