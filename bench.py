@@ -41,9 +41,9 @@ import inputs  # noqa: E402
 METRIC = "target-source kernel pairs/s, GMRES time-to-1e-8 per step: mixed/batched vs FP64"
 UNIT = "pairs/s"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (vector and tensor), 1/64 of the FP32 lane rate
-# DRAM bytes (read + write) per launch of the dominant kernel class from one ncu capture of the
-# same kernels on this workload; absent until a capture of the current kernels is recorded.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the pair kernel classes from one single-pass ncu capture of the
+# same kernels on this workload (profiles/); absent until a capture of the current kernels is recorded.
+TRAFFIC = {"pairs_fp32": 11.9e6, "pairs_fp64class": 46.3e6}
 WORKLOAD_NAME = ("config 3: 64 drops, p in {16,24,32,48} (seed 3), radii U(0.8,1.2), 12^3 box, gaps >= 0.2, "
                  "lambda U(0.5,10), R=2, Q=0.5, Ca_E=0.1, Langmuir beta=0.2 x_s=0.5, E=z; one midpoint time "
                  "step (Algorithm 1) = 2 x (geometry + singular rows + electric solve + potential + forces + "
@@ -223,7 +223,8 @@ def run_own(args):
                 "config3_fp64": lambda: time_to_solution_c3(S, torch, dev, fp64_full=True),
                 "config5": lambda: config5_leg(S, torch, dev),
                 "apps_config2": lambda: apps_config2(S, torch, dev),
-                "apps_batched_p16": lambda: apps_batched_p16(S, torch, dev)}
+                "apps_batched_p16": lambda: apps_batched_p16(S, torch, dev),
+                "apps_batched": lambda: apps_batched(S, torch, dev)}
         print(json.dumps({args.only: legs[args.only]()}))
         return
 
@@ -544,6 +545,18 @@ def apps_batched_p16(S, torch, dev):
     return res
 
 
+def apps_batched(S, torch, dev):
+    """One application of each kernel kind in FP32 and FP64-class arithmetic on the batched workload itself
+    (no FP64): a short program for capturing the pair kernels' DRAM traffic at full size."""
+    cfg = batched_workload()
+    ctx = S.Context(precision=S.FP32_COMP, R=cfg.R, gmres_tol=1e-8)
+    x, _ = upload(torch, dev, cfg)
+    ctx.set_drops([d.p for d in cfg.drops], x, [d.lam for d in cfg.drops])
+    res = applications_by_kind(S, torch, dev, ctx, with_fp64=False)
+    ctx.close()
+    return res
+
+
 def config5_leg(S, torch, dev):
     """16 drops of degree 64 in the quadrupole field (x, -y, 0), Pe = 10: geometry build, one mixed
     precision IMEX step (Algorithm 1) and the time to 1e-8, mixed vs FP64."""
@@ -823,7 +836,7 @@ def main():
     ap.add_argument("--learned-test", type=int, default=16, help="held-out solves of the learned leg")
     ap.add_argument("--learned-epochs", type=int, default=60, help="training epochs of the learned leg")
     ap.add_argument("--only", choices=["pairs_at_scale", "peaks", "learned", "config2", "config3_fp64", "config5",
-                                       "apps_config2", "apps_batched_p16"],
+                                       "apps_config2", "apps_batched_p16", "apps_batched"],
                     help="run one measurement leg alone and print its JSON")
     ap.add_argument("--serial", action="store_true",
                     help="operator applications on the caller's stream alone (no side-stream branches)")

@@ -844,6 +844,7 @@ int shbim_set_field_shape(shbim_ctx* ctx, const double* G_host) {
 int shbim_set_quantized_pairs(shbim_ctx* ctx, int on) {
   if (!ctx) return SHBIM_ERR_ARG;
   ctx->dq_pairs = on != 0;
+  for (auto& c : ctx->pair_cfg) c.fp64class_splits = 0;  // the other kernel's occupancy
   ctx->geom_version++;  // captured operator graphs hold the other kernel
   return SHBIM_OK;
 }

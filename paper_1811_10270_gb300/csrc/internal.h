@@ -183,6 +183,7 @@ struct shbim_ctx {
     int splits = 1;
     bool tuned = false;
     bool queue = false;           // persistent CTAs on an atomic work counter
+    int fp64class_splits = 0;     // source splits of the FP64-class kernel (0: not chosen yet)
   } pair_cfg[5];
   int* pair_queue = nullptr;      // [2] work counter and finished-CTA count (zero between launches)
   bool autotune = true;           // off: every layout keeps the default launch shape

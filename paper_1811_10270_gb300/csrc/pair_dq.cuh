@@ -12,7 +12,9 @@
 //   1/r = y + c: y = rsqrt(R) (FP32 seed, ~2^-22), rho = 1 - (R + delta) y^2 formed exactly up to
 //         ~2^-46 (1 - R y2 is exact by Sterbenz's lemma since R y2 ~ 1), c = y rho (1/2 + 3 rho/8);
 // and every product with a strength or a normal keeps its leading two-product and first-order cross
-// terms. Per term the result is good to ~2^-43 relative, as the general double-float form.
+// terms. The FP32 remainders hold the positions to ~2^-(Q+23) absolute (the general double-float form:
+// ~2^-47 of the offset), so a term is good to ~2^-(Q+23)/r relative: ~2^-42 for pairs of drops at least
+// 2^(19-Q) apart, the only ones the all-pairs kernel gives this form (pairs.cu).
 //
 // Staged source records (float4): Laplace a = (xq, yq, zq, xl), b = (yl, zl, s, s_lo); Stokes as the
 // double-float form's records with the quantised positions (pair_df.cuh). Th, Tl are the target's
@@ -28,6 +30,14 @@ struct DqGeo {
   float y, c;          // 1/r = y + c
   float y2, y2e;       // y^2 = y2 + y2e exactly
 };
+
+// FP32 reciprocal square root seed (~2^-22 relative): the approximate instruction alone; its input, a
+// squared distance between different drops' nodes, is never subnormal
+__device__ __forceinline__ float dq_rsqrt_seed(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 __device__ __forceinline__ void dq_two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -57,7 +67,7 @@ __device__ __forceinline__ void dq_geo(const float Th[3], const float Tl[3], flo
   t = __fmaf_rn(__fmaf_rn(2.0f, g.dh[1], g.dl[1]), g.dl[1], t);
   t = __fmaf_rn(__fmaf_rn(2.0f, g.dh[2], g.dl[2]), g.dl[2], t);
   const float delta = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e[0], e[1])), __fadd_rn(e[2], t));
-  const float y = rsqrtf(R);
+  const float y = dq_rsqrt_seed(R);
   const float y2 = __fmul_rn(y, y), y2e = __fmaf_rn(y, y, -y2);
   const float P = __fmul_rn(R, y2), Pe = __fmaf_rn(R, y2, -P);
   float rho = __fsub_rn(__fsub_rn(1.0f, P), Pe);

@@ -697,6 +697,36 @@ int autotune(shbim_ctx* ctx, bool has_f, bool has_u, cudaStream_t s) {
   return e == cudaSuccess ? SHBIM_OK : cuda_fail(ctx, e, "pair kernel autotune");
 }
 
+// Source splits of the FP64-class kernel: its CTAs are long (one target per thread, ~100-200 FP32
+// instructions per pair), so a grid of a few waves loses much of its last wave. The smallest split count
+// (at most the partial buffer's) that gives at least six waves of resident CTAs (occupancy query) is
+// taken, or the largest allowed if none does; chosen once per layout and kind.
+template <int KIND>
+int fp64class_splits(shbim_ctx* ctx) {
+  auto& C = ctx->pair_cfg[KIND];
+  if (C.fp64class_splits > 0) return C.fp64class_splits;
+  int dev = 0, nsm = 152, per = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const bool quant = ctx->dq_pairs && ctx->dq_scale > 0.0;
+  const cudaError_t e = quant ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_dq<KIND>, kThreads, 0)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_df<KIND>, kThreads, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    per = 1;
+  }
+  const int64_t resident = (int64_t)std::max(1, per) * nsm;
+  const int64_t units = (int64_t)ctx->tiles.size() * kMaxTPT;
+  int s = std::max(1, ctx->split_max);
+  for (int k = 1; k <= ctx->split_max; ++k)
+    if (units * k >= 6 * resident) {
+      s = k;
+      break;
+    }
+  C.fp64class_splits = std::max(s, std::min(ctx->pair_splits, ctx->split_max));
+  return C.fp64class_splits;
+}
+
 template <int KIND>
 int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream_t s, cudaEvent_t before_reduce) {
   constexpr int NC = stokes_kind(KIND) ? 3 : 1;
@@ -709,11 +739,12 @@ int launch_pairs(shbim_ctx* ctx, bool has_f, bool has_u, double* out, cudaStream
     int rc = autotune<KIND>(ctx, has_f, has_u, s);
     if (rc) return rc;
   }
-  // the FP64 and double-float kernels keep the layout's default shape (4 CTAs per tile for
-  // double-float, one target per thread)
+  // the FP64 kernels keep the layout's default shape; the FP64-class kernel (4 CTAs per tile, one target
+  // per thread) takes the split count fp64class_splits chooses for its occupancy
   const bool fp32 = ctx->opts.precision == SHBIM_PREC_FP32_COMP;
-  const int tpt = fp32 ? C.tpt : (ctx->opts.precision == SHBIM_PREC_DF64 ? 1 : 2);
-  const int splits = fp32 ? C.splits : ctx->pair_splits;
+  const bool df = ctx->opts.precision == SHBIM_PREC_DF64;
+  const int tpt = fp32 ? C.tpt : (df ? 1 : 2);
+  const int splits = fp32 ? C.splits : (df ? fp64class_splits<KIND>(ctx) : ctx->pair_splits);
   launch_raw<KIND>(ctx, has_f, has_u, tpt, splits, fp32 && C.queue, s);
   SHBIM_CHECK_LAUNCH(ctx, "k_pairs");
   if (before_reduce) SHBIM_CUDA(ctx, cudaStreamWaitEvent(s, before_reduce, 0));
