@@ -504,11 +504,13 @@ int shbim_set_self_precision(shbim_ctx* ctx, int precision);
 /* Tensor-core stages of the double-float row build (at the next shbim_set_drops), a bit mask:
  * SHBIM_TC_FOURIER, the GEMM of the rows' weights with the DFT table; SHBIM_TC_LEGENDRE, the
  * Legendre stage that follows it (used only together with SHBIM_TC_FOURIER); SHBIM_TC_ROTATION,
- * the pole rotations, one GEMM per latitude and degree. All apply for degrees p <= 39. They split
- * their operands into bfloat16 digits whose products accumulate exactly (error ~2^-40 of the sum
- * of magnitudes per output). A stage that is off, or does not fit, runs as the double-float
- * FP32-pipe kernel. Default SHBIM_TC_FOURIER | SHBIM_TC_ROTATION (the tensor-core Legendre stage
- * measured no faster than the FP32-pipe one at p = 32); any other bit is SHBIM_ERR_ARG. */
+ * the pole rotations, one GEMM per latitude and degree. The Fourier and Legendre stages apply for
+ * drops of degree p <= 39; the rotations for degrees n <= 39 of drops up to p = 52 (the higher degrees
+ * of such a drop, and every degree beyond, run on the FP32 pipe). They split their operands into
+ * bfloat16 digits whose products accumulate exactly (error ~2^-40 of the sum of magnitudes per
+ * output). A stage that is off, or does not fit, runs as the double-float FP32-pipe kernel. Default
+ * SHBIM_TC_ALL (the tensor-core Legendre stage measures as fast as the FP32-pipe one); any other bit is
+ * SHBIM_ERR_ARG. */
 #define SHBIM_TC_FOURIER 1
 #define SHBIM_TC_ROTATION 2
 #define SHBIM_TC_LEGENDRE 4

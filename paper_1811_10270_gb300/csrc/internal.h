@@ -221,7 +221,7 @@ struct shbim_ctx {
   const double* xcoef_cur = nullptr;  // position coefficients of the current geometry (during a rates call)
   bool tc_rows = true;            // double-float build: Fourier analysis on the tensor cores
   bool tc_rot = true;             // ... and the degree-block rotations (rot_tc.cu)
-  bool tc_leg = false;            // ... and the Legendre stage of the analysis (leg_tc.cu; opt-in)
+  bool tc_leg = true;             // ... and the Legendre stage of the analysis (leg_tc.cu)
   int* tc_err = nullptr;          // device flag: a tensor-core kernel timed out
   uint64_t wait_ns = 1000000000ull;  // limit of every bounded wait inside a kernel (nanoseconds)
   // workspaces
@@ -463,7 +463,8 @@ int laplace_beltrami(shbim_ctx* ctx, const double* coef, double* out, cudaStream
 // ---- tensor-core Fourier analysis of double-float rows (dft_tc.cu)
 // F[r][cs][m] = sum_k W[r][k] (cos|sin)(m phi_k), r < rows, on drop d's degree 2p+1 grid; W and F
 // double-float (float2), W rows of 2q+2 values, F rows of 2(p+1) values.
-bool rot_tc_fits(int p);
+// highest degree the tensor-core rotations take for drops of degree p (-1: none)
+int rot_tc_nmax(int p);
 int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, const std::vector<double>& theta,
                   DegreeTables& T);
 int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2* vin, int64_t in_stride, int nc,

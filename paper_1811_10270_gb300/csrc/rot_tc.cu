@@ -18,7 +18,8 @@
 // fill one of two stages and one thread issues the 21 digit products as 9 MMAs (one row digit
 // against up to three table digits, N <= 240); the epilogue combines the six
 // accumulators in double-float. Every wait is bounded; a timeout sets the error flag and the CTA
-// stops. Degrees with 2n+1 <= 80 (p <= 39) only: larger blocks use the FP32-pipe kernel.
+// stops. Degree blocks with 2n+1 <= 80 (n <= 39) only: for drops of higher degree (whose shared memory
+// still fits, p <= 48) the degrees above 39 use the FP32-pipe kernel (singular_df.cu).
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -66,22 +67,23 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __host__ __device__ inline int max_targets(int ncomp) { return kMT / ncomp + 2; }
 
 // The items of one launch: latitudes lat0 .. lat0 + L - 1 of the chunk, T tiles of 128 vectors per
-// latitude, degrees p .. 0.
+// latitude, degrees nmax .. 0 (nmax <= p: the higher degrees of a drop whose blocks exceed kNmax are
+// rotated by the double-float kernel).
 struct Items {
-  int p, nlon, ncomp, t_begin, ct, lat0, L, T;
+  int p, nmax, nlon, ncomp, t_begin, ct, lat0, L, T;
   int64_t total;
-  __host__ __device__ Items(int p_, int ncomp_, int t_begin_, int ct_)
-      : p(p_), nlon(2 * p_ + 2), ncomp(ncomp_), t_begin(t_begin_), ct(ct_) {
+  __host__ __device__ Items(int p_, int nmax_, int ncomp_, int t_begin_, int ct_)
+      : p(p_), nmax(nmax_), nlon(2 * p_ + 2), ncomp(ncomp_), t_begin(t_begin_), ct(ct_) {
     lat0 = t_begin / nlon;
     L = (t_begin + ct - 1) / nlon - lat0 + 1;
     T = (nlon * ncomp + kMT - 1) / kMT;
-    total = (int64_t)(p + 1) * L * T;
+    total = (int64_t)(nmax + 1) * L * T;
   }
   // degree, latitude and chunk-local vector range [va, vb) of an item (empty if va >= vb)
   __device__ void decode(int64_t it, int& n, int& lat, int& va, int& vb) const {
     const int64_t per_n = (int64_t)L * T;
-    n = p - (int)(it / per_n);
-    const int rem = (int)(it - (int64_t)(p - n) * per_n);
+    n = nmax - (int)(it / per_n);
+    const int rem = (int)(it - (int64_t)(nmax - n) * per_n);
     lat = lat0 + rem / T;
     const int tile = rem - (rem / T) * T;
     const int ta = max(t_begin, lat * nlon) - t_begin, tb = min(t_begin + ct, (lat + 1) * nlon) - t_begin;
@@ -101,7 +103,7 @@ struct Items {
 
 template <bool ADJ>
 __global__ void __launch_bounds__(kThreads, 1)
-k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int ct, int ncomp,
+k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int nmax, int t_begin, int ct, int ncomp,
             const float2* __restrict__ cs_phi, const uint4* __restrict__ tdig, const int* __restrict__ toff,
             const signed char* __restrict__ texp, float2* __restrict__ vout, float* __restrict__ rows_lap,
             float* __restrict__ rows_sto, int nt_drop, int* __restrict__ err, uint64_t wlim) {
@@ -119,7 +121,7 @@ k_rotate_tc(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, in
   float2* sX = reinterpret_cast<float2*>(smem + 2 * kStageBytes);
   float2* sCS = sX + kMT * WS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Items I(p, ncomp, t_begin, ct);
+  const Items I(p, nmax, ncomp, t_begin, ct);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
                  "r"(kTmemCols));
@@ -380,8 +382,15 @@ int rot_tc_smem(int p, int ncomp) {
 
 }  // namespace
 
-// the forward rotation (3 components per target) needs the most angle tables
-bool rot_tc_fits(int p) { return padded(2 * p + 1) <= kNmax && rot_tc_smem(p, 3) + 4096 <= 227 * 1024; }
+// Highest degree the tensor-core rotations take for drops of degree p (blocks up to kNmax), or -1 where
+// the shared memory of degree p does not fit (the forward rotation, 3 components per target, needs the
+// most angle tables); the degrees above it go to the double-float kernel.
+int rot_tc_nmax(int p) {
+  if (rot_tc_smem(p, 3) + 4096 > 227 * 1024) return -1;
+  int n = p;
+  while (n >= 0 && padded(2 * n + 1) > kNmax) --n;
+  return n;
+}
 
 // Digit planes of M = Dq_n^T Dz(-theta_j) Dq_n (forward, dir 0) and Dq_n^T Dz(theta_j) Dq_n
 // (adjoint, dir 1) for every base-grid latitude j and degree n, as the B operand B[m][k] = M[m][k]:
@@ -390,13 +399,14 @@ bool rot_tc_fits(int p) { return padded(2 * p + 1) <= kNmax && rot_tc_smem(p, 3)
 // digits keep ~42 bits of every row whatever its size.
 int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, const std::vector<double>& theta,
                   DegreeTables& T) {
-  if (!rot_tc_fits(p)) return SHBIM_OK;
+  const int nmax = rot_tc_nmax(p);
+  if (nmax < 0) return SHBIM_OK;
   const int P1 = p + 1;
-  std::vector<int64_t> off((size_t)2 * P1 * P1);
+  std::vector<int64_t> off((size_t)2 * P1 * P1, 0);
   int64_t total = 0;   // uint16 elements
   for (int dir = 0; dir < 2; ++dir)
     for (int j = 0; j < P1; ++j)
-      for (int n = 0; n <= p; ++n) {
+      for (int n = 0; n <= nmax; ++n) {
         off[((size_t)dir * P1 + j) * P1 + n] = total / 8;
         const int Np = padded(2 * n + 1);
         total += (int64_t)(Np / kKS) * kDig * Np * kKS;
@@ -409,7 +419,7 @@ int rot_tc_digits(shbim_ctx* ctx, int p, const std::vector<double>& D, const std
     const int dir = dj / P1, j = dj - dir * P1;
     const double a = dir == 0 ? -theta[j] : theta[j];
     std::vector<double> Z, M;
-    for (int n = 0; n <= p; ++n) {
+    for (int n = 0; n <= nmax; ++n) {
       const int w = 2 * n + 1, Np = padded(w);
       const double* Dn = &D[T.dq_off[n]];
       // Z = Dz(a) Dq_n: rows (n + m, n - m) turned by m a
@@ -476,21 +486,23 @@ int rotate_tc(shbim_ctx* ctx, const DegreeTables& T, bool adjoint, const float2*
     SHBIM_CUDA(ctx, cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), s));
   }
   const int p = T.p;
+  const int nmax = rot_tc_nmax(p);
+  if (nmax < 0) return fail(ctx, SHBIM_ERR_ARG, "degree too large for the tensor-core rotations");
   const int smem = rot_tc_smem(p, ncomp);
   int dev = 0, nsm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const Items I(p, ncomp, t_begin, ct);
+  const Items I(p, nmax, ncomp, t_begin, ct);
   const unsigned grid = (unsigned)std::min<int64_t>(I.total, nsm);
   const uint4* tdig = reinterpret_cast<const uint4*>(T.rot_digits);
   if (adjoint) {
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rotate_tc<true><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_phi_df, tdig,
+    k_rotate_tc<true><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, nmax, t_begin, ct, ncomp, T.cs_phi_df, tdig,
                                                    T.rot_toff, T.rot_exp, vout, rows_lap, rows_sto, nt_drop,
                                                    ctx->tc_err, ctx->wait_ns);
   } else {
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_rotate_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_rotate_tc<false><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, t_begin, ct, ncomp, T.cs_phi_df, tdig,
+    k_rotate_tc<false><<<grid, kThreads, smem, s>>>(vin, in_stride, nc, p, nmax, t_begin, ct, ncomp, T.cs_phi_df, tdig,
                                                     T.rot_toff, T.rot_exp, vout, rows_lap, rows_sto, nt_drop,
                                                    ctx->tc_err, ctx->wait_ns);
   }

@@ -38,14 +38,15 @@ __global__ void k_to_df(const double* __restrict__ x, int64_t n, float2* __restr
   if (e < n) st(out, e, dfl::from_double(x[e]));
 }
 
-// Rotation of all components of TPB targets per CTA, degree by degree: every stage of
+// Rotation of all components of TPB targets per CTA, degree by degree (degrees n_begin .. p; the lower
+// ones may have gone to the tensor-core kernel): every stage of
 // D_R = Dz(phi) Dq^T Dz(theta) Dq acts within a degree block, so the block Dq_n is staged in shared
 // memory once and applied to the TPB x ncomp vectors of the CTA.
 //   forward (ADJ = false): out = Dq^T Dz(-theta) Dq Dz(-phi) in   (position coefficients)
 //   adjoint (ADJ = true):  out = Dz(phi) Dq^T Dz(theta) Dq in     (rows, FP32 planes)
 template <bool ADJ>
 __global__ void __launch_bounds__(256)
-k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int t_begin, int t_count,
+k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p, int n_begin, int t_begin, int t_count,
                 int tpb, int ncomp, const float2* __restrict__ cs_theta, const float2* __restrict__ cs_phi,
                 const float2* __restrict__ dq, const int* __restrict__ dq_off, const int4* __restrict__ dq_rows,
                 const int4* __restrict__ dq_cols, float2* __restrict__ vout, float* __restrict__ rows_lap,
@@ -94,7 +95,7 @@ k_rotate_deg_df(const float2* __restrict__ vin, int64_t in_stride, int nc, int p
       st(out, v * w + m, acc.value());
     }
   };
-  for (int n = 0; n <= p; ++n) {
+  for (int n = n_begin; n <= p; ++n) {
     const int w = 2 * n + 1;
     __syncthreads();
     for (int i = threadIdx.x; i < w * w; i += blockDim.x) D[i] = dq[dq_off[n] + i];
@@ -519,7 +520,10 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
     const int budget = 46 * 1024 / (int)sizeof(float2) - 2 * N;
     const int rows = std::max(1, std::min(8, budget / (2 * N)));
     const size_t f_smem = (size_t)(2 * N + rows * 2 * N) * sizeof(float2);
-    const bool rot_tc = ctx->tc_rot && rot_tc_fits(d.p);
+    // tensor-core rotations for degrees 0 .. rot_n (all of them up to p = 39), the FP32-pipe kernel above
+    const int rot_n = ctx->tc_rot ? rot_tc_nmax(d.p) : -1;
+    const bool rot_tc = rot_n >= 0;
+    const int df_n0 = rot_n + 1;
     const int leg_smem = (d.q + 1) * 2 * (d.p + 1) * (int)sizeof(float2);
     SHBIM_CUDA(ctx, cudaFuncSetAttribute(k_analysis_leg_item_df, cudaFuncAttributeMaxDynamicSharedMemorySize, leg_smem));
     const bool dft_tc = ctx->tc_rows && dft_tc_fits(d.p);
@@ -546,10 +550,11 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
         TimeScope tr(ctx, SHBIM_K_SELF_ROTATION, st);
         if (rot_tc) {
           if ((rc = rotate_tc(ctx, *d.tab, false, xc, 0, nc, t0, ct, 3, rot, nullptr, nullptr, d.nt, st))) return rc;
-        } else {
+        }
+        if (df_n0 <= d.p) {
           k_rotate_deg_df<false><<<(ct + tpb3 - 1) / tpb3, 256, deg_smem3, st>>>(
-              xc, 0, nc, d.p, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df, d.tab->dq_off_dev,
-              d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
+              xc, 0, nc, d.p, df_n0, t0, ct, tpb3, 3, d.tab->cs_theta_df, d.tab->cs_phi_df, d.tab->dq_df,
+              d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, rot, nullptr, nullptr, d.nt);
           SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
         }
       }
@@ -585,9 +590,10 @@ int build_singular_rows_df(shbim_ctx* ctx, cudaStream_t s, const double* xcoef) 
           if ((rc = rotate_tc(ctx, *d.tab, true, vb, (int64_t)ncomp * nc, nc, t0, ct, ncomp, nullptr, d.rows_lap,
                               d.rows_sto, d.nt, st)))
             return rc;
-        } else {
+        }
+        if (df_n0 <= d.p) {
           k_rotate_deg_df<true><<<(ct + tpb14 - 1) / tpb14, 256, deg_smem14, st>>>(
-              vb, (int64_t)ncomp * nc, nc, d.p, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df,
+              vb, (int64_t)ncomp * nc, nc, d.p, df_n0, t0, ct, tpb14, ncomp, d.tab->cs_theta_df, d.tab->cs_phi_df,
               d.tab->dq_df, d.tab->dq_off_dev, d.tab->dq_rows, d.tab->dq_cols, nullptr, d.rows_lap, d.rows_sto, d.nt);
           SHBIM_CHECK_LAUNCH(ctx, "k_rotate_deg_df");
         }
