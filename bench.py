@@ -378,7 +378,7 @@ def run_own(args):
                 "d2h_bytes_per_step": int(x_h.numel() * 8 + g_h.numel() * 8)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline()
+        out["cpu_baseline"] = cpu_baseline(gpu_config1_step(S, torch, dev))
     ctx.close()
     if rank == 0:
         print(json.dumps(out))
@@ -747,15 +747,52 @@ def oracle_sample():
                    "sample_wall_s": t_geo + reg_s + sum(self_s.values())}
 
 
-def cpu_baseline():
+CONFIG1_PARAMS = dict(R=0.1, Q=1.0, Ca_E=0.1, beta=0.2, x_s=0.5, E_u=(0.0, 0.0, 1.0))
+
+
+def oracle_config1_step():
+    """One full time step of Algorithm 1 of the single unit-sphere drop (p = 16, Gamma = 1 + 0.1 Y_2^0,
+    R = 0.1, Q = 1, E = z, dt = 1e-3) by the FP64 oracle, measured in full (wall seconds)."""
+    from oracle import physics as P
+    cfg = inputs.config1(16)
+    d = cfg.drops[0]
+    prm = P.Params(gmres_tol=1e-8, **CONFIG1_PARAMS)
+    t0 = time.perf_counter()
+    P.step([d.xcoef], [d.gamma_coef], [d.p], [d.lam], 1e-3, prm, near=False)
+    return time.perf_counter() - t0
+
+
+def gpu_config1_step(S, torch, dev, steps=5):
+    """The same step on the GPU (FP64 context: one drop has no pair sums, every operator is its singular
+    rows), milliseconds per step over `steps` steps after one warm-up step."""
+    cfg = inputs.config1(16)
+    ctx = S.Context(precision=S.FP64, R=cfg.R, gmres_tol=1e-8)
+    x, g = upload(torch, dev, cfg)
+    ctx.set_drops([16], x, [1.0])
+    ph = S.phys(inner_tol=1e-5, **CONFIG1_PARAMS)
+    xo, go = torch.empty_like(x), torch.empty_like(g)
+    ctx.step(ph, x, g, 1e-3, xo, go)
+    ms, _ = cuda_time(torch, lambda: [ctx.step(ph, x, g, 1e-3, xo, go) for _ in range(steps)])
+    ctx.close()
+    return ms / steps
+
+
+def cpu_baseline(gpu_c1_ms=None):
     """The oracle on its sample (oracle_sample) with all host cores available to its BLAS calls and with
-    one thread, as pairs/s of one application of the batched workload (extrapolated)."""
+    one thread, as pairs/s of one application of the batched workload (extrapolated); beside it the
+    oracle's full time step of the single-drop workload, measured in full, against the GPU's."""
     cfg = batched_workload()
     P = pairs_per_application(cfg)
     t_all, info_all = oracle_sample()
     t_one, info_one = oracle_sample_one_thread()
     cores = threads_used()
-    return {"value": P / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+    t_c1 = oracle_config1_step()
+    c1 = {"workload": "single unit-sphere drop p=16, Gamma = 1 + 0.1 Y_2^0, R=0.1, Q=1, E=z, dt=1e-3 (config 1)",
+          "oracle_step_s": t_c1, "gpu_step_ms": gpu_c1_ms,
+          "gpu_speedup": (1e3 * t_c1 / gpu_c1_ms) if gpu_c1_ms else None,
+          "note": "one full time step of Algorithm 1 measured in full on all host threads (the oracle is "
+                  "elementwise numpy; one thread is within a few percent, see the sample above)"}
+    return {"value": P / t_all, "unit": UNIT, "cores": cores, "kind": "oracle", "config1_step": c1,
             "sample": "FP64 numpy oracle, Laplace double layer of the batched workload: one drop per degree, "
                       "regular sums at 8 targets each against the other sample drops' sources and one target's "
                       "self row each; extrapolated to one whole application (%d pairs): %.0f s on %d threads, "
