@@ -49,6 +49,29 @@ def near_pairs(system):
     return out
 
 
+def near_pairs_of(system, i: int, targets=None):
+    """The near pairs (i, t, j) of drop i's targets (all of them, or the given ones), by the same rule as
+    near_pairs; drops j whose bounding sphere (centre, largest node distance) is farther than
+    NEAR_FACTOR h_j from every target of drop i are skipped without testing their nodes."""
+    di = system.drops[i]
+    ts = np.arange(di.nt) if targets is None else np.asarray(targets, dtype=int)
+    x0 = di.x0[:, ts]
+    out = []
+    for j, dj in enumerate(system.drops):
+        if j == i:
+            continue
+        lim = NEAR_FACTOR * spacing(dj)
+        c = dj.xs.mean(axis=1)
+        rad = math.sqrt(((dj.xs - c[:, None]) ** 2).sum(axis=0).max())
+        dc = np.sqrt(((x0 - c[:, None]) ** 2).sum(axis=0))
+        cand = np.nonzero(dc < rad + lim)[0]
+        for k in cand:
+            d = dj.xs - x0[:, k:k + 1]
+            if math.sqrt((d * d).sum(axis=0).min()) < lim:
+                out.append((i, int(ts[k]), j))
+    return out
+
+
 class _Fine:
     def __init__(self, dj):
         self.q = near_degree(dj)

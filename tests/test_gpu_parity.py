@@ -462,6 +462,73 @@ def test_full_size_two_drops_sampled_targets(S, full_size_two_drops, precision, 
     ctx.close()
 
 
+@pytest.fixture(scope="module")
+def batched_sampled():
+    """The batched workload (64 drops, p 16-48, seed 3) with its oracle and sampled targets: on the first
+    drop of each degree, the first and last target and the edges of the 256- and 512-target launches,
+    plus up to four targets spread over the drop's near list (where the upsampled rule replaces the
+    degree-q one); oracle values of the Laplace double and single layers and of the Stokes
+    S[f] + (lambda - 1) D[f] there, one target at a time."""
+    from oracle import nearsing
+    cfg = inputs.config3(seed=3)
+    sysm = oracle_system(cfg.drops, near=True)
+    first = {}
+    for i, d in enumerate(cfg.drops):
+        first.setdefault(d.p, i)
+    sel, pairs = {}, []
+    for p, i in sorted(first.items()):
+        nt = sysm.drops[i].nt
+        prs = nearsing.near_pairs_of(sysm, i)
+        near_t = sorted({t for (_, t, _) in prs})
+        spread = [near_t[k] for k in np.linspace(0, len(near_t) - 1, min(4, len(near_t))).astype(int)] if near_t else []
+        sel[i] = sorted(set([0, 255, 256, 511, 512, nt - 1] + spread))
+        pairs += [pr for pr in prs if pr[1] in sel[i]]
+    assert len(pairs) >= 4
+    rng = np.random.default_rng(12)
+    sig = [inputs.random_density(d.p, rng)[0] for d in cfg.drops]
+    f = [inputs.random_density(d.p, rng, 3) for d in cfg.drops]
+    fine, ref = {}, {}
+    for i in sel:
+        ref[("ladl", i)] = nearsing.corrected_laplace_targets(sysm, "ladl", sig, i, sel[i], pairs, fine)
+        ref[("lsl", i)] = nearsing.corrected_laplace_targets(sysm, "lsl", sig, i, sel[i], pairs, fine)
+        ref[("sto", i)] = nearsing.corrected_stokes_targets(sysm, f, f, i, sel[i], pairs, fine)
+    return cfg, sel, sig, f, ref
+
+
+# FP64-class bound of the Stokes values at the batched workload: the singular rows (built in double-float
+# with tensor-core digit products, ~2^-40 of the sum of magnitudes per entry) give the self stresslet term
+# of its first p = 32 drop (lambda = 5.96, self term 80 % of the value) ~1.7e-10 relative with these
+# oscillating densities; measured 1.34e-10 for the whole value in FP64 mode
+TOL64_BATCHED_STOKES = 5e-10
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOL32), (2, TOL64)])
+def test_batched_workload_sampled_targets(S, batched_sampled, precision, tol):
+    """The bench's own workload (64 drops of degree 16-48, near correction on, the launch shapes the
+    bench uses) in each precision: target values of the Laplace double and single layers and of the
+    Stokes S[f] + (lambda - 1) D[f] at the sampled targets against the oracle (FP64 and FP64-class
+    Stokes values within TOL64_BATCHED_STOKES)."""
+    cfg, sel, sig, f, ref = batched_sampled
+    ctx = make(S, cfg.drops, precision, cfg.R, near=True)
+    nc, nt, ns = ctx.sizes()
+    offs = np.cumsum([0] + [(d.p + 1) * (2 * d.p + 2) for d in cfg.drops])
+    F = T(np.concatenate([a.ravel() for a in f]))
+    for which, kind in ((S.LAPLACE_DL, "ladl"), (S.LAPLACE_SL, "lsl")):
+        out = torch.empty(nt, device=DEV, dtype=torch.float64)
+        ctx.eval_electric(which, T(np.concatenate(sig)), out, S.OUT_GRID)
+        got = out.cpu().numpy()
+        for i in sel:
+            assert rel_err(got[offs[i]:offs[i + 1]][sel[i]], ref[(kind, i)]) < tol, (kind, i)
+    out3 = torch.empty(3 * nt, device=DEV, dtype=torch.float64)
+    ctx.eval_stokes(F, F, out3, S.OUT_GRID)
+    got = out3.cpu().numpy()
+    tol_sto = tol if precision == S.FP32_COMP else TOL64_BATCHED_STOKES
+    for i in sel:
+        n_i = offs[i + 1] - offs[i]
+        assert rel_err(got[3 * offs[i]:3 * offs[i + 1]].reshape(3, n_i)[:, sel[i]], ref[("sto", i)]) < tol_sto, i
+    ctx.close()
+
+
 @pytest.mark.parametrize("p", [44, 64])
 def test_large_degree_perturbed_drop_matches_oracle(S, p):
     """A perturbed drop above the tensor-core kernels' degree limit (p > 39: the double-float row

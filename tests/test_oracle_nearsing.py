@@ -30,6 +30,18 @@ def test_near_pairs_are_the_targets_within_six_spacings(close_pair):
     assert far and not any(t in far for (i, t, j) in pairs if i == 0)
 
 
+def test_near_pairs_of_one_drop_agree_with_the_full_list(close_pair):
+    """near_pairs_of (one drop's targets, bounding-sphere filter) gives that drop's part of near_pairs,
+    for all its targets and for a subset."""
+    sysm, drops = close_pair
+    pairs = sysm.near_pairs()
+    for i in range(2):
+        mine = sorted(pr for pr in pairs if pr[0] == i)
+        assert sorted(nearsing.near_pairs_of(sysm, i)) == mine
+        sub = sorted({t for (_, t, _) in mine[::3]} | {0, drops[i].nt - 1})
+        assert sorted(nearsing.near_pairs_of(sysm, i, sub)) == sorted(pr for pr in mine if pr[1] in sub)
+
+
 def _brute(kind, dj, x0, n0, dens_coef):
     qf = 16 * (dj.q + 1) - 1
     x, n, J = geometry.surface_on_grid(dj.xcoef, dj.p, qf)
