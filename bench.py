@@ -42,8 +42,13 @@ METRIC = "target-source kernel pairs/s, GMRES time-to-1e-8 per step: mixed/batch
 UNIT = "pairs/s"
 FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 rate (vector and tensor), 1/64 of the FP32 lane rate
 # DRAM bytes (read + write) per launch of the pair kernel classes from one single-pass ncu capture of the
-# same kernels on this workload (profiles/); absent until a capture of the current kernels is recorded.
-TRAFFIC = {"pairs_fp32": 11.9e6, "pairs_fp64class": 46.3e6}
+# same kernels on this workload (profiles/); None where the kernel has changed since its capture.
+TRAFFIC = {"pairs_fp32": 11.9e6, "pairs_fp64class": None}
+# the last capture of a class whose kernel has changed since (reported beside the null, not as traffic)
+TRAFFIC_BEFORE_CHANGE = {"pairs_fp64class": {
+    "bytes_per_launch": 46.3e6,
+    "changed_since": "k_pairs_dq's powers of 1/r now come from the renormalised pair (arithmetic only, the "
+                     "same loads); counters not taken again"}}
 WORKLOAD_NAME = ("config 3: 64 drops, p in {16,24,32,48} (seed 3), radii U(0.8,1.2), 12^3 box, gaps >= 0.2, "
                  "lambda U(0.5,10), R=2, Q=0.5, Ca_E=0.1, Langmuir beta=0.2 x_s=0.5, E=z; one midpoint time "
                  "step (Algorithm 1) = 2 x (geometry + singular rows + electric solve + potential + forces + "
@@ -165,6 +170,8 @@ def roofline(cls_ms, cls_n, cls_work, cfg, peaks, dom=None):
     out = {"kernel_class": dom, "launches": n, "avg_launch_ms": ms / max(1, n),
            "share_of_timed_kernel_time": ms / max(1e-9, sum(cls_ms.values())),
            "traffic": TRAFFIC.get(dom)}
+    if dom in TRAFFIC_BEFORE_CHANGE:
+        out["traffic_last_capture"] = TRAFFIC_BEFORE_CHANGE[dom]
     if dom in ("pairs_fp32", "pairs_fp64class"):
         ach = cls_work[dom] / (ms / 1e3) / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": ffma, "unit": "TFLOP/s", "frac": ach / ffma,
