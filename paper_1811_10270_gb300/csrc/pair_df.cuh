@@ -8,7 +8,8 @@
 //     a = (x, y, z, x_lo), b = (y_lo, z_lo, fx, fx_lo), c = (fy, fy_lo, fz, fz_lo),
 //     d = (ux, ux_lo, uy, uy_lo), e = (uz, uz_lo, nx, nx_lo), g = (ny, ny_lo, nz, nz_lo)
 // T is the target's offset from the drop centre, N0 its normal; the accumulators collect the
-// kernel sums without the 1/(4 pi).
+// kernel sums without the 1/(4 pi). Host-compilable (the CPU tests define float4 before including
+// this header and compile without FMA contraction).
 #pragma once
 
 #include "dfloat.cuh"
@@ -16,7 +17,7 @@
 namespace shbim {
 
 template <int KIND>
-__device__ __forceinline__ void df_term(const dfl::df T[3], const dfl::df N0[3], float4 a, float4 b, float4 c,
+DF_FN void df_term(const dfl::df T[3], const dfl::df N0[3], float4 a, float4 b, float4 c,
                                         float4 d, float4 e, float4 g, dfl::acc* A) {
   using dfl::df;
   const df dx = dfl::diff(T[0], df{a.x, a.w});
