@@ -70,7 +70,8 @@ def closest_point(drop, x0, fine=None, tol=1e-14, maxit=400):
     normal n(x*) and the signed distance (x0 - x*) . n(x*). Gauss-Newton on the parameter sphere: the
     step (a, b) along (theta_hat, phi_hat) solves the least-squares problem [x_theta, x_phi/sin] (a, b)
     = x0 - x, and the parameter direction moves by a theta_hat + b phi_hat (renormalised); at the
-    solution x0 - x is normal to the surface. Started from the nearest node of the upsampled grid."""
+    solution x0 - x is normal to the surface. Started from the nearest node of the grid `fine` (nodes x,
+    degree q; default the four times upsampled grid)."""
     x0 = np.asarray(x0, dtype=np.float64).ravel()
     F = nearsing._Fine(drop) if fine is None else fine
     k = int(np.argmin(((F.x - x0[:, None]) ** 2).sum(axis=0)))
@@ -160,13 +161,12 @@ class _Grid:
 
 class Source:
     """Drop j with a density of one kind: the four times upsampled grid of the near rule
-    (oracle.nearsing), the check points' grid (upsampled `up` times) and, for 'ladl', the single
-    layer's potential on S_j."""
+    (oracle.nearsing; also the closest-point search's starting nodes), the check points' grid
+    (upsampled `up` times) and, for 'ladl', the single layer's potential on S_j."""
 
     def __init__(self, drop, kind, dens, up=UP_CHECK):
         self.drop, self.kind = drop, kind
         self.dens = np.asarray(dens, dtype=np.float64)
-        self.fine = nearsing._Fine(drop)
         self.near = _Grid(drop, self.dens, nearsing.UPSAMPLE)
         self.check = self.near if up == nearsing.UPSAMPLE else _Grid(drop, self.dens, up)
         self.h = nearsing.spacing(drop)
@@ -197,7 +197,7 @@ def value(src, x0, n0=None, switch=None, t1=None, dt=None, m=None):
     switch = SWITCH if switch is None else switch
     t1, dt, m = (T1 if t1 is None else t1), (DT if dt is None else dt), (M if m is None else m)
     x0 = np.asarray(x0, dtype=np.float64).ravel()
-    th, ph, xs, ns, d = closest_point(src.drop, x0, src.fine)
+    th, ph, xs, ns, d = closest_point(src.drop, x0, src.near)
     if d < 0.0:
         raise ValueError("target inside the source drop")
     if d >= switch * src.h:
