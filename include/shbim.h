@@ -408,7 +408,7 @@ int shbim_pairs_laplace_noalloc(int which, const double* tgt_dev, int64_t n_tgt,
                                 int64_t n_src, double* out_dev, void* stream);
 
 /* ---- Learned warm start (an addition to the paper's method: the network only proposes an
- * initial guess; GMRES solves to its tolerance from there and is the judge of the error).
+ * initial guess; GMRES solves to its tolerance from there, so the residual test decides the error).
  * A multilayer perceptron h_l = tanh(bf16(h_{l-1}) bf16(W_l)^T + b_l) with a linear last
  * layer, bfloat16 weights (FP32 master copy) and FP32 accumulation on the tensor cores.
  *   widths      n_layers + 1 sizes (input, hidden..., output); max_batch rows per call
