@@ -31,3 +31,22 @@ def test_reference_arm_prints_one_line_on_rank_zero():
 
 def test_reference_arm_other_ranks_do_no_work():
     assert _run(1) == []
+
+
+def test_roofline_of_the_pair_classes():
+    """The roofline object: the dominant class by summed time, the method's flops over its time against
+    the measured FP32 rate, and DRAM traffic only where the capture is of the current kernel."""
+    import bench
+    import inputs
+    cfg = inputs.config3(seed=3)
+    peaks = {"ffma": {"value": 80.0}}
+    ms = {"pairs_fp32": 100.0, "pairs_fp64class": 300.0, "self_weights": 50.0}
+    n = {"pairs_fp32": 20, "pairs_fp64class": 10, "self_weights": 4}
+    work = {"pairs_fp32": 4.0e12, "pairs_fp64class": 6.0e12}
+    r = bench.roofline(ms, n, work, cfg, peaks)
+    assert r["kernel_class"] == "pairs_fp64class" and r["launches"] == 10
+    assert abs(r["achieved"] - 20.0) < 1e-9 and abs(r["frac"] - 0.25) < 1e-12   # 6e12 flops in 0.3 s
+    assert r["traffic"] is None and r["traffic_last_capture"]["bytes_per_launch"] > 0
+    r32 = bench.roofline(ms, n, work, cfg, peaks, dom="pairs_fp32")
+    assert abs(r32["frac"] - 0.5) < 1e-12 and r32["traffic"] == bench.TRAFFIC["pairs_fp32"]
+    assert "traffic_last_capture" not in r32
