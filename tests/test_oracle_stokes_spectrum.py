@@ -7,7 +7,9 @@ The self part of the Stokes system of a drop of viscosity ratio lambda (Eq. main
 eigenvalue 2; on the unit sphere the normal field n is an eigenfunction of D with eigenvalue -1 (the
 double layer of a uniform expansion), i.e. the eigenvalue 2 lambda. All other eigenvalues mu of D on the
 sphere lie in [-1/5, 3/5], so the self part's spectrum clusters near lambda + 1 apart from those seven
-modes, which the preconditioner maps to 1.
+modes, which the preconditioner maps to 1. The whole spectrum of both layers on the sphere follows in
+closed form from Lamb's solution (the last test), which pins the single and double layer on densities of
+every degree, tangential and normal.
 """
 import math
 
@@ -126,3 +128,43 @@ def test_preconditioner_cuts_gmres_steps_on_perturbed_drops():
     xp = Pinv(y)
     assert np.linalg.norm(xp - x) < 1e-8 * np.linalg.norm(x)
     assert info_p["iters"] <= 0.75 * info["iters"], (info_p["iters"], info["iters"])
+
+
+def _vector_harmonics(p, n, m):
+    """Cartesian coefficient arrays (3, ncoef) of Y r_hat, grad_S Y and r_hat x grad_S Y on the unit sphere
+    for the real harmonic Y = S_nm (each component has degree <= n + 1 <= p)."""
+    th, ph = sh.grid_points(p)
+    S, St, Sp = sh.basis(p, np.cos(th), np.sin(th), ph, derivs=True)
+    k = sh.idx(n, m)
+    rh = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    thh = np.stack([np.cos(th) * np.cos(ph), np.cos(th) * np.sin(ph), -np.sin(th)])
+    phh = np.stack([-np.sin(ph), np.cos(ph), np.zeros_like(ph)])
+    fields = (S[k] * rh, St[k] * thh + Sp[k] * phh, St[k] * phh - Sp[k] * thh)
+    return [np.stack([sh.sht_forward(f[i], p, p) for i in range(3)]) for f in fields]
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 0), (3, -2), (4, 3), (5, 0)])
+def test_stokes_operators_on_vector_harmonics_of_the_sphere(n, m):
+    """Closed forms on the unit sphere from Lamb's general solution (interior r^n and exterior r^-(n+1)
+    pressure harmonics with their potential flows), with the single layer continuous and its traction
+    jumping by the density (S[c] = (4/3) c fixes the factor) and the double layer jumping by 2u with
+    continuous traction (D[c] = 2c, c, 0 inside, on, outside). With den = (2n-1)(2n+1)(2n+3):
+      S[a Y r + b grad Y]: radial 2n(n+1)(2a + 3b)/den, tangential 2(3a + (2n(n+1) + 3) b)/den;
+      D[a Y r + b grad Y]: radial 3(a + 2n(n+1) b)/den, tangential 3(2a + 3b)/den;
+      S[r x grad Y] = 2/(2n+1), D[r x grad Y] = 3/(2n+1) times the field.
+    D's eigenvalues on the poloidal pair are 3/((2n-1)(2n+1)) and -3/((2n+1)(2n+3))."""
+    p, lam = 6, 3.0
+    drop = operators.DropGeom(inputs.sphere_coef(p), p, lam)
+    sysm = operators.System([drop], near=False)
+    Yr, Gy, Tor = _vector_harmonics(p, n, m)
+    S = lambda v: sysm.stokes_coef([v], None)[0]
+    D = lambda v: sysm.stokes_coef(None, [v])[0] / (lam - 1.0)
+    den = (2 * n - 1) * (2 * n + 1) * (2 * n + 3)
+    nn = n * (n + 1)
+    tol = 1e-13
+    np.testing.assert_allclose(S(Yr), 2 * nn * 2 / den * Yr + 2 * 3 / den * Gy, atol=tol)
+    np.testing.assert_allclose(S(Gy), 2 * nn * 3 / den * Yr + 2 * (2 * nn + 3) / den * Gy, atol=tol)
+    np.testing.assert_allclose(D(Yr), 3 / den * Yr + 6 / den * Gy, atol=tol)
+    np.testing.assert_allclose(D(Gy), 6 * nn / den * Yr + 9 / den * Gy, atol=tol)
+    np.testing.assert_allclose(S(Tor), 2 / (2 * n + 1) * Tor, atol=tol)
+    np.testing.assert_allclose(D(Tor), 3 / (2 * n + 1) * Tor, atol=tol)
