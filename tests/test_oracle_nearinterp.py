@@ -165,3 +165,19 @@ def test_far_targets_take_the_near_rule(sphere):
     x0 = np.array([0.0, 0.6, 0.8]) * (1.0 + 1.5 * ss.h)
     assert np.array_equal(NI.value(ss, x0)[0], ss.upsampled(x0[:, None])[:, 0])
     assert nearsing.UPSAMPLE == 4
+
+
+def test_near_rule_is_at_rounding_from_two_spacings(sphere):
+    """The library applies the four times upsampled rule at every near target; from d = 2 h_j on (the
+    workloads keep targets at least 2.6 h_j from other drops) it agrees with the closed forms to rounding."""
+    drop, lap, cv, ss, sd = sphere
+    rng = np.random.default_rng(6)
+    for dd in (2.0, 2.6):
+        for _ in range(3):
+            v, n0 = _unit(rng), _unit(rng)
+            x0 = v * (1.0 + dd * ss.h)
+            for n, (c, sl, fl) in lap.items():
+                assert abs(float(sl.upsampled(x0[:, None])[0]) - exact_single_layer(n, c, x0)) < 1e-13
+                assert abs(float(fl.upsampled(x0[:, None], n0)[0]) - exact_field(n, c, x0) @ n0) < 1e-13
+            assert np.abs(ss.upsampled(x0[:, None])[:, 0] - exact_stokeslet_of_constant(cv, x0)).max() < 1e-13
+            assert np.abs(sd.upsampled(x0[:, None])[:, 0]).max() < 1e-12
