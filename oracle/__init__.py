@@ -15,6 +15,13 @@ Modules:
                (Eqs. op_stokes, dl_op_laplace, BIM_galerkin, galerkin_En)
     gmres      restarted GMRES used to solve the Galerkin systems
     nearsing   nearly-singular correction by upsampling (Section 2.1)
+    nearinterp the interpolation step of the nearly-singular method for the closest targets
+               (Section 2.1, last paragraph)
+    fastrot    band-limited fields on the rotated grids of all targets of a latitude by FFTs, and
+               the singular rule built on them (Section 2.1, the fast all-target rotation)
     physics    forces, rates and the midpoint time step (Section 1, Algorithm 1)
+    reparam    the reparametrisation of the surfaces (Section 2.2)
+    upsampling adaptive upsampling from the mean curvature's spectrum (Section 2)
+    spt        small-deformation theory (Section 3, Appendix)
     mlp        the warm-start network (forward, backward, Adam)
 """
