@@ -10,7 +10,7 @@ import pytest
 from scipy.special import sph_harm_y
 
 import inputs
-from oracle import geometry, gmres, operators, quadrature, sh
+from oracle import geometry, gmres, operators, physics, quadrature, sh
 
 
 # --------------------------------------------------------------------------- basis / SHT
@@ -218,6 +218,26 @@ def test_electric_solution_unit_sphere(R):
     En = sh.sht_inverse(x, p, p)
     np.testing.assert_allclose(En, 3 * R / (R + 2) * (E[:, None] * sysm.drops[0].n0).sum(axis=0),
                                atol=1e-13)
+
+
+@pytest.mark.parametrize("R", [0.1, 2.0])
+def test_electric_solution_unit_sphere_linear_field(R):
+    """A linear far field E = G x (G symmetric, traceless: the quadrupole (-x, -y, 2z) and (x, -y, 0)) on
+    the unit sphere, through the field-shape path of the rates: its normal component is a degree-2
+    harmonic, the outer potential -r^2 h/2 + B r^-3 h with interior A r^2 h, and continuity of the potential
+    and of the current (R times the interior normal field) give E_n = 5R/(2R+3) E . n (degree l in
+    general: (2l+1) R / (l R + l + 1), 3R/(R+2) for the uniform field)."""
+    p = 6
+    for G in (np.diag([-1.0, -1.0, 2.0]), np.diag([1.0, -1.0, 0.0])):
+        prm = physics.Params(R=R, Q=0.5, E_u=(0.0, 0.0, 0.0), E_q=0.7, E_G=tuple(map(tuple, G)),
+                             gmres_tol=1e-13)
+        info = {}
+        physics.rates([inputs.sphere_coef(p)], [np.zeros(sh.ncoef(p))], [p], [1.0], prm, info=info,
+                      near=False)
+        d = operators.DropGeom(inputs.sphere_coef(p), p)
+        En = sh.sht_inverse(info["En"][0], p, p)
+        En_exact = 5.0 * R / (2.0 * R + 3.0) * 0.7 * ((G @ d.x0) * d.n0).sum(axis=0)
+        np.testing.assert_allclose(En, En_exact, atol=1e-12)
 
 
 def test_stokes_rigid_motion_is_a_solution_for_lambda_one_source():
